@@ -1,0 +1,894 @@
+// DQO-MAP hot-path oracle: a plain, slow FP64 CPU restatement of what the GPU path
+// computes.  TEST INFRASTRUCTURE ONLY: it is linked by the tests, the smoke check and
+// the bench's CPU-baseline leg, never by the library.  It shares no code, header,
+// table or constant generator with the CUDA path.
+//
+// What it follows (DQO-MAP, arXiv 2503.02223):
+//   * Sec. III-A Eq. 1-3: dual quadric Q* of an ellipsoid (centre, rotation, semi-axes).
+//   * Sec. III-B Eq. 4: image dual conic C* = P Q* P^T (the printed P^T Q* P is
+//     dimensionally impossible for a 3x4 P; the 3x3 reading is used).
+//   * Sec. III-D Eq. 12: bbox loss over the frames observing an object, read as
+//     sum (1 - IoU(BBox(C*), BBox_obs)).
+//   * Sec. III-D Eq. 7-10, 15: colour, depth and instance losses of the Gaussian-splatting
+//     render; ins = sum of blend weights of the pixel's own object's opaque Gaussians.
+//   * Sec. IV (impl.): "CUDA kernels for rasterization and back propagation" -- the
+//     rasterizer is the 3D Gaussian Splatting one the paper builds on (Sec. I, II-B);
+//     its unstated constants are the settings struct below.
+//
+// Conventions (readings where the paper is silent):
+//   pixel (u,v) centre at integer (u,v); u = fx x/z + cx.
+//   Gaussian: p_c = R_view mean + t_view; Sigma = R(q) diag(exp(2 s)) R(q)^T (q normalised);
+//   Sigma' = J W Sigma W^T J^T + lowpass I; conic = Sigma'^-1; radius = ceil(k sqrt(lmax)).
+//   Tile membership: tile contains a pixel centre inside [x-r, x+r] x [y-r, y+r].
+//   Per pixel: tile's Gaussians sorted by (z, index); alpha = min(clamp, o exp(power));
+//   skip alpha < alpha_min; stop before the Gaussian that would make T(1-alpha) < t_stop.
+//   C = sum w c + T_final bg; D = sum w z; A = sum w; ins = sum over Gaussians of the
+//   pixel's labelled object (opaque ones if og_filter) of w; id = argmax_k W_k.
+//   Losses (mean over H*W pixels, labelled pixels only): L1 colour, L1 depth (where the
+//   target depth > 0), L1 of (ins - 1); total = rgb + depth + lambda * ins.
+//   The derivative of |x| is sign(x) with sign(0) = 0.
+//
+// Quadric: params (centre xyz, log a b c, rotation vector); Q* = Z diag(a^2,b^2,c^2,-1) Z^T,
+//   Z = [R t; 0 1].  BBox(C*) from the vertical / horizontal tangent lines l with
+//   l^T C* l = 0.  A pair is valid iff c33 < 0, the centre is in front and both
+//   discriminants are positive; invalid pairs are left out of the loss.
+//   Gradients of the quadric loss are computed by forward-mode dual numbers run through
+//   the same forward code (an exact derivative, no hand-derived adjoint).
+//
+// Parity pins live in tests/: closed-form single Gaussian, sphere-quadric radius,
+// silhouette brute force, invariants, tiled vs per-pixel brute force, finite
+// differences of every gradient.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+extern "C" {
+
+struct OSettings {
+    int32_t tile_w, tile_h;
+    double alpha_clamp;   // alpha = min(alpha_clamp, o G)
+    double alpha_min;     // skip if alpha < alpha_min
+    double t_stop;        // stop before T (1 - alpha) < t_stop
+    double znear;         // cull if z < znear
+    double lowpass;       // added to the 2D covariance diagonal (px^2)
+    double radius_sigma;  // radius = ceil(radius_sigma * sqrt(lambda_max))
+    double lambda_ins;    // weight of the instance loss (Eq. 10)
+    double bg[3];         // background colour
+    int32_t og_filter;    // 1: only opaque (flag bit0) Gaussians count toward ins (Eq. 15)
+    int32_t num_objects;  // object ids outside [0, num_objects) carry no object
+    double amb_rel;       // relative margin for flagging threshold decisions
+    double amb_px;        // pixel margin for flagging tile-membership decisions
+};
+
+struct OCamera {
+    double fx, fy, cx, cy;
+    int32_t width, height;
+    double viewmat[12];  // row-major [R | t], world -> camera
+};
+
+}  // extern "C"
+
+namespace {
+
+// ------------------------------------------------------------------ projection (per Gaussian)
+
+struct Proj {
+    bool visible = false;
+    bool ambiguous = false;    // a discrete decision is within the flagging margin
+    double pc[3] = {0, 0, 0};  // camera-space mean
+    double xy[2] = {0, 0};
+    double cov2[3] = {0, 0, 0};   // Sigma' entries (A, B, C)
+    double conic[3] = {0, 0, 0};  // Sigma'^-1 entries (a, b, c)
+    double opac = 0;
+    double lmax = 0;
+    int radius = 0;
+    int rect[4] = {0, 0, 0, 0};   // tx0, ty0, tx1, ty1 (exclusive); empty if invisible
+    int urect[4] = {0, 0, 0, 0};  // union of rects over the flagging perturbations
+    int irect[4] = {0, 0, 0, 0};  // their intersection (empty if any of them is empty)
+    double S3[3][3];              // world-space 3D covariance
+    double Rq[3][3];              // rotation from the normalised quaternion
+    double qn[4];                 // normalised quaternion
+    double qnorm = 1;
+    double s[3];                  // exp(log_scales)
+    double T2[2][3];              // J W
+    double J[2][3];
+};
+
+void quat_to_rot(const double q[4], double R[3][3]) {
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0][0] = 1 - 2 * (y * y + z * z); R[0][1] = 2 * (x * y - w * z);     R[0][2] = 2 * (x * z + w * y);
+    R[1][0] = 2 * (x * y + w * z);     R[1][1] = 1 - 2 * (x * x + z * z); R[1][2] = 2 * (y * z - w * x);
+    R[2][0] = 2 * (x * z - w * y);     R[2][1] = 2 * (y * z + w * x);     R[2][2] = 1 - 2 * (x * x + y * y);
+}
+
+// Tiles containing a pixel centre inside the square [x-r, x+r] x [y-r, y+r].
+bool tile_rect(double x, double y, double r, const OSettings& st, const OCamera& cam, int rect[4]) {
+    double ulo = std::ceil(x - r), uhi = std::floor(x + r);
+    double vlo = std::ceil(y - r), vhi = std::floor(y + r);
+    if (ulo < 0) ulo = 0;
+    if (vlo < 0) vlo = 0;
+    if (uhi > cam.width - 1) uhi = cam.width - 1;
+    if (vhi > cam.height - 1) vhi = cam.height - 1;
+    if (ulo > uhi || vlo > vhi) { rect[0] = rect[1] = rect[2] = rect[3] = 0; return false; }
+    rect[0] = (int)ulo / st.tile_w;
+    rect[1] = (int)vlo / st.tile_h;
+    rect[2] = (int)uhi / st.tile_w + 1;
+    rect[3] = (int)vhi / st.tile_h + 1;
+    return true;
+}
+
+Proj project_gaussian(const OSettings& st, const OCamera& cam, const double* mean,
+                      const double* log_scale, const double* quat, double opacity_logit) {
+    Proj P;
+    const double* V = cam.viewmat;
+    for (int i = 0; i < 3; ++i)
+        P.pc[i] = V[4 * i + 0] * mean[0] + V[4 * i + 1] * mean[1] + V[4 * i + 2] * mean[2] + V[4 * i + 3];
+    const double x = P.pc[0], y = P.pc[1], z = P.pc[2];
+    if (!(z >= st.znear)) {
+        P.ambiguous = std::fabs(z - st.znear) <= st.amb_rel * st.znear;
+        return P;
+    }
+    // 3D covariance from the normalised quaternion and exponentiated scales
+    double qq = 0;
+    for (int i = 0; i < 4; ++i) qq += quat[i] * quat[i];
+    P.qnorm = std::sqrt(qq);
+    for (int i = 0; i < 4; ++i) P.qn[i] = quat[i] / P.qnorm;
+    quat_to_rot(P.qn, P.Rq);
+    for (int i = 0; i < 3; ++i) P.s[i] = std::exp(log_scale[i]);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0;
+            for (int k = 0; k < 3; ++k) acc += P.Rq[i][k] * P.s[k] * P.s[k] * P.Rq[j][k];
+            P.S3[i][j] = acc;
+        }
+    // EWA: Jacobian of (fx x/z + cx, fy y/z + cy) at the camera-space mean
+    P.J[0][0] = cam.fx / z; P.J[0][1] = 0;           P.J[0][2] = -cam.fx * x / (z * z);
+    P.J[1][0] = 0;          P.J[1][1] = cam.fy / z;  P.J[1][2] = -cam.fy * y / (z * z);
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0;
+            for (int k = 0; k < 3; ++k) acc += P.J[i][k] * V[4 * k + j];
+            P.T2[i][j] = acc;
+        }
+    double C2[2][2];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            double acc = 0;
+            for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l) acc += P.T2[i][k] * P.S3[k][l] * P.T2[j][l];
+            C2[i][j] = acc;
+        }
+    P.cov2[0] = C2[0][0] + st.lowpass;
+    P.cov2[1] = 0.5 * (C2[0][1] + C2[1][0]);
+    P.cov2[2] = C2[1][1] + st.lowpass;
+    const double det = P.cov2[0] * P.cov2[2] - P.cov2[1] * P.cov2[1];
+    if (!(det > 0)) return P;
+    P.conic[0] = P.cov2[2] / det;
+    P.conic[1] = -P.cov2[1] / det;
+    P.conic[2] = P.cov2[0] / det;
+    const double mid = 0.5 * (P.cov2[0] + P.cov2[2]);
+    P.lmax = mid + std::sqrt(std::max(0.0, mid * mid - det));
+    const double rr = st.radius_sigma * std::sqrt(P.lmax);
+    P.radius = (int)std::ceil(rr);
+    P.xy[0] = cam.fx * x / z + cam.cx;
+    P.xy[1] = cam.fy * y / z + cam.cy;
+    P.opac = 1.0 / (1.0 + std::exp(-opacity_logit));
+    P.visible = tile_rect(P.xy[0], P.xy[1], P.radius, st, cam, P.rect);
+
+    // Flag decisions that single precision may take the other way: the radius rounding,
+    // and the tile rect under a shift of the centre by amb_px.
+    int rlo = (int)std::ceil(rr * (1 - st.amb_rel)), rhi = (int)std::ceil(rr * (1 + st.amb_rel));
+    bool amb = (rlo != P.radius) || (rhi != P.radius) ||
+               std::fabs(z - st.znear) <= st.amb_rel * st.znear;
+    int u[4] = {P.rect[0], P.rect[1], P.rect[2], P.rect[3]};
+    int in4[4] = {P.rect[0], P.rect[1], P.rect[2], P.rect[3]};
+    bool all = P.visible;
+    bool any = P.visible;
+    for (int rad : {rlo, rhi}) {
+        for (int dxs = -1; dxs <= 1; ++dxs)
+            for (int dys = -1; dys <= 1; ++dys) {
+                int r2[4];
+                bool v2 = tile_rect(P.xy[0] + dxs * st.amb_px, P.xy[1] + dys * st.amb_px, rad, st, cam, r2);
+                if (v2 != P.visible || (v2 && (r2[0] != P.rect[0] || r2[1] != P.rect[1] ||
+                                               r2[2] != P.rect[2] || r2[3] != P.rect[3])))
+                    amb = true;
+                if (v2) {
+                    if (!any) { for (int k = 0; k < 4; ++k) u[k] = r2[k]; any = true; }
+                    u[0] = std::min(u[0], r2[0]); u[1] = std::min(u[1], r2[1]);
+                    u[2] = std::max(u[2], r2[2]); u[3] = std::max(u[3], r2[3]);
+                    in4[0] = std::max(in4[0], r2[0]); in4[1] = std::max(in4[1], r2[1]);
+                    in4[2] = std::min(in4[2], r2[2]); in4[3] = std::min(in4[3], r2[3]);
+                } else {
+                    all = false;
+                }
+            }
+    }
+    P.ambiguous = amb;
+    for (int k = 0; k < 4; ++k) P.urect[k] = any ? u[k] : 0;
+    for (int k = 0; k < 4; ++k) P.irect[k] = all ? in4[k] : 0;
+    return P;
+}
+
+struct Inputs {
+    int64_t n;
+    const double *means, *log_scales, *quats, *opacity_logit, *rgb;
+    const int32_t* obj_id;
+    const uint8_t* flags;
+};
+
+std::vector<Proj> project_all(const OSettings& st, const OCamera& cam, const Inputs& in) {
+    std::vector<Proj> pr((size_t)in.n);
+    for (int64_t i = 0; i < in.n; ++i)
+        pr[i] = project_gaussian(st, cam, in.means + 3 * i, in.log_scales + 3 * i, in.quats + 4 * i,
+                                 in.opacity_logit[i]);
+    return pr;
+}
+
+bool covers(const int rect[4], int tx, int ty) {
+    return tx >= rect[0] && tx < rect[2] && ty >= rect[1] && ty < rect[3];
+}
+
+// Gaussians whose rect covers tile (tx,ty), in ascending (z, index) order.
+std::vector<int64_t> tile_list(const std::vector<Proj>& pr, int tx, int ty) {
+    std::vector<int64_t> L;
+    for (int64_t i = 0; i < (int64_t)pr.size(); ++i)
+        if (pr[i].visible && covers(pr[i].rect, tx, ty)) L.push_back(i);
+    std::stable_sort(L.begin(), L.end(), [&](int64_t a, int64_t b) {
+        if (pr[a].pc[2] != pr[b].pc[2]) return pr[a].pc[2] < pr[b].pc[2];
+        return a < b;
+    });
+    return L;
+}
+
+// ------------------------------------------------------------------ per-pixel blending
+
+struct Contrib {
+    int64_t g;
+    double alpha, T, G, dx, dy;
+    bool clamped;
+};
+
+struct PixelResult {
+    double C[3] = {0, 0, 0}, D = 0, A = 0, ins = 0, T = 1;
+    int64_t n_contrib = 0;  // 1 + list position of the last blended Gaussian
+    int32_t id = -1;
+    double id_margin = 0;
+    uint8_t amb = 0;        // bit0 threshold, bit1 depth tie, bit2 tile membership, bit3 loss kink
+    std::vector<Contrib> contribs;
+};
+
+const uint8_t AMB_THRESH = 1, AMB_DEPTH = 2, AMB_RECT = 4, AMB_KINK = 8;
+
+bool near_rel(double a, double b, double rel) { return std::fabs(a - b) <= rel * std::fabs(b); }
+
+PixelResult blend_pixel(const OSettings& st, const Inputs& in, const std::vector<Proj>& pr,
+                        const std::vector<int64_t>& L, int px, int py, int32_t gt, bool keep) {
+    PixelResult R;
+    std::vector<double> Wk(st.num_objects > 0 ? st.num_objects : 0, 0.0);
+    double T = 1.0;
+    double last_z = -1;
+    for (size_t j = 0; j < L.size(); ++j) {
+        const int64_t g = L[j];
+        const Proj& P = pr[g];
+        const double dx = px - P.xy[0], dy = py - P.xy[1];
+        const double power = -0.5 * (P.conic[0] * dx * dx + P.conic[2] * dy * dy) - P.conic[1] * dx * dy;
+        if (power > 0) continue;
+        const double G = std::exp(power);
+        const double oG = P.opac * G;
+        bool clamped = oG > st.alpha_clamp;
+        const double alpha = clamped ? st.alpha_clamp : oG;
+        if (near_rel(oG, st.alpha_clamp, st.amb_rel)) R.amb |= AMB_THRESH;
+        if (near_rel(alpha, st.alpha_min, st.amb_rel)) R.amb |= AMB_THRESH;
+        if (alpha < st.alpha_min) continue;
+        const double Tn = T * (1 - alpha);
+        if (near_rel(Tn, st.t_stop, st.amb_rel)) R.amb |= AMB_THRESH;
+        if (Tn < st.t_stop) break;
+        if (last_z >= 0 && std::fabs(P.pc[2] - last_z) <= 1e-6 * P.pc[2]) R.amb |= AMB_DEPTH;
+        last_z = P.pc[2];
+        const double w = alpha * T;
+        for (int c = 0; c < 3; ++c) R.C[c] += w * in.rgb[3 * g + c];
+        R.D += w * P.pc[2];
+        R.A += w;
+        const int32_t id = in.obj_id[g];
+        const bool has_obj = id >= 0 && id < st.num_objects;
+        if (has_obj) {
+            Wk[id] += w;
+            const bool og = !st.og_filter || (in.flags[g] & 1);
+            if (og && id == gt) R.ins += w;
+        }
+        if (keep) R.contribs.push_back({g, alpha, T, G, dx, dy, clamped});
+        T = Tn;
+        R.n_contrib = (int64_t)j + 1;
+    }
+    R.T = T;
+    for (int c = 0; c < 3; ++c) R.C[c] += T * st.bg[c];
+    // argmax over objects, ties to the smallest id, -1 if nothing was blended
+    double best = 0, second = 0;
+    for (int k = 0; k < st.num_objects; ++k) {
+        if (Wk[k] > best) { second = best; best = Wk[k]; R.id = k; }
+        else if (Wk[k] > second) second = Wk[k];
+    }
+    R.id_margin = best - second;
+    return R;
+}
+
+struct PixelGrad { double dC[3], dD, dA, dins; };
+
+// Loss terms of one pixel (Eq. 7-10 reading) and dL/d(outputs).
+void pixel_loss(const OSettings& st, const PixelResult& R, const double* trgb, double tdepth, int32_t gt,
+                double inv_hw, double loss[3], PixelGrad& g, uint8_t& amb) {
+    g = PixelGrad{{0, 0, 0}, 0, 0, 0};
+    if (gt < 0) return;
+    auto sgn = [](double v) { return v > 0 ? 1.0 : (v < 0 ? -1.0 : 0.0); };
+    for (int c = 0; c < 3; ++c) {
+        const double e = R.C[c] - trgb[c];
+        loss[0] += std::fabs(e) * inv_hw;
+        g.dC[c] = sgn(e) * inv_hw;
+        if (e != 0 && std::fabs(e) < 1e-5) amb |= AMB_KINK;
+    }
+    if (tdepth > 0) {
+        const double e = R.D - tdepth;
+        loss[1] += std::fabs(e) * inv_hw;
+        g.dD = sgn(e) * inv_hw;
+        if (e != 0 && std::fabs(e) < 1e-5) amb |= AMB_KINK;
+    }
+    const double e = R.ins - 1.0;
+    loss[2] += std::fabs(e) * inv_hw;
+    g.dins = st.lambda_ins * sgn(e) * inv_hw;
+}
+
+// 2D gradient record per Gaussian: dxy(2), dconic(3: a,b,c), dopac, drgb(3), dz.
+const int G2 = 10;
+
+// Adjoint of one pixel's blend (plain definition: C = sum c_j a_j T_j + T_N bg, etc.).
+void pixel_backward(const OSettings& st, const Inputs& in, const std::vector<Proj>& pr,
+                    const PixelResult& R, const PixelGrad& pg, int32_t gt, double* g2) {
+    const size_t n = R.contribs.size();
+    // suffix sums of w_k * (upstream . value_k) behind each contributor, plus the background
+    double behind = R.T * (pg.dC[0] * st.bg[0] + pg.dC[1] * st.bg[1] + pg.dC[2] * st.bg[2]);
+    for (size_t jj = n; jj-- > 0;) {
+        const Contrib& c = R.contribs[jj];
+        const int64_t g = c.g;
+        const Proj& P = pr[g];
+        const int32_t id = in.obj_id[g];
+        const bool counts = id >= 0 && id < st.num_objects && id == gt && (!st.og_filter || (in.flags[g] & 1));
+        const double U = pg.dC[0] * in.rgb[3 * g] + pg.dC[1] * in.rgb[3 * g + 1] + pg.dC[2] * in.rgb[3 * g + 2] +
+                         pg.dD * P.pc[2] + pg.dA + (counts ? pg.dins : 0.0);
+        const double w = c.alpha * c.T;
+        // dL/dalpha_j = T_j U_j - (sum_{k>j} w_k U_k + T_N bg.dC) / (1 - alpha_j)
+        const double dalpha = c.T * U - behind / (1 - c.alpha);
+        behind += w * U;
+        double* o = g2 + G2 * g;
+        for (int ch = 0; ch < 3; ++ch) o[6 + ch] += w * pg.dC[ch];
+        o[9] += w * pg.dD;
+        if (c.clamped) continue;
+        // alpha = o G, G = exp(power), power = -(a dx^2 + c dy^2)/2 - b dx dy, dx = px - x
+        o[5] += dalpha * c.G;
+        const double dpow = dalpha * P.opac * c.G;
+        o[0] += dpow * (P.conic[0] * c.dx + P.conic[1] * c.dy);
+        o[1] += dpow * (P.conic[1] * c.dx + P.conic[2] * c.dy);
+        o[2] += dpow * (-0.5 * c.dx * c.dx);
+        o[3] += dpow * (-c.dx * c.dy);
+        o[4] += dpow * (-0.5 * c.dy * c.dy);
+    }
+}
+
+// Chain a Gaussian's 2D gradient record back to its parameters.
+void preprocess_backward(const OSettings& st, const OCamera& cam, const Proj& P, double opacity_logit,
+                         const double* g2, double* dmean, double* dlog_scale, double* dquat,
+                         double* dlogit, double* drgb) {
+    (void)st;
+    for (int c = 0; c < 3; ++c) drgb[c] += g2[6 + c];
+    *dlogit += g2[5] * P.opac * (1 - P.opac);
+    (void)opacity_logit;
+    const double x = P.pc[0], y = P.pc[1], z = P.pc[2];
+    const double* V = cam.viewmat;
+    double dpc[3] = {0, 0, 0};
+    // 2D mean
+    dpc[0] += g2[0] * cam.fx / z;
+    dpc[1] += g2[1] * cam.fy / z;
+    dpc[2] += -g2[0] * cam.fx * x / (z * z) - g2[1] * cam.fy * y / (z * z);
+    // depth output
+    dpc[2] += g2[9];
+    // conic = inverse(Sigma'): dL/dSigma' = -M^-1 Gm M^-1 with Gm the matrix gradient of the conic
+    const double M[2][2] = {{P.conic[0], P.conic[1]}, {P.conic[1], P.conic[2]}};
+    const double Gm[2][2] = {{g2[2], 0.5 * g2[3]}, {0.5 * g2[3], g2[4]}};
+    double GS[2][2];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            double acc = 0;
+            for (int k = 0; k < 2; ++k)
+                for (int l = 0; l < 2; ++l) acc += M[i][k] * Gm[k][l] * M[l][j];
+            GS[i][j] = -acc;
+        }
+    // Sigma' = T2 S3 T2^T + lowpass I;  dL/dS3 = T2^T GS T2;  dL/dT2 = 2 GS T2 S3
+    double dS3[3][3], dT2[2][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0;
+            for (int k = 0; k < 2; ++k)
+                for (int l = 0; l < 2; ++l) acc += P.T2[k][i] * GS[k][l] * P.T2[l][j];
+            dS3[i][j] = acc;
+        }
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0;
+            for (int k = 0; k < 2; ++k)
+                for (int l = 0; l < 3; ++l) acc += GS[i][k] * P.T2[k][l] * P.S3[l][j];
+            dT2[i][j] = 2 * acc;
+        }
+    // T2 = J W  ->  dL/dJ = dT2 W^T
+    double dJ[2][3];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0;
+            for (int k = 0; k < 3; ++k) acc += dT2[i][k] * V[4 * j + k];
+            dJ[i][j] = acc;
+        }
+    // J = [[fx/z, 0, -fx x/z^2], [0, fy/z, -fy y/z^2]]
+    dpc[0] += dJ[0][2] * (-cam.fx / (z * z));
+    dpc[1] += dJ[1][2] * (-cam.fy / (z * z));
+    dpc[2] += dJ[0][0] * (-cam.fx / (z * z)) + dJ[0][2] * (2 * cam.fx * x / (z * z * z)) +
+              dJ[1][1] * (-cam.fy / (z * z)) + dJ[1][2] * (2 * cam.fy * y / (z * z * z));
+    // p_c = Rv mean + t
+    for (int j = 0; j < 3; ++j) dmean[j] += V[j] * dpc[0] + V[4 + j] * dpc[1] + V[8 + j] * dpc[2];
+    // S3 = M M^T with M = Rq diag(s):  dL/dM = (dS3 + dS3^T) M
+    double Mm[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Mm[i][j] = P.Rq[i][j] * P.s[j];
+    double dM[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0;
+            for (int k = 0; k < 3; ++k) acc += (dS3[i][k] + dS3[k][i]) * Mm[k][j];
+            dM[i][j] = acc;
+        }
+    double dR[3][3];
+    for (int j = 0; j < 3; ++j) {
+        double ds = 0;
+        for (int i = 0; i < 3; ++i) {
+            ds += dM[i][j] * P.Rq[i][j];
+            dR[i][j] = dM[i][j] * P.s[j];
+        }
+        dlog_scale[j] += ds * P.s[j];
+    }
+    // R(q) for the normalised quaternion (w,x,y,z)
+    const double w = P.qn[0], qx = P.qn[1], qy = P.qn[2], qz = P.qn[3];
+    double dqn[4];
+    dqn[0] = 2 * (-qz * dR[0][1] + qy * dR[0][2] + qz * dR[1][0] - qx * dR[1][2] - qy * dR[2][0] + qx * dR[2][1]);
+    dqn[1] = 2 * (qy * dR[0][1] + qz * dR[0][2] + qy * dR[1][0] - 2 * qx * dR[1][1] - w * dR[1][2] +
+                  qz * dR[2][0] + w * dR[2][1] - 2 * qx * dR[2][2]);
+    dqn[2] = 2 * (-2 * qy * dR[0][0] + qx * dR[0][1] + w * dR[0][2] + qx * dR[1][0] + qz * dR[1][2] -
+                  w * dR[2][0] + qz * dR[2][1] - 2 * qy * dR[2][2]);
+    dqn[3] = 2 * (-2 * qz * dR[0][0] - w * dR[0][1] + qx * dR[0][2] + w * dR[1][0] - 2 * qz * dR[1][1] +
+                  qy * dR[1][2] + qx * dR[2][0] + qy * dR[2][1]);
+    // normalisation q / |q|
+    double dot = 0;
+    for (int k = 0; k < 4; ++k) dot += dqn[k] * P.qn[k];
+    for (int k = 0; k < 4; ++k) dquat[k] += (dqn[k] - P.qn[k] * dot) / P.qnorm;
+}
+
+Inputs make_inputs(int64_t n, const double* means, const double* log_scales, const double* quats,
+                   const double* opacity_logit, const double* rgb, const int32_t* obj_id, const uint8_t* flags) {
+    return Inputs{n, means, log_scales, quats, opacity_logit, rgb, obj_id, flags};
+}
+
+// Marks tiles whose membership is ambiguous for some Gaussian: those in the union of its
+// perturbed rects but not in their intersection.
+void rect_ambiguity(const OSettings& st, const OCamera& cam, const std::vector<Proj>& pr,
+                    std::vector<uint8_t>& tile_amb, int ntx, int nty) {
+    (void)st; (void)cam;
+    for (const Proj& P : pr) {
+        if (!P.ambiguous) continue;
+        for (int ty = P.urect[1]; ty < P.urect[3] && ty < nty; ++ty)
+            for (int tx = P.urect[0]; tx < P.urect[2] && tx < ntx; ++tx)
+                if (!covers(P.irect, tx, ty)) tile_amb[(size_t)ty * ntx + tx] = 1;
+    }
+}
+
+}  // namespace
+
+// ====================================================================== C entry points
+
+extern "C" {
+
+// Per-Gaussian projection.  Outputs (each may be NULL): xy[n*2], conic[n*3] (Sigma'^-1),
+// z[n], opac[n], radius[n], rect[n*4] (tx0,ty0,tx1,ty1 exclusive), visible[n], ambiguous[n].
+int oracle_preprocess(const OSettings* st, const OCamera* cam, int64_t n, const double* means,
+                      const double* log_scales, const double* quats, const double* opacity_logit,
+                      double* xy, double* conic, double* z, double* opac, int32_t* radius, int32_t* rect,
+                      uint8_t* visible, uint8_t* ambiguous) {
+    for (int64_t i = 0; i < n; ++i) {
+        Proj P = project_gaussian(*st, *cam, means + 3 * i, log_scales + 3 * i, quats + 4 * i, opacity_logit[i]);
+        if (xy) { xy[2 * i] = P.xy[0]; xy[2 * i + 1] = P.xy[1]; }
+        if (conic) for (int k = 0; k < 3; ++k) conic[3 * i + k] = P.conic[k];
+        if (z) z[i] = P.pc[2];
+        if (opac) opac[i] = P.opac;
+        if (radius) radius[i] = P.radius;
+        if (rect) for (int k = 0; k < 4; ++k) rect[4 * i + k] = P.visible ? P.rect[k] : 0;
+        if (visible) visible[i] = P.visible;
+        if (ambiguous) ambiguous[i] = P.ambiguous;
+    }
+    return 0;
+}
+
+// Full render.  mode 0: per-tile sorted lists; mode 1: per-pixel brute force over all
+// Gaussians in (z, index) order.  Targets may be NULL (then no loss / pixel gradients).
+// Outputs (each may be NULL): rgb[H*W*3], depth, alpha, ins, id_map, T_final, n_contrib,
+// amb[H*W] (flag bits), id_margin[H*W], loss[4] (rgb, depth, ins, total),
+// dl[H*W*6] (dC r,g,b, dD, dA, dins).
+int oracle_render(const OSettings* st, const OCamera* cam, int64_t n, const double* means,
+                  const double* log_scales, const double* quats, const double* opacity_logit,
+                  const double* rgb, const int32_t* obj_id, const uint8_t* flags,
+                  const double* t_rgb, const double* t_depth, const int32_t* t_gt, int mode,
+                  double* o_rgb, double* o_depth, double* o_alpha, double* o_ins, int32_t* o_id,
+                  double* o_T, int64_t* o_ncontrib, uint8_t* o_amb, double* o_margin, double* o_loss,
+                  double* o_dl) {
+    const Inputs in = make_inputs(n, means, log_scales, quats, opacity_logit, rgb, obj_id, flags);
+    const int W = cam->width, H = cam->height;
+    if (W <= 0 || H <= 0 || st->tile_w <= 0 || st->tile_h <= 0) return 1;
+    const int ntx = (W + st->tile_w - 1) / st->tile_w, nty = (H + st->tile_h - 1) / st->tile_h;
+    std::vector<Proj> pr = project_all(*st, *cam, in);
+    std::vector<uint8_t> tile_amb((size_t)ntx * nty, 0);
+    rect_ambiguity(*st, *cam, pr, tile_amb, ntx, nty);
+    std::vector<int64_t> all;
+    if (mode == 1) {
+        for (int64_t i = 0; i < n; ++i) all.push_back(i);
+        std::stable_sort(all.begin(), all.end(), [&](int64_t a, int64_t b) {
+            if (pr[a].pc[2] != pr[b].pc[2]) return pr[a].pc[2] < pr[b].pc[2];
+            return a < b;
+        });
+    }
+    double loss[3] = {0, 0, 0};
+    const double inv_hw = 1.0 / ((double)W * H);
+    for (int ty = 0; ty < nty; ++ty)
+        for (int tx = 0; tx < ntx; ++tx) {
+            std::vector<int64_t> L;
+            if (mode == 0) L = tile_list(pr, tx, ty);
+            for (int py = ty * st->tile_h; py < std::min(H, (ty + 1) * st->tile_h); ++py)
+                for (int px = tx * st->tile_w; px < std::min(W, (tx + 1) * st->tile_w); ++px) {
+                    const size_t p = (size_t)py * W + px;
+                    const int32_t gt = t_gt ? t_gt[p] : -1;
+                    std::vector<int64_t> Lp;
+                    if (mode == 1) {
+                        for (int64_t i : all)
+                            if (pr[i].visible && covers(pr[i].rect, px / st->tile_w, py / st->tile_h)) Lp.push_back(i);
+                    }
+                    PixelResult R = blend_pixel(*st, in, pr, mode == 0 ? L : Lp, px, py, gt, false);
+                    if (tile_amb[(size_t)ty * ntx + tx]) R.amb |= AMB_RECT;
+                    PixelGrad pg{{0, 0, 0}, 0, 0, 0};
+                    if (t_gt) pixel_loss(*st, R, t_rgb + 3 * p, t_depth ? t_depth[p] : 0.0, gt, inv_hw, loss, pg, R.amb);
+                    if (o_rgb) for (int c = 0; c < 3; ++c) o_rgb[3 * p + c] = R.C[c];
+                    if (o_depth) o_depth[p] = R.D;
+                    if (o_alpha) o_alpha[p] = R.A;
+                    if (o_ins) o_ins[p] = R.ins;
+                    if (o_id) o_id[p] = R.id;
+                    if (o_T) o_T[p] = R.T;
+                    if (o_ncontrib) o_ncontrib[p] = R.n_contrib;
+                    if (o_amb) o_amb[p] = R.amb;
+                    if (o_margin) o_margin[p] = R.id_margin;
+                    if (o_dl) {
+                        double* d = o_dl + 6 * p;
+                        d[0] = pg.dC[0]; d[1] = pg.dC[1]; d[2] = pg.dC[2]; d[3] = pg.dD; d[4] = pg.dA; d[5] = pg.dins;
+                    }
+                }
+        }
+    if (o_loss) {
+        o_loss[0] = loss[0]; o_loss[1] = loss[1]; o_loss[2] = loss[2];
+        o_loss[3] = loss[0] + loss[1] + st->lambda_ins * loss[2];
+    }
+    return 0;
+}
+
+// Render at a list of pixels only (for parity at full size).  px[npix*2] = (u, v).
+// Outputs per sampled pixel: rgb[npix*3], depth, alpha, ins, id, T, n_contrib, amb, margin.
+int oracle_render_pixels(const OSettings* st, const OCamera* cam, int64_t n, const double* means,
+                         const double* log_scales, const double* quats, const double* opacity_logit,
+                         const double* rgb, const int32_t* obj_id, const uint8_t* flags,
+                         const int32_t* t_gt, int64_t npix, const int32_t* pxy, double* o_rgb,
+                         double* o_depth, double* o_alpha, double* o_ins, int32_t* o_id, double* o_T,
+                         int64_t* o_ncontrib, uint8_t* o_amb, double* o_margin) {
+    const Inputs in = make_inputs(n, means, log_scales, quats, opacity_logit, rgb, obj_id, flags);
+    const int W = cam->width, H = cam->height;
+    const int ntx = (W + st->tile_w - 1) / st->tile_w, nty = (H + st->tile_h - 1) / st->tile_h;
+    std::vector<Proj> pr = project_all(*st, *cam, in);
+    std::vector<uint8_t> tile_amb((size_t)ntx * nty, 0);
+    rect_ambiguity(*st, *cam, pr, tile_amb, ntx, nty);
+    for (int64_t k = 0; k < npix; ++k) {
+        const int px = pxy[2 * k], py = pxy[2 * k + 1];
+        if (px < 0 || px >= W || py < 0 || py >= H) return 1;
+        const int tx = px / st->tile_w, ty = py / st->tile_h;
+        std::vector<int64_t> L = tile_list(pr, tx, ty);
+        const int32_t gt = t_gt ? t_gt[(size_t)py * W + px] : -1;
+        PixelResult R = blend_pixel(*st, in, pr, L, px, py, gt, false);
+        if (tile_amb[(size_t)ty * ntx + tx]) R.amb |= AMB_RECT;
+        if (o_rgb) for (int c = 0; c < 3; ++c) o_rgb[3 * k + c] = R.C[c];
+        if (o_depth) o_depth[k] = R.D;
+        if (o_alpha) o_alpha[k] = R.A;
+        if (o_ins) o_ins[k] = R.ins;
+        if (o_id) o_id[k] = R.id;
+        if (o_T) o_T[k] = R.T;
+        if (o_ncontrib) o_ncontrib[k] = R.n_contrib;
+        if (o_amb) o_amb[k] = R.amb;
+        if (o_margin) o_margin[k] = R.id_margin;
+    }
+    return 0;
+}
+
+// Backward of the render.  Pixel gradients: if dl (H*W*6 = dC rgb, dD, dA, dins) is NULL the
+// fused L1 losses against the targets are differentiated.  Outputs (accumulated +=, each may be
+// NULL): g2[n*10] (dxy, dconic a b c, dopac, drgb, dz), and parameter gradients.
+// Gaussians touching a flagged pixel are reported in g_amb[n] (bit0 threshold/tile, bit3 kink).
+int oracle_render_backward(const OSettings* st, const OCamera* cam, int64_t n, const double* means,
+                           const double* log_scales, const double* quats, const double* opacity_logit,
+                           const double* rgb, const int32_t* obj_id, const uint8_t* flags,
+                           const double* t_rgb, const double* t_depth, const int32_t* t_gt,
+                           const double* dl, double* g2_out, double* d_means, double* d_log_scales,
+                           double* d_quats, double* d_logit, double* d_rgb, uint8_t* g_amb) {
+    const Inputs in = make_inputs(n, means, log_scales, quats, opacity_logit, rgb, obj_id, flags);
+    const int W = cam->width, H = cam->height;
+    if (W <= 0 || H <= 0) return 1;
+    const int ntx = (W + st->tile_w - 1) / st->tile_w, nty = (H + st->tile_h - 1) / st->tile_h;
+    std::vector<Proj> pr = project_all(*st, *cam, in);
+    std::vector<uint8_t> tile_amb((size_t)ntx * nty, 0);
+    rect_ambiguity(*st, *cam, pr, tile_amb, ntx, nty);
+    std::vector<double> g2((size_t)n * G2, 0.0);
+    const double inv_hw = 1.0 / ((double)W * H);
+    for (int ty = 0; ty < nty; ++ty)
+        for (int tx = 0; tx < ntx; ++tx) {
+            std::vector<int64_t> L = tile_list(pr, tx, ty);
+            for (int py = ty * st->tile_h; py < std::min(H, (ty + 1) * st->tile_h); ++py)
+                for (int px = tx * st->tile_w; px < std::min(W, (tx + 1) * st->tile_w); ++px) {
+                    const size_t p = (size_t)py * W + px;
+                    const int32_t gt = t_gt ? t_gt[p] : -1;
+                    PixelResult R = blend_pixel(*st, in, pr, L, px, py, gt, true);
+                    if (tile_amb[(size_t)ty * ntx + tx]) R.amb |= AMB_RECT;
+                    PixelGrad pg{{0, 0, 0}, 0, 0, 0};
+                    if (dl) {
+                        const double* d = dl + 6 * p;
+                        pg = PixelGrad{{d[0], d[1], d[2]}, d[3], d[4], d[5]};
+                    } else if (t_gt) {
+                        double loss[3] = {0, 0, 0};
+                        pixel_loss(*st, R, t_rgb + 3 * p, t_depth ? t_depth[p] : 0.0, gt, inv_hw, loss, pg, R.amb);
+                    }
+                    pixel_backward(*st, in, pr, R, pg, gt, g2.data());
+                    if (g_amb && R.amb) {
+                        // every Gaussian this pixel walks may see its gradient change
+                        const uint8_t bits = (R.amb & (AMB_THRESH | AMB_DEPTH | AMB_RECT)) ? 1 : 0;
+                        const uint8_t kb = (R.amb & AMB_KINK) ? 8 : 0;
+                        for (const Contrib& c : R.contribs) g_amb[c.g] |= (uint8_t)(bits | kb);
+                        if (bits)
+                            for (int64_t g : L)
+                                if (covers(pr[g].rect, tx, ty)) g_amb[g] |= 1;
+                    }
+                }
+        }
+    for (int64_t i = 0; i < n; ++i) {
+        const double* r = g2.data() + G2 * i;
+        if (g2_out) for (int k = 0; k < G2; ++k) g2_out[G2 * i + k] += r[k];
+        if (!pr[i].visible) continue;
+        double dm[3] = {0, 0, 0}, ds[3] = {0, 0, 0}, dq[4] = {0, 0, 0, 0}, dlg = 0, dc[3] = {0, 0, 0};
+        preprocess_backward(*st, *cam, pr[i], opacity_logit[i], r, dm, ds, dq, &dlg, dc);
+        if (d_means) for (int k = 0; k < 3; ++k) d_means[3 * i + k] += dm[k];
+        if (d_log_scales) for (int k = 0; k < 3; ++k) d_log_scales[3 * i + k] += ds[k];
+        if (d_quats) for (int k = 0; k < 4; ++k) d_quats[4 * i + k] += dq[k];
+        if (d_logit) d_logit[i] += dlg;
+        if (d_rgb) for (int k = 0; k < 3; ++k) d_rgb[3 * i + k] += dc[k];
+    }
+    return 0;
+}
+
+// Tile lists from given single-precision projections: Gaussians i with visible[i] and
+// rect covering the tile, ordered by (tile row-major, zbits[i] as unsigned, i).
+// ranges[T*2] = [start, end); list[M] must hold sum of rect areas.  Returns M.
+int64_t oracle_bin_tiles(int64_t n, const int32_t* rect, const uint32_t* zbits, const uint8_t* visible,
+                         int ntx, int nty, int64_t* ranges, int64_t* list) {
+    int64_t m = 0;
+    for (int ty = 0; ty < nty; ++ty)
+        for (int tx = 0; tx < ntx; ++tx) {
+            const int64_t start = m;
+            std::vector<int64_t> L;
+            for (int64_t i = 0; i < n; ++i)
+                if (visible[i] && tx >= rect[4 * i] && tx < rect[4 * i + 2] && ty >= rect[4 * i + 1] &&
+                    ty < rect[4 * i + 3])
+                    L.push_back(i);
+            std::stable_sort(L.begin(), L.end(), [&](int64_t a, int64_t b) {
+                if (zbits[a] != zbits[b]) return zbits[a] < zbits[b];
+                return a < b;
+            });
+            for (int64_t i : L) list[m++] = i;
+            ranges[2 * ((int64_t)ty * ntx + tx)] = start;
+            ranges[2 * ((int64_t)ty * ntx + tx) + 1] = m;
+        }
+    return m;
+}
+
+}  // extern "C"
+
+// ====================================================================== dual quadrics
+
+namespace {
+
+const int ND = 9;  // derivative directions = quadric parameters
+
+struct Dual {
+    double v;
+    double d[ND];
+    Dual() : v(0) { std::memset(d, 0, sizeof d); }
+    Dual(double x) : v(x) { std::memset(d, 0, sizeof d); }
+};
+Dual operator+(const Dual& a, const Dual& b) { Dual r(a.v + b.v); for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] + b.d[i]; return r; }
+Dual operator-(const Dual& a, const Dual& b) { Dual r(a.v - b.v); for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] - b.d[i]; return r; }
+Dual operator-(const Dual& a) { Dual r(-a.v); for (int i = 0; i < ND; ++i) r.d[i] = -a.d[i]; return r; }
+Dual operator*(const Dual& a, const Dual& b) { Dual r(a.v * b.v); for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i]; return r; }
+Dual operator/(const Dual& a, const Dual& b) { Dual r(a.v / b.v); for (int i = 0; i < ND; ++i) r.d[i] = (a.d[i] * b.v - a.v * b.d[i]) / (b.v * b.v); return r; }
+Dual sqrt(const Dual& a) { const double s = std::sqrt(a.v); Dual r(s); for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] / (2 * s); return r; }
+Dual sin(const Dual& a) { Dual r(std::sin(a.v)); const double c = std::cos(a.v); for (int i = 0; i < ND; ++i) r.d[i] = c * a.d[i]; return r; }
+Dual cos(const Dual& a) { Dual r(std::cos(a.v)); const double s = -std::sin(a.v); for (int i = 0; i < ND; ++i) r.d[i] = s * a.d[i]; return r; }
+Dual exp(const Dual& a) { const double e = std::exp(a.v); Dual r(e); for (int i = 0; i < ND; ++i) r.d[i] = e * a.d[i]; return r; }
+double val(const Dual& a) { return a.v; }
+double val(double a) { return a; }
+using std::sqrt; using std::sin; using std::cos; using std::exp;
+
+// Rodrigues: R = I + A [r]x + B [r]x^2, A = sin(t)/t, B = (1 - cos t)/t^2, t = |r|.
+template <class T>
+void rotvec_to_rot(const T r[3], T R[3][3]) {
+    const T t2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+    T A, B;
+    if (val(t2) < 1e-8) {
+        A = T(1.0) - t2 / T(6.0);
+        B = T(0.5) - t2 / T(24.0);
+    } else {
+        const T t = sqrt(t2);
+        A = sin(t) / t;
+        B = (T(1.0) - cos(t)) / t2;
+    }
+    const T K[3][3] = {{T(0.0), -r[2], r[1]}, {r[2], T(0.0), -r[0]}, {-r[1], r[0], T(0.0)}};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            T kk = T(0.0);
+            for (int k = 0; k < 3; ++k) kk = kk + K[i][k] * K[k][j];
+            R[i][j] = T(i == j ? 1.0 : 0.0) + A * K[i][j] + B * kk;
+        }
+}
+
+// Eq. 1-3 reading: Q* = Z diag(a^2, b^2, c^2, -1) Z^T with Z = [R t; 0 1].
+template <class T>
+void quadric_from_params(const T p[9], T Q[4][4]) {
+    T R[3][3];
+    const T r[3] = {p[6], p[7], p[8]};
+    rotvec_to_rot(r, R);
+    T Z[4][4];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) Z[i][j] = T(0.0);
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) Z[i][j] = R[i][j];
+        Z[i][3] = p[i];
+    }
+    Z[3][3] = T(1.0);
+    const T D[4] = {exp(T(2.0) * p[3]), exp(T(2.0) * p[4]), exp(T(2.0) * p[5]), T(-1.0)};
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            T acc = T(0.0);
+            for (int k = 0; k < 4; ++k) acc = acc + Z[i][k] * D[k] * Z[j][k];
+            Q[i][j] = acc;
+        }
+}
+
+// Eq. 4 reading: C* = P Q* P^T.
+template <class T>
+void project_quadric(const T Q[4][4], const double P[12], T C[3][3]) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            T acc = T(0.0);
+            for (int k = 0; k < 4; ++k)
+                for (int l = 0; l < 4; ++l) acc = acc + T(P[4 * i + k]) * Q[k][l] * T(P[4 * j + l]);
+            C[i][j] = acc;
+        }
+}
+
+// BBox(C*): vertical line (1,0,-u) tangent iff c11 - 2u c13 + u^2 c33 = 0; likewise for v.
+template <class T>
+bool conic_bbox(const T C[3][3], double centre_depth, T box[4]) {
+    const T du = C[0][2] * C[0][2] - C[0][0] * C[2][2];
+    const T dv = C[1][2] * C[1][2] - C[1][1] * C[2][2];
+    const bool valid = val(C[2][2]) < 0 && centre_depth > 0 && val(du) > 0 && val(dv) > 0;
+    if (!valid) { for (int k = 0; k < 4; ++k) box[k] = T(0.0); return false; }
+    const T su = sqrt(du), sv = sqrt(dv);
+    const T u1 = (C[0][2] + su) / C[2][2], u2 = (C[0][2] - su) / C[2][2];
+    const T v1 = (C[1][2] + sv) / C[2][2], v2 = (C[1][2] - sv) / C[2][2];
+    box[0] = val(u1) < val(u2) ? u1 : u2;
+    box[2] = val(u1) < val(u2) ? u2 : u1;
+    box[1] = val(v1) < val(v2) ? v1 : v2;
+    box[3] = val(v1) < val(v2) ? v2 : v1;
+    return true;
+}
+
+// Axis-aligned IoU; the predicted box is not clipped to the image.
+template <class T>
+T box_iou(const T b[4], const double o[4]) {
+    const T ix0 = val(b[0]) > o[0] ? b[0] : T(o[0]);
+    const T iy0 = val(b[1]) > o[1] ? b[1] : T(o[1]);
+    const T ix1 = val(b[2]) < o[2] ? b[2] : T(o[2]);
+    const T iy1 = val(b[3]) < o[3] ? b[3] : T(o[3]);
+    T iw = ix1 - ix0, ih = iy1 - iy0;
+    if (val(iw) <= 0) iw = T(0.0);
+    if (val(ih) <= 0) ih = T(0.0);
+    const T inter = iw * ih;
+    const T ap = (b[2] - b[0]) * (b[3] - b[1]);
+    const T ao = T((o[2] - o[0]) * (o[3] - o[1]));
+    return inter / (ap + ao - inter);
+}
+
+double centre_depth(const double p[9], const double P[12]) {
+    return P[8] * p[0] + P[9] * p[1] + P[10] * p[2] + P[11];
+}
+
+}  // namespace
+
+extern "C" {
+
+// Per (quadric, view) pair in CSR order: pairs q_ptr[q] .. q_ptr[q+1]-1 belong to quadric q
+// and use view pair_v[k].  Outputs: conic[npairs*6] (c11 c12 c13 c22 c23 c33), bbox[npairs*4],
+// valid[npairs].  Each may be NULL.
+int oracle_quadric_project(int nq, const double* params, int nv, const double* P, const int32_t* q_ptr,
+                           const int32_t* pair_v, double* conic, double* bbox, uint8_t* valid) {
+    for (int q = 0; q < nq; ++q) {
+        double Q[4][4];
+        quadric_from_params(params + 9 * q, Q);
+        for (int k = q_ptr[q]; k < q_ptr[q + 1]; ++k) {
+            const int v = pair_v[k];
+            if (v < 0 || v >= nv) return 1;
+            double C[3][3], box[4];
+            project_quadric(Q, P + 12 * v, C);
+            const bool ok = conic_bbox(C, centre_depth(params + 9 * q, P + 12 * v), box);
+            if (conic) {
+                double* c = conic + 6 * k;
+                c[0] = C[0][0]; c[1] = C[0][1]; c[2] = C[0][2]; c[3] = C[1][1]; c[4] = C[1][2]; c[5] = C[2][2];
+            }
+            if (bbox) for (int j = 0; j < 4; ++j) bbox[4 * k + j] = box[j];
+            if (valid) valid[k] = ok;
+        }
+    }
+    return 0;
+}
+
+// Eq. 12 reading: loss[q] = sum over valid pairs of q of (1 - IoU); dparams[q*9] its gradient
+// (overwritten).  Gradient by forward-mode dual numbers through the same forward.
+int oracle_quadric_bbox_loss(int nq, const double* params, int nv, const double* P, const int32_t* q_ptr,
+                             const int32_t* pair_v, const double* obs, double* loss, double* dparams) {
+    for (int q = 0; q < nq; ++q) {
+        Dual p[9];
+        for (int i = 0; i < 9; ++i) { p[i] = Dual(params[9 * q + i]); p[i].d[i] = 1.0; }
+        Dual Q[4][4];
+        quadric_from_params(p, Q);
+        Dual L(0.0);
+        for (int k = q_ptr[q]; k < q_ptr[q + 1]; ++k) {
+            const int v = pair_v[k];
+            if (v < 0 || v >= nv) return 1;
+            Dual C[3][3], box[4];
+            project_quadric(Q, P + 12 * v, C);
+            if (!conic_bbox(C, centre_depth(params + 9 * q, P + 12 * v), box)) continue;
+            L = L + (Dual(1.0) - box_iou(box, obs + 4 * k));
+        }
+        if (loss) loss[q] = L.v;
+        if (dparams) for (int i = 0; i < 9; ++i) dparams[9 * q + i] = L.d[i];
+    }
+    return 0;
+}
+
+// 4x4 dual quadric of each parameter vector (row-major), for the decomposition pins.
+int oracle_quadric_matrix(int nq, const double* params, double* Q16) {
+    for (int q = 0; q < nq; ++q) {
+        double Q[4][4];
+        quadric_from_params(params + 9 * q, Q);
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) Q16[16 * q + 4 * i + j] = Q[i][j];
+    }
+    return 0;
+}
+
+}  // extern "C"
