@@ -1,0 +1,379 @@
+#!/usr/bin/env python3
+"""Benchmark of the DQO-MAP GPU optimisation hot path on GB300.
+
+One step = one keyframe iteration of the paper's GPU-side optimisation (Sec. III-D):
+  forward render with the fused colour / depth / instance losses (Eq. 7-10, 15),
+  the full backward to the Gaussian parameters, and the bbox loss + gradient of the
+  keyframe's 30 dual quadrics over their views (Eq. 12),
+on the indoor-keyframe workload: 300k Gaussians on 30 ellipsoidal objects plus room
+walls, a 1200x680 RGB-D keyframe, seeded synthetic data.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` = keyframe iterations per second over all ranks (device
+time, CUDA events, L2 flushed between steps); `e2e` = the same through the C ABI with
+the step's inputs copied from pinned host memory and its loss and gradients copied
+back inside the timed region; `roofline` = the dominant kernel against the FP32 pipe
+peak; `cpu_baseline` / `--impl reference` = the FP64 CPU oracle on a bounded sample.
+Multi-GPU (torchrun): every rank runs its own keyframe replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd keyframe iters/s (300k Gaussians,1200×680) & quadric fits/s vs plain"
+UNIT = "iters/s"
+SEED = 1002
+NUM_OBJECTS = 31                 # ids 0 (room) .. 30
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # FMA = 2 flops
+# Algorithmic FP32 flops per (pixel, Gaussian) evaluation, counted from the kernels'
+# arithmetic (FMA = 2): forward = exponent 9 + alpha/transmittance 5 + colour/depth 8 +
+# instance 2 + weight 1; backward = exponent 9 + alpha 3 + transmittance 2 + upstream dot 9
+# + dalpha 5 + accumulator 2 + ten partials 15 + their sums 10.
+FLOPS_PER_EVAL = {"blend_fwd": 25, "blend_bwd": 55}
+KERNEL_SRC = {"blend_fwd": "k_blend.cu", "blend_bwd": "k_blend.cu"}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--tile", default="16x16")
+    p.add_argument("--batch", type=int, default=256)
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid: str | None):
+        self.uuid = device_uuid
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        sel = [f"--id={self.uuid}"] if self.uuid else []
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", *sel, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- workload
+
+def make_workload():
+    from paper_2503_02223_gb300 import synth
+    kf = synth.indoor_keyframe(SEED)
+    targets = synth.raycast_targets(kf)
+    return kf, targets
+
+
+def oracle_sample(kf, targets, rows: int, reps: int):
+    """FP64 oracle forward + backward on a centred band of `rows` image rows (all Gaussians
+    projected); returns seconds per band."""
+    import numpy as np
+
+    import oracle
+    cam = kf["camera"]
+    H = cam["height"]
+    r0 = H // 2 - rows // 2
+    cam2 = dict(cam, height=rows, cy=cam["cy"] - r0)
+    t2 = {k: np.ascontiguousarray(v[r0:r0 + rows]) for k, v in targets.items()}
+    st = oracle.settings(num_objects=NUM_OBJECTS)
+    oracle.build()
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.render(kf["gaussians"], cam2, st, t2)
+        oracle.render_backward(kf["gaussians"], cam2, st, t2)
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def traffic_for(kernel: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if it matches the current source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2503_02223_gb300", "csrc", KERNEL_SRC.get(kernel, ""))
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return rec.get("bytes_per_launch") if rec.get("src_sha") == h else None
+
+
+# ----------------------------------------------------------------------------- arms
+
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle on this host's cores (the reference arm of this workload)."""
+    if rank != 0:
+        return
+    kf, targets = make_workload()
+    H = kf["camera"]["height"]
+    rows = 48                                      # 3 tile rows of 680: 1/14.2 of the pixels
+    frac = rows / H
+    for _ in range(min(args.warmup, 1)):
+        oracle_sample(kf, targets, rows, 1)
+    reps = max(1, min(args.steps, 8))          # bounded: about 3-4 s of CPU per sample
+    times = oracle_sample(kf, targets, rows, reps)
+    sec_per_iter = sum(times) / len(times) / frac
+    val = 1.0 / sec_per_iter
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": reps,
+            "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * sec_per_iter, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": workload_config(kf, None, args),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"rows {H // 2 - rows // 2}..{H // 2 + rows // 2 - 1} of {H} "
+                                       f"(all 300k Gaussians projected), forward+backward, {reps} runs, "
+                                       f"value scaled by {H}/{rows}"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(kf, m_pairs, args):
+    cam = kf["camera"]
+    return {"workload": "indoor keyframe: 300k Gaussians (30 ellipsoidal objects + room walls), "
+                        "1200x680 RGB-D keyframe, 30 dual quadrics with up to 8 views",
+            "gaussians": int(kf["gaussians"]["means"].shape[0]), "width": cam["width"], "height": cam["height"],
+            "quadrics": int(kf["quadrics"]["params"].shape[0]),
+            "quadric_pairs": int(kf["quadrics"]["pair_v"].shape[0]),
+            "tile_gaussian_pairs": m_pairs, "tile": args.tile, "batch": args.batch,
+            "l2": "flushed between steps (256 MiB write outside the timed events)",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2503_02223_gb300 import dqo
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dqo.load(build_if_missing=True)
+    kf, targets = make_workload()
+    cam = kf["camera"]
+    W, H = cam["width"], cam["height"]
+    tw, th = (int(x) for x in args.tile.split("x"))
+    ctx = dqo.Context(local_rank)
+    st = dqo.settings(tile_w=tw, tile_h=th, batch=args.batch)
+    g = dqo.to_device(kf["gaussians"], dev)
+    t = dqo.to_device(targets, dev)
+    q = dqo.to_device({k: kf["quadrics"][k] for k in ("params", "P", "q_ptr", "pair_v", "obs_bbox")}, dev)
+    n = g["means"].shape[0]
+    nq = q["params"].shape[0]
+    out = dqo.alloc_outputs(W, H, dev)
+    grads = dqo.alloc_grads(n, dev)
+    qloss = torch.zeros(nq, device=dev)
+    qgrad = torch.zeros(nq, 9, device=dev)
+    gs, cs, ts = dqo.gaussians(g, NUM_OBJECTS), dqo.camera(cam), dqo.targets(t)
+    outs, gg = dqo.render_out(out), dqo.gaussian_grads(grads)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for v in grads.values():
+            v.zero_()
+        dqo.dqo_render_forward(ctx, st, gs, cs, ts, outs, stream)
+        dqo.dqo_render_backward(ctx, st, gs, cs, ts, None, gg, stream)
+        dqo.dqo_quadric_bbox_loss(ctx, q["params"], q["P"], q["q_ptr"], q["pair_v"], q["obs_bbox"], qloss, qgrad,
+                                  stream)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    m_pairs, n_vis, n_tiles = dqo.dqo_get_counts(ctx)
+    nc = torch.empty(H * W, dtype=torch.int32, device=dev)
+    dqo.dqo_get_buffer(ctx, dqo.DQO_BUF_N_CONTRIB, nc)
+    torch.cuda.synchronize()
+    evals = int(nc.to(torch.int64).sum().item())
+
+    # ---- device-timed region
+    dqo.dqo_set_timing(ctx, True)
+    phase_sum = {k: 0.0 for k in dqo.PHASES}
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    uuid = getattr(torch.cuda.get_device_properties(local_rank), "uuid", None)
+    clocks = ClockSampler(f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else
+                          (str(uuid) if uuid is not None else None))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = dqo.dqo_launch_count(ctx)
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        ph = dqo.dqo_get_timings(ctx)
+        for k, v in ph.items():
+            if v >= 0:
+                phase_sum[k] += v
+    torch.cuda.synchronize()
+    launches = dqo.dqo_launch_count(ctx) - launches0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    dqo.dqo_set_timing(ctx, False)
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1e3)
+    phases = {k: v / args.steps for k, v in phase_sum.items()}
+
+    # ---- end to end through the C ABI with host buffers
+    pin = {k: v.cpu().pin_memory() for k, v in g.items()}
+    pin_t = {k: v.cpu().pin_memory() for k, v in t.items()}
+    pin_q = {k: v.cpu().pin_memory() for k, v in q.items()}
+    host_out = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in grads.items()}
+    host_loss = torch.empty(4, pin_memory=True)
+    host_q = (torch.empty(nq, pin_memory=True), torch.empty(nq, 9, pin_memory=True))
+    h2d = sum(v.numel() * v.element_size() for d in (pin, pin_t, pin_q) for v in d.values())
+    d2h = sum(v.numel() * v.element_size() for v in host_out.values()) + 16 + nq * 40
+
+    def e2e_step():
+        for d, src in ((g, pin), (t, pin_t), (q, pin_q)):
+            for k in d:
+                d[k].copy_(src[k], non_blocking=True)
+        step()
+        for k in grads:
+            host_out[k].copy_(grads[k], non_blocking=True)
+        host_loss.copy_(out["loss"], non_blocking=True)
+        host_q[0].copy_(qloss, non_blocking=True)
+        host_q[1].copy_(qgrad, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    e_steps = max(10, args.steps // 4)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        tt = torch.tensor([e_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e_ms = float(tt.item())
+    e2e_val = world * e_steps / (e_ms / 1e3)
+
+    # ---- roofline of the dominant kernel (FP32 pipe)
+    dom = max(("blend_fwd", "blend_bwd"), key=lambda k: phases[k])
+    flops = FLOPS_PER_EVAL[dom] * evals
+    achieved = flops / (phases[dom] * 1e-3) / 1e12
+    roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic_for(dom),
+            "evals_per_launch": evals, "flops_per_eval": FLOPS_PER_EVAL[dom],
+            "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, no measured FP32 peak)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(kf, m_pairs, args), "clocks": clk,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "roofline": roof,
+            "phases_ms": {k: round(v, 4) for k, v in phases.items()}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        H_ = kf["camera"]["height"]
+        rows = 80
+        times = oracle_sample(kf, targets, rows, 2)
+        v = 1.0 / (sum(times) / len(times) / (rows / H_))
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"forward+backward of rows {H_ // 2 - rows // 2}..{H_ // 2 + rows // 2 - 1} "
+                                          f"of {H_} (all 300k Gaussians projected), 2 runs, scaled by {H_}/{rows}"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,265 @@
+/* dqo.h -- C ABI of the GB300 (sm_103a) implementation of DQO-MAP's GPU optimisation
+ * hot path (arXiv 2503.02223):
+ *
+ *   - the differentiable 3D Gaussian Splatting tile rasterizer the paper optimises its
+ *     object Gaussians with ("CUDA kernels for rasterization and back propagation",
+ *     Sec. IV, implementation details): EWA projection, tile binning + depth radix
+ *     sort, front-to-back blending of colour, depth, alpha, the instance channel
+ *     ins (Eq. 15) and the object-id argmax map; the colour, depth and instance
+ *     losses (Eq. 7-10) fused into the blend epilogue; and the full backward;
+ *   - the dual-quadric pose step: Q* from (centre, semi-axes, rotation) (Eq. 1-3),
+ *     C* = P Q* P^T (Eq. 4), BBox(C*) and the bbox loss of Eq. 12 with its gradient.
+ *
+ * Conventions shared by every call
+ *   - Every array argument is a DEVICE pointer owned by the caller unless stated;
+ *     the library never frees or retains it past the call's stream work.
+ *   - Calls are asynchronous on the given stream (NULL = legacy default stream);
+ *     results are valid after the stream synchronises.  dqo_render_forward
+ *     synchronises the stream once, after binning, to size the pair buffers.
+ *   - Argument errors return DQO_EINVAL before anything is launched.  CUDA errors
+ *     return DQO_ECUDA; dqo_last_cuda_error() gives the cudaError_t code.
+ *   - A context owns a grow-only device workspace (projected Gaussians, sort
+ *     buffers, tile lists, per-pixel T_final / n_contrib, pixel loss gradients).  The
+ *     state of the last dqo_render_forward stays valid for the matching
+ *     dqo_render_backward on the same context; the next forward replaces it.  A
+ *     context is not thread-safe; use one per host thread / stream.
+ *   - Layouts are C-contiguous row-major; images are [H, W] (+ channel last).
+ */
+#ifndef DQO_H
+#define DQO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define DQO_API __attribute__((visibility("default")))
+#else
+#define DQO_API
+#endif
+
+/* Same type as cudaStream_t (a CUstream handle); no CUDA header needed. */
+typedef struct CUstream_st* dqo_stream;
+
+typedef struct dqo_ctx dqo_ctx;
+
+typedef enum {
+  DQO_OK = 0,
+  DQO_EINVAL = 1,   /* invalid argument (NULL pointer, size, setting out of range) */
+  DQO_ENOMEM = 2,   /* device workspace allocation failed */
+  DQO_ECUDA = 3,    /* a CUDA runtime call or launch failed */
+  DQO_ETIMEOUT = 4, /* a bounded device wait ran out */
+  DQO_ENOTIMPL = 5, /* not implemented */
+  DQO_ESTATE = 6    /* backward without a matching forward on this context */
+} dqo_status;
+
+/* Rasterizer settings.  The paper inherits these from 3D Gaussian Splatting without
+ * stating them; dqo_settings_default() gives the values below. */
+typedef struct {
+  int32_t tile_w, tile_h; /* tile shape in pixels; tile_w * tile_h == 256, tile_w in {8,16,32} (16x16) */
+  float alpha_clamp;      /* alpha = min(alpha_clamp, opacity * G)                  (0.99)  */
+  float alpha_min;        /* a Gaussian with alpha < alpha_min is skipped            (1/255) */
+  float t_stop;           /* stop before the Gaussian that makes T (1-alpha) < t_stop (1e-4)  */
+  float znear;            /* cull Gaussians with camera z < znear (m)                (0.2)   */
+  float lowpass;          /* added to the 2D covariance diagonal (px^2)              (0.3)   */
+  float radius_sigma;     /* screen radius = ceil(radius_sigma * sqrt(lambda_max))   (3)     */
+  float lambda_ins;       /* lambda of Eq. 10                                        (1)     */
+  float bg[3];            /* background colour                                       (0,0,0) */
+  int32_t og_filter;      /* 1: only opaque (OG) Gaussians count toward ins, Eq. 15  (1)     */
+  int32_t batch;          /* Gaussians staged per shared-memory batch: 64..256, multiple of 32 (256) */
+} dqo_settings;
+
+typedef struct {
+  float fx, fy, cx, cy;   /* pinhole intrinsics; pixel (u, v) centre is at integer (u, v) */
+  int32_t width, height;  /* image size in pixels, each 1..32768 */
+  float viewmat[12];      /* row-major [R | t], world -> camera, OpenCV axes (x right, y down, z forward) */
+} dqo_camera;
+
+/* Gaussians as structure-of-arrays (device pointers).  n may be 0. */
+typedef struct {
+  int64_t n;                  /* number of Gaussians, 0 .. 2^26 */
+  int32_t num_objects;        /* object ids live in [0, num_objects), 1 .. 4096 */
+  const float* means;         /* [n,3] world-space centres */
+  const float* log_scales;    /* [n,3] log standard deviations along the local axes */
+  const float* quats;         /* [n,4] rotation quaternion (w,x,y,z), normalised inside */
+  const float* opacity_logit; /* [n]   opacity = sigmoid(logit) */
+  const float* rgb;           /* [n,3] colour (SH degree 0, used as is) */
+  const int32_t* obj_id;      /* [n]   object id; outside [0, num_objects) = no object */
+  const uint8_t* flags;       /* [n]   bit0 = opaque Gaussian (OG), else transparent (TG) */
+} dqo_gaussians;
+
+/* Keyframe targets (device pointers, [H,W] images).  May be NULL as a whole: then no
+ * loss is computed and dqo_render_backward needs explicit pixel gradients. */
+typedef struct {
+  const float* rgb;      /* [H,W,3] observed colour */
+  const float* depth;    /* [H,W]   observed depth, <= 0 = no depth; may be NULL */
+  const int32_t* gt_id;  /* [H,W]   observed instance id, -1 = unlabelled; must not be NULL */
+} dqo_targets;
+
+/* Forward outputs (device pointers; each may be NULL to skip it). */
+typedef struct {
+  float* rgb;       /* [H,W,3] C = sum_i w_i c_i + T_final bg,  w_i = alpha_i T_i */
+  float* depth;     /* [H,W]   D = sum_i w_i z_i (camera z of the Gaussian centre) */
+  float* alpha;     /* [H,W]   A = 1 - T_final */
+  float* ins;       /* [H,W]   sum of w_i over the opaque Gaussians whose id equals the pixel's
+                               gt_id (Eq. 15 reading); 0 without targets */
+  int32_t* id_map;  /* [H,W]   argmax_k sum_{i: id_i = k} w_i, ties to the smaller id; -1 if empty */
+  float* loss;      /* [4]     (L_rgb, L_depth, L_ins, L_total) of Eq. 7-10 (needs targets) */
+} dqo_render_out;
+
+/* Upstream gradients of the forward outputs (device pointers; each may be NULL = zero). */
+typedef struct {
+  const float* rgb;    /* [H,W,3] */
+  const float* depth;  /* [H,W] */
+  const float* alpha;  /* [H,W] */
+  const float* ins;    /* [H,W] */
+} dqo_pixel_grads;
+
+/* Parameter gradients, ACCUMULATED (+=) into caller buffers (each may be NULL). */
+typedef struct {
+  float* means;          /* [n,3] */
+  float* log_scales;     /* [n,3] */
+  float* quats;          /* [n,4] */
+  float* opacity_logit;  /* [n] */
+  float* rgb;            /* [n,3] */
+} dqo_gaussian_grads;
+
+/* Intermediate buffers of the last forward, for inspection and parity tests. */
+typedef enum {
+  DQO_BUF_PROJ = 0,        /* float4 [3][n]: (x, y, a', b') (c', opacity, z, id|OG<<31) (r, g, b, 0);
+                              a', b', c' = conic (a, 2b, c) scaled by -log2(e)/2 */
+  DQO_BUF_RECT = 1,        /* uint16 [n][4]: tile rect (tx0, ty0, tx1, ty1), tx1/ty1 exclusive */
+  DQO_BUF_DEPTH_ORDER = 2, /* uint32 [n]: Gaussian indices sorted by (z bits, index), visible first */
+  DQO_BUF_TILE_RANGES = 3, /* uint32 [T][2]: [start, end) of each tile in the tile list */
+  DQO_BUF_TILE_LIST = 4,   /* uint32 [M]: Gaussian indices ordered by (tile, z bits, index) */
+  DQO_BUF_T_FINAL = 5,     /* float  [H,W] transmittance after the last blended Gaussian */
+  DQO_BUF_N_CONTRIB = 6,   /* uint32 [H,W] 1 + position in the tile list of the last blended Gaussian */
+  DQO_BUF_GRAD2D = 7       /* float  [n][12] backward moments (see dqo_render_backward) */
+} dqo_buffer;
+
+/* ------------------------------------------------------------------ context */
+
+/* Fills *s with the defaults listed in dqo_settings. */
+DQO_API void dqo_settings_default(dqo_settings* s);
+
+/* Creates a context on CUDA device `device` (makes it current for the call).
+ * Returns DQO_EINVAL for a NULL out pointer, DQO_ECUDA if the device is unusable. */
+DQO_API dqo_status dqo_create(dqo_ctx** out, int device);
+
+/* Frees the context's workspace.  NULL is allowed.  Waits for nothing: the caller must
+ * ensure no work using the context is still running. */
+DQO_API void dqo_destroy(dqo_ctx* ctx);
+
+/* Static English name of a status code. */
+DQO_API const char* dqo_status_str(dqo_status s);
+
+/* cudaError_t of the last DQO_ECUDA returned on this context (0 if none). */
+DQO_API int dqo_last_cuda_error(const dqo_ctx* ctx);
+
+/* Library version as major*10000 + minor*100 + patch. */
+DQO_API int dqo_version(void);
+
+/* ------------------------------------------------------------------ rasterizer */
+
+/* Forward render of one keyframe (3DGS rasterizer as used by DQO-MAP, Sec. III-D and
+ * Sec. IV impl.; ins per Eq. 15 reading; losses per Eq. 7-10 reading):
+ *   L_rgb   = 1/(HW) sum_{p: gt(p) >= 0} sum_c |C_c(p) - C^_c(p)|
+ *   L_depth = 1/(HW) sum_{p: gt(p) >= 0, D^(p) > 0} |D(p) - D^(p)|
+ *   L_ins   = 1/(HW) sum_{p: gt(p) >= 0} |ins(p) - 1|
+ *   L_total = L_rgb + L_depth + lambda_ins L_ins
+ * Stages: projection, depth radix sort, tile binning + pair radix sort, tile ranges,
+ * blend + fused loss.  With targets, dL/d(pixel) is kept in the context for the
+ * backward.  out->loss requires targets (DQO_EINVAL otherwise).
+ * Errors: DQO_EINVAL (NULL ctx/settings/gaussians/camera/out, settings out of range,
+ * n > 0 with a NULL input array, targets without gt_id or rgb), DQO_ENOMEM, DQO_ECUDA. */
+DQO_API dqo_status dqo_render_forward(dqo_ctx* ctx, const dqo_settings* settings, const dqo_gaussians* g,
+                              const dqo_camera* cam, const dqo_targets* targets,
+                              dqo_render_out* out, dqo_stream stream);
+
+/* Backward of the last forward on this context (same settings, Gaussians, camera and
+ * targets).  Upstream pixel gradients: `pixel_grads` if non-NULL, else the gradient of
+ * L_total saved by the forward (which then must have had targets).  Per pixel it walks
+ * the blended Gaussians back to front from the saved T_final / n_contrib, reduces
+ * per-Gaussian partials over the warp and the CTA, then adds them to a per-Gaussian
+ * moment record (DQO_BUF_GRAD2D: sum over pixels of g dx, g dy, g dx^2, g dx dy, g dy^2
+ * with g = dL/d(exponent), then dL/dopacity, dL/drgb (3), dL/dz), and chains the record
+ * through the projection to the parameters, ACCUMULATING into `grads`.
+ * Errors: DQO_EINVAL, DQO_ESTATE (no forward on this context, or different n / image
+ * size / tile shape, or neither pixel_grads nor saved loss gradients), DQO_ECUDA. */
+DQO_API dqo_status dqo_render_backward(dqo_ctx* ctx, const dqo_settings* settings, const dqo_gaussians* g,
+                               const dqo_camera* cam, const dqo_targets* targets,
+                               const dqo_pixel_grads* pixel_grads, dqo_gaussian_grads* grads,
+                               dqo_stream stream);
+
+/* Copies an intermediate buffer of the last forward into dst (device or host memory,
+ * asynchronously on `stream`).  *bytes receives the buffer's size; if dst is NULL only
+ * the size is returned.  DQO_EINVAL if capacity < size; DQO_ESTATE without a forward. */
+DQO_API dqo_status dqo_get_buffer(dqo_ctx* ctx, dqo_buffer which, void* dst, size_t capacity,
+                          size_t* bytes, dqo_stream stream);
+
+/* Phases timed by dqo_set_timing / dqo_get_timings. */
+typedef enum {
+  DQO_PHASE_PROJECT = 0,     /* K1 projection */
+  DQO_PHASE_DEPTH_SORT = 1,  /* scan of tiles per Gaussian, depth radix sort, depth ranks */
+  DQO_PHASE_BINNING = 2,     /* pair emission, pair radix sort, tile ranges (after the host sync) */
+  DQO_PHASE_BLEND_FWD = 3,   /* K6 blend + fused losses (+ loss reduction) */
+  DQO_PHASE_BLEND_BWD = 4,   /* K7 blend backward */
+  DQO_PHASE_PROJECT_BWD = 5, /* K8 projection backward */
+  DQO_PHASE_QUADRIC = 6,     /* dual-quadric projection or bbox loss */
+  DQO_PHASE_COUNT = 7
+} dqo_phase;
+
+/* Enables (1) or disables (0) CUDA-event timing of the phases above on the calls'
+ * streams.  Off by default; when on, every call records a start / end event per phase. */
+DQO_API dqo_status dqo_set_timing(dqo_ctx* ctx, int enable);
+
+/* Device milliseconds of each phase in its most recent timed call (ms[DQO_PHASE_COUNT];
+ * -1 for a phase not run since timing was enabled).  Waits for those events.
+ * n = capacity of ms.  DQO_EINVAL if ctx or ms is NULL or n < 1. */
+DQO_API dqo_status dqo_get_timings(dqo_ctx* ctx, float* ms, int32_t n);
+
+/* Number of kernels this context has launched since it was created. */
+DQO_API int64_t dqo_launch_count(const dqo_ctx* ctx);
+
+/* Sizes of the last forward: tile-Gaussian pairs M, visible Gaussians, tiles. */
+DQO_API dqo_status dqo_get_counts(const dqo_ctx* ctx, int64_t* n_pairs, int64_t* n_visible, int32_t* n_tiles);
+
+/* ------------------------------------------------------------------ dual quadrics */
+
+/* Projects dual quadrics into views (Eq. 1-4; reading C* = P Q* P^T).
+ * params [nq,9]: centre (3), log semi-axes (3), rotation vector (3); Q* = Z diag(a^2,
+ *   b^2, c^2, -1) Z^T with Z = [R t; 0 1].
+ * P [nv,12]: row-major 3x4 camera matrices K [R|t].
+ * Pairs in CSR: the pairs of quadric q are k = q_ptr[q] .. q_ptr[q+1]-1 (q_ptr[0] = 0,
+ *   non-decreasing, q_ptr[nq] = npairs) and pair k uses view pair_v[k] in [0, nv).
+ * Outputs per pair (each may be NULL): conic [npairs,6] = (c11 c12 c13 c22 c23 c33) of
+ *   C*, bbox [npairs,4] = (u_min, v_min, u_max, v_max), valid [npairs].  A pair is valid
+ *   iff c33 < 0 (ellipsoid clear of the principal plane), the centre is in front, and
+ *   both tangent discriminants are positive; invalid pairs get a zero box.
+ * Index arrays are device arrays; out-of-range view indices give valid = 0.
+ * Errors: DQO_EINVAL (nq < 0, npairs < 0, NULL required arrays), DQO_ECUDA. */
+DQO_API dqo_status dqo_quadric_project(dqo_ctx* ctx, int32_t nq, const float* params, int32_t nv,
+                               const float* P, const int32_t* q_ptr, const int32_t* pair_v,
+                               int32_t npairs, float* conic, float* bbox, uint8_t* valid,
+                               dqo_stream stream);
+
+/* Bbox loss of Eq. 12 (reading: J_k = sum over the valid views of quadric k of
+ * (1 - IoU(BBox(C*_k), obs))) and its gradient.  Same pair layout as
+ * dqo_quadric_project; obs_bbox [npairs,4] = (u_min, v_min, u_max, v_max).
+ * loss [nq] and dparams [nq,9] are OVERWRITTEN (either may be NULL).  The gradient of
+ * max/min in the intersection follows the predicted box only when it is strictly the
+ * selected one; zero overlap gives a zero IoU gradient.
+ * Errors: as dqo_quadric_project. */
+DQO_API dqo_status dqo_quadric_bbox_loss(dqo_ctx* ctx, int32_t nq, const float* params, int32_t nv,
+                                 const float* P, const int32_t* q_ptr, const int32_t* pair_v,
+                                 int32_t npairs, const float* obs_bbox, float* loss,
+                                 float* dparams, dqo_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DQO_H */

@@ -249,6 +249,7 @@ struct Contrib {
     int64_t g;
     double alpha, T, G, dx, dy;
     bool clamped;
+    size_t pos;  // position in the tile list
 };
 
 struct PixelResult {
@@ -257,6 +258,9 @@ struct PixelResult {
     int32_t id = -1;
     double id_margin = 0;
     uint8_t amb = 0;        // bit0 threshold, bit1 depth tie, bit2 tile membership, bit3 loss kink
+    int64_t amb_pos = -1;   // first list position with a threshold decision near its threshold
+    int64_t stop_pos = -1;  // list position where the walk stopped (-1: ran to the end)
+    std::vector<int64_t> amb_rect;  // Gaussians whose uncertain tile membership matters here
     std::vector<Contrib> contribs;
 };
 
@@ -280,12 +284,21 @@ PixelResult blend_pixel(const OSettings& st, const Inputs& in, const std::vector
         const double oG = P.opac * G;
         bool clamped = oG > st.alpha_clamp;
         const double alpha = clamped ? st.alpha_clamp : oG;
-        if (near_rel(oG, st.alpha_clamp, st.amb_rel)) R.amb |= AMB_THRESH;
-        if (near_rel(alpha, st.alpha_min, st.amb_rel)) R.amb |= AMB_THRESH;
+        const bool amb_a = near_rel(oG, st.alpha_clamp, st.amb_rel) || near_rel(alpha, st.alpha_min, st.amb_rel);
+        if (amb_a) {
+            R.amb |= AMB_THRESH;
+            if (R.amb_pos < 0) R.amb_pos = (int64_t)j;
+        }
         if (alpha < st.alpha_min) continue;
         const double Tn = T * (1 - alpha);
-        if (near_rel(Tn, st.t_stop, st.amb_rel)) R.amb |= AMB_THRESH;
-        if (Tn < st.t_stop) break;
+        if (near_rel(Tn, st.t_stop, st.amb_rel)) {
+            R.amb |= AMB_THRESH;
+            if (R.amb_pos < 0) R.amb_pos = (int64_t)j;
+        }
+        if (Tn < st.t_stop) {
+            R.stop_pos = (int64_t)j;
+            break;
+        }
         if (last_z >= 0 && std::fabs(P.pc[2] - last_z) <= 1e-6 * P.pc[2]) R.amb |= AMB_DEPTH;
         last_z = P.pc[2];
         const double w = alpha * T;
@@ -299,7 +312,7 @@ PixelResult blend_pixel(const OSettings& st, const Inputs& in, const std::vector
             const bool og = !st.og_filter || (in.flags[g] & 1);
             if (og && id == gt) R.ins += w;
         }
-        if (keep) R.contribs.push_back({g, alpha, T, G, dx, dy, clamped});
+        if (keep) R.contribs.push_back({g, alpha, T, G, dx, dy, clamped, j});
         T = Tn;
         R.n_contrib = (int64_t)j + 1;
     }
@@ -476,16 +489,37 @@ Inputs make_inputs(int64_t n, const double* means, const double* log_scales, con
     return Inputs{n, means, log_scales, quats, opacity_logit, rgb, obj_id, flags};
 }
 
-// Marks tiles whose membership is ambiguous for some Gaussian: those in the union of its
-// perturbed rects but not in their intersection.
-void rect_ambiguity(const OSettings& st, const OCamera& cam, const std::vector<Proj>& pr,
-                    std::vector<uint8_t>& tile_amb, int ntx, int nty) {
-    (void)st; (void)cam;
-    for (const Proj& P : pr) {
+// Per tile, the Gaussians whose tile membership is uncertain there: tiles in the union of
+// a Gaussian's perturbed rects but not in their intersection.
+std::vector<std::vector<int64_t>> rect_ambiguity(const std::vector<Proj>& pr, int ntx, int nty) {
+    std::vector<std::vector<int64_t>> amb((size_t)ntx * nty);
+    for (int64_t g = 0; g < (int64_t)pr.size(); ++g) {
+        const Proj& P = pr[g];
         if (!P.ambiguous) continue;
         for (int ty = P.urect[1]; ty < P.urect[3] && ty < nty; ++ty)
             for (int tx = P.urect[0]; tx < P.urect[2] && tx < ntx; ++tx)
-                if (!covers(P.irect, tx, ty)) tile_amb[(size_t)ty * ntx + tx] = 1;
+                if (!covers(P.irect, tx, ty)) amb[(size_t)ty * ntx + tx].push_back(g);
+    }
+    return amb;
+}
+
+// A pixel's result depends on an uncertain membership only if that Gaussian would reach
+// alpha_min there; records those Gaussians and flags the pixel.
+void rect_check(const OSettings& st, const std::vector<Proj>& pr, const std::vector<int64_t>& cand, int px,
+                int py, PixelResult& R) {
+    for (int64_t g : cand) {
+        const Proj& P = pr[g];
+        if (P.opac <= 0 || P.conic[0] == 0) {
+            if (!P.visible) { R.amb |= AMB_RECT; R.amb_rect.push_back(g); }
+            continue;
+        }
+        const double dx = px - P.xy[0], dy = py - P.xy[1];
+        const double power = -0.5 * (P.conic[0] * dx * dx + P.conic[2] * dy * dy) - P.conic[1] * dx * dy;
+        const double alpha = std::min(st.alpha_clamp, P.opac * std::exp(power));
+        if (alpha >= st.alpha_min * (1 - st.amb_rel)) {
+            R.amb |= AMB_RECT;
+            R.amb_rect.push_back(g);
+        }
     }
 }
 
@@ -532,8 +566,7 @@ int oracle_render(const OSettings* st, const OCamera* cam, int64_t n, const doub
     if (W <= 0 || H <= 0 || st->tile_w <= 0 || st->tile_h <= 0) return 1;
     const int ntx = (W + st->tile_w - 1) / st->tile_w, nty = (H + st->tile_h - 1) / st->tile_h;
     std::vector<Proj> pr = project_all(*st, *cam, in);
-    std::vector<uint8_t> tile_amb((size_t)ntx * nty, 0);
-    rect_ambiguity(*st, *cam, pr, tile_amb, ntx, nty);
+    const std::vector<std::vector<int64_t>> tile_amb = rect_ambiguity(pr, ntx, nty);
     std::vector<int64_t> all;
     if (mode == 1) {
         for (int64_t i = 0; i < n; ++i) all.push_back(i);
@@ -558,7 +591,7 @@ int oracle_render(const OSettings* st, const OCamera* cam, int64_t n, const doub
                             if (pr[i].visible && covers(pr[i].rect, px / st->tile_w, py / st->tile_h)) Lp.push_back(i);
                     }
                     PixelResult R = blend_pixel(*st, in, pr, mode == 0 ? L : Lp, px, py, gt, false);
-                    if (tile_amb[(size_t)ty * ntx + tx]) R.amb |= AMB_RECT;
+                    rect_check(*st, pr, tile_amb[(size_t)ty * ntx + tx], px, py, R);
                     PixelGrad pg{{0, 0, 0}, 0, 0, 0};
                     if (t_gt) pixel_loss(*st, R, t_rgb + 3 * p, t_depth ? t_depth[p] : 0.0, gt, inv_hw, loss, pg, R.amb);
                     if (o_rgb) for (int c = 0; c < 3; ++c) o_rgb[3 * p + c] = R.C[c];
@@ -595,8 +628,7 @@ int oracle_render_pixels(const OSettings* st, const OCamera* cam, int64_t n, con
     const int W = cam->width, H = cam->height;
     const int ntx = (W + st->tile_w - 1) / st->tile_w, nty = (H + st->tile_h - 1) / st->tile_h;
     std::vector<Proj> pr = project_all(*st, *cam, in);
-    std::vector<uint8_t> tile_amb((size_t)ntx * nty, 0);
-    rect_ambiguity(*st, *cam, pr, tile_amb, ntx, nty);
+    const std::vector<std::vector<int64_t>> tile_amb = rect_ambiguity(pr, ntx, nty);
     for (int64_t k = 0; k < npix; ++k) {
         const int px = pxy[2 * k], py = pxy[2 * k + 1];
         if (px < 0 || px >= W || py < 0 || py >= H) return 1;
@@ -604,7 +636,7 @@ int oracle_render_pixels(const OSettings* st, const OCamera* cam, int64_t n, con
         std::vector<int64_t> L = tile_list(pr, tx, ty);
         const int32_t gt = t_gt ? t_gt[(size_t)py * W + px] : -1;
         PixelResult R = blend_pixel(*st, in, pr, L, px, py, gt, false);
-        if (tile_amb[(size_t)ty * ntx + tx]) R.amb |= AMB_RECT;
+        rect_check(*st, pr, tile_amb[(size_t)ty * ntx + tx], px, py, R);
         if (o_rgb) for (int c = 0; c < 3; ++c) o_rgb[3 * k + c] = R.C[c];
         if (o_depth) o_depth[k] = R.D;
         if (o_alpha) o_alpha[k] = R.A;
@@ -633,8 +665,7 @@ int oracle_render_backward(const OSettings* st, const OCamera* cam, int64_t n, c
     if (W <= 0 || H <= 0) return 1;
     const int ntx = (W + st->tile_w - 1) / st->tile_w, nty = (H + st->tile_h - 1) / st->tile_h;
     std::vector<Proj> pr = project_all(*st, *cam, in);
-    std::vector<uint8_t> tile_amb((size_t)ntx * nty, 0);
-    rect_ambiguity(*st, *cam, pr, tile_amb, ntx, nty);
+    const std::vector<std::vector<int64_t>> tile_amb = rect_ambiguity(pr, ntx, nty);
     std::vector<double> g2((size_t)n * G2, 0.0);
     const double inv_hw = 1.0 / ((double)W * H);
     for (int ty = 0; ty < nty; ++ty)
@@ -645,7 +676,7 @@ int oracle_render_backward(const OSettings* st, const OCamera* cam, int64_t n, c
                     const size_t p = (size_t)py * W + px;
                     const int32_t gt = t_gt ? t_gt[p] : -1;
                     PixelResult R = blend_pixel(*st, in, pr, L, px, py, gt, true);
-                    if (tile_amb[(size_t)ty * ntx + tx]) R.amb |= AMB_RECT;
+                    rect_check(*st, pr, tile_amb[(size_t)ty * ntx + tx], px, py, R);
                     PixelGrad pg{{0, 0, 0}, 0, 0, 0};
                     if (dl) {
                         const double* d = dl + 6 * p;
@@ -656,13 +687,28 @@ int oracle_render_backward(const OSettings* st, const OCamera* cam, int64_t n, c
                     }
                     pixel_backward(*st, in, pr, R, pg, gt, g2.data());
                     if (g_amb && R.amb) {
-                        // every Gaussian this pixel walks may see its gradient change
-                        const uint8_t bits = (R.amb & (AMB_THRESH | AMB_DEPTH | AMB_RECT)) ? 1 : 0;
-                        const uint8_t kb = (R.amb & AMB_KINK) ? 8 : 0;
-                        for (const Contrib& c : R.contribs) g_amb[c.g] |= (uint8_t)(bits | kb);
-                        if (bits)
-                            for (int64_t g : L)
-                                if (covers(pr[g].rect, tx, ty)) g_amb[g] |= 1;
+                        // Gaussians whose gradient may change with the uncertain decision:
+                        // a threshold at list position j affects L[j..]; a depth tie, an
+                        // uncertain tile membership or an L1 kink affect every contributor
+                        // (and the uncertain member itself).
+                        if (R.amb & AMB_THRESH) {
+                            g_amb[L[(size_t)R.amb_pos]] |= 1;
+                            for (const Contrib& c : R.contribs)
+                                if (c.pos >= (size_t)R.amb_pos) g_amb[c.g] |= 1;
+                            // past an uncertain stop, Gaussians that reach alpha_min here may join
+                            if (R.stop_pos >= R.amb_pos) {
+                                std::vector<int64_t> tail(L.begin() + R.stop_pos, L.end());
+                                PixelResult T2;
+                                rect_check(*st, pr, tail, px, py, T2);
+                                for (int64_t g : T2.amb_rect) g_amb[g] |= 1;
+                            }
+                        }
+                        if (R.amb & (AMB_DEPTH | AMB_RECT | AMB_KINK)) {
+                            const uint8_t b = (R.amb & (AMB_DEPTH | AMB_RECT)) ? 1 : 0;
+                            const uint8_t kb = (R.amb & AMB_KINK) ? 8 : 0;
+                            for (const Contrib& c : R.contribs) g_amb[c.g] |= (uint8_t)(b | kb);
+                            for (int64_t g : R.amb_rect) g_amb[g] |= 1;
+                        }
                     }
                 }
         }

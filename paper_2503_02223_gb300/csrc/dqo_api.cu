@@ -1,0 +1,602 @@
+// Host side of the C ABI declared in include/dqo.h: argument checks, the context's
+// grow-only workspace, and the launch sequence of each entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "dqo_internal.cuh"
+
+using namespace dqo;
+
+namespace {
+
+struct Buf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+}  // namespace
+
+struct dqo_ctx {
+  int device = 0;
+  int last_err = 0;
+  // per-Gaussian
+  Buf p0, p1, p2, rect, ntiles, zkey_a, zkey_b, zval_a, zval_b, rank, gid, offsets, grad2d;
+  // sorting scratch
+  Buf scan_scratch, hist, pair_a, pair_b, list;
+  // per-tile / per-pixel
+  Buf ranges, loss_part, T_final, n_contrib, dl_rgb, dl_depth, dl_ins;
+  Buf counters;             // device: [0] uint64 total pairs, [1] uint32 n_visible
+  uint64_t* host_counters = nullptr;  // pinned mirror
+  // state of the last forward
+  bool have_fwd = false;
+  bool fwd_dl = false;
+  int64_t n = 0, m = 0, n_vis = 0;
+  int W = 0, H = 0, tile_w = 0, tile_h = 0, ntx = 0, nty = 0;
+  int order_sel = 0;
+  // phase timing and launch accounting
+  bool timing = false;
+  cudaEvent_t ev[2 * DQO_PHASE_COUNT] = {};
+  bool pending[DQO_PHASE_COUNT] = {};
+  float last_ms[DQO_PHASE_COUNT] = {};
+  int64_t launches = 0;
+};
+
+namespace {
+
+dqo_status cuda_fail(dqo_ctx* c, cudaError_t e) {
+  if (c) c->last_err = (int)e;
+  return e == cudaErrorMemoryAllocation ? DQO_ENOMEM : DQO_ECUDA;
+}
+
+#define DQO_CUDA(ctx, expr)                         \
+  do {                                              \
+    cudaError_t e_ = (expr);                        \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_); \
+  } while (0)
+
+cudaError_t ensure(Buf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.cap >= bytes) return cudaSuccess;
+  if (b.p) {
+    cudaError_t e = cudaFree(b.p);
+    if (e != cudaSuccess) return e;
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  const size_t want = std::max(bytes, b.cap + b.cap / 4);
+  cudaError_t e = cudaMalloc(&b.p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+      b.p = nullptr;
+      return e;
+    }
+    b.cap = bytes;
+    return cudaSuccess;
+  }
+  b.cap = want;
+  return cudaSuccess;
+}
+
+template <typename T>
+T* as(const Buf& b) {
+  return reinterpret_cast<T*>(b.p);
+}
+
+int bits_for(uint64_t v) {  // smallest b with v <= 2^b (at least 1)
+  int b = 1;
+  while (b < 64 && (uint64_t(1) << b) < v) ++b;
+  return b;
+}
+
+dqo_status check_settings(const dqo_settings* s) {
+  if (!s) return DQO_EINVAL;
+  if (!(s->tile_w == 8 || s->tile_w == 16 || s->tile_w == 32) || s->tile_w * s->tile_h != kThreads)
+    return DQO_EINVAL;
+  if (s->batch < 32 || s->batch > 256 || (s->batch & 31)) return DQO_EINVAL;
+  if (!(s->alpha_clamp > 0.f) || !(s->alpha_min >= 0.f) || !(s->t_stop >= 0.f) || !(s->znear > 0.f) ||
+      !(s->lowpass >= 0.f) || !(s->radius_sigma > 0.f) || !(s->lambda_ins >= 0.f))
+    return DQO_EINVAL;
+  return DQO_OK;
+}
+
+dqo_status check_gaussians(const dqo_gaussians* g) {
+  if (!g) return DQO_EINVAL;
+  if (g->n < 0 || g->n > (int64_t(1) << 26)) return DQO_EINVAL;
+  if (g->num_objects < 1 || g->num_objects > kMaxObjects) return DQO_EINVAL;
+  if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logit || !g->rgb || !g->obj_id ||
+                   !g->flags))
+    return DQO_EINVAL;
+  return DQO_OK;
+}
+
+dqo_status check_camera(const dqo_camera* c) {
+  if (!c) return DQO_EINVAL;
+  if (c->width < 1 || c->height < 1 || c->width > 32768 || c->height > 32768) return DQO_EINVAL;
+  if (!(c->fx > 0.f) || !(c->fy > 0.f)) return DQO_EINVAL;
+  return DQO_OK;
+}
+
+struct PhaseTimer {
+  dqo_ctx* c;
+  int ph;
+  cudaStream_t s;
+  PhaseTimer(dqo_ctx* c_, int ph_, cudaStream_t s_) : c(c_), ph(ph_), s(s_) {
+    if (c->timing) cudaEventRecord(c->ev[2 * ph], s);
+  }
+  ~PhaseTimer() {
+    if (c->timing) {
+      cudaEventRecord(c->ev[2 * ph + 1], s);
+      c->pending[ph] = true;
+    }
+  }
+};
+
+// kernels launched by one radix sort of n keys over end_bit bits, and by one scan
+int64_t scan_launches(int64_t n) { return n > 0 ? 3 : 0; }
+int64_t sort_launches(int64_t n, int end_bit) {
+  if (n <= 1 || end_bit <= 0) return 0;
+  const int passes = (end_bit + kRadixBits - 1) / kRadixBits;
+  return passes * (2 + scan_launches(1));
+}
+
+RasterParams make_params(const dqo_settings* s, const dqo_gaussians* g, const dqo_camera* c) {
+  RasterParams rp;
+  rp.W = c->width;
+  rp.H = c->height;
+  rp.tile_w = s->tile_w;
+  rp.tile_h = s->tile_h;
+  rp.ntx = (c->width + s->tile_w - 1) / s->tile_w;
+  rp.nty = (c->height + s->tile_h - 1) / s->tile_h;
+  rp.fx = c->fx;
+  rp.fy = c->fy;
+  rp.cx = c->cx;
+  rp.cy = c->cy;
+  std::memcpy(rp.vm, c->viewmat, sizeof(rp.vm));
+  rp.alpha_clamp = s->alpha_clamp;
+  rp.alpha_min = s->alpha_min;
+  rp.t_stop = s->t_stop;
+  rp.znear = s->znear;
+  rp.lowpass = s->lowpass;
+  rp.radius_sigma = s->radius_sigma;
+  rp.lambda_ins = s->lambda_ins;
+  rp.bg[0] = s->bg[0];
+  rp.bg[1] = s->bg[1];
+  rp.bg[2] = s->bg[2];
+  rp.og_filter = s->og_filter ? 1 : 0;
+  rp.batch = s->batch;
+  rp.num_objects = g->num_objects;
+  return rp;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dqo_settings_default(dqo_settings* s) {
+  if (!s) return;
+  s->tile_w = 16;
+  s->tile_h = 16;
+  s->alpha_clamp = 0.99f;
+  s->alpha_min = 1.0f / 255.0f;
+  s->t_stop = 1e-4f;
+  s->znear = 0.2f;
+  s->lowpass = 0.3f;
+  s->radius_sigma = 3.0f;
+  s->lambda_ins = 1.0f;
+  s->bg[0] = s->bg[1] = s->bg[2] = 0.0f;
+  s->og_filter = 1;
+  s->batch = 256;
+}
+
+int dqo_version(void) { return 100; }
+
+const char* dqo_status_str(dqo_status s) {
+  switch (s) {
+    case DQO_OK: return "ok";
+    case DQO_EINVAL: return "invalid argument";
+    case DQO_ENOMEM: return "out of device memory";
+    case DQO_ECUDA: return "CUDA error";
+    case DQO_ETIMEOUT: return "device wait timed out";
+    case DQO_ENOTIMPL: return "not implemented";
+    case DQO_ESTATE: return "no matching forward state";
+  }
+  return "unknown status";
+}
+
+dqo_status dqo_create(dqo_ctx** out, int device) {
+  if (!out) return DQO_EINVAL;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return DQO_ECUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return DQO_ECUDA;
+  dqo_ctx* c = new (std::nothrow) dqo_ctx();
+  if (!c) return DQO_ENOMEM;
+  c->device = device;
+  if (ensure(c->counters, 64) != cudaSuccess ||
+      cudaMallocHost(reinterpret_cast<void**>(&c->host_counters), 64) != cudaSuccess) {
+    dqo_destroy(c);
+    return DQO_ENOMEM;
+  }
+  *out = c;
+  return DQO_OK;
+}
+
+void dqo_destroy(dqo_ctx* c) {
+  if (!c) return;
+  Buf* all[] = {&c->p0, &c->p1, &c->p2, &c->rect, &c->ntiles, &c->zkey_a, &c->zkey_b, &c->zval_a,
+                &c->zval_b, &c->rank, &c->gid, &c->offsets, &c->grad2d, &c->scan_scratch, &c->hist,
+                &c->pair_a, &c->pair_b, &c->list, &c->ranges, &c->loss_part, &c->T_final, &c->n_contrib,
+                &c->dl_rgb, &c->dl_depth, &c->dl_ins, &c->counters};
+  for (Buf* b : all)
+    if (b->p) cudaFree(b->p);
+  if (c->host_counters) cudaFreeHost(c->host_counters);
+  for (int i = 0; i < 2 * DQO_PHASE_COUNT; ++i)
+    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  delete c;
+}
+
+int dqo_last_cuda_error(const dqo_ctx* c) { return c ? c->last_err : 0; }
+
+dqo_status dqo_render_forward(dqo_ctx* c, const dqo_settings* s, const dqo_gaussians* g, const dqo_camera* cam,
+                              const dqo_targets* t, dqo_render_out* out, dqo_stream stream_) {
+  if (!c || !out) return DQO_EINVAL;
+  dqo_status st;
+  if ((st = check_settings(s)) != DQO_OK) return st;
+  if ((st = check_gaussians(g)) != DQO_OK) return st;
+  if ((st = check_camera(cam)) != DQO_OK) return st;
+  if (t && (!t->gt_id || !t->rgb)) return DQO_EINVAL;
+  if (out->loss && !t) return DQO_EINVAL;
+  cudaStream_t s_ = reinterpret_cast<cudaStream_t>(stream_);
+  DQO_CUDA(c, cudaSetDevice(c->device));
+  c->have_fwd = false;
+
+  const RasterParams rp = make_params(s, g, cam);
+  const int64_t n = g->n;
+  const int64_t HW = (int64_t)rp.W * rp.H;
+  const int tiles = rp.ntx * rp.nty;
+
+  // ---- workspace
+  DQO_CUDA(c, ensure(c->p0, 16 * n));
+  DQO_CUDA(c, ensure(c->p1, 16 * n));
+  DQO_CUDA(c, ensure(c->p2, 16 * n));
+  DQO_CUDA(c, ensure(c->rect, 8 * n));
+  DQO_CUDA(c, ensure(c->ntiles, 4 * n));
+  DQO_CUDA(c, ensure(c->zkey_a, 4 * n));
+  DQO_CUDA(c, ensure(c->zkey_b, 4 * n));
+  DQO_CUDA(c, ensure(c->zval_a, 4 * n));
+  DQO_CUDA(c, ensure(c->zval_b, 4 * n));
+  DQO_CUDA(c, ensure(c->rank, 4 * n));
+  DQO_CUDA(c, ensure(c->gid, 4 * n));
+  DQO_CUDA(c, ensure(c->offsets, 4 * n));
+  DQO_CUDA(c, ensure(c->ranges, 8 * (size_t)tiles));
+  DQO_CUDA(c, ensure(c->loss_part, 12 * (size_t)tiles));
+  DQO_CUDA(c, ensure(c->T_final, 4 * HW));
+  DQO_CUDA(c, ensure(c->n_contrib, 4 * HW));
+  if (t) {
+    DQO_CUDA(c, ensure(c->dl_rgb, 12 * HW));
+    DQO_CUDA(c, ensure(c->dl_depth, 4 * HW));
+    DQO_CUDA(c, ensure(c->dl_ins, 4 * HW));
+  }
+  DQO_CUDA(c, ensure(c->scan_scratch, 8 * std::max(scan_scratch_words(n), scan_scratch_words(radix_scratch_words(n)))));
+  DQO_CUDA(c, ensure(c->hist, 4 * radix_scratch_words(n)));
+  DQO_CUDA(c, cudaMemsetAsync(c->counters.p, 0, 64, s_));
+
+  uint64_t* d_total = as<uint64_t>(c->counters);
+  uint32_t* d_nvis = reinterpret_cast<uint32_t*>(as<uint64_t>(c->counters) + 1);
+
+  // ---- K1 projection
+  ProjBuffers pb;
+  const int64_t nb_launch = n > 0 ? 1 : 0;
+  pb.p0 = as<float4>(c->p0);
+  pb.p1 = as<float4>(c->p1);
+  pb.p2 = as<float4>(c->p2);
+  pb.rect = as<ushort4>(c->rect);
+  pb.ntiles = as<uint32_t>(c->ntiles);
+  pb.zkey = as<uint32_t>(c->zkey_a);
+  pb.zval = as<uint32_t>(c->zval_a);
+  pb.gid = as<uint32_t>(c->gid);
+  pb.n_visible = d_nvis;
+  {
+    PhaseTimer pt(c, DQO_PHASE_PROJECT, s_);
+    DQO_CUDA(c, launch_preprocess(rp, *g, pb, s_));
+  }
+  c->launches += nb_launch;
+
+  // ---- K2 scan of tiles per Gaussian, depth sort, ranks
+  int sel = 0;
+  {
+    PhaseTimer pt(c, DQO_PHASE_DEPTH_SORT, s_);
+    DQO_CUDA(c, launch_exclusive_scan(as<uint32_t>(c->ntiles), as<uint32_t>(c->offsets), n,
+                                      as<uint64_t>(c->scan_scratch), d_total, s_));
+    DQO_CUDA(c, radix_sort_u32(as<uint32_t>(c->zkey_a), as<uint32_t>(c->zkey_b), as<uint32_t>(c->zval_a),
+                               as<uint32_t>(c->zval_b), n, 32, as<uint32_t>(c->hist),
+                               as<uint64_t>(c->scan_scratch), &sel, s_));
+    DQO_CUDA(c, launch_rank_scatter(sel ? as<uint32_t>(c->zval_b) : as<uint32_t>(c->zval_a), n,
+                                    as<uint32_t>(c->rank), s_));
+  }
+  const uint32_t* order = sel ? as<uint32_t>(c->zval_b) : as<uint32_t>(c->zval_a);
+  c->order_sel = sel;
+  c->launches += scan_launches(n) + sort_launches(n, 32) + nb_launch;
+
+  // ---- pair count to the host (the one synchronisation of the forward)
+  DQO_CUDA(c, cudaMemcpyAsync(c->host_counters, c->counters.p, 16, cudaMemcpyDeviceToHost, s_));
+  DQO_CUDA(c, cudaStreamSynchronize(s_));
+  const uint64_t m = c->host_counters[0];
+  const uint64_t n_vis = (uint32_t)(c->host_counters[1] & 0xFFFFFFFFu);
+  if (m >= (uint64_t(1) << 31)) return DQO_ENOMEM;  // tile ranges are int32 in the blend kernels
+
+  // ---- K3-K5 pairs, pair sort, tile ranges
+  {
+  PhaseTimer pt(c, DQO_PHASE_BINNING, s_);
+  DQO_CUDA(c, cudaMemsetAsync(c->ranges.p, 0, 8 * (size_t)tiles, s_));
+  if (m > 0) {
+    const int rank_bits = bits_for(n_vis);
+    const int tile_bits = bits_for((uint64_t)tiles);
+    const int end_bit = rank_bits + tile_bits;
+    const bool k32 = end_bit <= 32;
+    const size_t ks = k32 ? 4 : 8;
+    DQO_CUDA(c, ensure(c->pair_a, ks * m));
+    DQO_CUDA(c, ensure(c->pair_b, ks * m));
+    DQO_CUDA(c, ensure(c->list, 4 * m));
+    DQO_CUDA(c, ensure(c->hist, 4 * radix_scratch_words((int64_t)m)));
+    DQO_CUDA(c, ensure(c->scan_scratch, 8 * scan_scratch_words(radix_scratch_words((int64_t)m))));
+    int psel = 0;
+    c->launches += 2 + sort_launches((int64_t)m, end_bit);
+    if (k32) {
+      DQO_CUDA(c, launch_emit_pairs_u32(as<ushort4>(c->rect), as<uint32_t>(c->offsets), as<uint32_t>(c->rank), n,
+                                        rp.ntx, rank_bits, as<uint32_t>(c->pair_a), s_));
+      DQO_CUDA(c, radix_sort_u32(as<uint32_t>(c->pair_a), as<uint32_t>(c->pair_b), nullptr, nullptr, (int64_t)m,
+                                 end_bit, as<uint32_t>(c->hist), as<uint64_t>(c->scan_scratch), &psel, s_));
+      DQO_CUDA(c, launch_tile_ranges_u32(psel ? as<uint32_t>(c->pair_b) : as<uint32_t>(c->pair_a), (int64_t)m,
+                                         rank_bits, order, as<uint2>(c->ranges), as<uint32_t>(c->list), s_));
+    } else {
+      DQO_CUDA(c, launch_emit_pairs_u64(as<ushort4>(c->rect), as<uint32_t>(c->offsets), as<uint32_t>(c->rank), n,
+                                        rp.ntx, rank_bits, as<uint64_t>(c->pair_a), s_));
+      DQO_CUDA(c, radix_sort_u64(as<uint64_t>(c->pair_a), as<uint64_t>(c->pair_b), (int64_t)m, end_bit,
+                                 as<uint32_t>(c->hist), as<uint64_t>(c->scan_scratch), &psel, s_));
+      DQO_CUDA(c, launch_tile_ranges_u64(psel ? as<uint64_t>(c->pair_b) : as<uint64_t>(c->pair_a), (int64_t)m,
+                                         rank_bits, order, as<uint2>(c->ranges), as<uint32_t>(c->list), s_));
+    }
+  } else {
+    DQO_CUDA(c, ensure(c->list, 4));
+  }
+  }
+
+  // ---- K6 blend + fused losses
+  BlendFwdArgs a;
+  a.rp = rp;
+  a.p0 = pb.p0;
+  a.p1 = pb.p1;
+  a.p2 = pb.p2;
+  a.gid = pb.gid;
+  a.ranges = as<uint2>(c->ranges);
+  a.list = as<uint32_t>(c->list);
+  a.t_rgb = t ? t->rgb : nullptr;
+  a.t_depth = t ? t->depth : nullptr;
+  a.t_gt = t ? t->gt_id : nullptr;
+  a.o_rgb = out->rgb;
+  a.o_depth = out->depth;
+  a.o_alpha = out->alpha;
+  a.o_ins = out->ins;
+  a.o_id = out->id_map;
+  a.T_final = as<float>(c->T_final);
+  a.n_contrib = as<uint32_t>(c->n_contrib);
+  a.dl_rgb = t ? as<float>(c->dl_rgb) : nullptr;
+  a.dl_depth = t ? as<float>(c->dl_depth) : nullptr;
+  a.dl_ins = t ? as<float>(c->dl_ins) : nullptr;
+  a.loss_part = as<float>(c->loss_part);
+  {
+    PhaseTimer pt(c, DQO_PHASE_BLEND_FWD, s_);
+    DQO_CUDA(c, launch_blend_forward(a, out->id_map != nullptr, s_));
+    if (out->loss)
+      DQO_CUDA(c, launch_loss_reduce(as<float>(c->loss_part), tiles, rp.lambda_ins,
+                                     (float)(1.0 / ((double)rp.W * (double)rp.H)), out->loss, s_));
+  }
+  c->launches += (tiles > 0 ? 1 : 0) + (out->loss ? 1 : 0);
+
+  c->have_fwd = true;
+  c->fwd_dl = t != nullptr;
+  c->n = n;
+  c->m = (int64_t)m;
+  c->n_vis = (int64_t)n_vis;
+  c->W = rp.W;
+  c->H = rp.H;
+  c->tile_w = rp.tile_w;
+  c->tile_h = rp.tile_h;
+  c->ntx = rp.ntx;
+  c->nty = rp.nty;
+  return DQO_OK;
+}
+
+dqo_status dqo_render_backward(dqo_ctx* c, const dqo_settings* s, const dqo_gaussians* g, const dqo_camera* cam,
+                               const dqo_targets* t, const dqo_pixel_grads* pg, dqo_gaussian_grads* grads,
+                               dqo_stream stream_) {
+  if (!c || !grads) return DQO_EINVAL;
+  dqo_status st;
+  if ((st = check_settings(s)) != DQO_OK) return st;
+  if ((st = check_gaussians(g)) != DQO_OK) return st;
+  if ((st = check_camera(cam)) != DQO_OK) return st;
+  if (t && (!t->gt_id || !t->rgb)) return DQO_EINVAL;
+  if (!c->have_fwd || c->n != g->n || c->W != cam->width || c->H != cam->height || c->tile_w != s->tile_w ||
+      c->tile_h != s->tile_h)
+    return DQO_ESTATE;
+  if (!pg && !c->fwd_dl) return DQO_ESTATE;
+  cudaStream_t s_ = reinterpret_cast<cudaStream_t>(stream_);
+  DQO_CUDA(c, cudaSetDevice(c->device));
+  const RasterParams rp = make_params(s, g, cam);
+  const int64_t n = g->n;
+  DQO_CUDA(c, ensure(c->grad2d, 48 * n));
+  if (n > 0) DQO_CUDA(c, cudaMemsetAsync(c->grad2d.p, 0, 48 * n, s_));
+
+  BlendBwdArgs a;
+  a.rp = rp;
+  a.p0 = as<float4>(c->p0);
+  a.p1 = as<float4>(c->p1);
+  a.p2 = as<float4>(c->p2);
+  a.ranges = as<uint2>(c->ranges);
+  a.list = as<uint32_t>(c->list);
+  a.t_gt = t ? t->gt_id : nullptr;
+  a.T_final = as<float>(c->T_final);
+  a.n_contrib = as<uint32_t>(c->n_contrib);
+  if (pg) {
+    a.g_rgb = pg->rgb;
+    a.g_depth = pg->depth;
+    a.g_alpha = pg->alpha;
+    a.g_ins = pg->ins;
+  } else {
+    a.g_rgb = as<float>(c->dl_rgb);
+    a.g_depth = as<float>(c->dl_depth);
+    a.g_alpha = nullptr;
+    a.g_ins = as<float>(c->dl_ins);
+  }
+  a.grad2d = as<float>(c->grad2d);
+  {
+    PhaseTimer pt(c, DQO_PHASE_BLEND_BWD, s_);
+    DQO_CUDA(c, launch_blend_backward(a, s_));
+  }
+  c->launches += (c->ntx * c->nty > 0) ? 1 : 0;
+
+  PreBwdArgs b;
+  b.rp = rp;
+  b.n = n;
+  b.means = g->means;
+  b.log_scales = g->log_scales;
+  b.quats = g->quats;
+  b.opacity_logit = g->opacity_logit;
+  b.ntiles = as<uint32_t>(c->ntiles);
+  b.grad2d = as<float>(c->grad2d);
+  b.d_means = grads->means;
+  b.d_log_scales = grads->log_scales;
+  b.d_quats = grads->quats;
+  b.d_logit = grads->opacity_logit;
+  b.d_rgb = grads->rgb;
+  {
+    PhaseTimer pt(c, DQO_PHASE_PROJECT_BWD, s_);
+    DQO_CUDA(c, launch_preprocess_backward(b, s_));
+  }
+  c->launches += n > 0 ? 1 : 0;
+  return DQO_OK;
+}
+
+dqo_status dqo_get_buffer(dqo_ctx* c, dqo_buffer which, void* dst, size_t capacity, size_t* bytes,
+                          dqo_stream stream_) {
+  if (!c) return DQO_EINVAL;
+  if (!c->have_fwd) return DQO_ESTATE;
+  const void* src = nullptr;
+  size_t sz = 0;
+  const int64_t HW = (int64_t)c->W * c->H;
+  switch (which) {
+    case DQO_BUF_PROJ: {
+      // three float4 planes, copied back to back
+      sz = 48 * (size_t)c->n;
+      if (bytes) *bytes = sz;
+      if (!dst) return DQO_OK;
+      if (capacity < sz) return DQO_EINVAL;
+      cudaStream_t s_ = reinterpret_cast<cudaStream_t>(stream_);
+      const size_t pl = 16 * (size_t)c->n;
+      if (pl) {
+        DQO_CUDA(c, cudaMemcpyAsync(dst, c->p0.p, pl, cudaMemcpyDefault, s_));
+        DQO_CUDA(c, cudaMemcpyAsync((char*)dst + pl, c->p1.p, pl, cudaMemcpyDefault, s_));
+        DQO_CUDA(c, cudaMemcpyAsync((char*)dst + 2 * pl, c->p2.p, pl, cudaMemcpyDefault, s_));
+      }
+      return DQO_OK;
+    }
+    case DQO_BUF_RECT: src = c->rect.p; sz = 8 * (size_t)c->n; break;
+    case DQO_BUF_DEPTH_ORDER: src = c->order_sel ? c->zval_b.p : c->zval_a.p; sz = 4 * (size_t)c->n; break;
+    case DQO_BUF_TILE_RANGES: src = c->ranges.p; sz = 8 * (size_t)c->ntx * c->nty; break;
+    case DQO_BUF_TILE_LIST: src = c->list.p; sz = 4 * (size_t)c->m; break;
+    case DQO_BUF_T_FINAL: src = c->T_final.p; sz = 4 * (size_t)HW; break;
+    case DQO_BUF_N_CONTRIB: src = c->n_contrib.p; sz = 4 * (size_t)HW; break;
+    case DQO_BUF_GRAD2D: src = c->grad2d.p; sz = c->grad2d.p ? 48 * (size_t)c->n : 0; break;
+    default: return DQO_EINVAL;
+  }
+  if (bytes) *bytes = sz;
+  if (!dst) return DQO_OK;
+  if (capacity < sz) return DQO_EINVAL;
+  if (sz) DQO_CUDA(c, cudaMemcpyAsync(dst, src, sz, cudaMemcpyDefault, reinterpret_cast<cudaStream_t>(stream_)));
+  return DQO_OK;
+}
+
+dqo_status dqo_set_timing(dqo_ctx* c, int enable) {
+  if (!c) return DQO_EINVAL;
+  if (enable && !c->ev[0]) {
+    DQO_CUDA(c, cudaSetDevice(c->device));
+    for (int i = 0; i < 2 * DQO_PHASE_COUNT; ++i) DQO_CUDA(c, cudaEventCreate(&c->ev[i]));
+  }
+  c->timing = enable != 0;
+  for (int i = 0; i < DQO_PHASE_COUNT; ++i) {
+    c->pending[i] = false;
+    c->last_ms[i] = -1.f;
+  }
+  return DQO_OK;
+}
+
+dqo_status dqo_get_timings(dqo_ctx* c, float* ms, int32_t n) {
+  if (!c || !ms || n < 1) return DQO_EINVAL;
+  for (int i = 0; i < DQO_PHASE_COUNT; ++i) {
+    if (c->pending[i]) {
+      DQO_CUDA(c, cudaEventSynchronize(c->ev[2 * i + 1]));
+      float t = 0.f;
+      DQO_CUDA(c, cudaEventElapsedTime(&t, c->ev[2 * i], c->ev[2 * i + 1]));
+      c->last_ms[i] = t;
+      c->pending[i] = false;
+    }
+  }
+  for (int i = 0; i < n && i < DQO_PHASE_COUNT; ++i) ms[i] = c->last_ms[i];
+  for (int i = DQO_PHASE_COUNT; i < n; ++i) ms[i] = -1.f;
+  return DQO_OK;
+}
+
+int64_t dqo_launch_count(const dqo_ctx* c) { return c ? c->launches : 0; }
+
+dqo_status dqo_get_counts(const dqo_ctx* c, int64_t* n_pairs, int64_t* n_visible, int32_t* n_tiles) {
+  if (!c) return DQO_EINVAL;
+  if (!c->have_fwd) return DQO_ESTATE;
+  if (n_pairs) *n_pairs = c->m;
+  if (n_visible) *n_visible = c->n_vis;
+  if (n_tiles) *n_tiles = c->ntx * c->nty;
+  return DQO_OK;
+}
+
+dqo_status dqo_quadric_project(dqo_ctx* c, int32_t nq, const float* params, int32_t nv, const float* P,
+                               const int32_t* q_ptr, const int32_t* pair_v, int32_t npairs, float* conic,
+                               float* bbox, uint8_t* valid, dqo_stream stream_) {
+  if (!c || nq < 0 || nv < 0 || npairs < 0) return DQO_EINVAL;
+  if (nq > 0 && (!params || !q_ptr)) return DQO_EINVAL;
+  if (npairs > 0 && (!P || !pair_v || nv == 0)) return DQO_EINVAL;
+  DQO_CUDA(c, cudaSetDevice(c->device));
+  {
+    PhaseTimer pt(c, DQO_PHASE_QUADRIC, reinterpret_cast<cudaStream_t>(stream_));
+    DQO_CUDA(c, launch_quadric_project(nq, params, nv, P, q_ptr, pair_v, npairs, conic, bbox, valid,
+                                       reinterpret_cast<cudaStream_t>(stream_)));
+  }
+  c->launches += nq > 0 ? 1 : 0;
+  return DQO_OK;
+}
+
+dqo_status dqo_quadric_bbox_loss(dqo_ctx* c, int32_t nq, const float* params, int32_t nv, const float* P,
+                                 const int32_t* q_ptr, const int32_t* pair_v, int32_t npairs, const float* obs,
+                                 float* loss, float* dparams, dqo_stream stream_) {
+  if (!c || nq < 0 || nv < 0 || npairs < 0) return DQO_EINVAL;
+  if (nq > 0 && (!params || !q_ptr)) return DQO_EINVAL;
+  if (npairs > 0 && (!P || !pair_v || !obs || nv == 0)) return DQO_EINVAL;
+  DQO_CUDA(c, cudaSetDevice(c->device));
+  {
+    PhaseTimer pt(c, DQO_PHASE_QUADRIC, reinterpret_cast<cudaStream_t>(stream_));
+    DQO_CUDA(c, launch_quadric_bbox_loss(nq, params, nv, P, q_ptr, pair_v, npairs, obs, loss, dparams,
+                                         reinterpret_cast<cudaStream_t>(stream_)));
+  }
+  c->launches += nq > 0 ? 1 : 0;
+  return DQO_OK;
+}
+
+}  // extern "C"

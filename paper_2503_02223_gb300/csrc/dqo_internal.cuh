@@ -1,0 +1,181 @@
+// Internal declarations of the dqo CUDA library (sm_103a).  Host launchers are
+// declared here and defined next to their kernels; dqo_api.cu drives them.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dqo.h"
+
+namespace dqo {
+
+constexpr int kThreads = 256;          // CTA size of every rasterizer kernel (one pixel / thread)
+constexpr int kMaxObjects = 4096;      // object ids per scene handled by the id-map prepass
+constexpr int kMaskWords = kMaxObjects / 32;
+constexpr int kIdSlots = 16;           // per-tile object slots held in shared memory per round
+constexpr int kRadixBits = 8;
+constexpr int kRadixBins = 1 << kRadixBits;
+constexpr int kSortItems = 16;         // keys per thread in the radix and scan kernels
+constexpr int kSortTile = kThreads * kSortItems;   // keys per CTA
+constexpr uint32_t kNoObject = 0x7FFFFFFFu;
+constexpr float kLog2e = 1.4426950408889634f;
+
+// ---------------------------------------------------------------- device helpers
+
+// One MUFU.EX2: 2^x (x <= 0 here), flushing denormal results to zero.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Per-pixel evaluation of one projected Gaussian, shared bit-for-bit by the forward and
+// backward blend kernels so both take the same skip / clamp decisions.  p0 = (x, y, a',
+// b'), p1 = (c', opacity, z, id bits) with the conic pre-scaled so that
+// G = 2^(a' dx^2 + b' dx dy + c' dy^2) = exp(-q/2).  Returns false if the Gaussian is
+// skipped (exponent > 0 or alpha < alpha_min).
+__device__ __forceinline__ bool eval_gaussian(const float4& p0, const float4& p1, float px, float py,
+                                              float alpha_clamp, float alpha_min, float& alpha,
+                                              float& G, float& dx, float& dy) {
+  dx = __fsub_rn(px, p0.x);
+  dy = __fsub_rn(py, p0.y);
+  const float t = __fmaf_rn(p0.w, dy, __fmul_rn(p0.z, dx));
+  const float pw = __fmaf_rn(__fmul_rn(p1.x, dy), dy, __fmul_rn(t, dx));
+  if (pw > 0.f) return false;
+  G = ex2_approx(pw);
+  alpha = fminf(alpha_clamp, __fmul_rn(p1.y, G));
+  return alpha >= alpha_min;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// ---------------------------------------------------------------- launch descriptors
+
+struct RasterParams {
+  int W, H, tile_w, tile_h, ntx, nty;
+  float fx, fy, cx, cy;
+  float vm[12];
+  float alpha_clamp, alpha_min, t_stop, znear, lowpass, radius_sigma, lambda_ins;
+  float bg[3];
+  int og_filter;
+  int batch;
+  int num_objects;
+};
+
+struct ProjBuffers {
+  float4* p0;
+  float4* p1;
+  float4* p2;
+  ushort4* rect;
+  uint32_t* ntiles;
+  uint32_t* zkey;    // depth sort keys: float bits of z, 0xFFFFFFFF if culled
+  uint32_t* zval;    // depth sort values: Gaussian index
+  uint32_t* gid;     // object id (kNoObject if none) for the id-map prepass
+  uint32_t* n_visible;
+};
+
+struct BlendFwdArgs {
+  RasterParams rp;
+  const float4* p0;
+  const float4* p1;
+  const float4* p2;
+  const uint32_t* gid;
+  const uint2* ranges;
+  const uint32_t* list;
+  const float* t_rgb;
+  const float* t_depth;
+  const int32_t* t_gt;
+  float* o_rgb;
+  float* o_depth;
+  float* o_alpha;
+  float* o_ins;
+  int32_t* o_id;
+  float* T_final;
+  uint32_t* n_contrib;
+  float* dl_rgb;     // saved dL/dC  [H*W*3] (with targets)
+  float* dl_depth;   // saved dL/dD  [H*W]
+  float* dl_ins;     // saved dL/dins[H*W]
+  float* loss_part;  // [T*3] per-tile loss sums
+};
+
+struct BlendBwdArgs {
+  RasterParams rp;
+  const float4* p0;
+  const float4* p1;
+  const float4* p2;
+  const uint2* ranges;
+  const uint32_t* list;
+  const int32_t* t_gt;
+  const float* T_final;
+  const uint32_t* n_contrib;
+  const float* g_rgb;
+  const float* g_depth;
+  const float* g_alpha;
+  const float* g_ins;
+  float* grad2d;     // [n*12] moment records (accumulated with atomics)
+};
+
+struct PreBwdArgs {
+  RasterParams rp;
+  int64_t n;
+  const float* means;
+  const float* log_scales;
+  const float* quats;
+  const float* opacity_logit;
+  const uint32_t* ntiles;
+  const float* grad2d;
+  float* d_means;
+  float* d_log_scales;
+  float* d_quats;
+  float* d_logit;
+  float* d_rgb;
+};
+
+// ---------------------------------------------------------------- launchers (return cudaGetLastError)
+
+cudaError_t launch_preprocess(const RasterParams& rp, const dqo_gaussians& g, const ProjBuffers& out,
+                              cudaStream_t s);
+cudaError_t launch_preprocess_backward(const PreBwdArgs& a, cudaStream_t s);
+
+// Exclusive scan of n uint32 values; total (uint64) written to *total.  scratch must
+// hold scan_scratch_words(n) uint64 words.
+size_t scan_scratch_words(int64_t n);
+cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint64_t* scratch,
+                                  uint64_t* total, cudaStream_t s);
+
+// LSD radix sort of n keys (bits [0, end_bit)), optional uint32 values.  Results land in
+// whichever of the double buffers *sel says (0: *_a, 1: *_b).
+size_t radix_scratch_words(int64_t n);
+cudaError_t radix_sort_u32(uint32_t* keys_a, uint32_t* keys_b, uint32_t* vals_a, uint32_t* vals_b,
+                           int64_t n, int end_bit, uint32_t* hist_scratch, uint64_t* scan_scratch,
+                           int* sel, cudaStream_t s);
+cudaError_t radix_sort_u64(uint64_t* keys_a, uint64_t* keys_b, int64_t n, int end_bit,
+                           uint32_t* hist_scratch, uint64_t* scan_scratch, int* sel, cudaStream_t s);
+
+cudaError_t launch_rank_scatter(const uint32_t* order, int64_t n, uint32_t* rank, cudaStream_t s);
+cudaError_t launch_emit_pairs_u32(const ushort4* rect, const uint32_t* offsets, const uint32_t* rank,
+                                  int64_t n, int ntx, int rank_bits, uint32_t* keys, cudaStream_t s);
+cudaError_t launch_emit_pairs_u64(const ushort4* rect, const uint32_t* offsets, const uint32_t* rank,
+                                  int64_t n, int ntx, int rank_bits, uint64_t* keys, cudaStream_t s);
+cudaError_t launch_tile_ranges_u32(const uint32_t* keys, int64_t m, int rank_bits, const uint32_t* order,
+                                   uint2* ranges, uint32_t* list, cudaStream_t s);
+cudaError_t launch_tile_ranges_u64(const uint64_t* keys, int64_t m, int rank_bits, const uint32_t* order,
+                                   uint2* ranges, uint32_t* list, cudaStream_t s);
+
+cudaError_t launch_blend_forward(const BlendFwdArgs& a, bool with_id, cudaStream_t s);
+cudaError_t launch_loss_reduce(const float* part, int tiles, float lambda_ins, float scale, float* loss,
+                               cudaStream_t s);
+cudaError_t launch_blend_backward(const BlendBwdArgs& a, cudaStream_t s);
+
+cudaError_t launch_quadric_project(int nq, const float* params, int nv, const float* P, const int32_t* q_ptr,
+                                   const int32_t* pair_v, int npairs, float* conic, float* bbox, uint8_t* valid,
+                                   cudaStream_t s);
+cudaError_t launch_quadric_bbox_loss(int nq, const float* params, int nv, const float* P, const int32_t* q_ptr,
+                                     const int32_t* pair_v, int npairs, const float* obs, float* loss,
+                                     float* dparams, cudaStream_t s);
+
+}  // namespace dqo

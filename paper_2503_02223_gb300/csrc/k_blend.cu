@@ -1,0 +1,526 @@
+// K6 (blend forward + fused losses) and K7 (blend backward) of the rasterizer.
+//
+// One CTA of 256 threads per screen tile (16x16, 8x32 or 32x8 pixels), one pixel per
+// thread; each warp covers an 8x4 pixel block.  The tile's depth-ordered Gaussian list
+// is staged through shared memory in batches.
+//
+// Forward, per pixel, front to back (3DGS blending; Eq. 15 for ins; Eq. 7-10 losses):
+//   alpha = min(clamp, o G), skipped if < alpha_min; stop before T (1 - alpha) < t_stop;
+//   w = alpha T: C += w c, D += w z, ins += w if the Gaussian is opaque (or og_filter is
+//   off) and its id equals the pixel's labelled id; W_k += w for the id map.
+// The whole CTA leaves the list once every pixel has stopped (__syncthreads_count);
+// a warp whose pixels have all stopped skips the batch.  Per-object weights live in
+// shared memory per tile: the tile's distinct ids are found first and mapped to dense
+// slots, 16 slots per round (extra rounds re-walk the list only for tiles with more
+// than 16 objects).  The loss terms and dL/d(pixel) are computed in the epilogue.
+//
+// Backward, per pixel, back to front from T_final and n_contrib: T_j = T_{j+1}/(1-a_j),
+// dL/da_j = T_j U_j - R_j / (1 - a_j) with U_j = dC.c_j + dD z_j + dA + dins [j counts]
+// and R_j = sum_{k>j} w_k U_k + T_final dC.bg.  The ten per-Gaussian partials are
+// summed over the warp by a transposing butterfly (16 shuffles), over the CTA with
+// shared-memory atomics, and added to the global per-Gaussian record with vector
+// atomics once per (tile, Gaussian).
+#include "dqo_internal.cuh"
+
+namespace dqo {
+namespace {
+
+constexpr int kMaxBatch = 256;
+
+template <int TW>
+__device__ __forceinline__ void pixel_of(int tile_x0, int tile_y0, int& px, int& py) {
+  constexpr int WX = TW / 8;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  px = tile_x0 + (warp % WX) * 8 + (lane & 7);
+  py = tile_y0 + (warp / WX) * 4 + (lane >> 3);
+}
+
+__device__ __forceinline__ float sgnf(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
+
+// Fills s_slot_id[s - first] with the object id of dense slot s for s in [first, first+kIdSlots).
+__device__ __forceinline__ void slot_ids_for_round(const uint32_t* s_mask, const uint32_t* s_pref, int nw, int first,
+                                                   int32_t* s_slot_id) {
+  for (int t = threadIdx.x; t < nw; t += kThreads) {
+    uint32_t m = s_mask[t];
+    int s = (int)s_pref[t];
+    while (m) {
+      const int b = __ffs(m) - 1;
+      m &= m - 1;
+      if (s >= first && s < first + kIdSlots) s_slot_id[s - first] = t * 32 + b;
+      ++s;
+    }
+  }
+}
+
+template <int TW, bool kId>
+__global__ void __launch_bounds__(kThreads) k_blend_forward(BlendFwdArgs a) {
+  __shared__ float4 s_p0[kMaxBatch], s_p1[kMaxBatch], s_p2[kMaxBatch];
+  __shared__ int32_t s_slot[kId ? kMaxBatch : 1];
+  __shared__ uint32_t s_mask[kId ? kMaskWords : 1], s_pref[kId ? kMaskWords : 1];
+  __shared__ int32_t s_slot_id[kIdSlots];
+  __shared__ float s_W[kId ? kIdSlots : 1][kThreads];
+  __shared__ float s_red[3][kThreads / 32];
+  __shared__ uint32_t s_nslots;
+
+  const RasterParams& rp = a.rp;
+  const int tile = blockIdx.x;
+  const int tx = tile % rp.ntx, ty = tile / rp.ntx;
+  int px, py;
+  pixel_of<TW>(tx * rp.tile_w, ty * rp.tile_h, px, py);
+  const bool inside = px < rp.W && py < rp.H;
+  const int64_t pix = (int64_t)py * rp.W + px;
+  const uint2 rg = a.ranges[tile];
+  const int start = (int)rg.x, end = rg.y > rg.x ? (int)rg.y : (int)rg.x;
+  const int tid = threadIdx.x;
+  const int B = rp.batch;
+
+  int32_t gt = -1;
+  if (inside && a.t_gt) gt = a.t_gt[pix];
+  const uint32_t gt_match = (gt >= 0 && gt < rp.num_objects) ? (uint32_t)gt : 0xFFFFFFFEu;
+
+  // ---- distinct object ids of this tile -> dense slots (ascending id order)
+  int nslots = 0;
+  const int nw = (rp.num_objects + 31) >> 5;
+  if (kId) {
+    for (int t = tid; t < nw; t += kThreads) s_mask[t] = 0u;
+    __syncthreads();
+    for (int i = start + tid; i < end; i += kThreads) {
+      const uint32_t id = a.gid[a.list[i]];
+      if (id != 0xFFFFFFFFu) atomicOr(&s_mask[id >> 5], 1u << (id & 31));
+    }
+    __syncthreads();
+    if (tid < 32) {
+      uint32_t carry = 0;
+      for (int c = 0; c < nw; c += 32) {
+        const int t = c + tid;
+        const uint32_t pc = t < nw ? (uint32_t)__popc(s_mask[t]) : 0u;
+        uint32_t inc = pc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+          if (tid >= o) inc += u;
+        }
+        if (t < nw) s_pref[t] = carry + inc - pc;
+        carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
+      }
+      if (tid == 0) s_nslots = carry;
+    }
+    __syncthreads();
+    nslots = (int)s_nslots;
+    slot_ids_for_round(s_mask, s_pref, nw, 0, s_slot_id);
+#pragma unroll
+    for (int s = 0; s < kIdSlots; ++s) s_W[s][tid] = 0.f;
+  }
+
+  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, ins = 0.f;
+  int last = 0;
+  bool done = !inside;
+  int cur_slot = -1;
+  float cur_w = 0.f;
+  const float fpx = (float)px, fpy = (float)py;
+
+  for (int b0 = start; b0 < end; b0 += B) {
+    if (__syncthreads_count(!done) == 0) break;
+    const int nb = min(B, end - b0);
+    if (tid < nb) {
+      const uint32_t g = a.list[b0 + tid];
+      const float4 q1 = a.p1[g];
+      s_p0[tid] = a.p0[g];
+      s_p1[tid] = q1;
+      s_p2[tid] = a.p2[g];
+      if (kId) {
+        const uint32_t id = __float_as_uint(q1.w) & kNoObject;
+        int slot = -1;
+        if (id != kNoObject) {
+          const uint32_t w = s_mask[id >> 5];
+          slot = (int)(s_pref[id >> 5] + __popc(w & ((1u << (id & 31)) - 1u)));
+        }
+        s_slot[tid] = slot;
+      }
+    }
+    __syncthreads();
+    if (!done) {
+      for (int j = 0; j < nb; ++j) {
+        const float4 q0 = s_p0[j], q1 = s_p1[j];
+        float alpha, G, dx, dy;
+        if (!eval_gaussian(q0, q1, fpx, fpy, rp.alpha_clamp, rp.alpha_min, alpha, G, dx, dy)) continue;
+        const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
+        if (Tn < rp.t_stop) {
+          done = true;
+          break;
+        }
+        const float w = __fmul_rn(alpha, T);
+        const float4 q2 = s_p2[j];
+        C0 = fmaf(w, q2.x, C0);
+        C1 = fmaf(w, q2.y, C1);
+        C2 = fmaf(w, q2.z, C2);
+        D = fmaf(w, q1.z, D);
+        const uint32_t idog = __float_as_uint(q1.w);
+        if ((idog & kNoObject) == gt_match && (!rp.og_filter || (idog >> 31))) ins += w;
+        if (kId) {
+          const int slot = s_slot[j];
+          if (slot == cur_slot) {
+            cur_w += w;
+          } else {
+            if (cur_slot >= 0 && cur_slot < kIdSlots) s_W[cur_slot][tid] += cur_w;
+            cur_slot = slot;
+            cur_w = w;
+          }
+        }
+        T = Tn;
+        last = b0 - start + j + 1;
+      }
+    }
+  }
+
+  // ---- object-id argmax (ties to the smaller id: slots are in ascending id order)
+  int32_t best_id = -1;
+  if (kId) {
+    if (cur_slot >= 0 && cur_slot < kIdSlots) s_W[cur_slot][tid] += cur_w;
+    float best_w = 0.f;
+    const int n0 = min(nslots, kIdSlots);
+    for (int s = 0; s < n0; ++s) {
+      const float v = s_W[s][tid];
+      if (v > best_w) {
+        best_w = v;
+        best_id = s_slot_id[s];
+      }
+    }
+    // tiles with more than kIdSlots objects: re-walk the blended prefix once per extra round
+    if (nslots > kIdSlots) {
+      if (tid == 0) s_nslots = 0;
+      __syncthreads();
+      atomicMax(&s_nslots, (uint32_t)last);
+      __syncthreads();
+      const int maxlast = (int)s_nslots;
+      for (int first = kIdSlots; first < nslots; first += kIdSlots) {
+        __syncthreads();
+        slot_ids_for_round(s_mask, s_pref, nw, first, s_slot_id);
+#pragma unroll
+        for (int s = 0; s < kIdSlots; ++s) s_W[s][tid] = 0.f;
+        __syncthreads();
+        float Tr = 1.f;
+        for (int b0 = start; b0 < start + maxlast; b0 += B) {
+          const int nb = min(B, start + maxlast - b0);
+          __syncthreads();
+          if (tid < nb) {
+            const uint32_t g = a.list[b0 + tid];
+            const float4 q1 = a.p1[g];
+            s_p0[tid] = a.p0[g];
+            s_p1[tid] = q1;
+            const uint32_t id = __float_as_uint(q1.w) & kNoObject;
+            int slot = -1;
+            if (id != kNoObject)
+              slot = (int)(s_pref[id >> 5] + __popc(s_mask[id >> 5] & ((1u << (id & 31)) - 1u)));
+            s_slot[tid] = slot;
+          }
+          __syncthreads();
+          for (int j = 0; j < nb && b0 - start + j < last; ++j) {
+            float alpha, G, dx, dy;
+            if (!eval_gaussian(s_p0[j], s_p1[j], fpx, fpy, rp.alpha_clamp, rp.alpha_min, alpha, G, dx, dy)) continue;
+            const float w = __fmul_rn(alpha, Tr);
+            Tr = __fmul_rn(Tr, __fsub_rn(1.f, alpha));
+            const int s = s_slot[j] - first;
+            if (s >= 0 && s < kIdSlots) s_W[s][tid] += w;
+          }
+        }
+        const int nr = min(nslots - first, kIdSlots);
+        for (int s = 0; s < nr; ++s) {
+          const float v = s_W[s][tid];
+          if (v > best_w) {
+            best_w = v;
+            best_id = s_slot_id[s];
+          }
+        }
+      }
+    }
+  }
+
+  // ---- outputs and fused losses
+  float l_rgb = 0.f, l_d = 0.f, l_i = 0.f;
+  if (inside) {
+    const float c0 = fmaf(T, rp.bg[0], C0), c1 = fmaf(T, rp.bg[1], C1), c2 = fmaf(T, rp.bg[2], C2);
+    if (a.o_rgb) {
+      a.o_rgb[3 * pix + 0] = c0;
+      a.o_rgb[3 * pix + 1] = c1;
+      a.o_rgb[3 * pix + 2] = c2;
+    }
+    if (a.o_depth) a.o_depth[pix] = D;
+    if (a.o_alpha) a.o_alpha[pix] = 1.f - T;
+    if (a.o_ins) a.o_ins[pix] = ins;
+    if (a.o_id) a.o_id[pix] = best_id;
+    a.T_final[pix] = T;
+    a.n_contrib[pix] = (uint32_t)last;
+    if (a.t_gt) {
+      const float inv_hw = 1.f / ((float)rp.W * (float)rp.H);
+      float g0 = 0.f, g1 = 0.f, g2 = 0.f, gd = 0.f, gi = 0.f;
+      if (gt >= 0) {
+        const float e0 = c0 - a.t_rgb[3 * pix + 0], e1 = c1 - a.t_rgb[3 * pix + 1], e2 = c2 - a.t_rgb[3 * pix + 2];
+        l_rgb = fabsf(e0) + fabsf(e1) + fabsf(e2);
+        g0 = sgnf(e0) * inv_hw;
+        g1 = sgnf(e1) * inv_hw;
+        g2 = sgnf(e2) * inv_hw;
+        const float td = a.t_depth ? a.t_depth[pix] : 0.f;
+        if (td > 0.f) {
+          const float ed = D - td;
+          l_d = fabsf(ed);
+          gd = sgnf(ed) * inv_hw;
+        }
+        const float ei = ins - 1.f;
+        l_i = fabsf(ei);
+        gi = rp.lambda_ins * sgnf(ei) * inv_hw;
+      }
+      a.dl_rgb[3 * pix + 0] = g0;
+      a.dl_rgb[3 * pix + 1] = g1;
+      a.dl_rgb[3 * pix + 2] = g2;
+      a.dl_depth[pix] = gd;
+      a.dl_ins[pix] = gi;
+    }
+  }
+  if (a.t_gt) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      l_rgb += __shfl_xor_sync(0xFFFFFFFFu, l_rgb, o);
+      l_d += __shfl_xor_sync(0xFFFFFFFFu, l_d, o);
+      l_i += __shfl_xor_sync(0xFFFFFFFFu, l_i, o);
+    }
+    const int lane = tid & 31, warp = tid >> 5;
+    if (lane == 0) {
+      s_red[0][warp] = l_rgb;
+      s_red[1][warp] = l_d;
+      s_red[2][warp] = l_i;
+    }
+    __syncthreads();
+    if (tid < 3) {
+      float s = 0.f;
+#pragma unroll
+      for (int w = 0; w < kThreads / 32; ++w) s += s_red[tid][w];
+      a.loss_part[3 * tile + tid] = s;
+    }
+  }
+}
+
+// Deterministic sum of the per-tile loss partials in double, scaled by 1/(HW).
+__global__ void k_loss_reduce(const float* __restrict__ part, int tiles, float lambda_ins, float scale,
+                              float* __restrict__ loss) {
+  __shared__ double s[3][kThreads];
+  double acc[3] = {0, 0, 0};
+  for (int t = threadIdx.x; t < tiles; t += kThreads)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc[k] += (double)part[3 * t + k];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) s[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int o = kThreads / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double r = s[0][0] * scale, d = s[1][0] * scale, i = s[2][0] * scale;
+    loss[0] = (float)r;
+    loss[1] = (float)d;
+    loss[2] = (float)i;
+    loss[3] = (float)(r + d + (double)lambda_ins * i);
+  }
+}
+
+// Sum of 16 per-lane values over the warp with a transposing butterfly: after it, lane l
+// holds (in v[0]) the warp sum of value index (l >> 1) & 15.  16 shuffles in total.
+__device__ __forceinline__ void warp_transpose_sum16(float v[16]) {
+  const int lane = threadIdx.x & 31;
+  {
+    const bool hi = lane & 16;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float send = hi ? v[k] : v[k + 8];
+      const float keep = hi ? v[k + 8] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 16);
+    }
+  }
+  {
+    const bool hi = lane & 8;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float send = hi ? v[k] : v[k + 4];
+      const float keep = hi ? v[k + 4] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 8);
+    }
+  }
+  {
+    const bool hi = lane & 4;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const float send = hi ? v[k] : v[k + 2];
+      const float keep = hi ? v[k + 2] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 4);
+    }
+  }
+  {
+    const bool hi = lane & 2;
+    const float send = hi ? v[0] : v[1];
+    const float keep = hi ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 2);
+  }
+  v[0] += __shfl_xor_sync(0xFFFFFFFFu, v[0], 1);
+}
+
+template <int TW>
+__global__ void __launch_bounds__(kThreads) k_blend_backward(BlendBwdArgs a) {
+  constexpr int NV = 10;
+  __shared__ float4 s_p0[kMaxBatch], s_p1[kMaxBatch], s_p2[kMaxBatch];
+  __shared__ uint32_t s_g[kMaxBatch];
+  __shared__ float s_acc[kMaxBatch * NV];
+  __shared__ uint32_t s_maxn;
+
+  const RasterParams& rp = a.rp;
+  const int tile = blockIdx.x;
+  const int tx = tile % rp.ntx, ty = tile / rp.ntx;
+  int px, py;
+  pixel_of<TW>(tx * rp.tile_w, ty * rp.tile_h, px, py);
+  const bool inside = px < rp.W && py < rp.H;
+  const int64_t pix = (int64_t)py * rp.W + px;
+  const uint2 rg = a.ranges[tile];
+  const int start = (int)rg.x;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int B = rp.batch;
+
+  uint32_t nc = 0;
+  float T = 1.f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gA = 0.f, gI = 0.f;
+  uint32_t gt_match = 0xFFFFFFFEu;
+  if (inside) {
+    nc = a.n_contrib[pix];
+    T = a.T_final[pix];
+    if (a.g_rgb) {
+      gC0 = a.g_rgb[3 * pix];
+      gC1 = a.g_rgb[3 * pix + 1];
+      gC2 = a.g_rgb[3 * pix + 2];
+    }
+    if (a.g_depth) gD = a.g_depth[pix];
+    if (a.g_alpha) gA = a.g_alpha[pix];
+    if (a.g_ins) gI = a.g_ins[pix];
+    if (a.t_gt) {
+      const int32_t gt = a.t_gt[pix];
+      if (gt >= 0 && gt < rp.num_objects) gt_match = (uint32_t)gt;
+    }
+  }
+  if (tid == 0) s_maxn = 0;
+  __syncthreads();
+  const uint32_t wmax = __reduce_max_sync(0xFFFFFFFFu, nc);
+  if (lane == 0 && wmax) atomicMax(&s_maxn, wmax);
+  __syncthreads();
+  const int maxn = (int)s_maxn;
+  float R = T * (gC0 * rp.bg[0] + gC1 * rp.bg[1] + gC2 * rp.bg[2]);
+  const float fpx = (float)px, fpy = (float)py;
+
+  for (int hi = maxn; hi > 0; hi -= B) {
+    const int lo = max(0, hi - B);
+    const int nb = hi - lo;
+    if (tid < nb) {
+      const uint32_t g = a.list[start + lo + tid];
+      s_g[tid] = g;
+      s_p0[tid] = a.p0[g];
+      s_p1[tid] = a.p1[g];
+      s_p2[tid] = a.p2[g];
+    }
+    for (int k = tid; k < nb * NV; k += kThreads) s_acc[k] = 0.f;
+    __syncthreads();
+    const bool warp_live = __any_sync(0xFFFFFFFFu, (int)nc > lo);
+    if (warp_live) {
+      for (int j = nb - 1; j >= 0; --j) {
+        float v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = 0.f;
+        bool act = false;
+        if (lo + j < (int)nc) {
+          const float4 q0 = s_p0[j], q1 = s_p1[j];
+          float alpha, G, dx, dy;
+          if (eval_gaussian(q0, q1, fpx, fpy, rp.alpha_clamp, rp.alpha_min, alpha, G, dx, dy)) {
+            act = true;
+            const float oma = 1.f - alpha;
+            T = T / oma;
+            const float w = alpha * T;
+            const float4 q2 = s_p2[j];
+            const uint32_t idog = __float_as_uint(q1.w);
+            const bool counts = (idog & kNoObject) == gt_match && (!rp.og_filter || (idog >> 31));
+            const float U = gC0 * q2.x + gC1 * q2.y + gC2 * q2.z + gD * q1.z + gA + (counts ? gI : 0.f);
+            const float dalpha = T * U - R / oma;
+            R = fmaf(w, U, R);
+            const bool clamped = __fmul_rn(q1.y, G) > rp.alpha_clamp;
+            const float dpow = clamped ? 0.f : dalpha * alpha;
+            v[0] = dpow * dx;
+            v[1] = dpow * dy;
+            v[2] = v[0] * dx;
+            v[3] = v[0] * dy;
+            v[4] = v[1] * dy;
+            v[5] = clamped ? 0.f : dalpha * G;
+            v[6] = w * gC0;
+            v[7] = w * gC1;
+            v[8] = w * gC2;
+            v[9] = w * gD;
+          }
+        }
+        if (__any_sync(0xFFFFFFFFu, act)) {
+          warp_transpose_sum16(v);
+          const int k = lane >> 1;
+          if (!(lane & 1) && k < NV && v[0] != 0.f) atomicAdd(&s_acc[j * NV + k], v[0]);
+        }
+      }
+    }
+    __syncthreads();
+    if (tid < nb) {
+      const float* r = s_acc + tid * NV;
+      if (r[0] != 0.f || r[1] != 0.f || r[2] != 0.f || r[3] != 0.f || r[4] != 0.f || r[5] != 0.f ||
+          r[6] != 0.f || r[7] != 0.f || r[8] != 0.f || r[9] != 0.f) {
+        float4* dst = reinterpret_cast<float4*>(a.grad2d) + 3 * (int64_t)s_g[tid];
+        atomicAdd(dst + 0, make_float4(r[0], r[1], r[2], r[3]));
+        atomicAdd(dst + 1, make_float4(r[4], r[5], r[6], r[7]));
+        atomicAdd(dst + 2, make_float4(r[8], r[9], 0.f, 0.f));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int TW>
+cudaError_t launch_fwd_tw(const BlendFwdArgs& a, bool with_id, cudaStream_t s) {
+  const unsigned tiles = (unsigned)(a.rp.ntx * a.rp.nty);
+  if (with_id)
+    k_blend_forward<TW, true><<<tiles, kThreads, 0, s>>>(a);
+  else
+    k_blend_forward<TW, false><<<tiles, kThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_blend_forward(const BlendFwdArgs& a, bool with_id, cudaStream_t s) {
+  if (a.rp.ntx * a.rp.nty == 0) return cudaSuccess;
+  switch (a.rp.tile_w) {
+    case 8: return launch_fwd_tw<8>(a, with_id, s);
+    case 16: return launch_fwd_tw<16>(a, with_id, s);
+    case 32: return launch_fwd_tw<32>(a, with_id, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_loss_reduce(const float* part, int tiles, float lambda_ins, float scale, float* loss,
+                               cudaStream_t s) {
+  k_loss_reduce<<<1, kThreads, 0, s>>>(part, tiles, lambda_ins, scale, loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_blend_backward(const BlendBwdArgs& a, cudaStream_t s) {
+  const unsigned tiles = (unsigned)(a.rp.ntx * a.rp.nty);
+  if (tiles == 0) return cudaSuccess;
+  switch (a.rp.tile_w) {
+    case 8: k_blend_backward<8><<<tiles, kThreads, 0, s>>>(a); break;
+    case 16: k_blend_backward<16><<<tiles, kThreads, 0, s>>>(a); break;
+    case 32: k_blend_backward<32><<<tiles, kThreads, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace dqo

@@ -1,0 +1,283 @@
+// K1 (projection) and K8 (projection adjoint) of the rasterizer.
+//
+// K1 maps each 3D Gaussian to its screen footprint (EWA splatting, the 3DGS rasterizer
+// DQO-MAP optimises with; Sec. IV impl.): camera-space mean, 2D covariance
+// Sigma' = J W M M^T W^T J^T + lowpass I with M = R(q) diag(exp(s)), its inverse (the
+// conic, pre-scaled for exp2), a 3-sigma tile rect, opacity = sigmoid(logit), and the
+// depth-sort key.  One thread per Gaussian; each warp stages its 32 Gaussians' [n,3]
+// rows through shared memory with float4 loads.
+//
+// K8 recomputes the same forward quantities and chains the per-Gaussian moment record
+// of the blend backward through the conic inverse, the EWA Jacobian, the scale/rotation
+// factorisation, quaternion normalisation and the sigmoid.
+#include "dqo_internal.cuh"
+
+namespace dqo {
+namespace {
+
+struct Footprint {
+  bool visible;
+  float pc[3];
+  float xy[2];
+  float cov[3];     // Sigma' (A, B, C)
+  float conic[3];   // (a, b, c) = inverse of Sigma'
+  float opac;
+  ushort4 rect;
+  uint32_t ntiles;
+  // factors kept for the adjoint
+  float R[3][3], s[3], qn[4], qinv;
+  float T2[2][3], V[2][3];
+};
+
+__device__ __forceinline__ void quat_rot(const float q[4], float R[3][3]) {
+  const float w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0][0] = 1.f - 2.f * (y * y + z * z); R[0][1] = 2.f * (x * y - w * z);       R[0][2] = 2.f * (x * z + w * y);
+  R[1][0] = 2.f * (x * y + w * z);       R[1][1] = 1.f - 2.f * (x * x + z * z); R[1][2] = 2.f * (y * z - w * x);
+  R[2][0] = 2.f * (x * z - w * y);       R[2][1] = 2.f * (y * z + w * x);       R[2][2] = 1.f - 2.f * (x * x + y * y);
+}
+
+// Same footprint computation for K1 and K8 (identical code path, identical rounding).
+__device__ __forceinline__ void footprint(const RasterParams& rp, const float mean[3], const float ls[3],
+                                          const float4 q4, float logit, Footprint& f) {
+  f.visible = false;
+  f.ntiles = 0;
+  f.rect = make_ushort4(0, 0, 0, 0);
+  const float* V = rp.vm;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    f.pc[i] = fmaf(V[4 * i + 0], mean[0], fmaf(V[4 * i + 1], mean[1], fmaf(V[4 * i + 2], mean[2], V[4 * i + 3])));
+  const float x = f.pc[0], y = f.pc[1], z = f.pc[2];
+  f.opac = 1.f / (1.f + expf(-logit));
+  if (!(z >= rp.znear)) return;
+  const float qq = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
+  if (!(qq > 0.f)) return;
+  f.qinv = rsqrtf(qq);
+  f.qn[0] = q4.x * f.qinv; f.qn[1] = q4.y * f.qinv; f.qn[2] = q4.z * f.qinv; f.qn[3] = q4.w * f.qinv;
+  quat_rot(f.qn, f.R);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) f.s[k] = expf(ls[k]);
+  const float iz = 1.f / z;
+  const float J00 = rp.fx * iz, J02 = -rp.fx * x * iz * iz;
+  const float J11 = rp.fy * iz, J12 = -rp.fy * y * iz * iz;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    f.T2[0][j] = J00 * V[j] + J02 * V[8 + j];
+    f.T2[1][j] = J11 * V[4 + j] + J12 * V[8 + j];
+  }
+  // V = T2 R diag(s)
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      f.V[i][k] = (f.T2[i][0] * f.R[0][k] + f.T2[i][1] * f.R[1][k] + f.T2[i][2] * f.R[2][k]) * f.s[k];
+  const float a0 = f.V[0][0] * f.V[0][0] + f.V[0][1] * f.V[0][1] + f.V[0][2] * f.V[0][2];
+  const float c0 = f.V[1][0] * f.V[1][0] + f.V[1][1] * f.V[1][1] + f.V[1][2] * f.V[1][2];
+  f.cov[0] = a0 + rp.lowpass;
+  f.cov[1] = f.V[0][0] * f.V[1][0] + f.V[0][1] * f.V[1][1] + f.V[0][2] * f.V[1][2];
+  f.cov[2] = c0 + rp.lowpass;
+  // det(V V^T + l I) = sum of squared 2x2 minors of V (Cauchy-Binet) + l (|V0|^2 + |V1|^2) + l^2:
+  // all terms non-negative, so flat footprints seen edge-on keep full single precision
+  // (A C - B^2 would cancel to a few digits).
+  const float m01 = fmaf(f.V[0][0], f.V[1][1], -f.V[0][1] * f.V[1][0]);
+  const float m02 = fmaf(f.V[0][0], f.V[1][2], -f.V[0][2] * f.V[1][0]);
+  const float m12 = fmaf(f.V[0][1], f.V[1][2], -f.V[0][2] * f.V[1][1]);
+  const float det = m01 * m01 + m02 * m02 + m12 * m12 + rp.lowpass * (a0 + c0) + rp.lowpass * rp.lowpass;
+  if (!(det > 0.f)) return;
+  const float idet = 1.f / det;
+  f.conic[0] = f.cov[2] * idet;
+  f.conic[1] = -f.cov[1] * idet;
+  f.conic[2] = f.cov[0] * idet;
+  const float mid = 0.5f * (f.cov[0] + f.cov[2]);
+  const float lmax = mid + sqrtf(fmaxf(0.f, mid * mid - det));
+  const float r = ceilf(rp.radius_sigma * sqrtf(lmax));
+  f.xy[0] = fmaf(rp.fx, x * iz, rp.cx);
+  f.xy[1] = fmaf(rp.fy, y * iz, rp.cy);
+  if (!isfinite(f.xy[0]) || !isfinite(f.xy[1]) || !isfinite(r)) return;
+  // tiles holding a pixel centre inside [x - r, x + r] x [y - r, y + r]
+  float ulo = ceilf(f.xy[0] - r), uhi = floorf(f.xy[0] + r);
+  float vlo = ceilf(f.xy[1] - r), vhi = floorf(f.xy[1] + r);
+  ulo = fmaxf(ulo, 0.f);
+  vlo = fmaxf(vlo, 0.f);
+  uhi = fminf(uhi, (float)(rp.W - 1));
+  vhi = fminf(vhi, (float)(rp.H - 1));
+  if (ulo > uhi || vlo > vhi) return;
+  const int tx0 = (int)ulo / rp.tile_w, tx1 = (int)uhi / rp.tile_w + 1;
+  const int ty0 = (int)vlo / rp.tile_h, ty1 = (int)vhi / rp.tile_h + 1;
+  f.rect = make_ushort4((unsigned short)tx0, (unsigned short)ty0, (unsigned short)tx1, (unsigned short)ty1);
+  f.ntiles = (uint32_t)((tx1 - tx0) * (ty1 - ty0));
+  f.visible = true;
+}
+
+// Loads one Gaussian's [n,3] rows: whole warps with a 16-byte-aligned base stage the 96
+// floats of each array through shared memory as 24 float4 loads; others load scalars.
+__device__ __forceinline__ void load_rows3(const float* __restrict__ src, int64_t wbase, bool vec, int lane,
+                                           int64_t i, float* stage, float out[3]) {
+  if (vec) {
+    if (lane < 24) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(src + 3 * wbase) + lane);
+      stage[4 * lane + 0] = v.x; stage[4 * lane + 1] = v.y;
+      stage[4 * lane + 2] = v.z; stage[4 * lane + 3] = v.w;
+    }
+    __syncwarp();
+    out[0] = stage[3 * lane]; out[1] = stage[3 * lane + 1]; out[2] = stage[3 * lane + 2];
+    __syncwarp();
+  } else {
+    out[0] = __ldg(src + 3 * i); out[1] = __ldg(src + 3 * i + 1); out[2] = __ldg(src + 3 * i + 2);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_preprocess(RasterParams rp, dqo_gaussians g, ProjBuffers o) {
+  __shared__ float stage[kThreads / 32][96];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  const int64_t wbase = i - lane;
+  const bool full = wbase + 32 <= g.n;
+  const bool in = i < g.n;
+  float mean[3] = {0, 0, 0}, ls[3] = {0, 0, 0}, rgb[3] = {0, 0, 0};
+  const bool vm = full && ((reinterpret_cast<uintptr_t>(g.means) & 15) == 0);
+  const bool vl = full && ((reinterpret_cast<uintptr_t>(g.log_scales) & 15) == 0);
+  const bool vc = full && ((reinterpret_cast<uintptr_t>(g.rgb) & 15) == 0);
+  if (full || in) {
+    if (vm || in) load_rows3(g.means, wbase, vm, lane, i, stage[warp], mean);
+    if (vl || in) load_rows3(g.log_scales, wbase, vl, lane, i, stage[warp], ls);
+    if (vc || in) load_rows3(g.rgb, wbase, vc, lane, i, stage[warp], rgb);
+  }
+  Footprint f;
+  f.visible = false;
+  if (in) {
+    float4 q;
+    if ((reinterpret_cast<uintptr_t>(g.quats) & 15) == 0) {
+      q = __ldg(reinterpret_cast<const float4*>(g.quats) + i);
+    } else {
+      q = make_float4(g.quats[4 * i], g.quats[4 * i + 1], g.quats[4 * i + 2], g.quats[4 * i + 3]);
+    }
+    footprint(rp, mean, ls, q, __ldg(g.opacity_logit + i), f);
+    const int32_t id = __ldg(g.obj_id + i);
+    const bool has_obj = id >= 0 && id < rp.num_objects;
+    const uint32_t og = (__ldg(g.flags + i) & 1u) ? 0x80000000u : 0u;
+    const uint32_t idbits = (has_obj ? (uint32_t)id : kNoObject) | og;
+    const float sc = -0.5f * kLog2e;
+    o.p0[i] = make_float4(f.xy[0], f.xy[1], sc * f.conic[0], 2.f * sc * f.conic[1]);
+    o.p1[i] = make_float4(sc * f.conic[2], f.opac, f.pc[2], __uint_as_float(idbits));
+    o.p2[i] = make_float4(rgb[0], rgb[1], rgb[2], 0.f);
+    o.rect[i] = f.rect;
+    o.ntiles[i] = f.ntiles;
+    o.zkey[i] = f.visible ? __float_as_uint(f.pc[2]) : 0xFFFFFFFFu;
+    o.zval[i] = (uint32_t)i;
+    o.gid[i] = has_obj ? (uint32_t)id : 0xFFFFFFFFu;
+  }
+  const uint32_t vis = __ballot_sync(0xFFFFFFFFu, in && f.visible);
+  if (lane == 0 && vis) atomicAdd(o.n_visible, (uint32_t)__popc(vis));
+}
+
+__global__ void __launch_bounds__(kThreads) k_preprocess_backward(PreBwdArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (i >= a.n) return;
+  if (a.ntiles[i] == 0) return;  // culled: never blended, zero gradient
+  const RasterParams& rp = a.rp;
+  const float mean[3] = {a.means[3 * i], a.means[3 * i + 1], a.means[3 * i + 2]};
+  const float ls[3] = {a.log_scales[3 * i], a.log_scales[3 * i + 1], a.log_scales[3 * i + 2]};
+  const float4 q = make_float4(a.quats[4 * i], a.quats[4 * i + 1], a.quats[4 * i + 2], a.quats[4 * i + 3]);
+  const float logit = a.opacity_logit[i];
+  Footprint f;
+  footprint(rp, mean, ls, q, logit, f);
+  if (!f.visible) return;
+  const float4 r0 = reinterpret_cast<const float4*>(a.grad2d)[3 * i + 0];  // m_x m_y m_xx m_xy
+  const float4 r1 = reinterpret_cast<const float4*>(a.grad2d)[3 * i + 1];  // m_yy d_opac d_r d_g
+  const float4 r2 = reinterpret_cast<const float4*>(a.grad2d)[3 * i + 2];  // d_b d_z - -
+  const float ca = f.conic[0], cb = f.conic[1], cc = f.conic[2];
+  // 2D mean and conic gradients from the moments (exponent -(a dx^2 + 2 b dx dy + c dy^2)/2)
+  const float gx = ca * r0.x + cb * r0.y;
+  const float gy = cb * r0.x + cc * r0.y;
+  const float ga = -0.5f * r0.z, gb = -r0.w, gc = -0.5f * r1.x;
+  if (a.d_rgb) {
+    a.d_rgb[3 * i + 0] += r1.z;
+    a.d_rgb[3 * i + 1] += r1.w;
+    a.d_rgb[3 * i + 2] += r2.x;
+  }
+  if (a.d_logit) a.d_logit[i] += r1.y * f.opac * (1.f - f.opac);
+  // dL/dSigma' = -Cn Gm Cn, Cn = [[a, b], [b, c]], Gm = [[ga, gb/2], [gb/2, gc]]
+  const float m00 = ca * ga + cb * 0.5f * gb, m01 = ca * 0.5f * gb + cb * gc;
+  const float m10 = cb * ga + cc * 0.5f * gb, m11 = cb * 0.5f * gb + cc * gc;
+  const float S00 = -(m00 * ca + m01 * cb);
+  const float S01 = -(m00 * cb + m01 * cc);
+  const float S11 = -(m10 * cb + m11 * cc);
+  // Sigma' = V V^T (+ lowpass): dL/dV = 2 S V
+  float dV[2][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    dV[0][k] = 2.f * (S00 * f.V[0][k] + S01 * f.V[1][k]);
+    dV[1][k] = 2.f * (S01 * f.V[0][k] + S11 * f.V[1][k]);
+  }
+  // V = T2 Mm, Mm = R diag(s): dT2 = dV Mm^T, dMm = T2^T dV
+  float dT2[2][3], dR[3][3], ds[3];
+#pragma unroll
+  for (int i2 = 0; i2 < 2; ++i2)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      dT2[i2][j] = dV[i2][0] * f.R[j][0] * f.s[0] + dV[i2][1] * f.R[j][1] * f.s[1] + dV[i2][2] * f.R[j][2] * f.s[2];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float dM = f.T2[0][j] * dV[0][k] + f.T2[1][j] * dV[1][k];
+      dR[j][k] = dM * f.s[k];
+      acc += dM * f.R[j][k];
+    }
+    ds[k] = acc;
+  }
+  // T2 = J W: dJ = dT2 W^T
+  const float* W = rp.vm;
+  const float dJ00 = dT2[0][0] * W[0] + dT2[0][1] * W[1] + dT2[0][2] * W[2];
+  const float dJ02 = dT2[0][0] * W[8] + dT2[0][1] * W[9] + dT2[0][2] * W[10];
+  const float dJ11 = dT2[1][0] * W[4] + dT2[1][1] * W[5] + dT2[1][2] * W[6];
+  const float dJ12 = dT2[1][0] * W[8] + dT2[1][1] * W[9] + dT2[1][2] * W[10];
+  const float x = f.pc[0], y = f.pc[1], z = f.pc[2];
+  const float iz = 1.f / z, iz2 = iz * iz, iz3 = iz2 * iz;
+  float dpc0 = gx * rp.fx * iz + dJ02 * (-rp.fx * iz2);
+  float dpc1 = gy * rp.fy * iz + dJ12 * (-rp.fy * iz2);
+  float dpc2 = -gx * rp.fx * x * iz2 - gy * rp.fy * y * iz2 + r2.y + dJ00 * (-rp.fx * iz2) +
+               dJ02 * (2.f * rp.fx * x * iz3) + dJ11 * (-rp.fy * iz2) + dJ12 * (2.f * rp.fy * y * iz3);
+  if (a.d_means) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) a.d_means[3 * i + j] += W[j] * dpc0 + W[4 + j] * dpc1 + W[8 + j] * dpc2;
+  }
+  if (a.d_log_scales) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) a.d_log_scales[3 * i + k] += ds[k] * f.s[k];
+  }
+  if (a.d_quats) {
+    const float w = f.qn[0], qx = f.qn[1], qy = f.qn[2], qz = f.qn[3];
+    float dq[4];
+    dq[0] = 2.f * (-qz * dR[0][1] + qy * dR[0][2] + qz * dR[1][0] - qx * dR[1][2] - qy * dR[2][0] + qx * dR[2][1]);
+    dq[1] = 2.f * (qy * dR[0][1] + qz * dR[0][2] + qy * dR[1][0] - 2.f * qx * dR[1][1] - w * dR[1][2] +
+                   qz * dR[2][0] + w * dR[2][1] - 2.f * qx * dR[2][2]);
+    dq[2] = 2.f * (-2.f * qy * dR[0][0] + qx * dR[0][1] + w * dR[0][2] + qx * dR[1][0] + qz * dR[1][2] -
+                   w * dR[2][0] + qz * dR[2][1] - 2.f * qy * dR[2][2]);
+    dq[3] = 2.f * (-2.f * qz * dR[0][0] - w * dR[0][1] + qx * dR[0][2] + w * dR[1][0] - 2.f * qz * dR[1][1] +
+                   qy * dR[1][2] + qx * dR[2][0] + qy * dR[2][1]);
+    const float dot = dq[0] * w + dq[1] * qx + dq[2] * qy + dq[3] * qz;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a.d_quats[4 * i + k] += (dq[k] - f.qn[k] * dot) * f.qinv;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_preprocess(const RasterParams& rp, const dqo_gaussians& g, const ProjBuffers& out,
+                              cudaStream_t s) {
+  if (g.n == 0) return cudaSuccess;
+  const int64_t blocks = (g.n + kThreads - 1) / kThreads;
+  k_preprocess<<<(unsigned)blocks, kThreads, 0, s>>>(rp, g, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess_backward(const PreBwdArgs& a, cudaStream_t s) {
+  if (a.n == 0) return cudaSuccess;
+  const int64_t blocks = (a.n + kThreads - 1) / kThreads;
+  k_preprocess_backward<<<(unsigned)blocks, kThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace dqo

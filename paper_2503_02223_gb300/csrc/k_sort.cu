@@ -1,0 +1,329 @@
+// Binning and sorting (K2-K5): exclusive scan, LSD radix sort, pair emission and tile
+// ranges.  The tile lists the blend kernels walk are ordered by (tile, depth, index):
+//   1. the Gaussians are radix-sorted once by the bit pattern of their (positive) camera
+//      depth, stable on the index, which gives each visible Gaussian a depth rank;
+//   2. every (tile, Gaussian) pair gets the key (tile << rank_bits) | rank -- unique, so a
+//      plain radix sort of these keys yields (tile, depth bits, index) order with no
+//      values carried along;
+//   3. tile ranges are read off the sorted keys and ranks mapped back to indices.
+// Keys are 32-bit when tile and rank bits fit, else 64-bit.
+#include "dqo_internal.cuh"
+
+namespace dqo {
+namespace {
+
+// ---------------------------------------------------------------- block-wide scan helpers
+
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_scan(T v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T u = __shfl_up_sync(0xFFFFFFFFu, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
+// Exclusive scan across the CTA of one value per thread; returns the CTA total.
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T& total) {
+  __shared__ T warp_tot[kThreads / 32 + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const T inc = warp_inclusive_scan(v);
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    T t = lane < kThreads / 32 ? warp_tot[lane] : T(0);
+    const T ti = warp_inclusive_scan(t);
+    if (lane < kThreads / 32) warp_tot[lane] = ti - t;
+    if (lane == kThreads / 32 - 1) warp_tot[kThreads / 32] = ti;  // spare slot: see size below
+  }
+  __syncthreads();
+  const T ex = warp_tot[warp] + inc - v;
+  total = warp_tot[kThreads / 32];
+  __syncthreads();
+  return ex;
+}
+
+// ---------------------------------------------------------------- exclusive scan (3 phases)
+
+__global__ void __launch_bounds__(kThreads) k_scan_reduce(const uint32_t* __restrict__ in, int64_t n,
+                                                          uint64_t* __restrict__ partial) {
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  uint64_t acc = 0;
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    const int64_t i = base + k * kThreads + threadIdx.x;
+    if (i < n) acc += in[i];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+  __shared__ uint64_t ws[kThreads / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t t = 0;
+    for (int w = 0; w < kThreads / 32; ++w) t += ws[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
+// Single CTA: exclusive scan of the per-CTA partials in place; writes the grand total.
+__global__ void __launch_bounds__(kThreads) k_scan_partials(uint64_t* __restrict__ partial, int64_t nb,
+                                                            uint64_t* __restrict__ total) {
+  __shared__ uint64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t c = 0; c < nb; c += kThreads) {
+    const int64_t i = c + threadIdx.x;
+    const uint64_t v = i < nb ? partial[i] : 0;
+    uint64_t tot;
+    const uint64_t ex = block_exclusive_scan<uint64_t>(v, tot);
+    if (i < nb) partial[i] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void __launch_bounds__(kThreads) k_scan_down(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                                        int64_t n, const uint64_t* __restrict__ partial) {
+  __shared__ uint32_t tile[kSortTile];
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    const int64_t i = base + k * kThreads + threadIdx.x;
+    tile[k * kThreads + threadIdx.x] = i < n ? in[i] : 0u;
+  }
+  __syncthreads();
+  uint32_t v[kSortItems];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    v[k] = tile[threadIdx.x * kSortItems + k];
+    sum += v[k];
+  }
+  uint32_t tot;
+  uint32_t run = block_exclusive_scan<uint32_t>(sum, tot) + (uint32_t)partial[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    tile[threadIdx.x * kSortItems + k] = run;
+    run += v[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    const int64_t i = base + k * kThreads + threadIdx.x;
+    if (i < n) out[i] = tile[k * kThreads + threadIdx.x];
+  }
+}
+
+// ---------------------------------------------------------------- LSD radix sort passes
+
+// Per-CTA digit histogram, stored digit-major: hist[d * nblocks + b].
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_radix_hist(const K* __restrict__ keys, int64_t n, int shift,
+                                                         uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[kRadixBins];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    const int64_t i = base + k * kThreads + threadIdx.x;
+    if (i < n) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & (kRadixBins - 1)], 1u);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter of one pass.  Warp w of a CTA owns keys [base + 512 w, base + 512 (w+1))
+// and ranks them round by round (32 consecutive keys per round) with __match_any_sync
+// against a warp-private digit counter; warps are then offset by an exclusive scan of
+// their counts per digit, and the CTA by the global digit-major scan.
+template <typename K, bool kVals>
+__global__ void __launch_bounds__(kThreads) k_radix_scatter(const K* __restrict__ kin, K* __restrict__ kout,
+                                                            const uint32_t* __restrict__ vin,
+                                                            uint32_t* __restrict__ vout, int64_t n, int shift,
+                                                            const uint32_t* __restrict__ offs) {
+  __shared__ uint32_t cnt[kThreads / 32][kRadixBins];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int d = threadIdx.x; d < (kThreads / 32) * kRadixBins; d += kThreads) (&cnt[0][0])[d] = 0;
+  __syncthreads();
+  const int64_t wbase = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * 32 * kSortItems;
+  K key[kSortItems];
+  uint32_t val[kSortItems];
+  uint32_t pos[kSortItems];
+  const uint32_t lt = lanemask_lt();
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const int64_t i = wbase + r * 32 + lane;
+    const bool ok = i < n;
+    key[r] = ok ? kin[i] : K(0);
+    if (kVals) val[r] = ok ? vin[i] : 0u;
+    const uint32_t d = (uint32_t)(key[r] >> shift) & (kRadixBins - 1);
+    const uint32_t active = __ballot_sync(0xFFFFFFFFu, ok);
+    uint32_t peers = __match_any_sync(0xFFFFFFFFu, ok ? d : 0xFFFFFFFFu);
+    peers &= active;
+    const uint32_t before = cnt[warp][d];
+    __syncwarp();
+    if (ok) {
+      pos[r] = before + __popc(peers & lt);
+      const int leader = __ffs(peers) - 1;
+      if (lane == leader) cnt[warp][d] = before + __popc(peers);
+    } else {
+      pos[r] = 0xFFFFFFFFu;
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // exclusive scan over warps per digit (thread t owns digit t)
+  {
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) {
+      const uint32_t c = cnt[w][threadIdx.x];
+      cnt[w][threadIdx.x] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    if (pos[r] == 0xFFFFFFFFu) continue;
+    const uint32_t d = (uint32_t)(key[r] >> shift) & (kRadixBins - 1);
+    const uint32_t dst = offs[(int64_t)d * gridDim.x + blockIdx.x] + cnt[warp][d] + pos[r];
+    kout[dst] = key[r];
+    if (kVals) vout[dst] = val[r];
+  }
+}
+
+// ---------------------------------------------------------------- binning helpers
+
+__global__ void k_rank_scatter(const uint32_t* __restrict__ order, int64_t n, uint32_t* __restrict__ rank) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) rank[order[r]] = (uint32_t)r;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_emit_pairs(const ushort4* __restrict__ rect,
+                                                         const uint32_t* __restrict__ offsets,
+                                                         const uint32_t* __restrict__ rank, int64_t n, int ntx,
+                                                         int rank_bits, K* __restrict__ keys) {
+  const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (i >= n) return;
+  const ushort4 r = rect[i];
+  if (r.z <= r.x || r.w <= r.y) return;
+  uint32_t o = offsets[i];
+  const K rk = (K)rank[i];
+  for (int ty = r.y; ty < r.w; ++ty)
+    for (int tx = r.x; tx < r.z; ++tx) keys[o++] = ((K)((uint32_t)ty * ntx + tx) << rank_bits) | rk;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_tile_ranges(const K* __restrict__ keys, int64_t m, int rank_bits,
+                                                          const uint32_t* __restrict__ order,
+                                                          uint2* __restrict__ ranges, uint32_t* __restrict__ list) {
+  const int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (p >= m) return;
+  const K k = keys[p];
+  const uint32_t tile = (uint32_t)(k >> rank_bits);
+  list[p] = order[(uint32_t)(k & (((K)1 << rank_bits) - 1))];
+  if (p == 0 || (uint32_t)(keys[p - 1] >> rank_bits) != tile) ranges[tile].x = (uint32_t)p;
+  if (p == m - 1 || (uint32_t)(keys[p + 1] >> rank_bits) != tile) ranges[tile].y = (uint32_t)(p + 1);
+}
+
+inline unsigned grid_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
+
+template <typename K, bool kVals>
+cudaError_t radix_sort_impl(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n, int end_bit, uint32_t* hist,
+                            uint64_t* scan_scratch, int* sel, cudaStream_t s) {
+  *sel = 0;
+  if (n <= 1 || end_bit <= 0) return cudaSuccess;
+  const unsigned nb = grid_for(n, kSortTile);
+  const int64_t hn = (int64_t)nb * kRadixBins;
+  K* kin = ka; K* kout = kb;
+  uint32_t* vin = va; uint32_t* vout = vb;
+  for (int shift = 0; shift < end_bit; shift += kRadixBits) {
+    k_radix_hist<K><<<nb, kThreads, 0, s>>>(kin, n, shift, hist);
+    cudaError_t e = launch_exclusive_scan(hist, hist, hn, scan_scratch, nullptr, s);
+    if (e != cudaSuccess) return e;
+    k_radix_scatter<K, kVals><<<nb, kThreads, 0, s>>>(kin, kout, vin, vout, n, shift, hist);
+    std::swap(kin, kout);
+    std::swap(vin, vout);
+    *sel ^= 1;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t scan_scratch_words(int64_t n) { return (size_t)grid_for(n > 0 ? n : 1, kSortTile) + 1; }
+
+cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint64_t* scratch, uint64_t* total,
+                                  cudaStream_t s) {
+  if (n <= 0) {
+    if (total) return cudaMemsetAsync(total, 0, sizeof(uint64_t), s);
+    return cudaSuccess;
+  }
+  const unsigned nb = grid_for(n, kSortTile);
+  k_scan_reduce<<<nb, kThreads, 0, s>>>(in, n, scratch);
+  k_scan_partials<<<1, kThreads, 0, s>>>(scratch, nb, total);
+  k_scan_down<<<nb, kThreads, 0, s>>>(in, out, n, scratch);
+  return cudaGetLastError();
+}
+
+size_t radix_scratch_words(int64_t n) { return (size_t)grid_for(n > 0 ? n : 1, kSortTile) * kRadixBins; }
+
+cudaError_t radix_sort_u32(uint32_t* keys_a, uint32_t* keys_b, uint32_t* vals_a, uint32_t* vals_b, int64_t n,
+                           int end_bit, uint32_t* hist_scratch, uint64_t* scan_scratch, int* sel, cudaStream_t s) {
+  if (vals_a)
+    return radix_sort_impl<uint32_t, true>(keys_a, keys_b, vals_a, vals_b, n, end_bit, hist_scratch, scan_scratch,
+                                           sel, s);
+  return radix_sort_impl<uint32_t, false>(keys_a, keys_b, nullptr, nullptr, n, end_bit, hist_scratch,
+                                          scan_scratch, sel, s);
+}
+
+cudaError_t radix_sort_u64(uint64_t* keys_a, uint64_t* keys_b, int64_t n, int end_bit, uint32_t* hist_scratch,
+                           uint64_t* scan_scratch, int* sel, cudaStream_t s) {
+  return radix_sort_impl<uint64_t, false>(keys_a, keys_b, nullptr, nullptr, n, end_bit, hist_scratch,
+                                          scan_scratch, sel, s);
+}
+
+cudaError_t launch_rank_scatter(const uint32_t* order, int64_t n, uint32_t* rank, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_rank_scatter<<<grid_for(n, kThreads), kThreads, 0, s>>>(order, n, rank);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emit_pairs_u32(const ushort4* rect, const uint32_t* offsets, const uint32_t* rank, int64_t n,
+                                  int ntx, int rank_bits, uint32_t* keys, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_emit_pairs<uint32_t><<<grid_for(n, kThreads), kThreads, 0, s>>>(rect, offsets, rank, n, ntx, rank_bits, keys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emit_pairs_u64(const ushort4* rect, const uint32_t* offsets, const uint32_t* rank, int64_t n,
+                                  int ntx, int rank_bits, uint64_t* keys, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_emit_pairs<uint64_t><<<grid_for(n, kThreads), kThreads, 0, s>>>(rect, offsets, rank, n, ntx, rank_bits, keys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_ranges_u32(const uint32_t* keys, int64_t m, int rank_bits, const uint32_t* order,
+                                   uint2* ranges, uint32_t* list, cudaStream_t s) {
+  if (m == 0) return cudaSuccess;
+  k_tile_ranges<uint32_t><<<grid_for(m, kThreads), kThreads, 0, s>>>(keys, m, rank_bits, order, ranges, list);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_ranges_u64(const uint64_t* keys, int64_t m, int rank_bits, const uint32_t* order,
+                                   uint2* ranges, uint32_t* list, cudaStream_t s) {
+  if (m == 0) return cudaSuccess;
+  k_tile_ranges<uint64_t><<<grid_for(m, kThreads), kThreads, 0, s>>>(keys, m, rank_bits, order, ranges, list);
+  return cudaGetLastError();
+}
+
+}  // namespace dqo

@@ -1,0 +1,339 @@
+"""Thin Python binding of libdqo.so (include/dqo.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and passes torch tensors'
+device pointers and the current CUDA stream through ctypes; all arithmetic runs in the
+library's CUDA kernels.  PyTorch supplies device memory and streams.  There is no
+fallback: if the library is missing or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+c_f = C.c_float
+c_i32 = C.c_int32
+c_i64 = C.c_int64
+c_p = C.c_void_p
+
+DQO_OK, DQO_EINVAL, DQO_ENOMEM, DQO_ECUDA, DQO_ETIMEOUT, DQO_ENOTIMPL, DQO_ESTATE = range(7)
+PHASES = ("project", "depth_sort", "binning", "blend_fwd", "blend_bwd", "project_bwd", "quadric")
+(DQO_BUF_PROJ, DQO_BUF_RECT, DQO_BUF_DEPTH_ORDER, DQO_BUF_TILE_RANGES, DQO_BUF_TILE_LIST, DQO_BUF_T_FINAL,
+ DQO_BUF_N_CONTRIB, DQO_BUF_GRAD2D) = range(8)
+
+
+class dqo_settings(C.Structure):
+    _fields_ = [("tile_w", c_i32), ("tile_h", c_i32), ("alpha_clamp", c_f), ("alpha_min", c_f), ("t_stop", c_f),
+                ("znear", c_f), ("lowpass", c_f), ("radius_sigma", c_f), ("lambda_ins", c_f), ("bg", c_f * 3),
+                ("og_filter", c_i32), ("batch", c_i32)]
+
+
+class dqo_camera(C.Structure):
+    _fields_ = [("fx", c_f), ("fy", c_f), ("cx", c_f), ("cy", c_f), ("width", c_i32), ("height", c_i32),
+                ("viewmat", c_f * 12)]
+
+
+class dqo_gaussians(C.Structure):
+    _fields_ = [("n", c_i64), ("num_objects", c_i32), ("means", c_p), ("log_scales", c_p), ("quats", c_p),
+                ("opacity_logit", c_p), ("rgb", c_p), ("obj_id", c_p), ("flags", c_p)]
+
+
+class dqo_targets(C.Structure):
+    _fields_ = [("rgb", c_p), ("depth", c_p), ("gt_id", c_p)]
+
+
+class dqo_render_out(C.Structure):
+    _fields_ = [("rgb", c_p), ("depth", c_p), ("alpha", c_p), ("ins", c_p), ("id_map", c_p), ("loss", c_p)]
+
+
+class dqo_pixel_grads(C.Structure):
+    _fields_ = [("rgb", c_p), ("depth", c_p), ("alpha", c_p), ("ins", c_p)]
+
+
+class dqo_gaussian_grads(C.Structure):
+    _fields_ = [("means", c_p), ("log_scales", c_p), ("quats", c_p), ("opacity_logit", c_p), ("rgb", c_p)]
+
+
+# Exported entry points and their argument types (must match include/dqo.h).
+_SIGS = {
+    "dqo_settings_default": (None, [c_p]),
+    "dqo_create": (c_i32, [c_p, C.c_int]),
+    "dqo_destroy": (None, [c_p]),
+    "dqo_status_str": (C.c_char_p, [c_i32]),
+    "dqo_last_cuda_error": (C.c_int, [c_p]),
+    "dqo_version": (C.c_int, []),
+    "dqo_render_forward": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_p, c_p]),
+    "dqo_render_backward": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p]),
+    "dqo_get_buffer": (c_i32, [c_p, c_i32, c_p, C.c_size_t, c_p, c_p]),
+    "dqo_get_counts": (c_i32, [c_p, c_p, c_p, c_p]),
+    "dqo_set_timing": (c_i32, [c_p, C.c_int]),
+    "dqo_get_timings": (c_i32, [c_p, c_p, c_i32]),
+    "dqo_launch_count": (c_i64, [c_p]),
+    "dqo_quadric_project": (c_i32, [c_p, c_i32, c_p, c_i32, c_p, c_p, c_p, c_i32, c_p, c_p, c_p, c_p]),
+    "dqo_quadric_bbox_loss": (c_i32, [c_p, c_i32, c_p, c_i32, c_p, c_p, c_p, c_i32, c_p, c_p, c_p, c_p]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+class DqoError(RuntimeError):
+    def __init__(self, fn, status, cuda_err=0):
+        msg = f"{fn} failed: status {status}"
+        if _lib is not None:
+            msg += f" ({_lib.dqo_status_str(status).decode()})"
+        if cuda_err:
+            msg += f", cudaError {cuda_err}"
+        super().__init__(msg)
+        self.status = status
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Loads libdqo.so; raises if it is missing (no fallback path exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = lib_path()
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"{path} is missing: build it with paper_2503_02223_gb300.build.build()")
+            _build.build()
+        lib = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(fn: str, status: int, ctx=None):
+    if status != DQO_OK:
+        err = _lib.dqo_last_cuda_error(ctx) if ctx else 0
+        raise DqoError(fn, status, err)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tensor must be on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+# ------------------------------------------------------------------------ structs from python
+
+def settings(**kw) -> dqo_settings:
+    lib = load()
+    s = dqo_settings()
+    lib.dqo_settings_default(C.byref(s))
+    for k, v in kw.items():
+        if k == "bg":
+            s.bg = (c_f * 3)(*v)
+        else:
+            setattr(s, k, v)
+    return s
+
+
+def camera(cam: dict) -> dqo_camera:
+    c = dqo_camera()
+    c.fx, c.fy, c.cx, c.cy = cam["fx"], cam["fy"], cam["cx"], cam["cy"]
+    c.width, c.height = cam["width"], cam["height"]
+    vm = cam["viewmat"]
+    vm = vm.reshape(-1).tolist() if hasattr(vm, "reshape") else list(vm)
+    c.viewmat = (c_f * 12)(*vm)
+    return c
+
+
+_GAUSS_TYPES = dict(means=torch.float32, log_scales=torch.float32, quats=torch.float32,
+                    opacity_logit=torch.float32, rgb=torch.float32, obj_id=torch.int32, flags=torch.uint8)
+
+
+def gaussians(g: dict, num_objects: int) -> dqo_gaussians:
+    """g: dict of contiguous CUDA tensors (means [n,3], log_scales [n,3], quats [n,4],
+    opacity_logit [n], rgb [n,3], obj_id [n] int32, flags [n] uint8)."""
+    for k, dt in _GAUSS_TYPES.items():
+        if g[k].dtype != dt:
+            raise ValueError(f"{k} must be {dt}, got {g[k].dtype}")
+    s = dqo_gaussians()
+    s.n = g["means"].shape[0]
+    s.num_objects = num_objects
+    for k in _GAUSS_TYPES:
+        setattr(s, k, _ptr(g[k]))
+    return s
+
+
+def targets(t: dict | None):
+    if t is None:
+        return None
+    s = dqo_targets()
+    s.rgb = _ptr(t["rgb"])
+    s.depth = _ptr(t.get("depth"))
+    s.gt_id = _ptr(t["gt_id"])
+    return s
+
+
+def render_out(o: dict) -> dqo_render_out:
+    s = dqo_render_out()
+    for k in ("rgb", "depth", "alpha", "ins", "id_map", "loss"):
+        setattr(s, k, _ptr(o.get(k)))
+    return s
+
+
+def pixel_grads(pg: dict | None):
+    if pg is None:
+        return None
+    s = dqo_pixel_grads()
+    for k in ("rgb", "depth", "alpha", "ins"):
+        setattr(s, k, _ptr(pg.get(k)))
+    return s
+
+
+def gaussian_grads(gg: dict) -> dqo_gaussian_grads:
+    s = dqo_gaussian_grads()
+    for k in ("means", "log_scales", "quats", "opacity_logit", "rgb"):
+        setattr(s, k, _ptr(gg.get(k)))
+    return s
+
+
+# ------------------------------------------------------------------------ entry points
+
+class Context:
+    """Owns a dqo_ctx (the library's workspace) on one device."""
+
+    def __init__(self, device: int | None = None):
+        lib = load()
+        self.device = torch.cuda.current_device() if device is None else device
+        h = c_p()
+        _check("dqo_create", lib.dqo_create(C.byref(h), self.device))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            torch.cuda.synchronize(self.device)
+            _lib.dqo_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dqo_render_forward(ctx: Context, st: dqo_settings, g: dqo_gaussians, cam: dqo_camera, t, out: dqo_render_out,
+                       stream=None):
+    lib = load()
+    tp = C.byref(t) if t is not None else None
+    _check("dqo_render_forward",
+           lib.dqo_render_forward(ctx.handle, C.byref(st), C.byref(g), C.byref(cam), tp, C.byref(out),
+                                  _stream(stream)), ctx.handle)
+
+
+def dqo_render_backward(ctx: Context, st: dqo_settings, g: dqo_gaussians, cam: dqo_camera, t, pg,
+                        grads: dqo_gaussian_grads, stream=None):
+    lib = load()
+    tp = C.byref(t) if t is not None else None
+    pp = C.byref(pg) if pg is not None else None
+    _check("dqo_render_backward",
+           lib.dqo_render_backward(ctx.handle, C.byref(st), C.byref(g), C.byref(cam), tp, pp, C.byref(grads),
+                                   _stream(stream)), ctx.handle)
+
+
+def dqo_get_buffer(ctx: Context, which: int, dst: torch.Tensor | None = None, stream=None):
+    """Returns the buffer size in bytes; copies into dst (any device) when given."""
+    lib = load()
+    nbytes = C.c_size_t(0)
+    _check("dqo_get_buffer", lib.dqo_get_buffer(ctx.handle, which, None, 0, C.byref(nbytes), _stream(stream)),
+           ctx.handle)
+    if dst is not None:
+        cap = dst.numel() * dst.element_size()
+        _check("dqo_get_buffer", lib.dqo_get_buffer(ctx.handle, which, dst.data_ptr(), cap, C.byref(nbytes),
+                                                    _stream(stream)), ctx.handle)
+    return nbytes.value
+
+
+def dqo_get_counts(ctx: Context):
+    lib = load()
+    m, v, t = c_i64(0), c_i64(0), c_i32(0)
+    _check("dqo_get_counts", lib.dqo_get_counts(ctx.handle, C.byref(m), C.byref(v), C.byref(t)), ctx.handle)
+    return m.value, v.value, t.value
+
+
+def dqo_set_timing(ctx: Context, enable: bool):
+    _check("dqo_set_timing", load().dqo_set_timing(ctx.handle, 1 if enable else 0), ctx.handle)
+
+
+def dqo_get_timings(ctx: Context) -> dict:
+    """Device milliseconds per phase of the most recent timed calls (-1 if not run)."""
+    buf = (c_f * len(PHASES))()
+    _check("dqo_get_timings", load().dqo_get_timings(ctx.handle, buf, len(PHASES)), ctx.handle)
+    return dict(zip(PHASES, list(buf)))
+
+
+def dqo_launch_count(ctx: Context) -> int:
+    return int(load().dqo_launch_count(ctx.handle))
+
+
+def dqo_quadric_project(ctx: Context, params, P, q_ptr, pair_v, conic=None, bbox=None, valid=None, stream=None):
+    lib = load()
+    _check("dqo_quadric_project",
+           lib.dqo_quadric_project(ctx.handle, params.shape[0], _ptr(params), P.shape[0], _ptr(P), _ptr(q_ptr),
+                                   _ptr(pair_v), pair_v.shape[0], _ptr(conic), _ptr(bbox), _ptr(valid),
+                                   _stream(stream)), ctx.handle)
+
+
+def dqo_quadric_bbox_loss(ctx: Context, params, P, q_ptr, pair_v, obs, loss=None, dparams=None, stream=None):
+    lib = load()
+    _check("dqo_quadric_bbox_loss",
+           lib.dqo_quadric_bbox_loss(ctx.handle, params.shape[0], _ptr(params), P.shape[0], _ptr(P), _ptr(q_ptr),
+                                     _ptr(pair_v), pair_v.shape[0], _ptr(obs), _ptr(loss), _ptr(dparams),
+                                     _stream(stream)), ctx.handle)
+
+
+# ------------------------------------------------------------------------ conveniences
+
+def to_device(arrays: dict, device="cuda") -> dict:
+    """numpy dict -> contiguous CUDA tensors (same dtypes)."""
+    out = {}
+    for k, v in arrays.items():
+        if v is None:
+            out[k] = None
+        elif hasattr(v, "dtype") and hasattr(v, "shape") and not isinstance(v, torch.Tensor):
+            out[k] = torch.from_numpy(v.copy() if not v.flags["C_CONTIGUOUS"] else v).to(device)
+        else:
+            out[k] = v
+    return out
+
+
+def alloc_outputs(W: int, H: int, device="cuda", loss=True, id_map=True) -> dict:
+    f = dict(dtype=torch.float32, device=device)
+    o = dict(rgb=torch.empty(H, W, 3, **f), depth=torch.empty(H, W, **f), alpha=torch.empty(H, W, **f),
+             ins=torch.empty(H, W, **f))
+    if id_map:
+        o["id_map"] = torch.empty(H, W, dtype=torch.int32, device=device)
+    if loss:
+        o["loss"] = torch.zeros(4, **f)
+    return o
+
+
+def alloc_grads(n: int, device="cuda") -> dict:
+    f = dict(dtype=torch.float32, device=device)
+    return dict(means=torch.zeros(n, 3, **f), log_scales=torch.zeros(n, 3, **f), quats=torch.zeros(n, 4, **f),
+                opacity_logit=torch.zeros(n, **f), rgb=torch.zeros(n, 3, **f))
