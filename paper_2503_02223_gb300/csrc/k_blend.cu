@@ -20,22 +20,40 @@
 // summed over the warp by a transposing butterfly (16 shuffles), over the CTA with
 // shared-memory atomics, and added to the global per-Gaussian record with vector
 // atomics once per (tile, Gaussian).
+#include <cuda_fp16.h>
+
 #include "dqo_internal.cuh"
 
 namespace dqo {
 namespace {
 
 constexpr int kMaxBatch = 256;
+constexpr uint32_t kFull = 0xFFFFFFFFu;
 
 template <int TW>
-__device__ __forceinline__ void pixel_of(int tile_x0, int tile_y0, int& px, int& py) {
+__device__ __forceinline__ void pixel_of(int tile_x0, int tile_y0, int& px, int& py, float& wx0, float& wy0) {
   constexpr int WX = TW / 8;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  px = tile_x0 + (warp % WX) * 8 + (lane & 7);
-  py = tile_y0 + (warp / WX) * 4 + (lane >> 3);
+  const int bx = tile_x0 + (warp % WX) * 8, by = tile_y0 + (warp / WX) * 4;
+  px = bx + (lane & 7);
+  py = by + (lane >> 3);
+  wx0 = (float)bx;
+  wy0 = (float)by;
 }
 
 __device__ __forceinline__ float sgnf(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
+
+// Box (x0, x1, y0, y1) of the pixels where a Gaussian's alpha can reach alpha_min, from its
+// centre (p0.xy) and the rounded-up half-extents stored as half2 in p2.w.
+__device__ __forceinline__ float4 support_box(const float4& p0, const float4& p2) {
+  const float2 e = __half22float2(*reinterpret_cast<const __half2*>(&p2.w));
+  return make_float4(p0.x - e.x, p0.x + e.x, p0.y - e.y, p0.y + e.y);
+}
+
+// Does the box meet the warp's 8x4 block of pixel centres [wx0, wx0+7] x [wy0, wy0+3]?
+__device__ __forceinline__ bool box_hits(const float4& b, float wx0, float wy0) {
+  return b.x <= wx0 + 7.f && b.y >= wx0 && b.z <= wy0 + 3.f && b.w >= wy0;
+}
 
 // Fills s_slot_id[s - first] with the object id of dense slot s for s in [first, first+kIdSlots).
 __device__ __forceinline__ void slot_ids_for_round(const uint32_t* s_mask, const uint32_t* s_pref, int nw, int first,
@@ -54,7 +72,7 @@ __device__ __forceinline__ void slot_ids_for_round(const uint32_t* s_mask, const
 
 template <int TW, bool kId>
 __global__ void __launch_bounds__(kThreads) k_blend_forward(BlendFwdArgs a) {
-  __shared__ float4 s_p0[kMaxBatch], s_p1[kMaxBatch], s_p2[kMaxBatch];
+  __shared__ float4 s_p0[kMaxBatch], s_p1[kMaxBatch], s_p2[kMaxBatch], s_box[kMaxBatch];
   __shared__ int32_t s_slot[kId ? kMaxBatch : 1];
   __shared__ uint32_t s_mask[kId ? kMaskWords : 1], s_pref[kId ? kMaskWords : 1];
   __shared__ int32_t s_slot_id[kIdSlots];
@@ -66,12 +84,13 @@ __global__ void __launch_bounds__(kThreads) k_blend_forward(BlendFwdArgs a) {
   const int tile = blockIdx.x;
   const int tx = tile % rp.ntx, ty = tile / rp.ntx;
   int px, py;
-  pixel_of<TW>(tx * rp.tile_w, ty * rp.tile_h, px, py);
+  float wx0, wy0;
+  pixel_of<TW>(tx * rp.tile_w, ty * rp.tile_h, px, py, wx0, wy0);
   const bool inside = px < rp.W && py < rp.H;
   const int64_t pix = (int64_t)py * rp.W + px;
   const uint2 rg = a.ranges[tile];
   const int start = (int)rg.x, end = rg.y > rg.x ? (int)rg.y : (int)rg.x;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
   const int B = rp.batch;
 
   int32_t gt = -1;
@@ -124,10 +143,11 @@ __global__ void __launch_bounds__(kThreads) k_blend_forward(BlendFwdArgs a) {
     const int nb = min(B, end - b0);
     if (tid < nb) {
       const uint32_t g = a.list[b0 + tid];
-      const float4 q1 = a.p1[g];
-      s_p0[tid] = a.p0[g];
+      const float4 q0 = a.p0[g], q1 = a.p1[g], q2 = a.p2[g];
+      s_p0[tid] = q0;
       s_p1[tid] = q1;
-      s_p2[tid] = a.p2[g];
+      s_p2[tid] = q2;
+      s_box[tid] = support_box(q0, q2);
       if (kId) {
         const uint32_t id = __float_as_uint(q1.w) & kNoObject;
         int slot = -1;
@@ -139,15 +159,23 @@ __global__ void __launch_bounds__(kThreads) k_blend_forward(BlendFwdArgs a) {
       }
     }
     __syncthreads();
-    if (!done) {
-      for (int j = 0; j < nb; ++j) {
+    if (__all_sync(kFull, done)) continue;
+    // walk only the Gaussians whose alpha-support box meets this warp's pixels, in order
+    for (int c = 0; c < nb; c += 32) {
+      const int jl = c + lane;
+      const bool hit = jl < nb && box_hits(s_box[jl], wx0, wy0);
+      uint32_t m = __ballot_sync(kFull, hit);
+      while (m) {
+        const int j = c + __ffs(m) - 1;
+        m &= m - 1;
+        if (done) continue;
         const float4 q0 = s_p0[j], q1 = s_p1[j];
         float alpha, G, dx, dy;
         if (!eval_gaussian(q0, q1, fpx, fpy, rp.alpha_clamp, rp.alpha_min, alpha, G, dx, dy)) continue;
         const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
         if (Tn < rp.t_stop) {
           done = true;
-          break;
+          continue;
         }
         const float w = __fmul_rn(alpha, T);
         const float4 q2 = s_p2[j];
@@ -170,6 +198,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_forward(BlendFwdArgs a) {
         T = Tn;
         last = b0 - start + j + 1;
       }
+      if (__all_sync(kFull, done)) break;
     }
   }
 
@@ -369,7 +398,7 @@ __device__ __forceinline__ void warp_transpose_sum16(float v[16]) {
 template <int TW>
 __global__ void __launch_bounds__(kThreads) k_blend_backward(BlendBwdArgs a) {
   constexpr int NV = 10;
-  __shared__ float4 s_p0[kMaxBatch], s_p1[kMaxBatch], s_p2[kMaxBatch];
+  __shared__ float4 s_p0[kMaxBatch], s_p1[kMaxBatch], s_p2[kMaxBatch], s_box[kMaxBatch];
   __shared__ uint32_t s_g[kMaxBatch];
   __shared__ float s_acc[kMaxBatch * NV];
   __shared__ uint32_t s_maxn;
@@ -378,7 +407,8 @@ __global__ void __launch_bounds__(kThreads) k_blend_backward(BlendBwdArgs a) {
   const int tile = blockIdx.x;
   const int tx = tile % rp.ntx, ty = tile / rp.ntx;
   int px, py;
-  pixel_of<TW>(tx * rp.tile_w, ty * rp.tile_h, px, py);
+  float wx0, wy0;
+  pixel_of<TW>(tx * rp.tile_w, ty * rp.tile_h, px, py, wx0, wy0);
   const bool inside = px < rp.W && py < rp.H;
   const int64_t pix = (int64_t)py * rp.W + px;
   const uint2 rg = a.ranges[tile];
@@ -407,8 +437,8 @@ __global__ void __launch_bounds__(kThreads) k_blend_backward(BlendBwdArgs a) {
   }
   if (tid == 0) s_maxn = 0;
   __syncthreads();
-  const uint32_t wmax = __reduce_max_sync(0xFFFFFFFFu, nc);
-  if (lane == 0 && wmax) atomicMax(&s_maxn, wmax);
+  const int wmax = (int)__reduce_max_sync(kFull, nc);
+  if (lane == 0 && wmax) atomicMax(&s_maxn, (uint32_t)wmax);
   __syncthreads();
   const int maxn = (int)s_maxn;
   float R = T * (gC0 * rp.bg[0] + gC1 * rp.bg[1] + gC2 * rp.bg[2]);
@@ -419,52 +449,62 @@ __global__ void __launch_bounds__(kThreads) k_blend_backward(BlendBwdArgs a) {
     const int nb = hi - lo;
     if (tid < nb) {
       const uint32_t g = a.list[start + lo + tid];
+      const float4 q0 = a.p0[g], q2 = a.p2[g];
       s_g[tid] = g;
-      s_p0[tid] = a.p0[g];
+      s_p0[tid] = q0;
       s_p1[tid] = a.p1[g];
-      s_p2[tid] = a.p2[g];
+      s_p2[tid] = q2;
+      s_box[tid] = support_box(q0, q2);
     }
     for (int k = tid; k < nb * NV; k += kThreads) s_acc[k] = 0.f;
     __syncthreads();
-    const bool warp_live = __any_sync(0xFFFFFFFFu, (int)nc > lo);
-    if (warp_live) {
-      for (int j = nb - 1; j >= 0; --j) {
-        float v[16];
+    if (wmax > lo) {
+      // back to front over the Gaussians that can reach this warp's pixels
+      for (int c = (nb - 1) & ~31; c >= 0; c -= 32) {
+        const int jl = c + lane;
+        const bool hit = jl < nb && lo + jl < wmax && box_hits(s_box[jl], wx0, wy0);
+        uint32_t m = __ballot_sync(kFull, hit);
+        while (m) {
+          const int bit = 31 - __clz(m);
+          m &= ~(1u << bit);
+          const int j = c + bit;
+          float v[16];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) v[k] = 0.f;
-        bool act = false;
-        if (lo + j < (int)nc) {
-          const float4 q0 = s_p0[j], q1 = s_p1[j];
-          float alpha, G, dx, dy;
-          if (eval_gaussian(q0, q1, fpx, fpy, rp.alpha_clamp, rp.alpha_min, alpha, G, dx, dy)) {
-            act = true;
-            const float oma = 1.f - alpha;
-            T = T / oma;
-            const float w = alpha * T;
-            const float4 q2 = s_p2[j];
-            const uint32_t idog = __float_as_uint(q1.w);
-            const bool counts = (idog & kNoObject) == gt_match && (!rp.og_filter || (idog >> 31));
-            const float U = gC0 * q2.x + gC1 * q2.y + gC2 * q2.z + gD * q1.z + gA + (counts ? gI : 0.f);
-            const float dalpha = T * U - R / oma;
-            R = fmaf(w, U, R);
-            const bool clamped = __fmul_rn(q1.y, G) > rp.alpha_clamp;
-            const float dpow = clamped ? 0.f : dalpha * alpha;
-            v[0] = dpow * dx;
-            v[1] = dpow * dy;
-            v[2] = v[0] * dx;
-            v[3] = v[0] * dy;
-            v[4] = v[1] * dy;
-            v[5] = clamped ? 0.f : dalpha * G;
-            v[6] = w * gC0;
-            v[7] = w * gC1;
-            v[8] = w * gC2;
-            v[9] = w * gD;
+          for (int k = 0; k < 16; ++k) v[k] = 0.f;
+          bool act = false;
+          if (lo + j < (int)nc) {
+            const float4 q0 = s_p0[j], q1 = s_p1[j];
+            float alpha, G, dx, dy;
+            if (eval_gaussian(q0, q1, fpx, fpy, rp.alpha_clamp, rp.alpha_min, alpha, G, dx, dy)) {
+              act = true;
+              const float inv = __frcp_rn(1.f - alpha);
+              T = T * inv;
+              const float w = alpha * T;
+              const float4 q2 = s_p2[j];
+              const uint32_t idog = __float_as_uint(q1.w);
+              const bool counts = (idog & kNoObject) == gt_match && (!rp.og_filter || (idog >> 31));
+              const float U = gC0 * q2.x + gC1 * q2.y + gC2 * q2.z + gD * q1.z + gA + (counts ? gI : 0.f);
+              const float dalpha = T * U - R * inv;
+              R = fmaf(w, U, R);
+              const bool clamped = __fmul_rn(q1.y, G) > rp.alpha_clamp;
+              const float dpow = clamped ? 0.f : dalpha * alpha;
+              v[0] = dpow * dx;
+              v[1] = dpow * dy;
+              v[2] = v[0] * dx;
+              v[3] = v[0] * dy;
+              v[4] = v[1] * dy;
+              v[5] = clamped ? 0.f : dalpha * G;
+              v[6] = w * gC0;
+              v[7] = w * gC1;
+              v[8] = w * gC2;
+              v[9] = w * gD;
+            }
           }
-        }
-        if (__any_sync(0xFFFFFFFFu, act)) {
-          warp_transpose_sum16(v);
-          const int k = lane >> 1;
-          if (!(lane & 1) && k < NV && v[0] != 0.f) atomicAdd(&s_acc[j * NV + k], v[0]);
+          if (__any_sync(kFull, act)) {
+            warp_transpose_sum16(v);
+            const int k = lane >> 1;
+            if (!(lane & 1) && k < NV && v[0] != 0.f) atomicAdd(&s_acc[j * NV + k], v[0]);
+          }
         }
       }
     }
