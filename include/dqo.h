@@ -228,6 +228,28 @@ DQO_API int64_t dqo_launch_count(const dqo_ctx* ctx);
 /* Sizes of the last forward: tile-Gaussian pairs M, visible Gaussians, tiles. */
 DQO_API dqo_status dqo_get_counts(const dqo_ctx* ctx, int64_t* n_pairs, int64_t* n_visible, int32_t* n_tiles);
 
+/* ------------------------------------------------------------------ allocation-free depth order */
+
+/* Stable ascending sort of Gaussian indices by 32-bit depth keys, allocating nothing.
+ * The paper has no counterpart: this is a library service for callers that cannot call
+ * cudaMalloc while they run -- a real-time loop that must not take the implicit device
+ * synchronisation of an allocation, a plugin whose host framework owns all device
+ * memory, or a deployment with a fixed memory budget.  It runs the depth radix sort of
+ * dqo_render_forward (DQO_BUF_DEPTH_ORDER) on keys the caller supplies.
+ *   depth_keys [n] (device, read only): the float bit pattern of each Gaussian's positive
+ *     camera depth, or 0xFFFFFFFF for a culled Gaussian (any uint32 keys sort correctly);
+ *   order [n] (device, written): indices 0..n-1 ordered by (key, index).
+ * Scratch memory is a fixed array of about 12.3 MiB inside the library, held by every GPU
+ * that loads the library until the process exits.  n may be 0 .. 1048576 (2^20);
+ * larger n returns DQO_EINVAL, as do NULL arrays with n > 0.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) for that device; make that
+ * first call before any stream capture.  No call allocates device or host memory.  All
+ * calls share the one scratch array, which keeps the previous call's contents: calls
+ * that overlap on the GPU race and must be serialised by the caller (for example by
+ * issuing them on one stream).  Asynchronous on `stream`; DQO_ECUDA on a CUDA failure. */
+DQO_API dqo_status dqo_depth_order_noalloc(const uint32_t* depth_keys, int64_t n, uint32_t* order,
+                                           dqo_stream stream);
+
 /* ------------------------------------------------------------------ dual quadrics */
 
 /* Projects dual quadrics into views (Eq. 1-4; reading C* = P Q* P^T).

@@ -73,6 +73,7 @@ _SIGS = {
     "dqo_set_timing": (c_i32, [c_p, C.c_int]),
     "dqo_get_timings": (c_i32, [c_p, c_p, c_i32]),
     "dqo_launch_count": (c_i64, [c_p]),
+    "dqo_depth_order_noalloc": (c_i32, [c_p, c_i64, c_p, c_p]),
     "dqo_quadric_project": (c_i32, [c_p, c_i32, c_p, c_i32, c_p, c_p, c_p, c_i32, c_p, c_p, c_p, c_p]),
     "dqo_quadric_bbox_loss": (c_i32, [c_p, c_i32, c_p, c_i32, c_p, c_p, c_p, c_i32, c_p, c_p, c_p, c_p]),
 }
@@ -289,6 +290,18 @@ def dqo_get_timings(ctx: Context) -> dict:
 
 def dqo_launch_count(ctx: Context) -> int:
     return int(load().dqo_launch_count(ctx.handle))
+
+
+def dqo_depth_order_noalloc(depth_keys: torch.Tensor, order: torch.Tensor, stream=None):
+    """Depth order without any device allocation (scratch lives in the library); see
+    include/dqo.h.  depth_keys: uint32 bit patterns as an int32 CUDA tensor [n]; order:
+    int32 CUDA tensor [n] receiving the sorted indices."""
+    if depth_keys.dtype != torch.int32 or order.dtype != torch.int32:
+        raise ValueError("depth_keys and order must be int32 tensors (uint32 bit patterns)")
+    if order.numel() != depth_keys.numel():
+        raise ValueError("order must have as many elements as depth_keys")
+    _check("dqo_depth_order_noalloc",
+           load().dqo_depth_order_noalloc(_ptr(depth_keys), depth_keys.numel(), _ptr(order), _stream(stream)))
 
 
 def dqo_quadric_project(ctx: Context, params, P, q_ptr, pair_v, conic=None, bbox=None, valid=None, stream=None):
