@@ -69,7 +69,8 @@ typedef struct {
   float lambda_ins;       /* lambda of Eq. 10                                        (1)     */
   float bg[3];            /* background colour                                       (0,0,0) */
   int32_t og_filter;      /* 1: only opaque (OG) Gaussians count toward ins, Eq. 15  (1)     */
-  int32_t batch;          /* Gaussians staged per shared-memory batch: 64..256, multiple of 32 (256) */
+  int32_t batch;          /* reserved: checked (32..256, multiple of 32) but unused -- every warp of the
+                             blend kernels stages its own 32-Gaussian chunks                   (256) */
 } dqo_settings;
 
 typedef struct {

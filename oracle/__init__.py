@@ -57,7 +57,7 @@ def _lib_handle():
             lib.oracle_preprocess.argtypes = [_P, _P, i64] + [_P] * 12
             lib.oracle_render.argtypes = [_P, _P, i64] + [_P] * 10 + [C.c_int] + [_P] * 11
             lib.oracle_render_pixels.argtypes = [_P, _P, i64] + [_P] * 8 + [i64] + [_P] * 10
-            lib.oracle_render_backward.argtypes = [_P, _P, i64] + [_P] * 18
+            lib.oracle_render_backward.argtypes = [_P, _P, i64] + [_P] * 19
             lib.oracle_bin_tiles.argtypes = [i64, _P, _P, _P, C.c_int, C.c_int, _P, _P]
             lib.oracle_bin_tiles.restype = i64
             lib.oracle_quadric_project.argtypes = [C.c_int, _P, C.c_int, _P, _P, _P, _P, _P, _P]
@@ -180,7 +180,9 @@ def render_pixels(g: dict, cam: dict, pxy, st: OSettings | None = None, gt_id=No
 def render_backward(g: dict, cam: dict, st: OSettings | None = None, targets: dict | None = None,
                     dl=None) -> dict:
     """Adjoint of the render ("back propagation", Sec. IV impl.).  dl[H,W,6] = upstream
-    (dC rgb, dD, dA, dins); if None, the fused L1 losses against the targets are used."""
+    (dC rgb, dD, dA, dins); if None, the fused L1 losses against the targets are used.
+    out["unc"][param] bounds how far a correct single-precision evaluation may differ
+    because of decisions within rounding distance of their thresholds."""
     st = st or settings()
     m, s, q, o, c, i, f = _gauss(g)
     n = m.shape[0]
@@ -188,14 +190,17 @@ def render_backward(g: dict, cam: dict, st: OSettings | None = None, targets: di
     dl = None if dl is None else _d(dl)
     out = dict(g2=np.zeros((n, 10)), means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)),
                quats=np.zeros((n, 4)), opacity_logit=np.zeros(n), rgb=np.zeros((n, 3)),
-               amb=np.zeros(n, np.uint8))
+               amb=np.zeros(n, np.uint8), unc_all=np.zeros((n, 14)))
     oc = camera(cam)
     rc = _lib_handle().oracle_render_backward(C.byref(st), C.byref(oc), n, _ptr(m), _ptr(s), _ptr(q), _ptr(o),
                                               _ptr(c), _ptr(i), _ptr(f), _ptr(tr), _ptr(td), _ptr(tg), _ptr(dl),
                                               *[_ptr(out[k]) for k in ("g2", "means", "log_scales", "quats",
-                                                                       "opacity_logit", "rgb", "amb")])
+                                                                       "opacity_logit", "rgb", "amb", "unc_all")])
     if rc:
         raise ValueError("oracle_render_backward: invalid arguments")
+    u = out.pop("unc_all")
+    out["unc"] = dict(means=u[:, 0:3], log_scales=u[:, 3:6], quats=u[:, 6:10], opacity_logit=u[:, 10],
+                      rgb=u[:, 11:14])
     return out
 
 

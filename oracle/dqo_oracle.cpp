@@ -20,7 +20,8 @@
 //   Gaussian: p_c = R_view mean + t_view; Sigma = R(q) diag(exp(2 s)) R(q)^T (q normalised);
 //   Sigma' = J W Sigma W^T J^T + lowpass I; conic = Sigma'^-1; radius = ceil(k sqrt(lmax)).
 //   Tile membership: tile contains a pixel centre inside [x-r, x+r] x [y-r, y+r].
-//   Per pixel: tile's Gaussians sorted by (z, index); alpha = min(clamp, o exp(power));
+//   Per pixel: tile's Gaussians sorted by (float bit pattern of z, index), the 3DGS depth
+//   key; alpha = min(clamp, o exp(power));
 //   skip alpha < alpha_min; stop before the Gaussian that would make T(1-alpha) < t_stop.
 //   C = sum w c + T_final bg; D = sum w z; A = sum w; ins = sum over Gaussians of the
 //   pixel's labelled object (opaque ones if og_filter) of w; id = argmax_k W_k.
@@ -40,7 +41,9 @@
 // differences of every gradient.
 
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <map>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -231,15 +234,27 @@ bool covers(const int rect[4], int tx, int ty) {
     return tx >= rect[0] && tx < rect[2] && ty >= rect[1] && ty < rect[3];
 }
 
-// Gaussians whose rect covers tile (tx,ty), in ascending (z, index) order.
+// Depth-sort key: the single-precision bit pattern of the camera depth (3DGS sorts its
+// tile lists by float depth keys), rounded once from the exact double value; ties by index.
+uint32_t depth_key(double z) {
+    const float f = (float)z;
+    uint32_t u;
+    std::memcpy(&u, &f, sizeof u);
+    return u;
+}
+
+bool depth_less(const std::vector<Proj>& pr, int64_t a, int64_t b) {
+    const uint32_t ka = depth_key(pr[a].pc[2]), kb = depth_key(pr[b].pc[2]);
+    if (ka != kb) return ka < kb;
+    return a < b;
+}
+
+// Gaussians whose rect covers tile (tx,ty), in ascending (depth key, index) order.
 std::vector<int64_t> tile_list(const std::vector<Proj>& pr, int tx, int ty) {
     std::vector<int64_t> L;
     for (int64_t i = 0; i < (int64_t)pr.size(); ++i)
         if (pr[i].visible && covers(pr[i].rect, tx, ty)) L.push_back(i);
-    std::stable_sort(L.begin(), L.end(), [&](int64_t a, int64_t b) {
-        if (pr[a].pc[2] != pr[b].pc[2]) return pr[a].pc[2] < pr[b].pc[2];
-        return a < b;
-    });
+    std::stable_sort(L.begin(), L.end(), [&](int64_t a, int64_t b) { return depth_less(pr, a, b); });
     return L;
 }
 
@@ -257,23 +272,29 @@ struct PixelResult {
     int64_t n_contrib = 0;  // 1 + list position of the last blended Gaussian
     int32_t id = -1;
     double id_margin = 0;
-    uint8_t amb = 0;        // bit0 threshold, bit1 depth tie, bit2 tile membership, bit3 loss kink
+    uint8_t amb = 0;        // bit0 threshold, bit2 tile membership, bit3 loss kink
     int64_t amb_pos = -1;   // first list position with a threshold decision near its threshold
+    int amb_kind = 0;       // which decision there: 1 alpha_min skip, 2 clamp, 3 stop
+    std::vector<std::pair<int64_t, int>> near;  // every (position, kind) near its threshold
     int64_t stop_pos = -1;  // list position where the walk stopped (-1: ran to the end)
     std::vector<int64_t> amb_rect;  // Gaussians whose uncertain tile membership matters here
     std::vector<Contrib> contribs;
 };
 
-const uint8_t AMB_THRESH = 1, AMB_DEPTH = 2, AMB_RECT = 4, AMB_KINK = 8;
+const uint8_t AMB_THRESH = 1, AMB_RECT = 4, AMB_KINK = 8;
+const int FLIP_SKIP = 1, FLIP_CLAMP = 2, FLIP_STOP = 3;
 
 bool near_rel(double a, double b, double rel) { return std::fabs(a - b) <= rel * std::fabs(b); }
 
+// Front-to-back blend of one pixel over the tile list L.  flip_pos / flip_kind invert one
+// decision (used to measure how much a decision near its threshold matters).
 PixelResult blend_pixel(const OSettings& st, const Inputs& in, const std::vector<Proj>& pr,
-                        const std::vector<int64_t>& L, int px, int py, int32_t gt, bool keep) {
+                        const std::vector<int64_t>& L, int px, int py, int32_t gt, bool keep,
+                        int64_t flip_pos = -1, int flip_kind = 0) {
     PixelResult R;
     std::vector<double> Wk(st.num_objects > 0 ? st.num_objects : 0, 0.0);
     double T = 1.0;
-    double last_z = -1;
+    double eT = 0;  // relative error a single-precision evaluation may have accumulated in T
     for (size_t j = 0; j < L.size(); ++j) {
         const int64_t g = L[j];
         const Proj& P = pr[g];
@@ -282,25 +303,32 @@ PixelResult blend_pixel(const OSettings& st, const Inputs& in, const std::vector
         if (power > 0) continue;
         const double G = std::exp(power);
         const double oG = P.opac * G;
+        // Single precision stores the pixel-space mean rounded to half an ulp; the
+        // exponent then moves by |grad| * ulp / 2 and alpha by that much relatively.
+        const double ulpx = std::ldexp(1.0, std::ilogb(std::fabs(P.xy[0]) + 1.0) - 23);
+        const double ulpy = std::ldexp(1.0, std::ilogb(std::fabs(P.xy[1]) + 1.0) - 23);
+        const double ea = 0.5 * (std::fabs(P.conic[0] * dx + P.conic[1] * dy) * ulpx +
+                                 std::fabs(P.conic[1] * dx + P.conic[2] * dy) * ulpy) + 1e-6;
+        const double marg = std::max(st.amb_rel, 4 * ea);
+        const bool flip = (int64_t)j == flip_pos;
         bool clamped = oG > st.alpha_clamp;
+        if (flip && flip_kind == FLIP_CLAMP) clamped = !clamped;
         const double alpha = clamped ? st.alpha_clamp : oG;
-        const bool amb_a = near_rel(oG, st.alpha_clamp, st.amb_rel) || near_rel(alpha, st.alpha_min, st.amb_rel);
-        if (amb_a) {
+        auto mark = [&](int kind) {
             R.amb |= AMB_THRESH;
-            if (R.amb_pos < 0) R.amb_pos = (int64_t)j;
-        }
-        if (alpha < st.alpha_min) continue;
+            if (R.amb_pos < 0) { R.amb_pos = (int64_t)j; R.amb_kind = kind; }
+            R.near.push_back({(int64_t)j, kind});
+        };
+        if (near_rel(oG, st.alpha_clamp, marg)) mark(FLIP_CLAMP);
+        else if (near_rel(alpha, st.alpha_min, marg)) mark(FLIP_SKIP);
+        if ((alpha < st.alpha_min) != (flip && flip_kind == FLIP_SKIP)) continue;
         const double Tn = T * (1 - alpha);
-        if (near_rel(Tn, st.t_stop, st.amb_rel)) {
-            R.amb |= AMB_THRESH;
-            if (R.amb_pos < 0) R.amb_pos = (int64_t)j;
-        }
-        if (Tn < st.t_stop) {
+        eT += (clamped ? 0.0 : alpha * ea / (1 - alpha)) + 1e-7;
+        if (near_rel(Tn, st.t_stop, std::max(st.amb_rel, 4 * eT))) mark(FLIP_STOP);
+        if ((Tn < st.t_stop) != (flip && flip_kind == FLIP_STOP)) {
             R.stop_pos = (int64_t)j;
             break;
         }
-        if (last_z >= 0 && std::fabs(P.pc[2] - last_z) <= 1e-6 * P.pc[2]) R.amb |= AMB_DEPTH;
-        last_z = P.pc[2];
         const double w = alpha * T;
         for (int c = 0; c < 3; ++c) R.C[c] += w * in.rgb[3 * g + c];
         R.D += w * P.pc[2];
@@ -340,13 +368,13 @@ void pixel_loss(const OSettings& st, const PixelResult& R, const double* trgb, d
         const double e = R.C[c] - trgb[c];
         loss[0] += std::fabs(e) * inv_hw;
         g.dC[c] = sgn(e) * inv_hw;
-        if (e != 0 && std::fabs(e) < 1e-5) amb |= AMB_KINK;
+        if (e != 0 && std::fabs(e) < 1e-4) amb |= AMB_KINK;
     }
     if (tdepth > 0) {
         const double e = R.D - tdepth;
         loss[1] += std::fabs(e) * inv_hw;
         g.dD = sgn(e) * inv_hw;
-        if (e != 0 && std::fabs(e) < 1e-5) amb |= AMB_KINK;
+        if (e != 0 && std::fabs(e) < 1e-4) amb |= AMB_KINK;
     }
     const double e = R.ins - 1.0;
     loss[2] += std::fabs(e) * inv_hw;
@@ -357,8 +385,10 @@ void pixel_loss(const OSettings& st, const PixelResult& R, const double* trgb, d
 const int G2 = 10;
 
 // Adjoint of one pixel's blend (plain definition: C = sum c_j a_j T_j + T_N bg, etc.).
+// acc(g) returns the 10-entry record of Gaussian g to add into.
+template <class Acc>
 void pixel_backward(const OSettings& st, const Inputs& in, const std::vector<Proj>& pr,
-                    const PixelResult& R, const PixelGrad& pg, int32_t gt, double* g2) {
+                    const PixelResult& R, const PixelGrad& pg, int32_t gt, Acc acc) {
     const size_t n = R.contribs.size();
     // suffix sums of w_k * (upstream . value_k) behind each contributor, plus the background
     double behind = R.T * (pg.dC[0] * st.bg[0] + pg.dC[1] * st.bg[1] + pg.dC[2] * st.bg[2]);
@@ -374,7 +404,7 @@ void pixel_backward(const OSettings& st, const Inputs& in, const std::vector<Pro
         // dL/dalpha_j = T_j U_j - (sum_{k>j} w_k U_k + T_N bg.dC) / (1 - alpha_j)
         const double dalpha = c.T * U - behind / (1 - c.alpha);
         behind += w * U;
-        double* o = g2 + G2 * g;
+        double* o = acc(g);
         for (int ch = 0; ch < 3; ++ch) o[6 + ch] += w * pg.dC[ch];
         o[9] += w * pg.dD;
         if (c.clamped) continue;
@@ -550,7 +580,7 @@ int oracle_preprocess(const OSettings* st, const OCamera* cam, int64_t n, const 
 }
 
 // Full render.  mode 0: per-tile sorted lists; mode 1: per-pixel brute force over all
-// Gaussians in (z, index) order.  Targets may be NULL (then no loss / pixel gradients).
+// Gaussians in (depth key, index) order.  Targets may be NULL (then no loss / pixel gradients).
 // Outputs (each may be NULL): rgb[H*W*3], depth, alpha, ins, id_map, T_final, n_contrib,
 // amb[H*W] (flag bits), id_margin[H*W], loss[4] (rgb, depth, ins, total),
 // dl[H*W*6] (dC r,g,b, dD, dA, dins).
@@ -570,10 +600,7 @@ int oracle_render(const OSettings* st, const OCamera* cam, int64_t n, const doub
     std::vector<int64_t> all;
     if (mode == 1) {
         for (int64_t i = 0; i < n; ++i) all.push_back(i);
-        std::stable_sort(all.begin(), all.end(), [&](int64_t a, int64_t b) {
-            if (pr[a].pc[2] != pr[b].pc[2]) return pr[a].pc[2] < pr[b].pc[2];
-            return a < b;
-        });
+        std::stable_sort(all.begin(), all.end(), [&](int64_t a, int64_t b) { return depth_less(pr, a, b); });
     }
     double loss[3] = {0, 0, 0};
     const double inv_hw = 1.0 / ((double)W * H);
@@ -653,13 +680,18 @@ int oracle_render_pixels(const OSettings* st, const OCamera* cam, int64_t n, con
 // Backward of the render.  Pixel gradients: if dl (H*W*6 = dC rgb, dD, dA, dins) is NULL the
 // fused L1 losses against the targets are differentiated.  Outputs (accumulated +=, each may be
 // NULL): g2[n*10] (dxy, dconic a b c, dopac, drgb, dz), and parameter gradients.
-// Gaussians touching a flagged pixel are reported in g_amb[n] (bit0 threshold/tile, bit3 kink).
+// g_amb[n]: bit0 the Gaussian's alpha decision is near a threshold somewhere, bit2 its tile
+// membership is uncertain somewhere, bit3 it feeds a pixel at an L1 kink.
+// unc[n*14]: per parameter (means, log_scales, quats, logit, rgb) the summed absolute change
+// of the gradient when each near-threshold decision or uncertain membership is taken the
+// other way, pixel by pixel -- the amount by which a correct single-precision evaluation
+// may differ from this one beyond rounding.
 int oracle_render_backward(const OSettings* st, const OCamera* cam, int64_t n, const double* means,
                            const double* log_scales, const double* quats, const double* opacity_logit,
                            const double* rgb, const int32_t* obj_id, const uint8_t* flags,
                            const double* t_rgb, const double* t_depth, const int32_t* t_gt,
                            const double* dl, double* g2_out, double* d_means, double* d_log_scales,
-                           double* d_quats, double* d_logit, double* d_rgb, uint8_t* g_amb) {
+                           double* d_quats, double* d_logit, double* d_rgb, uint8_t* g_amb, double* unc) {
     const Inputs in = make_inputs(n, means, log_scales, quats, opacity_logit, rgb, obj_id, flags);
     const int W = cam->width, H = cam->height;
     if (W <= 0 || H <= 0) return 1;
@@ -668,6 +700,39 @@ int oracle_render_backward(const OSettings* st, const OCamera* cam, int64_t n, c
     const std::vector<std::vector<int64_t>> tile_amb = rect_ambiguity(pr, ntx, nty);
     std::vector<double> g2((size_t)n * G2, 0.0);
     const double inv_hw = 1.0 / ((double)W * H);
+    auto dense = [&](int64_t g) { return g2.data() + G2 * g; };
+    using Sparse = std::map<int64_t, std::array<double, G2>>;
+    auto sparse_acc = [](Sparse& m) {
+        return [&m](int64_t g) {
+            auto it = m.find(g);
+            if (it == m.end()) it = m.emplace(g, std::array<double, G2>{}).first;
+            return it->second.data();
+        };
+    };
+    // unc[14 i ..] += |parameter-gradient change| of Gaussian i if FP32 took the other
+    // side of a decision near its threshold at some pixel (means 3, log_scales 3, quats 4,
+    // opacity logit 1, rgb 3).
+    auto add_uncertainty = [&](const Sparse& m0, const Sparse& m1) {
+        Sparse keys = m0;
+        for (const auto& kv : m1) keys.emplace(kv.first, std::array<double, G2>{});
+        for (const auto& kv : keys) {
+            const int64_t g = kv.first;
+            const Proj& P = pr[g];
+            if (P.conic[0] == 0) continue;  // culled before projection: no gradient either way
+            std::array<double, G2> d{};
+            auto i0 = m0.find(g), i1 = m1.find(g);
+            for (int k = 0; k < G2; ++k)
+                d[k] = (i1 != m1.end() ? i1->second[k] : 0.0) - (i0 != m0.end() ? i0->second[k] : 0.0);
+            double dm[3] = {0, 0, 0}, ds[3] = {0, 0, 0}, dq[4] = {0, 0, 0, 0}, dlg = 0, dc[3] = {0, 0, 0};
+            preprocess_backward(*st, *cam, P, opacity_logit[g], d.data(), dm, ds, dq, &dlg, dc);
+            double* u = unc + 14 * g;
+            for (int k = 0; k < 3; ++k) u[k] += std::fabs(dm[k]);
+            for (int k = 0; k < 3; ++k) u[3 + k] += std::fabs(ds[k]);
+            for (int k = 0; k < 4; ++k) u[6 + k] += std::fabs(dq[k]);
+            u[10] += std::fabs(dlg);
+            for (int k = 0; k < 3; ++k) u[11 + k] += std::fabs(dc[k]);
+        }
+    };
     for (int ty = 0; ty < nty; ++ty)
         for (int tx = 0; tx < ntx; ++tx) {
             std::vector<int64_t> L = tile_list(pr, tx, ty);
@@ -685,29 +750,41 @@ int oracle_render_backward(const OSettings* st, const OCamera* cam, int64_t n, c
                         double loss[3] = {0, 0, 0};
                         pixel_loss(*st, R, t_rgb + 3 * p, t_depth ? t_depth[p] : 0.0, gt, inv_hw, loss, pg, R.amb);
                     }
-                    pixel_backward(*st, in, pr, R, pg, gt, g2.data());
-                    if (g_amb && R.amb) {
-                        // Gaussians whose gradient may change with the uncertain decision:
-                        // a threshold at list position j affects L[j..]; a depth tie, an
-                        // uncertain tile membership or an L1 kink affect every contributor
-                        // (and the uncertain member itself).
-                        if (R.amb & AMB_THRESH) {
-                            g_amb[L[(size_t)R.amb_pos]] |= 1;
-                            for (const Contrib& c : R.contribs)
-                                if (c.pos >= (size_t)R.amb_pos) g_amb[c.g] |= 1;
-                            // past an uncertain stop, Gaussians that reach alpha_min here may join
-                            if (R.stop_pos >= R.amb_pos) {
-                                std::vector<int64_t> tail(L.begin() + R.stop_pos, L.end());
-                                PixelResult T2;
-                                rect_check(*st, pr, tail, px, py, T2);
-                                for (int64_t g : T2.amb_rect) g_amb[g] |= 1;
-                            }
+                    pixel_backward(*st, in, pr, R, pg, gt, dense);
+                    if (g_amb && (R.amb & AMB_KINK))
+                        for (const Contrib& c : R.contribs) g_amb[c.g] |= AMB_KINK;
+                    if (unc && (R.amb & (AMB_THRESH | AMB_RECT))) {
+                        Sparse m0;
+                        pixel_backward(*st, in, pr, R, pg, gt, sparse_acc(m0));
+                        for (const auto& nk : R.near) {
+                            // the same pixel with one near-threshold decision taken the other way
+                            PixelResult R1 = blend_pixel(*st, in, pr, L, px, py, gt, true, nk.first, nk.second);
+                            Sparse m1;
+                            pixel_backward(*st, in, pr, R1, pg, gt, sparse_acc(m1));
+                            add_uncertainty(m0, m1);
+                            if (g_amb) g_amb[L[(size_t)nk.first]] |= AMB_THRESH;
                         }
-                        if (R.amb & (AMB_DEPTH | AMB_RECT | AMB_KINK)) {
-                            const uint8_t b = (R.amb & (AMB_DEPTH | AMB_RECT)) ? 1 : 0;
-                            const uint8_t kb = (R.amb & AMB_KINK) ? 8 : 0;
-                            for (const Contrib& c : R.contribs) g_amb[c.g] |= (uint8_t)(b | kb);
-                            for (int64_t g : R.amb_rect) g_amb[g] |= 1;
+                        std::vector<int64_t> cand = R.amb_rect;
+                        std::sort(cand.begin(), cand.end());
+                        cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+                        for (int64_t ga : cand) {
+                            // the same pixel with ga's tile membership toggled
+                            std::vector<int64_t> L1;
+                            bool had = false;
+                            for (int64_t g : L) {
+                                if (g == ga) { had = true; continue; }
+                                L1.push_back(g);
+                            }
+                            if (!had) {
+                                L1.push_back(ga);
+                                std::stable_sort(L1.begin(), L1.end(),
+                                                 [&](int64_t a, int64_t b) { return depth_less(pr, a, b); });
+                            }
+                            PixelResult R1 = blend_pixel(*st, in, pr, L1, px, py, gt, true);
+                            Sparse m1;
+                            pixel_backward(*st, in, pr, R1, pg, gt, sparse_acc(m1));
+                            add_uncertainty(m0, m1);
+                            if (g_amb) g_amb[ga] |= AMB_RECT;
                         }
                     }
                 }

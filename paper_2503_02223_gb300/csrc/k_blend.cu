@@ -27,7 +27,6 @@
 namespace dqo {
 namespace {
 
-constexpr int kMaxBatch = 256;
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 
 template <int TW>
@@ -72,8 +71,10 @@ __device__ __forceinline__ void slot_ids_for_round(const uint32_t* s_mask, const
 
 template <int TW, bool kId>
 __global__ void __launch_bounds__(kThreads) k_blend_forward(BlendFwdArgs a) {
-  __shared__ float4 s_p0[kMaxBatch], s_p1[kMaxBatch], s_p2[kMaxBatch], s_box[kMaxBatch];
-  __shared__ int32_t s_slot[kId ? kMaxBatch : 1];
+  constexpr int NW = kThreads / 32;
+  // per-warp staging of the Gaussians that can reach the warp's pixels
+  __shared__ float4 s_q0[NW][32], s_q1[NW][32], s_q2[NW][32];
+  __shared__ int32_t s_pos[NW][32], s_wslot[kId ? NW : 1][32];
   __shared__ uint32_t s_mask[kId ? kMaskWords : 1], s_pref[kId ? kMaskWords : 1];
   __shared__ int32_t s_slot_id[kIdSlots];
   __shared__ float s_W[kId ? kIdSlots : 1][kThreads];
@@ -90,8 +91,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_forward(BlendFwdArgs a) {
   const int64_t pix = (int64_t)py * rp.W + px;
   const uint2 rg = a.ranges[tile];
   const int start = (int)rg.x, end = rg.y > rg.x ? (int)rg.y : (int)rg.x;
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int B = rp.batch;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   int32_t gt = -1;
   if (inside && a.t_gt) gt = a.t_gt[pix];
@@ -137,75 +137,84 @@ __global__ void __launch_bounds__(kThreads) k_blend_forward(BlendFwdArgs a) {
   int cur_slot = -1;
   float cur_w = 0.f;
   const float fpx = (float)px, fpy = (float)py;
+  const uint32_t lt = lanemask_lt();
 
-  for (int b0 = start; b0 < end; b0 += B) {
-    if (__syncthreads_count(!done) == 0) break;
-    const int nb = min(B, end - b0);
-    if (tid < nb) {
-      const uint32_t g = a.list[b0 + tid];
-      const float4 q0 = a.p0[g], q1 = a.p1[g], q2 = a.p2[g];
-      s_p0[tid] = q0;
-      s_p1[tid] = q1;
-      s_p2[tid] = q2;
-      s_box[tid] = support_box(q0, q2);
+  // Dense slot of an object id in this tile's ascending-id slot map (-1: no object).
+  auto slot_of = [&](uint32_t idbits) -> int {
+    const uint32_t id = idbits & kNoObject;
+    if (id == kNoObject) return -1;
+    return (int)(s_pref[id >> 5] + __popc(s_mask[id >> 5] & ((1u << (id & 31)) - 1u)));
+  };
+  // Stages, in list order, the Gaussians of list chunk [c, c+32) that can reach this warp's
+  // pixels and sit before list position `lim`; returns how many.
+  auto stage = [&](int c, int lim) -> int {
+    const int i = c + lane;
+    bool hit = false;
+    float4 q0, q2;
+    uint32_t g = 0;
+    if (i < lim) {
+      g = a.list[i];
+      q0 = a.p0[g];
+      q2 = a.p2[g];
+      hit = box_hits(support_box(q0, q2), wx0, wy0);
+    }
+    const uint32_t m = __ballot_sync(kFull, hit);
+    if (hit) {
+      const int k = __popc(m & lt);
+      const float4 q1 = a.p1[g];
+      s_q0[warp][k] = q0;
+      s_q1[warp][k] = q1;
+      s_q2[warp][k] = q2;
+      s_pos[warp][k] = i - start;
+      if (kId) s_wslot[warp][k] = slot_of(__float_as_uint(q1.w));
+    }
+    __syncwarp();
+    return __popc(m);
+  };
+
+  // ---- front to back, each warp on its own: no block-wide barrier inside the walk
+  for (int c = start; c < end; c += 32) {
+    if (__all_sync(kFull, done)) break;
+    const int nh = stage(c, end);
+    for (int h = 0; h < nh; ++h) {
+      if (done) continue;
+      const float4 q0 = s_q0[warp][h], q1 = s_q1[warp][h];
+      float alpha, G, dx, dy;
+      if (!eval_gaussian(q0, q1, fpx, fpy, rp.alpha_clamp, rp.alpha_min, alpha, G, dx, dy)) continue;
+      const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
+      if (Tn < rp.t_stop) {
+        done = true;
+        continue;
+      }
+      const float w = __fmul_rn(alpha, T);
+      const float4 q2 = s_q2[warp][h];
+      C0 = fmaf(w, q2.x, C0);
+      C1 = fmaf(w, q2.y, C1);
+      C2 = fmaf(w, q2.z, C2);
+      D = fmaf(w, q1.z, D);
+      const uint32_t idog = __float_as_uint(q1.w);
+      if ((idog & kNoObject) == gt_match && (!rp.og_filter || (idog >> 31))) ins += w;
       if (kId) {
-        const uint32_t id = __float_as_uint(q1.w) & kNoObject;
-        int slot = -1;
-        if (id != kNoObject) {
-          const uint32_t w = s_mask[id >> 5];
-          slot = (int)(s_pref[id >> 5] + __popc(w & ((1u << (id & 31)) - 1u)));
+        const int slot = s_wslot[warp][h];
+        if (slot == cur_slot) {
+          cur_w += w;
+        } else {
+          if (cur_slot >= 0 && cur_slot < kIdSlots) s_W[cur_slot][tid] += cur_w;
+          cur_slot = slot;
+          cur_w = w;
         }
-        s_slot[tid] = slot;
       }
+      T = Tn;
+      last = s_pos[warp][h] + 1;
     }
-    __syncthreads();
-    if (__all_sync(kFull, done)) continue;
-    // walk only the Gaussians whose alpha-support box meets this warp's pixels, in order
-    for (int c = 0; c < nb; c += 32) {
-      const int jl = c + lane;
-      const bool hit = jl < nb && box_hits(s_box[jl], wx0, wy0);
-      uint32_t m = __ballot_sync(kFull, hit);
-      while (m) {
-        const int j = c + __ffs(m) - 1;
-        m &= m - 1;
-        if (done) continue;
-        const float4 q0 = s_p0[j], q1 = s_p1[j];
-        float alpha, G, dx, dy;
-        if (!eval_gaussian(q0, q1, fpx, fpy, rp.alpha_clamp, rp.alpha_min, alpha, G, dx, dy)) continue;
-        const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
-        if (Tn < rp.t_stop) {
-          done = true;
-          continue;
-        }
-        const float w = __fmul_rn(alpha, T);
-        const float4 q2 = s_p2[j];
-        C0 = fmaf(w, q2.x, C0);
-        C1 = fmaf(w, q2.y, C1);
-        C2 = fmaf(w, q2.z, C2);
-        D = fmaf(w, q1.z, D);
-        const uint32_t idog = __float_as_uint(q1.w);
-        if ((idog & kNoObject) == gt_match && (!rp.og_filter || (idog >> 31))) ins += w;
-        if (kId) {
-          const int slot = s_slot[j];
-          if (slot == cur_slot) {
-            cur_w += w;
-          } else {
-            if (cur_slot >= 0 && cur_slot < kIdSlots) s_W[cur_slot][tid] += cur_w;
-            cur_slot = slot;
-            cur_w = w;
-          }
-        }
-        T = Tn;
-        last = b0 - start + j + 1;
-      }
-      if (__all_sync(kFull, done)) break;
-    }
+    __syncwarp();
   }
 
   // ---- object-id argmax (ties to the smaller id: slots are in ascending id order)
   int32_t best_id = -1;
   if (kId) {
     if (cur_slot >= 0 && cur_slot < kIdSlots) s_W[cur_slot][tid] += cur_w;
+    __syncthreads();  // slot ids of round 0 were written block-wide before the walk
     float best_w = 0.f;
     const int n0 = min(nslots, kIdSlots);
     for (int s = 0; s < n0; ++s) {
@@ -217,11 +226,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_forward(BlendFwdArgs a) {
     }
     // tiles with more than kIdSlots objects: re-walk the blended prefix once per extra round
     if (nslots > kIdSlots) {
-      if (tid == 0) s_nslots = 0;
-      __syncthreads();
-      atomicMax(&s_nslots, (uint32_t)last);
-      __syncthreads();
-      const int maxlast = (int)s_nslots;
+      const int wlast = (int)__reduce_max_sync(kFull, (uint32_t)last);
       for (int first = kIdSlots; first < nslots; first += kIdSlots) {
         __syncthreads();
         slot_ids_for_round(s_mask, s_pref, nw, first, s_slot_id);
@@ -229,29 +234,20 @@ __global__ void __launch_bounds__(kThreads) k_blend_forward(BlendFwdArgs a) {
         for (int s = 0; s < kIdSlots; ++s) s_W[s][tid] = 0.f;
         __syncthreads();
         float Tr = 1.f;
-        for (int b0 = start; b0 < start + maxlast; b0 += B) {
-          const int nb = min(B, start + maxlast - b0);
-          __syncthreads();
-          if (tid < nb) {
-            const uint32_t g = a.list[b0 + tid];
-            const float4 q1 = a.p1[g];
-            s_p0[tid] = a.p0[g];
-            s_p1[tid] = q1;
-            const uint32_t id = __float_as_uint(q1.w) & kNoObject;
-            int slot = -1;
-            if (id != kNoObject)
-              slot = (int)(s_pref[id >> 5] + __popc(s_mask[id >> 5] & ((1u << (id & 31)) - 1u)));
-            s_slot[tid] = slot;
-          }
-          __syncthreads();
-          for (int j = 0; j < nb && b0 - start + j < last; ++j) {
+        for (int c = start; c < start + wlast; c += 32) {
+          const int nh = stage(c, start + wlast);
+          for (int h = 0; h < nh; ++h) {
+            if (s_pos[warp][h] >= last) continue;
             float alpha, G, dx, dy;
-            if (!eval_gaussian(s_p0[j], s_p1[j], fpx, fpy, rp.alpha_clamp, rp.alpha_min, alpha, G, dx, dy)) continue;
+            if (!eval_gaussian(s_q0[warp][h], s_q1[warp][h], fpx, fpy, rp.alpha_clamp, rp.alpha_min, alpha, G,
+                               dx, dy))
+              continue;
             const float w = __fmul_rn(alpha, Tr);
             Tr = __fmul_rn(Tr, __fsub_rn(1.f, alpha));
-            const int s = s_slot[j] - first;
+            const int s = s_wslot[warp][h] - first;
             if (s >= 0 && s < kIdSlots) s_W[s][tid] += w;
           }
+          __syncwarp();
         }
         const int nr = min(nslots - first, kIdSlots);
         for (int s = 0; s < nr; ++s) {
@@ -397,11 +393,10 @@ __device__ __forceinline__ void warp_transpose_sum16(float v[16]) {
 
 template <int TW>
 __global__ void __launch_bounds__(kThreads) k_blend_backward(BlendBwdArgs a) {
-  constexpr int NV = 10;
-  __shared__ float4 s_p0[kMaxBatch], s_p1[kMaxBatch], s_p2[kMaxBatch], s_box[kMaxBatch];
-  __shared__ uint32_t s_g[kMaxBatch];
-  __shared__ float s_acc[kMaxBatch * NV];
-  __shared__ uint32_t s_maxn;
+  constexpr int NW = kThreads / 32;
+  __shared__ float4 s_q0[NW][32], s_q1[NW][32], s_q2[NW][32];
+  __shared__ uint32_t s_g[NW][32];
+  __shared__ int32_t s_pos[NW][32];
 
   const RasterParams& rp = a.rp;
   const int tile = blockIdx.x;
@@ -411,10 +406,8 @@ __global__ void __launch_bounds__(kThreads) k_blend_backward(BlendBwdArgs a) {
   pixel_of<TW>(tx * rp.tile_w, ty * rp.tile_h, px, py, wx0, wy0);
   const bool inside = px < rp.W && py < rp.H;
   const int64_t pix = (int64_t)py * rp.W + px;
-  const uint2 rg = a.ranges[tile];
-  const int start = (int)rg.x;
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int B = rp.batch;
+  const int start = (int)a.ranges[tile].x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   uint32_t nc = 0;
   float T = 1.f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gA = 0.f, gI = 0.f;
@@ -435,91 +428,82 @@ __global__ void __launch_bounds__(kThreads) k_blend_backward(BlendBwdArgs a) {
       if (gt >= 0 && gt < rp.num_objects) gt_match = (uint32_t)gt;
     }
   }
-  if (tid == 0) s_maxn = 0;
-  __syncthreads();
+  // each warp walks its own pixels' lists back to front: no block-wide barrier
   const int wmax = (int)__reduce_max_sync(kFull, nc);
-  if (lane == 0 && wmax) atomicMax(&s_maxn, (uint32_t)wmax);
-  __syncthreads();
-  const int maxn = (int)s_maxn;
   float R = T * (gC0 * rp.bg[0] + gC1 * rp.bg[1] + gC2 * rp.bg[2]);
   const float fpx = (float)px, fpy = (float)py;
+  const uint32_t lt = lanemask_lt();
+  // lanes 0..2 gather the butterfly's ten sums (held by lanes 0, 2, .., 18) as float4s
+  const int src0 = (lane < 3 ? 8 * lane : 0);
 
-  for (int hi = maxn; hi > 0; hi -= B) {
-    const int lo = max(0, hi - B);
-    const int nb = hi - lo;
-    if (tid < nb) {
-      const uint32_t g = a.list[start + lo + tid];
-      const float4 q0 = a.p0[g], q2 = a.p2[g];
-      s_g[tid] = g;
-      s_p0[tid] = q0;
-      s_p1[tid] = a.p1[g];
-      s_p2[tid] = q2;
-      s_box[tid] = support_box(q0, q2);
+  for (int c = (wmax - 1) & ~31; c >= 0 && wmax > 0; c -= 32) {
+    const int jl = c + lane;
+    bool hit = false;
+    float4 q0, q2;
+    uint32_t g = 0;
+    if (jl < wmax) {
+      g = a.list[start + jl];
+      q0 = a.p0[g];
+      q2 = a.p2[g];
+      hit = box_hits(support_box(q0, q2), wx0, wy0);
     }
-    for (int k = tid; k < nb * NV; k += kThreads) s_acc[k] = 0.f;
-    __syncthreads();
-    if (wmax > lo) {
-      // back to front over the Gaussians that can reach this warp's pixels
-      for (int c = (nb - 1) & ~31; c >= 0; c -= 32) {
-        const int jl = c + lane;
-        const bool hit = jl < nb && lo + jl < wmax && box_hits(s_box[jl], wx0, wy0);
-        uint32_t m = __ballot_sync(kFull, hit);
-        while (m) {
-          const int bit = 31 - __clz(m);
-          m &= ~(1u << bit);
-          const int j = c + bit;
-          float v[16];
+    const uint32_t m = __ballot_sync(kFull, hit);
+    if (hit) {
+      const int k = __popc(m & lt);
+      s_q0[warp][k] = q0;
+      s_q1[warp][k] = a.p1[g];
+      s_q2[warp][k] = q2;
+      s_g[warp][k] = g;
+      s_pos[warp][k] = jl;
+    }
+    __syncwarp();
+    for (int h = __popc(m) - 1; h >= 0; --h) {
+      float v[16];
 #pragma unroll
-          for (int k = 0; k < 16; ++k) v[k] = 0.f;
-          bool act = false;
-          if (lo + j < (int)nc) {
-            const float4 q0 = s_p0[j], q1 = s_p1[j];
-            float alpha, G, dx, dy;
-            if (eval_gaussian(q0, q1, fpx, fpy, rp.alpha_clamp, rp.alpha_min, alpha, G, dx, dy)) {
-              act = true;
-              const float inv = __frcp_rn(1.f - alpha);
-              T = T * inv;
-              const float w = alpha * T;
-              const float4 q2 = s_p2[j];
-              const uint32_t idog = __float_as_uint(q1.w);
-              const bool counts = (idog & kNoObject) == gt_match && (!rp.og_filter || (idog >> 31));
-              const float U = gC0 * q2.x + gC1 * q2.y + gC2 * q2.z + gD * q1.z + gA + (counts ? gI : 0.f);
-              const float dalpha = T * U - R * inv;
-              R = fmaf(w, U, R);
-              const bool clamped = __fmul_rn(q1.y, G) > rp.alpha_clamp;
-              const float dpow = clamped ? 0.f : dalpha * alpha;
-              v[0] = dpow * dx;
-              v[1] = dpow * dy;
-              v[2] = v[0] * dx;
-              v[3] = v[0] * dy;
-              v[4] = v[1] * dy;
-              v[5] = clamped ? 0.f : dalpha * G;
-              v[6] = w * gC0;
-              v[7] = w * gC1;
-              v[8] = w * gC2;
-              v[9] = w * gD;
-            }
-          }
-          if (__any_sync(kFull, act)) {
-            warp_transpose_sum16(v);
-            const int k = lane >> 1;
-            if (!(lane & 1) && k < NV && v[0] != 0.f) atomicAdd(&s_acc[j * NV + k], v[0]);
-          }
+      for (int k = 0; k < 16; ++k) v[k] = 0.f;
+      bool act = false;
+      if (s_pos[warp][h] < (int)nc) {
+        const float4 p0 = s_q0[warp][h], p1 = s_q1[warp][h];
+        float alpha, G, dx, dy;
+        if (eval_gaussian(p0, p1, fpx, fpy, rp.alpha_clamp, rp.alpha_min, alpha, G, dx, dy)) {
+          act = true;
+          const float inv = __frcp_rn(1.f - alpha);
+          T = T * inv;
+          const float w = alpha * T;
+          const float4 p2 = s_q2[warp][h];
+          const uint32_t idog = __float_as_uint(p1.w);
+          const bool counts = (idog & kNoObject) == gt_match && (!rp.og_filter || (idog >> 31));
+          const float U = gC0 * p2.x + gC1 * p2.y + gC2 * p2.z + gD * p1.z + gA + (counts ? gI : 0.f);
+          const float dalpha = T * U - R * inv;
+          R = fmaf(w, U, R);
+          const bool clamped = __fmul_rn(p1.y, G) > rp.alpha_clamp;
+          const float dpow = clamped ? 0.f : dalpha * alpha;
+          v[0] = dpow * dx;
+          v[1] = dpow * dy;
+          v[2] = v[0] * dx;
+          v[3] = v[0] * dy;
+          v[4] = v[1] * dy;
+          v[5] = clamped ? 0.f : dalpha * G;
+          v[6] = w * gC0;
+          v[7] = w * gC1;
+          v[8] = w * gC2;
+          v[9] = w * gD;
+        }
+      }
+      if (__any_sync(kFull, act)) {
+        warp_transpose_sum16(v);
+        // lane 2k holds sum k (k < 10; k = 10, 11 are zero): lane L < 3 collects 4L .. 4L+3
+        const float a0 = __shfl_sync(kFull, v[0], src0);
+        const float a1 = __shfl_sync(kFull, v[0], src0 + 2);
+        const float a2 = __shfl_sync(kFull, v[0], src0 + 4);
+        const float a3 = __shfl_sync(kFull, v[0], src0 + 6);
+        if (lane < 3) {
+          float4* dst = reinterpret_cast<float4*>(a.grad2d) + 3 * (int64_t)s_g[warp][h] + lane;
+          atomicAdd(dst, make_float4(a0, a1, a2, a3));
         }
       }
     }
-    __syncthreads();
-    if (tid < nb) {
-      const float* r = s_acc + tid * NV;
-      if (r[0] != 0.f || r[1] != 0.f || r[2] != 0.f || r[3] != 0.f || r[4] != 0.f || r[5] != 0.f ||
-          r[6] != 0.f || r[7] != 0.f || r[8] != 0.f || r[9] != 0.f) {
-        float4* dst = reinterpret_cast<float4*>(a.grad2d) + 3 * (int64_t)s_g[tid];
-        atomicAdd(dst + 0, make_float4(r[0], r[1], r[2], r[3]));
-        atomicAdd(dst + 1, make_float4(r[4], r[5], r[6], r[7]));
-        atomicAdd(dst + 2, make_float4(r[8], r[9], 0.f, 0.f));
-      }
-    }
-    __syncthreads();
+    __syncwarp();
   }
 }
 

@@ -45,9 +45,16 @@ __device__ __forceinline__ void footprint(const RasterParams& rp, const float me
   f.ntiles = 0;
   f.rect = make_ushort4(0, 0, 0, 0);
   const float* V = rp.vm;
+  // Camera-space mean in double, rounded once to float: products of two floats are exact
+  // in double, so z (the depth-sort key) is the correctly rounded depth of the float
+  // inputs, reproducible by any exact evaluation.
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
-    f.pc[i] = fmaf(V[4 * i + 0], mean[0], fmaf(V[4 * i + 1], mean[1], fmaf(V[4 * i + 2], mean[2], V[4 * i + 3])));
+  for (int i = 0; i < 3; ++i) {
+    double acc = __dmul_rn((double)V[4 * i + 0], (double)mean[0]);
+    acc = __dadd_rn(acc, __dmul_rn((double)V[4 * i + 1], (double)mean[1]));
+    acc = __dadd_rn(acc, __dmul_rn((double)V[4 * i + 2], (double)mean[2]));
+    f.pc[i] = __double2float_rn(__dadd_rn(acc, (double)V[4 * i + 3]));
+  }
   const float x = f.pc[0], y = f.pc[1], z = f.pc[2];
   f.opac = 1.f / (1.f + expf(-logit));
   if (!(z >= rp.znear)) return;
