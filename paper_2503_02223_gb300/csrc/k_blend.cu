@@ -20,8 +20,6 @@
 // summed over the warp by a transposing butterfly (16 shuffles), over the CTA with
 // shared-memory atomics, and added to the global per-Gaussian record with vector
 // atomics once per (tile, Gaussian).
-#include <cuda_fp16.h>
-
 #include "dqo_internal.cuh"
 
 namespace dqo {
@@ -42,16 +40,36 @@ __device__ __forceinline__ void pixel_of(int tile_x0, int tile_y0, int& px, int&
 
 __device__ __forceinline__ float sgnf(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
 
-// Box (x0, x1, y0, y1) of the pixels where a Gaussian's alpha can reach alpha_min, from its
-// centre (p0.xy) and the rounded-up half-extents stored as half2 in p2.w.
-__device__ __forceinline__ float4 support_box(const float4& p0, const float4& p2) {
-  const float2 e = __half22float2(*reinterpret_cast<const __half2*>(&p2.w));
-  return make_float4(p0.x - e.x, p0.x + e.x, p0.y - e.y, p0.y + e.y);
-}
-
-// Does the box meet the warp's 8x4 block of pixel centres [wx0, wx0+7] x [wy0, wy0+3]?
-__device__ __forceinline__ bool box_hits(const float4& b, float wx0, float wy0) {
-  return b.x <= wx0 + 7.f && b.y >= wx0 && b.z <= wy0 + 3.f && b.w >= wy0;
+// Can the Gaussian reach alpha_min at some pixel centre of the block [bx, bx + bw] x
+// [by, by + bh]?  f(d) = -(a' dx^2 + b' dx dy + c' dy^2) is a convex quadratic of d = p - mean;
+// its minimum over the rectangle is 0 if the mean lies inside, else the least of the
+// four edge minima (each a clamped 1D minimum).  Hit iff that minimum <= the level in p2.w.
+__device__ __forceinline__ bool ellipse_hits(const float4& p0, const float4& p1, const float4& p2, float bx,
+                                             float by, float bw, float bh) {
+  const float lvl = p2.w;
+  if (!(lvl >= 0.f)) return false;
+  const float A = -p0.z, B = -p0.w, C = -p1.x;
+  const float X0 = bx - p0.x, X1 = X0 + bw, Y0 = by - p0.y, Y1 = Y0 + bh;
+  if (X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f) return true;
+  const float hA = 0.5f / A, hC = 0.5f / C;
+  float m;
+  {
+    const float y = fminf(fmaxf(-B * X0 * hC, Y0), Y1);
+    m = (A * X0 + B * y) * X0 + C * y * y;
+  }
+  {
+    const float y = fminf(fmaxf(-B * X1 * hC, Y0), Y1);
+    m = fminf(m, (A * X1 + B * y) * X1 + C * y * y);
+  }
+  {
+    const float x = fminf(fmaxf(-B * Y0 * hA, X0), X1);
+    m = fminf(m, (A * x + B * Y0) * x + C * Y0 * Y0);
+  }
+  {
+    const float x = fminf(fmaxf(-B * Y1 * hA, X0), X1);
+    m = fminf(m, (A * x + B * Y1) * x + C * Y1 * Y1);
+  }
+  return m <= lvl;
 }
 
 // Fills s_slot_id[s - first] with the object id of dense slot s for s in [first, first+kIdSlots).
@@ -150,18 +168,17 @@ __global__ void __launch_bounds__(kThreads) k_blend_forward(BlendFwdArgs a) {
   auto stage = [&](int c, int lim) -> int {
     const int i = c + lane;
     bool hit = false;
-    float4 q0, q2;
-    uint32_t g = 0;
+    float4 q0, q1, q2;
     if (i < lim) {
-      g = a.list[i];
+      const uint32_t g = a.list[i];
       q0 = a.p0[g];
+      q1 = a.p1[g];
       q2 = a.p2[g];
-      hit = box_hits(support_box(q0, q2), wx0, wy0);
+      hit = ellipse_hits(q0, q1, q2, wx0, wy0, 7.f, 3.f);
     }
     const uint32_t m = __ballot_sync(kFull, hit);
     if (hit) {
       const int k = __popc(m & lt);
-      const float4 q1 = a.p1[g];
       s_q0[warp][k] = q0;
       s_q1[warp][k] = q1;
       s_q2[warp][k] = q2;
@@ -439,19 +456,20 @@ __global__ void __launch_bounds__(kThreads) k_blend_backward(BlendBwdArgs a) {
   for (int c = (wmax - 1) & ~31; c >= 0 && wmax > 0; c -= 32) {
     const int jl = c + lane;
     bool hit = false;
-    float4 q0, q2;
+    float4 q0, q1, q2;
     uint32_t g = 0;
     if (jl < wmax) {
       g = a.list[start + jl];
       q0 = a.p0[g];
+      q1 = a.p1[g];
       q2 = a.p2[g];
-      hit = box_hits(support_box(q0, q2), wx0, wy0);
+      hit = ellipse_hits(q0, q1, q2, wx0, wy0, 7.f, 3.f);
     }
     const uint32_t m = __ballot_sync(kFull, hit);
     if (hit) {
       const int k = __popc(m & lt);
       s_q0[warp][k] = q0;
-      s_q1[warp][k] = a.p1[g];
+      s_q1[warp][k] = q1;
       s_q2[warp][k] = q2;
       s_g[warp][k] = g;
       s_pos[warp][k] = jl;

@@ -10,8 +10,6 @@
 // K8 recomputes the same forward quantities and chains the per-Gaussian moment record
 // of the blend backward through the conic inverse, the EWA Jacobian, the scale/rotation
 // factorisation, quaternion normalisation and the sigmoid.
-#include <cuda_fp16.h>
-
 #include "dqo_internal.cuh"
 
 namespace dqo {
@@ -168,22 +166,20 @@ __global__ void __launch_bounds__(kThreads) k_preprocess(RasterParams rp, dqo_ga
     const float sc = -0.5f * kLog2e;
     o.p0[i] = make_float4(f.xy[0], f.xy[1], sc * f.conic[0], 2.f * sc * f.conic[1]);
     o.p1[i] = make_float4(sc * f.conic[2], f.opac, f.pc[2], __uint_as_float(idbits));
-    // Half-extents of the box holding every pixel where alpha can reach alpha_min:
-    // o exp(-q/2) >= alpha_min  <=>  q <= Q = 2 ln(o / alpha_min), and the ellipse q <= Q
-    // spans x +- sqrt(Q Sigma'_xx), y +- sqrt(Q Sigma'_yy).  Half 0.5 px of margin,
-    // rounded up to half precision; negative if the Gaussian can reach no pixel.
-    float hx = -1.f, hy = -1.f;
+    // Level of the alpha-support ellipse in the exponent's log2 units: alpha can reach
+    // alpha_min only where -(a' dx^2 + b' dx dy + c' dy^2) <= log2(o / alpha_min).  Widened
+    // by a small margin (the blend kernels cull with it, so it must be conservative);
+    // negative if the Gaussian can reach no pixel.
+    float lvl = -1.f;
     if (f.visible) {
       if (rp.alpha_min <= 0.f) {
-        hx = hy = INFINITY;
+        lvl = INFINITY;
       } else if (f.opac > rp.alpha_min) {
-        const float Q = 2.f * logf(f.opac / rp.alpha_min);
-        hx = sqrtf(Q * f.cov[0]) + 0.5f;
-        hy = sqrtf(Q * f.cov[2]) + 0.5f;
+        const float q2 = log2f(f.opac / rp.alpha_min);
+        lvl = q2 * (1.f + 1e-4f) + 1e-3f;
       }
     }
-    const __half2 ext = __halves2half2(__float2half_ru(hx), __float2half_ru(hy));
-    o.p2[i] = make_float4(rgb[0], rgb[1], rgb[2], *reinterpret_cast<const float*>(&ext));
+    o.p2[i] = make_float4(rgb[0], rgb[1], rgb[2], lvl);
     o.rect[i] = f.rect;
     o.ntiles[i] = f.ntiles;
     o.zkey[i] = f.visible ? __float_as_uint(f.pc[2]) : 0xFFFFFFFFu;

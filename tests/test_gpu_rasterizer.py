@@ -200,8 +200,11 @@ def test_backward_accumulates_and_errors():
         dqo.dqo_render_backward(r.ctx, r.st, r.gs, r.cs, r.ts, None, dqo.gaussian_grads(grads))
     once = r.backward()
     torch.cuda.synchronize()
+    # float atomics add in a run-dependent order: agree to rounding, scaled per tensor
     for k in once:
-        np.testing.assert_allclose(grads[k].cpu().numpy(), 2 * once[k], rtol=1e-5, atol=1e-9)
+        acc = grads[k].cpu().numpy().astype(np.float64)
+        ref = 2 * once[k].astype(np.float64)
+        assert np.abs(acc - ref).max() <= 1e-5 * np.abs(ref).max(), k
     r.close()
 
 
