@@ -44,6 +44,7 @@ FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # FMA =
 # instance 2 + weight 1; backward = exponent 9 + alpha 3 + transmittance 2 + upstream dot 9
 # + dalpha 5 + accumulator 2 + ten partials 15 + their sums 10.
 FLOPS_PER_EVAL = {"blend_fwd": 25, "blend_bwd": 55}
+FIT_ITERS = 100
 KERNEL_SRC = {"blend_fwd": "k_blend.cu", "blend_bwd": "k_blend.cu"}
 
 
@@ -334,13 +335,43 @@ def run_ours(args, rank, world, local_rank):
             "evals_per_launch": evals, "flops_per_eval": FLOPS_PER_EVAL[dom],
             "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, no measured FP32 peak)"}
 
+    # ---- batched plain quadric fits: 512 quadrics, 3..40 views, Eq. 1 init + 100 Adam steps
+    from paper_2503_02223_gb300 import synth
+    fq = synth.batched_quadric_fits(SEED + 1)
+    fd = dqo.to_device({k: fq[k] for k in ("P", "q_ptr", "pair_v", "obs_bbox")}, dev)
+    nfit = fq["q_ptr"].shape[0] - 1
+    f_par = torch.zeros(nfit, 9, device=dev)
+    f_loss = torch.zeros(nfit, device=dev)
+    f_ok = torch.zeros(nfit, dtype=torch.uint8, device=dev)
+
+    def fit_call():
+        dqo.dqo_quadric_fit(ctx, fd["P"], fd["q_ptr"], fd["pair_v"], fd["obs_bbox"], FIT_ITERS, 1e-2, None,
+                            f_par, f_loss, f_ok, stream)
+
+    for _ in range(3):
+        fit_call()
+    torch.cuda.synchronize()
+    fit_reps = 20
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(fit_reps):
+        fit_call()
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fit_ms = f0.elapsed_time(f1) / fit_reps
+    fits = {"value": world * nfit / (fit_ms * 1e-3), "unit": "fits/s", "ms_per_batch": fit_ms,
+            "batch": nfit, "views": f"{int(fq['counts'].min())}..{int(fq['counts'].max())}",
+            "iters": FIT_ITERS, "form": "plain: Eq. 1 SVD init + 100 Adam steps, one launch",
+            "ok_fraction": float(f_ok.float().mean().item())}
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(kf, m_pairs, args), "clocks": clk,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "roofline": roof,
-            "phases_ms": {k: round(v, 4) for k, v in phases.items()}}
+            "phases_ms": {k: round(v, 4) for k, v in phases.items()},
+            "quadric_fits": fits}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         H_ = kf["camera"]["height"]
         rows = 80

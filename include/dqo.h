@@ -71,6 +71,9 @@ typedef struct {
   int32_t og_filter;      /* 1: only opaque (OG) Gaussians count toward ins, Eq. 15  (1)     */
   int32_t batch;          /* reserved: checked (32..256, multiple of 32) but unused -- every warp of the
                              blend kernels stages its own 32-Gaussian chunks                   (256) */
+  float theta_alpha;      /* Eq. 11 instance threshold of Mask_geo (not given in the paper)    (0.5)   */
+  float theta_d;          /* Eq. 11 depth threshold of Mask_geo (m)                            (0.1)   */
+  float theta_c;          /* Eq. 11 colour threshold of Mask_rgb                               (0.1)   */
 } dqo_settings;
 
 typedef struct {
@@ -109,6 +112,10 @@ typedef struct {
                                gt_id (Eq. 15 reading); 0 without targets */
   int32_t* id_map;  /* [H,W]   argmax_k sum_{i: id_i = k} w_i, ties to the smaller id; -1 if empty */
   float* loss;      /* [4]     (L_rgb, L_depth, L_ins, L_total) of Eq. 7-10 (needs targets) */
+  uint8_t* update_mask; /* [H,W] incremental-update masks of Eq. 11 (needs targets; 0 on unlabelled
+                               pixels): bit0 Mask_geo = ins < theta_alpha or |D - D^| > theta_d (where
+                               D^ > 0); bit1 Mask_rgb = max_c |C_c - C^_c| > theta_c.  Mask^{O_k} of
+                               Eq. 13 = the pixels whose gt_id is k. */
 } dqo_render_out;
 
 /* Upstream gradients of the forward outputs (device pointers; each may be NULL = zero). */
@@ -281,6 +288,26 @@ DQO_API dqo_status dqo_quadric_bbox_loss(dqo_ctx* ctx, int32_t nq, const float* 
                                  const float* P, const int32_t* q_ptr, const int32_t* pair_v,
                                  int32_t npairs, const float* obs_bbox, float* loss,
                                  float* dparams, dqo_stream stream);
+
+/* Plain multi-view fit of each quadric (Eq. 1 initialisation + Eq. 12 refinement), all
+ * quadrics in one launch, one warp per quadric.
+ *   Initialisation (Eq. 1, pi^T Q* pi = 0 for every plane pi = P^T l through a box edge
+ *   line l): the 4V planes of a quadric's V >= 3 views, taken in a frame centred on the
+ *   views' camera centres and scaled to unit mean distance and scaled to unit norm, give
+ *   a 4V x 10 linear system in Q*'s entries; its least-squares null vector (smallest
+ *   eigenvector of A^T A, fp64) is scaled to Q*44 = -1 and decomposed into centre
+ *   t = -Q*[0:3,3] and R diag(a^2, b^2, c^2) R^T = Q*[0:3,0:3] + t t^T (axes descending,
+ *   a^2 >= 1e-6 m^2, det R = +1).
+ *   Refinement: `iters` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, step `lr`) on the
+ *   bbox loss of dqo_quadric_bbox_loss (fp32).
+ * Pairs in CSR as in dqo_quadric_project.  Outputs (device, each may be NULL): init [nq,9]
+ * and params [nq,9] in the dqo_quadric_project parameterisation, loss [nq] at the final
+ * parameters, ok [nq] (0 if fewer than 3 views or a degenerate system: zeros written).
+ * Errors: DQO_EINVAL (nq < 0, iters < 0, NULL required arrays), DQO_ECUDA. */
+DQO_API dqo_status dqo_quadric_fit(dqo_ctx* ctx, int32_t nq, int32_t nv, const float* P, const int32_t* q_ptr,
+                                   const int32_t* pair_v, int32_t npairs, const float* obs_bbox, int32_t iters,
+                                   float lr, float* init, float* params, float* loss, uint8_t* ok,
+                                   dqo_stream stream);
 
 #ifdef __cplusplus
 }

@@ -37,7 +37,8 @@ class OSettings(C.Structure):
                 ("alpha_min", C.c_double), ("t_stop", C.c_double), ("znear", C.c_double),
                 ("lowpass", C.c_double), ("radius_sigma", C.c_double), ("lambda_ins", C.c_double),
                 ("bg", C.c_double * 3), ("og_filter", C.c_int32), ("num_objects", C.c_int32),
-                ("amb_rel", C.c_double), ("amb_px", C.c_double)]
+                ("amb_rel", C.c_double), ("amb_px", C.c_double), ("theta_alpha", C.c_double),
+                ("theta_d", C.c_double), ("theta_c", C.c_double)]
 
 
 class OCamera(C.Structure):
@@ -55,7 +56,7 @@ def _lib_handle():
             lib = C.CDLL(build())
             i64 = C.c_int64
             lib.oracle_preprocess.argtypes = [_P, _P, i64] + [_P] * 12
-            lib.oracle_render.argtypes = [_P, _P, i64] + [_P] * 10 + [C.c_int] + [_P] * 11
+            lib.oracle_render.argtypes = [_P, _P, i64] + [_P] * 10 + [C.c_int] + [_P] * 13
             lib.oracle_render_pixels.argtypes = [_P, _P, i64] + [_P] * 8 + [i64] + [_P] * 10
             lib.oracle_render_backward.argtypes = [_P, _P, i64] + [_P] * 19
             lib.oracle_bin_tiles.argtypes = [i64, _P, _P, _P, C.c_int, C.c_int, _P, _P]
@@ -63,6 +64,10 @@ def _lib_handle():
             lib.oracle_quadric_project.argtypes = [C.c_int, _P, C.c_int, _P, _P, _P, _P, _P, _P]
             lib.oracle_quadric_bbox_loss.argtypes = [C.c_int, _P, C.c_int, _P, _P, _P, _P, _P, _P]
             lib.oracle_quadric_matrix.argtypes = [C.c_int, _P, _P]
+            lib.oracle_quadric_fit.argtypes = [C.c_int, C.c_int, _P, _P, _P, _P, C.c_int, C.c_double,
+                                               _P, _P, _P, _P, _P, _P]
+            lib.oracle_jacobi_eigen.argtypes = [C.c_int, _P, _P]
+            lib.oracle_rot_to_rotvec.argtypes = [_P, _P]
             _lib = lib
     return _lib
 
@@ -71,7 +76,8 @@ def _lib_handle():
 
 DEFAULTS = dict(tile_w=16, tile_h=16, alpha_clamp=0.99, alpha_min=1.0 / 255.0, t_stop=1e-4,
                 znear=0.2, lowpass=0.3, radius_sigma=3.0, lambda_ins=1.0, bg=(0.0, 0.0, 0.0),
-                og_filter=1, num_objects=64, amb_rel=1e-4, amb_px=2e-3)
+                og_filter=1, num_objects=64, amb_rel=1e-4, amb_px=2e-3, theta_alpha=0.5, theta_d=0.1,
+                theta_c=0.1)
 
 # Smooth settings for finite differences: no skip, no stop, no clamp, wide cutoff.
 SMOOTH = dict(alpha_min=0.0, t_stop=0.0, alpha_clamp=1.0, radius_sigma=9.0)
@@ -135,7 +141,8 @@ def _targets(t):
 
 def render(g: dict, cam: dict, st: OSettings | None = None, targets: dict | None = None, mode: int = 0) -> dict:
     """Front-to-back blend of RGB, depth, alpha, ins (Eq. 15 reading) and the object-id argmax,
-    with the losses of Eq. 7-10 (reading: per-pixel L1 means over labelled pixels)."""
+    with the losses of Eq. 7-10 (reading: per-pixel L1 means over labelled pixels) and the
+    incremental-update masks of Eq. 11 (update_mask bit0 Mask_geo, bit1 Mask_rgb)."""
     st = st or settings()
     m, s, q, o, c, i, f = _gauss(g)
     n = m.shape[0]
@@ -144,13 +151,14 @@ def render(g: dict, cam: dict, st: OSettings | None = None, targets: dict | None
     out = dict(rgb=np.zeros((H, W, 3)), depth=np.zeros((H, W)), alpha=np.zeros((H, W)),
                ins=np.zeros((H, W)), id_map=np.zeros((H, W), np.int32), T_final=np.zeros((H, W)),
                n_contrib=np.zeros((H, W), np.int64), amb=np.zeros((H, W), np.uint8),
-               id_margin=np.zeros((H, W)), loss=np.zeros(4), dl=np.zeros((H, W, 6)))
+               id_margin=np.zeros((H, W)), loss=np.zeros(4), dl=np.zeros((H, W, 6)),
+               update_mask=np.zeros((H, W), np.uint8), mask_amb=np.zeros((H, W), np.uint8))
     oc = camera(cam)
     rc = _lib_handle().oracle_render(C.byref(st), C.byref(oc), n, _ptr(m), _ptr(s), _ptr(q), _ptr(o),
                                      _ptr(c), _ptr(i), _ptr(f), _ptr(tr), _ptr(td), _ptr(tg), mode,
                                      *[_ptr(out[k]) for k in ("rgb", "depth", "alpha", "ins", "id_map",
                                                               "T_final", "n_contrib", "amb", "id_margin",
-                                                              "loss", "dl")])
+                                                              "loss", "dl", "update_mask", "mask_amb")])
     if rc:
         raise ValueError("oracle_render: invalid arguments")
     return out
@@ -258,3 +266,39 @@ def quadric_matrix(params) -> np.ndarray:
     out = np.zeros((params.shape[0], 4, 4))
     _lib_handle().oracle_quadric_matrix(params.shape[0], _ptr(params), _ptr(out))
     return out
+
+
+def quadric_fit(P, q_ptr, pair_v, obs, iters: int = 100, lr: float = 1e-2, start=None) -> dict:
+    """Plain multi-view fit: Eq. 1 initialisation from the boxes' tangent planes (or the
+    given start parameters), then `iters` Adam steps on the Eq. 12 bbox loss (readings in
+    the C++ source)."""
+    P = _d(P).reshape(-1, 12)
+    q_ptr = np.ascontiguousarray(q_ptr, np.int32)
+    pair_v = np.ascontiguousarray(pair_v, np.int32)
+    obs = _d(obs).reshape(-1, 4)
+    nq = q_ptr.shape[0] - 1
+    out = dict(init=np.zeros((nq, 9)), params=np.zeros((nq, 9)), init_Q=np.zeros((nq, 4, 4)),
+               loss=np.zeros(nq), ok=np.zeros(nq, np.uint8))
+    st = None if start is None else _d(start).reshape(nq, 9)
+    rc = _lib_handle().oracle_quadric_fit(nq, P.shape[0], _ptr(P), _ptr(q_ptr), _ptr(pair_v), _ptr(obs), iters, lr,
+                                          *[_ptr(out[k]) for k in ("init", "params", "init_Q", "loss", "ok")],
+                                          _ptr(st))
+    if rc:
+        raise ValueError("oracle_quadric_fit: view index out of range")
+    return out
+
+
+def jacobi_eigen(A):
+    """Cyclic Jacobi eigen-decomposition of a symmetric matrix: (eigenvalues, vectors as columns)."""
+    A = _d(A).copy()
+    n = A.shape[0]
+    V = np.zeros((n, n))
+    _lib_handle().oracle_jacobi_eigen(n, _ptr(A), _ptr(V))
+    return np.diag(A).copy(), V
+
+
+def rot_to_rotvec(R):
+    R = _d(R).reshape(3, 3)
+    r = np.zeros(3)
+    _lib_handle().oracle_rot_to_rotvec(_ptr(R), _ptr(r))
+    return r

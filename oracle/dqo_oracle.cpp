@@ -42,6 +42,7 @@
 
 #include <algorithm>
 #include <array>
+#define _USE_MATH_DEFINES
 #include <cmath>
 #include <map>
 #include <cstdint>
@@ -64,6 +65,7 @@ struct OSettings {
     int32_t num_objects;  // object ids outside [0, num_objects) carry no object
     double amb_rel;       // relative margin for flagging threshold decisions
     double amb_px;        // pixel margin for flagging tile-membership decisions
+    double theta_alpha, theta_d, theta_c;  // Eq. 11 thresholds
 };
 
 struct OCamera {
@@ -386,9 +388,15 @@ const int G2 = 10;
 
 // Adjoint of one pixel's blend (plain definition: C = sum c_j a_j T_j + T_N bg, etc.).
 // acc(g) returns the 10-entry record of Gaussian g to add into.
-template <class Acc>
+struct NoMag {
+    double* operator()(int64_t) const { return nullptr; }
+};
+
+// acc(g): record to add the terms into; mag(g) (may return NULL): record to add their
+// magnitudes into.
+template <class Acc, class Mag = NoMag>
 void pixel_backward(const OSettings& st, const Inputs& in, const std::vector<Proj>& pr,
-                    const PixelResult& R, const PixelGrad& pg, int32_t gt, Acc acc) {
+                    const PixelResult& R, const PixelGrad& pg, int32_t gt, Acc acc, Mag mag = Mag()) {
     const size_t n = R.contribs.size();
     // suffix sums of w_k * (upstream . value_k) behind each contributor, plus the background
     double behind = R.T * (pg.dC[0] * st.bg[0] + pg.dC[1] * st.bg[1] + pg.dC[2] * st.bg[2]);
@@ -404,18 +412,21 @@ void pixel_backward(const OSettings& st, const Inputs& in, const std::vector<Pro
         // dL/dalpha_j = T_j U_j - (sum_{k>j} w_k U_k + T_N bg.dC) / (1 - alpha_j)
         const double dalpha = c.T * U - behind / (1 - c.alpha);
         behind += w * U;
+        double t[G2] = {0, 0, 0, 0, 0, 0, w * pg.dC[0], w * pg.dC[1], w * pg.dC[2], w * pg.dD};
+        if (!c.clamped) {
+            // alpha = o G, G = exp(power), power = -(a dx^2 + c dy^2)/2 - b dx dy, dx = px - x
+            t[5] = dalpha * c.G;
+            const double dpow = dalpha * P.opac * c.G;
+            t[0] = dpow * (P.conic[0] * c.dx + P.conic[1] * c.dy);
+            t[1] = dpow * (P.conic[1] * c.dx + P.conic[2] * c.dy);
+            t[2] = dpow * (-0.5 * c.dx * c.dx);
+            t[3] = dpow * (-c.dx * c.dy);
+            t[4] = dpow * (-0.5 * c.dy * c.dy);
+        }
         double* o = acc(g);
-        for (int ch = 0; ch < 3; ++ch) o[6 + ch] += w * pg.dC[ch];
-        o[9] += w * pg.dD;
-        if (c.clamped) continue;
-        // alpha = o G, G = exp(power), power = -(a dx^2 + c dy^2)/2 - b dx dy, dx = px - x
-        o[5] += dalpha * c.G;
-        const double dpow = dalpha * P.opac * c.G;
-        o[0] += dpow * (P.conic[0] * c.dx + P.conic[1] * c.dy);
-        o[1] += dpow * (P.conic[1] * c.dx + P.conic[2] * c.dy);
-        o[2] += dpow * (-0.5 * c.dx * c.dx);
-        o[3] += dpow * (-c.dx * c.dy);
-        o[4] += dpow * (-0.5 * c.dy * c.dy);
+        for (int k = 0; k < G2; ++k) o[k] += t[k];
+        if (double* m = mag(g))
+            for (int k = 0; k < G2; ++k) m[k] += std::fabs(t[k]);
     }
 }
 
@@ -590,7 +601,7 @@ int oracle_render(const OSettings* st, const OCamera* cam, int64_t n, const doub
                   const double* t_rgb, const double* t_depth, const int32_t* t_gt, int mode,
                   double* o_rgb, double* o_depth, double* o_alpha, double* o_ins, int32_t* o_id,
                   double* o_T, int64_t* o_ncontrib, uint8_t* o_amb, double* o_margin, double* o_loss,
-                  double* o_dl) {
+                  double* o_dl, uint8_t* o_mask, uint8_t* o_mask_amb) {
     const Inputs in = make_inputs(n, means, log_scales, quats, opacity_logit, rgb, obj_id, flags);
     const int W = cam->width, H = cam->height;
     if (W <= 0 || H <= 0 || st->tile_w <= 0 || st->tile_h <= 0) return 1;
@@ -633,6 +644,23 @@ int oracle_render(const OSettings* st, const OCamera* cam, int64_t n, const doub
                     if (o_dl) {
                         double* d = o_dl + 6 * p;
                         d[0] = pg.dC[0]; d[1] = pg.dC[1]; d[2] = pg.dC[2]; d[3] = pg.dD; d[4] = pg.dA; d[5] = pg.dins;
+                    }
+                    if (o_mask && t_gt) {
+                        // Eq. 11 update masks; o_mask_amb flags values within 1e-4 of a threshold
+                        uint8_t m = 0, am = 0;
+                        if (gt >= 0) {
+                            const double td = t_depth ? t_depth[p] : 0.0;
+                            const double ed = std::fabs(R.D - td);
+                            const bool geo = R.ins < st->theta_alpha || (td > 0 && ed > st->theta_d);
+                            double ec = 0;
+                            for (int c = 0; c < 3; ++c) ec = std::max(ec, std::fabs(R.C[c] - t_rgb[3 * p + c]));
+                            m = (uint8_t)((geo ? 1 : 0) | (ec > st->theta_c ? 2 : 0));
+                            if (std::fabs(R.ins - st->theta_alpha) < 1e-4 || (td > 0 && std::fabs(ed - st->theta_d) < 1e-4))
+                                am |= 1;
+                            if (std::fabs(ec - st->theta_c) < 1e-4) am |= 2;
+                        }
+                        o_mask[p] = m;
+                        if (o_mask_amb) o_mask_amb[p] = am;
                     }
                 }
         }
@@ -684,8 +712,8 @@ int oracle_render_pixels(const OSettings* st, const OCamera* cam, int64_t n, con
 // membership is uncertain somewhere, bit3 it feeds a pixel at an L1 kink.
 // unc[n*14]: per parameter (means, log_scales, quats, logit, rgb) the summed absolute change
 // of the gradient when each near-threshold decision or uncertain membership is taken the
-// other way, pixel by pixel -- the amount by which a correct single-precision evaluation
-// may differ from this one beyond rounding.
+// other way, pixel by pixel, plus a bound on single-precision rounding of the gradient's
+// sum -- the amount by which a correct single-precision evaluation may differ from this one.
 int oracle_render_backward(const OSettings* st, const OCamera* cam, int64_t n, const double* means,
                            const double* log_scales, const double* quats, const double* opacity_logit,
                            const double* rgb, const int32_t* obj_id, const uint8_t* flags,
@@ -699,6 +727,8 @@ int oracle_render_backward(const OSettings* st, const OCamera* cam, int64_t n, c
     std::vector<Proj> pr = project_all(*st, *cam, in);
     const std::vector<std::vector<int64_t>> tile_amb = rect_ambiguity(pr, ntx, nty);
     std::vector<double> g2((size_t)n * G2, 0.0);
+    // magnitudes of the per-pixel terms: plain, and weighted by the pixel's walk length
+    std::vector<double> magA(unc ? (size_t)n * G2 : 0, 0.0), magS(unc ? (size_t)n * G2 : 0, 0.0);
     const double inv_hw = 1.0 / ((double)W * H);
     auto dense = [&](int64_t g) { return g2.data() + G2 * g; };
     using Sparse = std::map<int64_t, std::array<double, G2>>;
@@ -750,7 +780,26 @@ int oracle_render_backward(const OSettings* st, const OCamera* cam, int64_t n, c
                         double loss[3] = {0, 0, 0};
                         pixel_loss(*st, R, t_rgb + 3 * p, t_depth ? t_depth[p] : 0.0, gt, inv_hw, loss, pg, R.amb);
                     }
-                    pixel_backward(*st, in, pr, R, pg, gt, dense);
+                    if (unc) {
+                        // a single-precision walk of k contributors carries a relative error
+                        // of about k unit roundoffs in T (forward product, backward quotients)
+                        std::vector<double> tmp(G2 * R.contribs.size());
+                        size_t slot = 0;
+                        std::map<int64_t, double*> where;
+                        pixel_backward(*st, in, pr, R, pg, gt, dense, [&](int64_t g) {
+                            double* m = tmp.data() + G2 * slot++;
+                            where[g] = m;
+                            return m;
+                        });
+                        const double wk = (double)R.contribs.size() + 16.0;
+                        for (const auto& kv : where)
+                            for (int k = 0; k < G2; ++k) {
+                                magA[G2 * kv.first + k] += kv.second[k];
+                                magS[G2 * kv.first + k] += wk * kv.second[k];
+                            }
+                    } else {
+                        pixel_backward(*st, in, pr, R, pg, gt, dense);
+                    }
                     if (g_amb && (R.amb & AMB_KINK))
                         for (const Contrib& c : R.contribs) g_amb[c.g] |= AMB_KINK;
                     if (unc && (R.amb & (AMB_THRESH | AMB_RECT))) {
@@ -789,6 +838,31 @@ int oracle_render_backward(const OSettings* st, const OCamera* cam, int64_t n, c
                     }
                 }
         }
+    // Single-precision rounding bound of every Gaussian's gradient: its per-pixel terms
+    // carry ~(walk length + 16) unit roundoffs each, and the GPU adds them through about
+    // sqrt(8 x tiles covered) levels of partial sums; chained to the parameters through
+    // the element-wise magnitude of the projection Jacobian, times a safety factor of 4.
+    const double u = std::ldexp(1.0, -24);
+    for (int64_t i = 0; unc && i < n; ++i) {
+        if (!pr[i].visible) continue;
+        const int nt = (pr[i].rect[2] - pr[i].rect[0]) * (pr[i].rect[3] - pr[i].rect[1]);
+        double bound2d[G2];
+        for (int k = 0; k < G2; ++k)
+            bound2d[k] = 4 * u * (magS[G2 * i + k] + std::sqrt(8.0 * nt) * magA[G2 * i + k]);
+        for (int k = 0; k < G2; ++k) {
+            if (bound2d[k] == 0) continue;
+            double e[G2] = {0};
+            e[k] = 1;
+            double dm[3] = {0, 0, 0}, ds[3] = {0, 0, 0}, dq[4] = {0, 0, 0, 0}, dlg = 0, dc[3] = {0, 0, 0};
+            preprocess_backward(*st, *cam, pr[i], opacity_logit[i], e, dm, ds, dq, &dlg, dc);
+            double* uu = unc + 14 * i;
+            for (int j = 0; j < 3; ++j) uu[j] += std::fabs(dm[j]) * bound2d[k];
+            for (int j = 0; j < 3; ++j) uu[3 + j] += std::fabs(ds[j]) * bound2d[k];
+            for (int j = 0; j < 4; ++j) uu[6 + j] += std::fabs(dq[j]) * bound2d[k];
+            uu[10] += std::fabs(dlg) * bound2d[k];
+            for (int j = 0; j < 3; ++j) uu[11 + j] += std::fabs(dc[j]) * bound2d[k];
+        }
+    }
     for (int64_t i = 0; i < n; ++i) {
         const double* r = g2.data() + G2 * i;
         if (g2_out) for (int k = 0; k < G2; ++k) g2_out[G2 * i + k] += r[k];
@@ -1010,6 +1084,255 @@ int oracle_quadric_matrix(int nq, const double* params, double* Q16) {
         quadric_from_params(params + 9 * q, Q);
         for (int i = 0; i < 4; ++i)
             for (int j = 0; j < 4; ++j) Q16[16 * q + 4 * i + j] = Q[i][j];
+    }
+    return 0;
+}
+
+}  // extern "C"
+
+// ====================================================================== plain multi-view fit
+
+namespace {
+
+// Cyclic Jacobi eigen-decomposition of a symmetric n x n matrix (row-major, overwritten);
+// eigenvalues on the diagonal of A, eigenvectors in the columns of V.
+void jacobi_eigen(int n, double* A, double* V) {
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) V[i * n + j] = i == j ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0, tot = 0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                tot += A[i * n + j] * A[i * n + j];
+                if (i != j) off += A[i * n + j] * A[i * n + j];
+            }
+        if (off <= 1e-30 * tot || off == 0) break;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = A[p * n + q];
+                if (apq == 0) continue;
+                const double theta = (A[q * n + q] - A[p * n + p]) / (2 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1));
+                const double c = 1 / std::sqrt(t * t + 1), sn = t * c;
+                for (int k = 0; k < n; ++k) {  // A <- A J (columns p, q)
+                    const double akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = c * akp - sn * akq;
+                    A[k * n + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {  // A <- J^T A (rows p, q)
+                    const double apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = c * apk - sn * aqk;
+                    A[q * n + k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {  // V <- V J
+                    const double vkp = V[k * n + p], vkq = V[k * n + q];
+                    V[k * n + p] = c * vkp - sn * vkq;
+                    V[k * n + q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+}
+
+// Rotation matrix -> rotation vector (axis times angle in [0, pi]).
+void rot_to_rotvec(const double R[3][3], double r[3]) {
+    const double w[3] = {R[2][1] - R[1][2], R[0][2] - R[2][0], R[1][0] - R[0][1]};
+    const double ct = std::max(-1.0, std::min(1.0, 0.5 * (R[0][0] + R[1][1] + R[2][2] - 1)));
+    const double th = std::acos(ct);
+    const double sw = std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    if (th < 1e-8) {
+        for (int k = 0; k < 3; ++k) r[k] = 0.5 * w[k];
+        return;
+    }
+    if (M_PI - th < 1e-4 || sw < 1e-12) {
+        // near pi the skew part vanishes: (R + R^T)/2 = cos(th) I + (1 - cos(th)) a a^T
+        double S[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) S[i][j] = (0.5 * (R[i][j] + R[j][i]) - (i == j ? ct : 0.0)) / (1 - ct);
+        int k = 0;
+        for (int i = 1; i < 3; ++i)
+            if (S[i][i] > S[k][k]) k = i;
+        const double d = std::sqrt(std::max(S[k][k], 1e-300));
+        double ax[3] = {S[0][k] / d, S[1][k] / d, S[2][k] / d};
+        if (ax[0] * w[0] + ax[1] * w[1] + ax[2] * w[2] < 0)
+            for (int i = 0; i < 3; ++i) ax[i] = -ax[i];
+        for (int i = 0; i < 3; ++i) r[i] = th * ax[i];
+        return;
+    }
+    for (int k = 0; k < 3; ++k) r[k] = th / (2 * std::sin(th)) * w[k];
+}
+
+// Plain initialisation (Eq. 1): every bbox edge line l back-projects to a plane pi = P^T l
+// tangent to the quadric, pi^T Q* pi = 0, linear in Q*'s 10 entries.  Reading: planes in a
+// world frame centred on the views' camera centres and scaled to unit mean distance,
+// each plane scaled to unit norm; the null vector is the eigenvector of A^T A with the
+// smallest eigenvalue; Q* scaled to Q*44 = -1; t = -Q*[0:3,3]; R diag(a^2,b^2,c^2) R^T =
+// Q*[0:3,0:3] + t t^T with eigenvalues sorted descending, clamped to >= 1e-6 m^2, det R = +1.
+bool quadric_init(int nview, const double* const* Pv, const double* const* obs, double params[9],
+                  double Qout[16]) {
+    // camera centres C = -M^-1 p
+    std::vector<std::array<double, 3>> C(nview);
+    double c[3] = {0, 0, 0};
+    for (int v = 0; v < nview; ++v) {
+        const double* P = Pv[v];
+        const double M[3][3] = {{P[0], P[1], P[2]}, {P[4], P[5], P[6]}, {P[8], P[9], P[10]}};
+        const double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+                           M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                           M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+        if (det == 0) return false;
+        double inv[3][3];
+        inv[0][0] = (M[1][1] * M[2][2] - M[1][2] * M[2][1]) / det;
+        inv[0][1] = (M[0][2] * M[2][1] - M[0][1] * M[2][2]) / det;
+        inv[0][2] = (M[0][1] * M[1][2] - M[0][2] * M[1][1]) / det;
+        inv[1][0] = (M[1][2] * M[2][0] - M[1][0] * M[2][2]) / det;
+        inv[1][1] = (M[0][0] * M[2][2] - M[0][2] * M[2][0]) / det;
+        inv[1][2] = (M[0][2] * M[1][0] - M[0][0] * M[1][2]) / det;
+        inv[2][0] = (M[1][0] * M[2][1] - M[1][1] * M[2][0]) / det;
+        inv[2][1] = (M[0][1] * M[2][0] - M[0][0] * M[2][1]) / det;
+        inv[2][2] = (M[0][0] * M[1][1] - M[0][1] * M[1][0]) / det;
+        for (int i = 0; i < 3; ++i) {
+            C[v][i] = -(inv[i][0] * P[3] + inv[i][1] * P[7] + inv[i][2] * P[11]);
+            c[i] += C[v][i] / nview;
+        }
+    }
+    double md = 0;
+    for (int v = 0; v < nview; ++v)
+        md += std::sqrt((C[v][0] - c[0]) * (C[v][0] - c[0]) + (C[v][1] - c[1]) * (C[v][1] - c[1]) +
+                        (C[v][2] - c[2]) * (C[v][2] - c[2])) / nview;
+    const double sc = md > 0 ? 1.0 / md : 1.0;
+    // A^T A over the normalised planes
+    double AtA[100] = {0};
+    for (int v = 0; v < nview; ++v) {
+        const double* P = Pv[v];
+        const double* b = obs[v];
+        const double lines[4][3] = {{1, 0, -b[0]}, {1, 0, -b[2]}, {0, 1, -b[1]}, {0, 1, -b[3]}};
+        for (int e = 0; e < 4; ++e) {
+            double pi[4];
+            for (int k = 0; k < 4; ++k)
+                pi[k] = lines[e][0] * P[k] + lines[e][1] * P[4 + k] + lines[e][2] * P[8 + k];
+            // plane in the normalised frame X' = sc (X - c): (n / sc, n.c + d)
+            double pn[4] = {pi[0] / sc, pi[1] / sc, pi[2] / sc, pi[0] * c[0] + pi[1] * c[1] + pi[2] * c[2] + pi[3]};
+            const double nrm = std::sqrt(pn[0] * pn[0] + pn[1] * pn[1] + pn[2] * pn[2] + pn[3] * pn[3]);
+            for (int k = 0; k < 4; ++k) pn[k] /= nrm;
+            const double row[10] = {pn[0] * pn[0], 2 * pn[0] * pn[1], 2 * pn[0] * pn[2], 2 * pn[0] * pn[3],
+                                    pn[1] * pn[1], 2 * pn[1] * pn[2], 2 * pn[1] * pn[3], pn[2] * pn[2],
+                                    2 * pn[2] * pn[3], pn[3] * pn[3]};
+            for (int i = 0; i < 10; ++i)
+                for (int j = 0; j < 10; ++j) AtA[i * 10 + j] += row[i] * row[j];
+        }
+    }
+    double V[100];
+    jacobi_eigen(10, AtA, V);
+    int kmin = 0;
+    for (int k = 1; k < 10; ++k)
+        if (AtA[k * 10 + k] < AtA[kmin * 10 + kmin]) kmin = k;
+    double q[10];
+    for (int k = 0; k < 10; ++k) q[k] = V[k * 10 + kmin];
+    const int idx[4][4] = {{0, 1, 2, 3}, {1, 4, 5, 6}, {2, 5, 7, 8}, {3, 6, 8, 9}};
+    double Qn[4][4];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) Qn[i][j] = q[idx[i][j]];
+    // back to the world frame: Q* = T^-1 Q*' T^-T with T^-1 = [[I/sc, c], [0, 1]]
+    double Ti[4][4] = {{1 / sc, 0, 0, c[0]}, {0, 1 / sc, 0, c[1]}, {0, 0, 1 / sc, c[2]}, {0, 0, 0, 1}};
+    double Q[4][4];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            double acc = 0;
+            for (int k = 0; k < 4; ++k)
+                for (int l = 0; l < 4; ++l) acc += Ti[i][k] * Qn[k][l] * Ti[j][l];
+            Q[i][j] = acc;
+        }
+    if (std::fabs(Q[3][3]) < 1e-300) return false;
+    const double f = -1.0 / Q[3][3];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) Q[i][j] *= f;
+    if (Qout)
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) Qout[4 * i + j] = Q[i][j];
+    const double t[3] = {-Q[0][3], -Q[1][3], -Q[2][3]};
+    double M[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) M[3 * i + j] = Q[i][j] + t[i] * t[j];
+    double E[9];
+    jacobi_eigen(3, M, E);
+    int order[3] = {0, 1, 2};
+    std::sort(order, order + 3, [&](int a, int b) { return M[4 * a] > M[4 * b]; });
+    double R[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k) R[i][k] = E[3 * i + order[k]];
+    const double detR = R[0][0] * (R[1][1] * R[2][2] - R[1][2] * R[2][1]) -
+                        R[0][1] * (R[1][0] * R[2][2] - R[1][2] * R[2][0]) +
+                        R[0][2] * (R[1][0] * R[2][1] - R[1][1] * R[2][0]);
+    if (detR < 0)
+        for (int i = 0; i < 3; ++i) R[i][2] = -R[i][2];
+    for (int k = 0; k < 3; ++k) {
+        params[k] = t[k];
+        params[3 + k] = 0.5 * std::log(std::max(M[4 * order[k]], 1e-6));
+    }
+    rot_to_rotvec(R, params + 6);
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Helpers exposed for pinning: symmetric eigen-decomposition and the rotation log map.
+int oracle_jacobi_eigen(int n, double* A, double* V) {
+    jacobi_eigen(n, A, V);
+    return 0;
+}
+int oracle_rot_to_rotvec(const double* R9, double* r3) {
+    const double R[3][3] = {{R9[0], R9[1], R9[2]}, {R9[3], R9[4], R9[5]}, {R9[6], R9[7], R9[8]}};
+    rot_to_rotvec(R, r3);
+    return 0;
+}
+
+// Plain multi-view fit of each quadric: the Eq. 1 initialisation from its views' boxes
+// (or the given start[nq*9], if not NULL), then `iters` Adam steps (Kingma & Ba; lr, beta1 = 0.9, beta2 = 0.999, eps = 1e-8) on the
+// Eq. 12 bbox loss.  Outputs (each may be NULL): init[nq*9], params[nq*9], init_Q[nq*16]
+// (Q* after the initialisation, Q*44 = -1), loss[nq] (loss at the final parameters),
+// ok[nq] (initialisation succeeded).
+int oracle_quadric_fit(int nq, int nv, const double* P, const int32_t* q_ptr, const int32_t* pair_v,
+                       const double* obs, int iters, double lr, double* init, double* params, double* init_Q,
+                       double* loss, uint8_t* ok, const double* start) {
+    for (int q = 0; q < nq; ++q) {
+        const int k0 = q_ptr[q], k1 = q_ptr[q + 1];
+        std::vector<const double*> Pv, ob;
+        for (int k = k0; k < k1; ++k) {
+            if (pair_v[k] < 0 || pair_v[k] >= nv) return 1;
+            Pv.push_back(P + 12 * pair_v[k]);
+            ob.push_back(obs + 4 * k);
+        }
+        double p[9] = {0}, Q16[16] = {0};
+        bool good;
+        if (start) {  // refine from a given starting point instead of the initialisation
+            for (int i = 0; i < 9; ++i) p[i] = start[9 * q + i];
+            good = k1 - k0 >= 1;
+        } else {
+            good = k1 - k0 >= 3 && quadric_init(k1 - k0, Pv.data(), ob.data(), p, Q16);
+        }
+        if (ok) ok[q] = good;
+        if (init) for (int i = 0; i < 9; ++i) init[9 * q + i] = p[i];
+        if (init_Q) for (int i = 0; i < 16; ++i) init_Q[16 * q + i] = Q16[i];
+        double m[9] = {0}, v2[9] = {0};
+        double b1t = 1, b2t = 1;
+        double L = 0, g[9];
+        const int32_t zero_ptr[2] = {0, k1 - k0};
+        std::vector<int32_t> views(pair_v + k0, pair_v + k1);
+        for (int it = 1; good && it <= iters; ++it) {
+            oracle_quadric_bbox_loss(1, p, nv, P, zero_ptr, views.data(), obs + 4 * k0, &L, g);
+            b1t *= 0.9;
+            b2t *= 0.999;
+            for (int i = 0; i < 9; ++i) {
+                m[i] = 0.9 * m[i] + 0.1 * g[i];
+                v2[i] = 0.999 * v2[i] + 0.001 * g[i] * g[i];
+                const double mh = m[i] / (1 - b1t), vh = v2[i] / (1 - b2t);
+                p[i] -= lr * mh / (std::sqrt(vh) + 1e-8);
+            }
+        }
+        if (good) oracle_quadric_bbox_loss(1, p, nv, P, zero_ptr, views.data(), obs + 4 * k0, &L, g);
+        if (params) for (int i = 0; i < 9; ++i) params[9 * q + i] = p[i];
+        if (loss) loss[q] = good ? L : 0;
     }
     return 0;
 }

@@ -26,11 +26,12 @@ struct dqo_ctx {
   // per-Gaussian
   Buf p0, p1, p2, rect, ntiles, zkey_a, zkey_b, zval_a, zval_b, rank, gid, offsets, grad2d;
   // sorting scratch
-  Buf scan_scratch, hist, pair_a, pair_b, list;
+  Buf scan_scratch, depth_scan_scratch, hist, depth_hist, pair_a, pair_b, list;
   // per-tile / per-pixel
   Buf ranges, loss_part, T_final, n_contrib, dl_rgb, dl_depth, dl_ins;
   Buf counters;             // device: [0] uint64 total pairs, [1] uint32 n_visible
   uint64_t* host_counters = nullptr;  // pinned mirror
+  cudaEvent_t count_ready = nullptr;  // recorded after the pair count is copied to the host
   // state of the last forward
   bool have_fwd = false;
   bool fwd_dl = false;
@@ -171,6 +172,9 @@ RasterParams make_params(const dqo_settings* s, const dqo_gaussians* g, const dq
   rp.og_filter = s->og_filter ? 1 : 0;
   rp.batch = s->batch;
   rp.num_objects = g->num_objects;
+  rp.theta_alpha = s->theta_alpha;
+  rp.theta_d = s->theta_d;
+  rp.theta_c = s->theta_c;
   return rp;
 }
 
@@ -192,6 +196,9 @@ void dqo_settings_default(dqo_settings* s) {
   s->bg[0] = s->bg[1] = s->bg[2] = 0.0f;
   s->og_filter = 1;
   s->batch = 256;
+  s->theta_alpha = 0.5f;
+  s->theta_d = 0.1f;
+  s->theta_c = 0.1f;
 }
 
 int dqo_version(void) { return 100; }
@@ -222,7 +229,8 @@ dqo_status dqo_create(dqo_ctx** out, int device) {
   if (!c) return DQO_ENOMEM;
   c->device = device;
   if (ensure(c->counters, 64) != cudaSuccess ||
-      cudaMallocHost(reinterpret_cast<void**>(&c->host_counters), 64) != cudaSuccess) {
+      cudaMallocHost(reinterpret_cast<void**>(&c->host_counters), 64) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->count_ready, cudaEventDisableTiming) != cudaSuccess) {
     dqo_destroy(c);
     return DQO_ENOMEM;
   }
@@ -233,12 +241,14 @@ dqo_status dqo_create(dqo_ctx** out, int device) {
 void dqo_destroy(dqo_ctx* c) {
   if (!c) return;
   Buf* all[] = {&c->p0, &c->p1, &c->p2, &c->rect, &c->ntiles, &c->zkey_a, &c->zkey_b, &c->zval_a,
-                &c->zval_b, &c->rank, &c->gid, &c->offsets, &c->grad2d, &c->scan_scratch, &c->hist,
+                &c->zval_b, &c->rank, &c->gid, &c->offsets, &c->grad2d, &c->scan_scratch,
+                &c->depth_scan_scratch, &c->hist, &c->depth_hist,
                 &c->pair_a, &c->pair_b, &c->list, &c->ranges, &c->loss_part, &c->T_final, &c->n_contrib,
                 &c->dl_rgb, &c->dl_depth, &c->dl_ins, &c->counters};
   for (Buf* b : all)
     if (b->p) cudaFree(b->p);
   if (c->host_counters) cudaFreeHost(c->host_counters);
+  if (c->count_ready) cudaEventDestroy(c->count_ready);
   for (int i = 0; i < 2 * DQO_PHASE_COUNT; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   delete c;
@@ -254,7 +264,7 @@ dqo_status dqo_render_forward(dqo_ctx* c, const dqo_settings* s, const dqo_gauss
   if ((st = check_gaussians(g)) != DQO_OK) return st;
   if ((st = check_camera(cam)) != DQO_OK) return st;
   if (t && (!t->gt_id || !t->rgb)) return DQO_EINVAL;
-  if (out->loss && !t) return DQO_EINVAL;
+  if ((out->loss || out->update_mask) && !t) return DQO_EINVAL;
   cudaStream_t s_ = reinterpret_cast<cudaStream_t>(stream_);
   DQO_CUDA(c, cudaSetDevice(c->device));
   c->have_fwd = false;
@@ -286,8 +296,9 @@ dqo_status dqo_render_forward(dqo_ctx* c, const dqo_settings* s, const dqo_gauss
     DQO_CUDA(c, ensure(c->dl_depth, 4 * HW));
     DQO_CUDA(c, ensure(c->dl_ins, 4 * HW));
   }
-  DQO_CUDA(c, ensure(c->scan_scratch, 8 * std::max(scan_scratch_words(n), scan_scratch_words(radix_scratch_words(n)))));
-  DQO_CUDA(c, ensure(c->hist, 4 * radix_scratch_words(n)));
+  DQO_CUDA(c, ensure(c->scan_scratch, 8 * scan_scratch_words(n)));
+  DQO_CUDA(c, ensure(c->depth_scan_scratch, 8 * scan_scratch_words(radix_scratch_words(n))));
+  DQO_CUDA(c, ensure(c->depth_hist, 4 * radix_scratch_words(n)));
   DQO_CUDA(c, cudaMemsetAsync(c->counters.p, 0, 64, s_));
 
   uint64_t* d_total = as<uint64_t>(c->counters);
@@ -311,15 +322,18 @@ dqo_status dqo_render_forward(dqo_ctx* c, const dqo_settings* s, const dqo_gauss
   }
   c->launches += nb_launch;
 
-  // ---- K2 scan of tiles per Gaussian, depth sort, ranks
+  // ---- K2 scan of tiles per Gaussian; the pair count goes to the host while the depth
+  // sort runs (the host waits on that copy only, not on the sort)
   int sel = 0;
   {
     PhaseTimer pt(c, DQO_PHASE_DEPTH_SORT, s_);
     DQO_CUDA(c, launch_exclusive_scan(as<uint32_t>(c->ntiles), as<uint32_t>(c->offsets), n,
                                       as<uint64_t>(c->scan_scratch), d_total, s_));
+    DQO_CUDA(c, cudaMemcpyAsync(c->host_counters, c->counters.p, 16, cudaMemcpyDeviceToHost, s_));
+    DQO_CUDA(c, cudaEventRecord(c->count_ready, s_));
     DQO_CUDA(c, radix_sort_u32(as<uint32_t>(c->zkey_a), as<uint32_t>(c->zkey_b), as<uint32_t>(c->zval_a),
-                               as<uint32_t>(c->zval_b), n, 32, as<uint32_t>(c->hist),
-                               as<uint64_t>(c->scan_scratch), &sel, s_));
+                               as<uint32_t>(c->zval_b), n, 32, as<uint32_t>(c->depth_hist),
+                               as<uint64_t>(c->depth_scan_scratch), &sel, s_));
     DQO_CUDA(c, launch_rank_scatter(sel ? as<uint32_t>(c->zval_b) : as<uint32_t>(c->zval_a), n,
                                     as<uint32_t>(c->rank), s_));
   }
@@ -327,9 +341,8 @@ dqo_status dqo_render_forward(dqo_ctx* c, const dqo_settings* s, const dqo_gauss
   c->order_sel = sel;
   c->launches += scan_launches(n) + sort_launches(n, 32) + nb_launch;
 
-  // ---- pair count to the host (the one synchronisation of the forward)
-  DQO_CUDA(c, cudaMemcpyAsync(c->host_counters, c->counters.p, 16, cudaMemcpyDeviceToHost, s_));
-  DQO_CUDA(c, cudaStreamSynchronize(s_));
+  // ---- pair count on the host (the one wait of the forward)
+  DQO_CUDA(c, cudaEventSynchronize(c->count_ready));
   const uint64_t m = c->host_counters[0];
   const uint64_t n_vis = (uint32_t)(c->host_counters[1] & 0xFFFFFFFFu);
   if (m >= (uint64_t(1) << 31)) return DQO_ENOMEM;  // tile ranges are int32 in the blend kernels
@@ -394,6 +407,7 @@ dqo_status dqo_render_forward(dqo_ctx* c, const dqo_settings* s, const dqo_gauss
   a.dl_depth = t ? as<float>(c->dl_depth) : nullptr;
   a.dl_ins = t ? as<float>(c->dl_ins) : nullptr;
   a.loss_part = as<float>(c->loss_part);
+  a.o_mask = out->update_mask;
   {
     PhaseTimer pt(c, DQO_PHASE_BLEND_FWD, s_);
     DQO_CUDA(c, launch_blend_forward(a, out->id_map != nullptr, s_));
@@ -594,6 +608,22 @@ dqo_status dqo_quadric_bbox_loss(dqo_ctx* c, int32_t nq, const float* params, in
     PhaseTimer pt(c, DQO_PHASE_QUADRIC, reinterpret_cast<cudaStream_t>(stream_));
     DQO_CUDA(c, launch_quadric_bbox_loss(nq, params, nv, P, q_ptr, pair_v, npairs, obs, loss, dparams,
                                          reinterpret_cast<cudaStream_t>(stream_)));
+  }
+  c->launches += nq > 0 ? 1 : 0;
+  return DQO_OK;
+}
+
+dqo_status dqo_quadric_fit(dqo_ctx* c, int32_t nq, int32_t nv, const float* P, const int32_t* q_ptr,
+                           const int32_t* pair_v, int32_t npairs, const float* obs, int32_t iters, float lr,
+                           float* init, float* params, float* loss, uint8_t* ok, dqo_stream stream_) {
+  if (!c || nq < 0 || nv < 0 || npairs < 0 || iters < 0 || !(lr >= 0.f)) return DQO_EINVAL;
+  if (nq > 0 && !q_ptr) return DQO_EINVAL;
+  if (npairs > 0 && (!P || !pair_v || !obs || nv == 0)) return DQO_EINVAL;
+  DQO_CUDA(c, cudaSetDevice(c->device));
+  {
+    PhaseTimer pt(c, DQO_PHASE_QUADRIC, reinterpret_cast<cudaStream_t>(stream_));
+    DQO_CUDA(c, launch_quadric_fit(nq, nv, P, q_ptr, pair_v, npairs, obs, iters, lr, init, params, loss, ok,
+                                   reinterpret_cast<cudaStream_t>(stream_)));
   }
   c->launches += nq > 0 ? 1 : 0;
   return DQO_OK;

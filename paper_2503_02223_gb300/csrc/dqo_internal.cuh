@@ -64,6 +64,7 @@ struct RasterParams {
   int og_filter;
   int batch;
   int num_objects;
+  float theta_alpha, theta_d, theta_c;
 };
 
 struct ProjBuffers {
@@ -100,6 +101,7 @@ struct BlendFwdArgs {
   float* dl_depth;   // saved dL/dD  [H*W]
   float* dl_ins;     // saved dL/dins[H*W]
   float* loss_part;  // [T*3] per-tile loss sums
+  uint8_t* o_mask;   // [H*W] Eq. 11 update masks (with targets)
 };
 
 struct BlendBwdArgs {
@@ -177,5 +179,9 @@ cudaError_t launch_quadric_project(int nq, const float* params, int nv, const fl
 cudaError_t launch_quadric_bbox_loss(int nq, const float* params, int nv, const float* P, const int32_t* q_ptr,
                                      const int32_t* pair_v, int npairs, const float* obs, float* loss,
                                      float* dparams, cudaStream_t s);
+
+cudaError_t launch_quadric_fit(int nq, int nv, const float* P, const int32_t* q_ptr, const int32_t* pair_v,
+                               int npairs, const float* obs, int iters, float lr, float* init, float* params,
+                               float* loss, uint8_t* ok, cudaStream_t s);
 
 }  // namespace dqo

@@ -311,6 +311,14 @@ __global__ void __launch_bounds__(kThreads) k_blend_forward(BlendFwdArgs a) {
         const float ei = ins - 1.f;
         l_i = fabsf(ei);
         gi = rp.lambda_ins * sgnf(ei) * inv_hw;
+        if (a.o_mask) {
+          // Eq. 11: Mask_geo (bit0) and Mask_rgb (bit1)
+          const bool geo = ins < rp.theta_alpha || (td > 0.f && fabsf(D - td) > rp.theta_d);
+          const bool col = fmaxf(fabsf(e0), fmaxf(fabsf(e1), fabsf(e2))) > rp.theta_c;
+          a.o_mask[pix] = (uint8_t)((geo ? 1 : 0) | (col ? 2 : 0));
+        }
+      } else if (a.o_mask) {
+        a.o_mask[pix] = 0;
       }
       a.dl_rgb[3 * pix + 0] = g0;
       a.dl_rgb[3 * pix + 1] = g1;

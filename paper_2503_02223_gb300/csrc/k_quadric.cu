@@ -265,7 +265,284 @@ __global__ void k_quadric_bbox_loss(int nq, const float* __restrict__ params, in
   }
 }
 
+
+// ---------------------------------------------------------------- plain multi-view fit
+
+constexpr int kFitWarps = 4;
+
+// One cyclic-Jacobi rotation sweep set on a symmetric n x n fp64 matrix held in shared
+// memory, the element updates spread over the warp's lanes (lane k owns row / column k).
+__device__ void warp_jacobi(int n, double* A, double* V, int lane) {
+  for (int k = lane; k < n * n; k += 32) V[k] = (k / n == k % n) ? 1.0 : 0.0;
+  __syncwarp();
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int k = lane; k < n * n; k += 32) {
+      const double a = A[k] * A[k];
+      tot += a;
+      if (k / n != k % n) off += a;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xFFFFFFFFu, off, o);
+      tot += __shfl_xor_sync(0xFFFFFFFFu, tot, o);
+    }
+    if (off <= 1e-30 * tot || off == 0.0) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[p * n + q];
+        if (apq == 0.0) continue;  // uniform: every lane reads the same value
+        const double th = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        const double c = rsqrt(t * t + 1.0), sn = t * c;
+        __syncwarp();
+        if (lane < n) {
+          const double akp = A[lane * n + p], akq = A[lane * n + q];
+          A[lane * n + p] = c * akp - sn * akq;
+          A[lane * n + q] = sn * akp + c * akq;
+        }
+        __syncwarp();
+        if (lane < n) {
+          const double apk = A[p * n + lane], aqk = A[q * n + lane];
+          A[p * n + lane] = c * apk - sn * aqk;
+          A[q * n + lane] = sn * apk + c * aqk;
+          const double vkp = V[lane * n + p], vkq = V[lane * n + q];
+          V[lane * n + p] = c * vkp - sn * vkq;
+          V[lane * n + q] = sn * vkp + c * vkq;
+        }
+        __syncwarp();
+      }
+  }
+}
+
+// Rotation matrix -> rotation vector through the unit quaternion (Shepperd's branch).
+__device__ void rotmat_to_rotvec(const double R[3][3], double r[3]) {
+  const double tr = R[0][0] + R[1][1] + R[2][2];
+  double w, x, y, z;
+  if (tr > 0.0) {
+    const double s = 2.0 * sqrt(tr + 1.0);
+    w = 0.25 * s; x = (R[2][1] - R[1][2]) / s; y = (R[0][2] - R[2][0]) / s; z = (R[1][0] - R[0][1]) / s;
+  } else if (R[0][0] > R[1][1] && R[0][0] > R[2][2]) {
+    const double s = 2.0 * sqrt(1.0 + R[0][0] - R[1][1] - R[2][2]);
+    w = (R[2][1] - R[1][2]) / s; x = 0.25 * s; y = (R[0][1] + R[1][0]) / s; z = (R[0][2] + R[2][0]) / s;
+  } else if (R[1][1] > R[2][2]) {
+    const double s = 2.0 * sqrt(1.0 + R[1][1] - R[0][0] - R[2][2]);
+    w = (R[0][2] - R[2][0]) / s; x = (R[0][1] + R[1][0]) / s; y = 0.25 * s; z = (R[1][2] + R[2][1]) / s;
+  } else {
+    const double s = 2.0 * sqrt(1.0 + R[2][2] - R[0][0] - R[1][1]);
+    w = (R[1][0] - R[0][1]) / s; x = (R[0][2] + R[2][0]) / s; y = (R[1][2] + R[2][1]) / s; z = 0.25 * s;
+  }
+  if (w < 0.0) { w = -w; x = -x; y = -y; z = -z; }
+  const double vn = sqrt(x * x + y * y + z * z);
+  const double f = vn > 1e-300 ? 2.0 * atan2(vn, w) / vn : 2.0;
+  r[0] = f * x; r[1] = f * y; r[2] = f * z;
+}
+
+// Eq. 1 initialisation of one quadric by one warp (fp64).  Same reading as the library's
+// documentation: planes of the box edges in a frame centred on the views' camera centres
+// and scaled to unit mean distance, unit-norm rows, null vector of A^T A, Q*44 = -1,
+// eigen-decomposition of Q*[0:3,0:3] + t t^T (descending, >= 1e-6, det R = +1).
+__device__ bool warp_quadric_init(int k0, int k1, const float* __restrict__ Pm, const int32_t* __restrict__ pair_v,
+                                  const float* __restrict__ obs, int nv, double* sm, int lane, float out[9]) {
+  double* AtA = sm;        // 100
+  double* V = sm + 100;    // 100
+  const int nview = k1 - k0;
+  // camera centres: C = -M^-1 p, accumulated over the warp
+  double cs[3] = {0.0, 0.0, 0.0};
+  bool good = true;
+  for (int k = k0 + lane; k < k1; k += 32) {
+    const int v = pair_v[k];
+    if (v < 0 || v >= nv) { good = false; continue; }
+    const float* P = Pm + 12 * v;
+    const double a = P[0], b = P[1], c = P[2], d = P[4], e = P[5], f = P[6], g = P[8], h = P[9], i = P[10];
+    const double det = a * (e * i - f * h) - b * (d * i - f * g) + c * (d * h - e * g);
+    if (det == 0.0) { good = false; continue; }
+    const double p0 = P[3], p1 = P[7], p2 = P[11];
+    cs[0] += -((e * i - f * h) * p0 + (c * h - b * i) * p1 + (b * f - c * e) * p2) / det;
+    cs[1] += -((f * g - d * i) * p0 + (a * i - c * g) * p1 + (c * d - a * f) * p2) / det;
+    cs[2] += -((d * h - e * g) * p0 + (b * g - a * h) * p1 + (a * e - b * d) * p2) / det;
+  }
+  good = __all_sync(0xFFFFFFFFu, good);
+  if (!good || nview < 3) return false;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) cs[j] += __shfl_xor_sync(0xFFFFFFFFu, cs[j], o);
+  const double cx = cs[0] / nview, cy = cs[1] / nview, cz = cs[2] / nview;
+  double md = 0.0;
+  for (int k = k0 + lane; k < k1; k += 32) {
+    const float* P = Pm + 12 * pair_v[k];
+    const double a = P[0], b = P[1], c = P[2], d = P[4], e = P[5], f = P[6], g = P[8], h = P[9], i = P[10];
+    const double det = a * (e * i - f * h) - b * (d * i - f * g) + c * (d * h - e * g);
+    const double p0 = P[3], p1 = P[7], p2 = P[11];
+    const double X = -((e * i - f * h) * p0 + (c * h - b * i) * p1 + (b * f - c * e) * p2) / det;
+    const double Y = -((f * g - d * i) * p0 + (a * i - c * g) * p1 + (c * d - a * f) * p2) / det;
+    const double Z = -((d * h - e * g) * p0 + (b * g - a * h) * p1 + (a * e - b * d) * p2) / det;
+    md += sqrt((X - cx) * (X - cx) + (Y - cy) * (Y - cy) + (Z - cz) * (Z - cz));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) md += __shfl_xor_sync(0xFFFFFFFFu, md, o);
+  md /= nview;
+  const double sc = md > 0.0 ? 1.0 / md : 1.0;
+  // A^T A: lane j < 100 owns entry j; every lane walks all rows (4 per view)
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // entries lane, lane + 32, lane + 64, lane + 96
+  for (int k = k0; k < k1; ++k) {
+    const float* P = Pm + 12 * pair_v[k];
+    const float* bb = obs + 4 * (int64_t)k;
+    for (int ed = 0; ed < 4; ++ed) {
+      const double l0 = ed < 2 ? 1.0 : 0.0, l1 = ed < 2 ? 0.0 : 1.0;
+      const double l2 = -(double)bb[ed == 0 ? 0 : ed == 1 ? 2 : ed == 2 ? 1 : 3];
+      double pi[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) pi[j] = l0 * P[j] + l1 * P[4 + j] + l2 * P[8 + j];
+      double pn[4] = {pi[0] / sc, pi[1] / sc, pi[2] / sc, pi[0] * cx + pi[1] * cy + pi[2] * cz + pi[3]};
+      const double nr = rsqrt(pn[0] * pn[0] + pn[1] * pn[1] + pn[2] * pn[2] + pn[3] * pn[3]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) pn[j] *= nr;
+      const double row[10] = {pn[0] * pn[0], 2 * pn[0] * pn[1], 2 * pn[0] * pn[2], 2 * pn[0] * pn[3], pn[1] * pn[1],
+                              2 * pn[1] * pn[2], 2 * pn[1] * pn[3], pn[2] * pn[2], 2 * pn[2] * pn[3], pn[3] * pn[3]};
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int e = lane + 32 * m;
+        if (e < 100) acc[m] += row[e / 10] * row[e % 10];
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int e = lane + 32 * m;
+    if (e < 100) AtA[e] = acc[m];
+  }
+  __syncwarp();
+  warp_jacobi(10, AtA, V, lane);
+  // smallest eigenvalue's vector
+  int kmin = 0;
+  for (int k = 1; k < 10; ++k)
+    if (AtA[k * 11] < AtA[kmin * 11]) kmin = k;
+  double q[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) q[k] = V[k * 10 + kmin];
+  // back to the world frame: Q* = Ti Q' Ti^T, Ti = [[I/sc, c], [0, 1]]
+  const double Qn[4][4] = {{q[0], q[1], q[2], q[3]}, {q[1], q[4], q[5], q[6]},
+                           {q[2], q[5], q[7], q[8]}, {q[3], q[6], q[8], q[9]}};
+  const double Ti[4][4] = {{1 / sc, 0, 0, cx}, {0, 1 / sc, 0, cy}, {0, 0, 1 / sc, cz}, {0, 0, 0, 1}};
+  double Q[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      double s2 = 0.0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int l = 0; l < 4; ++l) s2 += Ti[i][k] * Qn[k][l] * Ti[j][l];
+      Q[i][j] = s2;
+    }
+  if (fabs(Q[3][3]) < 1e-300) return false;
+  const double fs = -1.0 / Q[3][3];
+  const double t[3] = {-Q[0][3] * fs, -Q[1][3] * fs, -Q[2][3] * fs};
+  double* M = sm;  // reuse: 9 entries + 9 eigenvectors
+  double* E = sm + 16;
+  __syncwarp();
+  if (lane < 9) M[lane] = Q[lane / 3][lane % 3] * fs + t[lane / 3] * t[lane % 3];
+  __syncwarp();
+  warp_jacobi(3, M, E, lane);
+  int ord[3] = {0, 1, 2};
+  if (M[4 * ord[1]] > M[4 * ord[0]]) { const int x = ord[0]; ord[0] = ord[1]; ord[1] = x; }
+  if (M[4 * ord[2]] > M[4 * ord[1]]) { const int x = ord[1]; ord[1] = ord[2]; ord[2] = x; }
+  if (M[4 * ord[1]] > M[4 * ord[0]]) { const int x = ord[0]; ord[0] = ord[1]; ord[1] = x; }
+  double R[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) R[i][k] = E[3 * i + ord[k]];
+  const double dR = R[0][0] * (R[1][1] * R[2][2] - R[1][2] * R[2][1]) - R[0][1] * (R[1][0] * R[2][2] - R[1][2] * R[2][0]) +
+                    R[0][2] * (R[1][0] * R[2][1] - R[1][1] * R[2][0]);
+  if (dR < 0.0)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) R[i][2] = -R[i][2];
+  double rv[3];
+  rotmat_to_rotvec(R, rv);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    out[k] = (float)t[k];
+    out[3 + k] = (float)(0.5 * log(fmax(M[4 * ord[k]], 1e-6)));
+    out[6 + k] = (float)rv[k];
+  }
+  __syncwarp();
+  return true;
+}
+
+__global__ void __launch_bounds__(32 * kFitWarps) k_quadric_fit(int nq, int nv, const float* __restrict__ Pm,
+                                                                  const int32_t* __restrict__ q_ptr,
+                                                                  const int32_t* __restrict__ pair_v, int npairs,
+                                                                  const float* __restrict__ obs, int iters, float lr,
+                                                                  float* __restrict__ init_out,
+                                                                  float* __restrict__ params_out,
+                                                                  float* __restrict__ loss_out,
+                                                                  uint8_t* __restrict__ ok_out) {
+  __shared__ double sm[kFitWarps][200];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = blockIdx.x * kFitWarps + w;
+  if (q >= nq) return;
+  const int k0 = max(q_ptr[q], 0), k1 = min(q_ptr[q + 1], npairs);
+  float p[9];
+  const bool good = warp_quadric_init(k0, k1, Pm, pair_v, obs, nv, sm[w], lane, p);
+  if (lane == 0 && ok_out) ok_out[q] = good ? 1 : 0;
+  if (!good) {
+    if (lane < 9) {
+      if (init_out) init_out[9 * q + lane] = 0.f;
+      if (params_out) params_out[9 * q + lane] = 0.f;
+    }
+    if (lane == 0 && loss_out) loss_out[q] = 0.f;
+    return;
+  }
+  if (init_out && lane < 9) init_out[9 * q + lane] = p[lane];
+  // refinement: Adam on the Eq. 12 loss, every lane holding the parameters
+  float m[9], v[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) m[k] = v[k] = 0.f;
+  float b1t = 1.f, b2t = 1.f, L = 0.f;
+  for (int it = 0; it <= iters; ++it) {
+    float g[9], l = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) g[k] = 0.f;
+    for (int k = k0 + lane; k < k1; k += 32) {
+      const int vw = pair_v[k];
+      PairFwd f;
+      pair_forward(p, Pm + 12 * vw, f);
+      if (!f.valid) continue;
+      l += pair_loss_grad(Pm + 12 * vw, p, obs + 4 * (int64_t)k, f, g);
+    }
+    L = warp_sum(l);
+    if (it == iters) break;  // the last pass only evaluates the final loss
+#pragma unroll
+    for (int k = 0; k < 9; ++k) g[k] = warp_sum(g[k]);
+    b1t *= 0.9f;
+    b2t *= 0.999f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      m[k] = 0.9f * m[k] + 0.1f * g[k];
+      v[k] = 0.999f * v[k] + 0.001f * g[k] * g[k];
+      const float mh = m[k] / (1.f - b1t), vh = v[k] / (1.f - b2t);
+      p[k] -= lr * mh / (sqrtf(vh) + 1e-8f);
+    }
+  }
+  if (params_out && lane < 9) params_out[9 * q + lane] = p[lane];
+  if (lane == 0 && loss_out) loss_out[q] = L;
+}
+
 }  // namespace
+
+cudaError_t launch_quadric_fit(int nq, int nv, const float* P, const int32_t* q_ptr, const int32_t* pair_v,
+                               int npairs, const float* obs, int iters, float lr, float* init, float* params,
+                               float* loss, uint8_t* ok, cudaStream_t s) {
+  if (nq == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((nq + kFitWarps - 1) / kFitWarps);
+  k_quadric_fit<<<blocks, 32 * kFitWarps, 0, s>>>(nq, nv, P, q_ptr, pair_v, npairs, obs, iters, lr, init, params,
+                                                 loss, ok);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_quadric_project(int nq, const float* params, int nv, const float* P, const int32_t* q_ptr,
                                    const int32_t* pair_v, int npairs, float* conic, float* bbox, uint8_t* valid,

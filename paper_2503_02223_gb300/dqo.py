@@ -29,7 +29,7 @@ PHASES = ("project", "depth_sort", "binning", "blend_fwd", "blend_bwd", "project
 class dqo_settings(C.Structure):
     _fields_ = [("tile_w", c_i32), ("tile_h", c_i32), ("alpha_clamp", c_f), ("alpha_min", c_f), ("t_stop", c_f),
                 ("znear", c_f), ("lowpass", c_f), ("radius_sigma", c_f), ("lambda_ins", c_f), ("bg", c_f * 3),
-                ("og_filter", c_i32), ("batch", c_i32)]
+                ("og_filter", c_i32), ("batch", c_i32), ("theta_alpha", c_f), ("theta_d", c_f), ("theta_c", c_f)]
 
 
 class dqo_camera(C.Structure):
@@ -47,7 +47,8 @@ class dqo_targets(C.Structure):
 
 
 class dqo_render_out(C.Structure):
-    _fields_ = [("rgb", c_p), ("depth", c_p), ("alpha", c_p), ("ins", c_p), ("id_map", c_p), ("loss", c_p)]
+    _fields_ = [("rgb", c_p), ("depth", c_p), ("alpha", c_p), ("ins", c_p), ("id_map", c_p), ("loss", c_p),
+                ("update_mask", c_p)]
 
 
 class dqo_pixel_grads(C.Structure):
@@ -76,6 +77,7 @@ _SIGS = {
     "dqo_depth_order_noalloc": (c_i32, [c_p, c_i64, c_p, c_p]),
     "dqo_quadric_project": (c_i32, [c_p, c_i32, c_p, c_i32, c_p, c_p, c_p, c_i32, c_p, c_p, c_p, c_p]),
     "dqo_quadric_bbox_loss": (c_i32, [c_p, c_i32, c_p, c_i32, c_p, c_p, c_p, c_i32, c_p, c_p, c_p, c_p]),
+    "dqo_quadric_fit": (c_i32, [c_p, c_i32, c_i32, c_p, c_p, c_p, c_i32, c_p, c_i32, c_f, c_p, c_p, c_p, c_p, c_p]),
 }
 
 _lib = None
@@ -192,7 +194,7 @@ def targets(t: dict | None):
 
 def render_out(o: dict) -> dqo_render_out:
     s = dqo_render_out()
-    for k in ("rgb", "depth", "alpha", "ins", "id_map", "loss"):
+    for k in ("rgb", "depth", "alpha", "ins", "id_map", "loss", "update_mask"):
         setattr(s, k, _ptr(o.get(k)))
     return s
 
@@ -320,6 +322,16 @@ def dqo_quadric_bbox_loss(ctx: Context, params, P, q_ptr, pair_v, obs, loss=None
                                      _stream(stream)), ctx.handle)
 
 
+def dqo_quadric_fit(ctx: Context, P, q_ptr, pair_v, obs, iters=100, lr=1e-2, init=None, params=None, loss=None,
+                    ok=None, stream=None):
+    lib = load()
+    nq = q_ptr.shape[0] - 1
+    _check("dqo_quadric_fit",
+           lib.dqo_quadric_fit(ctx.handle, nq, P.shape[0], _ptr(P), _ptr(q_ptr), _ptr(pair_v), pair_v.shape[0],
+                               _ptr(obs), iters, lr, _ptr(init), _ptr(params), _ptr(loss), _ptr(ok),
+                               _stream(stream)), ctx.handle)
+
+
 # ------------------------------------------------------------------------ conveniences
 
 def to_device(arrays: dict, device="cuda") -> dict:
@@ -335,7 +347,7 @@ def to_device(arrays: dict, device="cuda") -> dict:
     return out
 
 
-def alloc_outputs(W: int, H: int, device="cuda", loss=True, id_map=True) -> dict:
+def alloc_outputs(W: int, H: int, device="cuda", loss=True, id_map=True, mask=False) -> dict:
     f = dict(dtype=torch.float32, device=device)
     o = dict(rgb=torch.empty(H, W, 3, **f), depth=torch.empty(H, W, **f), alpha=torch.empty(H, W, **f),
              ins=torch.empty(H, W, **f))
@@ -343,6 +355,8 @@ def alloc_outputs(W: int, H: int, device="cuda", loss=True, id_map=True) -> dict
         o["id_map"] = torch.empty(H, W, dtype=torch.int32, device=device)
     if loss:
         o["loss"] = torch.zeros(4, **f)
+    if mask:
+        o["update_mask"] = torch.empty(H, W, dtype=torch.uint8, device=device)
     return o
 
 

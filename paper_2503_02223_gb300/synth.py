@@ -458,3 +458,32 @@ def raycast_targets(kf: dict) -> dict:
     return dict(rgb=np.ascontiguousarray(col.reshape(H, W, 3), np.float32),
                 depth=np.ascontiguousarray(depth.reshape(H, W), np.float32),
                 gt_id=np.ascontiguousarray(gid.reshape(H, W), np.int32))
+
+
+def batched_quadric_fits(seed: int, nq: int = 512, min_views: int = 3, max_views: int = 40,
+                         noise_px: float = 2.0, f: float = 525.0, width: int = 640, height: int = 480,
+                         radius: float = 3.5, surface_points: int = 1024) -> dict:
+    """nq ellipsoids (axes U[0.1,0.5], centres U[-1,1]^3, random rotation), each seen from
+    U{min_views..max_views} views on a sphere of `radius` around the origin; observed boxes =
+    box of projected surface samples + N(0, noise^2).  CSR pairs, one view per pair."""
+    rng = rng_for(seed)
+    params, centres, axes, Rs = random_quadrics(rng, nq)
+    counts = rng.integers(min_views, max_views + 1, nq)
+    K = intrinsics(f, f, width / 2.0, height / 2.0)
+    Ps, obs = [], []
+    for k in range(nq):
+        pts = ellipsoid_surface_points(centres[k], axes[k], Rs[k], surface_points)
+        got = 0
+        while got < counts[k]:
+            P = K @ sphere_views(rng, 1, radius=radius)[0]
+            bb = sampled_bbox(P, pts)
+            if bb is None:
+                continue
+            Ps.append(P)
+            obs.append(bb + rng.normal(0.0, noise_px, 4))
+            got += 1
+    q_ptr = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    return dict(params_true=params.astype(np.float32),
+                P=np.ascontiguousarray(np.stack(Ps, 0), np.float32), q_ptr=q_ptr,
+                pair_v=np.arange(len(Ps), dtype=np.int32),
+                obs_bbox=np.ascontiguousarray(np.stack(obs, 0), np.float32), counts=counts)

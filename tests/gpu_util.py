@@ -121,4 +121,6 @@ def assert_grads_close(got: dict, ref: dict, keys=("means", "log_scales", "quats
             report[k] = dict(bad=int(bad.sum()), norm=float(nrm), unc_norm=float(unrm),
                              worst=float((err / (base + un)).max()), widened=float((un > base).mean()))
         assert nrm <= rel + unrm, (k, nrm, unrm)
-        assert not bad.any(), (k, int(bad.sum()), float((err / (base + un)).max()))
+        worst = int(np.argmax(err / (base + un)))
+        assert not bad.any(), (k, int(bad.sum()), float((err / (base + un)).max()),
+                               int(np.nonzero(keep)[0][worst]), r[worst].tolist(), g[worst].tolist())

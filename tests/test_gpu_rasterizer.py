@@ -250,3 +250,20 @@ def test_indoor_keyframe_full_size_parity():
     # the uncertainty allowance widens the tolerance of few elements
     assert all(v["widened"] < 0.05 for v in report.values()), report
     r.close()
+
+
+def test_update_masks_eq11():
+    # Mask_geo / Mask_rgb of Eq. 11 fused into the blend epilogue, against the oracle
+    # (pixels within 1e-4 of a mask threshold or flagged for the render are left out)
+    g, cam, t = tiny_case(seed=1041)
+    st_kw = dict(theta_alpha=0.6, theta_d=0.1, theta_c=0.1)
+    r = Render(g, cam, 4, t, **st_kw)
+    r.out["update_mask"] = torch.empty(cam["height"], cam["width"], dtype=torch.uint8, device="cuda")
+    out = r.forward()
+    ref = oracle.render(g, cam, oracle_settings(4, **st_kw), t)
+    ok = (ref["amb"] == 0) & (ref["mask_amb"] == 0)
+    assert ok.mean() > 0.97
+    assert np.array_equal(out["update_mask"][ok], ref["update_mask"][ok])
+    assert (ref["update_mask"] & 1).any() and (ref["update_mask"] & 2).any() and (ref["update_mask"] == 0).any()
+    assert np.all(out["update_mask"][t["gt_id"] < 0] == 0)
+    r.close()
