@@ -46,6 +46,13 @@ FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # FMA =
 FLOPS_PER_EVAL = {"blend_fwd": 25, "blend_bwd": 55}
 FIT_ITERS = 100
 KERNEL_SRC = {"blend_fwd": "k_blend.cu", "blend_bwd": "k_blend.cu"}
+# Learned proposal: algorithmic flops per sample of one training step (FMA = 2): forward
+# 2 (128*128 + 128*128 + 9*128); backward dH2 and dW3 2 (9*128) each, dH1, dW2, dW1
+# 2 (128*128) each.
+MLP_FLOPS_PER_SAMPLE = 2 * (128 * 128 + 128 * 128 + 9 * 128) + 2 * (2 * 9 * 128 + 3 * 128 * 128)
+MLP_TRAIN_SAMPLES = 1 << 20
+MLP_EPOCHS = 10
+MLP_BATCH = 4096
 
 
 def parse():
@@ -57,7 +64,16 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--tile", default="16x16")
     p.add_argument("--batch", type=int, default=256)
+    p.add_argument("--no-learned", action="store_true", help="skip the learned-proposal section")
     return p.parse_args()
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -364,6 +380,9 @@ def run_ours(args, rank, world, local_rank):
             "iters": FIT_ITERS, "form": "plain: Eq. 1 SVD init + 100 Adam steps, one launch",
             "ok_fraction": float(f_ok.float().mean().item())}
 
+    if not args.no_learned:
+        fits["learned"] = learned_section(ctx, dev, stream, world, fd, nfit, fit_ms)
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -383,6 +402,73 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
+
+
+def learned_section(ctx, dev, stream, world, fd, nfit, plain_fit_ms):
+    """Learned quadric proposal: train the network on 1M samples with the library's tensor-core
+    kernels (one CUDA graph per epoch), then fit the 512-quadric batch from its proposals."""
+    import numpy as np
+    import torch
+
+    from paper_2503_02223_gb300 import dqo, proposal, synth
+    t0 = time.perf_counter()
+    s = synth.proposal_samples(SEED + 3, MLP_TRAIN_SAMPLES)
+    gen_s = time.perf_counter() - t0
+    d = dqo.to_device({k: s[k] for k in ("P", "q_ptr", "pair_v", "obs_bbox")}, dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    labels, ok = proposal.make_labels(ctx, d)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    label_ms = e0.elapsed_time(e1)
+    st = dqo.MlpState(dev)
+    dqo.dqo_mlp_set_params(st, torch.from_numpy(synth.mlp_init_params(SEED + 3)).to(dev))
+    tr = proposal.Trainer(ctx, st, d, labels, batch=MLP_BATCH, epochs=MLP_EPOCHS, length_scale=s["length_scale"],
+                          lr=2e-3, lr_final=1e-5)
+    first = tr.epoch()                         # eager epoch, then captured
+    torch.cuda.synchronize()
+    e0.record(stream)
+    hist = [tr.epoch() for _ in range(MLP_EPOCHS - 1)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1) / (MLP_EPOCHS - 1)
+    samples = tr.steps * MLP_BATCH
+    flops = MLP_FLOPS_PER_SAMPLE * samples
+    peaks = measured_peaks()
+    peak = peaks.get("bf16_tflops_sustained")
+    achieved = flops / (train_ms * 1e-3) / 1e12
+    # the 512-fit batch: proposal from the first <= 8 views + the same 100 refinement steps
+    reps = 20
+
+    def learned_call():
+        prop = proposal.propose(ctx, st, fd, length_scale=s["length_scale"])
+        return proposal.fit(ctx, fd, start=prop)
+
+    for _ in range(3):
+        learned_call()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        out = learned_call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    learned_ms = e0.elapsed_time(e1) / reps
+    plain = proposal.fit(ctx, fd)
+    return {"value": world * nfit / (learned_ms * 1e-3), "unit": "fits/s", "ms_per_batch": learned_ms,
+            "vs_plain_speed": plain_fit_ms / learned_ms,
+            "mean_bbox_loss": float(out["loss"].mean().item()),
+            "plain_mean_bbox_loss": float(plain["loss"].mean().item()),
+            "form": "features + BF16 MLP proposal (tcgen05) + 100 Adam steps from it, 4 launches",
+            "training": {"samples": samples, "epochs": MLP_EPOCHS, "batch": MLP_BATCH,
+                         "ms_per_epoch": train_ms, "samples_per_s": samples / (train_ms * 1e-3),
+                         "loss_first_epoch": first, "loss_last_epoch": hist[-1],
+                         "label_fits_ms": label_ms, "label_fits_ok": float(ok.float().mean().item()),
+                         "generation_s_host": gen_s,
+                         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                      "frac": achieved / peak if peak else None,
+                                      "peak_basis": "measured bf16 cuBLAS sustained (MEASURED_PEAKS.json)",
+                                      "flops_per_sample": MLP_FLOPS_PER_SAMPLE,
+                                      "traffic": None}}}
 
 
 def main():

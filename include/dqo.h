@@ -300,14 +300,102 @@ DQO_API dqo_status dqo_quadric_bbox_loss(dqo_ctx* ctx, int32_t nq, const float* 
  *   a^2 >= 1e-6 m^2, det R = +1).
  *   Refinement: `iters` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, step `lr`) on the
  *   bbox loss of dqo_quadric_bbox_loss (fp32).
+ * start [nq,9] (device, may be NULL): if given, the refinement starts from these
+ * parameters instead of the initialisation (any quadric with at least one view is ok; init
+ * then holds the start).
  * Pairs in CSR as in dqo_quadric_project.  Outputs (device, each may be NULL): init [nq,9]
  * and params [nq,9] in the dqo_quadric_project parameterisation, loss [nq] at the final
  * parameters, ok [nq] (0 if fewer than 3 views or a degenerate system: zeros written).
  * Errors: DQO_EINVAL (nq < 0, iters < 0, NULL required arrays), DQO_ECUDA. */
 DQO_API dqo_status dqo_quadric_fit(dqo_ctx* ctx, int32_t nq, int32_t nv, const float* P, const int32_t* q_ptr,
                                    const int32_t* pair_v, int32_t npairs, const float* obs_bbox, int32_t iters,
-                                   float lr, float* init, float* params, float* loss, uint8_t* ok,
+                                   float lr, const float* start, float* init, float* params, float* loss,
+                                   uint8_t* ok, dqo_stream stream);
+
+/* Canonical parameters of each quadric (same ellipsoid, same Q*): semi-axes in descending
+ * order (equal axes keep their order), the rotation's columns permuted with them (the third
+ * negated if needed for det +1), and of the four rotations that differ by negating two
+ * columns, the one with the largest trace.  The learned proposal regresses this form.
+ * params, out: device [nq,9] (may alias).  Errors: DQO_EINVAL, DQO_ECUDA. */
+DQO_API dqo_status dqo_quadric_canonical(int32_t nq, const float* params, float* out, dqo_stream stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Learned quadric proposal.  The paper initialises each quadric geometrically (Eq. 1);
+ * this small network proposes the initial value from up to 8 views instead, including
+ * from 2 views, where the Eq. 1 system is underdetermined, and dqo_quadric_fit (start =
+ * the proposal) refines it on the Eq. 12 loss.  The plain fit stays the fallback and the
+ * reference its error is measured against.
+ * Network: 128 features -> 128 -> 128 -> 9 (ReLU after the two hidden layers), output =
+ * canonical quadric parameters (dqo_quadric_canonical).  BF16 operands (features, weights,
+ * activations, output gradients), FP32 accumulation on the tensor cores, FP32 biases,
+ * master weights and Adam state.
+ * BF16 arrays cross this interface as uint16_t (the bit pattern of bfloat16).
+ * ------------------------------------------------------------------------------------- */
+
+#define DQO_MLP_FEATURES 128
+#define DQO_MLP_PARAMS 35088
+/* Parameter vector (fp32, DQO_MLP_PARAMS): W1 [128][128] (row = output unit), b1 [128],
+ * W2 [128][128], b2 [128], W3 [16][128] (rows 9..15 must be zero), b3 [16] (9..15 zero). */
+
+typedef struct dqo_mlp_hparams {
+  float lr;              /* Adam step at the start of the cosine schedule */
+  float lr_final;        /* ... and at step total_steps and after */
+  int64_t total_steps;   /* schedule length (<= 0: constant lr) */
+  float beta1, beta2, eps;
+  float loss_w[9];       /* per-output weights of the squared error */
+} dqo_mlp_hparams;
+
+/* Features of each quadric (device in, device out): view slot j < min(counts[q] (or 8 if
+ * counts is NULL), views of q, 8) holds the j-th view of q in its CSR list; later slots
+ * are zero.  For a slot, P = K [R | t] (K upper triangular with positive diagonal; the
+ * overall scale and sign of P are normalised) gives camera axes r1, r2, r3 (rows of R)
+ * and centre C = -R^T t; with the box centre in normalised image coordinates (xn, yn),
+ * its half-extents (hw, hh) = ((u1-u0)/(2 fx), (v1-v0)/(2 fy)) and d the unit direction of
+ * the ray through the box centre (xn r1 + yn r2 + r3, normalised), the slot is
+ *   [xn, yn, hw, hh, r1, r2, d, C / length_scale]      (4 + 12 values).
+ * X [nq][128] BF16; XT [128][ldt] BF16 (may be NULL), XT[f][q] = X[q][f]; ldt >= nq and a
+ * multiple of 8.  Errors: DQO_EINVAL (bad sizes, NULL, length_scale <= 0), DQO_ECUDA. */
+DQO_API dqo_status dqo_mlp_features(int32_t nq, int32_t nv, const float* P, const int32_t* q_ptr,
+                                    const int32_t* pair_v, int32_t npairs, const float* obs_bbox,
+                                    const int32_t* counts, float length_scale, uint16_t* X, uint16_t* XT,
+                                    int64_t ldt, dqo_stream stream);
+
+/* Size in bytes of an MLP state buffer (parameters, gradient, Adam moments, BF16 weight
+ * copies, step count).  The caller allocates it on the device (256-byte aligned). */
+DQO_API size_t dqo_mlp_state_bytes(void);
+/* params (device, fp32 DQO_MLP_PARAMS) -> state; resets the Adam moments and step count. */
+DQO_API dqo_status dqo_mlp_set_params(void* state, const float* params, dqo_stream stream);
+/* state -> params (device, fp32 DQO_MLP_PARAMS). */
+DQO_API dqo_status dqo_mlp_get_params(const void* state, float* params, dqo_stream stream);
+
+/* Proposal for n quadrics: X [n][128] BF16 (device) -> out [n][9] fp32 (device). */
+DQO_API dqo_status dqo_mlp_forward(dqo_ctx* ctx, const void* state, int64_t n, const uint16_t* X, float* out,
                                    dqo_stream stream);
+
+/* Loss L = (1/n) sum_rows sum_j loss_w[j] (y_j - labels_j)^2 of a batch and its gradient
+ * w.r.t. the parameter vector.  n > 0, n % 128 == 0.  X [n][128] BF16; XT [128][ldxt]
+ * BF16 (its first n columns are this batch, XT[f][q] = X[q][f]); labels [n][9] fp32;
+ * loss_w: 9 host floats.  grads (device, DQO_MLP_PARAMS) and loss (device, 1 float) are
+ * OVERWRITTEN.  Backward precision: dL/dy rounded to BF16, hidden-layer gradients rounded
+ * to BF16 after the ReLU derivative (the activation > 0).
+ * Errors: DQO_EINVAL, DQO_ECUDA (a tensor-core wait that ran out is reported by
+ * dqo_mlp_check). */
+DQO_API dqo_status dqo_mlp_gradients(dqo_ctx* ctx, void* state, int64_t n, const uint16_t* X, const uint16_t* XT,
+                                     int64_t ldxt, const float* labels, const float* loss_w, float* grads,
+                                     float* loss, dqo_stream stream);
+
+/* One Adam step on a batch (as dqo_mlp_gradients, then the update; the learning rate
+ * follows hp's cosine schedule at the state's step count).  loss (device, 1 float) is
+ * OVERWRITTEN with the batch loss before the update; may be NULL.  Allocates nothing once
+ * the context has seen a batch of this size, so a sequence of steps can be captured in a
+ * CUDA graph after one call.  Errors: as dqo_mlp_gradients. */
+DQO_API dqo_status dqo_mlp_train_step(dqo_ctx* ctx, void* state, const dqo_mlp_hparams* hp, int64_t n,
+                                      const uint16_t* X, const uint16_t* XT, int64_t ldxt, const float* labels,
+                                      float* loss, dqo_stream stream);
+
+/* Error flag of the last tensor-core kernels on this context (1 if a completion wait ran
+ * out), read synchronously and cleared. */
+DQO_API dqo_status dqo_mlp_check(dqo_ctx* ctx, int* timed_out);
 
 #ifdef __cplusplus
 }

@@ -68,6 +68,12 @@ def _lib_handle():
                                                _P, _P, _P, _P, _P, _P]
             lib.oracle_jacobi_eigen.argtypes = [C.c_int, _P, _P]
             lib.oracle_rot_to_rotvec.argtypes = [_P, _P]
+            lib.oracle_round_bf16.argtypes = [C.c_double]
+            lib.oracle_round_bf16.restype = C.c_double
+            lib.oracle_mlp_features.argtypes = [C.c_int, C.c_int, _P, _P, _P, _P, _P, C.c_double, _P]
+            lib.oracle_mlp_forward.argtypes = [i64, _P, _P, C.c_int, _P, _P, _P]
+            lib.oracle_mlp_backward.argtypes = [i64, _P, _P, _P, _P, C.c_int, _P, _P]
+            lib.oracle_quadric_canonical.argtypes = [C.c_int, _P, _P]
             _lib = lib
     return _lib
 
@@ -302,3 +308,84 @@ def rot_to_rotvec(R):
     r = np.zeros(3)
     _lib_handle().oracle_rot_to_rotvec(_ptr(R), _ptr(r))
     return r
+
+
+# ------------------------------------------------------------------------- learned proposal
+# (an addition to the paper's method: a network proposes each quadric's initial value,
+# refined by the Eq. 12 fit; FP64 with bfloat16 rounding at the kernels' rounding points)
+
+MLP_PARAMS = 35088
+MLP_LAYOUT = {"W1": (0, (128, 128)), "b1": (16384, (128,)), "W2": (16512, (128, 128)), "b2": (32896, (128,)),
+              "W3": (33024, (16, 128)), "b3": (35072, (16,))}
+
+
+def round_bf16(x) -> np.ndarray:
+    """Nearest bfloat16 value of each element (ties to even), as float64."""
+    f = _lib_handle().oracle_round_bf16
+    a = _d(x)
+    return np.array([f(float(v)) for v in a.reshape(-1)]).reshape(a.shape)
+
+
+def mlp_features(P, q_ptr, pair_v, obs, counts=None, length_scale: float = 1.0) -> np.ndarray:
+    """Features [nq][128] of the learned proposal (FP64, unrounded): per view slot
+    [xn, yn, hw, hh, r1, r2, d, C / length_scale] from P = K [R | t] and the box."""
+    P = _d(P).reshape(-1, 12)
+    q_ptr = np.ascontiguousarray(q_ptr, np.int32)
+    pair_v = np.ascontiguousarray(pair_v, np.int32)
+    obs = _d(obs).reshape(-1, 4)
+    nq = q_ptr.shape[0] - 1
+    F = np.zeros((nq, 128))
+    cnt = None if counts is None else np.ascontiguousarray(counts, np.int32)
+    rc = _lib_handle().oracle_mlp_features(nq, P.shape[0], _ptr(P), _ptr(q_ptr), _ptr(pair_v), _ptr(obs),
+                                           _ptr(cnt), 1.0 / length_scale, _ptr(F))
+    if rc:
+        raise ValueError("oracle_mlp_features: view index out of range")
+    return F
+
+
+def mlp_forward(X, params, round_bf16_points: bool = True) -> dict:
+    """y [n][9] and hidden activations h1, h2 [n][128] of the network for inputs X [n][128]."""
+    X = _d(X).reshape(-1, 128)
+    prm = _d(params).reshape(-1)
+    n = X.shape[0]
+    out = dict(y=np.zeros((n, 9)), h1=np.zeros((n, 128)), h2=np.zeros((n, 128)))
+    _lib_handle().oracle_mlp_forward(n, _ptr(X), _ptr(prm), int(round_bf16_points), _ptr(out["y"]),
+                                     _ptr(out["h1"]), _ptr(out["h2"]))
+    return out
+
+
+def mlp_backward(X, labels, loss_w, params, round_bf16_points: bool = True):
+    """(gradient [35088], loss) of (1/n) sum w_j (y_j - label_j)^2."""
+    X = _d(X).reshape(-1, 128)
+    lab = _d(labels).reshape(-1, 9)
+    w = _d(loss_w).reshape(9)
+    prm = _d(params).reshape(-1)
+    g = np.zeros(MLP_PARAMS)
+    loss = np.zeros(1)
+    _lib_handle().oracle_mlp_backward(X.shape[0], _ptr(X), _ptr(lab), _ptr(w), _ptr(prm), int(round_bf16_points),
+                                      _ptr(g), _ptr(loss))
+    return g, float(loss[0])
+
+
+def mlp_adam(params, grads, m, v, step: int, lr: float, lr_final: float = 0.0, total_steps: int = 0,
+             beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+    """One Adam step (Kingma & Ba, bias-corrected; `step` counts this step, from 1) with the
+    learning rate on a cosine schedule from lr to lr_final over total_steps (constant if
+    total_steps <= 0).  Returns (params, m, v)."""
+    g = _d(grads)
+    m = beta1 * _d(m) + (1 - beta1) * g
+    v = beta2 * _d(v) + (1 - beta2) * g * g
+    prog = min((step - 1) / total_steps, 1.0) if total_steps > 0 else 0.0
+    a = lr_final + 0.5 * (lr - lr_final) * (1 + np.cos(np.pi * prog))
+    mh = m / (1 - beta1 ** step)
+    vh = v / (1 - beta2 ** step)
+    return _d(params) - a * mh / (np.sqrt(vh) + eps), m, v
+
+
+def quadric_canonical(params) -> np.ndarray:
+    """Canonical parameters of each quadric (same ellipsoid; axes descending, rotation of
+    largest trace among the equivalent ones)."""
+    p = _d(params).reshape(-1, 9)
+    out = np.zeros_like(p)
+    _lib_handle().oracle_quadric_canonical(p.shape[0], _ptr(p), _ptr(out))
+    return out

@@ -1338,3 +1338,251 @@ int oracle_quadric_fit(int nq, int nv, const double* P, const int32_t* q_ptr, co
 }
 
 }  // extern "C"
+
+// ============================================================================ learned proposal
+//
+// FP64 reference of the learned quadric proposal (an addition to the paper's method: a
+// small network proposes the quadric's initial value, which the Eq. 12 refinement then
+// fits).  Rounding to bfloat16 happens at the same points as in the kernels (weights,
+// hidden activations, the output gradient and the hidden-layer gradients) unless `rb` is
+// 0, which gives the plain FP64 network the finite-difference pins differentiate.
+
+namespace {
+
+// Nearest bfloat16 value (8 significant bits, ties to even; fp32 exponent range).
+double round_bf16(double x) {
+    if (x == 0 || !std::isfinite(x)) return x;
+    int e;
+    const double m = std::frexp(x, &e);  // x = m 2^e, 0.5 <= |m| < 1
+    int bits = 8;
+    if (e < -125) bits = std::max(0, 8 - (-125 - e));  // subnormal: spacing 2^-133
+    return std::ldexp(std::nearbyint(std::ldexp(m, bits)), e - bits);
+}
+
+constexpr int MI = 128, MH = 128, MO = 9, MOP = 16;
+constexpr int OW1 = 0, OB1 = 16384, OW2 = 16512, OB2 = 32896, OW3 = 33024, OB3 = 35072, OPARAMS = 35088;
+
+// Upper-triangular K (positive diagonal, K22 = 1) and rotation R with M = lambda K R, from
+// M M^T = lambda^2 K K^T: Cholesky of the row- and column-reversed matrix.
+bool camera_from_P(const double P[12], double K[3][3], double R[3][3], double t[3]) {
+    double M[3][3], p[3];
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) M[i][j] = P[4 * i + j];
+        p[i] = P[4 * i + 3];
+    }
+    double A[3][3];  // A = J M M^T J, J the reversal
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0;
+            for (int k = 0; k < 3; ++k) s += M[2 - i][k] * M[2 - j][k];
+            A[i][j] = s;
+        }
+    double L[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = A[i][j];
+            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+            if (i == j) {
+                if (!(s > 0)) return false;
+                L[i][i] = std::sqrt(s);
+            } else {
+                L[i][j] = s / L[j][j];
+            }
+        }
+    // K = J L J is upper triangular with K K^T = M M^T
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) K[i][j] = L[2 - i][2 - j];
+    const double lam = K[2][2];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) K[i][j] /= lam;
+    // R = K^-1 M / lambda (back substitution), sign fixed by det R = +1
+    double Ki[3][3];
+    Ki[2][2] = 1; Ki[2][1] = 0; Ki[2][0] = 0; Ki[1][0] = 0; Ki[0][0] = 1 / K[0][0]; Ki[1][1] = 1 / K[1][1];
+    Ki[1][2] = -K[1][2] / K[1][1];
+    Ki[0][1] = -K[0][1] / (K[0][0] * K[1][1]);
+    Ki[0][2] = (K[0][1] * K[1][2] - K[0][2] * K[1][1]) / (K[0][0] * K[1][1]);
+    double sg = 1;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double s = 0;
+                for (int k = 0; k < 3; ++k) s += Ki[i][k] * M[k][j];
+                R[i][j] = sg * s / lam;
+            }
+        const double det = R[0][0] * (R[1][1] * R[2][2] - R[1][2] * R[2][1]) -
+                           R[0][1] * (R[1][0] * R[2][2] - R[1][2] * R[2][0]) +
+                           R[0][2] * (R[1][0] * R[2][1] - R[1][1] * R[2][0]);
+        if (det > 0) break;
+        sg = -1;
+    }
+    for (int i = 0; i < 3; ++i) {
+        double s = 0;
+        for (int k = 0; k < 3; ++k) s += Ki[i][k] * p[k];
+        t[i] = sg * s / lam;
+    }
+    return true;
+}
+
+void mlp_forward_one(const double* x, const double* prm, bool rb, double* h1, double* h2, double* y) {
+    auto W = [&](int off, int o, int i, int ld) { const double w = prm[off + o * ld + i]; return rb ? round_bf16(w) : w; };
+    for (int o = 0; o < MH; ++o) {
+        double z = prm[OB1 + o];
+        for (int i = 0; i < MI; ++i) z += W(OW1, o, i, MI) * x[i];
+        const double h = std::max(z, 0.0);
+        h1[o] = rb ? round_bf16(h) : h;
+    }
+    for (int o = 0; o < MH; ++o) {
+        double z = prm[OB2 + o];
+        for (int i = 0; i < MH; ++i) z += W(OW2, o, i, MH) * h1[i];
+        const double h = std::max(z, 0.0);
+        h2[o] = rb ? round_bf16(h) : h;
+    }
+    for (int o = 0; o < MO; ++o) {
+        double z = prm[OB3 + o];
+        for (int i = 0; i < MH; ++i) z += W(OW3, o, i, MH) * h2[i];
+        y[o] = z;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+double oracle_round_bf16(double x) { return round_bf16(x); }
+
+// Features of the learned proposal (FP64, not rounded): per quadric 8 view slots of
+// [xn, yn, hw, hh, r1, r2, d, C * inv_scale]; see dqo_mlp_features for the definition.
+int oracle_mlp_features(int nq, int nv, const double* P, const int32_t* q_ptr, const int32_t* pair_v,
+                        const double* obs, const int32_t* counts, double inv_scale, double* F) {
+    for (int q = 0; q < nq; ++q) {
+        const int k0 = q_ptr[q], k1 = q_ptr[q + 1];
+        int use = std::min(k1 - k0, 8);
+        if (counts) use = std::min(use, (int)counts[q]);
+        for (int j = 0; j < 8; ++j) {
+            double* f = F + (int64_t)q * MI + 16 * j;
+            for (int k = 0; k < 16; ++k) f[k] = 0;
+            if (j >= use) continue;
+            const int v = pair_v[k0 + j];
+            if (v < 0 || v >= nv) return 1;
+            double K[3][3], R[3][3], t[3];
+            if (!camera_from_P(P + 12 * v, K, R, t)) continue;
+            const double* b = obs + 4 * (int64_t)(k0 + j);
+            const double uc = 0.5 * (b[0] + b[2]), vc = 0.5 * (b[1] + b[3]);
+            // normalised coordinates = K^-1 (uc, vc, 1)
+            const double yn = (vc - K[1][2]) / K[1][1];
+            const double xn = (uc - K[0][2] - K[0][1] * yn) / K[0][0];
+            f[0] = xn;
+            f[1] = yn;
+            f[2] = (b[2] - b[0]) / (2 * K[0][0]);
+            f[3] = (b[3] - b[1]) / (2 * K[1][1]);
+            double d[3];
+            for (int k = 0; k < 3; ++k) d[k] = R[0][k] * xn + R[1][k] * yn + R[2][k];  // R^T (xn, yn, 1)
+            const double dn = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            for (int k = 0; k < 3; ++k) {
+                f[4 + k] = R[0][k];
+                f[7 + k] = R[1][k];
+                f[10 + k] = d[k] / dn;
+                f[13 + k] = -(R[0][k] * t[0] + R[1][k] * t[1] + R[2][k] * t[2]) * inv_scale;
+            }
+        }
+    }
+    return 0;
+}
+
+// Network outputs y [n][9] (and the hidden activations h1, h2 [n][128], each may be NULL)
+// for inputs X [n][128] and the parameter vector prm (layout of dqo_mlp_features' network).
+int oracle_mlp_forward(int64_t n, const double* X, const double* prm, int rb, double* y, double* h1, double* h2) {
+    std::vector<double> a(MH), b(MH);
+    for (int64_t s = 0; s < n; ++s) {
+        double yy[MO];
+        mlp_forward_one(X + s * MI, prm, rb != 0, a.data(), b.data(), yy);
+        if (y) for (int k = 0; k < MO; ++k) y[s * MO + k] = yy[k];
+        if (h1) for (int k = 0; k < MH; ++k) h1[s * MH + k] = a[k];
+        if (h2) for (int k = 0; k < MH; ++k) h2[s * MH + k] = b[k];
+    }
+    return 0;
+}
+
+// Loss (1/n) sum_s sum_j w_j (y_sj - label_sj)^2 and its gradient w.r.t. the parameter
+// vector (grads [35088] overwritten), by the chain rule through the three layers.
+int oracle_mlp_backward(int64_t n, const double* X, const double* labels, const double* w, const double* prm,
+                        int rb, double* grads, double* loss) {
+    const bool r = rb != 0;
+    auto W = [&](int off, int o, int i, int ld) { const double v = prm[off + o * ld + i]; return r ? round_bf16(v) : v; };
+    for (int k = 0; k < OPARAMS; ++k) grads[k] = 0;
+    double L = 0;
+    std::vector<double> h1(MH), h2(MH), dz2(MH), dz1(MH);
+    for (int64_t s = 0; s < n; ++s) {
+        const double* x = X + s * MI;
+        double y[MO], dy[MO];
+        mlp_forward_one(x, prm, r, h1.data(), h2.data(), y);
+        for (int j = 0; j < MO; ++j) {
+            const double e = y[j] - labels[s * MO + j];
+            L += w[j] * e * e / (double)n;
+            dy[j] = 2 * w[j] * e / (double)n;
+            if (r) dy[j] = round_bf16(dy[j]);
+        }
+        for (int j = 0; j < MO; ++j) {
+            grads[OB3 + j] += dy[j];
+            for (int i = 0; i < MH; ++i) grads[OW3 + j * MH + i] += dy[j] * h2[i];
+        }
+        for (int i = 0; i < MH; ++i) {
+            double g = 0;
+            for (int j = 0; j < MO; ++j) g += dy[j] * W(OW3, j, i, MH);
+            const double v = h2[i] > 0 ? g : 0.0;
+            dz2[i] = r ? round_bf16(v) : v;
+        }
+        for (int o = 0; o < MH; ++o) {
+            grads[OB2 + o] += dz2[o];
+            for (int i = 0; i < MH; ++i) grads[OW2 + o * MH + i] += dz2[o] * h1[i];
+        }
+        for (int i = 0; i < MH; ++i) {
+            double g = 0;
+            for (int o = 0; o < MH; ++o) g += dz2[o] * W(OW2, o, i, MH);
+            const double v = h1[i] > 0 ? g : 0.0;
+            dz1[i] = r ? round_bf16(v) : v;
+        }
+        for (int o = 0; o < MH; ++o) {
+            grads[OB1 + o] += dz1[o];
+            for (int i = 0; i < MI; ++i) grads[OW1 + o * MI + i] += dz1[o] * x[i];
+        }
+    }
+    if (loss) *loss = L;
+    return 0;
+}
+
+// Canonical parameters (see dqo_quadric_canonical): the same ellipsoid with axes
+// descending (stable), the rotation's columns permuted with them, det +1, and of the four
+// sign patterns diag(1,1,1), (1,-1,-1), (-1,1,-1), (-1,-1,1) the first of largest trace.
+int oracle_quadric_canonical(int nq, const double* in, double* out) {
+    for (int q = 0; q < nq; ++q) {
+        const double* p = in + 9 * q;
+        double R[3][3];
+        rotvec_to_rot(p + 6, R);
+        int ord[3] = {0, 1, 2};
+        std::stable_sort(ord, ord + 3, [&](int a, int b) { return p[3 + a] > p[3 + b]; });
+        double S[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) S[i][k] = R[i][ord[k]];
+        const double det = S[0][0] * (S[1][1] * S[2][2] - S[1][2] * S[2][1]) -
+                           S[0][1] * (S[1][0] * S[2][2] - S[1][2] * S[2][0]) +
+                           S[0][2] * (S[1][0] * S[2][1] - S[1][1] * S[2][0]);
+        if (det < 0) for (int i = 0; i < 3; ++i) S[i][2] = -S[i][2];
+        const double sg[4][3] = {{1, 1, 1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}};
+        int best = 0;
+        double bt = -1e300;
+        for (int c = 0; c < 4; ++c) {
+            const double tr = sg[c][0] * S[0][0] + sg[c][1] * S[1][1] + sg[c][2] * S[2][2];
+            if (tr > bt) { bt = tr; best = c; }
+        }
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) S[i][k] *= sg[best][k];
+        double* o = out + 9 * q;
+        const double c0 = p[0], c1 = p[1], c2 = p[2], l0 = p[3 + ord[0]], l1 = p[3 + ord[1]], l2 = p[3 + ord[2]];
+        o[0] = c0; o[1] = c1; o[2] = c2; o[3] = l0; o[4] = l1; o[5] = l2;
+        rot_to_rotvec(S, o + 6);
+    }
+    return 0;
+}
+
+}  // extern "C"

@@ -44,6 +44,10 @@ struct dqo_ctx {
   bool pending[DQO_PHASE_COUNT] = {};
   float last_ms[DQO_PHASE_COUNT] = {};
   int64_t launches = 0;
+  // learned proposal: activations of the last batch size, error flag
+  Buf mlp_work;
+  int64_t mlp_n = 0;
+  bool mlp_ready = false;
 };
 
 namespace {
@@ -615,17 +619,192 @@ dqo_status dqo_quadric_bbox_loss(dqo_ctx* c, int32_t nq, const float* params, in
 
 dqo_status dqo_quadric_fit(dqo_ctx* c, int32_t nq, int32_t nv, const float* P, const int32_t* q_ptr,
                            const int32_t* pair_v, int32_t npairs, const float* obs, int32_t iters, float lr,
-                           float* init, float* params, float* loss, uint8_t* ok, dqo_stream stream_) {
+                           const float* start, float* init, float* params, float* loss, uint8_t* ok,
+                           dqo_stream stream_) {
   if (!c || nq < 0 || nv < 0 || npairs < 0 || iters < 0 || !(lr >= 0.f)) return DQO_EINVAL;
   if (nq > 0 && !q_ptr) return DQO_EINVAL;
   if (npairs > 0 && (!P || !pair_v || !obs || nv == 0)) return DQO_EINVAL;
   DQO_CUDA(c, cudaSetDevice(c->device));
   {
     PhaseTimer pt(c, DQO_PHASE_QUADRIC, reinterpret_cast<cudaStream_t>(stream_));
-    DQO_CUDA(c, launch_quadric_fit(nq, nv, P, q_ptr, pair_v, npairs, obs, iters, lr, init, params, loss, ok,
-                                   reinterpret_cast<cudaStream_t>(stream_)));
+    DQO_CUDA(c, launch_quadric_fit(nq, nv, P, q_ptr, pair_v, npairs, obs, iters, lr, start, init, params, loss,
+                                   ok, reinterpret_cast<cudaStream_t>(stream_)));
   }
   c->launches += nq > 0 ? 1 : 0;
+  return DQO_OK;
+}
+
+dqo_status dqo_quadric_canonical(int32_t nq, const float* params, float* out, dqo_stream stream_) {
+  if (nq < 0 || (nq > 0 && (!params || !out))) return DQO_EINVAL;
+  if (launch_quadric_canonical(nq, params, out, reinterpret_cast<cudaStream_t>(stream_)) != cudaSuccess)
+    return DQO_ECUDA;
+  return DQO_OK;
+}
+
+// ----------------------------------------------------------------------------- learned proposal
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+constexpr size_t kParamBytes = align_up(sizeof(float) * kMlpParams);
+constexpr size_t kW128Bytes = align_up(2 * kMlpHidden * kMlpHidden);
+constexpr size_t kW3Bytes = align_up(2 * kMlpOutPad * kMlpHidden);
+constexpr size_t kStateBytes = 4 * kParamBytes + 3 * kW128Bytes + 2 * kW3Bytes + kAlign;
+
+MlpState state_view(const void* state) {
+  unsigned char* b = static_cast<unsigned char*>(const_cast<void*>(state));
+  MlpState st;
+  st.param = reinterpret_cast<float*>(b);
+  st.grad = reinterpret_cast<float*>(b + kParamBytes);
+  st.m1 = reinterpret_cast<float*>(b + 2 * kParamBytes);
+  st.m2 = reinterpret_cast<float*>(b + 3 * kParamBytes);
+  b += 4 * kParamBytes;
+  st.w1b = reinterpret_cast<__nv_bfloat16*>(b);
+  st.w2b = reinterpret_cast<__nv_bfloat16*>(b + kW128Bytes);
+  st.w2tb = reinterpret_cast<__nv_bfloat16*>(b + 2 * kW128Bytes);
+  b += 3 * kW128Bytes;
+  st.w3b = reinterpret_cast<__nv_bfloat16*>(b);
+  st.w3tb = reinterpret_cast<__nv_bfloat16*>(b + kW3Bytes);
+  st.step = reinterpret_cast<int*>(b + 2 * kW3Bytes);
+  return st;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Workspace for batches of up to n rows (n rounded up to 128); sets up the GEMM kernels'
+// shared-memory limit on first use.
+dqo_status mlp_work(dqo_ctx* c, int64_t n, MlpWork* wk) {
+  if (!c->mlp_ready) {
+    DQO_CUDA(c, mlp_gemm_setup());
+    c->mlp_ready = true;
+  }
+  // the layout follows the largest batch seen, so the error flag keeps its place
+  const int64_t nn = std::max((n + 127) / 128 * 128, c->mlp_n);
+  const size_t big = align_up((size_t)nn * kMlpHidden * 2), small = align_up((size_t)nn * kMlpOutPad * 2);
+  const size_t bytes = 8 * big + 2 * small + kAlign;
+  const bool grow = nn > c->mlp_n;
+  DQO_CUDA(c, ensure(c->mlp_work, bytes));
+  unsigned char* b = as<unsigned char>(c->mlp_work);
+  __nv_bfloat16** bigs[8] = {&wk->h1, &wk->h1t, &wk->h2, &wk->h2t, &wk->dz1, &wk->dz1t, &wk->dz2, &wk->dz2t};
+  for (int i = 0; i < 8; ++i) *bigs[i] = reinterpret_cast<__nv_bfloat16*>(b + i * big);
+  wk->dy = reinterpret_cast<__nv_bfloat16*>(b + 8 * big);
+  wk->dyt = reinterpret_cast<__nv_bfloat16*>(b + 8 * big + small);
+  wk->err = reinterpret_cast<int*>(b + 8 * big + 2 * small);
+  if (grow) DQO_CUDA(c, cudaMemset(wk->err, 0, sizeof(int)));
+  c->mlp_n = nn;
+  return DQO_OK;
+}
+
+dqo_status check_batch(int64_t n, const uint16_t* X, const uint16_t* XT, int64_t ldxt, const float* labels) {
+  if (n <= 0 || n % 128 != 0 || n > (int64_t(1) << 30)) return DQO_EINVAL;
+  if (!X || !XT || !labels || ldxt < n || ldxt % 8 != 0 || !aligned16(X) || !aligned16(XT)) return DQO_EINVAL;
+  return DQO_OK;
+}
+
+}  // namespace
+
+dqo_status dqo_mlp_features(int32_t nq, int32_t nv, const float* P, const int32_t* q_ptr, const int32_t* pair_v,
+                            int32_t npairs, const float* obs, const int32_t* counts, float length_scale,
+                            uint16_t* X, uint16_t* XT, int64_t ldt, dqo_stream stream_) {
+  if (nq < 0 || nv < 0 || npairs < 0 || !(length_scale > 0.f)) return DQO_EINVAL;
+  if (nq == 0) return DQO_OK;
+  if (!q_ptr || !X || !aligned16(X)) return DQO_EINVAL;
+  if (npairs > 0 && (!P || !pair_v || !obs || nv == 0)) return DQO_EINVAL;
+  if (XT && (ldt < nq || ldt % 8 != 0)) return DQO_EINVAL;
+  if (launch_mlp_features(nq, nv, P, q_ptr, pair_v, npairs, obs, counts, 1.f / length_scale, X, XT, ldt,
+                          reinterpret_cast<cudaStream_t>(stream_)) != cudaSuccess)
+    return DQO_ECUDA;
+  return DQO_OK;
+}
+
+size_t dqo_mlp_state_bytes(void) { return kStateBytes; }
+
+dqo_status dqo_mlp_set_params(void* state, const float* params, dqo_stream stream_) {
+  if (!state || !params || (reinterpret_cast<uintptr_t>(state) % kAlign) != 0) return DQO_EINVAL;
+  if (launch_mlp_set(state_view(state), params, reinterpret_cast<cudaStream_t>(stream_)) != cudaSuccess)
+    return DQO_ECUDA;
+  return DQO_OK;
+}
+
+dqo_status dqo_mlp_get_params(const void* state, float* params, dqo_stream stream_) {
+  if (!state || !params || (reinterpret_cast<uintptr_t>(state) % kAlign) != 0) return DQO_EINVAL;
+  if (cudaMemcpyAsync(params, state_view(state).param, sizeof(float) * kMlpParams, cudaMemcpyDeviceToDevice,
+                      reinterpret_cast<cudaStream_t>(stream_)) != cudaSuccess)
+    return DQO_ECUDA;
+  return DQO_OK;
+}
+
+dqo_status dqo_mlp_forward(dqo_ctx* c, const void* state, int64_t n, const uint16_t* X, float* out,
+                           dqo_stream stream_) {
+  if (!c || !state || n < 0 || n > (int64_t(1) << 30) || (reinterpret_cast<uintptr_t>(state) % kAlign) != 0)
+    return DQO_EINVAL;
+  if (n == 0) return DQO_OK;
+  if (!X || !out || !aligned16(X)) return DQO_EINVAL;
+  DQO_CUDA(c, cudaSetDevice(c->device));
+  MlpWork wk;
+  dqo_status st = mlp_work(c, n, &wk);
+  if (st != DQO_OK) return st;
+  DQO_CUDA(c, launch_mlp_forward(state_view(state), wk, n, X, out, reinterpret_cast<cudaStream_t>(stream_)));
+  c->launches += 3;
+  return DQO_OK;
+}
+
+dqo_status dqo_mlp_gradients(dqo_ctx* c, void* state, int64_t n, const uint16_t* X, const uint16_t* XT,
+                             int64_t ldxt, const float* labels, const float* loss_w, float* grads, float* loss,
+                             dqo_stream stream_) {
+  if (!c || !state || !loss_w || !grads || !loss || (reinterpret_cast<uintptr_t>(state) % kAlign) != 0)
+    return DQO_EINVAL;
+  dqo_status st = check_batch(n, X, XT, ldxt, labels);
+  if (st != DQO_OK) return st;
+  DQO_CUDA(c, cudaSetDevice(c->device));
+  MlpWork wk;
+  if ((st = mlp_work(c, n, &wk)) != DQO_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+  const MlpState ms = state_view(state);
+  DQO_CUDA(c, cudaMemsetAsync(ms.grad, 0, sizeof(float) * kMlpParams, s));
+  DQO_CUDA(c, cudaMemsetAsync(loss, 0, sizeof(float), s));
+  DQO_CUDA(c, launch_mlp_backward(ms, wk, n, X, XT, ldxt, labels, loss_w, loss, nullptr, s));
+  DQO_CUDA(c, cudaMemcpyAsync(grads, ms.grad, sizeof(float) * kMlpParams, cudaMemcpyDeviceToDevice, s));
+  DQO_CUDA(c, cudaMemsetAsync(ms.grad, 0, sizeof(float) * kMlpParams, s));
+  c->launches += 8;
+  return DQO_OK;
+}
+
+dqo_status dqo_mlp_train_step(dqo_ctx* c, void* state, const dqo_mlp_hparams* hp, int64_t n, const uint16_t* X,
+                              const uint16_t* XT, int64_t ldxt, const float* labels, float* loss,
+                              dqo_stream stream_) {
+  if (!c || !state || !hp || (reinterpret_cast<uintptr_t>(state) % kAlign) != 0) return DQO_EINVAL;
+  if (!(hp->lr >= 0.f) || !(hp->lr_final >= 0.f) || !(hp->beta1 >= 0.f && hp->beta1 < 1.f) ||
+      !(hp->beta2 >= 0.f && hp->beta2 < 1.f) || !(hp->eps > 0.f))
+    return DQO_EINVAL;
+  dqo_status st = check_batch(n, X, XT, ldxt, labels);
+  if (st != DQO_OK) return st;
+  DQO_CUDA(c, cudaSetDevice(c->device));
+  MlpWork wk;
+  if ((st = mlp_work(c, n, &wk)) != DQO_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+  const MlpState ms = state_view(state);
+  float* lp = loss;
+  if (lp) DQO_CUDA(c, cudaMemsetAsync(lp, 0, sizeof(float), s));
+  DQO_CUDA(c, launch_mlp_backward(ms, wk, n, X, XT, ldxt, labels, hp->loss_w, lp, ms.step, s));
+  DQO_CUDA(c, launch_mlp_adam(ms, *hp, s));
+  c->launches += 9;
+  return DQO_OK;
+}
+
+dqo_status dqo_mlp_check(dqo_ctx* c, int* timed_out) {
+  if (!c || !timed_out) return DQO_EINVAL;
+  *timed_out = 0;
+  if (!c->mlp_work.p) return DQO_OK;
+  DQO_CUDA(c, cudaSetDevice(c->device));
+  MlpWork wk;
+  dqo_status st = mlp_work(c, c->mlp_n, &wk);
+  if (st != DQO_OK) return st;
+  int v = 0;
+  DQO_CUDA(c, cudaMemcpy(&v, wk.err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (v) DQO_CUDA(c, cudaMemset(wk.err, 0, sizeof(int)));
+  *timed_out = v;
   return DQO_OK;
 }
 

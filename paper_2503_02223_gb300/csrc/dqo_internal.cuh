@@ -2,6 +2,7 @@
 // declared here and defined next to their kernels; dqo_api.cu drives them.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -181,7 +182,58 @@ cudaError_t launch_quadric_bbox_loss(int nq, const float* params, int nv, const 
                                      float* dparams, cudaStream_t s);
 
 cudaError_t launch_quadric_fit(int nq, int nv, const float* P, const int32_t* q_ptr, const int32_t* pair_v,
-                               int npairs, const float* obs, int iters, float lr, float* init, float* params,
-                               float* loss, uint8_t* ok, cudaStream_t s);
+                               int npairs, const float* obs, int iters, float lr, const float* start, float* init,
+                               float* params, float* loss, uint8_t* ok, cudaStream_t s);
+cudaError_t launch_quadric_canonical(int nq, const float* in, float* out, cudaStream_t s);
+
+// ----------------------------------------------------------------------------- learned proposal
+
+constexpr int kMlpViews = 8, kMlpIn = 128, kMlpHidden = 128, kMlpOut = 9, kMlpOutPad = 16;
+// FP32 parameter vector: W1 [128][128] (out x in), b1, W2 [128][128], b2, W3 [16][128]
+// (rows 9..15 zero), b3 [16]
+constexpr int kMlpW1 = 0, kMlpB1 = 16384, kMlpW2 = 16512, kMlpB2 = 32896, kMlpW3 = 33024, kMlpB3 = 35072,
+              kMlpParams = 35088;
+
+// Views into the caller-owned state buffer.
+struct MlpState {
+  float *param, *grad, *m1, *m2;       // [kMlpParams] each
+  __nv_bfloat16 *w1b, *w2b, *w2tb;     // [128][128]: W1, W2, W2^T
+  __nv_bfloat16 *w3b, *w3tb;           // W3 [16][128], W3^T [128][16]
+  int* step;                           // optimiser steps taken
+};
+
+// Activations and output gradients of one batch (context workspace).
+struct MlpWork {
+  __nv_bfloat16 *h1, *h1t, *h2, *h2t, *dz1, *dz1t, *dz2, *dz2t;  // [n][128] and [128][n]
+  __nv_bfloat16 *dy, *dyt;                                     // [n][16] and [16][n]
+  int* err;
+};
+
+__device__ __forceinline__ void write_bf16_copies(const MlpState& st, int i, float p) {
+  const __nv_bfloat16 b = __float2bfloat16_rn(p);
+  if (i < kMlpB1) {
+    st.w1b[i] = b;
+  } else if (i >= kMlpW2 && i < kMlpB2) {
+    const int k = i - kMlpW2;
+    st.w2b[k] = b;
+    st.w2tb[(k % kMlpHidden) * kMlpHidden + k / kMlpHidden] = b;
+  } else if (i >= kMlpW3 && i < kMlpB3) {
+    const int k = i - kMlpW3;
+    st.w3b[k] = b;
+    st.w3tb[(k % kMlpHidden) * kMlpOutPad + k / kMlpHidden] = b;
+  }
+}
+
+cudaError_t mlp_gemm_setup();
+cudaError_t launch_mlp_features(int nq, int nv, const float* P, const int32_t* q_ptr, const int32_t* pair_v,
+                                int npairs, const float* obs, const int32_t* counts, float inv_scale, uint16_t* X,
+                                uint16_t* XT, int64_t ldt, cudaStream_t s);
+cudaError_t launch_mlp_set(const MlpState& st, const float* params, cudaStream_t s);
+cudaError_t launch_mlp_adam(const MlpState& st, const dqo_mlp_hparams& hp, cudaStream_t s);
+cudaError_t launch_mlp_forward(const MlpState& st, const MlpWork& wk, int64_t n, const uint16_t* X, float* y,
+                               cudaStream_t s);
+cudaError_t launch_mlp_backward(const MlpState& st, const MlpWork& wk, int64_t n, const uint16_t* X,
+                                const uint16_t* XT, int64_t ldxt, const float* labels, const float* loss_w,
+                                float* loss, int* step_inc, cudaStream_t s);
 
 }  // namespace dqo

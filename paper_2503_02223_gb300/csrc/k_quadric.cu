@@ -477,6 +477,7 @@ __global__ void __launch_bounds__(32 * kFitWarps) k_quadric_fit(int nq, int nv, 
                                                                   const int32_t* __restrict__ q_ptr,
                                                                   const int32_t* __restrict__ pair_v, int npairs,
                                                                   const float* __restrict__ obs, int iters, float lr,
+                                                                  const float* __restrict__ start,
                                                                   float* __restrict__ init_out,
                                                                   float* __restrict__ params_out,
                                                                   float* __restrict__ loss_out,
@@ -487,7 +488,14 @@ __global__ void __launch_bounds__(32 * kFitWarps) k_quadric_fit(int nq, int nv, 
   if (q >= nq) return;
   const int k0 = max(q_ptr[q], 0), k1 = min(q_ptr[q + 1], npairs);
   float p[9];
-  const bool good = warp_quadric_init(k0, k1, Pm, pair_v, obs, nv, sm[w], lane, p);
+  bool good;
+  if (start) {  // refine from the given parameters instead of the Eq. 1 initialisation
+#pragma unroll
+    for (int k = 0; k < 9; ++k) p[k] = start[9 * q + k];
+    good = k1 > k0;
+  } else {
+    good = warp_quadric_init(k0, k1, Pm, pair_v, obs, nv, sm[w], lane, p);
+  }
   if (lane == 0 && ok_out) ok_out[q] = good ? 1 : 0;
   if (!good) {
     if (lane < 9) {
@@ -532,15 +540,90 @@ __global__ void __launch_bounds__(32 * kFitWarps) k_quadric_fit(int nq, int nv, 
   if (lane == 0 && loss_out) loss_out[q] = L;
 }
 
+// Canonical parameters of a quadric (the learned proposal's regression target): the same
+// ellipsoid with its semi-axes in descending order (ties kept in index order), the
+// rotation's columns permuted with them and the third negated if that makes det < 0, and,
+// of the four rotations that differ by negating two columns (all describe the same
+// ellipsoid), the one of largest trace (first in the order identity, flip axes 2-3,
+// flip 1-3, flip 1-2 on ties).  Centre unchanged.
+__global__ void k_quadric_canonical(int nq, const float* __restrict__ in, float* __restrict__ out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  double p[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) p[k] = in[9 * q + k];
+  // rotation vector -> matrix, R = I + A K + B K^2
+  const double th2 = p[6] * p[6] + p[7] * p[7] + p[8] * p[8];
+  const double th = sqrt(th2);
+  double A, B;
+  if (th < 1e-4) {
+    A = 1.0 - th2 / 6.0;
+    B = 0.5 - th2 / 24.0;
+  } else {
+    A = sin(th) / th;
+    B = (1.0 - cos(th)) / th2;
+  }
+  const double Kx[3][3] = {{0.0, -p[8], p[7]}, {p[8], 0.0, -p[6]}, {-p[7], p[6], 0.0}};
+  double R[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const double k2 = Kx[i][0] * Kx[0][j] + Kx[i][1] * Kx[1][j] + Kx[i][2] * Kx[2][j];
+      R[i][j] = (i == j ? 1.0 : 0.0) + A * Kx[i][j] + B * k2;
+    }
+  int ord[3] = {0, 1, 2};
+  const double* la = p + 3;
+  if (la[ord[1]] > la[ord[0]]) { const int x = ord[0]; ord[0] = ord[1]; ord[1] = x; }
+  if (la[ord[2]] > la[ord[1]]) { const int x = ord[1]; ord[1] = ord[2]; ord[2] = x; }
+  if (la[ord[1]] > la[ord[0]]) { const int x = ord[0]; ord[0] = ord[1]; ord[1] = x; }
+  double Rs[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Rs[i][k] = R[i][ord[k]];
+  const double det = Rs[0][0] * (Rs[1][1] * Rs[2][2] - Rs[1][2] * Rs[2][1]) -
+                     Rs[0][1] * (Rs[1][0] * Rs[2][2] - Rs[1][2] * Rs[2][0]) +
+                     Rs[0][2] * (Rs[1][0] * Rs[2][1] - Rs[1][1] * Rs[2][0]);
+  if (det < 0.0)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Rs[i][2] = -Rs[i][2];
+  const double sg[4][3] = {{1, 1, 1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}};
+  int best = 0;
+  double bt = Rs[0][0] + Rs[1][1] + Rs[2][2];
+  for (int c = 1; c < 4; ++c) {
+    const double tr = sg[c][0] * Rs[0][0] + sg[c][1] * Rs[1][1] + sg[c][2] * Rs[2][2];
+    if (tr > bt) { bt = tr; best = c; }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Rs[i][k] *= sg[best][k];
+  double rv[3];
+  rotmat_to_rotvec(Rs, rv);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    out[9 * q + k] = (float)p[k];
+    out[9 * q + 3 + k] = (float)la[ord[k]];
+    out[9 * q + 6 + k] = (float)rv[k];
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_quadric_fit(int nq, int nv, const float* P, const int32_t* q_ptr, const int32_t* pair_v,
-                               int npairs, const float* obs, int iters, float lr, float* init, float* params,
-                               float* loss, uint8_t* ok, cudaStream_t s) {
+                               int npairs, const float* obs, int iters, float lr, const float* start, float* init,
+                               float* params, float* loss, uint8_t* ok, cudaStream_t s) {
   if (nq == 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((nq + kFitWarps - 1) / kFitWarps);
-  k_quadric_fit<<<blocks, 32 * kFitWarps, 0, s>>>(nq, nv, P, q_ptr, pair_v, npairs, obs, iters, lr, init, params,
-                                                 loss, ok);
+  k_quadric_fit<<<blocks, 32 * kFitWarps, 0, s>>>(nq, nv, P, q_ptr, pair_v, npairs, obs, iters, lr, start, init,
+                                                 params, loss, ok);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quadric_canonical(int nq, const float* in, float* out, cudaStream_t s) {
+  if (nq == 0) return cudaSuccess;
+  k_quadric_canonical<<<(unsigned)((nq + 127) / 128), 128, 0, s>>>(nq, in, out);
   return cudaGetLastError();
 }
 

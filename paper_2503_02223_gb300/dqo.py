@@ -77,8 +77,29 @@ _SIGS = {
     "dqo_depth_order_noalloc": (c_i32, [c_p, c_i64, c_p, c_p]),
     "dqo_quadric_project": (c_i32, [c_p, c_i32, c_p, c_i32, c_p, c_p, c_p, c_i32, c_p, c_p, c_p, c_p]),
     "dqo_quadric_bbox_loss": (c_i32, [c_p, c_i32, c_p, c_i32, c_p, c_p, c_p, c_i32, c_p, c_p, c_p, c_p]),
-    "dqo_quadric_fit": (c_i32, [c_p, c_i32, c_i32, c_p, c_p, c_p, c_i32, c_p, c_i32, c_f, c_p, c_p, c_p, c_p, c_p]),
+    "dqo_quadric_fit": (c_i32, [c_p, c_i32, c_i32, c_p, c_p, c_p, c_i32, c_p, c_i32, c_f, c_p, c_p, c_p, c_p, c_p,
+                                c_p]),
+    "dqo_quadric_canonical": (c_i32, [c_i32, c_p, c_p, c_p]),
+    "dqo_mlp_features": (c_i32, [c_i32, c_i32, c_p, c_p, c_p, c_i32, c_p, c_p, c_f, c_p, c_p, c_i64, c_p]),
+    "dqo_mlp_state_bytes": (C.c_size_t, []),
+    "dqo_mlp_set_params": (c_i32, [c_p, c_p, c_p]),
+    "dqo_mlp_get_params": (c_i32, [c_p, c_p, c_p]),
+    "dqo_mlp_forward": (c_i32, [c_p, c_p, c_i64, c_p, c_p, c_p]),
+    "dqo_mlp_gradients": (c_i32, [c_p, c_p, c_i64, c_p, c_p, c_i64, c_p, c_p, c_p, c_p, c_p]),
+    "dqo_mlp_train_step": (c_i32, [c_p, c_p, c_p, c_i64, c_p, c_p, c_i64, c_p, c_p, c_p]),
+    "dqo_mlp_check": (c_i32, [c_p, c_p]),
 }
+
+MLP_FEATURES = 128
+MLP_PARAMS = 35088
+# offsets into the fp32 parameter vector
+MLP_LAYOUT = {"W1": (0, (128, 128)), "b1": (16384, (128,)), "W2": (16512, (128, 128)), "b2": (32896, (128,)),
+              "W3": (33024, (16, 128)), "b3": (35072, (16,))}
+
+
+class dqo_mlp_hparams(C.Structure):
+    _fields_ = [("lr", c_f), ("lr_final", c_f), ("total_steps", c_i64), ("beta1", c_f), ("beta2", c_f),
+                ("eps", c_f), ("loss_w", c_f * 9)]
 
 _lib = None
 _lock = threading.Lock()
@@ -323,13 +344,107 @@ def dqo_quadric_bbox_loss(ctx: Context, params, P, q_ptr, pair_v, obs, loss=None
 
 
 def dqo_quadric_fit(ctx: Context, P, q_ptr, pair_v, obs, iters=100, lr=1e-2, init=None, params=None, loss=None,
-                    ok=None, stream=None):
+                    ok=None, stream=None, start=None):
     lib = load()
     nq = q_ptr.shape[0] - 1
     _check("dqo_quadric_fit",
            lib.dqo_quadric_fit(ctx.handle, nq, P.shape[0], _ptr(P), _ptr(q_ptr), _ptr(pair_v), pair_v.shape[0],
-                               _ptr(obs), iters, lr, _ptr(init), _ptr(params), _ptr(loss), _ptr(ok),
+                               _ptr(obs), iters, lr, _ptr(start), _ptr(init), _ptr(params), _ptr(loss), _ptr(ok),
                                _stream(stream)), ctx.handle)
+
+
+def dqo_quadric_canonical(params, out=None, stream=None):
+    out = torch.empty_like(params) if out is None else out
+    _check("dqo_quadric_canonical", load().dqo_quadric_canonical(params.shape[0], _ptr(params), _ptr(out),
+                                                                 _stream(stream)))
+    return out
+
+
+# ------------------------------------------------------------------------ learned proposal
+
+def mlp_hparams(lr=2e-3, lr_final=1e-5, total_steps=0, beta1=0.9, beta2=0.999, eps=1e-8,
+                loss_w=(1, 1, 1, 1, 1, 1, 0.3, 0.3, 0.3)) -> dqo_mlp_hparams:
+    h = dqo_mlp_hparams(lr=lr, lr_final=lr_final, total_steps=total_steps, beta1=beta1, beta2=beta2, eps=eps)
+    for i, v in enumerate(loss_w):
+        h.loss_w[i] = v
+    return h
+
+
+def dqo_mlp_features(P, q_ptr, pair_v, obs, counts=None, length_scale=1.0, X=None, XT=None, ldt=None,
+                     stream=None):
+    """Features [nq][128] (bfloat16) and optionally their transpose [128][ldt]."""
+    nq = q_ptr.shape[0] - 1
+    if X is None:
+        X = torch.empty(nq, MLP_FEATURES, dtype=torch.bfloat16, device=q_ptr.device)
+    ld = 0 if XT is None else (XT.shape[1] if ldt is None else ldt)
+    _check("dqo_mlp_features",
+           load().dqo_mlp_features(nq, P.shape[0], _ptr(P), _ptr(q_ptr), _ptr(pair_v), pair_v.shape[0], _ptr(obs),
+                                   _ptr(counts), length_scale, _ptr(X), _ptr(XT), ld, _stream(stream)))
+    return X
+
+
+class MlpState:
+    """Device buffer holding the network's parameters, gradient, Adam moments and BF16 copies."""
+
+    def __init__(self, device="cuda"):
+        nbytes = load().dqo_mlp_state_bytes()
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+    @property
+    def handle(self) -> int:
+        return self.buf.data_ptr()
+
+
+def dqo_mlp_set_params(state: MlpState, params, stream=None):
+    _check("dqo_mlp_set_params", load().dqo_mlp_set_params(state.handle, _ptr(params), _stream(stream)))
+
+
+def dqo_mlp_get_params(state: MlpState, params=None, stream=None):
+    params = torch.empty(MLP_PARAMS, device=state.buf.device) if params is None else params
+    _check("dqo_mlp_get_params", load().dqo_mlp_get_params(state.handle, _ptr(params), _stream(stream)))
+    return params
+
+
+def dqo_mlp_forward(ctx: Context, state: MlpState, X, out=None, stream=None):
+    out = torch.empty(X.shape[0], 9, device=X.device) if out is None else out
+    _check("dqo_mlp_forward", load().dqo_mlp_forward(ctx.handle, state.handle, X.shape[0], _ptr(X), _ptr(out),
+                                                     _stream(stream)), ctx.handle)
+    return out
+
+
+def dqo_mlp_gradients(ctx: Context, state: MlpState, X, XT, labels, loss_w, grads=None, loss=None, ldxt=None,
+                      stream=None):
+    grads = torch.empty(MLP_PARAMS, device=X.device) if grads is None else grads
+    loss = torch.empty(1, device=X.device) if loss is None else loss
+    w = (c_f * 9)(*[float(v) for v in loss_w])
+    _check("dqo_mlp_gradients",
+           load().dqo_mlp_gradients(ctx.handle, state.handle, X.shape[0], _ptr(X), _ptr(XT),
+                                    XT.shape[1] if ldxt is None else ldxt, _ptr(labels), C.cast(w, c_p),
+                                    _ptr(grads), _ptr(loss), _stream(stream)), ctx.handle)
+    return grads, loss
+
+
+def dqo_mlp_train_step(ctx: Context, state: MlpState, hp: dqo_mlp_hparams, X, XT, labels, loss=None, ldxt=None,
+                       stream=None):
+    """One Adam step on the batch X [n][128] (XT: a [128][ldxt] view whose first n columns are
+    this batch, passed as the tensor starting at the batch's first column)."""
+    _check("dqo_mlp_train_step",
+           load().dqo_mlp_train_step(ctx.handle, state.handle, C.byref(hp), X.shape[0], _ptr_any(X), _ptr_any(XT),
+                                     XT.shape[1] if ldxt is None else ldxt, _ptr(labels), _ptr(loss),
+                                     _stream(stream)), ctx.handle)
+
+
+def _ptr_any(t) -> int:
+    """Device pointer of a tensor that may be a strided view (row pitch passed separately)."""
+    if not t.is_cuda:
+        raise ValueError("tensor must be on a CUDA device")
+    return t.data_ptr()
+
+
+def dqo_mlp_check(ctx: Context) -> bool:
+    v = C.c_int(0)
+    _check("dqo_mlp_check", load().dqo_mlp_check(ctx.handle, C.byref(v)), ctx.handle)
+    return bool(v.value)
 
 
 # ------------------------------------------------------------------------ conveniences

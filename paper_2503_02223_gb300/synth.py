@@ -487,3 +487,75 @@ def batched_quadric_fits(seed: int, nq: int = 512, min_views: int = 3, max_views
                 P=np.ascontiguousarray(np.stack(Ps, 0), np.float32), q_ptr=q_ptr,
                 pair_v=np.arange(len(Ps), dtype=np.int32),
                 obs_bbox=np.ascontiguousarray(np.stack(obs, 0), np.float32), counts=counts)
+
+
+# ----------------------------------------------------------------------------- learned proposal
+
+def look_at_batch(eyes, target=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """look_at for an array of eyes [..., 3] (same convention; 'up' = -y unless the view is
+    within acos(0.95) of vertical, then +z).  Returns [..., 3, 4]."""
+    eyes = np.asarray(eyes, np.float64)
+    z = np.asarray(target, np.float64) - eyes
+    z /= np.linalg.norm(z, axis=-1, keepdims=True)
+    up = np.broadcast_to(np.array([0.0, -1.0, 0.0]), eyes.shape).copy()
+    up[np.abs(z[..., 1]) > 0.95] = np.array([0.0, 0.0, 1.0])
+    x = np.cross(z, -up)
+    x /= np.linalg.norm(x, axis=-1, keepdims=True)
+    y = np.cross(z, x)
+    R = np.stack([x, y, z], -2)
+    t = -np.einsum("...ij,...j->...i", R, eyes)
+    return np.concatenate([R, t[..., None]], -1)
+
+
+def proposal_samples(seed: int, n: int, views: int = 8, noise_px: float = 2.0, f: float = 525.0,
+                     width: int = 640, height: int = 480, radius: float = 3.5, points: int = 96,
+                     chunk: int = 8192) -> dict:
+    """n random ellipsoids (axes U[0.1,0.5] m, centres U[-1,1]^3, random rotation), each seen
+    from `views` cameras on a sphere of `radius` around the origin looking at it; observed
+    box = box of `points` projected surface samples + N(0, noise^2) px.  CSR pairs with
+    exactly `views` views per quadric, in order."""
+    rng = rng_for(seed)
+    params, centres, axes, Rs = random_quadrics(rng, n)
+    d = rng.standard_normal((n, views, 3))
+    d /= np.linalg.norm(d, axis=-1, keepdims=True)
+    vm = look_at_batch(radius * d)
+    P = intrinsics(f, f, width / 2.0, height / 2.0)[None, None] @ vm           # n, views, 3, 4
+    i = np.arange(points) + 0.5
+    phi = np.arccos(1 - 2 * i / points)
+    th = np.pi * (1 + 5 ** 0.5) * i
+    sph = np.stack([np.cos(th) * np.sin(phi), np.sin(th) * np.sin(phi), np.cos(phi)], 0)   # 3, points
+    box = np.empty((n, views, 4))
+    for s in range(0, n, chunk):
+        e = slice(s, s + chunk)
+        pts = centres[e, :, None] + Rs[e] @ (axes[e, :, None] * sph[None])                  # q, 3, points
+        h = P[e, :, :, :3] @ pts[:, None] + P[e, :, :, 3:]                                 # q, views, 3, points
+        u, v = h[:, :, 0] / h[:, :, 2], h[:, :, 1] / h[:, :, 2]
+        box[e] = np.stack([u.min(-1), v.min(-1), u.max(-1), v.max(-1)], -1)
+    box += rng.normal(0.0, noise_px, box.shape)
+    return dict(params_true=params.astype(np.float32),
+                P=np.ascontiguousarray(P.reshape(n * views, 12), np.float32),
+                q_ptr=(np.arange(n + 1) * views).astype(np.int32),
+                pair_v=np.arange(n * views, dtype=np.int32),
+                obs_bbox=np.ascontiguousarray(box.reshape(n * views, 4), np.float32),
+                views=views, length_scale=radius)
+
+
+def subset_views(s: dict, k: int) -> dict:
+    """The first k views of every quadric of a proposal_samples set, as its own CSR set."""
+    n = s["q_ptr"].shape[0] - 1
+    v = s["views"]
+    sel = (np.arange(n)[:, None] * v + np.arange(k)[None]).reshape(-1)
+    return dict(params_true=s["params_true"], P=np.ascontiguousarray(s["P"][sel]),
+                q_ptr=(np.arange(n + 1) * k).astype(np.int32), pair_v=np.arange(n * k, dtype=np.int32),
+                obs_bbox=np.ascontiguousarray(s["obs_bbox"][sel]), views=k, length_scale=s["length_scale"])
+
+
+def mlp_init_params(seed: int) -> np.ndarray:
+    """He-normal weights, zero biases, for the 128-128-128-9 proposal network (fp32 vector of
+    35088 in the library's layout; padding rows zero)."""
+    rng = rng_for(seed)
+    p = np.zeros(35088, np.float32)
+    p[0:16384] = rng.normal(0.0, np.sqrt(2.0 / 128), 16384)
+    p[16512:32896] = rng.normal(0.0, np.sqrt(2.0 / 128), 16384)
+    p[33024:33024 + 9 * 128] = rng.normal(0.0, np.sqrt(1.0 / 128), 9 * 128)
+    return p
