@@ -65,6 +65,7 @@ def parse():
     p.add_argument("--tile", default="16x16")
     p.add_argument("--batch", type=int, default=256)
     p.add_argument("--no-learned", action="store_true", help="skip the learned-proposal section")
+    p.add_argument("--no-batched", action="store_true", help="skip the batched-keyframes section")
     return p.parse_args()
 
 
@@ -382,6 +383,7 @@ def run_ours(args, rank, world, local_rank):
 
     if not args.no_learned:
         fits["learned"] = learned_section(ctx, dev, stream, world, fd, nfit, fit_ms)
+    batched = None if args.no_batched else batched_section(dev, stream, world, fq, fd)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -391,6 +393,8 @@ def run_ours(args, rank, world, local_rank):
             "gpu_launches": launches, "roofline": roof,
             "phases_ms": {k: round(v, 4) for k, v in phases.items()},
             "quadric_fits": fits}
+    if batched is not None:
+        line["batched"] = batched
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         H_ = kf["camera"]["height"]
         rows = 80
@@ -469,6 +473,108 @@ def learned_section(ctx, dev, stream, world, fd, nfit, plain_fit_ms):
                                       "peak_basis": "measured bf16 cuBLAS sustained (MEASURED_PEAKS.json)",
                                       "flops_per_sample": MLP_FLOPS_PER_SAMPLE,
                                       "traffic": None}}}
+
+
+BATCH_KEYFRAMES = 8
+BATCH_REPS = 20
+
+
+def batched_section(dev, stream, world, fq, fd):
+    """8 keyframes of uneven resolution (four 640x480 f=525, four 1200x680 f=600) over 8
+    indoor scenes of 200k..500k Gaussians and 20..60 objects, plus the 512 plain fits:
+    the single-launch form (each keyframe's forward + backward calls in turn, then the fit
+    launch) against the batched step (tuned, replayed from a CUDA graph)."""
+    import numpy as np
+    import torch
+
+    from paper_2503_02223_gb300 import dqo, synth
+    Ns = np.linspace(200_000, 500_000, BATCH_KEYFRAMES).astype(int)
+    objs = np.linspace(20, 60, BATCH_KEYFRAMES).astype(int)
+    cases = []
+    for k in range(BATCH_KEYFRAMES):
+        small = k % 2 == 0
+        kf = synth.indoor_keyframe(SEED + 10 + k, n_total=int(Ns[k]), n_obj=int(objs[k]),
+                                   width=640 if small else 1200, height=480 if small else 680,
+                                   f=525.0 if small else 600.0, object_total=int(0.783 * Ns[k]))
+        cases.append((kf, synth.raycast_targets(kf), int(objs[k]) + 1))
+    gd = [dqo.to_device(kf["gaussians"], dev) for kf, _, _ in cases]
+    td = [dqo.to_device(t, dev) for _, t, _ in cases]
+    outs = [dqo.alloc_outputs(kf["camera"]["width"], kf["camera"]["height"], dev) for kf, _, _ in cases]
+    grads = [dqo.alloc_grads(kf["gaussians"]["means"].shape[0], dev) for kf, _, _ in cases]
+    nfit = fd["q_ptr"].shape[0] - 1
+    f_par = torch.zeros(nfit, 9, device=dev)
+    f_loss = torch.zeros(nfit, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    # ---- single-launch form
+    ctx = dqo.Context(dev.index)
+    st = dqo.settings()
+    per = [(dqo.gaussians(gd[k], cases[k][2]), dqo.camera(cases[k][0]["camera"]), dqo.targets(td[k]),
+            dqo.render_out(outs[k]), dqo.gaussian_grads(grads[k])) for k in range(BATCH_KEYFRAMES)]
+
+    def single():
+        for gs, cs, ts, os_, gg in per:
+            dqo.dqo_render_forward(ctx, st, gs, cs, ts, os_, stream)
+            dqo.dqo_render_backward(ctx, st, gs, cs, ts, None, gg, stream)
+        dqo.dqo_quadric_fit(ctx, fd["P"], fd["q_ptr"], fd["pair_v"], fd["obs_bbox"], FIT_ITERS, 1e-2, None, f_par,
+                            f_loss, None, stream)
+
+    for _ in range(3):
+        single()
+    torch.cuda.synchronize()
+    loss_single = [o["loss"].clone() for o in outs]
+    e0.record(stream)
+    for _ in range(BATCH_REPS):
+        single()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    single_ms = e0.elapsed_time(e1) / BATCH_REPS
+
+    # ---- batched form: tuned, captured, replayed
+    bctx = dqo.Context(dev.index)
+    bst = dqo.settings()
+    kfs = [dqo.keyframe(gd[k], cases[k][2], cases[k][0]["camera"], td[k], outs[k], grads[k])
+           for k in range(BATCH_KEYFRAMES)]
+    fb = dqo.fit_batch(fd["P"], fd["q_ptr"], fd["pair_v"], fd["obs_bbox"], FIT_ITERS, 1e-2, None, None, f_par,
+                       f_loss, None)
+    dqo.dqo_batch_step(bctx, bst, kfs, fb)             # same 16x16 tiles as the single form
+    torch.cuda.synchronize()
+    same_loss = all(torch.equal(a, o["loss"]) for a, o in zip(loss_single, outs))
+    cps, tune_ms = dqo.dqo_batch_tune(bctx, bst, kfs, fb, reps=3)
+    dqo.dqo_batch_step(bctx, bst, kfs, fb, cps)        # sizing call for the chosen shape
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    cs_ = torch.cuda.Stream(dev)
+    cs_.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(cs_):
+        with torch.cuda.graph(graph, stream=cs_, capture_error_mode="thread_local"):
+            dqo.dqo_batch_step(bctx, bst, kfs, fb, cps)
+    torch.cuda.current_stream().wait_stream(cs_)
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(BATCH_REPS):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batched_ms = e0.elapsed_time(e1) / BATCH_REPS
+    pairs, over = dqo.dqo_batch_check(bctx)
+    res = {"workload": "8 keyframes (4x 640x480, 4x 1200x680) over 8 indoor scenes of 200k..500k Gaussians, "
+                       "20..60 objects, + 512 plain fits (3..40 views, 100 Adam steps)",
+           "gaussians": int(Ns.sum()), "tile_gaussian_pairs": pairs, "overflow": over,
+           "single_launch_ms": single_ms, "batched_graph_ms": batched_ms, "speedup": single_ms / batched_ms,
+           "keyframe_iters_per_s": world * BATCH_KEYFRAMES / (batched_ms * 1e-3),
+           "single_keyframe_iters_per_s": world * BATCH_KEYFRAMES / (single_ms * 1e-3),
+           "losses_match_single": same_loss,
+           "tuned": {"tile": f"{bst.tile_w}x{bst.tile_h}", "ctas_per_sm": cps,
+                     "candidates_ms": {f"{w}x{h}/{c}": round(m, 4) for (w, h), c, m in
+                                       zip([(16, 16)] * 3 + [(8, 32)] * 3 + [(32, 8)] * 3, [2, 3, 4] * 3, tune_ms)}},
+           "form": "one launch per phase over all keyframes, persistent fused forward+backward blend on a work "
+                   "queue, fits on a concurrent graph branch, one CUDA graph"}
+    ctx.close()
+    bctx.close()
+    return res
 
 
 def main():

@@ -320,6 +320,79 @@ DQO_API dqo_status dqo_quadric_fit(dqo_ctx* ctx, int32_t nq, int32_t nv, const f
 DQO_API dqo_status dqo_quadric_canonical(int32_t nq, const float* params, float* out, dqo_stream stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Batched optimisation step.  The paper's GPU side optimises several keyframes and many
+ * quadrics per mapping round (Sec. III-D, IV); this entry point runs one step for a
+ * batch of keyframes of any resolutions and scenes, plus a batch of quadric fits, with
+ * every phase a single launch over the whole batch, and captures cleanly in a CUDA graph.
+ * ------------------------------------------------------------------------------------- */
+
+#define DQO_MAX_BATCH 16
+
+/* One keyframe of a batch: its scene, camera, targets (required: the step optimises the
+ * fused losses), outputs (as dqo_render_forward; NULL members are skipped) and the
+ * gradient buffers its step ADDS to (several keyframes may share a scene and its
+ * gradient buffers: additions are atomic). */
+typedef struct dqo_keyframe {
+  dqo_gaussians gaussians;
+  dqo_camera camera;
+  dqo_targets targets;
+  dqo_render_out out;
+  dqo_gaussian_grads grads;
+} dqo_keyframe;
+
+/* A batch of plain quadric fits, as the arguments of dqo_quadric_fit. */
+typedef struct dqo_fit_batch {
+  int32_t nq, nv, npairs, iters;
+  float lr;
+  const float* P;
+  const int32_t* q_ptr;
+  const int32_t* pair_v;
+  const float* obs_bbox;
+  const float* start;
+  float *init, *params, *loss;
+  uint8_t* ok;
+} dqo_fit_batch;
+
+/* One optimisation step for nkf keyframes (1 <= nkf <= DQO_MAX_BATCH) and, if fits is not
+ * NULL, a batch of quadric fits.  Per keyframe: the forward render with the fused losses
+ * of Eq. 7-10 and 15 (out->loss [4] if given) and the backward of those losses, added to
+ * kf->grads.  Results are those of dqo_render_forward + dqo_render_backward (pixel
+ * gradients = the saved loss derivatives) on each keyframe alone; images are bitwise the
+ * same, gradients up to the order of floating-point additions.  The fits run concurrently
+ * on a second stream of the context, joined into `stream` before the call's work ends.
+ *   Phases: projection, scan, depth sort, pair emission, pair sort and tile ranges each
+ *   run once over all keyframes; the blend runs as one persistent kernel whose CTAs take
+ *   tiles of all keyframes from an atomic work queue, each tile's forward followed at once
+ *   by its backward; then the per-keyframe loss sums and the projection adjoint.
+ * Sizing: the first call, and any call whose batch layout (keyframe count, Gaussian
+ * counts, image sizes, tile shape) differs from the previous one, waits once on the host
+ * for the pair count and sizes the pair buffers with 25% headroom; other calls do not
+ * synchronise or allocate (so they can be captured in a CUDA graph) and read the pair
+ * count on the device.  If a later step needs more pairs than that capacity, pairs past
+ * it are dropped and dqo_batch_check reports it (and makes the next step a sizing call).
+ * settings->tile_w/tile_h apply to every keyframe; ctas_per_sm bounds the persistent
+ * kernel's CTAs per SM (<= 0: as many as fit).
+ * Errors: DQO_EINVAL (bad arguments, nkf out of range, missing targets), DQO_ENOMEM,
+ * DQO_ESTATE (a sizing call while the stream is being captured), DQO_ECUDA. */
+DQO_API dqo_status dqo_batch_step(dqo_ctx* ctx, const dqo_settings* settings, int32_t nkf,
+                                  const dqo_keyframe* kfs, const dqo_fit_batch* fits, int32_t ctas_per_sm,
+                                  dqo_stream stream);
+
+/* After the last dqo_batch_step has completed: pairs it needed and whether they exceeded
+ * the capacity (synchronous). */
+DQO_API dqo_status dqo_batch_check(dqo_ctx* ctx, uint64_t* pairs, int* overflow);
+
+/* Autotuner of the batched step: times each candidate (tile shapes 16x16, 8x32, 32x8 x
+ * persistent CTAs per SM 2, 3, 4) over `reps` steps on this batch (CUDA events on the
+ * stream; gradients accumulate into kfs' buffers while it runs) and writes the fastest
+ * tile shape into settings and its CTAs per SM into *ctas_per_sm.  ms [9] (host, may be
+ * NULL) receives each candidate's mean step time in the order listed.
+ * Errors: as dqo_batch_step. */
+DQO_API dqo_status dqo_batch_tune(dqo_ctx* ctx, dqo_settings* settings, int32_t nkf, const dqo_keyframe* kfs,
+                                  const dqo_fit_batch* fits, int32_t reps, int32_t* ctas_per_sm, float* ms,
+                                  dqo_stream stream);
+
+/* ---------------------------------------------------------------------------------------
  * Learned quadric proposal.  The paper initialises each quadric geometrically (Eq. 1);
  * this small network proposes the initial value from up to 8 views instead, including
  * from 2 views, where the Eq. 1 system is underdetermined, and dqo_quadric_fit (start =
@@ -393,9 +466,17 @@ DQO_API dqo_status dqo_mlp_train_step(dqo_ctx* ctx, void* state, const dqo_mlp_h
                                       const uint16_t* X, const uint16_t* XT, int64_t ldxt, const float* labels,
                                       float* loss, dqo_stream stream);
 
-/* Error flag of the last tensor-core kernels on this context (1 if a completion wait ran
- * out), read synchronously and cleared. */
+/* Error flag of the last tensor-core kernels on this context, read synchronously and
+ * cleared: *timed_out = 1 and DQO_ETIMEOUT if a tensor-core completion wait ran out (the
+ * kernel then skipped its epilogue, freed its tensor memory and returned). */
 DQO_API dqo_status dqo_mlp_check(dqo_ctx* ctx, int* timed_out);
+
+/* Exercises the bounded device wait the tensor-core kernels use: one kernel waits on an
+ * mbarrier that nothing arrives at, gives up after about one second and records it; the
+ * call synchronises `stream` and returns DQO_ETIMEOUT (DQO_OK would mean the wait did not
+ * give up).  The context stays usable afterwards.  No counterpart in the paper: this is
+ * how a stalled completion is reported instead of hanging the GPU. */
+DQO_API dqo_status dqo_wait_probe(dqo_ctx* ctx, dqo_stream stream);
 
 #ifdef __cplusplus
 }

@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "dqo_internal.cuh"
 
@@ -44,6 +45,18 @@ struct dqo_ctx {
   bool pending[DQO_PHASE_COUNT] = {};
   float last_ms[DQO_PHASE_COUNT] = {};
   int64_t launches = 0;
+  // batched step: joint buffers of all keyframes of a batch, pair capacity, side stream
+  struct Batch {
+    Buf p0, p1, p2, rect, ntiles, zkey_a, zkey_b, zval_a, zval_b, rank, gid, offsets, grad2d;
+    Buf scan_scratch, depth_scan_scratch, depth_hist, hist, pair_a, pair_b, list, ranges, loss_part;
+    Buf T_final, n_contrib, dl_rgb, dl_depth, dl_ins, counters;
+    uint64_t* host = nullptr;  // pinned: pair count of a sizing call
+    std::vector<int64_t> sig;  // layout of the last sizing call
+    uint64_t capacity = 0;
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    int sms = 0;
+  } b;
   // learned proposal: activations of the last batch size, error flag
   Buf mlp_work;
   int64_t mlp_n = 0;
@@ -251,6 +264,17 @@ void dqo_destroy(dqo_ctx* c) {
                 &c->dl_rgb, &c->dl_depth, &c->dl_ins, &c->counters};
   for (Buf* b : all)
     if (b->p) cudaFree(b->p);
+  dqo_ctx::Batch& B = c->b;
+  Buf* ball[] = {&B.p0, &B.p1, &B.p2, &B.rect, &B.ntiles, &B.zkey_a, &B.zkey_b, &B.zval_a, &B.zval_b, &B.rank,
+                 &B.gid, &B.offsets, &B.grad2d, &B.scan_scratch, &B.depth_scan_scratch, &B.depth_hist, &B.hist,
+                 &B.pair_a, &B.pair_b, &B.list, &B.ranges, &B.loss_part, &B.T_final, &B.n_contrib, &B.dl_rgb,
+                 &B.dl_depth, &B.dl_ins, &B.counters, &c->mlp_work};
+  for (Buf* b : ball)
+    if (b->p) cudaFree(b->p);
+  if (B.host) cudaFreeHost(B.host);
+  if (B.fork) cudaEventDestroy(B.fork);
+  if (B.join) cudaEventDestroy(B.join);
+  if (B.side) cudaStreamDestroy(B.side);
   if (c->host_counters) cudaFreeHost(c->host_counters);
   if (c->count_ready) cudaEventDestroy(c->count_ready);
   for (int i = 0; i < 2 * DQO_PHASE_COUNT; ++i)
@@ -634,6 +658,334 @@ dqo_status dqo_quadric_fit(dqo_ctx* c, int32_t nq, int32_t nv, const float* P, c
   return DQO_OK;
 }
 
+// ----------------------------------------------------------------------------- batched step
+
+namespace {
+
+dqo_status check_fits(const dqo_fit_batch* f) {
+  if (!f) return DQO_OK;
+  if (f->nq < 0 || f->nv < 0 || f->npairs < 0 || f->iters < 0 || !(f->lr >= 0.f)) return DQO_EINVAL;
+  if (f->nq > 0 && !f->q_ptr) return DQO_EINVAL;
+  if (f->npairs > 0 && (!f->P || !f->pair_v || !f->obs_bbox || f->nv == 0)) return DQO_EINVAL;
+  return DQO_OK;
+}
+
+}  // namespace
+
+dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const dqo_keyframe* kfs,
+                          const dqo_fit_batch* fits, int32_t ctas_per_sm, dqo_stream stream_) {
+  if (!c || !kfs || nkf < 1 || nkf > kMaxBatch) return DQO_EINVAL;
+  dqo_status st;
+  if ((st = check_settings(s)) != DQO_OK) return st;
+  if ((st = check_fits(fits)) != DQO_OK) return st;
+  for (int k = 0; k < nkf; ++k) {
+    if ((st = check_gaussians(&kfs[k].gaussians)) != DQO_OK) return st;
+    if ((st = check_camera(&kfs[k].camera)) != DQO_OK) return st;
+    if (!kfs[k].targets.gt_id || !kfs[k].targets.rgb) return DQO_EINVAL;
+  }
+  cudaStream_t s_ = reinterpret_cast<cudaStream_t>(stream_);
+  DQO_CUDA(c, cudaSetDevice(c->device));
+  dqo_ctx::Batch& B = c->b;
+
+  // ---- joint layout: Gaussians, tiles and pixels of keyframe k at base / toff / poff
+  RasterParams rp[kMaxBatch];
+  int64_t base[kMaxBatch], poff[kMaxBatch];
+  uint32_t toff[kMaxBatch + 1];
+  int64_t N = 0, P = 0, max_n = 0;
+  uint64_t T = 0;
+  std::vector<int64_t> sig = {nkf, s->tile_w, s->tile_h};
+  bool with_id = false;
+  for (int k = 0; k < nkf; ++k) {
+    const dqo_keyframe& kf = kfs[k];
+    rp[k] = make_params(s, &kf.gaussians, &kf.camera);
+    base[k] = N;
+    N += kf.gaussians.n;
+    max_n = std::max(max_n, kf.gaussians.n);
+    toff[k] = (uint32_t)T;
+    T += (uint64_t)rp[k].ntx * rp[k].nty;
+    poff[k] = P;
+    P += (int64_t)rp[k].W * rp[k].H;
+    with_id = with_id || kf.out.id_map != nullptr;
+    sig.push_back(kf.gaussians.n);
+    sig.push_back(rp[k].W);
+    sig.push_back(rp[k].H);
+  }
+  if (T >= (uint64_t(1) << 31) || N >= (int64_t(1) << 31)) return DQO_EINVAL;
+  toff[nkf] = (uint32_t)T;
+  const bool sizing = B.capacity == 0 || sig != B.sig;
+  if (sizing) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    DQO_CUDA(c, cudaStreamIsCapturing(s_, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return DQO_ESTATE;
+    DQO_CUDA(c, ensure(B.p0, 16 * N));
+    DQO_CUDA(c, ensure(B.p1, 16 * N));
+    DQO_CUDA(c, ensure(B.p2, 16 * N));
+    DQO_CUDA(c, ensure(B.rect, 8 * N));
+    DQO_CUDA(c, ensure(B.ntiles, 4 * N));
+    DQO_CUDA(c, ensure(B.zkey_a, 4 * N));
+    DQO_CUDA(c, ensure(B.zkey_b, 4 * N));
+    DQO_CUDA(c, ensure(B.zval_a, 4 * N));
+    DQO_CUDA(c, ensure(B.zval_b, 4 * N));
+    DQO_CUDA(c, ensure(B.rank, 4 * N));
+    DQO_CUDA(c, ensure(B.gid, 4 * N));
+    DQO_CUDA(c, ensure(B.offsets, 4 * N));
+    DQO_CUDA(c, ensure(B.grad2d, 48 * N));
+    DQO_CUDA(c, ensure(B.ranges, 8 * T));
+    DQO_CUDA(c, ensure(B.loss_part, 12 * T));
+    DQO_CUDA(c, ensure(B.T_final, 4 * P));
+    DQO_CUDA(c, ensure(B.n_contrib, 4 * P));
+    DQO_CUDA(c, ensure(B.dl_rgb, 12 * P));
+    DQO_CUDA(c, ensure(B.dl_depth, 4 * P));
+    DQO_CUDA(c, ensure(B.dl_ins, 4 * P));
+    DQO_CUDA(c, ensure(B.depth_hist, 4 * radix_scratch_words(N)));
+    DQO_CUDA(c, ensure(B.depth_scan_scratch, 8 * scan_scratch_words(radix_scratch_words(N))));
+    DQO_CUDA(c, ensure(B.scan_scratch, 8 * scan_scratch_words(N)));
+    DQO_CUDA(c, ensure(B.counters, 64));
+    if (!B.host) DQO_CUDA(c, cudaMallocHost(reinterpret_cast<void**>(&B.host), 64));
+    if (!B.side) DQO_CUDA(c, cudaStreamCreateWithFlags(&B.side, cudaStreamNonBlocking));
+    if (!B.fork) DQO_CUDA(c, cudaEventCreateWithFlags(&B.fork, cudaEventDisableTiming));
+    if (!B.join) DQO_CUDA(c, cudaEventCreateWithFlags(&B.join, cudaEventDisableTiming));
+    if (!B.sms) DQO_CUDA(c, cudaDeviceGetAttribute(&B.sms, cudaDevAttrMultiProcessorCount, c->device));
+  }
+  uint64_t* d_total = as<uint64_t>(B.counters);
+  uint32_t* d_nvis = reinterpret_cast<uint32_t*>(d_total + 1);
+  uint32_t* d_overflow = d_nvis + 1;
+  uint32_t* d_queue = reinterpret_cast<uint32_t*>(d_total + 2);
+  const int rank_bits = bits_for((uint64_t)N);  // static bounds, so the step captures
+  const int tile_bits = bits_for(T);
+  const int end_bit = rank_bits + tile_bits;
+  int64_t launches = 0;
+
+  DQO_CUDA(c, cudaMemsetAsync(B.counters.p, 0, 64, s_));
+  DQO_CUDA(c, cudaMemsetAsync(B.ranges.p, 0, 8 * T, s_));
+  DQO_CUDA(c, cudaMemsetAsync(B.grad2d.p, 0, 48 * (size_t)N, s_));
+
+  // ---- quadric fits on the side stream, concurrent with the keyframes
+  const bool run_fits = fits && fits->nq > 0;
+  if (run_fits) {
+    DQO_CUDA(c, cudaEventRecord(B.fork, s_));
+    DQO_CUDA(c, cudaStreamWaitEvent(B.side, B.fork, 0));
+    DQO_CUDA(c, launch_quadric_fit(fits->nq, fits->nv, fits->P, fits->q_ptr, fits->pair_v, fits->npairs,
+                                   fits->obs_bbox, fits->iters, fits->lr, fits->start, fits->init, fits->params,
+                                   fits->loss, fits->ok, B.side));
+    DQO_CUDA(c, cudaEventRecord(B.join, B.side));
+    launches += 1;
+  }
+
+  // ---- projection of every keyframe's Gaussians into the joint arrays
+  ProjBuffers pb;
+  pb.p0 = as<float4>(B.p0);
+  pb.p1 = as<float4>(B.p1);
+  pb.p2 = as<float4>(B.p2);
+  pb.rect = as<ushort4>(B.rect);
+  pb.ntiles = as<uint32_t>(B.ntiles);
+  pb.zkey = as<uint32_t>(B.zkey_a);
+  pb.zval = as<uint32_t>(B.zval_a);
+  pb.gid = as<uint32_t>(B.gid);
+  pb.n_visible = d_nvis;
+  {
+    PreTable pt;
+    for (int k = 0; k < nkf; ++k) {
+      pt.kf[k].rp = rp[k];
+      pt.kf[k].g = kfs[k].gaussians;
+      pt.kf[k].base = base[k];
+    }
+    DQO_CUDA(c, launch_preprocess_batch(pt, nkf, max_n, pb, s_));
+    launches += 1;
+  }
+  // ---- pair offsets, depth order (one sort over all keyframes: ranks keep each
+  // keyframe's (depth, index) order because its indices are contiguous)
+  int sel = 0;
+  DQO_CUDA(c, launch_exclusive_scan(as<uint32_t>(B.ntiles), as<uint32_t>(B.offsets), N, as<uint64_t>(B.scan_scratch),
+                                    d_total, s_));
+  DQO_CUDA(c, radix_sort_u32(as<uint32_t>(B.zkey_a), as<uint32_t>(B.zkey_b), as<uint32_t>(B.zval_a),
+                             as<uint32_t>(B.zval_b), N, 32, as<uint32_t>(B.depth_hist),
+                             as<uint64_t>(B.depth_scan_scratch), &sel, s_));
+  const uint32_t* order = sel ? as<uint32_t>(B.zval_b) : as<uint32_t>(B.zval_a);
+  DQO_CUDA(c, launch_rank_scatter(order, N, as<uint32_t>(B.rank), s_));
+  launches += scan_launches(N) + sort_launches(N, 32) + 1;
+
+  if (sizing) {
+    DQO_CUDA(c, cudaMemcpyAsync(B.host, d_total, 8, cudaMemcpyDeviceToHost, s_));
+    DQO_CUDA(c, cudaStreamSynchronize(s_));
+    const uint64_t m = B.host[0];
+    if (m >= (uint64_t(1) << 31)) return DQO_ENOMEM;
+    const uint64_t cap = m + m / 4 + 65536;
+    DQO_CUDA(c, ensure(B.pair_a, 8 * cap));
+    DQO_CUDA(c, ensure(B.pair_b, 8 * cap));
+    DQO_CUDA(c, ensure(B.list, 4 * cap));
+    DQO_CUDA(c, ensure(B.hist, 4 * radix_scratch_words((int64_t)cap)));
+    DQO_CUDA(c, ensure(B.scan_scratch, 8 * std::max(scan_scratch_words(N),
+                                                    scan_scratch_words(radix_scratch_words((int64_t)cap)))));
+    B.capacity = cap;
+    B.sig = sig;
+  }
+  const uint64_t cap = B.capacity;
+
+  // ---- pairs of the joint tile numbering, pair sort, tile ranges (counts on the device)
+  {
+    EmitTable et;
+    for (int k = 0; k < nkf; ++k) {
+      et.kf[k].base = base[k];
+      et.kf[k].n = kfs[k].gaussians.n;
+      et.kf[k].tile_off = toff[k];
+      et.kf[k].ntx = rp[k].ntx;
+    }
+    DQO_CUDA(c, launch_emit_pairs_batch(et, nkf, max_n, as<ushort4>(B.rect), as<uint32_t>(B.offsets),
+                                        as<uint32_t>(B.rank), rank_bits, cap, as<uint64_t>(B.pair_a), d_overflow,
+                                        s_));
+    int psel = 0;
+    DQO_CUDA(c, radix_sort_u64(as<uint64_t>(B.pair_a), as<uint64_t>(B.pair_b), (int64_t)cap, end_bit,
+                               as<uint32_t>(B.hist), as<uint64_t>(B.scan_scratch), &psel, s_, d_total));
+    DQO_CUDA(c, launch_tile_ranges_u64(psel ? as<uint64_t>(B.pair_b) : as<uint64_t>(B.pair_a), (int64_t)cap,
+                                       rank_bits, order, as<uint2>(B.ranges), as<uint32_t>(B.list), s_, d_total));
+    launches += 2 + sort_launches((int64_t)cap, end_bit);
+  }
+
+  // ---- persistent forward + backward over all tiles, losses, projection adjoint
+  {
+    StepTable tt;
+    LossTable lt;
+    PreBwdTable bt;
+    for (int k = 0; k < nkf; ++k) {
+      const dqo_keyframe& kf = kfs[k];
+      const int64_t po = poff[k];
+      BlendFwdArgs& a = tt.f[k];
+      a.rp = rp[k];
+      a.p0 = pb.p0;
+      a.p1 = pb.p1;
+      a.p2 = pb.p2;
+      a.gid = pb.gid;
+      a.ranges = as<uint2>(B.ranges) + toff[k];
+      a.list = as<uint32_t>(B.list);
+      a.t_rgb = kf.targets.rgb;
+      a.t_depth = kf.targets.depth;
+      a.t_gt = kf.targets.gt_id;
+      a.o_rgb = kf.out.rgb;
+      a.o_depth = kf.out.depth;
+      a.o_alpha = kf.out.alpha;
+      a.o_ins = kf.out.ins;
+      a.o_id = kf.out.id_map;
+      a.T_final = as<float>(B.T_final) + po;
+      a.n_contrib = as<uint32_t>(B.n_contrib) + po;
+      a.dl_rgb = as<float>(B.dl_rgb) + 3 * po;
+      a.dl_depth = as<float>(B.dl_depth) + po;
+      a.dl_ins = as<float>(B.dl_ins) + po;
+      a.loss_part = as<float>(B.loss_part) + 3 * (int64_t)toff[k];
+      a.o_mask = kf.out.update_mask;
+      BlendBwdArgs& bb = tt.b[k];
+      bb.rp = rp[k];
+      bb.p0 = pb.p0;
+      bb.p1 = pb.p1;
+      bb.p2 = pb.p2;
+      bb.ranges = a.ranges;
+      bb.list = a.list;
+      bb.t_gt = kf.targets.gt_id;
+      bb.T_final = a.T_final;
+      bb.n_contrib = a.n_contrib;
+      bb.g_rgb = a.dl_rgb;
+      bb.g_depth = a.dl_depth;
+      bb.g_alpha = nullptr;
+      bb.g_ins = a.dl_ins;
+      bb.grad2d = as<float>(B.grad2d);
+      tt.tile_off[k] = toff[k];
+      lt.kf[k].part = a.loss_part;
+      lt.kf[k].tiles = (int)(toff[k + 1] - toff[k]);
+      lt.kf[k].lambda_ins = rp[k].lambda_ins;
+      lt.kf[k].scale = (float)(1.0 / ((double)rp[k].W * (double)rp[k].H));
+      lt.kf[k].loss = kf.out.loss;
+      PreBwdArgs& pa = bt.kf[k];
+      pa.rp = rp[k];
+      pa.n = kf.gaussians.n;
+      pa.means = kf.gaussians.means;
+      pa.log_scales = kf.gaussians.log_scales;
+      pa.quats = kf.gaussians.quats;
+      pa.opacity_logit = kf.gaussians.opacity_logit;
+      pa.ntiles = as<uint32_t>(B.ntiles) + base[k];
+      pa.grad2d = as<float>(B.grad2d) + 12 * base[k];
+      pa.d_means = kf.grads.means;
+      pa.d_log_scales = kf.grads.log_scales;
+      pa.d_quats = kf.grads.quats;
+      pa.d_logit = kf.grads.opacity_logit;
+      pa.d_rgb = kf.grads.rgb;
+    }
+    tt.tile_off[nkf] = toff[nkf];
+    tt.nkf = nkf;
+    DQO_CUDA(c, launch_blend_step(tt, d_queue, s->tile_w, with_id, ctas_per_sm, B.sms, s_));
+    DQO_CUDA(c, launch_loss_reduce_batch(lt, nkf, s_));
+    DQO_CUDA(c, launch_preprocess_backward_batch(bt, nkf, max_n, s_));
+    launches += 3;
+  }
+  if (run_fits) DQO_CUDA(c, cudaStreamWaitEvent(s_, B.join, 0));
+  c->launches += launches;
+  return DQO_OK;
+}
+
+dqo_status dqo_batch_check(dqo_ctx* c, uint64_t* pairs, int* overflow) {
+  if (!c) return DQO_EINVAL;
+  if (pairs) *pairs = 0;
+  if (overflow) *overflow = 0;
+  if (!c->b.counters.p) return DQO_OK;
+  DQO_CUDA(c, cudaSetDevice(c->device));
+  DQO_CUDA(c, cudaDeviceSynchronize());
+  uint64_t h[2] = {0, 0};
+  DQO_CUDA(c, cudaMemcpy(h, c->b.counters.p, 16, cudaMemcpyDeviceToHost));
+  const int over = (int)(h[1] >> 32) != 0;
+  if (pairs) *pairs = h[0];
+  if (overflow) *overflow = over;
+  if (over) c->b.capacity = 0;  // the next step sizes again
+  return DQO_OK;
+}
+
+dqo_status dqo_batch_tune(dqo_ctx* c, dqo_settings* s, int32_t nkf, const dqo_keyframe* kfs,
+                          const dqo_fit_batch* fits, int32_t reps, int32_t* ctas_per_sm, float* ms,
+                          dqo_stream stream_) {
+  if (!c || !s || !ctas_per_sm || reps < 1) return DQO_EINVAL;
+  static const int shapes[3][2] = {{16, 16}, {8, 32}, {32, 8}};
+  static const int ctas[3] = {2, 3, 4};
+  cudaStream_t s_ = reinterpret_cast<cudaStream_t>(stream_);
+  DQO_CUDA(c, cudaSetDevice(c->device));
+  cudaEvent_t e0, e1;
+  DQO_CUDA(c, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return DQO_ECUDA;
+  }
+  float best = 0.f;
+  int best_i = -1;
+  dqo_status st = DQO_OK;
+  for (int i = 0; i < 9 && st == DQO_OK; ++i) {
+    dqo_settings t = *s;
+    t.tile_w = shapes[i / 3][0];
+    t.tile_h = shapes[i / 3][1];
+    const int cps = ctas[i % 3];
+    st = dqo_batch_step(c, &t, nkf, kfs, fits, cps, stream_);  // warm-up (sizes the layout)
+    if (st != DQO_OK) break;
+    cudaEventRecord(e0, s_);
+    for (int r = 0; r < reps && st == DQO_OK; ++r) st = dqo_batch_step(c, &t, nkf, kfs, fits, cps, stream_);
+    cudaEventRecord(e1, s_);
+    if (st != DQO_OK) break;
+    float t_ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t_ms, e0, e1) != cudaSuccess) {
+      st = DQO_ECUDA;
+      break;
+    }
+    t_ms /= (float)reps;
+    if (ms) ms[i] = t_ms;
+    if (best_i < 0 || t_ms < best) {
+      best = t_ms;
+      best_i = i;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != DQO_OK) return st;
+  s->tile_w = shapes[best_i / 3][0];
+  s->tile_h = shapes[best_i / 3][1];
+  *ctas_per_sm = ctas[best_i % 3];
+  return DQO_OK;
+}
+
 dqo_status dqo_quadric_canonical(int32_t nq, const float* params, float* out, dqo_stream stream_) {
   if (nq < 0 || (nq > 0 && (!params || !out))) return DQO_EINVAL;
   if (launch_quadric_canonical(nq, params, out, reinterpret_cast<cudaStream_t>(stream_)) != cudaSuccess)
@@ -805,7 +1157,24 @@ dqo_status dqo_mlp_check(dqo_ctx* c, int* timed_out) {
   DQO_CUDA(c, cudaMemcpy(&v, wk.err, sizeof(int), cudaMemcpyDeviceToHost));
   if (v) DQO_CUDA(c, cudaMemset(wk.err, 0, sizeof(int)));
   *timed_out = v;
-  return DQO_OK;
+  return v ? DQO_ETIMEOUT : DQO_OK;
+}
+
+dqo_status dqo_wait_probe(dqo_ctx* c, dqo_stream stream_) {
+  if (!c) return DQO_EINVAL;
+  DQO_CUDA(c, cudaSetDevice(c->device));
+  int* flag = nullptr;
+  DQO_CUDA(c, cudaMalloc(&flag, sizeof(int)));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+  int v = 0;
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = launch_bounded_wait_probe(flag, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&v, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(flag);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  c->launches += 1;
+  return v ? DQO_ETIMEOUT : DQO_OK;
 }
 
 }  // extern "C"

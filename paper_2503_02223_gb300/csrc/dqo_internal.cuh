@@ -144,6 +144,28 @@ cudaError_t launch_preprocess(const RasterParams& rp, const dqo_gaussians& g, co
                               cudaStream_t s);
 cudaError_t launch_preprocess_backward(const PreBwdArgs& a, cudaStream_t s);
 
+// ----------------------------------------------------------------------------- batches
+// Per-keyframe tables of a batch travel as __grid_constant__ kernel parameters (captured
+// with the launch in a CUDA graph; no staging buffer).
+
+constexpr int kMaxBatch = 16;
+
+// One keyframe of a batch for projection: its parameters, Gaussians and global offset.
+struct PreKf {
+  RasterParams rp;
+  dqo_gaussians g;
+  int64_t base;
+};
+struct PreTable {
+  PreKf kf[kMaxBatch];
+};
+struct PreBwdTable {
+  PreBwdArgs kf[kMaxBatch];
+};
+cudaError_t launch_preprocess_batch(const PreTable& t, int nkf, int64_t max_n, const ProjBuffers& out,
+                                    cudaStream_t s);
+cudaError_t launch_preprocess_backward_batch(const PreBwdTable& t, int nkf, int64_t max_n, cudaStream_t s);
+
 // Exclusive scan of n uint32 values; total (uint64) written to *total.  scratch must
 // hold scan_scratch_words(n) uint64 words.
 size_t scan_scratch_words(int64_t n);
@@ -156,8 +178,8 @@ size_t radix_scratch_words(int64_t n);
 cudaError_t radix_sort_u32(uint32_t* keys_a, uint32_t* keys_b, uint32_t* vals_a, uint32_t* vals_b,
                            int64_t n, int end_bit, uint32_t* hist_scratch, uint64_t* scan_scratch,
                            int* sel, cudaStream_t s);
-cudaError_t radix_sort_u64(uint64_t* keys_a, uint64_t* keys_b, int64_t n, int end_bit,
-                           uint32_t* hist_scratch, uint64_t* scan_scratch, int* sel, cudaStream_t s);
+cudaError_t radix_sort_u64(uint64_t* keys_a, uint64_t* keys_b, int64_t n, int end_bit, uint32_t* hist_scratch,
+                           uint64_t* scan_scratch, int* sel, cudaStream_t s, const uint64_t* n_dev = nullptr);
 
 cudaError_t launch_rank_scatter(const uint32_t* order, int64_t n, uint32_t* rank, cudaStream_t s);
 cudaError_t launch_emit_pairs_u32(const ushort4* rect, const uint32_t* offsets, const uint32_t* rank,
@@ -167,12 +189,48 @@ cudaError_t launch_emit_pairs_u64(const ushort4* rect, const uint32_t* offsets, 
 cudaError_t launch_tile_ranges_u32(const uint32_t* keys, int64_t m, int rank_bits, const uint32_t* order,
                                    uint2* ranges, uint32_t* list, cudaStream_t s);
 cudaError_t launch_tile_ranges_u64(const uint64_t* keys, int64_t m, int rank_bits, const uint32_t* order,
-                                   uint2* ranges, uint32_t* list, cudaStream_t s);
+                                   uint2* ranges, uint32_t* list, cudaStream_t s, const uint64_t* m_dev = nullptr);
+
+// One keyframe of a batch for pair emission: its Gaussians occupy global indices
+// [base, base + n), its tiles [tile_off, tile_off + ntx * nty) of the joint numbering.
+struct EmitKf {
+  int64_t base;
+  int64_t n;
+  uint32_t tile_off;
+  int ntx;
+};
+struct EmitTable {
+  EmitKf kf[16];
+};
+cudaError_t launch_emit_pairs_batch(const EmitTable& t, int nkf, int64_t max_n, const ushort4* rect,
+                                    const uint32_t* offsets, const uint32_t* rank, int rank_bits, uint64_t capacity,
+                                    uint64_t* keys, uint32_t* overflow, cudaStream_t s);
 
 cudaError_t launch_blend_forward(const BlendFwdArgs& a, bool with_id, cudaStream_t s);
 cudaError_t launch_loss_reduce(const float* part, int tiles, float lambda_ins, float scale, float* loss,
                                cudaStream_t s);
 cudaError_t launch_blend_backward(const BlendBwdArgs& a, cudaStream_t s);
+
+// Persistent forward + backward over the tiles of a batch (tables in device memory).
+// ctas_per_sm <= 0: as many as fit.
+struct StepTable {
+  BlendFwdArgs f[16];
+  BlendBwdArgs b[16];
+  uint32_t tile_off[17];  // keyframe k owns joint tiles [tile_off[k], tile_off[k+1])
+  int nkf;
+};
+cudaError_t launch_blend_step(const StepTable& t, uint32_t* queue, int tile_w, bool with_id, int ctas_per_sm,
+                              int sms, cudaStream_t s);
+struct LossKf {
+  const float* part;
+  int tiles;
+  float lambda_ins, scale;
+  float* loss;
+};
+struct LossTable {
+  LossKf kf[16];
+};
+cudaError_t launch_loss_reduce_batch(const LossTable& t, int nkf, cudaStream_t s);
 
 cudaError_t launch_quadric_project(int nq, const float* params, int nv, const float* P, const int32_t* q_ptr,
                                    const int32_t* pair_v, int npairs, float* conic, float* bbox, uint8_t* valid,
@@ -225,6 +283,7 @@ __device__ __forceinline__ void write_bf16_copies(const MlpState& st, int i, flo
 }
 
 cudaError_t mlp_gemm_setup();
+cudaError_t launch_bounded_wait_probe(int* flag, cudaStream_t s);
 cudaError_t launch_mlp_features(int nq, int nv, const float* P, const int32_t* q_ptr, const int32_t* pair_v,
                                 int npairs, const float* obs, const int32_t* counts, float inv_scale, uint16_t* X,
                                 uint16_t* XT, int64_t ldt, cudaStream_t s);

@@ -87,8 +87,10 @@ __device__ __forceinline__ void slot_ids_for_round(const uint32_t* s_mask, const
   }
 }
 
+// Forward of one tile (tile index local to a's image).  Called by all threads of a
+// block; uses the block's shared memory and barriers.
 template <int TW, bool kId>
-__global__ void __launch_bounds__(kThreads) k_blend_forward(BlendFwdArgs a) {
+__device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const int tile) {
   constexpr int NW = kThreads / 32;
   // per-warp staging of the Gaussians that can reach the warp's pixels
   __shared__ float4 s_q0[NW][32], s_q1[NW][32], s_q2[NW][32];
@@ -100,7 +102,6 @@ __global__ void __launch_bounds__(kThreads) k_blend_forward(BlendFwdArgs a) {
   __shared__ uint32_t s_nslots;
 
   const RasterParams& rp = a.rp;
-  const int tile = blockIdx.x;
   const int tx = tile % rp.ntx, ty = tile / rp.ntx;
   int px, py;
   float wx0, wy0;
@@ -350,9 +351,14 @@ __global__ void __launch_bounds__(kThreads) k_blend_forward(BlendFwdArgs a) {
   }
 }
 
+template <int TW, bool kId>
+__global__ void __launch_bounds__(kThreads) k_blend_forward(BlendFwdArgs a) {
+  blend_fwd_tile<TW, kId>(a, (int)blockIdx.x);
+}
+
 // Deterministic sum of the per-tile loss partials in double, scaled by 1/(HW).
-__global__ void k_loss_reduce(const float* __restrict__ part, int tiles, float lambda_ins, float scale,
-                              float* __restrict__ loss) {
+__device__ __forceinline__ void loss_reduce(const float* __restrict__ part, int tiles, float lambda_ins, float scale,
+                                            float* __restrict__ loss) {
   __shared__ double s[3][kThreads];
   double acc[3] = {0, 0, 0};
   for (int t = threadIdx.x; t < tiles; t += kThreads)
@@ -374,6 +380,17 @@ __global__ void k_loss_reduce(const float* __restrict__ part, int tiles, float l
     loss[2] = (float)i;
     loss[3] = (float)(r + d + (double)lambda_ins * i);
   }
+}
+
+__global__ void k_loss_reduce(const float* __restrict__ part, int tiles, float lambda_ins, float scale,
+                              float* __restrict__ loss) {
+  loss_reduce(part, tiles, lambda_ins, scale, loss);
+}
+
+// One block per keyframe of a batch.
+__global__ void k_loss_reduce_batch(const __grid_constant__ LossTable t) {
+  const LossKf& k = t.kf[blockIdx.x];
+  if (k.loss) loss_reduce(k.part, k.tiles, k.lambda_ins, k.scale, k.loss);
 }
 
 // Sum of 16 per-lane values over the warp with a transposing butterfly: after it, lane l
@@ -416,15 +433,15 @@ __device__ __forceinline__ void warp_transpose_sum16(float v[16]) {
   v[0] += __shfl_xor_sync(0xFFFFFFFFu, v[0], 1);
 }
 
+// Backward of one tile (local tile index); warp-autonomous, no block barrier.
 template <int TW>
-__global__ void __launch_bounds__(kThreads) k_blend_backward(BlendBwdArgs a) {
+__device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const int tile) {
   constexpr int NW = kThreads / 32;
   __shared__ float4 s_q0[NW][32], s_q1[NW][32], s_q2[NW][32];
   __shared__ uint32_t s_g[NW][32];
   __shared__ int32_t s_pos[NW][32];
 
   const RasterParams& rp = a.rp;
-  const int tile = blockIdx.x;
   const int tx = tile % rp.ntx, ty = tile / rp.ntx;
   int px, py;
   float wx0, wy0;
@@ -534,6 +551,37 @@ __global__ void __launch_bounds__(kThreads) k_blend_backward(BlendBwdArgs a) {
 }
 
 template <int TW>
+__global__ void __launch_bounds__(kThreads) k_blend_backward(BlendBwdArgs a) {
+  blend_bwd_tile<TW>(a, (int)blockIdx.x);
+}
+
+// Persistent step over the tiles of a batch of keyframes: each CTA takes tiles from an
+// atomic work queue (joint tile numbering, keyframe k owning [tile_off[k],
+// tile_off[k+1])) and runs the tile's forward with the fused losses and then its
+// backward.  A tile's backward needs only its own pixels' forward state (transmittance,
+// blended count, dL/dpixel), written by the same threads just before, so no grid-wide
+// barrier separates the two.  Per-keyframe arguments are read from the kernel's
+// parameter table.
+template <int TW, bool kId>
+__global__ void __launch_bounds__(kThreads, 4) k_blend_step(const __grid_constant__ StepTable t,
+                                                            uint32_t* __restrict__ queue) {
+  __shared__ uint32_t s_item;
+  const uint32_t total = t.tile_off[t.nkf];
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
+    __syncthreads();
+    const uint32_t it = s_item;
+    if (it >= total) break;
+    int k = 0;
+    while (k + 1 < t.nkf && t.tile_off[k + 1] <= it) ++k;
+    const int tile = (int)(it - t.tile_off[k]);
+    blend_fwd_tile<TW, kId>(t.f[k], tile);
+    blend_bwd_tile<TW>(t.b[k], tile);
+    __syncthreads();
+  }
+}
+
+template <int TW>
 cudaError_t launch_fwd_tw(const BlendFwdArgs& a, bool with_id, cudaStream_t s) {
   const unsigned tiles = (unsigned)(a.rp.ntx * a.rp.nty);
   if (with_id)
@@ -570,6 +618,47 @@ cudaError_t launch_blend_backward(const BlendBwdArgs& a, cudaStream_t s) {
     case 32: k_blend_backward<32><<<tiles, kThreads, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+}  // namespace dqo
+
+namespace dqo {
+namespace {
+
+template <int TW, bool kId>
+cudaError_t step_tw(const StepTable& t, uint32_t* queue, int ctas_per_sm, int sms, cudaStream_t s) {
+  int occ = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_blend_step<TW, kId>, kThreads, 0);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) occ = 1;
+  const int per = ctas_per_sm > 0 ? (ctas_per_sm < occ ? ctas_per_sm : occ) : occ;
+  const uint32_t total = t.tile_off[t.nkf];
+  unsigned grid = (unsigned)(per * sms);
+  if (grid > total) grid = total;
+  if (grid == 0) return cudaSuccess;
+  k_blend_step<TW, kId><<<grid, kThreads, 0, s>>>(t, queue);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_blend_step(const StepTable& t, uint32_t* queue, int tile_w, bool with_id, int ctas_per_sm,
+                              int sms, cudaStream_t s) {
+  switch (tile_w * 2 + (with_id ? 1 : 0)) {
+    case 16: return step_tw<8, false>(t, queue, ctas_per_sm, sms, s);
+    case 17: return step_tw<8, true>(t, queue, ctas_per_sm, sms, s);
+    case 32: return step_tw<16, false>(t, queue, ctas_per_sm, sms, s);
+    case 33: return step_tw<16, true>(t, queue, ctas_per_sm, sms, s);
+    case 64: return step_tw<32, false>(t, queue, ctas_per_sm, sms, s);
+    case 65: return step_tw<32, true>(t, queue, ctas_per_sm, sms, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_loss_reduce_batch(const LossTable& t, int nkf, cudaStream_t s) {
+  if (nkf == 0) return cudaSuccess;
+  k_loss_reduce_batch<<<(unsigned)nkf, kThreads, 0, s>>>(t);
   return cudaGetLastError();
 }
 

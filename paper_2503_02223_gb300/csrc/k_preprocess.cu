@@ -133,10 +133,11 @@ __device__ __forceinline__ void load_rows3(const float* __restrict__ src, int64_
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_preprocess(RasterParams rp, dqo_gaussians g, ProjBuffers o) {
-  __shared__ float stage[kThreads / 32][96];
+// Gaussian i of g (inputs at i, outputs at base + i of o; the depth-sort value is the
+// output index).  Called by every thread of a block; `stage` is the block's staging area.
+__device__ __forceinline__ void preprocess_item(const RasterParams& rp, const dqo_gaussians& g, const ProjBuffers& o,
+                                                int64_t i, int64_t base, float (*stage)[96]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   const int64_t wbase = i - lane;
   const bool full = wbase + 32 <= g.n;
   const bool in = i < g.n;
@@ -164,8 +165,9 @@ __global__ void __launch_bounds__(kThreads) k_preprocess(RasterParams rp, dqo_ga
     const uint32_t og = (__ldg(g.flags + i) & 1u) ? 0x80000000u : 0u;
     const uint32_t idbits = (has_obj ? (uint32_t)id : kNoObject) | og;
     const float sc = -0.5f * kLog2e;
-    o.p0[i] = make_float4(f.xy[0], f.xy[1], sc * f.conic[0], 2.f * sc * f.conic[1]);
-    o.p1[i] = make_float4(sc * f.conic[2], f.opac, f.pc[2], __uint_as_float(idbits));
+    const int64_t j = base + i;
+    o.p0[j] = make_float4(f.xy[0], f.xy[1], sc * f.conic[0], 2.f * sc * f.conic[1]);
+    o.p1[j] = make_float4(sc * f.conic[2], f.opac, f.pc[2], __uint_as_float(idbits));
     // Level of the alpha-support ellipse in the exponent's log2 units: alpha can reach
     // alpha_min only where -(a' dx^2 + b' dx dy + c' dy^2) <= log2(o / alpha_min).  Widened
     // by a small margin (the blend kernels cull with it, so it must be conservative);
@@ -179,19 +181,40 @@ __global__ void __launch_bounds__(kThreads) k_preprocess(RasterParams rp, dqo_ga
         lvl = q2 * (1.f + 1e-4f) + 1e-3f;
       }
     }
-    o.p2[i] = make_float4(rgb[0], rgb[1], rgb[2], lvl);
-    o.rect[i] = f.rect;
-    o.ntiles[i] = f.ntiles;
-    o.zkey[i] = f.visible ? __float_as_uint(f.pc[2]) : 0xFFFFFFFFu;
-    o.zval[i] = (uint32_t)i;
-    o.gid[i] = has_obj ? (uint32_t)id : 0xFFFFFFFFu;
+    o.p2[j] = make_float4(rgb[0], rgb[1], rgb[2], lvl);
+    o.rect[j] = f.rect;
+    o.ntiles[j] = f.ntiles;
+    o.zkey[j] = f.visible ? __float_as_uint(f.pc[2]) : 0xFFFFFFFFu;
+    o.zval[j] = (uint32_t)j;
+    o.gid[j] = has_obj ? (uint32_t)id : 0xFFFFFFFFu;
   }
   const uint32_t vis = __ballot_sync(0xFFFFFFFFu, in && f.visible);
   if (lane == 0 && vis) atomicAdd(o.n_visible, (uint32_t)__popc(vis));
 }
 
-__global__ void __launch_bounds__(kThreads) k_preprocess_backward(PreBwdArgs a) {
-  const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+__global__ void __launch_bounds__(kThreads) k_preprocess(RasterParams rp, dqo_gaussians g, ProjBuffers o) {
+  __shared__ float stage[kThreads / 32][96];
+  preprocess_item(rp, g, o, (int64_t)blockIdx.x * kThreads + threadIdx.x, 0, stage);
+}
+
+// Keyframe blockIdx.y of a batch.
+__global__ void __launch_bounds__(kThreads) k_preprocess_batch(const __grid_constant__ PreTable t, ProjBuffers o) {
+  __shared__ float stage[kThreads / 32][96];
+  const PreKf& kf = t.kf[blockIdx.y];
+  if ((int64_t)blockIdx.x * kThreads >= kf.g.n) return;  // uniform over the block
+  preprocess_item(kf.rp, kf.g, o, (int64_t)blockIdx.x * kThreads + threadIdx.x, kf.base, stage);
+}
+
+template <bool kAtomic>
+__device__ __forceinline__ void add_grad(float* p, float v) {
+  if (kAtomic) atomicAdd(p, v);
+  else *p += v;
+}
+
+// Adjoint of Gaussian i (gradients added to a's parameter gradients; atomically when
+// several keyframes of a batch may share them).
+template <bool kAtomic>
+__device__ __forceinline__ void preprocess_backward_item(const PreBwdArgs& a, int64_t i) {
   if (i >= a.n) return;
   if (a.ntiles[i] == 0) return;  // culled: never blended, zero gradient
   const RasterParams& rp = a.rp;
@@ -211,11 +234,11 @@ __global__ void __launch_bounds__(kThreads) k_preprocess_backward(PreBwdArgs a) 
   const float gy = cb * r0.x + cc * r0.y;
   const float ga = -0.5f * r0.z, gb = -r0.w, gc = -0.5f * r1.x;
   if (a.d_rgb) {
-    a.d_rgb[3 * i + 0] += r1.z;
-    a.d_rgb[3 * i + 1] += r1.w;
-    a.d_rgb[3 * i + 2] += r2.x;
+    add_grad<kAtomic>(a.d_rgb + 3 * i + 0, r1.z);
+    add_grad<kAtomic>(a.d_rgb + 3 * i + 1, r1.w);
+    add_grad<kAtomic>(a.d_rgb + 3 * i + 2, r2.x);
   }
-  if (a.d_logit) a.d_logit[i] += r1.y * f.opac * (1.f - f.opac);
+  if (a.d_logit) add_grad<kAtomic>(a.d_logit + i, r1.y * f.opac * (1.f - f.opac));
   // dL/dSigma' = -Cn Gm Cn, Cn = [[a, b], [b, c]], Gm = [[ga, gb/2], [gb/2, gc]]
   const float m00 = ca * ga + cb * 0.5f * gb, m01 = ca * 0.5f * gb + cb * gc;
   const float m10 = cb * ga + cc * 0.5f * gb, m11 = cb * 0.5f * gb + cc * gc;
@@ -261,11 +284,11 @@ __global__ void __launch_bounds__(kThreads) k_preprocess_backward(PreBwdArgs a) 
                dJ02 * (2.f * rp.fx * x * iz3) + dJ11 * (-rp.fy * iz2) + dJ12 * (2.f * rp.fy * y * iz3);
   if (a.d_means) {
 #pragma unroll
-    for (int j = 0; j < 3; ++j) a.d_means[3 * i + j] += W[j] * dpc0 + W[4 + j] * dpc1 + W[8 + j] * dpc2;
+    for (int j = 0; j < 3; ++j) add_grad<kAtomic>(a.d_means + 3 * i + j, W[j] * dpc0 + W[4 + j] * dpc1 + W[8 + j] * dpc2);
   }
   if (a.d_log_scales) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) a.d_log_scales[3 * i + k] += ds[k] * f.s[k];
+    for (int k = 0; k < 3; ++k) add_grad<kAtomic>(a.d_log_scales + 3 * i + k, ds[k] * f.s[k]);
   }
   if (a.d_quats) {
     const float w = f.qn[0], qx = f.qn[1], qy = f.qn[2], qz = f.qn[3];
@@ -279,8 +302,18 @@ __global__ void __launch_bounds__(kThreads) k_preprocess_backward(PreBwdArgs a) 
                    qy * dR[1][2] + qx * dR[2][0] + qy * dR[2][1]);
     const float dot = dq[0] * w + dq[1] * qx + dq[2] * qy + dq[3] * qz;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) a.d_quats[4 * i + k] += (dq[k] - f.qn[k] * dot) * f.qinv;
+    for (int k = 0; k < 4; ++k) add_grad<kAtomic>(a.d_quats + 4 * i + k, (dq[k] - f.qn[k] * dot) * f.qinv);
   }
+}
+
+__global__ void __launch_bounds__(kThreads) k_preprocess_backward(PreBwdArgs a) {
+  preprocess_backward_item<false>(a, (int64_t)blockIdx.x * kThreads + threadIdx.x);
+}
+
+// Keyframe blockIdx.y of a batch (its ntiles and grad2d pointers already offset to its
+// first Gaussian); gradients added atomically.
+__global__ void __launch_bounds__(kThreads) k_preprocess_backward_batch(const __grid_constant__ PreBwdTable t) {
+  preprocess_backward_item<true>(t.kf[blockIdx.y], (int64_t)blockIdx.x * kThreads + threadIdx.x);
 }
 
 }  // namespace
@@ -290,6 +323,21 @@ cudaError_t launch_preprocess(const RasterParams& rp, const dqo_gaussians& g, co
   if (g.n == 0) return cudaSuccess;
   const int64_t blocks = (g.n + kThreads - 1) / kThreads;
   k_preprocess<<<(unsigned)blocks, kThreads, 0, s>>>(rp, g, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess_batch(const PreTable& t, int nkf, int64_t max_n, const ProjBuffers& out,
+                                    cudaStream_t s) {
+  if (nkf == 0 || max_n == 0) return cudaSuccess;
+  const dim3 grid((unsigned)((max_n + kThreads - 1) / kThreads), (unsigned)nkf);
+  k_preprocess_batch<<<grid, kThreads, 0, s>>>(t, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_preprocess_backward_batch(const PreBwdTable& t, int nkf, int64_t max_n, cudaStream_t s) {
+  if (nkf == 0 || max_n == 0) return cudaSuccess;
+  const dim3 grid((unsigned)((max_n + kThreads - 1) / kThreads), (unsigned)nkf);
+  k_preprocess_backward_batch<<<grid, kThreads, 0, s>>>(t);
   return cudaGetLastError();
 }
 

@@ -123,9 +123,19 @@ __global__ void __launch_bounds__(kThreads) k_scan_down(const uint32_t* __restri
 // ---------------------------------------------------------------- LSD radix sort passes
 
 // Per-CTA digit histogram, stored digit-major: hist[d * nblocks + b].
+// Element count: n, or the smaller of n and *n_dev when the count lives on the device
+// (launches sized for a capacity n).
+__device__ __forceinline__ int64_t live_count(int64_t n, const uint64_t* n_dev) {
+  if (!n_dev) return n;
+  const uint64_t d = *n_dev;
+  return d < (uint64_t)n ? (int64_t)d : n;
+}
+
 template <typename K>
-__global__ void __launch_bounds__(kThreads) k_radix_hist(const K* __restrict__ keys, int64_t n, int shift,
+__global__ void __launch_bounds__(kThreads) k_radix_hist(const K* __restrict__ keys, int64_t n_cap,
+                                                         const uint64_t* __restrict__ n_dev, int shift,
                                                          uint32_t* __restrict__ hist) {
+  const int64_t n = live_count(n_cap, n_dev);
   __shared__ uint32_t h[kRadixBins];
   h[threadIdx.x] = 0;
   __syncthreads();
@@ -146,8 +156,10 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist(const K* __restrict__ k
 template <typename K, bool kVals>
 __global__ void __launch_bounds__(kThreads) k_radix_scatter(const K* __restrict__ kin, K* __restrict__ kout,
                                                             const uint32_t* __restrict__ vin,
-                                                            uint32_t* __restrict__ vout, int64_t n, int shift,
+                                                            uint32_t* __restrict__ vout, int64_t n_cap,
+                                                            const uint64_t* __restrict__ n_dev, int shift,
                                                             const uint32_t* __restrict__ offs) {
+  const int64_t n = live_count(n_cap, n_dev);
   __shared__ uint32_t cnt[kThreads / 32][kRadixBins];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int d = threadIdx.x; d < (kThreads / 32) * kRadixBins; d += kThreads) (&cnt[0][0])[d] = 0;
@@ -222,10 +234,40 @@ __global__ void __launch_bounds__(kThreads) k_emit_pairs(const ushort4* __restri
     for (int tx = r.x; tx < r.z; ++tx) keys[o++] = ((K)((uint32_t)ty * ntx + tx) << rank_bits) | rk;
 }
 
+// Pairs of a batch of keyframes: Gaussian i of keyframe blockIdx.y (global index
+// base + i) covers tiles tile_off + ty * ntx + tx of the batch's joint tile numbering.
+// Pairs past `capacity` are not written; *overflow is set instead.
 template <typename K>
-__global__ void __launch_bounds__(kThreads) k_tile_ranges(const K* __restrict__ keys, int64_t m, int rank_bits,
+__global__ void __launch_bounds__(kThreads) k_emit_pairs_batch(const __grid_constant__ EmitTable t,
+                                                               const ushort4* __restrict__ rect,
+                                                               const uint32_t* __restrict__ offsets,
+                                                               const uint32_t* __restrict__ rank, int rank_bits,
+                                                               uint64_t capacity, K* __restrict__ keys,
+                                                               uint32_t* __restrict__ overflow) {
+  const EmitKf& kf = t.kf[blockIdx.y];
+  const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (i >= kf.n) return;
+  const int64_t gi = kf.base + i;
+  const ushort4 r = rect[gi];
+  if (r.z <= r.x || r.w <= r.y) return;
+  uint64_t o = offsets[gi];
+  const uint64_t cnt = (uint64_t)(r.z - r.x) * (uint64_t)(r.w - r.y);
+  if (o + cnt > capacity) {
+    atomicExch(overflow, 1u);
+    return;
+  }
+  const K rk = (K)rank[gi];
+  for (int ty = r.y; ty < r.w; ++ty)
+    for (int tx = r.x; tx < r.z; ++tx)
+      keys[o++] = ((K)(kf.tile_off + (uint32_t)ty * kf.ntx + tx) << rank_bits) | rk;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_tile_ranges(const K* __restrict__ keys, int64_t m_cap,
+                                                          const uint64_t* __restrict__ m_dev, int rank_bits,
                                                           const uint32_t* __restrict__ order,
                                                           uint2* __restrict__ ranges, uint32_t* __restrict__ list) {
+  const int64_t m = live_count(m_cap, m_dev);
   const int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (p >= m) return;
   const K k = keys[p];
@@ -239,7 +281,7 @@ inline unsigned grid_for(int64_t n, int per) { return (unsigned)((n + per - 1) /
 
 template <typename K, bool kVals>
 cudaError_t radix_sort_impl(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n, int end_bit, uint32_t* hist,
-                            uint64_t* scan_scratch, int* sel, cudaStream_t s) {
+                            uint64_t* scan_scratch, int* sel, cudaStream_t s, const uint64_t* n_dev = nullptr) {
   *sel = 0;
   if (n <= 1 || end_bit <= 0) return cudaSuccess;
   const unsigned nb = grid_for(n, kSortTile);
@@ -247,10 +289,10 @@ cudaError_t radix_sort_impl(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n,
   K* kin = ka; K* kout = kb;
   uint32_t* vin = va; uint32_t* vout = vb;
   for (int shift = 0; shift < end_bit; shift += kRadixBits) {
-    k_radix_hist<K><<<nb, kThreads, 0, s>>>(kin, n, shift, hist);
+    k_radix_hist<K><<<nb, kThreads, 0, s>>>(kin, n, n_dev, shift, hist);
     cudaError_t e = launch_exclusive_scan(hist, hist, hn, scan_scratch, nullptr, s);
     if (e != cudaSuccess) return e;
-    k_radix_scatter<K, kVals><<<nb, kThreads, 0, s>>>(kin, kout, vin, vout, n, shift, hist);
+    k_radix_scatter<K, kVals><<<nb, kThreads, 0, s>>>(kin, kout, vin, vout, n, n_dev, shift, hist);
     std::swap(kin, kout);
     std::swap(vin, vout);
     *sel ^= 1;
@@ -287,9 +329,9 @@ cudaError_t radix_sort_u32(uint32_t* keys_a, uint32_t* keys_b, uint32_t* vals_a,
 }
 
 cudaError_t radix_sort_u64(uint64_t* keys_a, uint64_t* keys_b, int64_t n, int end_bit, uint32_t* hist_scratch,
-                           uint64_t* scan_scratch, int* sel, cudaStream_t s) {
+                           uint64_t* scan_scratch, int* sel, cudaStream_t s, const uint64_t* n_dev) {
   return radix_sort_impl<uint64_t, false>(keys_a, keys_b, nullptr, nullptr, n, end_bit, hist_scratch,
-                                          scan_scratch, sel, s);
+                                          scan_scratch, sel, s, n_dev);
 }
 
 cudaError_t launch_rank_scatter(const uint32_t* order, int64_t n, uint32_t* rank, cudaStream_t s) {
@@ -315,14 +357,26 @@ cudaError_t launch_emit_pairs_u64(const ushort4* rect, const uint32_t* offsets, 
 cudaError_t launch_tile_ranges_u32(const uint32_t* keys, int64_t m, int rank_bits, const uint32_t* order,
                                    uint2* ranges, uint32_t* list, cudaStream_t s) {
   if (m == 0) return cudaSuccess;
-  k_tile_ranges<uint32_t><<<grid_for(m, kThreads), kThreads, 0, s>>>(keys, m, rank_bits, order, ranges, list);
+  k_tile_ranges<uint32_t><<<grid_for(m, kThreads), kThreads, 0, s>>>(keys, m, nullptr, rank_bits, order, ranges,
+                                                                       list);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tile_ranges_u64(const uint64_t* keys, int64_t m, int rank_bits, const uint32_t* order,
-                                   uint2* ranges, uint32_t* list, cudaStream_t s) {
+                                   uint2* ranges, uint32_t* list, cudaStream_t s, const uint64_t* m_dev) {
   if (m == 0) return cudaSuccess;
-  k_tile_ranges<uint64_t><<<grid_for(m, kThreads), kThreads, 0, s>>>(keys, m, rank_bits, order, ranges, list);
+  k_tile_ranges<uint64_t><<<grid_for(m, kThreads), kThreads, 0, s>>>(keys, m, m_dev, rank_bits, order, ranges,
+                                                                       list);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emit_pairs_batch(const EmitTable& t, int nkf, int64_t max_n, const ushort4* rect,
+                                    const uint32_t* offsets, const uint32_t* rank, int rank_bits, uint64_t capacity,
+                                    uint64_t* keys, uint32_t* overflow, cudaStream_t s) {
+  if (nkf == 0 || max_n == 0) return cudaSuccess;
+  const dim3 grid(grid_for(max_n, kThreads), (unsigned)nkf);
+  k_emit_pairs_batch<uint64_t><<<grid, kThreads, 0, s>>>(t, rect, offsets, rank, rank_bits, capacity, keys,
+                                                         overflow);
   return cudaGetLastError();
 }
 

@@ -80,6 +80,9 @@ _SIGS = {
     "dqo_quadric_fit": (c_i32, [c_p, c_i32, c_i32, c_p, c_p, c_p, c_i32, c_p, c_i32, c_f, c_p, c_p, c_p, c_p, c_p,
                                 c_p]),
     "dqo_quadric_canonical": (c_i32, [c_i32, c_p, c_p, c_p]),
+    "dqo_batch_step": (c_i32, [c_p, c_p, c_i32, c_p, c_p, c_i32, c_p]),
+    "dqo_batch_check": (c_i32, [c_p, c_p, c_p]),
+    "dqo_batch_tune": (c_i32, [c_p, c_p, c_i32, c_p, c_p, c_i32, c_p, c_p, c_p]),
     "dqo_mlp_features": (c_i32, [c_i32, c_i32, c_p, c_p, c_p, c_i32, c_p, c_p, c_f, c_p, c_p, c_i64, c_p]),
     "dqo_mlp_state_bytes": (C.c_size_t, []),
     "dqo_mlp_set_params": (c_i32, [c_p, c_p, c_p]),
@@ -88,8 +91,21 @@ _SIGS = {
     "dqo_mlp_gradients": (c_i32, [c_p, c_p, c_i64, c_p, c_p, c_i64, c_p, c_p, c_p, c_p, c_p]),
     "dqo_mlp_train_step": (c_i32, [c_p, c_p, c_p, c_i64, c_p, c_p, c_i64, c_p, c_p, c_p]),
     "dqo_mlp_check": (c_i32, [c_p, c_p]),
+    "dqo_wait_probe": (c_i32, [c_p, c_p]),
 }
 
+class dqo_keyframe(C.Structure):
+    _fields_ = [("gaussians", dqo_gaussians), ("camera", dqo_camera), ("targets", dqo_targets),
+                ("out", dqo_render_out), ("grads", dqo_gaussian_grads)]
+
+
+class dqo_fit_batch(C.Structure):
+    _fields_ = [("nq", c_i32), ("nv", c_i32), ("npairs", c_i32), ("iters", c_i32), ("lr", c_f),
+                ("P", c_p), ("q_ptr", c_p), ("pair_v", c_p), ("obs_bbox", c_p), ("start", c_p),
+                ("init", c_p), ("params", c_p), ("loss", c_p), ("ok", c_p)]
+
+
+MAX_BATCH = 16
 MLP_FEATURES = 128
 MLP_PARAMS = 35088
 # offsets into the fp32 parameter vector
@@ -360,6 +376,55 @@ def dqo_quadric_canonical(params, out=None, stream=None):
     return out
 
 
+# ------------------------------------------------------------------------ batched step
+
+def keyframe(g: dict, num_objects: int, cam: dict, t: dict, out: dict, grads: dict) -> dqo_keyframe:
+    """One keyframe of a batch (the tensors must stay alive while the batch is used)."""
+    k = dqo_keyframe()
+    k.gaussians = gaussians(g, num_objects)
+    k.camera = camera(cam)
+    k.targets = targets(t)
+    k.out = render_out(out)
+    k.grads = gaussian_grads(grads)
+    return k
+
+
+def fit_batch(P, q_ptr, pair_v, obs, iters=100, lr=1e-2, start=None, init=None, params=None, loss=None,
+              ok=None) -> dqo_fit_batch:
+    f = dqo_fit_batch(nq=q_ptr.shape[0] - 1, nv=P.shape[0], npairs=pair_v.shape[0], iters=iters, lr=lr)
+    for name, t in (("P", P), ("q_ptr", q_ptr), ("pair_v", pair_v), ("obs_bbox", obs), ("start", start),
+                    ("init", init), ("params", params), ("loss", loss), ("ok", ok)):
+        setattr(f, name, _ptr(t))
+    return f
+
+
+def dqo_batch_step(ctx: Context, st: dqo_settings, kfs: list, fits: dqo_fit_batch | None = None,
+                   ctas_per_sm: int = 0, stream=None):
+    arr = (dqo_keyframe * len(kfs))(*kfs)
+    _check("dqo_batch_step",
+           load().dqo_batch_step(ctx.handle, C.byref(st), len(kfs), arr, None if fits is None else C.byref(fits),
+                                 ctas_per_sm, _stream(stream)), ctx.handle)
+
+
+def dqo_batch_check(ctx: Context) -> tuple[int, bool]:
+    pairs, over = C.c_uint64(0), C.c_int(0)
+    _check("dqo_batch_check", load().dqo_batch_check(ctx.handle, C.byref(pairs), C.byref(over)), ctx.handle)
+    return int(pairs.value), bool(over.value)
+
+
+def dqo_batch_tune(ctx: Context, st: dqo_settings, kfs: list, fits: dqo_fit_batch | None = None, reps: int = 3,
+                   stream=None) -> tuple[int, list]:
+    """Picks the fastest tile shape (written into st) and CTAs per SM (returned), with the
+    nine candidates' mean step times in ms."""
+    arr = (dqo_keyframe * len(kfs))(*kfs)
+    cps = c_i32(0)
+    ms = (c_f * 9)()
+    _check("dqo_batch_tune",
+           load().dqo_batch_tune(ctx.handle, C.byref(st), len(kfs), arr, None if fits is None else C.byref(fits),
+                                 reps, C.byref(cps), ms, _stream(stream)), ctx.handle)
+    return int(cps.value), list(ms)
+
+
 # ------------------------------------------------------------------------ learned proposal
 
 def mlp_hparams(lr=2e-3, lr_final=1e-5, total_steps=0, beta1=0.9, beta2=0.999, eps=1e-8,
@@ -442,9 +507,17 @@ def _ptr_any(t) -> int:
 
 
 def dqo_mlp_check(ctx: Context) -> bool:
+    """True if a tensor-core completion wait ran out since the last check."""
     v = C.c_int(0)
-    _check("dqo_mlp_check", load().dqo_mlp_check(ctx.handle, C.byref(v)), ctx.handle)
+    st = load().dqo_mlp_check(ctx.handle, C.byref(v))
+    if st not in (DQO_OK, DQO_ETIMEOUT):
+        _check("dqo_mlp_check", st, ctx.handle)
     return bool(v.value)
+
+
+def dqo_wait_probe(ctx: Context, stream=None) -> int:
+    """Runs the bounded-wait probe; returns the status (DQO_ETIMEOUT expected)."""
+    return int(load().dqo_wait_probe(ctx.handle, _stream(stream)))
 
 
 # ------------------------------------------------------------------------ conveniences

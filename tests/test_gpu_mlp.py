@@ -262,3 +262,22 @@ def test_learned_proposal_against_plain_fit_at_three_views(trained):
     e_learn = _centre_err(refined["params"].cpu().numpy().astype(np.float64), ref["params"])[ok]
     print(f"3 views: plain centre error median {np.median(e_plain):.4f} m, learned+refined {np.median(e_learn):.4f} m")
     assert np.median(e_learn) < 2.0 * np.median(e_plain)
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    import time
+    ctx = dqo.Context()
+    t0 = time.perf_counter()
+    status = dqo.dqo_wait_probe(ctx)
+    dt = time.perf_counter() - t0
+    assert status == dqo.DQO_ETIMEOUT
+    assert 0.5 < dt < 30.0
+    # the tensor-core path still works on the same context
+    s, F, params, _ = _net_case(1109, 256)
+    st = _state(params)
+    X = torch.from_numpy(F.astype(np.float32)).cuda().to(torch.bfloat16)
+    y = dqo.dqo_mlp_forward(ctx, st, X).cpu().numpy().astype(np.float64)
+    ref = oracle.mlp_forward(F, params.astype(np.float64))["y"]
+    assert np.abs(y - ref).max() < 2e-3
+    assert not dqo.dqo_mlp_check(ctx)
+    ctx.close()
