@@ -43,9 +43,9 @@ FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # FMA =
 # arithmetic (FMA = 2): forward = exponent 9 + alpha/transmittance 5 + colour/depth 8 +
 # instance 2 + weight 1; backward = exponent 9 + alpha 3 + transmittance 2 + upstream dot 9
 # + dalpha 5 + accumulator 2 + ten partials 15 + their sums 10.
-FLOPS_PER_EVAL = {"blend_fwd": 25, "blend_bwd": 55}
+FLOPS_PER_EVAL = {"blend_fwd": 25, "blend_bwd": 55, "blend_step": 80}
 FIT_ITERS = 100
-KERNEL_SRC = {"blend_fwd": "k_blend.cu", "blend_bwd": "k_blend.cu"}
+KERNEL_SRC = {"blend_fwd": "k_blend.cu", "blend_bwd": "k_blend.cu", "blend_step": "k_blend.cu"}
 # Learned proposal: algorithmic flops per sample of one training step (FMA = 2): forward
 # 2 (128*128 + 128*128 + 9*128); backward dH2 and dW3 2 (9*128) each, dH1, dW2, dW1
 # 2 (128*128) each.
@@ -265,34 +265,76 @@ def run_ours(args, rank, world, local_rank):
     dqo.dqo_get_buffer(ctx, dqo.DQO_BUF_N_CONTRIB, nc)
     torch.cuda.synchronize()
     evals = int(nc.to(torch.int64).sum().item())
+    uuid = getattr(torch.cuda.get_device_properties(local_rank), "uuid", None)
+    smi_id = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else \
+        (str(uuid) if uuid is not None else None)
+
+    # ---- the step as deployed: the batched path with this one keyframe and the quadric
+    # loss, captured once in a CUDA graph (no host synchronisation, no launch gaps)
+    bctx = dqo.Context(local_rank)
+    kfb = dqo.keyframe(g, NUM_OBJECTS, cam, t, out, grads)
+
+    bst = dqo.settings(tile_w=tw, tile_h=th, batch=args.batch)
+    cps, sched, tune_ms = dqo.dqo_batch_tune(bctx, bst, [kfb], None, reps=5)
+
+    def graph_body():
+        for v in grads.values():
+            v.zero_()
+        dqo.dqo_batch_step(bctx, bst, [kfb], None, cps, sched)
+        dqo.dqo_quadric_bbox_loss(bctx, q["params"], q["P"], q["q_ptr"], q["pair_v"], q["obs_bbox"], qloss, qgrad)
+
+    dqo.dqo_batch_step(bctx, bst, [kfb], None, cps, sched, stream)      # sizing call
+    torch.cuda.synchronize()
+    if (bst.tile_w, bst.tile_h) != (tw, th):
+        # evaluations walked depend on the tile lists: count them with the tuned tiles
+        ectx = dqo.Context(local_rank)
+        dqo.dqo_render_forward(ectx, bst, gs, cs, ts, outs, stream)
+        dqo.dqo_get_buffer(ectx, dqo.DQO_BUF_N_CONTRIB, nc)
+        torch.cuda.synchronize()
+        evals = int(nc.to(torch.int64).sum().item())
+        ectx.close()
+    dqo.dqo_set_timing(bctx, True)
+    graph = torch.cuda.CUDAGraph()
+    cap_stream = torch.cuda.Stream(dev)
+    cap_stream.wait_stream(torch.cuda.current_stream())
+    l0 = dqo.dqo_launch_count(bctx)
+    with torch.cuda.stream(cap_stream):
+        with torch.cuda.graph(graph, stream=cap_stream, capture_error_mode="thread_local"):
+            graph_body()
+    torch.cuda.current_stream().wait_stream(cap_stream)
+    launches_per_step = dqo.dqo_launch_count(bctx) - l0
+    for _ in range(max(args.warmup, 3)):
+        graph.replay()
+    torch.cuda.synchronize()
 
     # ---- device-timed region
-    dqo.dqo_set_timing(ctx, True)
     phase_sum = {k: 0.0 for k in dqo.PHASES}
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    uuid = getattr(torch.cuda.get_device_properties(local_rank), "uuid", None)
-    clocks = ClockSampler(f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else
-                          (str(uuid) if uuid is not None else None))
+    clocks = ClockSampler(smi_id)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    launches0 = dqo.dqo_launch_count(ctx)
+    graph_timing = True
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
-        step()
+        graph.replay()
         ev[i][1].record(stream)
-        ph = dqo.dqo_get_timings(ctx)
-        for k, v in ph.items():
-            if v >= 0:
-                phase_sum[k] += v
+        if graph_timing:
+            try:
+                ph = dqo.dqo_get_timings(bctx)
+            except dqo.DqoError:
+                graph_timing = False
+                continue
+            for k, v in ph.items():
+                if v >= 0:
+                    phase_sum[k] += v
     torch.cuda.synchronize()
-    launches = dqo.dqo_launch_count(ctx) - launches0
+    launches = launches_per_step * args.steps
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    dqo.dqo_set_timing(ctx, False)
     total_ms = sum(a.elapsed_time(b) for a, b in ev)
     if world > 1:
         tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
@@ -300,7 +342,45 @@ def run_ours(args, rank, world, local_rank):
         total_ms = float(tt.item())
     ms_per_step = total_ms / args.steps
     value = world * args.steps / (total_ms / 1e3)
-    phases = {k: v / args.steps for k, v in phase_sum.items()}
+    phases = {k: v / args.steps for k, v in phase_sum.items() if v > 0}
+    phase_source = "event-record nodes of the replayed graph"
+    if not graph_timing:
+        # the same kernels run eagerly (phase events recorded on the stream)
+        dqo.dqo_set_timing(bctx, True)
+        reps = max(20, args.steps // 5)
+        phase_sum = {k: 0.0 for k in dqo.PHASES}
+        for _ in range(reps):
+            flush.zero_()
+            graph_body()
+            for k, v in dqo.dqo_get_timings(bctx).items():
+                if v >= 0:
+                    phase_sum[k] += v
+        phases = {k: v / reps for k, v in phase_sum.items() if v > 0}
+        phase_source = "eager calls of the same step (graph events could not be timed)"
+    pairs_b, over_b = dqo.dqo_batch_check(bctx)
+
+    # ---- the same step through the single-keyframe calls (host waits once per forward)
+    dqo.dqo_set_timing(ctx, True)
+    s_steps = max(20, args.steps // 3)
+    s_phase = {k: 0.0 for k in dqo.PHASES}
+    s_ms = 0.0
+    for i in range(s_steps):
+        flush.zero_()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        step()
+        a1.record(stream)
+        ph = dqo.dqo_get_timings(ctx)
+        for k, v in ph.items():
+            if v >= 0:
+                s_phase[k] += v
+        torch.cuda.synchronize()
+        s_ms += a0.elapsed_time(a1)
+    dqo.dqo_set_timing(ctx, False)
+    single_call = {"value": world * s_steps / (s_ms / 1e3), "unit": UNIT, "ms_per_step": s_ms / s_steps,
+                   "phases_ms": {k: round(v / s_steps, 4) for k, v in s_phase.items() if v > 0},
+                   "form": "dqo_render_forward + dqo_render_backward + dqo_quadric_bbox_loss per step (the "
+                           "forward waits on the host for the pair count)"}
 
     # ---- end to end through the C ABI with host buffers
     pin = {k: v.cpu().pin_memory() for k, v in g.items()}
@@ -316,7 +396,7 @@ def run_ours(args, rank, world, local_rank):
         for d, src in ((g, pin), (t, pin_t), (q, pin_q)):
             for k in d:
                 d[k].copy_(src[k], non_blocking=True)
-        step()
+        graph.replay()
         for k in grads:
             host_out[k].copy_(grads[k], non_blocking=True)
         host_loss.copy_(out["loss"], non_blocking=True)
@@ -343,12 +423,15 @@ def run_ours(args, rank, world, local_rank):
         e_ms = float(tt.item())
     e2e_val = world * e_steps / (e_ms / 1e3)
 
-    # ---- roofline of the dominant kernel (FP32 pipe)
-    dom = max(("blend_fwd", "blend_bwd"), key=lambda k: phases[k])
+    # ---- roofline of the dominant kernel (FP32 pipe): the persistent forward + backward
+    # blend (its phase also holds the per-keyframe loss sum, a few microseconds)
+    dom = "blend_step"
     flops = FLOPS_PER_EVAL[dom] * evals
     achieved = flops / (phases[dom] * 1e-3) / 1e12
-    roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic_for(dom),
+    kname = {dqo.SCHEDULE_FUSED: "k_blend_step", dqo.SCHEDULE_SPLIT: "k_blend_fwd_queue + k_blend_bwd_queue",
+             dqo.SCHEDULE_PER_KEYFRAME: "k_blend_forward + k_blend_backward"}[sched]
+    roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic_for(dom),
             "evals_per_launch": evals, "flops_per_eval": FLOPS_PER_EVAL[dom],
             "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, no measured FP32 peak)"}
 
@@ -391,7 +474,12 @@ def run_ours(args, rank, world, local_rank):
             "config": workload_config(kf, m_pairs, args), "clocks": clk,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "roofline": roof,
-            "phases_ms": {k: round(v, 4) for k, v in phases.items()},
+            "phases_ms": {k: round(v, 4) for k, v in phases.items()}, "phases_from": phase_source,
+            "step_form": "dqo_batch_step (1 keyframe) + dqo_quadric_bbox_loss in one CUDA graph, "
+                         f"{launches_per_step} kernels per step; tile pairs {pairs_b}, overflow {over_b}",
+            "tuned": {"tile": f"{bst.tile_w}x{bst.tile_h}", "ctas_per_sm": cps, "schedule": sched,
+                      "candidates_ms": tune_table(dqo, tune_ms)},
+            "single_call": single_call,
             "quadric_fits": fits}
     if batched is not None:
         line["batched"] = batched
@@ -406,6 +494,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
+    bctx.close()
 
 
 def learned_section(ctx, dev, stream, world, fd, nfit, plain_fit_ms):
@@ -475,6 +564,15 @@ def learned_section(ctx, dev, stream, world, fd, nfit, plain_fit_ms):
                                       "traffic": None}}}
 
 
+def tune_table(dqo, ms) -> dict:
+    names = {0: "fused", 1: "split", 2: "per-keyframe"}
+    out = {}
+    for i, m in enumerate(ms):
+        w, h, c, sc = dqo.tune_candidate(i)
+        out[f"{w}x{h}/{names[sc]}" + (f"/{c}" if sc != 2 else "")] = round(m, 4)
+    return out
+
+
 BATCH_KEYFRAMES = 8
 BATCH_REPS = 20
 
@@ -540,15 +638,15 @@ def batched_section(dev, stream, world, fq, fd):
     dqo.dqo_batch_step(bctx, bst, kfs, fb)             # same 16x16 tiles as the single form
     torch.cuda.synchronize()
     same_loss = all(torch.equal(a, o["loss"]) for a, o in zip(loss_single, outs))
-    cps, tune_ms = dqo.dqo_batch_tune(bctx, bst, kfs, fb, reps=3)
-    dqo.dqo_batch_step(bctx, bst, kfs, fb, cps)        # sizing call for the chosen shape
+    cps, sched, tune_ms = dqo.dqo_batch_tune(bctx, bst, kfs, fb, reps=3)
+    dqo.dqo_batch_step(bctx, bst, kfs, fb, cps, sched)        # sizing call for the chosen configuration
     torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()
     cs_ = torch.cuda.Stream(dev)
     cs_.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(cs_):
         with torch.cuda.graph(graph, stream=cs_, capture_error_mode="thread_local"):
-            dqo.dqo_batch_step(bctx, bst, kfs, fb, cps)
+            dqo.dqo_batch_step(bctx, bst, kfs, fb, cps, sched)
     torch.cuda.current_stream().wait_stream(cs_)
     for _ in range(3):
         graph.replay()
@@ -567,9 +665,8 @@ def batched_section(dev, stream, world, fq, fd):
            "keyframe_iters_per_s": world * BATCH_KEYFRAMES / (batched_ms * 1e-3),
            "single_keyframe_iters_per_s": world * BATCH_KEYFRAMES / (single_ms * 1e-3),
            "losses_match_single": same_loss,
-           "tuned": {"tile": f"{bst.tile_w}x{bst.tile_h}", "ctas_per_sm": cps,
-                     "candidates_ms": {f"{w}x{h}/{c}": round(m, 4) for (w, h), c, m in
-                                       zip([(16, 16)] * 3 + [(8, 32)] * 3 + [(32, 8)] * 3, [2, 3, 4] * 3, tune_ms)}},
+           "tuned": {"tile": f"{bst.tile_w}x{bst.tile_h}", "ctas_per_sm": cps, "schedule": sched,
+                     "candidates_ms": tune_table(dqo, tune_ms)},
            "form": "one launch per phase over all keyframes, persistent fused forward+backward blend on a work "
                    "queue, fits on a concurrent graph branch, one CUDA graph"}
     ctx.close()

@@ -218,7 +218,8 @@ typedef enum {
   DQO_PHASE_BLEND_BWD = 4,   /* K7 blend backward */
   DQO_PHASE_PROJECT_BWD = 5, /* K8 projection backward */
   DQO_PHASE_QUADRIC = 6,     /* dual-quadric projection or bbox loss */
-  DQO_PHASE_COUNT = 7
+  DQO_PHASE_BLEND_STEP = 7,  /* dqo_batch_step: persistent forward + backward blend, loss sums */
+  DQO_PHASE_COUNT = 8
 } dqo_phase;
 
 /* Enables (1) or disables (0) CUDA-event timing of the phases above on the calls'
@@ -226,7 +227,9 @@ typedef enum {
 DQO_API dqo_status dqo_set_timing(dqo_ctx* ctx, int enable);
 
 /* Device milliseconds of each phase in its most recent timed call (ms[DQO_PHASE_COUNT];
- * -1 for a phase not run since timing was enabled).  Waits for those events.
+ * -1 for a phase not run since timing was enabled).  Waits for those events.  A call
+ * captured in a CUDA graph records its events as graph nodes: each query then reads the
+ * times of the latest replay.
  * n = capacity of ms.  DQO_EINVAL if ctx or ms is NULL or n < 1. */
 DQO_API dqo_status dqo_get_timings(dqo_ctx* ctx, float* ms, int32_t n);
 
@@ -370,27 +373,37 @@ typedef struct dqo_fit_batch {
  * synchronise or allocate (so they can be captured in a CUDA graph) and read the pair
  * count on the device.  If a later step needs more pairs than that capacity, pairs past
  * it are dropped and dqo_batch_check reports it (and makes the next step a sizing call).
- * settings->tile_w/tile_h apply to every keyframe; ctas_per_sm bounds the persistent
- * kernel's CTAs per SM (<= 0: as many as fit).
- * Errors: DQO_EINVAL (bad arguments, nkf out of range, missing targets), DQO_ENOMEM,
- * DQO_ESTATE (a sizing call while the stream is being captured), DQO_ECUDA. */
+ * settings->tile_w/tile_h apply to every keyframe.  schedule selects how the blend runs:
+ *   DQO_SCHEDULE_FUSED (0): one persistent kernel, each tile's forward then its backward;
+ *   DQO_SCHEDULE_SPLIT (1): a persistent forward kernel then a persistent backward kernel,
+ *     each on its own work queue;
+ *   DQO_SCHEDULE_PER_KEYFRAME (2): the one-keyframe forward and backward kernels launched
+ *     per keyframe.
+ * ctas_per_sm bounds the persistent kernels' CTAs per SM (<= 0: as many as fit).
+ * Errors: DQO_EINVAL (bad arguments, nkf out of range, missing targets, unknown schedule),
+ * DQO_ENOMEM, DQO_ESTATE (a sizing call while the stream is being captured), DQO_ECUDA. */
+#define DQO_SCHEDULE_FUSED 0
+#define DQO_SCHEDULE_SPLIT 1
+#define DQO_SCHEDULE_PER_KEYFRAME 2
 DQO_API dqo_status dqo_batch_step(dqo_ctx* ctx, const dqo_settings* settings, int32_t nkf,
                                   const dqo_keyframe* kfs, const dqo_fit_batch* fits, int32_t ctas_per_sm,
-                                  dqo_stream stream);
+                                  int32_t schedule, dqo_stream stream);
 
 /* After the last dqo_batch_step has completed: pairs it needed and whether they exceeded
  * the capacity (synchronous). */
 DQO_API dqo_status dqo_batch_check(dqo_ctx* ctx, uint64_t* pairs, int* overflow);
 
-/* Autotuner of the batched step: times each candidate (tile shapes 16x16, 8x32, 32x8 x
- * persistent CTAs per SM 2, 3, 4) over `reps` steps on this batch (CUDA events on the
- * stream; gradients accumulate into kfs' buffers while it runs) and writes the fastest
- * tile shape into settings and its CTAs per SM into *ctas_per_sm.  ms [9] (host, may be
- * NULL) receives each candidate's mean step time in the order listed.
- * Errors: as dqo_batch_step. */
+/* Autotuner of the batched step: times each of DQO_TUNE_CANDIDATES candidates over `reps`
+ * steps on this batch (CUDA events on the stream; gradients accumulate into kfs' buffers
+ * while it runs) and writes the fastest tile shape into settings, its CTAs per SM into
+ * *ctas_per_sm and its schedule into *schedule.  Candidate i: tile shape i / 7 of
+ * (16x16, 8x32, 32x8); j = i % 7: j < 3 fused with 2 + j CTAs per SM, 3 <= j < 6 split
+ * with j - 1 CTAs per SM, j = 6 per keyframe.  ms [DQO_TUNE_CANDIDATES] (host, may be
+ * NULL) receives each candidate's mean step time.  Errors: as dqo_batch_step. */
+#define DQO_TUNE_CANDIDATES 21
 DQO_API dqo_status dqo_batch_tune(dqo_ctx* ctx, dqo_settings* settings, int32_t nkf, const dqo_keyframe* kfs,
-                                  const dqo_fit_batch* fits, int32_t reps, int32_t* ctas_per_sm, float* ms,
-                                  dqo_stream stream);
+                                  const dqo_fit_batch* fits, int32_t reps, int32_t* ctas_per_sm,
+                                  int32_t* schedule, float* ms, dqo_stream stream);
 
 /* ---------------------------------------------------------------------------------------
  * Learned quadric proposal.  The paper initialises each quadric geometrically (Eq. 1);

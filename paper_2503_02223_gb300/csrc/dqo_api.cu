@@ -43,6 +43,7 @@ struct dqo_ctx {
   bool timing = false;
   cudaEvent_t ev[2 * DQO_PHASE_COUNT] = {};
   bool pending[DQO_PHASE_COUNT] = {};
+  bool captured[DQO_PHASE_COUNT] = {};  // recorded inside a graph capture: re-read each query
   float last_ms[DQO_PHASE_COUNT] = {};
   int64_t launches = 0;
   // batched step: joint buffers of all keyframes of a batch, pair capacity, side stream
@@ -144,13 +145,20 @@ struct PhaseTimer {
   dqo_ctx* c;
   int ph;
   cudaStream_t s;
+  unsigned flags = cudaEventRecordDefault;
   PhaseTimer(dqo_ctx* c_, int ph_, cudaStream_t s_) : c(c_), ph(ph_), s(s_) {
-    if (c->timing) cudaEventRecord(c->ev[2 * ph], s);
+    if (!c->timing) return;
+    // inside a graph capture the events must become event-record nodes of the graph
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+      flags = cudaEventRecordExternal;
+    cudaEventRecordWithFlags(c->ev[2 * ph], s, flags);
   }
   ~PhaseTimer() {
     if (c->timing) {
-      cudaEventRecord(c->ev[2 * ph + 1], s);
+      cudaEventRecordWithFlags(c->ev[2 * ph + 1], s, flags);
       c->pending[ph] = true;
+      c->captured[ph] = flags == cudaEventRecordExternal;
     }
   }
 };
@@ -577,6 +585,7 @@ dqo_status dqo_set_timing(dqo_ctx* c, int enable) {
   c->timing = enable != 0;
   for (int i = 0; i < DQO_PHASE_COUNT; ++i) {
     c->pending[i] = false;
+    c->captured[i] = false;
     c->last_ms[i] = -1.f;
   }
   return DQO_OK;
@@ -585,7 +594,7 @@ dqo_status dqo_set_timing(dqo_ctx* c, int enable) {
 dqo_status dqo_get_timings(dqo_ctx* c, float* ms, int32_t n) {
   if (!c || !ms || n < 1) return DQO_EINVAL;
   for (int i = 0; i < DQO_PHASE_COUNT; ++i) {
-    if (c->pending[i]) {
+    if (c->pending[i] || c->captured[i]) {
       DQO_CUDA(c, cudaEventSynchronize(c->ev[2 * i + 1]));
       float t = 0.f;
       DQO_CUDA(c, cudaEventElapsedTime(&t, c->ev[2 * i], c->ev[2 * i + 1]));
@@ -673,8 +682,8 @@ dqo_status check_fits(const dqo_fit_batch* f) {
 }  // namespace
 
 dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const dqo_keyframe* kfs,
-                          const dqo_fit_batch* fits, int32_t ctas_per_sm, dqo_stream stream_) {
-  if (!c || !kfs || nkf < 1 || nkf > kMaxBatch) return DQO_EINVAL;
+                          const dqo_fit_batch* fits, int32_t ctas_per_sm, int32_t schedule, dqo_stream stream_) {
+  if (!c || !kfs || nkf < 1 || nkf > kMaxBatch || schedule < 0 || schedule > 2) return DQO_EINVAL;
   dqo_status st;
   if ((st = check_settings(s)) != DQO_OK) return st;
   if ((st = check_fits(fits)) != DQO_OK) return st;
@@ -784,6 +793,7 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
   pb.gid = as<uint32_t>(B.gid);
   pb.n_visible = d_nvis;
   {
+    PhaseTimer timer(c, DQO_PHASE_PROJECT, s_);
     PreTable pt;
     for (int k = 0; k < nkf; ++k) {
       pt.kf[k].rp = rp[k];
@@ -796,14 +806,18 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
   // ---- pair offsets, depth order (one sort over all keyframes: ranks keep each
   // keyframe's (depth, index) order because its indices are contiguous)
   int sel = 0;
-  DQO_CUDA(c, launch_exclusive_scan(as<uint32_t>(B.ntiles), as<uint32_t>(B.offsets), N, as<uint64_t>(B.scan_scratch),
-                                    d_total, s_));
-  DQO_CUDA(c, radix_sort_u32(as<uint32_t>(B.zkey_a), as<uint32_t>(B.zkey_b), as<uint32_t>(B.zval_a),
-                             as<uint32_t>(B.zval_b), N, 32, as<uint32_t>(B.depth_hist),
-                             as<uint64_t>(B.depth_scan_scratch), &sel, s_));
-  const uint32_t* order = sel ? as<uint32_t>(B.zval_b) : as<uint32_t>(B.zval_a);
-  DQO_CUDA(c, launch_rank_scatter(order, N, as<uint32_t>(B.rank), s_));
-  launches += scan_launches(N) + sort_launches(N, 32) + 1;
+  const uint32_t* order = nullptr;
+  {
+    PhaseTimer timer(c, DQO_PHASE_DEPTH_SORT, s_);
+    DQO_CUDA(c, launch_exclusive_scan(as<uint32_t>(B.ntiles), as<uint32_t>(B.offsets), N,
+                                      as<uint64_t>(B.scan_scratch), d_total, s_));
+    DQO_CUDA(c, radix_sort_u32(as<uint32_t>(B.zkey_a), as<uint32_t>(B.zkey_b), as<uint32_t>(B.zval_a),
+                               as<uint32_t>(B.zval_b), N, 32, as<uint32_t>(B.depth_hist),
+                               as<uint64_t>(B.depth_scan_scratch), &sel, s_));
+    order = sel ? as<uint32_t>(B.zval_b) : as<uint32_t>(B.zval_a);
+    DQO_CUDA(c, launch_rank_scatter(order, N, as<uint32_t>(B.rank), s_));
+    launches += scan_launches(N) + sort_launches(N, 32) + 1;
+  }
 
   if (sizing) {
     DQO_CUDA(c, cudaMemcpyAsync(B.host, d_total, 8, cudaMemcpyDeviceToHost, s_));
@@ -824,6 +838,7 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
 
   // ---- pairs of the joint tile numbering, pair sort, tile ranges (counts on the device)
   {
+    PhaseTimer timer(c, DQO_PHASE_BINNING, s_);
     EmitTable et;
     for (int k = 0; k < nkf; ++k) {
       et.kf[k].base = base[k];
@@ -831,14 +846,23 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
       et.kf[k].tile_off = toff[k];
       et.kf[k].ntx = rp[k].ntx;
     }
+    const bool k32 = end_bit <= 32;
     DQO_CUDA(c, launch_emit_pairs_batch(et, nkf, max_n, as<ushort4>(B.rect), as<uint32_t>(B.offsets),
-                                        as<uint32_t>(B.rank), rank_bits, cap, as<uint64_t>(B.pair_a), d_overflow,
-                                        s_));
+                                        as<uint32_t>(B.rank), rank_bits, cap, B.pair_a.p, k32, d_overflow, s_));
     int psel = 0;
-    DQO_CUDA(c, radix_sort_u64(as<uint64_t>(B.pair_a), as<uint64_t>(B.pair_b), (int64_t)cap, end_bit,
-                               as<uint32_t>(B.hist), as<uint64_t>(B.scan_scratch), &psel, s_, d_total));
-    DQO_CUDA(c, launch_tile_ranges_u64(psel ? as<uint64_t>(B.pair_b) : as<uint64_t>(B.pair_a), (int64_t)cap,
-                                       rank_bits, order, as<uint2>(B.ranges), as<uint32_t>(B.list), s_, d_total));
+    if (k32) {
+      DQO_CUDA(c, radix_sort_u32_dev(as<uint32_t>(B.pair_a), as<uint32_t>(B.pair_b), (int64_t)cap, end_bit,
+                                     as<uint32_t>(B.hist), as<uint64_t>(B.scan_scratch), &psel, s_, d_total));
+      DQO_CUDA(c, launch_tile_ranges_u32(psel ? as<uint32_t>(B.pair_b) : as<uint32_t>(B.pair_a), (int64_t)cap,
+                                         rank_bits, order, as<uint2>(B.ranges), as<uint32_t>(B.list), s_,
+                                         d_total));
+    } else {
+      DQO_CUDA(c, radix_sort_u64(as<uint64_t>(B.pair_a), as<uint64_t>(B.pair_b), (int64_t)cap, end_bit,
+                                 as<uint32_t>(B.hist), as<uint64_t>(B.scan_scratch), &psel, s_, d_total));
+      DQO_CUDA(c, launch_tile_ranges_u64(psel ? as<uint64_t>(B.pair_b) : as<uint64_t>(B.pair_a), (int64_t)cap,
+                                         rank_bits, order, as<uint2>(B.ranges), as<uint32_t>(B.list), s_,
+                                         d_total));
+    }
     launches += 2 + sort_launches((int64_t)cap, end_bit);
   }
 
@@ -911,10 +935,18 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
     }
     tt.tile_off[nkf] = toff[nkf];
     tt.nkf = nkf;
-    DQO_CUDA(c, launch_blend_step(tt, d_queue, s->tile_w, with_id, ctas_per_sm, B.sms, s_));
-    DQO_CUDA(c, launch_loss_reduce_batch(lt, nkf, s_));
-    DQO_CUDA(c, launch_preprocess_backward_batch(bt, nkf, max_n, s_));
-    launches += 3;
+    {
+      PhaseTimer timer(c, DQO_PHASE_BLEND_STEP, s_);
+      const BlendCommon cm{pb.p0, pb.p1, pb.p2, pb.gid, as<uint32_t>(B.list), as<float>(B.grad2d), s->alpha_clamp,
+                           s->alpha_min, s->t_stop, s->og_filter ? 1 : 0};
+      DQO_CUDA(c, launch_blend_step(tt, cm, d_queue, s->tile_w, with_id, ctas_per_sm, B.sms, schedule, s_));
+      DQO_CUDA(c, launch_loss_reduce_batch(lt, nkf, s_));
+    }
+    {
+      PhaseTimer timer(c, DQO_PHASE_PROJECT_BWD, s_);
+      DQO_CUDA(c, launch_preprocess_backward_batch(bt, nkf, max_n, s_));
+    }
+    launches += 2 + (schedule == 0 ? 1 : schedule == 1 ? 2 : 2 * nkf);
   }
   if (run_fits) DQO_CUDA(c, cudaStreamWaitEvent(s_, B.join, 0));
   c->launches += launches;
@@ -938,11 +970,10 @@ dqo_status dqo_batch_check(dqo_ctx* c, uint64_t* pairs, int* overflow) {
 }
 
 dqo_status dqo_batch_tune(dqo_ctx* c, dqo_settings* s, int32_t nkf, const dqo_keyframe* kfs,
-                          const dqo_fit_batch* fits, int32_t reps, int32_t* ctas_per_sm, float* ms,
+                          const dqo_fit_batch* fits, int32_t reps, int32_t* ctas_per_sm, int32_t* schedule, float* ms,
                           dqo_stream stream_) {
-  if (!c || !s || !ctas_per_sm || reps < 1) return DQO_EINVAL;
+  if (!c || !s || !ctas_per_sm || !schedule || reps < 1) return DQO_EINVAL;
   static const int shapes[3][2] = {{16, 16}, {8, 32}, {32, 8}};
-  static const int ctas[3] = {2, 3, 4};
   cudaStream_t s_ = reinterpret_cast<cudaStream_t>(stream_);
   DQO_CUDA(c, cudaSetDevice(c->device));
   cudaEvent_t e0, e1;
@@ -954,15 +985,21 @@ dqo_status dqo_batch_tune(dqo_ctx* c, dqo_settings* s, int32_t nkf, const dqo_ke
   float best = 0.f;
   int best_i = -1;
   dqo_status st = DQO_OK;
-  for (int i = 0; i < 9 && st == DQO_OK; ++i) {
+  auto cand = [](int i, int* cps, int* sched) {
+    const int j = i % 7;
+    *sched = j < 3 ? DQO_SCHEDULE_FUSED : (j < 6 ? DQO_SCHEDULE_SPLIT : DQO_SCHEDULE_PER_KEYFRAME);
+    *cps = j < 3 ? 2 + j : (j < 6 ? j - 1 : 0);
+  };
+  for (int i = 0; i < DQO_TUNE_CANDIDATES && st == DQO_OK; ++i) {
     dqo_settings t = *s;
-    t.tile_w = shapes[i / 3][0];
-    t.tile_h = shapes[i / 3][1];
-    const int cps = ctas[i % 3];
-    st = dqo_batch_step(c, &t, nkf, kfs, fits, cps, stream_);  // warm-up (sizes the layout)
+    t.tile_w = shapes[i / 7][0];
+    t.tile_h = shapes[i / 7][1];
+    int cps, sched;
+    cand(i, &cps, &sched);
+    st = dqo_batch_step(c, &t, nkf, kfs, fits, cps, sched, stream_);  // warm-up (sizes the layout)
     if (st != DQO_OK) break;
     cudaEventRecord(e0, s_);
-    for (int r = 0; r < reps && st == DQO_OK; ++r) st = dqo_batch_step(c, &t, nkf, kfs, fits, cps, stream_);
+    for (int r = 0; r < reps && st == DQO_OK; ++r) st = dqo_batch_step(c, &t, nkf, kfs, fits, cps, sched, stream_);
     cudaEventRecord(e1, s_);
     if (st != DQO_OK) break;
     float t_ms = 0.f;
@@ -980,9 +1017,9 @@ dqo_status dqo_batch_tune(dqo_ctx* c, dqo_settings* s, int32_t nkf, const dqo_ke
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != DQO_OK) return st;
-  s->tile_w = shapes[best_i / 3][0];
-  s->tile_h = shapes[best_i / 3][1];
-  *ctas_per_sm = ctas[best_i % 3];
+  s->tile_w = shapes[best_i / 7][0];
+  s->tile_h = shapes[best_i / 7][1];
+  cand(best_i, ctas_per_sm, schedule);
   return DQO_OK;
 }
 

@@ -187,7 +187,9 @@ cudaError_t launch_emit_pairs_u32(const ushort4* rect, const uint32_t* offsets, 
 cudaError_t launch_emit_pairs_u64(const ushort4* rect, const uint32_t* offsets, const uint32_t* rank,
                                   int64_t n, int ntx, int rank_bits, uint64_t* keys, cudaStream_t s);
 cudaError_t launch_tile_ranges_u32(const uint32_t* keys, int64_t m, int rank_bits, const uint32_t* order,
-                                   uint2* ranges, uint32_t* list, cudaStream_t s);
+                                   uint2* ranges, uint32_t* list, cudaStream_t s, const uint64_t* m_dev = nullptr);
+cudaError_t radix_sort_u32_dev(uint32_t* keys_a, uint32_t* keys_b, int64_t n, int end_bit, uint32_t* hist_scratch,
+                               uint64_t* scan_scratch, int* sel, cudaStream_t s, const uint64_t* n_dev);
 cudaError_t launch_tile_ranges_u64(const uint64_t* keys, int64_t m, int rank_bits, const uint32_t* order,
                                    uint2* ranges, uint32_t* list, cudaStream_t s, const uint64_t* m_dev = nullptr);
 
@@ -202,9 +204,10 @@ struct EmitKf {
 struct EmitTable {
   EmitKf kf[16];
 };
+// keys: uint32_t[capacity] if k32 (tile and rank bits fit 32), else uint64_t[capacity].
 cudaError_t launch_emit_pairs_batch(const EmitTable& t, int nkf, int64_t max_n, const ushort4* rect,
                                     const uint32_t* offsets, const uint32_t* rank, int rank_bits, uint64_t capacity,
-                                    uint64_t* keys, uint32_t* overflow, cudaStream_t s);
+                                    void* keys, bool k32, uint32_t* overflow, cudaStream_t s);
 
 cudaError_t launch_blend_forward(const BlendFwdArgs& a, bool with_id, cudaStream_t s);
 cudaError_t launch_loss_reduce(const float* part, int tiles, float lambda_ins, float scale, float* loss,
@@ -219,8 +222,25 @@ struct StepTable {
   uint32_t tile_off[17];  // keyframe k owns joint tiles [tile_off[k], tile_off[k+1])
   int nkf;
 };
-cudaError_t launch_blend_step(const StepTable& t, uint32_t* queue, int tile_w, bool with_id, int ctas_per_sm,
-                              int sms, cudaStream_t s);
+// What every tile of a batch reads in its inner loops: the joint projected-Gaussian arrays,
+// the tile lists, the gradient record and the blending thresholds.  Passed by value, so the
+// loops read it as constant-bank operands; the per-keyframe table is read only at a tile's
+// start and end.
+struct BlendCommon {
+  const float4* p0;
+  const float4* p1;
+  const float4* p2;
+  const uint32_t* gid;
+  const uint32_t* list;
+  float* grad2d;
+  float alpha_clamp, alpha_min, t_stop;
+  int og_filter;
+};
+// schedule: 0 = one fused persistent kernel (forward then backward per tile), 1 = forward
+// and backward persistent kernels (queue and queue + 1), 2 = the one-keyframe kernels per
+// keyframe.
+cudaError_t launch_blend_step(const StepTable& t, const BlendCommon& cm, uint32_t* queue, int tile_w, bool with_id,
+                              int ctas_per_sm, int sms, int schedule, cudaStream_t s);
 struct LossKf {
   const float* part;
   int tiles;

@@ -90,7 +90,7 @@ __device__ __forceinline__ void slot_ids_for_round(const uint32_t* s_mask, const
 // Forward of one tile (tile index local to a's image).  Called by all threads of a
 // block; uses the block's shared memory and barriers.
 template <int TW, bool kId>
-__device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const int tile) {
+__device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const BlendCommon& cm, const int tile) {
   constexpr int NW = kThreads / 32;
   // per-warp staging of the Gaussians that can reach the warp's pixels
   __shared__ float4 s_q0[NW][32], s_q1[NW][32], s_q2[NW][32];
@@ -123,7 +123,7 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const int 
     for (int t = tid; t < nw; t += kThreads) s_mask[t] = 0u;
     __syncthreads();
     for (int i = start + tid; i < end; i += kThreads) {
-      const uint32_t id = a.gid[a.list[i]];
+      const uint32_t id = cm.gid[cm.list[i]];
       if (id != 0xFFFFFFFFu) atomicOr(&s_mask[id >> 5], 1u << (id & 31));
     }
     __syncthreads();
@@ -171,10 +171,10 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const int 
     bool hit = false;
     float4 q0, q1, q2;
     if (i < lim) {
-      const uint32_t g = a.list[i];
-      q0 = a.p0[g];
-      q1 = a.p1[g];
-      q2 = a.p2[g];
+      const uint32_t g = cm.list[i];
+      q0 = cm.p0[g];
+      q1 = cm.p1[g];
+      q2 = cm.p2[g];
       hit = ellipse_hits(q0, q1, q2, wx0, wy0, 7.f, 3.f);
     }
     const uint32_t m = __ballot_sync(kFull, hit);
@@ -198,9 +198,9 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const int 
       if (done) continue;
       const float4 q0 = s_q0[warp][h], q1 = s_q1[warp][h];
       float alpha, G, dx, dy;
-      if (!eval_gaussian(q0, q1, fpx, fpy, rp.alpha_clamp, rp.alpha_min, alpha, G, dx, dy)) continue;
+      if (!eval_gaussian(q0, q1, fpx, fpy, cm.alpha_clamp, cm.alpha_min, alpha, G, dx, dy)) continue;
       const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
-      if (Tn < rp.t_stop) {
+      if (Tn < cm.t_stop) {
         done = true;
         continue;
       }
@@ -211,7 +211,7 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const int 
       C2 = fmaf(w, q2.z, C2);
       D = fmaf(w, q1.z, D);
       const uint32_t idog = __float_as_uint(q1.w);
-      if ((idog & kNoObject) == gt_match && (!rp.og_filter || (idog >> 31))) ins += w;
+      if ((idog & kNoObject) == gt_match && (!cm.og_filter || (idog >> 31))) ins += w;
       if (kId) {
         const int slot = s_wslot[warp][h];
         if (slot == cur_slot) {
@@ -257,7 +257,7 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const int 
           for (int h = 0; h < nh; ++h) {
             if (s_pos[warp][h] >= last) continue;
             float alpha, G, dx, dy;
-            if (!eval_gaussian(s_q0[warp][h], s_q1[warp][h], fpx, fpy, rp.alpha_clamp, rp.alpha_min, alpha, G,
+            if (!eval_gaussian(s_q0[warp][h], s_q1[warp][h], fpx, fpy, cm.alpha_clamp, cm.alpha_min, alpha, G,
                                dx, dy))
               continue;
             const float w = __fmul_rn(alpha, Tr);
@@ -353,7 +353,9 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const int 
 
 template <int TW, bool kId>
 __global__ void __launch_bounds__(kThreads) k_blend_forward(BlendFwdArgs a) {
-  blend_fwd_tile<TW, kId>(a, (int)blockIdx.x);
+  const BlendCommon cm{a.p0, a.p1, a.p2, a.gid, a.list, nullptr, a.rp.alpha_clamp, a.rp.alpha_min, a.rp.t_stop,
+                       a.rp.og_filter};
+  blend_fwd_tile<TW, kId>(a, cm, (int)blockIdx.x);
 }
 
 // Deterministic sum of the per-tile loss partials in double, scaled by 1/(HW).
@@ -393,49 +395,50 @@ __global__ void k_loss_reduce_batch(const __grid_constant__ LossTable t) {
   if (k.loss) loss_reduce(k.part, k.tiles, k.lambda_ins, k.scale, k.loss);
 }
 
-// Sum of 16 per-lane values over the warp with a transposing butterfly: after it, lane l
-// holds (in v[0]) the warp sum of value index (l >> 1) & 15.  16 shuffles in total.
-__device__ __forceinline__ void warp_transpose_sum16(float v[16]) {
+// Sum over the warp of 10 per-lane values, transposing as it halves: stage 1 (lanes l and
+// l^16) pairs value k with value k+5, stage 2 (l^8) pairs slots 0/2 and 1/3 and sums slot 4
+// plainly, stage 3 (l^4) pairs slots 0/1 and sums slot 2 plainly, stage 4 (l^2) pairs the
+// last two, stage 5 (l^1) sums plainly: 12 shuffles.  Lane l ends with the total of value
+// (l & 16 ? 5 : 0) + (l & 2 ? 4 : (l & 8 ? 2 : 0) + (l & 4 ? 1 : 0)).
+__device__ __forceinline__ float warp_transpose_sum10(const float v[10]) {
   const int lane = threadIdx.x & 31;
+  float u[5], w[3], x[2];
   {
     const bool hi = lane & 16;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const float send = hi ? v[k] : v[k + 8];
-      const float keep = hi ? v[k + 8] : v[k];
-      v[k] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 16);
+    for (int k = 0; k < 5; ++k) {
+      const float send = hi ? v[k] : v[k + 5];
+      const float keep = hi ? v[k + 5] : v[k];
+      u[k] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 16);
     }
   }
   {
     const bool hi = lane & 8;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float send = hi ? v[k] : v[k + 4];
-      const float keep = hi ? v[k + 4] : v[k];
-      v[k] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 8);
+    for (int k = 0; k < 2; ++k) {
+      const float send = hi ? u[k] : u[k + 2];
+      const float keep = hi ? u[k + 2] : u[k];
+      w[k] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 8);
     }
+    w[2] = u[4] + __shfl_xor_sync(0xFFFFFFFFu, u[4], 8);
   }
   {
     const bool hi = lane & 4;
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const float send = hi ? v[k] : v[k + 2];
-      const float keep = hi ? v[k + 2] : v[k];
-      v[k] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 4);
-    }
+    const float send = hi ? w[0] : w[1];
+    const float keep = hi ? w[1] : w[0];
+    x[0] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 4);
+    x[1] = w[2] + __shfl_xor_sync(0xFFFFFFFFu, w[2], 4);
   }
-  {
-    const bool hi = lane & 2;
-    const float send = hi ? v[0] : v[1];
-    const float keep = hi ? v[1] : v[0];
-    v[0] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 2);
-  }
-  v[0] += __shfl_xor_sync(0xFFFFFFFFu, v[0], 1);
+  const bool hi = lane & 2;
+  const float send = hi ? x[0] : x[1];
+  const float keep = hi ? x[1] : x[0];
+  const float y = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 2);
+  return y + __shfl_xor_sync(0xFFFFFFFFu, y, 1);
 }
 
 // Backward of one tile (local tile index); warp-autonomous, no block barrier.
 template <int TW>
-__device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const int tile) {
+__device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const BlendCommon& cm, const int tile) {
   constexpr int NW = kThreads / 32;
   __shared__ float4 s_q0[NW][32], s_q1[NW][32], s_q2[NW][32];
   __shared__ uint32_t s_g[NW][32];
@@ -475,8 +478,12 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const int 
   float R = T * (gC0 * rp.bg[0] + gC1 * rp.bg[1] + gC2 * rp.bg[2]);
   const float fpx = (float)px, fpy = (float)py;
   const uint32_t lt = lanemask_lt();
-  // lanes 0..2 gather the butterfly's ten sums (held by lanes 0, 2, .., 18) as float4s
-  const int src0 = (lane < 3 ? 8 * lane : 0);
+  // lanes 0..2 gather the ten warp totals as float4s: lane 0 values 0-3 (held by lanes 0,
+  // 4, 8, 12), lane 1 values 4-7 (lanes 2, 16, 20, 24), lane 2 values 8-9 (lanes 28, 18)
+  const int src0 = lane == 1 ? 2 : (lane == 2 ? 28 : 0);
+  const int src1 = lane == 1 ? 16 : (lane == 2 ? 18 : 4);
+  const int src2 = lane == 1 ? 20 : 8;
+  const int src3 = lane == 1 ? 24 : 12;
 
   for (int c = (wmax - 1) & ~31; c >= 0 && wmax > 0; c -= 32) {
     const int jl = c + lane;
@@ -484,10 +491,10 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const int 
     float4 q0, q1, q2;
     uint32_t g = 0;
     if (jl < wmax) {
-      g = a.list[start + jl];
-      q0 = a.p0[g];
-      q1 = a.p1[g];
-      q2 = a.p2[g];
+      g = cm.list[start + jl];
+      q0 = cm.p0[g];
+      q1 = cm.p1[g];
+      q2 = cm.p2[g];
       hit = ellipse_hits(q0, q1, q2, wx0, wy0, 7.f, 3.f);
     }
     const uint32_t m = __ballot_sync(kFull, hit);
@@ -501,25 +508,25 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const int 
     }
     __syncwarp();
     for (int h = __popc(m) - 1; h >= 0; --h) {
-      float v[16];
+      float v[10];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) v[k] = 0.f;
+      for (int k = 0; k < 10; ++k) v[k] = 0.f;
       bool act = false;
       if (s_pos[warp][h] < (int)nc) {
         const float4 p0 = s_q0[warp][h], p1 = s_q1[warp][h];
         float alpha, G, dx, dy;
-        if (eval_gaussian(p0, p1, fpx, fpy, rp.alpha_clamp, rp.alpha_min, alpha, G, dx, dy)) {
+        if (eval_gaussian(p0, p1, fpx, fpy, cm.alpha_clamp, cm.alpha_min, alpha, G, dx, dy)) {
           act = true;
           const float inv = __frcp_rn(1.f - alpha);
           T = T * inv;
           const float w = alpha * T;
           const float4 p2 = s_q2[warp][h];
           const uint32_t idog = __float_as_uint(p1.w);
-          const bool counts = (idog & kNoObject) == gt_match && (!rp.og_filter || (idog >> 31));
+          const bool counts = (idog & kNoObject) == gt_match && (!cm.og_filter || (idog >> 31));
           const float U = gC0 * p2.x + gC1 * p2.y + gC2 * p2.z + gD * p1.z + gA + (counts ? gI : 0.f);
           const float dalpha = T * U - R * inv;
           R = fmaf(w, U, R);
-          const bool clamped = __fmul_rn(p1.y, G) > rp.alpha_clamp;
+          const bool clamped = __fmul_rn(p1.y, G) > cm.alpha_clamp;
           const float dpow = clamped ? 0.f : dalpha * alpha;
           v[0] = dpow * dx;
           v[1] = dpow * dy;
@@ -534,14 +541,14 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const int 
         }
       }
       if (__any_sync(kFull, act)) {
-        warp_transpose_sum16(v);
-        // lane 2k holds sum k (k < 10; k = 10, 11 are zero): lane L < 3 collects 4L .. 4L+3
-        const float a0 = __shfl_sync(kFull, v[0], src0);
-        const float a1 = __shfl_sync(kFull, v[0], src0 + 2);
-        const float a2 = __shfl_sync(kFull, v[0], src0 + 4);
-        const float a3 = __shfl_sync(kFull, v[0], src0 + 6);
+        const float y = warp_transpose_sum10(v);
+        const float a0 = __shfl_sync(kFull, y, src0);
+        const float a1 = __shfl_sync(kFull, y, src1);
+        float a2 = __shfl_sync(kFull, y, src2);
+        float a3 = __shfl_sync(kFull, y, src3);
+        if (lane == 2) a2 = a3 = 0.f;   // record slots 10 and 11 are unused
         if (lane < 3) {
-          float4* dst = reinterpret_cast<float4*>(a.grad2d) + 3 * (int64_t)s_g[warp][h] + lane;
+          float4* dst = reinterpret_cast<float4*>(cm.grad2d) + 3 * (int64_t)s_g[warp][h] + lane;
           atomicAdd(dst, make_float4(a0, a1, a2, a3));
         }
       }
@@ -552,7 +559,9 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const int 
 
 template <int TW>
 __global__ void __launch_bounds__(kThreads) k_blend_backward(BlendBwdArgs a) {
-  blend_bwd_tile<TW>(a, (int)blockIdx.x);
+  const BlendCommon cm{a.p0, a.p1, a.p2, nullptr, a.list, a.grad2d, a.rp.alpha_clamp, a.rp.alpha_min, 0.f,
+                       a.rp.og_filter};
+  blend_bwd_tile<TW>(a, cm, (int)blockIdx.x);
 }
 
 // Persistent step over the tiles of a batch of keyframes: each CTA takes tiles from an
@@ -563,7 +572,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_backward(BlendBwdArgs a) {
 // barrier separates the two.  Per-keyframe arguments are read from the kernel's
 // parameter table.
 template <int TW, bool kId>
-__global__ void __launch_bounds__(kThreads, 4) k_blend_step(const __grid_constant__ StepTable t,
+__global__ void __launch_bounds__(kThreads, 4) k_blend_step(const __grid_constant__ StepTable t, BlendCommon cm,
                                                             uint32_t* __restrict__ queue) {
   __shared__ uint32_t s_item;
   const uint32_t total = t.tile_off[t.nkf];
@@ -575,8 +584,44 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_step(const __grid_constan
     int k = 0;
     while (k + 1 < t.nkf && t.tile_off[k + 1] <= it) ++k;
     const int tile = (int)(it - t.tile_off[k]);
-    blend_fwd_tile<TW, kId>(t.f[k], tile);
-    blend_bwd_tile<TW>(t.b[k], tile);
+    blend_fwd_tile<TW, kId>(t.f[k], cm, tile);
+    blend_bwd_tile<TW>(t.b[k], cm, tile);
+    __syncthreads();
+  }
+}
+
+// The same queue walk with the forward and the backward as two persistent kernels (each
+// with its own queue): fewer registers per kernel than the fused walk.
+template <int TW, bool kId>
+__global__ void __launch_bounds__(kThreads) k_blend_fwd_queue(const __grid_constant__ StepTable t, BlendCommon cm,
+                                                              uint32_t* __restrict__ queue) {
+  __shared__ uint32_t s_item;
+  const uint32_t total = t.tile_off[t.nkf];
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
+    __syncthreads();
+    const uint32_t it = s_item;
+    if (it >= total) break;
+    int k = 0;
+    while (k + 1 < t.nkf && t.tile_off[k + 1] <= it) ++k;
+    blend_fwd_tile<TW, kId>(t.f[k], cm, (int)(it - t.tile_off[k]));
+    __syncthreads();
+  }
+}
+
+template <int TW>
+__global__ void __launch_bounds__(kThreads) k_blend_bwd_queue(const __grid_constant__ StepTable t, BlendCommon cm,
+                                                              uint32_t* __restrict__ queue) {
+  __shared__ uint32_t s_item;
+  const uint32_t total = t.tile_off[t.nkf];
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
+    __syncthreads();
+    const uint32_t it = s_item;
+    if (it >= total) break;
+    int k = 0;
+    while (k + 1 < t.nkf && t.tile_off[k + 1] <= it) ++k;
+    blend_bwd_tile<TW>(t.b[k], cm, (int)(it - t.tile_off[k]));
     __syncthreads();
   }
 }
@@ -626,32 +671,74 @@ cudaError_t launch_blend_backward(const BlendBwdArgs& a, cudaStream_t s) {
 namespace dqo {
 namespace {
 
-template <int TW, bool kId>
-cudaError_t step_tw(const StepTable& t, uint32_t* queue, int ctas_per_sm, int sms, cudaStream_t s) {
+template <typename Kernel>
+unsigned persistent_grid(Kernel k, int ctas_per_sm, int sms, uint32_t total, cudaError_t* e) {
   int occ = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_blend_step<TW, kId>, kThreads, 0);
-  if (e != cudaSuccess) return e;
+  *e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kThreads, 0);
+  if (*e != cudaSuccess) return 0;
   if (occ < 1) occ = 1;
   const int per = ctas_per_sm > 0 ? (ctas_per_sm < occ ? ctas_per_sm : occ) : occ;
-  const uint32_t total = t.tile_off[t.nkf];
   unsigned grid = (unsigned)(per * sms);
-  if (grid > total) grid = total;
-  if (grid == 0) return cudaSuccess;
-  k_blend_step<TW, kId><<<grid, kThreads, 0, s>>>(t, queue);
+  return grid > total ? total : grid;
+}
+
+// Blend schedules of a batch: 0 = fused queue kernel, 1 = forward and backward queue
+// kernels, 2 = the one-keyframe kernels launched per keyframe (arguments by value).
+template <int TW, bool kId>
+cudaError_t step_tw(const StepTable& t, const BlendCommon& cm, uint32_t* queue, int ctas_per_sm, int sms,
+                    int schedule, cudaStream_t s) {
+  const uint32_t total = t.tile_off[t.nkf];
+  if (total == 0) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  if (schedule == 0) {
+    const unsigned grid = persistent_grid(k_blend_step<TW, kId>, ctas_per_sm, sms, total, &e);
+    if (e != cudaSuccess) return e;
+    k_blend_step<TW, kId><<<grid, kThreads, 0, s>>>(t, cm, queue);
+  } else if (schedule == 1) {
+    unsigned grid = persistent_grid(k_blend_fwd_queue<TW, kId>, ctas_per_sm, sms, total, &e);
+    if (e != cudaSuccess) return e;
+    k_blend_fwd_queue<TW, kId><<<grid, kThreads, 0, s>>>(t, cm, queue);
+    grid = persistent_grid(k_blend_bwd_queue<TW>, ctas_per_sm, sms, total, &e);
+    if (e != cudaSuccess) return e;
+    k_blend_bwd_queue<TW><<<grid, kThreads, 0, s>>>(t, cm, queue + 1);
+  } else {
+    for (int k = 0; k < t.nkf; ++k) {
+      const unsigned tiles = t.tile_off[k + 1] - t.tile_off[k];
+      if (tiles == 0) continue;
+      BlendFwdArgs f = t.f[k];
+      f.p0 = cm.p0;
+      f.p1 = cm.p1;
+      f.p2 = cm.p2;
+      f.gid = cm.gid;
+      f.list = cm.list;
+      k_blend_forward<TW, kId><<<tiles, kThreads, 0, s>>>(f);
+    }
+    for (int k = 0; k < t.nkf; ++k) {
+      const unsigned tiles = t.tile_off[k + 1] - t.tile_off[k];
+      if (tiles == 0) continue;
+      BlendBwdArgs b = t.b[k];
+      b.p0 = cm.p0;
+      b.p1 = cm.p1;
+      b.p2 = cm.p2;
+      b.list = cm.list;
+      b.grad2d = cm.grad2d;
+      k_blend_backward<TW><<<tiles, kThreads, 0, s>>>(b);
+    }
+  }
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_blend_step(const StepTable& t, uint32_t* queue, int tile_w, bool with_id, int ctas_per_sm,
-                              int sms, cudaStream_t s) {
+cudaError_t launch_blend_step(const StepTable& t, const BlendCommon& cm, uint32_t* queue, int tile_w, bool with_id,
+                              int ctas_per_sm, int sms, int schedule, cudaStream_t s) {
   switch (tile_w * 2 + (with_id ? 1 : 0)) {
-    case 16: return step_tw<8, false>(t, queue, ctas_per_sm, sms, s);
-    case 17: return step_tw<8, true>(t, queue, ctas_per_sm, sms, s);
-    case 32: return step_tw<16, false>(t, queue, ctas_per_sm, sms, s);
-    case 33: return step_tw<16, true>(t, queue, ctas_per_sm, sms, s);
-    case 64: return step_tw<32, false>(t, queue, ctas_per_sm, sms, s);
-    case 65: return step_tw<32, true>(t, queue, ctas_per_sm, sms, s);
+    case 16: return step_tw<8, false>(t, cm, queue, ctas_per_sm, sms, schedule, s);
+    case 17: return step_tw<8, true>(t, cm, queue, ctas_per_sm, sms, schedule, s);
+    case 32: return step_tw<16, false>(t, cm, queue, ctas_per_sm, sms, schedule, s);
+    case 33: return step_tw<16, true>(t, cm, queue, ctas_per_sm, sms, schedule, s);
+    case 64: return step_tw<32, false>(t, cm, queue, ctas_per_sm, sms, schedule, s);
+    case 65: return step_tw<32, true>(t, cm, queue, ctas_per_sm, sms, schedule, s);
     default: return cudaErrorInvalidValue;
   }
 }

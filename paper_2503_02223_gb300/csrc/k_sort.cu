@@ -355,9 +355,9 @@ cudaError_t launch_emit_pairs_u64(const ushort4* rect, const uint32_t* offsets, 
 }
 
 cudaError_t launch_tile_ranges_u32(const uint32_t* keys, int64_t m, int rank_bits, const uint32_t* order,
-                                   uint2* ranges, uint32_t* list, cudaStream_t s) {
+                                   uint2* ranges, uint32_t* list, cudaStream_t s, const uint64_t* m_dev) {
   if (m == 0) return cudaSuccess;
-  k_tile_ranges<uint32_t><<<grid_for(m, kThreads), kThreads, 0, s>>>(keys, m, nullptr, rank_bits, order, ranges,
+  k_tile_ranges<uint32_t><<<grid_for(m, kThreads), kThreads, 0, s>>>(keys, m, m_dev, rank_bits, order, ranges,
                                                                        list);
   return cudaGetLastError();
 }
@@ -372,12 +372,22 @@ cudaError_t launch_tile_ranges_u64(const uint64_t* keys, int64_t m, int rank_bit
 
 cudaError_t launch_emit_pairs_batch(const EmitTable& t, int nkf, int64_t max_n, const ushort4* rect,
                                     const uint32_t* offsets, const uint32_t* rank, int rank_bits, uint64_t capacity,
-                                    uint64_t* keys, uint32_t* overflow, cudaStream_t s) {
+                                    void* keys, bool k32, uint32_t* overflow, cudaStream_t s) {
   if (nkf == 0 || max_n == 0) return cudaSuccess;
   const dim3 grid(grid_for(max_n, kThreads), (unsigned)nkf);
-  k_emit_pairs_batch<uint64_t><<<grid, kThreads, 0, s>>>(t, rect, offsets, rank, rank_bits, capacity, keys,
-                                                         overflow);
+  if (k32)
+    k_emit_pairs_batch<uint32_t><<<grid, kThreads, 0, s>>>(t, rect, offsets, rank, rank_bits, capacity,
+                                                           static_cast<uint32_t*>(keys), overflow);
+  else
+    k_emit_pairs_batch<uint64_t><<<grid, kThreads, 0, s>>>(t, rect, offsets, rank, rank_bits, capacity,
+                                                           static_cast<uint64_t*>(keys), overflow);
   return cudaGetLastError();
+}
+
+cudaError_t radix_sort_u32_dev(uint32_t* keys_a, uint32_t* keys_b, int64_t n, int end_bit, uint32_t* hist_scratch,
+                               uint64_t* scan_scratch, int* sel, cudaStream_t s, const uint64_t* n_dev) {
+  return radix_sort_impl<uint32_t, false>(keys_a, keys_b, nullptr, nullptr, n, end_bit, hist_scratch,
+                                          scan_scratch, sel, s, n_dev);
 }
 
 }  // namespace dqo

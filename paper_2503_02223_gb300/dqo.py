@@ -21,7 +21,7 @@ c_i64 = C.c_int64
 c_p = C.c_void_p
 
 DQO_OK, DQO_EINVAL, DQO_ENOMEM, DQO_ECUDA, DQO_ETIMEOUT, DQO_ENOTIMPL, DQO_ESTATE = range(7)
-PHASES = ("project", "depth_sort", "binning", "blend_fwd", "blend_bwd", "project_bwd", "quadric")
+PHASES = ("project", "depth_sort", "binning", "blend_fwd", "blend_bwd", "project_bwd", "quadric", "blend_step")
 (DQO_BUF_PROJ, DQO_BUF_RECT, DQO_BUF_DEPTH_ORDER, DQO_BUF_TILE_RANGES, DQO_BUF_TILE_LIST, DQO_BUF_T_FINAL,
  DQO_BUF_N_CONTRIB, DQO_BUF_GRAD2D) = range(8)
 
@@ -80,9 +80,9 @@ _SIGS = {
     "dqo_quadric_fit": (c_i32, [c_p, c_i32, c_i32, c_p, c_p, c_p, c_i32, c_p, c_i32, c_f, c_p, c_p, c_p, c_p, c_p,
                                 c_p]),
     "dqo_quadric_canonical": (c_i32, [c_i32, c_p, c_p, c_p]),
-    "dqo_batch_step": (c_i32, [c_p, c_p, c_i32, c_p, c_p, c_i32, c_p]),
+    "dqo_batch_step": (c_i32, [c_p, c_p, c_i32, c_p, c_p, c_i32, c_i32, c_p]),
     "dqo_batch_check": (c_i32, [c_p, c_p, c_p]),
-    "dqo_batch_tune": (c_i32, [c_p, c_p, c_i32, c_p, c_p, c_i32, c_p, c_p, c_p]),
+    "dqo_batch_tune": (c_i32, [c_p, c_p, c_i32, c_p, c_p, c_i32, c_p, c_p, c_p, c_p]),
     "dqo_mlp_features": (c_i32, [c_i32, c_i32, c_p, c_p, c_p, c_i32, c_p, c_p, c_f, c_p, c_p, c_i64, c_p]),
     "dqo_mlp_state_bytes": (C.c_size_t, []),
     "dqo_mlp_set_params": (c_i32, [c_p, c_p, c_p]),
@@ -398,12 +398,25 @@ def fit_batch(P, q_ptr, pair_v, obs, iters=100, lr=1e-2, start=None, init=None, 
     return f
 
 
+SCHEDULE_FUSED, SCHEDULE_SPLIT, SCHEDULE_PER_KEYFRAME = 0, 1, 2
+TUNE_CANDIDATES = 21
+
+
+def tune_candidate(i: int) -> tuple:
+    """(tile_w, tile_h, ctas_per_sm, schedule) of autotuner candidate i."""
+    w, h = ((16, 16), (8, 32), (32, 8))[i // 7]
+    j = i % 7
+    sched = SCHEDULE_FUSED if j < 3 else (SCHEDULE_SPLIT if j < 6 else SCHEDULE_PER_KEYFRAME)
+    cps = 2 + j if j < 3 else (j - 1 if j < 6 else 0)
+    return w, h, cps, sched
+
+
 def dqo_batch_step(ctx: Context, st: dqo_settings, kfs: list, fits: dqo_fit_batch | None = None,
-                   ctas_per_sm: int = 0, stream=None):
+                   ctas_per_sm: int = 0, schedule: int = SCHEDULE_FUSED, stream=None):
     arr = (dqo_keyframe * len(kfs))(*kfs)
     _check("dqo_batch_step",
            load().dqo_batch_step(ctx.handle, C.byref(st), len(kfs), arr, None if fits is None else C.byref(fits),
-                                 ctas_per_sm, _stream(stream)), ctx.handle)
+                                 ctas_per_sm, schedule, _stream(stream)), ctx.handle)
 
 
 def dqo_batch_check(ctx: Context) -> tuple[int, bool]:
@@ -413,16 +426,16 @@ def dqo_batch_check(ctx: Context) -> tuple[int, bool]:
 
 
 def dqo_batch_tune(ctx: Context, st: dqo_settings, kfs: list, fits: dqo_fit_batch | None = None, reps: int = 3,
-                   stream=None) -> tuple[int, list]:
-    """Picks the fastest tile shape (written into st) and CTAs per SM (returned), with the
-    nine candidates' mean step times in ms."""
+                   stream=None) -> tuple[int, int, list]:
+    """Picks the fastest tile shape (written into st), CTAs per SM and schedule (returned),
+    with every candidate's mean step time in ms (order of tune_candidate)."""
     arr = (dqo_keyframe * len(kfs))(*kfs)
-    cps = c_i32(0)
-    ms = (c_f * 9)()
+    cps, sched = c_i32(0), c_i32(0)
+    ms = (c_f * TUNE_CANDIDATES)()
     _check("dqo_batch_tune",
            load().dqo_batch_tune(ctx.handle, C.byref(st), len(kfs), arr, None if fits is None else C.byref(fits),
-                                 reps, C.byref(cps), ms, _stream(stream)), ctx.handle)
-    return int(cps.value), list(ms)
+                                 reps, C.byref(cps), C.byref(sched), ms, _stream(stream)), ctx.handle)
+    return int(cps.value), int(sched.value), list(ms)
 
 
 # ------------------------------------------------------------------------ learned proposal

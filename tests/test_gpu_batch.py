@@ -55,8 +55,8 @@ class Batch:
             self.grads.append(gr)
             self.kfs.append(dqo.keyframe(gd, NUM_OBJECTS, cam, td, out, gr))
 
-    def step(self, fits=None, ctas_per_sm=0):
-        dqo.dqo_batch_step(self.ctx, self.st, self.kfs, fits, ctas_per_sm)
+    def step(self, fits=None, ctas_per_sm=0, schedule=dqo.SCHEDULE_FUSED):
+        dqo.dqo_batch_step(self.ctx, self.st, self.kfs, fits, ctas_per_sm, schedule)
 
     def zero_grads(self):
         for gd, gr in self.scenes.values():
@@ -99,12 +99,13 @@ def _check_against_singles(bt, cases, **st):
             assert _close(gr[name], ref), (key, name, np.abs(gr[name] - ref).max(), np.abs(ref).max())
 
 
+@pytest.mark.parametrize("schedule", [dqo.SCHEDULE_FUSED, dqo.SCHEDULE_SPLIT, dqo.SCHEDULE_PER_KEYFRAME])
 @pytest.mark.parametrize("tile", [(16, 16), (8, 32), (32, 8)])
-def test_batch_step_matches_single_keyframe_calls(tile):
+def test_batch_step_matches_single_keyframe_calls(tile, schedule):
     cases = _scenes()
     st = dict(tile_w=tile[0], tile_h=tile[1])
     bt = Batch(cases, **st)
-    bt.step()
+    bt.step(schedule=schedule)
     torch.cuda.synchronize()
     _check_against_singles(bt, cases, **st)
     pairs, over = dqo.dqo_batch_check(bt.ctx)
@@ -210,11 +211,12 @@ def test_batch_capacity_overflow_is_reported_then_resized():
 def test_batch_autotuner_picks_a_working_configuration():
     cases = _scenes()
     bt = Batch(cases)
-    cps, ms = dqo.dqo_batch_tune(bt.ctx, bt.st, bt.kfs, None, reps=2)
-    assert (bt.st.tile_w, bt.st.tile_h) in ((16, 16), (8, 32), (32, 8)) and cps in (2, 3, 4)
-    assert all(m > 0 for m in ms)
+    cps, sched, ms = dqo.dqo_batch_tune(bt.ctx, bt.st, bt.kfs, None, reps=2)
+    assert len(ms) == dqo.TUNE_CANDIDATES and all(m > 0 for m in ms)
+    best = int(np.argmin(ms))
+    assert dqo.tune_candidate(best) == (bt.st.tile_w, bt.st.tile_h, cps, sched)
     bt.zero_grads()
-    bt.step(ctas_per_sm=cps)
+    bt.step(ctas_per_sm=cps, schedule=sched)
     torch.cuda.synchronize()
     _check_against_singles(bt, cases, tile_w=bt.st.tile_w, tile_h=bt.st.tile_h)
     bt.ctx.close()
