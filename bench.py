@@ -66,6 +66,9 @@ def parse():
     p.add_argument("--batch", type=int, default=256)
     p.add_argument("--no-learned", action="store_true", help="skip the learned-proposal section")
     p.add_argument("--no-batched", action="store_true", help="skip the batched-keyframes section")
+    p.add_argument("--no-tune", action="store_true",
+                   help="fixed step configuration (--tile, per-keyframe blend schedule) instead of the autotuner; "
+                        "for profiling, where the tuner's timings are distorted")
     return p.parse_args()
 
 
@@ -275,7 +278,10 @@ def run_ours(args, rank, world, local_rank):
     kfb = dqo.keyframe(g, NUM_OBJECTS, cam, t, out, grads)
 
     bst = dqo.settings(tile_w=tw, tile_h=th, batch=args.batch)
-    cps, sched, tune_ms = dqo.dqo_batch_tune(bctx, bst, [kfb], None, reps=5)
+    if args.no_tune:
+        cps, sched, tune_ms = 0, dqo.SCHEDULE_PER_KEYFRAME, []
+    else:
+        cps, sched, tune_ms = dqo.dqo_batch_tune(bctx, bst, [kfb], None, reps=5)
 
     def graph_body():
         for v in grads.values():
@@ -466,6 +472,7 @@ def run_ours(args, rank, world, local_rank):
 
     if not args.no_learned:
         fits["learned"] = learned_section(ctx, dev, stream, world, fd, nfit, fit_ms)
+    batched_section.no_tune = args.no_tune
     batched = None if args.no_batched else batched_section(dev, stream, world, fq, fd)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -638,7 +645,10 @@ def batched_section(dev, stream, world, fq, fd):
     dqo.dqo_batch_step(bctx, bst, kfs, fb)             # same 16x16 tiles as the single form
     torch.cuda.synchronize()
     same_loss = all(torch.equal(a, o["loss"]) for a, o in zip(loss_single, outs))
-    cps, sched, tune_ms = dqo.dqo_batch_tune(bctx, bst, kfs, fb, reps=3)
+    if getattr(batched_section, "no_tune", False):
+        cps, sched, tune_ms = 0, dqo.SCHEDULE_SPLIT, []
+    else:
+        cps, sched, tune_ms = dqo.dqo_batch_tune(bctx, bst, kfs, fb, reps=3)
     dqo.dqo_batch_step(bctx, bst, kfs, fb, cps, sched)        # sizing call for the chosen configuration
     torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()

@@ -148,6 +148,7 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const Blen
     slot_ids_for_round(s_mask, s_pref, nw, 0, s_slot_id);
 #pragma unroll
     for (int s = 0; s < kIdSlots; ++s) s_W[s][tid] = 0.f;
+    __syncthreads();  // round 0's slot ids are published before the walk, not after it
   }
 
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, ins = 0.f;
@@ -232,7 +233,6 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const Blen
   int32_t best_id = -1;
   if (kId) {
     if (cur_slot >= 0 && cur_slot < kIdSlots) s_W[cur_slot][tid] += cur_w;
-    __syncthreads();  // slot ids of round 0 were written block-wide before the walk
     float best_w = 0.f;
     const int n0 = min(nslots, kIdSlots);
     for (int s = 0; s < n0; ++s) {
@@ -436,6 +436,10 @@ __device__ __forceinline__ float warp_transpose_sum10(const float v[10]) {
   return y + __shfl_xor_sync(0xFFFFFFFFu, y, 1);
 }
 
+// Up to this many contributing lanes a (warp, Gaussian) adds its partials with per-lane
+// atomics instead of a warp sum.
+constexpr int kFewLanes = 4;
+
 // Backward of one tile (local tile index); warp-autonomous, no block barrier.
 template <int TW>
 __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const BlendCommon& cm, const int tile) {
@@ -540,7 +544,17 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const Blen
           v[9] = w * gD;
         }
       }
-      if (__any_sync(kFull, act)) {
+      const uint32_t am = __ballot_sync(kFull, act);
+      if (am != 0u && __popc(am) <= kFewLanes) {
+        // few contributing lanes: each adds its own partials (three vector atomics, one
+        // warp instruction each) instead of the 46-instruction warp sum
+        if (act) {
+          float4* dst = reinterpret_cast<float4*>(cm.grad2d) + 3 * (int64_t)s_g[warp][h];
+          atomicAdd(dst, make_float4(v[0], v[1], v[2], v[3]));
+          atomicAdd(dst + 1, make_float4(v[4], v[5], v[6], v[7]));
+          atomicAdd(dst + 2, make_float4(v[8], v[9], 0.f, 0.f));
+        }
+      } else if (am != 0u) {
         const float y = warp_transpose_sum10(v);
         const float a0 = __shfl_sync(kFull, y, src0);
         const float a1 = __shfl_sync(kFull, y, src1);
@@ -558,7 +572,7 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const Blen
 }
 
 template <int TW>
-__global__ void __launch_bounds__(kThreads) k_blend_backward(BlendBwdArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) k_blend_backward(BlendBwdArgs a) {
   const BlendCommon cm{a.p0, a.p1, a.p2, nullptr, a.list, a.grad2d, a.rp.alpha_clamp, a.rp.alpha_min, 0.f,
                        a.rp.og_filter};
   blend_bwd_tile<TW>(a, cm, (int)blockIdx.x);
@@ -610,7 +624,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd_queue(const __grid_const
 }
 
 template <int TW>
-__global__ void __launch_bounds__(kThreads) k_blend_bwd_queue(const __grid_constant__ StepTable t, BlendCommon cm,
+__global__ void __launch_bounds__(kThreads, 4) k_blend_bwd_queue(const __grid_constant__ StepTable t, BlendCommon cm,
                                                               uint32_t* __restrict__ queue) {
   __shared__ uint32_t s_item;
   const uint32_t total = t.tile_off[t.nkf];

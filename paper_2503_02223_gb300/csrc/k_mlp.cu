@@ -135,16 +135,30 @@ __device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
 }
 
 // rows x K tile from K-contiguous global rows (leading dimension ld elements, 16-byte
-// aligned rows); rows at or past `valid_rows` are zero.
+// aligned rows); rows at or past `valid_rows` are zero.  Each thread issues 8 loads before
+// it stores any, so 8 pieces per thread are in flight at once.
 __device__ __forceinline__ void load_tile(unsigned char* dst, const __nv_bfloat16* __restrict__ src, int64_t ld,
                                           int rows, int valid_rows, int K) {
+  constexpr int kUnroll = 8;
   const int per_row = K >> 3;
   const int total = rows * per_row;
-  for (int i = threadIdx.x; i < total; i += blockDim.x) {
-    const int r = i / per_row, kc = i - r * per_row;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (r < valid_rows) v = __ldg(reinterpret_cast<const uint4*>(src + (int64_t)r * ld + kc * 8));
-    *reinterpret_cast<uint4*>(dst + tile_offset(r, kc * 8, rows)) = v;
+  for (int base = threadIdx.x; base < total; base += kUnroll * blockDim.x) {
+    uint4 v[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int i = base + u * blockDim.x;
+      const int r = i / per_row, kc = i - r * per_row;
+      v[u] = make_uint4(0u, 0u, 0u, 0u);
+      if (i < total && r < valid_rows) v[u] = __ldg(reinterpret_cast<const uint4*>(src + (int64_t)r * ld + kc * 8));
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int i = base + u * blockDim.x;
+      if (i < total) {
+        const int r = i / per_row, kc = i - r * per_row;
+        *reinterpret_cast<uint4*>(dst + tile_offset(r, kc * 8, rows)) = v[u];
+      }
+    }
   }
 }
 
