@@ -50,6 +50,20 @@ KERNEL_SRC = {"blend_fwd": "k_blend.cu", "blend_bwd": "k_blend.cu", "blend_step"
 # 2 (128*128 + 128*128 + 9*128); backward dH2 and dW3 2 (9*128) each, dH1, dW2, dW1
 # 2 (128*128) each.
 MLP_FLOPS_PER_SAMPLE = 2 * (128 * 128 + 128 * 128 + 9 * 128) + 2 * (2 * 9 * 128 + 3 * 128 * 128)
+# Bytes each HBM-bound phase of the step moves (design bytes, counted from the kernels):
+# projection: reads means 12, log-scales 12, quaternion 16, logit 4, rgb 12, id 4, flags 1;
+#   writes 3 x float4 48, rect 8, tiles 4, depth key 4, value 4, id 4        -> 133 B/Gaussian
+# depth sort: scan of tiles per Gaussian (read 4, write 4, read 4); 4 radix passes of
+#   (histogram read 4 + scatter read 8, write 8) on key+value; ranks written 4 -> 92 B/Gaussian
+# binning: emission reads rect 8, offset 4, rank 4 per Gaussian and writes 4 per pair; 4
+#   passes of (histogram read 4 + scatter read 4, write 4) per pair; ranges read key 4 and
+#   the order 4, write the list 4 per pair                                   -> 16 B/Gaussian + 64 B/pair
+#   (the algorithmic minimum: write each pair's value once and read it once in the blend,
+#   8 B/pair, plus 16 B/Gaussian)
+# projection adjoint: reads the 10 inputs 61, tiles 4, moment record 48; read-modify-write of
+#   the 14 gradient floats 112                                              -> 225 B/Gaussian
+HBM_BYTES = {"project": (133, 0), "depth_sort": (92, 0), "binning": (16, 64), "project_bwd": (225, 0)}
+SORT_MIN_BYTES = (16, 8)
 MLP_TRAIN_SAMPLES = 1 << 20
 MLP_EPOCHS = 10
 MLP_BATCH = 4096
@@ -441,6 +455,24 @@ def run_ours(args, rank, world, local_rank):
             "evals_per_launch": evals, "flops_per_eval": FLOPS_PER_EVAL[dom],
             "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, no measured FP32 peak)"}
 
+    # ---- HBM rooflines of the projection, sort and gradient-scatter phases
+    hbm_peak = measured_peaks().get("hbm_gbs")
+    hbm = {}
+    for ph, (per_g, per_pair) in HBM_BYTES.items():
+        if ph not in phases:
+            continue
+        nbytes = per_g * n + per_pair * pairs_b
+        gbs = nbytes / (phases[ph] * 1e-3) / 1e9
+        hbm[ph] = {"bytes": nbytes, "ms": round(phases[ph], 4), "achieved": round(gbs, 1),
+                   "frac": round(gbs / hbm_peak, 4) if hbm_peak else None}
+    if "depth_sort" in phases and "binning" in phases:
+        t_sort = (phases["depth_sort"] + phases["binning"]) * 1e-3
+        amin = SORT_MIN_BYTES[0] * n + SORT_MIN_BYTES[1] * pairs_b
+        hbm["sort_algorithmic_minimum"] = {"bytes": amin, "achieved": round(amin / t_sort / 1e9, 1),
+                                           "frac": round(amin / t_sort / 1e9 / hbm_peak, 4) if hbm_peak else None}
+    hbm["peak_gbs"] = hbm_peak
+    hbm["peak_basis"] = "measured STREAM-style copy (MEASURED_PEAKS.json)"
+
     # ---- batched plain quadric fits: 512 quadrics, 3..40 views, Eq. 1 init + 100 Adam steps
     from paper_2503_02223_gb300 import synth
     fq = synth.batched_quadric_fits(SEED + 1)
@@ -480,7 +512,7 @@ def run_ours(args, rank, world, local_rank):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(kf, m_pairs, args), "clocks": clk,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches, "roofline": roof,
+            "gpu_launches": launches, "roofline": roof, "hbm_phases": hbm,
             "phases_ms": {k: round(v, 4) for k, v in phases.items()}, "phases_from": phase_source,
             "step_form": "dqo_batch_step (1 keyframe) + dqo_quadric_bbox_loss in one CUDA graph, "
                          f"{launches_per_step} kernels per step; tile pairs {pairs_b}, overflow {over_b}",

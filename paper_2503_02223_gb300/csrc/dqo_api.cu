@@ -165,11 +165,6 @@ struct PhaseTimer {
 
 // kernels launched by one radix sort of n keys over end_bit bits, and by one scan
 int64_t scan_launches(int64_t n) { return n > 0 ? 3 : 0; }
-int64_t sort_launches(int64_t n, int end_bit) {
-  if (n <= 1 || end_bit <= 0) return 0;
-  const int passes = (end_bit + kRadixBits - 1) / kRadixBits;
-  return passes * (2 + scan_launches(1));
-}
 
 RasterParams make_params(const dqo_settings* s, const dqo_gaussians* g, const dqo_camera* c) {
   RasterParams rp;
@@ -369,13 +364,11 @@ dqo_status dqo_render_forward(dqo_ctx* c, const dqo_settings* s, const dqo_gauss
     DQO_CUDA(c, cudaEventRecord(c->count_ready, s_));
     DQO_CUDA(c, radix_sort_u32(as<uint32_t>(c->zkey_a), as<uint32_t>(c->zkey_b), as<uint32_t>(c->zval_a),
                                as<uint32_t>(c->zval_b), n, 32, as<uint32_t>(c->depth_hist),
-                               as<uint64_t>(c->depth_scan_scratch), &sel, s_));
-    DQO_CUDA(c, launch_rank_scatter(sel ? as<uint32_t>(c->zval_b) : as<uint32_t>(c->zval_a), n,
-                                    as<uint32_t>(c->rank), s_));
+                               as<uint64_t>(c->depth_scan_scratch), &sel, s_, as<uint32_t>(c->rank)));
   }
   const uint32_t* order = sel ? as<uint32_t>(c->zval_b) : as<uint32_t>(c->zval_a);
   c->order_sel = sel;
-  c->launches += scan_launches(n) + sort_launches(n, 32) + nb_launch;
+  c->launches += scan_launches(n) + radix_sort_launches(n, 32) + (n == 1 ? 1 : 0);
 
   // ---- pair count on the host (the one wait of the forward)
   DQO_CUDA(c, cudaEventSynchronize(c->count_ready));
@@ -399,7 +392,7 @@ dqo_status dqo_render_forward(dqo_ctx* c, const dqo_settings* s, const dqo_gauss
     DQO_CUDA(c, ensure(c->hist, 4 * radix_scratch_words((int64_t)m)));
     DQO_CUDA(c, ensure(c->scan_scratch, 8 * scan_scratch_words(radix_scratch_words((int64_t)m))));
     int psel = 0;
-    c->launches += 2 + sort_launches((int64_t)m, end_bit);
+    c->launches += 2 + radix_sort_launches((int64_t)m, end_bit);
     if (k32) {
       DQO_CUDA(c, launch_emit_pairs_u32(as<ushort4>(c->rect), as<uint32_t>(c->offsets), as<uint32_t>(c->rank), n,
                                         rp.ntx, rank_bits, as<uint32_t>(c->pair_a), s_));
@@ -813,10 +806,9 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
                                       as<uint64_t>(B.scan_scratch), d_total, s_));
     DQO_CUDA(c, radix_sort_u32(as<uint32_t>(B.zkey_a), as<uint32_t>(B.zkey_b), as<uint32_t>(B.zval_a),
                                as<uint32_t>(B.zval_b), N, 32, as<uint32_t>(B.depth_hist),
-                               as<uint64_t>(B.depth_scan_scratch), &sel, s_));
+                               as<uint64_t>(B.depth_scan_scratch), &sel, s_, as<uint32_t>(B.rank)));
     order = sel ? as<uint32_t>(B.zval_b) : as<uint32_t>(B.zval_a);
-    DQO_CUDA(c, launch_rank_scatter(order, N, as<uint32_t>(B.rank), s_));
-    launches += scan_launches(N) + sort_launches(N, 32) + 1;
+    launches += scan_launches(N) + radix_sort_launches(N, 32) + (N == 1 ? 1 : 0);
   }
 
   if (sizing) {
@@ -863,7 +855,7 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
                                          rank_bits, order, as<uint2>(B.ranges), as<uint32_t>(B.list), s_,
                                          d_total));
     }
-    launches += 2 + sort_launches((int64_t)cap, end_bit);
+    launches += 2 + radix_sort_launches((int64_t)cap, end_bit);
   }
 
   // ---- persistent forward + backward over all tiles, losses, projection adjoint

@@ -175,9 +175,12 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, 
 // LSD radix sort of n keys (bits [0, end_bit)), optional uint32 values.  Results land in
 // whichever of the double buffers *sel says (0: *_a, 1: *_b).
 size_t radix_scratch_words(int64_t n);
-cudaError_t radix_sort_u32(uint32_t* keys_a, uint32_t* keys_b, uint32_t* vals_a, uint32_t* vals_b,
-                           int64_t n, int end_bit, uint32_t* hist_scratch, uint64_t* scan_scratch,
-                           int* sel, cudaStream_t s);
+// Stable LSD radix sort (keys, optional uint32 values).  rank (optional, needs values):
+// rank[value] = the value's position in the sorted order, written by the last pass.
+cudaError_t radix_sort_u32(uint32_t* keys_a, uint32_t* keys_b, uint32_t* vals_a, uint32_t* vals_b, int64_t n,
+                           int end_bit, uint32_t* hist_scratch, uint64_t* scan_scratch, int* sel, cudaStream_t s,
+                           uint32_t* rank = nullptr);
+int64_t radix_sort_launches(int64_t n, int end_bit);
 cudaError_t radix_sort_u64(uint64_t* keys_a, uint64_t* keys_b, int64_t n, int end_bit, uint32_t* hist_scratch,
                            uint64_t* scan_scratch, int* sel, cudaStream_t s, const uint64_t* n_dev = nullptr);
 

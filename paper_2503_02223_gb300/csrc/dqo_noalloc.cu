@@ -9,7 +9,7 @@
 // all scratch memory in a fixed array that lives in the library image.
 //
 // The scratch array below is a static __device__ array: every GPU that loads this
-// library holds it (about 12.3 MiB) until the process exits.  In host code its name is
+// library holds it (about 12.5 MiB) until the process exits.  In host code its name is
 // only a host-side stand-in, so the device address is fetched once per device with
 // cudaGetSymbolAddress (done by the first call on that device) and passed to the
 // kernels.  All calls share the one array and it keeps the last call's contents, so
@@ -23,7 +23,9 @@ namespace dqo {
 namespace {
 
 constexpr int64_t kNoAllocMaxKeys = int64_t(1) << 20;
-constexpr int64_t kNoAllocMaxBlocks = (kNoAllocMaxKeys + kSortTile - 1) / kSortTile;
+// radix passes take 2048 or 4096 keys per CTA (fewer per CTA for smaller inputs): bound
+// the CTA count with the smaller tile
+constexpr int64_t kNoAllocMaxBlocks = (kNoAllocMaxKeys + 2047) / 2048;
 // layout: keys_a | keys_b | vals_b (uint32 each) | histograms | scan partials (uint64)
 constexpr size_t kKeysBytes = sizeof(uint32_t) * kNoAllocMaxKeys;
 constexpr size_t kHistWords = kNoAllocMaxBlocks * kRadixBins;
@@ -74,7 +76,8 @@ extern "C" dqo_status dqo_depth_order_noalloc(const uint32_t* depth_keys, int64_
   if (n < 0 || n > kNoAllocMaxKeys) return DQO_EINVAL;
   if (n == 0) return DQO_OK;
   if (!depth_keys || !order) return DQO_EINVAL;
-  if (scan_scratch_words(radix_scratch_words(n)) > kScanWords) return DQO_EINVAL;
+  if (radix_scratch_words(n) > kHistWords || scan_scratch_words(radix_scratch_words(n)) > kScanWords)
+    return DQO_EINVAL;
   unsigned char* base = nullptr;
   if (scratch_address(&base) != cudaSuccess) return DQO_ECUDA;
   uint32_t* keys_a = reinterpret_cast<uint32_t*>(base);

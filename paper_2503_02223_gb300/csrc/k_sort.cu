@@ -131,7 +131,7 @@ __device__ __forceinline__ int64_t live_count(int64_t n, const uint64_t* n_dev) 
   return d < (uint64_t)n ? (int64_t)d : n;
 }
 
-template <typename K>
+template <typename K, int IPT>
 __global__ void __launch_bounds__(kThreads) k_radix_hist(const K* __restrict__ keys, int64_t n_cap,
                                                          const uint64_t* __restrict__ n_dev, int shift,
                                                          uint32_t* __restrict__ hist) {
@@ -139,9 +139,9 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist(const K* __restrict__ k
   __shared__ uint32_t h[kRadixBins];
   h[threadIdx.x] = 0;
   __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  const int64_t base = (int64_t)blockIdx.x * (kThreads * IPT);
 #pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
+  for (int k = 0; k < IPT; ++k) {
     const int64_t i = base + k * kThreads + threadIdx.x;
     if (i < n) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & (kRadixBins - 1)], 1u);
   }
@@ -153,24 +153,26 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist(const K* __restrict__ k
 // and ranks them round by round (32 consecutive keys per round) with __match_any_sync
 // against a warp-private digit counter; warps are then offset by an exclusive scan of
 // their counts per digit, and the CTA by the global digit-major scan.
-template <typename K, bool kVals>
+// (rank, if given: rank[value] = destination, the value's position in the sorted order)
+template <typename K, bool kVals, int IPT>
 __global__ void __launch_bounds__(kThreads) k_radix_scatter(const K* __restrict__ kin, K* __restrict__ kout,
                                                             const uint32_t* __restrict__ vin,
                                                             uint32_t* __restrict__ vout, int64_t n_cap,
                                                             const uint64_t* __restrict__ n_dev, int shift,
-                                                            const uint32_t* __restrict__ offs) {
+                                                            const uint32_t* __restrict__ offs,
+                                                            uint32_t* __restrict__ rank) {
   const int64_t n = live_count(n_cap, n_dev);
   __shared__ uint32_t cnt[kThreads / 32][kRadixBins];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int d = threadIdx.x; d < (kThreads / 32) * kRadixBins; d += kThreads) (&cnt[0][0])[d] = 0;
   __syncthreads();
-  const int64_t wbase = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * 32 * kSortItems;
-  K key[kSortItems];
-  uint32_t val[kSortItems];
-  uint32_t pos[kSortItems];
+  const int64_t wbase = (int64_t)blockIdx.x * (kThreads * IPT) + (int64_t)warp * 32 * IPT;
+  K key[IPT];
+  uint32_t val[IPT];
+  uint32_t pos[IPT];
   const uint32_t lt = lanemask_lt();
 #pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
+  for (int r = 0; r < IPT; ++r) {
     const int64_t i = wbase + r * 32 + lane;
     const bool ok = i < n;
     key[r] = ok ? kin[i] : K(0);
@@ -203,12 +205,15 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const K* __restrict_
   }
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < kSortItems; ++r) {
+  for (int r = 0; r < IPT; ++r) {
     if (pos[r] == 0xFFFFFFFFu) continue;
     const uint32_t d = (uint32_t)(key[r] >> shift) & (kRadixBins - 1);
     const uint32_t dst = offs[(int64_t)d * gridDim.x + blockIdx.x] + cnt[warp][d] + pos[r];
     kout[dst] = key[r];
-    if (kVals) vout[dst] = val[r];
+    if (kVals) {
+      vout[dst] = val[r];
+      if (rank) rank[val[r]] = dst;
+    }
   }
 }
 
@@ -279,25 +284,42 @@ __global__ void __launch_bounds__(kThreads) k_tile_ranges(const K* __restrict__ 
 
 inline unsigned grid_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
 
-template <typename K, bool kVals>
-cudaError_t radix_sort_impl(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n, int end_bit, uint32_t* hist,
-                            uint64_t* scan_scratch, int* sel, cudaStream_t s, const uint64_t* n_dev = nullptr) {
-  *sel = 0;
-  if (n <= 1 || end_bit <= 0) return cudaSuccess;
-  const unsigned nb = grid_for(n, kSortTile);
+// Keys per CTA of a radix pass: 4096, or 2048 when a 4096-key grid would leave SMs idle.
+inline int sort_items(int64_t n) { return n < int64_t(152) * 4096 ? 8 : 16; }
+
+template <typename K, bool kVals, int IPT>
+cudaError_t radix_passes(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n, int end_bit, uint32_t* hist,
+                         uint64_t* scan_scratch, int* sel, cudaStream_t s, const uint64_t* n_dev, uint32_t* rank) {
+  const unsigned nb = grid_for(n, kThreads * IPT);
   const int64_t hn = (int64_t)nb * kRadixBins;
   K* kin = ka; K* kout = kb;
   uint32_t* vin = va; uint32_t* vout = vb;
   for (int shift = 0; shift < end_bit; shift += kRadixBits) {
-    k_radix_hist<K><<<nb, kThreads, 0, s>>>(kin, n, n_dev, shift, hist);
+    const bool last = shift + kRadixBits >= end_bit;
+    k_radix_hist<K, IPT><<<nb, kThreads, 0, s>>>(kin, n, n_dev, shift, hist);
     cudaError_t e = launch_exclusive_scan(hist, hist, hn, scan_scratch, nullptr, s);
     if (e != cudaSuccess) return e;
-    k_radix_scatter<K, kVals><<<nb, kThreads, 0, s>>>(kin, kout, vin, vout, n, n_dev, shift, hist);
+    k_radix_scatter<K, kVals, IPT><<<nb, kThreads, 0, s>>>(kin, kout, vin, vout, n, n_dev, shift, hist,
+                                                           last ? rank : nullptr);
     std::swap(kin, kout);
     std::swap(vin, vout);
     *sel ^= 1;
   }
   return cudaGetLastError();
+}
+
+template <typename K, bool kVals>
+cudaError_t radix_sort_impl(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n, int end_bit, uint32_t* hist,
+                            uint64_t* scan_scratch, int* sel, cudaStream_t s, const uint64_t* n_dev = nullptr,
+                            uint32_t* rank = nullptr) {
+  *sel = 0;
+  if (n <= 1 || end_bit <= 0) {  // already in order: ranks from the values as they stand
+    if (rank && va && n > 0) k_rank_scatter<<<grid_for(n, kThreads), kThreads, 0, s>>>(va, n, rank);
+    return cudaGetLastError();
+  }
+  if (sort_items(n) == 8)
+    return radix_passes<K, kVals, 8>(ka, kb, va, vb, n, end_bit, hist, scan_scratch, sel, s, n_dev, rank);
+  return radix_passes<K, kVals, 16>(ka, kb, va, vb, n, end_bit, hist, scan_scratch, sel, s, n_dev, rank);
 }
 
 }  // namespace
@@ -317,13 +339,23 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, 
   return cudaGetLastError();
 }
 
-size_t radix_scratch_words(int64_t n) { return (size_t)grid_for(n > 0 ? n : 1, kSortTile) * kRadixBins; }
+size_t radix_scratch_words(int64_t n) {
+  const int64_t m = n > 0 ? n : 1;
+  return (size_t)grid_for(m, kThreads * sort_items(m)) * kRadixBins;
+}
+
+int64_t radix_sort_launches(int64_t n, int end_bit) {
+  if (n <= 1 || end_bit <= 0) return 0;
+  const int passes = (end_bit + kRadixBits - 1) / kRadixBits;
+  return (int64_t)passes * 5;  // histogram, 3-kernel scan, scatter
+}
 
 cudaError_t radix_sort_u32(uint32_t* keys_a, uint32_t* keys_b, uint32_t* vals_a, uint32_t* vals_b, int64_t n,
-                           int end_bit, uint32_t* hist_scratch, uint64_t* scan_scratch, int* sel, cudaStream_t s) {
+                           int end_bit, uint32_t* hist_scratch, uint64_t* scan_scratch, int* sel, cudaStream_t s,
+                           uint32_t* rank) {
   if (vals_a)
     return radix_sort_impl<uint32_t, true>(keys_a, keys_b, vals_a, vals_b, n, end_bit, hist_scratch, scan_scratch,
-                                           sel, s);
+                                           sel, s, nullptr, rank);
   return radix_sort_impl<uint32_t, false>(keys_a, keys_b, nullptr, nullptr, n, end_bit, hist_scratch,
                                           scan_scratch, sel, s);
 }
