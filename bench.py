@@ -412,19 +412,78 @@ def run_ours(args, rank, world, local_rank):
     h2d = sum(v.numel() * v.element_size() for d in (pin, pin_t, pin_q) for v in d.values())
     d2h = sum(v.numel() * v.element_size() for v in host_out.values()) + 16 + nq * 40
 
-    def e2e_step():
-        for d, src in ((g, pin), (t, pin_t), (q, pin_q)):
-            for k in d:
-                d[k].copy_(src[k], non_blocking=True)
-        graph.replay()
-        for k in grads:
-            host_out[k].copy_(grads[k], non_blocking=True)
-        host_loss.copy_(out["loss"], non_blocking=True)
-        host_q[0].copy_(qloss, non_blocking=True)
-        host_q[1].copy_(qgrad, non_blocking=True)
+    # two buffer sets, one captured graph each: step i+1's inputs go up on a copy stream
+    # while step i computes, and step i's results come down while step i+1 computes
+    g2 = {k: torch.empty_like(v) for k, v in g.items()}
+    t2 = {k: torch.empty_like(v) for k, v in t.items()}
+    q2 = {k: torch.empty_like(v) for k, v in q.items()}
+    out2 = {k: torch.empty_like(v) for k, v in out.items()}
+    grads2 = {k: torch.empty_like(v) for k, v in grads.items()}
+    qloss2, qgrad2 = torch.empty_like(qloss), torch.empty_like(qgrad)
+    kfb2 = dqo.keyframe(g2, NUM_OBJECTS, cam, t2, out2, grads2)
+    for d, src in ((g2, g), (t2, t), (q2, q)):
+        for k in d:
+            d[k].copy_(src[k])
 
-    for _ in range(3):
-        e2e_step()
+    def graph_body2():
+        for v in grads2.values():
+            v.zero_()
+        dqo.dqo_batch_step(bctx, bst, [kfb2], None, cps, sched)
+        dqo.dqo_quadric_bbox_loss(bctx, q2["params"], q2["P"], q2["q_ptr"], q2["pair_v"], q2["obs_bbox"], qloss2,
+                                  qgrad2)
+
+    dqo.dqo_set_timing(bctx, False)
+    graph2 = torch.cuda.CUDAGraph()
+    cap_stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(cap_stream):
+        with torch.cuda.graph(graph2, stream=cap_stream, capture_error_mode="thread_local"):
+            graph_body2()
+    torch.cuda.current_stream().wait_stream(cap_stream)
+    sets = [dict(g=g, t=t, q=q, grads=grads, out=out, ql=qloss, qg=qgrad, graph=graph),
+            dict(g=g2, t=t2, q=q2, grads=grads2, out=out2, ql=qloss2, qg=qgrad2, graph=graph2)]
+    copy_stream = torch.cuda.Stream(dev)
+    ev_in = [torch.cuda.Event(), torch.cuda.Event()]
+    ev_done = [torch.cuda.Event(), torch.cuda.Event()]
+    ev_out = [torch.cuda.Event(), torch.cuda.Event()]
+    for e in ev_out:
+        e.record(stream)
+
+    def upload(k):
+        sk = sets[k]
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(ev_done[k])     # the set's previous step has finished with it
+            for d, src in ((sk["g"], pin), (sk["t"], pin_t), (sk["q"], pin_q)):
+                for name in d:
+                    d[name].copy_(src[name], non_blocking=True)
+            ev_in[k].record(copy_stream)
+
+    def download(k):
+        sk = sets[k]
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(ev_done[k])
+            for name in sk["grads"]:
+                host_out[name].copy_(sk["grads"][name], non_blocking=True)
+            host_loss.copy_(sk["out"]["loss"], non_blocking=True)
+            host_q[0].copy_(sk["ql"], non_blocking=True)
+            host_q[1].copy_(sk["qg"], non_blocking=True)
+            ev_out[k].record(copy_stream)
+
+    def run_e2e(steps_):
+        for e in ev_done:
+            e.record(stream)
+        upload(0)
+        for i in range(steps_):
+            k = i % 2
+            stream.wait_event(ev_in[k])
+            stream.wait_event(ev_out[k])        # its previous results are on the host
+            sets[k]["graph"].replay()
+            ev_done[k].record(stream)
+            if i + 1 < steps_:
+                upload(1 - k)
+            download(k)
+        stream.wait_stream(copy_stream)
+
+    run_e2e(3)
     torch.cuda.synchronize()
     e_steps = max(10, args.steps // 4)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -432,8 +491,7 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     e0.record(stream)
-    for _ in range(e_steps):
-        e2e_step()
+    run_e2e(e_steps)
     e1.record(stream)
     torch.cuda.synchronize()
     e_ms = e0.elapsed_time(e1)
@@ -511,7 +569,10 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(kf, m_pairs, args), "clocks": clk,
-            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "form": "each step's inputs copied from pinned host memory and its gradients, losses and "
+                            "quadric gradient copied back, overlapped with the neighbouring steps' compute "
+                            "(two buffer sets, a copy stream)"},
             "gpu_launches": launches, "roofline": roof, "hbm_phases": hbm,
             "phases_ms": {k: round(v, 4) for k, v in phases.items()}, "phases_from": phase_source,
             "step_form": "dqo_batch_step (1 keyframe) + dqo_quadric_bbox_loss in one CUDA graph, "
