@@ -250,7 +250,7 @@ DQO_API dqo_status dqo_get_counts(const dqo_ctx* ctx, int64_t* n_pairs, int64_t*
  *   depth_keys [n] (device, read only): the float bit pattern of each Gaussian's positive
  *     camera depth, or 0xFFFFFFFF for a culled Gaussian (any uint32 keys sort correctly);
  *   order [n] (device, written): indices 0..n-1 ordered by (key, index).
- * Scratch memory is a fixed array of about 12.5 MiB inside the library, held by every GPU
+ * Scratch memory is a fixed array of about 14.5 MiB inside the library, held by every GPU
  * that loads the library until the process exits.  n may be 0 .. 1048576 (2^20);
  * larger n returns DQO_EINVAL, as do NULL arrays with n > 0.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) for that device; make that

@@ -31,6 +31,7 @@ struct dqo_ctx {
   // per-tile / per-pixel
   Buf ranges, loss_part, T_final, n_contrib, dl_rgb, dl_depth, dl_ins;
   Buf counters;             // device: [0] uint64 total pairs, [1] uint32 n_visible
+  Buf sort_err;             // device uint32: a radix sort's look-back wait gave up (sticky until read)
   uint64_t* host_counters = nullptr;  // pinned mirror
   cudaEvent_t count_ready = nullptr;  // recorded after the pair count is copied to the host
   // state of the last forward
@@ -248,7 +249,8 @@ dqo_status dqo_create(dqo_ctx** out, int device) {
   dqo_ctx* c = new (std::nothrow) dqo_ctx();
   if (!c) return DQO_ENOMEM;
   c->device = device;
-  if (ensure(c->counters, 64) != cudaSuccess ||
+  if (ensure(c->counters, 64) != cudaSuccess || ensure(c->sort_err, 16) != cudaSuccess ||
+      cudaMemset(c->sort_err.p, 0, 16) != cudaSuccess ||
       cudaMallocHost(reinterpret_cast<void**>(&c->host_counters), 64) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->count_ready, cudaEventDisableTiming) != cudaSuccess) {
     dqo_destroy(c);
@@ -264,7 +266,7 @@ void dqo_destroy(dqo_ctx* c) {
                 &c->zval_b, &c->rank, &c->gid, &c->offsets, &c->grad2d, &c->scan_scratch,
                 &c->depth_scan_scratch, &c->hist, &c->depth_hist,
                 &c->pair_a, &c->pair_b, &c->list, &c->ranges, &c->loss_part, &c->T_final, &c->n_contrib,
-                &c->dl_rgb, &c->dl_depth, &c->dl_ins, &c->counters};
+                &c->dl_rgb, &c->dl_depth, &c->dl_ins, &c->counters, &c->sort_err};
   for (Buf* b : all)
     if (b->p) cudaFree(b->p);
   dqo_ctx::Batch& B = c->b;
@@ -361,10 +363,11 @@ dqo_status dqo_render_forward(dqo_ctx* c, const dqo_settings* s, const dqo_gauss
     DQO_CUDA(c, launch_exclusive_scan(as<uint32_t>(c->ntiles), as<uint32_t>(c->offsets), n,
                                       as<uint64_t>(c->scan_scratch), d_total, s_));
     DQO_CUDA(c, cudaMemcpyAsync(c->host_counters, c->counters.p, 16, cudaMemcpyDeviceToHost, s_));
+    DQO_CUDA(c, cudaMemcpyAsync(c->host_counters + 2, c->sort_err.p, 4, cudaMemcpyDeviceToHost, s_));
     DQO_CUDA(c, cudaEventRecord(c->count_ready, s_));
     DQO_CUDA(c, radix_sort_u32(as<uint32_t>(c->zkey_a), as<uint32_t>(c->zkey_b), as<uint32_t>(c->zval_a),
-                               as<uint32_t>(c->zval_b), n, 32, as<uint32_t>(c->depth_hist),
-                               as<uint64_t>(c->depth_scan_scratch), &sel, s_, as<uint32_t>(c->rank)));
+                               as<uint32_t>(c->zval_b), n, 32, as<uint32_t>(c->depth_hist), &sel, s_,
+                               as<uint32_t>(c->rank), as<uint32_t>(c->sort_err)));
   }
   const uint32_t* order = sel ? as<uint32_t>(c->zval_b) : as<uint32_t>(c->zval_a);
   c->order_sel = sel;
@@ -375,6 +378,10 @@ dqo_status dqo_render_forward(dqo_ctx* c, const dqo_settings* s, const dqo_gauss
   const uint64_t m = c->host_counters[0];
   const uint64_t n_vis = (uint32_t)(c->host_counters[1] & 0xFFFFFFFFu);
   if (m >= (uint64_t(1) << 31)) return DQO_ENOMEM;  // tile ranges are int32 in the blend kernels
+  if (c->host_counters[2] & 0xFFFFFFFFu) {          // an earlier call's sort wait gave up
+    DQO_CUDA(c, cudaMemsetAsync(c->sort_err.p, 0, 4, s_));
+    return DQO_ETIMEOUT;
+  }
 
   // ---- K3-K5 pairs, pair sort, tile ranges
   {
@@ -397,14 +404,14 @@ dqo_status dqo_render_forward(dqo_ctx* c, const dqo_settings* s, const dqo_gauss
       DQO_CUDA(c, launch_emit_pairs_u32(as<ushort4>(c->rect), as<uint32_t>(c->offsets), as<uint32_t>(c->rank), n,
                                         rp.ntx, rank_bits, as<uint32_t>(c->pair_a), s_));
       DQO_CUDA(c, radix_sort_u32(as<uint32_t>(c->pair_a), as<uint32_t>(c->pair_b), nullptr, nullptr, (int64_t)m,
-                                 end_bit, as<uint32_t>(c->hist), as<uint64_t>(c->scan_scratch), &psel, s_));
+                                 end_bit, as<uint32_t>(c->hist), &psel, s_, nullptr, as<uint32_t>(c->sort_err)));
       DQO_CUDA(c, launch_tile_ranges_u32(psel ? as<uint32_t>(c->pair_b) : as<uint32_t>(c->pair_a), (int64_t)m,
                                          rank_bits, order, as<uint2>(c->ranges), as<uint32_t>(c->list), s_));
     } else {
       DQO_CUDA(c, launch_emit_pairs_u64(as<ushort4>(c->rect), as<uint32_t>(c->offsets), as<uint32_t>(c->rank), n,
                                         rp.ntx, rank_bits, as<uint64_t>(c->pair_a), s_));
       DQO_CUDA(c, radix_sort_u64(as<uint64_t>(c->pair_a), as<uint64_t>(c->pair_b), (int64_t)m, end_bit,
-                                 as<uint32_t>(c->hist), as<uint64_t>(c->scan_scratch), &psel, s_));
+                                 as<uint32_t>(c->hist), &psel, s_, nullptr, as<uint32_t>(c->sort_err)));
       DQO_CUDA(c, launch_tile_ranges_u64(psel ? as<uint64_t>(c->pair_b) : as<uint64_t>(c->pair_a), (int64_t)m,
                                          rank_bits, order, as<uint2>(c->ranges), as<uint32_t>(c->list), s_));
     }
@@ -753,6 +760,7 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
   uint32_t* d_nvis = reinterpret_cast<uint32_t*>(d_total + 1);
   uint32_t* d_overflow = d_nvis + 1;
   uint32_t* d_queue = reinterpret_cast<uint32_t*>(d_total + 2);
+  uint32_t* d_sort_err = d_queue + 2;  // byte 24: a sort's look-back wait gave up
   const int rank_bits = bits_for((uint64_t)N);  // static bounds, so the step captures
   const int tile_bits = bits_for(T);
   const int end_bit = rank_bits + tile_bits;
@@ -805,8 +813,8 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
     DQO_CUDA(c, launch_exclusive_scan(as<uint32_t>(B.ntiles), as<uint32_t>(B.offsets), N,
                                       as<uint64_t>(B.scan_scratch), d_total, s_));
     DQO_CUDA(c, radix_sort_u32(as<uint32_t>(B.zkey_a), as<uint32_t>(B.zkey_b), as<uint32_t>(B.zval_a),
-                               as<uint32_t>(B.zval_b), N, 32, as<uint32_t>(B.depth_hist),
-                               as<uint64_t>(B.depth_scan_scratch), &sel, s_, as<uint32_t>(B.rank)));
+                               as<uint32_t>(B.zval_b), N, 32, as<uint32_t>(B.depth_hist), &sel, s_,
+                               as<uint32_t>(B.rank), d_sort_err));
     order = sel ? as<uint32_t>(B.zval_b) : as<uint32_t>(B.zval_a);
     launches += scan_launches(N) + radix_sort_launches(N, 32) + (N == 1 ? 1 : 0);
   }
@@ -844,13 +852,13 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
     int psel = 0;
     if (k32) {
       DQO_CUDA(c, radix_sort_u32_dev(as<uint32_t>(B.pair_a), as<uint32_t>(B.pair_b), (int64_t)cap, end_bit,
-                                     as<uint32_t>(B.hist), as<uint64_t>(B.scan_scratch), &psel, s_, d_total));
+                                     as<uint32_t>(B.hist), &psel, s_, d_total, d_sort_err));
       DQO_CUDA(c, launch_tile_ranges_u32(psel ? as<uint32_t>(B.pair_b) : as<uint32_t>(B.pair_a), (int64_t)cap,
                                          rank_bits, order, as<uint2>(B.ranges), as<uint32_t>(B.list), s_,
                                          d_total));
     } else {
       DQO_CUDA(c, radix_sort_u64(as<uint64_t>(B.pair_a), as<uint64_t>(B.pair_b), (int64_t)cap, end_bit,
-                                 as<uint32_t>(B.hist), as<uint64_t>(B.scan_scratch), &psel, s_, d_total));
+                                 as<uint32_t>(B.hist), &psel, s_, d_total, d_sort_err));
       DQO_CUDA(c, launch_tile_ranges_u64(psel ? as<uint64_t>(B.pair_b) : as<uint64_t>(B.pair_a), (int64_t)cap,
                                          rank_bits, order, as<uint2>(B.ranges), as<uint32_t>(B.list), s_,
                                          d_total));
@@ -952,13 +960,13 @@ dqo_status dqo_batch_check(dqo_ctx* c, uint64_t* pairs, int* overflow) {
   if (!c->b.counters.p) return DQO_OK;
   DQO_CUDA(c, cudaSetDevice(c->device));
   DQO_CUDA(c, cudaDeviceSynchronize());
-  uint64_t h[2] = {0, 0};
-  DQO_CUDA(c, cudaMemcpy(h, c->b.counters.p, 16, cudaMemcpyDeviceToHost));
+  uint64_t h[4] = {0, 0, 0, 0};
+  DQO_CUDA(c, cudaMemcpy(h, c->b.counters.p, 32, cudaMemcpyDeviceToHost));
   const int over = (int)(h[1] >> 32) != 0;
   if (pairs) *pairs = h[0];
   if (overflow) *overflow = over;
   if (over) c->b.capacity = 0;  // the next step sizes again
-  return DQO_OK;
+  return (h[3] & 0xFFFFFFFFu) ? DQO_ETIMEOUT : DQO_OK;
 }
 
 dqo_status dqo_batch_tune(dqo_ctx* c, dqo_settings* s, int32_t nkf, const dqo_keyframe* kfs,

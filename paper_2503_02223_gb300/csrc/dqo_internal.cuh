@@ -11,6 +11,7 @@
 namespace dqo {
 
 constexpr int kThreads = 256;          // CTA size of every rasterizer kernel (one pixel / thread)
+constexpr int kMaxRadixPasses = 8;    // 8-bit digits of up to 64-bit keys
 constexpr int kMaxObjects = 4096;      // object ids per scene handled by the id-map prepass
 constexpr int kMaskWords = kMaxObjects / 32;
 constexpr int kIdSlots = 16;           // per-tile object slots held in shared memory per round
@@ -172,17 +173,23 @@ size_t scan_scratch_words(int64_t n);
 cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint64_t* scratch,
                                   uint64_t* total, cudaStream_t s);
 
-// LSD radix sort of n keys (bits [0, end_bit)), optional uint32 values.  Results land in
-// whichever of the double buffers *sel says (0: *_a, 1: *_b).
+// Stable LSD radix sort of n keys (bits [0, end_bit)), optional uint32 values: one kernel
+// counts all digits, then one kernel per 8-bit digit with decoupled look-back.  Results
+// land in whichever of the double buffers *sel says (0: *_a, 1: *_b).  scratch holds
+// radix_scratch_words(n) uint32 words (histograms, look-back status, counters).  rank
+// (optional, with values): rank[value] = the value's position in the sorted order, written
+// by the last pass.  n_dev (optional): live count on the device, n being the capacity.
+// err (optional): set to 1 if a look-back wait gave up (about a second); NULL keeps the
+// flag inside scratch.
 size_t radix_scratch_words(int64_t n);
-// Stable LSD radix sort (keys, optional uint32 values).  rank (optional, needs values):
-// rank[value] = the value's position in the sorted order, written by the last pass.
-cudaError_t radix_sort_u32(uint32_t* keys_a, uint32_t* keys_b, uint32_t* vals_a, uint32_t* vals_b, int64_t n,
-                           int end_bit, uint32_t* hist_scratch, uint64_t* scan_scratch, int* sel, cudaStream_t s,
-                           uint32_t* rank = nullptr);
 int64_t radix_sort_launches(int64_t n, int end_bit);
-cudaError_t radix_sort_u64(uint64_t* keys_a, uint64_t* keys_b, int64_t n, int end_bit, uint32_t* hist_scratch,
-                           uint64_t* scan_scratch, int* sel, cudaStream_t s, const uint64_t* n_dev = nullptr);
+cudaError_t radix_sort_u32(uint32_t* keys_a, uint32_t* keys_b, uint32_t* vals_a, uint32_t* vals_b, int64_t n,
+                           int end_bit, uint32_t* scratch, int* sel, cudaStream_t s, uint32_t* rank = nullptr,
+                           uint32_t* err = nullptr);
+cudaError_t radix_sort_u64(uint64_t* keys_a, uint64_t* keys_b, int64_t n, int end_bit, uint32_t* scratch, int* sel,
+                           cudaStream_t s, const uint64_t* n_dev = nullptr, uint32_t* err = nullptr);
+cudaError_t radix_sort_u32_dev(uint32_t* keys_a, uint32_t* keys_b, int64_t n, int end_bit, uint32_t* scratch,
+                               int* sel, cudaStream_t s, const uint64_t* n_dev, uint32_t* err = nullptr);
 
 cudaError_t launch_rank_scatter(const uint32_t* order, int64_t n, uint32_t* rank, cudaStream_t s);
 cudaError_t launch_emit_pairs_u32(const ushort4* rect, const uint32_t* offsets, const uint32_t* rank,
@@ -191,8 +198,7 @@ cudaError_t launch_emit_pairs_u64(const ushort4* rect, const uint32_t* offsets, 
                                   int64_t n, int ntx, int rank_bits, uint64_t* keys, cudaStream_t s);
 cudaError_t launch_tile_ranges_u32(const uint32_t* keys, int64_t m, int rank_bits, const uint32_t* order,
                                    uint2* ranges, uint32_t* list, cudaStream_t s, const uint64_t* m_dev = nullptr);
-cudaError_t radix_sort_u32_dev(uint32_t* keys_a, uint32_t* keys_b, int64_t n, int end_bit, uint32_t* hist_scratch,
-                               uint64_t* scan_scratch, int* sel, cudaStream_t s, const uint64_t* n_dev);
+
 cudaError_t launch_tile_ranges_u64(const uint64_t* keys, int64_t m, int rank_bits, const uint32_t* order,
                                    uint2* ranges, uint32_t* list, cudaStream_t s, const uint64_t* m_dev = nullptr);
 

@@ -9,7 +9,7 @@
 // all scratch memory in a fixed array that lives in the library image.
 //
 // The scratch array below is a static __device__ array: every GPU that loads this
-// library holds it (about 12.5 MiB) until the process exits.  In host code its name is
+// library holds it (about 14.5 MiB) until the process exits.  In host code its name is
 // only a host-side stand-in, so the device address is fetched once per device with
 // cudaGetSymbolAddress (done by the first call on that device) and passed to the
 // kernels.  All calls share the one array and it keeps the last call's contents, so
@@ -23,15 +23,14 @@ namespace dqo {
 namespace {
 
 constexpr int64_t kNoAllocMaxKeys = int64_t(1) << 20;
-// radix passes take 2048 or 4096 keys per CTA (fewer per CTA for smaller inputs): bound
-// the CTA count with the smaller tile
-constexpr int64_t kNoAllocMaxBlocks = (kNoAllocMaxKeys + 2047) / 2048;
-// layout: keys_a | keys_b | vals_b (uint32 each) | histograms | scan partials (uint64)
+// radix passes take 2048 keys per CTA below 152 x 4096 keys and 4096 above: at most 305 CTAs
+constexpr int64_t kNoAllocMaxBlocks = 305;
+// layout: keys_a | keys_b | vals_b (uint32 each) | sort scratch (histograms, look-back status
+// of up to 8 passes, counters)
 constexpr size_t kKeysBytes = sizeof(uint32_t) * kNoAllocMaxKeys;
-constexpr size_t kHistWords = kNoAllocMaxBlocks * kRadixBins;
-constexpr size_t kHistBytes = sizeof(uint32_t) * kHistWords;
-constexpr size_t kScanWords = 1024;  // >= scan_scratch_words(kHistWords), checked at run time
-constexpr size_t kScratchBytes = 3 * kKeysBytes + kHistBytes + sizeof(uint64_t) * kScanWords;
+constexpr size_t kHistWords = (size_t)kMaxRadixPasses * kRadixBins * (kNoAllocMaxBlocks + 1) + kMaxRadixPasses + 1;
+constexpr size_t kHistBytes = (sizeof(uint32_t) * kHistWords + 255) / 256 * 256;
+constexpr size_t kScratchBytes = 3 * kKeysBytes + kHistBytes;
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -76,21 +75,19 @@ extern "C" dqo_status dqo_depth_order_noalloc(const uint32_t* depth_keys, int64_
   if (n < 0 || n > kNoAllocMaxKeys) return DQO_EINVAL;
   if (n == 0) return DQO_OK;
   if (!depth_keys || !order) return DQO_EINVAL;
-  if (radix_scratch_words(n) > kHistWords || scan_scratch_words(radix_scratch_words(n)) > kScanWords)
-    return DQO_EINVAL;
+  if (radix_scratch_words(n) > kHistWords) return DQO_EINVAL;
   unsigned char* base = nullptr;
   if (scratch_address(&base) != cudaSuccess) return DQO_ECUDA;
   uint32_t* keys_a = reinterpret_cast<uint32_t*>(base);
   uint32_t* keys_b = reinterpret_cast<uint32_t*>(base + kKeysBytes);
   uint32_t* vals_b = reinterpret_cast<uint32_t*>(base + 2 * kKeysBytes);
   uint32_t* hist = reinterpret_cast<uint32_t*>(base + 3 * kKeysBytes);
-  uint64_t* scan = reinterpret_cast<uint64_t*>(base + 3 * kKeysBytes + kHistBytes);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
   k_seed_order<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(depth_keys, keys_a, order, n);
   if (cudaGetLastError() != cudaSuccess) return DQO_ECUDA;
   // 32-bit keys take an even number of 8-bit passes, so the sorted indices end in `order`
   int sel = 0;
-  if (radix_sort_u32(keys_a, keys_b, order, vals_b, n, 32, hist, scan, &sel, s) != cudaSuccess) return DQO_ECUDA;
+  if (radix_sort_u32(keys_a, keys_b, order, vals_b, n, 32, hist, &sel, s) != cudaSuccess) return DQO_ECUDA;
   if (sel != 0) return DQO_ECUDA;
   return DQO_OK;
 }

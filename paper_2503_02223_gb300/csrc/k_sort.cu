@@ -1,5 +1,5 @@
-// Binning and sorting (K2-K5): exclusive scan, LSD radix sort, pair emission and tile
-// ranges.  The tile lists the blend kernels walk are ordered by (tile, depth, index):
+// Binning and sorting (K2-K5): exclusive scan, LSD radix sort (one kernel per 8-bit digit,
+// decoupled look-back), pair emission and tile ranges.  The tile lists the blend kernels walk are ordered by (tile, depth, index):
 //   1. the Gaussians are radix-sorted once by the bit pattern of their (positive) camera
 //      depth, stable on the index, which gives each visible Gaussian a depth rank;
 //   2. every (tile, Gaussian) pair gets the key (tile << rank_bits) | rank -- unique, so a
@@ -122,7 +122,6 @@ __global__ void __launch_bounds__(kThreads) k_scan_down(const uint32_t* __restri
 
 // ---------------------------------------------------------------- LSD radix sort passes
 
-// Per-CTA digit histogram, stored digit-major: hist[d * nblocks + b].
 // Element count: n, or the smaller of n and *n_dev when the count lives on the device
 // (launches sized for a capacity n).
 __device__ __forceinline__ int64_t live_count(int64_t n, const uint64_t* n_dev) {
@@ -131,42 +130,70 @@ __device__ __forceinline__ int64_t live_count(int64_t n, const uint64_t* n_dev) 
   return d < (uint64_t)n ? (int64_t)d : n;
 }
 
+// Single-pass-per-digit LSD radix sort with decoupled look-back.  One kernel counts the
+// digits of every pass at once into global histograms; then each pass is one kernel whose
+// CTAs take tile indices from an atomic counter (so a CTA's predecessors have all started),
+// rank their keys locally and stably, publish their per-digit counts, and find their
+// global offsets by looking back over their predecessors' published counts: a
+// predecessor's word is an aggregate (its own count) or an inclusive prefix (everything up
+// to and including it), flag and count in one 32-bit word.  Every CTA publishes before it
+// waits, so each wait is on a CTA that is running; the wait still gives up after about a
+// second and raises an error flag instead of hanging.
+
+constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kCountMask = (1u << 30) - 1;
+
 template <typename K, int IPT>
-__global__ void __launch_bounds__(kThreads) k_radix_hist(const K* __restrict__ keys, int64_t n_cap,
-                                                         const uint64_t* __restrict__ n_dev, int shift,
-                                                         uint32_t* __restrict__ hist) {
-  const int64_t n = live_count(n_cap, n_dev);
-  __shared__ uint32_t h[kRadixBins];
-  h[threadIdx.x] = 0;
+__global__ void __launch_bounds__(kThreads) k_onesweep_hist(const K* __restrict__ keys, int64_t n_cap,
+                                                            const uint64_t* __restrict__ n_dev, int passes,
+                                                            uint32_t* __restrict__ ghist) {
+  __shared__ uint32_t h[kMaxRadixPasses][kRadixBins];
+  for (int i = threadIdx.x; i < passes * kRadixBins; i += kThreads) (&h[0][0])[i] = 0;
   __syncthreads();
+  const int64_t n = live_count(n_cap, n_dev);
   const int64_t base = (int64_t)blockIdx.x * (kThreads * IPT);
 #pragma unroll
   for (int k = 0; k < IPT; ++k) {
     const int64_t i = base + k * kThreads + threadIdx.x;
-    if (i < n) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & (kRadixBins - 1)], 1u);
+    if (i < n) {
+      const K key = keys[i];
+      for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(uint32_t)(key >> (p * kRadixBits)) & (kRadixBins - 1)], 1u);
+    }
   }
   __syncthreads();
-  hist[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+  for (int i = threadIdx.x; i < passes * kRadixBins; i += kThreads) {
+    const uint32_t c = (&h[0][0])[i];
+    if (c) atomicAdd(ghist + i, c);
+  }
 }
 
-// Stable scatter of one pass.  Warp w of a CTA owns keys [base + 512 w, base + 512 (w+1))
-// and ranks them round by round (32 consecutive keys per round) with __match_any_sync
-// against a warp-private digit counter; warps are then offset by an exclusive scan of
-// their counts per digit, and the CTA by the global digit-major scan.
-// (rank, if given: rank[value] = destination, the value's position in the sorted order)
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// One pass.  ghist: this pass's 256 global digit counts; status: [tiles][256] words, zero
+// before the pass; counter: this pass's tile counter, zero before the pass.  rank (optional,
+// with values): rank[value] = destination.  err: set to 1 if a look-back wait gave up.
 template <typename K, bool kVals, int IPT>
-__global__ void __launch_bounds__(kThreads) k_radix_scatter(const K* __restrict__ kin, K* __restrict__ kout,
+__global__ void __launch_bounds__(kThreads) k_onesweep_pass(const K* __restrict__ kin, K* __restrict__ kout,
                                                             const uint32_t* __restrict__ vin,
                                                             uint32_t* __restrict__ vout, int64_t n_cap,
                                                             const uint64_t* __restrict__ n_dev, int shift,
-                                                            const uint32_t* __restrict__ offs,
-                                                            uint32_t* __restrict__ rank) {
-  const int64_t n = live_count(n_cap, n_dev);
+                                                            const uint32_t* __restrict__ ghist,
+                                                            uint32_t* __restrict__ status,
+                                                            uint32_t* __restrict__ counter,
+                                                            uint32_t* __restrict__ rank, uint32_t* __restrict__ err) {
   __shared__ uint32_t cnt[kThreads / 32][kRadixBins];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int d = threadIdx.x; d < (kThreads / 32) * kRadixBins; d += kThreads) (&cnt[0][0])[d] = 0;
+  __shared__ uint32_t s_base[kRadixBins];
+  __shared__ uint32_t s_tile;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, t = threadIdx.x;
+  if (t == 0) s_tile = atomicAdd(counter, 1u);
+  for (int d = t; d < (kThreads / 32) * kRadixBins; d += kThreads) (&cnt[0][0])[d] = 0;
   __syncthreads();
-  const int64_t wbase = (int64_t)blockIdx.x * (kThreads * IPT) + (int64_t)warp * 32 * IPT;
+  const uint32_t tile = s_tile;
+  const int64_t n = live_count(n_cap, n_dev);
+  const int64_t wbase = (int64_t)tile * (kThreads * IPT) + (int64_t)warp * 32 * IPT;
   K key[IPT];
   uint32_t val[IPT];
   uint32_t pos[IPT];
@@ -193,22 +220,47 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(const K* __restrict_
     __syncwarp();
   }
   __syncthreads();
-  // exclusive scan over warps per digit (thread t owns digit t)
-  {
-    uint32_t run = 0;
+  // thread t owns digit t: offsets of the warps within the tile, and the tile's count
+  uint32_t total = 0;
 #pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) {
-      const uint32_t c = cnt[w][threadIdx.x];
-      cnt[w][threadIdx.x] = run;
-      run += c;
-    }
+  for (int w = 0; w < kThreads / 32; ++w) {
+    const uint32_t c = cnt[w][t];
+    cnt[w][t] = total;
+    total += c;
   }
+  volatile uint32_t* st = status;
+  st[(int64_t)tile * kRadixBins + t] = (tile == 0 ? kFlagInc : kFlagAgg) | total;
+  // the digit's global start: exclusive scan of the pass's histogram over digits
+  uint32_t gtot;
+  const uint32_t gex = block_exclusive_scan<uint32_t>(ghist[t], gtot);
+  uint32_t excl = 0;
+  if (tile > 0) {
+    int64_t p = (int64_t)tile - 1;
+    const uint64_t t0 = global_ns();
+    uint32_t it = 0;
+    while (p >= 0) {
+      const uint32_t w = st[p * kRadixBins + t];
+      const uint32_t f = w & ~kCountMask;
+      if (f == 0u) {
+        if ((++it & 63u) == 0u && global_ns() - t0 > 1000000000ull) {
+          atomicExch(err, 1u);
+          break;
+        }
+        continue;
+      }
+      excl += w & kCountMask;
+      if (f == kFlagInc) break;
+      --p;
+    }
+    st[(int64_t)tile * kRadixBins + t] = kFlagInc | (excl + total);
+  }
+  s_base[t] = gex + excl;
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < IPT; ++r) {
     if (pos[r] == 0xFFFFFFFFu) continue;
     const uint32_t d = (uint32_t)(key[r] >> shift) & (kRadixBins - 1);
-    const uint32_t dst = offs[(int64_t)d * gridDim.x + blockIdx.x] + cnt[warp][d] + pos[r];
+    const uint32_t dst = s_base[d] + cnt[warp][d] + pos[r];
     kout[dst] = key[r];
     if (kVals) {
       vout[dst] = val[r];
@@ -287,20 +339,31 @@ inline unsigned grid_for(int64_t n, int per) { return (unsigned)((n + per - 1) /
 // Keys per CTA of a radix pass: 4096, or 2048 when a 4096-key grid would leave SMs idle.
 inline int sort_items(int64_t n) { return n < int64_t(152) * 4096 ? 8 : 16; }
 
+// Scratch of one sort (uint32 words): [passes][256] histograms, [passes][tiles][256] status
+// words, [passes] tile counters and an error flag.
+inline size_t onesweep_words(int64_t tiles, int passes) {
+  return (size_t)passes * kRadixBins * (size_t)(tiles + 1) + (size_t)passes + 1;
+}
+
 template <typename K, bool kVals, int IPT>
-cudaError_t radix_passes(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n, int end_bit, uint32_t* hist,
-                         uint64_t* scan_scratch, int* sel, cudaStream_t s, const uint64_t* n_dev, uint32_t* rank) {
+cudaError_t radix_passes(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n, int end_bit, uint32_t* scratch,
+                         int* sel, cudaStream_t s, const uint64_t* n_dev, uint32_t* rank, uint32_t* err_out) {
   const unsigned nb = grid_for(n, kThreads * IPT);
-  const int64_t hn = (int64_t)nb * kRadixBins;
+  const int passes = (end_bit + kRadixBits - 1) / kRadixBits;
+  uint32_t* ghist = scratch;
+  uint32_t* status = ghist + (size_t)passes * kRadixBins;
+  uint32_t* counters = status + (size_t)passes * nb * kRadixBins;
+  uint32_t* err = err_out ? err_out : counters + passes;
+  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * onesweep_words(nb, passes), s);
+  if (e != cudaSuccess) return e;
+  k_onesweep_hist<K, IPT><<<nb, kThreads, 0, s>>>(ka, n, n_dev, passes, ghist);
   K* kin = ka; K* kout = kb;
   uint32_t* vin = va; uint32_t* vout = vb;
-  for (int shift = 0; shift < end_bit; shift += kRadixBits) {
-    const bool last = shift + kRadixBits >= end_bit;
-    k_radix_hist<K, IPT><<<nb, kThreads, 0, s>>>(kin, n, n_dev, shift, hist);
-    cudaError_t e = launch_exclusive_scan(hist, hist, hn, scan_scratch, nullptr, s);
-    if (e != cudaSuccess) return e;
-    k_radix_scatter<K, kVals, IPT><<<nb, kThreads, 0, s>>>(kin, kout, vin, vout, n, n_dev, shift, hist,
-                                                           last ? rank : nullptr);
+  for (int p = 0; p < passes; ++p) {
+    k_onesweep_pass<K, kVals, IPT><<<nb, kThreads, 0, s>>>(kin, kout, vin, vout, n, n_dev, p * kRadixBits,
+                                                           ghist + p * kRadixBins,
+                                                           status + (size_t)p * nb * kRadixBins, counters + p,
+                                                           p == passes - 1 ? rank : nullptr, err);
     std::swap(kin, kout);
     std::swap(vin, vout);
     *sel ^= 1;
@@ -310,16 +373,17 @@ cudaError_t radix_passes(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n, in
 
 template <typename K, bool kVals>
 cudaError_t radix_sort_impl(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n, int end_bit, uint32_t* hist,
-                            uint64_t* scan_scratch, int* sel, cudaStream_t s, const uint64_t* n_dev = nullptr,
-                            uint32_t* rank = nullptr) {
+                            int* sel, cudaStream_t s, const uint64_t* n_dev = nullptr, uint32_t* rank = nullptr,
+                            uint32_t* err = nullptr) {
   *sel = 0;
   if (n <= 1 || end_bit <= 0) {  // already in order: ranks from the values as they stand
     if (rank && va && n > 0) k_rank_scatter<<<grid_for(n, kThreads), kThreads, 0, s>>>(va, n, rank);
     return cudaGetLastError();
   }
+  if (end_bit > kMaxRadixPasses * kRadixBits) return cudaErrorInvalidValue;
   if (sort_items(n) == 8)
-    return radix_passes<K, kVals, 8>(ka, kb, va, vb, n, end_bit, hist, scan_scratch, sel, s, n_dev, rank);
-  return radix_passes<K, kVals, 16>(ka, kb, va, vb, n, end_bit, hist, scan_scratch, sel, s, n_dev, rank);
+    return radix_passes<K, kVals, 8>(ka, kb, va, vb, n, end_bit, hist, sel, s, n_dev, rank, err);
+  return radix_passes<K, kVals, 16>(ka, kb, va, vb, n, end_bit, hist, sel, s, n_dev, rank, err);
 }
 
 }  // namespace
@@ -341,29 +405,27 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, 
 
 size_t radix_scratch_words(int64_t n) {
   const int64_t m = n > 0 ? n : 1;
-  return (size_t)grid_for(m, kThreads * sort_items(m)) * kRadixBins;
+  return onesweep_words(grid_for(m, kThreads * sort_items(m)), kMaxRadixPasses);
 }
 
 int64_t radix_sort_launches(int64_t n, int end_bit) {
   if (n <= 1 || end_bit <= 0) return 0;
-  const int passes = (end_bit + kRadixBits - 1) / kRadixBits;
-  return (int64_t)passes * 5;  // histogram, 3-kernel scan, scatter
+  return 1 + (end_bit + kRadixBits - 1) / kRadixBits;  // histograms, one kernel per pass
 }
 
 cudaError_t radix_sort_u32(uint32_t* keys_a, uint32_t* keys_b, uint32_t* vals_a, uint32_t* vals_b, int64_t n,
-                           int end_bit, uint32_t* hist_scratch, uint64_t* scan_scratch, int* sel, cudaStream_t s,
-                           uint32_t* rank) {
+                           int end_bit, uint32_t* scratch, int* sel, cudaStream_t s, uint32_t* rank, uint32_t* err) {
   if (vals_a)
-    return radix_sort_impl<uint32_t, true>(keys_a, keys_b, vals_a, vals_b, n, end_bit, hist_scratch, scan_scratch,
-                                           sel, s, nullptr, rank);
-  return radix_sort_impl<uint32_t, false>(keys_a, keys_b, nullptr, nullptr, n, end_bit, hist_scratch,
-                                          scan_scratch, sel, s);
+    return radix_sort_impl<uint32_t, true>(keys_a, keys_b, vals_a, vals_b, n, end_bit, scratch, sel, s, nullptr,
+                                           rank, err);
+  return radix_sort_impl<uint32_t, false>(keys_a, keys_b, nullptr, nullptr, n, end_bit, scratch, sel, s, nullptr,
+                                          nullptr, err);
 }
 
-cudaError_t radix_sort_u64(uint64_t* keys_a, uint64_t* keys_b, int64_t n, int end_bit, uint32_t* hist_scratch,
-                           uint64_t* scan_scratch, int* sel, cudaStream_t s, const uint64_t* n_dev) {
-  return radix_sort_impl<uint64_t, false>(keys_a, keys_b, nullptr, nullptr, n, end_bit, hist_scratch,
-                                          scan_scratch, sel, s, n_dev);
+cudaError_t radix_sort_u64(uint64_t* keys_a, uint64_t* keys_b, int64_t n, int end_bit, uint32_t* scratch, int* sel,
+                           cudaStream_t s, const uint64_t* n_dev, uint32_t* err) {
+  return radix_sort_impl<uint64_t, false>(keys_a, keys_b, nullptr, nullptr, n, end_bit, scratch, sel, s, n_dev,
+                                          nullptr, err);
 }
 
 cudaError_t launch_rank_scatter(const uint32_t* order, int64_t n, uint32_t* rank, cudaStream_t s) {
@@ -416,10 +478,10 @@ cudaError_t launch_emit_pairs_batch(const EmitTable& t, int nkf, int64_t max_n, 
   return cudaGetLastError();
 }
 
-cudaError_t radix_sort_u32_dev(uint32_t* keys_a, uint32_t* keys_b, int64_t n, int end_bit, uint32_t* hist_scratch,
-                               uint64_t* scan_scratch, int* sel, cudaStream_t s, const uint64_t* n_dev) {
-  return radix_sort_impl<uint32_t, false>(keys_a, keys_b, nullptr, nullptr, n, end_bit, hist_scratch,
-                                          scan_scratch, sel, s, n_dev);
+cudaError_t radix_sort_u32_dev(uint32_t* keys_a, uint32_t* keys_b, int64_t n, int end_bit, uint32_t* scratch,
+                               int* sel, cudaStream_t s, const uint64_t* n_dev, uint32_t* err) {
+  return radix_sort_impl<uint32_t, false>(keys_a, keys_b, nullptr, nullptr, n, end_bit, scratch, sel, s, n_dev,
+                                          nullptr, err);
 }
 
 }  // namespace dqo
