@@ -165,7 +165,7 @@ struct PhaseTimer {
 };
 
 // kernels launched by one radix sort of n keys over end_bit bits, and by one scan
-int64_t scan_launches(int64_t n) { return n > 0 ? 3 : 0; }
+int64_t scan_launches(int64_t n) { return n > 0 ? 1 : 0; }
 
 RasterParams make_params(const dqo_settings* s, const dqo_gaussians* g, const dqo_camera* c) {
   RasterParams rp;
@@ -361,7 +361,7 @@ dqo_status dqo_render_forward(dqo_ctx* c, const dqo_settings* s, const dqo_gauss
   {
     PhaseTimer pt(c, DQO_PHASE_DEPTH_SORT, s_);
     DQO_CUDA(c, launch_exclusive_scan(as<uint32_t>(c->ntiles), as<uint32_t>(c->offsets), n,
-                                      as<uint64_t>(c->scan_scratch), d_total, s_));
+                                      as<uint64_t>(c->scan_scratch), d_total, s_, as<uint32_t>(c->sort_err)));
     DQO_CUDA(c, cudaMemcpyAsync(c->host_counters, c->counters.p, 16, cudaMemcpyDeviceToHost, s_));
     DQO_CUDA(c, cudaMemcpyAsync(c->host_counters + 2, c->sort_err.p, 4, cudaMemcpyDeviceToHost, s_));
     DQO_CUDA(c, cudaEventRecord(c->count_ready, s_));
@@ -811,7 +811,7 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
   {
     PhaseTimer timer(c, DQO_PHASE_DEPTH_SORT, s_);
     DQO_CUDA(c, launch_exclusive_scan(as<uint32_t>(B.ntiles), as<uint32_t>(B.offsets), N,
-                                      as<uint64_t>(B.scan_scratch), d_total, s_));
+                                      as<uint64_t>(B.scan_scratch), d_total, s_, d_sort_err));
     DQO_CUDA(c, radix_sort_u32(as<uint32_t>(B.zkey_a), as<uint32_t>(B.zkey_b), as<uint32_t>(B.zval_a),
                                as<uint32_t>(B.zval_b), N, 32, as<uint32_t>(B.depth_hist), &sel, s_,
                                as<uint32_t>(B.rank), d_sort_err));

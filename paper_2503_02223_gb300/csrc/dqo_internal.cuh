@@ -167,11 +167,12 @@ cudaError_t launch_preprocess_batch(const PreTable& t, int nkf, int64_t max_n, c
                                     cudaStream_t s);
 cudaError_t launch_preprocess_backward_batch(const PreBwdTable& t, int nkf, int64_t max_n, cudaStream_t s);
 
-// Exclusive scan of n uint32 values; total (uint64) written to *total.  scratch must
-// hold scan_scratch_words(n) uint64 words.
+// Exclusive scan of n uint32 values (one kernel, decoupled look-back); total (uint64)
+// written to *total.  scratch must hold scan_scratch_words(n) uint64 words.  err
+// (optional): set to 1 if a look-back wait gave up.
 size_t scan_scratch_words(int64_t n);
 cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint64_t* scratch,
-                                  uint64_t* total, cudaStream_t s);
+                                  uint64_t* total, cudaStream_t s, uint32_t* err = nullptr);
 
 // Stable LSD radix sort of n keys (bits [0, end_bit)), optional uint32 values: one kernel
 // counts all digits, then one kernel per 8-bit digit with decoupled look-back.  Results

@@ -46,77 +46,84 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T& total) {
   return ex;
 }
 
-// ---------------------------------------------------------------- exclusive scan (3 phases)
+__device__ __forceinline__ uint64_t scan_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
-__global__ void __launch_bounds__(kThreads) k_scan_reduce(const uint32_t* __restrict__ in, int64_t n,
-                                                          uint64_t* __restrict__ partial) {
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
-  uint64_t acc = 0;
+// Single-pass exclusive scan with decoupled look-back: CTAs take tiles of 4096 values from
+// an atomic counter, scan their tile, publish its sum (64-bit word: 2 flag bits, 62 value
+// bits) and add their predecessors' published sums back to the first inclusive prefix;
+// the last tile writes the total.  Waits give up after about a second (err).
+constexpr uint64_t kScanAgg = 1ull << 62, kScanInc = 2ull << 62, kScanMask = (1ull << 62) - 1;
+
+__global__ void __launch_bounds__(kThreads) k_scan_lookback(const uint32_t* __restrict__ in,
+                                                            uint32_t* __restrict__ out, int64_t n,
+                                                            uint64_t* __restrict__ status,
+                                                            uint32_t* __restrict__ counter,
+                                                            uint32_t* __restrict__ err, uint64_t* __restrict__ total) {
+  __shared__ uint32_t tile_s[kSortTile];
+  __shared__ uint32_t s_tile;
+  __shared__ uint64_t s_prefix;
+  if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const int64_t base = (int64_t)tile * kSortTile;
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
     const int64_t i = base + k * kThreads + threadIdx.x;
-    if (i < n) acc += in[i];
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-  __shared__ uint64_t ws[kThreads / 32];
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint64_t t = 0;
-    for (int w = 0; w < kThreads / 32; ++w) t += ws[w];
-    partial[blockIdx.x] = t;
-  }
-}
-
-// Single CTA: exclusive scan of the per-CTA partials in place; writes the grand total.
-__global__ void __launch_bounds__(kThreads) k_scan_partials(uint64_t* __restrict__ partial, int64_t nb,
-                                                            uint64_t* __restrict__ total) {
-  __shared__ uint64_t carry;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (int64_t c = 0; c < nb; c += kThreads) {
-    const int64_t i = c + threadIdx.x;
-    const uint64_t v = i < nb ? partial[i] : 0;
-    uint64_t tot;
-    const uint64_t ex = block_exclusive_scan<uint64_t>(v, tot);
-    if (i < nb) partial[i] = carry + ex;
-    __syncthreads();
-    if (threadIdx.x == 0) carry += tot;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0 && total) *total = carry;
-}
-
-__global__ void __launch_bounds__(kThreads) k_scan_down(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
-                                                        int64_t n, const uint64_t* __restrict__ partial) {
-  __shared__ uint32_t tile[kSortTile];
-  const int64_t base = (int64_t)blockIdx.x * kSortTile;
-#pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
-    const int64_t i = base + k * kThreads + threadIdx.x;
-    tile[k * kThreads + threadIdx.x] = i < n ? in[i] : 0u;
+    tile_s[k * kThreads + threadIdx.x] = i < n ? in[i] : 0u;
   }
   __syncthreads();
   uint32_t v[kSortItems];
   uint32_t sum = 0;
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
-    v[k] = tile[threadIdx.x * kSortItems + k];
+    v[k] = tile_s[threadIdx.x * kSortItems + k];
     sum += v[k];
   }
   uint32_t tot;
-  uint32_t run = block_exclusive_scan<uint32_t>(sum, tot) + (uint32_t)partial[blockIdx.x];
+  uint32_t run = block_exclusive_scan<uint32_t>(sum, tot);
+  if (threadIdx.x == 0) {
+    volatile uint64_t* st = status;
+    st[tile] = (tile == 0 ? kScanInc : kScanAgg) | (uint64_t)tot;
+    uint64_t excl = 0;
+    if (tile > 0) {
+      int64_t p = (int64_t)tile - 1;
+      const uint64_t t0 = scan_ns();
+      uint32_t it = 0;
+      while (p >= 0) {
+        const uint64_t w = st[p];
+        const uint64_t f = w & ~kScanMask;
+        if (f == 0) {
+          if ((++it & 63u) == 0u && scan_ns() - t0 > 1000000000ull) {
+            atomicExch(err, 1u);
+            break;
+          }
+          continue;
+        }
+        excl += w & kScanMask;
+        if (f == kScanInc) break;
+        --p;
+      }
+      st[tile] = kScanInc | (excl + tot);
+    }
+    s_prefix = excl;
+    if (total && base + kSortTile >= n) *total = excl + tot;
+  }
+  __syncthreads();
+  run += (uint32_t)s_prefix;
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
-    tile[threadIdx.x * kSortItems + k] = run;
+    tile_s[threadIdx.x * kSortItems + k] = run;
     run += v[k];
   }
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
     const int64_t i = base + k * kThreads + threadIdx.x;
-    if (i < n) out[i] = tile[k * kThreads + threadIdx.x];
+    if (i < n) out[i] = tile_s[k * kThreads + threadIdx.x];
   }
 }
 
@@ -276,19 +283,50 @@ __global__ void k_rank_scatter(const uint32_t* __restrict__ order, int64_t n, ui
   if (r < n) rank[order[r]] = (uint32_t)r;
 }
 
+// The warp writes the pairs of its 32 Gaussians together: lane l holds Gaussian l's tile
+// rectangle, first pair offset, pair count (0: none) and rank; one Gaussian at a time, the
+// lanes write its pairs row-major over its rectangle in strided (coalesced) order, so a
+// Gaussian covering many tiles does not leave the rest of its warp idle.
+template <typename K>
+__device__ __forceinline__ void warp_emit(const ushort4 r, const uint64_t o, const uint32_t cnt, const K rk,
+                                          uint32_t tile_off, int ntx, int rank_bits, K* __restrict__ keys) {
+  const int lane = threadIdx.x & 31;
+  uint32_t pending = __ballot_sync(0xFFFFFFFFu, cnt > 0);
+  while (pending) {
+    const int j = __ffs(pending) - 1;
+    pending &= pending - 1;
+    const uint32_t c = __shfl_sync(0xFFFFFFFFu, cnt, j);
+    const uint64_t oj = __shfl_sync(0xFFFFFFFFu, o, j);
+    const uint32_t x0 = __shfl_sync(0xFFFFFFFFu, (uint32_t)r.x, j);
+    const uint32_t y0 = __shfl_sync(0xFFFFFFFFu, (uint32_t)r.y, j);
+    const uint32_t w = __shfl_sync(0xFFFFFFFFu, (uint32_t)(r.z - r.x), j);
+    const K rj = __shfl_sync(0xFFFFFFFFu, rk, j);
+    for (uint32_t k = lane; k < c; k += 32) {
+      const uint32_t ty = y0 + k / w, tx = x0 + k % w;
+      keys[oj + k] = ((K)(tile_off + ty * (uint32_t)ntx + tx) << rank_bits) | rj;
+    }
+  }
+}
+
 template <typename K>
 __global__ void __launch_bounds__(kThreads) k_emit_pairs(const ushort4* __restrict__ rect,
                                                          const uint32_t* __restrict__ offsets,
                                                          const uint32_t* __restrict__ rank, int64_t n, int ntx,
                                                          int rank_bits, K* __restrict__ keys) {
   const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-  if (i >= n) return;
-  const ushort4 r = rect[i];
-  if (r.z <= r.x || r.w <= r.y) return;
-  uint32_t o = offsets[i];
-  const K rk = (K)rank[i];
-  for (int ty = r.y; ty < r.w; ++ty)
-    for (int tx = r.x; tx < r.z; ++tx) keys[o++] = ((K)((uint32_t)ty * ntx + tx) << rank_bits) | rk;
+  ushort4 r = make_ushort4(0, 0, 0, 0);
+  uint64_t o = 0;
+  uint32_t cnt = 0;
+  K rk = 0;
+  if (i < n) {
+    r = rect[i];
+    if (r.z > r.x && r.w > r.y) {
+      o = offsets[i];
+      cnt = (uint32_t)(r.z - r.x) * (uint32_t)(r.w - r.y);
+      rk = (K)rank[i];
+    }
+  }
+  warp_emit<K>(r, o, cnt, rk, 0u, ntx, rank_bits, keys);
 }
 
 // Pairs of a batch of keyframes: Gaussian i of keyframe blockIdx.y (global index
@@ -302,21 +340,26 @@ __global__ void __launch_bounds__(kThreads) k_emit_pairs_batch(const __grid_cons
                                                                uint64_t capacity, K* __restrict__ keys,
                                                                uint32_t* __restrict__ overflow) {
   const EmitKf& kf = t.kf[blockIdx.y];
+  if ((int64_t)blockIdx.x * kThreads >= kf.n) return;  // uniform over the block
   const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-  if (i >= kf.n) return;
-  const int64_t gi = kf.base + i;
-  const ushort4 r = rect[gi];
-  if (r.z <= r.x || r.w <= r.y) return;
-  uint64_t o = offsets[gi];
-  const uint64_t cnt = (uint64_t)(r.z - r.x) * (uint64_t)(r.w - r.y);
-  if (o + cnt > capacity) {
-    atomicExch(overflow, 1u);
-    return;
+  ushort4 r = make_ushort4(0, 0, 0, 0);
+  uint64_t o = 0;
+  uint32_t cnt = 0;
+  K rk = 0;
+  if (i < kf.n) {
+    const int64_t gi = kf.base + i;
+    r = rect[gi];
+    if (r.z > r.x && r.w > r.y) {
+      o = offsets[gi];
+      cnt = (uint32_t)(r.z - r.x) * (uint32_t)(r.w - r.y);
+      rk = (K)rank[gi];
+      if (o + cnt > capacity) {
+        atomicExch(overflow, 1u);
+        cnt = 0;
+      }
+    }
   }
-  const K rk = (K)rank[gi];
-  for (int ty = r.y; ty < r.w; ++ty)
-    for (int tx = r.x; tx < r.z; ++tx)
-      keys[o++] = ((K)(kf.tile_off + (uint32_t)ty * kf.ntx + tx) << rank_bits) | rk;
+  warp_emit<K>(r, o, cnt, rk, kf.tile_off, kf.ntx, rank_bits, keys);
 }
 
 template <typename K>
@@ -388,18 +431,21 @@ cudaError_t radix_sort_impl(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n,
 
 }  // namespace
 
-size_t scan_scratch_words(int64_t n) { return (size_t)grid_for(n > 0 ? n : 1, kSortTile) + 1; }
+// scratch: [tiles] look-back status words, a tile counter and an error flag (uint64 each)
+size_t scan_scratch_words(int64_t n) { return (size_t)grid_for(n > 0 ? n : 1, kSortTile) + 2; }
 
 cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint64_t* scratch, uint64_t* total,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, uint32_t* err) {
   if (n <= 0) {
     if (total) return cudaMemsetAsync(total, 0, sizeof(uint64_t), s);
     return cudaSuccess;
   }
   const unsigned nb = grid_for(n, kSortTile);
-  k_scan_reduce<<<nb, kThreads, 0, s>>>(in, n, scratch);
-  k_scan_partials<<<1, kThreads, 0, s>>>(scratch, nb, total);
-  k_scan_down<<<nb, kThreads, 0, s>>>(in, out, n, scratch);
+  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(uint64_t) * (nb + 2), s);
+  if (e != cudaSuccess) return e;
+  uint32_t* counter = reinterpret_cast<uint32_t*>(scratch + nb);
+  k_scan_lookback<<<nb, kThreads, 0, s>>>(in, out, n, scratch, counter,
+                                          err ? err : reinterpret_cast<uint32_t*>(scratch + nb + 1), total);
   return cudaGetLastError();
 }
 
