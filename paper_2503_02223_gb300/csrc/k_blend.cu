@@ -8,8 +8,8 @@
 //   alpha = min(clamp, o G), skipped if < alpha_min; stop before T (1 - alpha) < t_stop;
 //   w = alpha T: C += w c, D += w z, ins += w if the Gaussian is opaque (or og_filter is
 //   off) and its id equals the pixel's labelled id; W_k += w for the id map.
-// The whole CTA leaves the list once every pixel has stopped (__syncthreads_count);
-// a warp whose pixels have all stopped skips the batch.  Per-object weights live in
+// Each warp walks the list on its own (no barrier inside the walk) and leaves it once
+// all its pixels have stopped.  Per-object weights live in
 // shared memory per tile: the tile's distinct ids are found first and mapped to dense
 // slots, 16 slots per round (extra rounds re-walk the list only for tiles with more
 // than 16 objects).  The loss terms and dL/d(pixel) are computed in the epilogue.
@@ -17,15 +17,42 @@
 // Backward, per pixel, back to front from T_final and n_contrib: T_j = T_{j+1}/(1-a_j),
 // dL/da_j = T_j U_j - R_j / (1 - a_j) with U_j = dC.c_j + dD z_j + dA + dins [j counts]
 // and R_j = sum_{k>j} w_k U_k + T_final dC.bg.  The ten per-Gaussian partials are
-// summed over the warp by a transposing butterfly (16 shuffles), over the CTA with
-// shared-memory atomics, and added to the global per-Gaussian record with vector
-// atomics once per (tile, Gaussian).
+// summed over the warp by a transposing reduction (12 shuffles) and added to the global
+// per-Gaussian record with vector atomics once per (warp, Gaussian); when at most four
+// lanes contribute, each adds its own partials instead.
 #include "dqo_internal.cuh"
 
 namespace dqo {
 namespace {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr uint32_t kOgOut = 1u << 30;          // staged key bit: excluded from ins by the OG filter
+constexpr uint32_t kSlotMask = kOgOut - 1u;    // staged key bits holding the dense slot
+
+// eval_gaussian without branches: the same operations, the skip decision returned
+// instead of taken (outputs are defined either way).
+__device__ __forceinline__ bool eval_terms(const float4& p0, const float4& p1, float px, float py, float alpha_clamp,
+                                           float alpha_min, float& alpha, float& G, float& dx, float& dy) {
+  dx = __fsub_rn(px, p0.x);
+  dy = __fsub_rn(py, p0.y);
+  const float t = __fmaf_rn(p0.w, dy, __fmul_rn(p0.z, dx));
+  const float pw = __fmaf_rn(__fmul_rn(p1.x, dy), dy, __fmul_rn(t, dx));
+  G = ex2_approx(pw);
+  alpha = fminf(alpha_clamp, __fmul_rn(p1.y, G));
+  return !(pw > 0.f) && alpha >= alpha_min;
+}
+
+// alpha of a Gaussian at pixel (px, py), without branches: the same operations as
+// eval_gaussian, with the skip decision returned instead of taken.
+__device__ __forceinline__ bool eval_alpha(const float4& p0, const float4& p1, float px, float py,
+                                           float alpha_clamp, float alpha_min, float& alpha) {
+  const float dx = __fsub_rn(px, p0.x);
+  const float dy = __fsub_rn(py, p0.y);
+  const float t = __fmaf_rn(p0.w, dy, __fmul_rn(p0.z, dx));
+  const float pw = __fmaf_rn(__fmul_rn(p1.x, dy), dy, __fmul_rn(t, dx));
+  alpha = fminf(alpha_clamp, __fmul_rn(p1.y, ex2_approx(pw)));
+  return !(pw > 0.f) && alpha >= alpha_min;
+}
 
 template <int TW>
 __device__ __forceinline__ void pixel_of(int tile_x0, int tile_y0, int& px, int& py, float& wx0, float& wy0) {
@@ -94,7 +121,6 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const Blen
   constexpr int NW = kThreads / 32;
   // per-warp staging of the Gaussians that can reach the warp's pixels
   __shared__ float4 s_q0[NW][32], s_q1[NW][32], s_q2[NW][32];
-  __shared__ int32_t s_pos[NW][32], s_wslot[kId ? NW : 1][32];
   __shared__ uint32_t s_mask[kId ? kMaskWords : 1], s_pref[kId ? kMaskWords : 1];
   __shared__ int32_t s_slot_id[kIdSlots];
   __shared__ float s_W[kId ? kIdSlots : 1][kThreads];
@@ -154,8 +180,6 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const Blen
   float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, ins = 0.f;
   int last = 0;
   bool done = !inside;
-  int cur_slot = -1;
-  float cur_w = 0.f;
   const float fpx = (float)px, fpy = (float)py;
   const uint32_t lt = lanemask_lt();
 
@@ -165,8 +189,26 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const Blen
     if (id == kNoObject) return -1;
     return (int)(s_pref[id >> 5] + __popc(s_mask[id >> 5] & ((1u << (id & 31)) - 1u)));
   };
+  // Staged key of a Gaussian (replaces q1.w): with the id map, its dense slot, with bit 30
+  // set when the OG filter excludes it from ins, all ones without an object; without the
+  // id map, its object id, or all ones when the OG filter excludes it.  ins counts a
+  // Gaussian iff its key equals the pixel's key gt_key.
+  auto key_of = [&](uint32_t idog) -> uint32_t {
+    const bool og_out = cm.og_filter && !(idog >> 31);
+    if (kId) {
+      const int sl = slot_of(idog);
+      return sl < 0 ? 0xFFFFFFFFu : ((uint32_t)sl | (og_out ? kOgOut : 0u));
+    }
+    return og_out ? 0xFFFFFFFFu : (idog & kNoObject);
+  };
+  uint32_t gt_key = gt_match;
+  if (kId && gt_match != 0xFFFFFFFEu)
+    gt_key = (s_mask[gt_match >> 5] >> (gt_match & 31)) & 1u ? (uint32_t)slot_of(gt_match) : 0xFFFFFFFEu;
+  uint32_t cur_key = 0xFFFFFFFFu;
+  float cur_w = 0.f;
   // Stages, in list order, the Gaussians of list chunk [c, c+32) that can reach this warp's
-  // pixels and sit before list position `lim`; returns how many.
+  // pixels and sit before list position `lim`; returns how many.  q1.w holds the key and
+  // q2.w the list position (both consumed at staging otherwise).
   auto stage = [&](int c, int lim) -> int {
     const int i = c + lane;
     bool hit = false;
@@ -181,50 +223,62 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const Blen
     const uint32_t m = __ballot_sync(kFull, hit);
     if (hit) {
       const int k = __popc(m & lt);
+      q1.w = __uint_as_float(key_of(__float_as_uint(q1.w)));
+      q2.w = __int_as_float(i - start);
       s_q0[warp][k] = q0;
       s_q1[warp][k] = q1;
       s_q2[warp][k] = q2;
-      s_pos[warp][k] = i - start;
-      if (kId) s_wslot[warp][k] = slot_of(__float_as_uint(q1.w));
     }
     __syncwarp();
     return __popc(m);
   };
+  // Blends one evaluated Gaussian into the pixel (front to back).
+  auto blend = [&](float alpha, const float4& q1, int h) {
+    const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
+    if (Tn < cm.t_stop) {
+      done = true;
+      return;
+    }
+    const float w = __fmul_rn(alpha, T);
+    const float4 q2 = s_q2[warp][h];
+    C0 = fmaf(w, q2.x, C0);
+    C1 = fmaf(w, q2.y, C1);
+    C2 = fmaf(w, q2.z, C2);
+    D = fmaf(w, q1.z, D);
+    const uint32_t key = __float_as_uint(q1.w);
+    if (key == gt_key) ins += w;
+    if (kId) {
+      if (key == cur_key) {
+        cur_w += w;
+      } else {
+        const uint32_t sl = cur_key & kSlotMask;
+        if (sl < (uint32_t)kIdSlots) s_W[sl][tid] += cur_w;
+        cur_key = key;
+        cur_w = w;
+      }
+    }
+    T = Tn;
+    last = __float_as_int(q2.w) + 1;
+  };
 
-  // ---- front to back, each warp on its own: no block-wide barrier inside the walk
+  // ---- front to back, each warp on its own: no block-wide barrier inside the walk.  Two
+  // staged Gaussians per iteration: their exponentials are independent, only the blending
+  // is sequential.
   for (int c = start; c < end; c += 32) {
     if (__all_sync(kFull, done)) break;
     const int nh = stage(c, end);
-    for (int h = 0; h < nh; ++h) {
+    for (int h = 0; h < nh; h += 2) {
       if (done) continue;
-      const float4 q0 = s_q0[warp][h], q1 = s_q1[warp][h];
-      float alpha, G, dx, dy;
-      if (!eval_gaussian(q0, q1, fpx, fpy, cm.alpha_clamp, cm.alpha_min, alpha, G, dx, dy)) continue;
-      const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
-      if (Tn < cm.t_stop) {
-        done = true;
-        continue;
-      }
-      const float w = __fmul_rn(alpha, T);
-      const float4 q2 = s_q2[warp][h];
-      C0 = fmaf(w, q2.x, C0);
-      C1 = fmaf(w, q2.y, C1);
-      C2 = fmaf(w, q2.z, C2);
-      D = fmaf(w, q1.z, D);
-      const uint32_t idog = __float_as_uint(q1.w);
-      if ((idog & kNoObject) == gt_match && (!cm.og_filter || (idog >> 31))) ins += w;
-      if (kId) {
-        const int slot = s_wslot[warp][h];
-        if (slot == cur_slot) {
-          cur_w += w;
-        } else {
-          if (cur_slot >= 0 && cur_slot < kIdSlots) s_W[cur_slot][tid] += cur_w;
-          cur_slot = slot;
-          cur_w = w;
-        }
-      }
-      T = Tn;
-      last = s_pos[warp][h] + 1;
+      // slot h + 1 <= 31 is inside the staging arrays even when h + 1 == nh (stale data,
+      // masked by hb)
+      const bool hb = h + 1 < nh;
+      const float4 a0 = s_q0[warp][h], a1 = s_q1[warp][h];
+      const float4 b0 = s_q0[warp][h + 1], b1 = s_q1[warp][h + 1];
+      float aA, aB;
+      const bool vA = eval_alpha(a0, a1, fpx, fpy, cm.alpha_clamp, cm.alpha_min, aA);
+      const bool vB = eval_alpha(b0, b1, fpx, fpy, cm.alpha_clamp, cm.alpha_min, aB) && hb;
+      if (vA) blend(aA, a1, h);
+      if (vB && !done) blend(aB, b1, h + 1);
     }
     __syncwarp();
   }
@@ -232,7 +286,7 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const Blen
   // ---- object-id argmax (ties to the smaller id: slots are in ascending id order)
   int32_t best_id = -1;
   if (kId) {
-    if (cur_slot >= 0 && cur_slot < kIdSlots) s_W[cur_slot][tid] += cur_w;
+    if ((cur_key & kSlotMask) < (uint32_t)kIdSlots) s_W[cur_key & kSlotMask][tid] += cur_w;
     float best_w = 0.f;
     const int n0 = min(nslots, kIdSlots);
     for (int s = 0; s < n0; ++s) {
@@ -255,14 +309,14 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const Blen
         for (int c = start; c < start + wlast; c += 32) {
           const int nh = stage(c, start + wlast);
           for (int h = 0; h < nh; ++h) {
-            if (s_pos[warp][h] >= last) continue;
+            if (__float_as_int(s_q2[warp][h].w) >= last) continue;
             float alpha, G, dx, dy;
             if (!eval_gaussian(s_q0[warp][h], s_q1[warp][h], fpx, fpy, cm.alpha_clamp, cm.alpha_min, alpha, G,
                                dx, dy))
               continue;
             const float w = __fmul_rn(alpha, Tr);
             Tr = __fmul_rn(Tr, __fsub_rn(1.f, alpha));
-            const int s = s_wslot[warp][h] - first;
+            const int s = (int)(__float_as_uint(s_q1[warp][h].w) & kSlotMask) - first;
             if (s >= 0 && s < kIdSlots) s_W[s][tid] += w;
           }
           __syncwarp();
@@ -511,38 +565,35 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const Blen
       s_pos[warp][k] = jl;
     }
     __syncwarp();
-    for (int h = __popc(m) - 1; h >= 0; --h) {
+    // Adds one evaluated Gaussian's partials (staged slot h) back to front and sums them
+    // into its gradient record.
+    auto accumulate = [&](bool act, float alpha, float G, float dx, float dy, int h) {
       float v[10];
 #pragma unroll
       for (int k = 0; k < 10; ++k) v[k] = 0.f;
-      bool act = false;
-      if (s_pos[warp][h] < (int)nc) {
-        const float4 p0 = s_q0[warp][h], p1 = s_q1[warp][h];
-        float alpha, G, dx, dy;
-        if (eval_gaussian(p0, p1, fpx, fpy, cm.alpha_clamp, cm.alpha_min, alpha, G, dx, dy)) {
-          act = true;
-          const float inv = __frcp_rn(1.f - alpha);
-          T = T * inv;
-          const float w = alpha * T;
-          const float4 p2 = s_q2[warp][h];
-          const uint32_t idog = __float_as_uint(p1.w);
-          const bool counts = (idog & kNoObject) == gt_match && (!cm.og_filter || (idog >> 31));
-          const float U = gC0 * p2.x + gC1 * p2.y + gC2 * p2.z + gD * p1.z + gA + (counts ? gI : 0.f);
-          const float dalpha = T * U - R * inv;
-          R = fmaf(w, U, R);
-          const bool clamped = __fmul_rn(p1.y, G) > cm.alpha_clamp;
-          const float dpow = clamped ? 0.f : dalpha * alpha;
-          v[0] = dpow * dx;
-          v[1] = dpow * dy;
-          v[2] = v[0] * dx;
-          v[3] = v[0] * dy;
-          v[4] = v[1] * dy;
-          v[5] = clamped ? 0.f : dalpha * G;
-          v[6] = w * gC0;
-          v[7] = w * gC1;
-          v[8] = w * gC2;
-          v[9] = w * gD;
-        }
+      if (act) {
+        const float4 p1 = s_q1[warp][h];
+        const float inv = __frcp_rn(1.f - alpha);
+        T = T * inv;
+        const float w = alpha * T;
+        const float4 p2 = s_q2[warp][h];
+        const uint32_t idog = __float_as_uint(p1.w);
+        const bool counts = (idog & kNoObject) == gt_match && (!cm.og_filter || (idog >> 31));
+        const float U = gC0 * p2.x + gC1 * p2.y + gC2 * p2.z + gD * p1.z + gA + (counts ? gI : 0.f);
+        const float dalpha = T * U - R * inv;
+        R = fmaf(w, U, R);
+        const bool clamped = __fmul_rn(p1.y, G) > cm.alpha_clamp;
+        const float dpow = clamped ? 0.f : dalpha * alpha;
+        v[0] = dpow * dx;
+        v[1] = dpow * dy;
+        v[2] = v[0] * dx;
+        v[3] = v[0] * dy;
+        v[4] = v[1] * dy;
+        v[5] = clamped ? 0.f : dalpha * G;
+        v[6] = w * gC0;
+        v[7] = w * gC1;
+        v[8] = w * gC2;
+        v[9] = w * gD;
       }
       const uint32_t am = __ballot_sync(kFull, act);
       if (am != 0u && __popc(am) <= kFewLanes) {
@@ -566,6 +617,20 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const Blen
           atomicAdd(dst, make_float4(a0, a1, a2, a3));
         }
       }
+    };
+    // two staged Gaussians per iteration (h, then h - 1): their exponentials are
+    // independent; the transmittance and partial sums stay sequential
+    for (int h = __popc(m) - 1; h >= 0; h -= 2) {
+      const int hb = h > 0 ? h - 1 : 0;
+      float aA, GA, dxA, dyA, aB, GB, dxB, dyB;
+      const bool eA =
+          eval_terms(s_q0[warp][h], s_q1[warp][h], fpx, fpy, cm.alpha_clamp, cm.alpha_min, aA, GA, dxA, dyA);
+      const bool eB =
+          eval_terms(s_q0[warp][hb], s_q1[warp][hb], fpx, fpy, cm.alpha_clamp, cm.alpha_min, aB, GB, dxB, dyB);
+      const bool vA = eA && s_pos[warp][h] < (int)nc;
+      const bool vB = eB && h > 0 && s_pos[warp][hb] < (int)nc;
+      accumulate(vA, aA, GA, dxA, dyA, h);
+      if (h > 0) accumulate(vB, aB, GB, dxB, dyB, hb);
     }
     __syncwarp();
   }
