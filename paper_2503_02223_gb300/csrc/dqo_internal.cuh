@@ -31,6 +31,13 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// PTX rcp.approx (relative error within 1 ulp on normal inputs).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Per-pixel evaluation of one projected Gaussian, shared bit-for-bit by the forward and
 // backward blend kernels so both take the same skip / clamp decisions.  p0 = (x, y, a',
 // b'), p1 = (c', opacity, z, id bits) with the conic pre-scaled so that

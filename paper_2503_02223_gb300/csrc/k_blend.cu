@@ -28,6 +28,8 @@ namespace {
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 constexpr uint32_t kOgOut = 1u << 30;          // staged key bit: excluded from ins by the OG filter
 constexpr uint32_t kSlotMask = kOgOut - 1u;    // staged key bits holding the dense slot
+constexpr int kFwdIlp = 2;                     // Gaussians evaluated together in the forward walk
+static_assert(32 % kFwdIlp == 0, "staging holds 32 slots");
 
 // eval_gaussian without branches: the same operations, the skip decision returned
 // instead of taken (outputs are defined either way).
@@ -233,7 +235,7 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const Blen
     return __popc(m);
   };
   // Blends one evaluated Gaussian into the pixel (front to back).
-  auto blend = [&](float alpha, const float4& q1, int h) {
+  auto blend = [&](float alpha, float z, uint32_t key, int h) {
     const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
     if (Tn < cm.t_stop) {
       done = true;
@@ -244,8 +246,7 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const Blen
     C0 = fmaf(w, q2.x, C0);
     C1 = fmaf(w, q2.y, C1);
     C2 = fmaf(w, q2.z, C2);
-    D = fmaf(w, q1.z, D);
-    const uint32_t key = __float_as_uint(q1.w);
+    D = fmaf(w, z, D);
     if (key == gt_key) ins += w;
     if (kId) {
       if (key == cur_key) {
@@ -261,24 +262,29 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const Blen
     last = __float_as_int(q2.w) + 1;
   };
 
-  // ---- front to back, each warp on its own: no block-wide barrier inside the walk.  Two
+  // ---- front to back, each warp on its own: no block-wide barrier inside the walk.  kFwdIlp
   // staged Gaussians per iteration: their exponentials are independent, only the blending
   // is sequential.
   for (int c = start; c < end; c += 32) {
     if (__all_sync(kFull, done)) break;
     const int nh = stage(c, end);
-    for (int h = 0; h < nh; h += 2) {
+    for (int h = 0; h < nh; h += kFwdIlp) {
       if (done) continue;
-      // slot h + 1 <= 31 is inside the staging arrays even when h + 1 == nh (stale data,
-      // masked by hb)
-      const bool hb = h + 1 < nh;
-      const float4 a0 = s_q0[warp][h], a1 = s_q1[warp][h];
-      const float4 b0 = s_q0[warp][h + 1], b1 = s_q1[warp][h + 1];
-      float aA, aB;
-      const bool vA = eval_alpha(a0, a1, fpx, fpy, cm.alpha_clamp, cm.alpha_min, aA);
-      const bool vB = eval_alpha(b0, b1, fpx, fpy, cm.alpha_clamp, cm.alpha_min, aB) && hb;
-      if (vA) blend(aA, a1, h);
-      if (vB && !done) blend(aB, b1, h + 1);
+      // slots h .. h + kFwdIlp - 1 <= 31 are inside the staging arrays even past nh
+      // (stale data, masked)
+      float al[kFwdIlp], z[kFwdIlp];
+      uint32_t key[kFwdIlp];
+      bool v[kFwdIlp];
+#pragma unroll
+      for (int u = 0; u < kFwdIlp; ++u) {
+        const float4 q0 = s_q0[warp][h + u], q1 = s_q1[warp][h + u];
+        v[u] = eval_alpha(q0, q1, fpx, fpy, cm.alpha_clamp, cm.alpha_min, al[u]) && h + u < nh;
+        z[u] = q1.z;
+        key[u] = __float_as_uint(q1.w);
+      }
+#pragma unroll
+      for (int u = 0; u < kFwdIlp; ++u)
+        if (v[u] && !done) blend(al[u], z[u], key[u], h + u);
     }
     __syncwarp();
   }
@@ -573,7 +579,7 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const Blen
       for (int k = 0; k < 10; ++k) v[k] = 0.f;
       if (act) {
         const float4 p1 = s_q1[warp][h];
-        const float inv = __frcp_rn(1.f - alpha);
+        const float inv = rcp_approx(1.f - alpha);   // 1 - alpha in [1 - clamp, 1]: no special cases
         T = T * inv;
         const float w = alpha * T;
         const float4 p2 = s_q2[warp][h];
