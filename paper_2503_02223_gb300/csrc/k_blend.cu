@@ -506,7 +506,6 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const Blen
   constexpr int NW = kThreads / 32;
   __shared__ float4 s_q0[NW][32], s_q1[NW][32], s_q2[NW][32];
   __shared__ uint32_t s_g[NW][32];
-  __shared__ int32_t s_pos[NW][32];
 
   const RasterParams& rp = a.rp;
   const int tx = tile % rp.ntx, ty = tile / rp.ntx;
@@ -564,13 +563,19 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const Blen
     const uint32_t m = __ballot_sync(kFull, hit);
     if (hit) {
       const int k = __popc(m & lt);
+      // q1.w becomes the ins key: the object id, or all ones when the OG filter excludes it
+      const uint32_t idog = __float_as_uint(q1.w);
+      q1.w = __uint_as_float(cm.og_filter && !(idog >> 31) ? 0xFFFFFFFFu : (idog & kNoObject));
       s_q0[warp][k] = q0;
       s_q1[warp][k] = q1;
       s_q2[warp][k] = q2;
       s_g[warp][k] = g;
-      s_pos[warp][k] = jl;
     }
     __syncwarp();
+    // staged slots [0, hlim) hold this lane's contributors (list positions below nc): the
+    // slots are in list order and slot k came from chunk lane k's position c + k
+    const int below = (int)nc - c;
+    const int hlim = __popc(m & (below >= 32 ? kFull : (below <= 0 ? 0u : (1u << below) - 1u)));
     // Adds one evaluated Gaussian's partials (staged slot h) back to front and sums them
     // into its gradient record.
     auto accumulate = [&](bool act, float alpha, float G, float dx, float dy, int h) {
@@ -583,8 +588,7 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const Blen
         T = T * inv;
         const float w = alpha * T;
         const float4 p2 = s_q2[warp][h];
-        const uint32_t idog = __float_as_uint(p1.w);
-        const bool counts = (idog & kNoObject) == gt_match && (!cm.og_filter || (idog >> 31));
+        const bool counts = __float_as_uint(p1.w) == gt_match;
         const float U = gC0 * p2.x + gC1 * p2.y + gC2 * p2.z + gD * p1.z + gA + (counts ? gI : 0.f);
         const float dalpha = T * U - R * inv;
         R = fmaf(w, U, R);
@@ -633,8 +637,8 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const Blen
           eval_terms(s_q0[warp][h], s_q1[warp][h], fpx, fpy, cm.alpha_clamp, cm.alpha_min, aA, GA, dxA, dyA);
       const bool eB =
           eval_terms(s_q0[warp][hb], s_q1[warp][hb], fpx, fpy, cm.alpha_clamp, cm.alpha_min, aB, GB, dxB, dyB);
-      const bool vA = eA && s_pos[warp][h] < (int)nc;
-      const bool vB = eB && h > 0 && s_pos[warp][hb] < (int)nc;
+      const bool vA = eA && h < hlim;
+      const bool vB = eB && h > 0 && hb < hlim;
       accumulate(vA, aA, GA, dxA, dyA, h);
       if (h > 0) accumulate(vB, aB, GB, dxB, dyB, hb);
     }
