@@ -18,7 +18,7 @@
 // dL/da_j = T_j U_j - R_j / (1 - a_j) with U_j = dC.c_j + dD z_j + dA + dins [j counts]
 // and R_j = sum_{k>j} w_k U_k + T_final dC.bg.  The ten per-Gaussian partials are
 // summed over the warp by a transposing reduction (12 shuffles) and added to the global
-// per-Gaussian record with vector atomics once per (warp, Gaussian); when at most four
+// per-Gaussian record with vector atomics once per (warp, Gaussian); when at most twelve
 // lanes contribute, each adds its own partials instead.
 #include "dqo_internal.cuh"
 
@@ -498,7 +498,7 @@ __device__ __forceinline__ float warp_transpose_sum10(const float v[10]) {
 
 // Up to this many contributing lanes a (warp, Gaussian) adds its partials with per-lane
 // atomics instead of a warp sum.
-constexpr int kFewLanes = 4;
+constexpr int kFewLanes = 12;
 
 // Backward of one tile (local tile index); warp-autonomous, no block barrier.
 template <int TW>
@@ -647,7 +647,7 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const Blen
 }
 
 template <int TW>
-__global__ void __launch_bounds__(kThreads, 4) k_blend_backward(BlendBwdArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) k_blend_backward(BlendBwdArgs a) {
   const BlendCommon cm{a.p0, a.p1, a.p2, nullptr, a.list, a.grad2d, a.rp.alpha_clamp, a.rp.alpha_min, 0.f,
                        a.rp.og_filter};
   blend_bwd_tile<TW>(a, cm, (int)blockIdx.x);
