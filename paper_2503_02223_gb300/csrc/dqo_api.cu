@@ -30,6 +30,7 @@ struct dqo_ctx {
   Buf scan_scratch, depth_scan_scratch, hist, depth_hist, pair_a, pair_b, list;
   // per-tile / per-pixel
   Buf ranges, loss_part, T_final, n_contrib, dl_rgb, dl_depth, dl_ins;
+  Buf tile_sched;           // [3][tiles] uint32: forward tile order, tile costs, backward tile order
   Buf counters;             // device: [0] uint64 total pairs, [1] uint32 n_visible
   Buf sort_err;             // device uint32: a radix sort's look-back wait gave up (sticky until read)
   uint64_t* host_counters = nullptr;  // pinned mirror
@@ -51,7 +52,7 @@ struct dqo_ctx {
   struct Batch {
     Buf p0, p1, p2, rect, ntiles, zkey_a, zkey_b, zval_a, zval_b, rank, gid, offsets, grad2d;
     Buf scan_scratch, depth_scan_scratch, depth_hist, hist, pair_a, pair_b, list, ranges, loss_part;
-    Buf T_final, n_contrib, dl_rgb, dl_depth, dl_ins, counters;
+    Buf T_final, n_contrib, dl_rgb, dl_depth, dl_ins, counters, tile_sched;
     uint64_t* host = nullptr;  // pinned: pair count of a sizing call
     std::vector<int64_t> sig;  // layout of the last sizing call
     uint64_t capacity = 0;
@@ -266,14 +267,14 @@ void dqo_destroy(dqo_ctx* c) {
                 &c->zval_b, &c->rank, &c->gid, &c->offsets, &c->grad2d, &c->scan_scratch,
                 &c->depth_scan_scratch, &c->hist, &c->depth_hist,
                 &c->pair_a, &c->pair_b, &c->list, &c->ranges, &c->loss_part, &c->T_final, &c->n_contrib,
-                &c->dl_rgb, &c->dl_depth, &c->dl_ins, &c->counters, &c->sort_err};
+                &c->dl_rgb, &c->dl_depth, &c->dl_ins, &c->counters, &c->sort_err, &c->tile_sched};
   for (Buf* b : all)
     if (b->p) cudaFree(b->p);
   dqo_ctx::Batch& B = c->b;
   Buf* ball[] = {&B.p0, &B.p1, &B.p2, &B.rect, &B.ntiles, &B.zkey_a, &B.zkey_b, &B.zval_a, &B.zval_b, &B.rank,
                  &B.gid, &B.offsets, &B.grad2d, &B.scan_scratch, &B.depth_scan_scratch, &B.depth_hist, &B.hist,
                  &B.pair_a, &B.pair_b, &B.list, &B.ranges, &B.loss_part, &B.T_final, &B.n_contrib, &B.dl_rgb,
-                 &B.dl_depth, &B.dl_ins, &B.counters, &c->mlp_work};
+                 &B.dl_depth, &B.dl_ins, &B.counters, &B.tile_sched, &c->mlp_work};
   for (Buf* b : ball)
     if (b->p) cudaFree(b->p);
   if (B.host) cudaFreeHost(B.host);
@@ -321,6 +322,7 @@ dqo_status dqo_render_forward(dqo_ctx* c, const dqo_settings* s, const dqo_gauss
   DQO_CUDA(c, ensure(c->gid, 4 * n));
   DQO_CUDA(c, ensure(c->offsets, 4 * n));
   DQO_CUDA(c, ensure(c->ranges, 8 * (size_t)tiles));
+  DQO_CUDA(c, ensure(c->tile_sched, 12 * (size_t)tiles));
   DQO_CUDA(c, ensure(c->loss_part, 12 * (size_t)tiles));
   DQO_CUDA(c, ensure(c->T_final, 4 * HW));
   DQO_CUDA(c, ensure(c->n_contrib, 4 * HW));
@@ -444,14 +446,17 @@ dqo_status dqo_render_forward(dqo_ctx* c, const dqo_settings* s, const dqo_gauss
   a.dl_ins = t ? as<float>(c->dl_ins) : nullptr;
   a.loss_part = as<float>(c->loss_part);
   a.o_mask = out->update_mask;
+  a.tile_order = as<uint32_t>(c->tile_sched);
+  a.tile_cost = as<uint32_t>(c->tile_sched) + tiles;
   {
     PhaseTimer pt(c, DQO_PHASE_BLEND_FWD, s_);
+    DQO_CUDA(c, launch_tile_schedule(a.ranges, nullptr, tiles, const_cast<uint32_t*>(a.tile_order), s_));
     DQO_CUDA(c, launch_blend_forward(a, out->id_map != nullptr, s_));
     if (out->loss)
       DQO_CUDA(c, launch_loss_reduce(as<float>(c->loss_part), tiles, rp.lambda_ins,
                                      (float)(1.0 / ((double)rp.W * (double)rp.H)), out->loss, s_));
   }
-  c->launches += (tiles > 0 ? 1 : 0) + (out->loss ? 1 : 0);
+  c->launches += (tiles > 0 ? 2 : 0) + (out->loss ? 1 : 0);
 
   c->have_fwd = true;
   c->fwd_dl = t != nullptr;
@@ -509,11 +514,15 @@ dqo_status dqo_render_backward(dqo_ctx* c, const dqo_settings* s, const dqo_gaus
     a.g_ins = as<float>(c->dl_ins);
   }
   a.grad2d = as<float>(c->grad2d);
+  const int tiles = c->ntx * c->nty;
+  a.tile_order = as<uint32_t>(c->tile_sched) + 2 * (size_t)tiles;
   {
     PhaseTimer pt(c, DQO_PHASE_BLEND_BWD, s_);
+    DQO_CUDA(c, launch_tile_schedule(nullptr, as<uint32_t>(c->tile_sched) + tiles, tiles,
+                                     const_cast<uint32_t*>(a.tile_order), s_));
     DQO_CUDA(c, launch_blend_backward(a, s_));
   }
-  c->launches += (c->ntx * c->nty > 0) ? 1 : 0;
+  c->launches += tiles > 0 ? 2 : 0;
 
   PreBwdArgs b;
   b.rp = rp;
@@ -740,6 +749,7 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
     DQO_CUDA(c, ensure(B.offsets, 4 * N));
     DQO_CUDA(c, ensure(B.grad2d, 48 * N));
     DQO_CUDA(c, ensure(B.ranges, 8 * T));
+    DQO_CUDA(c, ensure(B.tile_sched, 12 * T));
     DQO_CUDA(c, ensure(B.loss_part, 12 * T));
     DQO_CUDA(c, ensure(B.T_final, 4 * P));
     DQO_CUDA(c, ensure(B.n_contrib, 4 * P));
@@ -897,6 +907,8 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
       a.dl_ins = as<float>(B.dl_ins) + po;
       a.loss_part = as<float>(B.loss_part) + 3 * (int64_t)toff[k];
       a.o_mask = kf.out.update_mask;
+      a.tile_order = as<uint32_t>(B.tile_sched) + toff[k];
+      a.tile_cost = as<uint32_t>(B.tile_sched) + T + toff[k];
       BlendBwdArgs& bb = tt.b[k];
       bb.rp = rp[k];
       bb.p0 = pb.p0;
@@ -912,6 +924,7 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
       bb.g_alpha = nullptr;
       bb.g_ins = a.dl_ins;
       bb.grad2d = as<float>(B.grad2d);
+      bb.tile_order = as<uint32_t>(B.tile_sched) + 2 * T + toff[k];
       tt.tile_off[k] = toff[k];
       lt.kf[k].part = a.loss_part;
       lt.kf[k].tiles = (int)(toff[k + 1] - toff[k]);
@@ -946,7 +959,7 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
       PhaseTimer timer(c, DQO_PHASE_PROJECT_BWD, s_);
       DQO_CUDA(c, launch_preprocess_backward_batch(bt, nkf, max_n, s_));
     }
-    launches += 2 + (schedule == 0 ? 1 : schedule == 1 ? 2 : 2 * nkf);
+    launches += 2 + (schedule == 0 ? 1 : schedule == 1 ? 2 : 2 * nkf + 2);
   }
   if (run_fits) DQO_CUDA(c, cudaStreamWaitEvent(s_, B.join, 0));
   c->launches += launches;

@@ -111,6 +111,8 @@ struct BlendFwdArgs {
   float* dl_ins;     // saved dL/dins[H*W]
   float* loss_part;  // [T*3] per-tile loss sums
   uint8_t* o_mask;   // [H*W] Eq. 11 update masks (with targets)
+  const uint32_t* tile_order = nullptr;  // [T] block b blends tile tile_order[b] (null: tile b)
+  uint32_t* tile_cost = nullptr;         // [T] out: longest blended prefix of the tile's pixels
 };
 
 struct BlendBwdArgs {
@@ -128,6 +130,7 @@ struct BlendBwdArgs {
   const float* g_alpha;
   const float* g_ins;
   float* grad2d;     // [n*12] moment records (accumulated with atomics)
+  const uint32_t* tile_order = nullptr;  // [T] block b walks tile tile_order[b] (null: tile b)
 };
 
 struct PreBwdArgs {
@@ -227,6 +230,11 @@ cudaError_t launch_emit_pairs_batch(const EmitTable& t, int nkf, int64_t max_n, 
                                     void* keys, bool k32, uint32_t* overflow, cudaStream_t s);
 
 cudaError_t launch_blend_forward(const BlendFwdArgs& a, bool with_id, cudaStream_t s);
+// Tile schedule: order[0..tiles) lists the tiles by decreasing cost (cost[t], or the
+// tile's list length ranges[t].y - ranges[t].x when cost is null), on a log scale of four
+// buckets per octave; tiles of one bucket come in no fixed order.  One CTA.
+cudaError_t launch_tile_schedule(const uint2* ranges, const uint32_t* cost, int tiles, uint32_t* order,
+                                 cudaStream_t s);
 cudaError_t launch_loss_reduce(const float* part, int tiles, float lambda_ins, float scale, float* loss,
                                cudaStream_t s);
 cudaError_t launch_blend_backward(const BlendBwdArgs& a, cudaStream_t s);

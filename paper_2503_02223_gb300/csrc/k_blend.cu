@@ -127,6 +127,7 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const Blen
   __shared__ int32_t s_slot_id[kIdSlots];
   __shared__ float s_W[kId ? kIdSlots : 1][kThreads];
   __shared__ float s_red[3][kThreads / 32];
+  __shared__ uint32_t s_wlast[kThreads / 32];
   __shared__ uint32_t s_nslots;
 
   const RasterParams& rp = a.rp;
@@ -395,18 +396,28 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const Blen
       l_d += __shfl_xor_sync(0xFFFFFFFFu, l_d, o);
       l_i += __shfl_xor_sync(0xFFFFFFFFu, l_i, o);
     }
-    const int lane = tid & 31, warp = tid >> 5;
     if (lane == 0) {
       s_red[0][warp] = l_rgb;
       s_red[1][warp] = l_d;
       s_red[2][warp] = l_i;
     }
+  }
+  // the tile's backward cost: its longest blended prefix
+  const uint32_t wlast = __reduce_max_sync(kFull, (uint32_t)last);
+  if (lane == 0) s_wlast[warp] = wlast;
+  if (a.t_gt || a.tile_cost) {
     __syncthreads();
-    if (tid < 3) {
+    if (a.t_gt && tid < 3) {
       float s = 0.f;
 #pragma unroll
       for (int w = 0; w < kThreads / 32; ++w) s += s_red[tid][w];
       a.loss_part[3 * tile + tid] = s;
+    }
+    if (a.tile_cost && tid == 32) {
+      uint32_t m = 0;
+#pragma unroll
+      for (int w = 0; w < kThreads / 32; ++w) m = max(m, s_wlast[w]);
+      a.tile_cost[tile] = m;
     }
   }
 }
@@ -415,7 +426,7 @@ template <int TW, bool kId>
 __global__ void __launch_bounds__(kThreads) k_blend_forward(BlendFwdArgs a) {
   const BlendCommon cm{a.p0, a.p1, a.p2, a.gid, a.list, nullptr, a.rp.alpha_clamp, a.rp.alpha_min, a.rp.t_stop,
                        a.rp.og_filter};
-  blend_fwd_tile<TW, kId>(a, cm, (int)blockIdx.x);
+  blend_fwd_tile<TW, kId>(a, cm, a.tile_order ? (int)a.tile_order[blockIdx.x] : (int)blockIdx.x);
 }
 
 // Deterministic sum of the per-tile loss partials in double, scaled by 1/(HW).
@@ -453,6 +464,68 @@ __global__ void k_loss_reduce(const float* __restrict__ part, int tiles, float l
 __global__ void k_loss_reduce_batch(const __grid_constant__ LossTable t) {
   const LossKf& k = t.kf[blockIdx.x];
   if (k.loss) loss_reduce(k.part, k.tiles, k.lambda_ins, k.scale, k.loss);
+}
+
+// ---------------------------------------------------------------- tile schedule
+// Tiles differ in cost by orders of magnitude (empty sky against cluttered objects), and a
+// tile's CTA lives as long as its slowest warp: launched in raster order, the last wave is
+// a few heavy tiles on otherwise idle SMs.  The blend kernels therefore take their tiles
+// heaviest first (the hardware hands out CTAs roughly in block order): the forward by
+// list length, the backward by the forward's longest blended prefix per tile.
+constexpr int kSchedBuckets = 128;
+
+// Bucket of a cost on a log scale, four buckets per octave (0 for cost 0).
+__device__ __forceinline__ int sched_bucket(uint32_t x) {
+  if (x == 0u) return 0;
+  const int lz = 31 - __clz(x);
+  const uint32_t frac = lz >= 2 ? (x >> (lz - 2)) & 3u : (x << (2 - lz)) & 3u;
+  return min(kSchedBuckets - 1, lz * 4 + (int)frac + 1);
+}
+
+// One CTA: counting sort of the tiles by decreasing bucket.
+__device__ __forceinline__ void schedule_tiles(const uint2* __restrict__ ranges, const uint32_t* __restrict__ cost,
+                                               int tiles, uint32_t* __restrict__ order) {
+  __shared__ uint32_t s_h[kSchedBuckets];
+  auto cost_of = [&](int t) -> uint32_t {
+    if (cost) return cost[t];
+    const uint2 r = ranges[t];
+    return r.y > r.x ? r.y - r.x : 0u;
+  };
+  for (int b = threadIdx.x; b < kSchedBuckets; b += blockDim.x) s_h[b] = 0u;
+  __syncthreads();
+  for (int t = threadIdx.x; t < tiles; t += blockDim.x) atomicAdd(&s_h[sched_bucket(cost_of(t))], 1u);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    // exclusive scan in decreasing bucket order: lane l owns buckets 127-4l .. 124-4l
+    constexpr int kPer = kSchedBuckets / 32;
+    const int lane = threadIdx.x;
+    uint32_t v[kPer], sum = 0;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      v[j] = s_h[kSchedBuckets - 1 - (lane * kPer + j)];
+      sum += v[j];
+    }
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(kFull, inc, o);
+      if (lane >= o) inc += u;
+    }
+    uint32_t run = inc - sum;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      s_h[kSchedBuckets - 1 - (lane * kPer + j)] = run;
+      run += v[j];
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < tiles; t += blockDim.x) order[atomicAdd(&s_h[sched_bucket(cost_of(t))], 1u)] = t;
+}
+
+__global__ void __launch_bounds__(kThreads) k_tile_schedule(const uint2* __restrict__ ranges,
+                                                            const uint32_t* __restrict__ cost, int tiles,
+                                                            uint32_t* __restrict__ order) {
+  schedule_tiles(ranges, cost, tiles, order);
 }
 
 // Sum over the warp of 10 per-lane values, transposing as it halves: stage 1 (lanes l and
@@ -650,7 +723,7 @@ template <int TW>
 __global__ void __launch_bounds__(kThreads, 3) k_blend_backward(BlendBwdArgs a) {
   const BlendCommon cm{a.p0, a.p1, a.p2, nullptr, a.list, a.grad2d, a.rp.alpha_clamp, a.rp.alpha_min, 0.f,
                        a.rp.og_filter};
-  blend_bwd_tile<TW>(a, cm, (int)blockIdx.x);
+  blend_bwd_tile<TW>(a, cm, a.tile_order ? (int)a.tile_order[blockIdx.x] : (int)blockIdx.x);
 }
 
 // Persistent step over the tiles of a batch of keyframes: each CTA takes tiles from an
@@ -737,6 +810,13 @@ cudaError_t launch_blend_forward(const BlendFwdArgs& a, bool with_id, cudaStream
   }
 }
 
+cudaError_t launch_tile_schedule(const uint2* ranges, const uint32_t* cost, int tiles, uint32_t* order,
+                                 cudaStream_t s) {
+  if (tiles <= 0) return cudaSuccess;
+  k_tile_schedule<<<1, kThreads, 0, s>>>(ranges, cost, tiles, order);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_loss_reduce(const float* part, int tiles, float lambda_ins, float scale, float* loss,
                                cudaStream_t s) {
   k_loss_reduce<<<1, kThreads, 0, s>>>(part, tiles, lambda_ins, scale, loss);
@@ -771,6 +851,17 @@ unsigned persistent_grid(Kernel k, int ctas_per_sm, int sms, uint32_t total, cud
   return grid > total ? total : grid;
 }
 
+// One CTA per keyframe of a step table: which = 0 orders t.f[k]'s tiles by list length
+// into t.f[k].tile_order, which = 1 by t.f[k].tile_cost into t.b[k].tile_order.
+__global__ void __launch_bounds__(kThreads) k_tile_schedule_batch(const __grid_constant__ StepTable t, int which) {
+  const int k = blockIdx.x;
+  const int tiles = (int)(t.tile_off[k + 1] - t.tile_off[k]);
+  if (which == 0)
+    schedule_tiles(t.f[k].ranges, nullptr, tiles, const_cast<uint32_t*>(t.f[k].tile_order));
+  else
+    schedule_tiles(nullptr, t.f[k].tile_cost, tiles, const_cast<uint32_t*>(t.b[k].tile_order));
+}
+
 // Blend schedules of a batch: 0 = fused queue kernel, 1 = forward and backward queue
 // kernels, 2 = the one-keyframe kernels launched per keyframe (arguments by value).
 template <int TW, bool kId>
@@ -791,6 +882,9 @@ cudaError_t step_tw(const StepTable& t, const BlendCommon& cm, uint32_t* queue, 
     if (e != cudaSuccess) return e;
     k_blend_bwd_queue<TW><<<grid, kThreads, 0, s>>>(t, cm, queue + 1);
   } else {
+    // heaviest tiles first (see schedule_tiles)
+    const bool sched = t.f[0].tile_order && t.f[0].tile_cost && t.b[0].tile_order;
+    if (sched) k_tile_schedule_batch<<<(unsigned)t.nkf, kThreads, 0, s>>>(t, 0);
     for (int k = 0; k < t.nkf; ++k) {
       const unsigned tiles = t.tile_off[k + 1] - t.tile_off[k];
       if (tiles == 0) continue;
@@ -802,6 +896,7 @@ cudaError_t step_tw(const StepTable& t, const BlendCommon& cm, uint32_t* queue, 
       f.list = cm.list;
       k_blend_forward<TW, kId><<<tiles, kThreads, 0, s>>>(f);
     }
+    if (sched) k_tile_schedule_batch<<<(unsigned)t.nkf, kThreads, 0, s>>>(t, 1);
     for (int k = 0; k < t.nkf; ++k) {
       const unsigned tiles = t.tile_off[k + 1] - t.tile_off[k];
       if (tiles == 0) continue;
