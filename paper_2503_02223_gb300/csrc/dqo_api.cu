@@ -959,7 +959,7 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
       PhaseTimer timer(c, DQO_PHASE_PROJECT_BWD, s_);
       DQO_CUDA(c, launch_preprocess_backward_batch(bt, nkf, max_n, s_));
     }
-    launches += 2 + (schedule == 0 ? 1 : schedule == 1 ? 2 : 2 * nkf + 2);
+    launches += 2 + (schedule == 0 ? 2 : schedule == 1 ? 4 : 2 * nkf + 2);
   }
   if (run_fits) DQO_CUDA(c, cudaStreamWaitEvent(s_, B.join, 0));
   c->launches += launches;

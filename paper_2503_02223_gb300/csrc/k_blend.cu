@@ -735,11 +735,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_blend_backward(BlendBwdArgs a) 
 // parameter table.
 template <int TW, bool kId>
 __global__ void __launch_bounds__(kThreads, 4) k_blend_step(const __grid_constant__ StepTable t, BlendCommon cm,
-                                                            uint32_t* __restrict__ queue) {
+                                                            uint32_t* __restrict__ queue,
+                                                            const uint32_t* __restrict__ order) {
   __shared__ uint32_t s_item;
   const uint32_t total = t.tile_off[t.nkf];
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
+    if (threadIdx.x == 0) {
+      const uint32_t q = atomicAdd(queue, 1u);
+      s_item = q < total && order ? order[q] : q;
+    }
     __syncthreads();
     const uint32_t it = s_item;
     if (it >= total) break;
@@ -756,11 +760,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_blend_step(const __grid_constan
 // with its own queue): fewer registers per kernel than the fused walk.
 template <int TW, bool kId>
 __global__ void __launch_bounds__(kThreads) k_blend_fwd_queue(const __grid_constant__ StepTable t, BlendCommon cm,
-                                                              uint32_t* __restrict__ queue) {
+                                                              uint32_t* __restrict__ queue,
+                                                              const uint32_t* __restrict__ order) {
   __shared__ uint32_t s_item;
   const uint32_t total = t.tile_off[t.nkf];
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
+    if (threadIdx.x == 0) {
+      const uint32_t q = atomicAdd(queue, 1u);
+      s_item = q < total && order ? order[q] : q;
+    }
     __syncthreads();
     const uint32_t it = s_item;
     if (it >= total) break;
@@ -773,11 +781,15 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd_queue(const __grid_const
 
 template <int TW>
 __global__ void __launch_bounds__(kThreads, 4) k_blend_bwd_queue(const __grid_constant__ StepTable t, BlendCommon cm,
-                                                              uint32_t* __restrict__ queue) {
+                                                              uint32_t* __restrict__ queue,
+                                                              const uint32_t* __restrict__ order) {
   __shared__ uint32_t s_item;
   const uint32_t total = t.tile_off[t.nkf];
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
+    if (threadIdx.x == 0) {
+      const uint32_t q = atomicAdd(queue, 1u);
+      s_item = q < total && order ? order[q] : q;
+    }
     __syncthreads();
     const uint32_t it = s_item;
     if (it >= total) break;
@@ -870,20 +882,27 @@ cudaError_t step_tw(const StepTable& t, const BlendCommon& cm, uint32_t* queue, 
   const uint32_t total = t.tile_off[t.nkf];
   if (total == 0) return cudaSuccess;
   cudaError_t e = cudaSuccess;
+  // heaviest tiles first (see schedule_tiles): the queue kernels take the batch's joint
+  // tiles in one joint order (the per-keyframe arrays are slices of joint arrays, so
+  // keyframe 0's pointers are the joint bases), the per-keyframe kernels per keyframe
+  const bool sched = t.f[0].tile_order && t.f[0].tile_cost && t.b[0].tile_order && t.tile_off[0] == 0;
+  uint32_t* f_order = sched ? const_cast<uint32_t*>(t.f[0].tile_order) : nullptr;
+  uint32_t* b_order = sched ? const_cast<uint32_t*>(t.b[0].tile_order) : nullptr;
   if (schedule == 0) {
     const unsigned grid = persistent_grid(k_blend_step<TW, kId>, ctas_per_sm, sms, total, &e);
     if (e != cudaSuccess) return e;
-    k_blend_step<TW, kId><<<grid, kThreads, 0, s>>>(t, cm, queue);
+    if (sched) k_tile_schedule<<<1, kThreads, 0, s>>>(t.f[0].ranges, nullptr, (int)total, f_order);
+    k_blend_step<TW, kId><<<grid, kThreads, 0, s>>>(t, cm, queue, f_order);
   } else if (schedule == 1) {
     unsigned grid = persistent_grid(k_blend_fwd_queue<TW, kId>, ctas_per_sm, sms, total, &e);
     if (e != cudaSuccess) return e;
-    k_blend_fwd_queue<TW, kId><<<grid, kThreads, 0, s>>>(t, cm, queue);
+    if (sched) k_tile_schedule<<<1, kThreads, 0, s>>>(t.f[0].ranges, nullptr, (int)total, f_order);
+    k_blend_fwd_queue<TW, kId><<<grid, kThreads, 0, s>>>(t, cm, queue, f_order);
     grid = persistent_grid(k_blend_bwd_queue<TW>, ctas_per_sm, sms, total, &e);
     if (e != cudaSuccess) return e;
-    k_blend_bwd_queue<TW><<<grid, kThreads, 0, s>>>(t, cm, queue + 1);
+    if (sched) k_tile_schedule<<<1, kThreads, 0, s>>>(nullptr, t.f[0].tile_cost, (int)total, b_order);
+    k_blend_bwd_queue<TW><<<grid, kThreads, 0, s>>>(t, cm, queue + 1, b_order);
   } else {
-    // heaviest tiles first (see schedule_tiles)
-    const bool sched = t.f[0].tile_order && t.f[0].tile_cost && t.b[0].tile_order;
     if (sched) k_tile_schedule_batch<<<(unsigned)t.nkf, kThreads, 0, s>>>(t, 0);
     for (int k = 0; k < t.nkf; ++k) {
       const unsigned tiles = t.tile_off[k + 1] - t.tile_off[k];
