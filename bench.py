@@ -781,8 +781,11 @@ def batched_section(dev, stream, world, fq, fd):
            "losses_match_single": same_loss,
            "tuned": {"tile": f"{bst.tile_w}x{bst.tile_h}", "ctas_per_sm": cps, "schedule": sched,
                      "candidates_ms": tune_table(dqo, tune_ms)},
-           "form": "one launch per phase over all keyframes, persistent fused forward+backward blend on a work "
-                   "queue, fits on a concurrent graph branch, one CUDA graph"}
+           "form": "one launch per phase over all keyframes; blend: "
+                   + {0: "one persistent forward+backward kernel on a work queue",
+                      1: "persistent forward and backward kernels on work queues",
+                      2: "forward and backward kernels per keyframe"}[sched]
+                   + " (tiles heaviest first); fits on a concurrent graph branch; one CUDA graph"}
     ctx.close()
     bctx.close()
     return res
