@@ -25,7 +25,7 @@ struct dqo_ctx {
   int device = 0;
   int last_err = 0;
   // per-Gaussian
-  Buf p0, p1, p2, rect, ntiles, zkey_a, zkey_b, zval_a, zval_b, rank, gid, offsets, grad2d;
+  Buf p0, p1, p2, rect, ntiles, zkey_a, zkey_b, zval_a, zval_b, gid, offsets, grad2d;
   // sorting scratch
   Buf scan_scratch, depth_scan_scratch, hist, depth_hist, pair_a, pair_b, list;
   // per-tile / per-pixel
@@ -50,7 +50,7 @@ struct dqo_ctx {
   int64_t launches = 0;
   // batched step: joint buffers of all keyframes of a batch, pair capacity, side stream
   struct Batch {
-    Buf p0, p1, p2, rect, ntiles, zkey_a, zkey_b, zval_a, zval_b, rank, gid, offsets, grad2d;
+    Buf p0, p1, p2, rect, ntiles, zkey_a, zkey_b, zval_a, zval_b, gid, offsets, grad2d;
     Buf scan_scratch, depth_scan_scratch, depth_hist, hist, pair_a, pair_b, list, ranges, loss_part;
     Buf T_final, n_contrib, dl_rgb, dl_depth, dl_ins, counters, tile_sched;
     uint64_t* host = nullptr;  // pinned: pair count of a sizing call
@@ -264,14 +264,14 @@ dqo_status dqo_create(dqo_ctx** out, int device) {
 void dqo_destroy(dqo_ctx* c) {
   if (!c) return;
   Buf* all[] = {&c->p0, &c->p1, &c->p2, &c->rect, &c->ntiles, &c->zkey_a, &c->zkey_b, &c->zval_a,
-                &c->zval_b, &c->rank, &c->gid, &c->offsets, &c->grad2d, &c->scan_scratch,
+                &c->zval_b, &c->gid, &c->offsets, &c->grad2d, &c->scan_scratch,
                 &c->depth_scan_scratch, &c->hist, &c->depth_hist,
                 &c->pair_a, &c->pair_b, &c->list, &c->ranges, &c->loss_part, &c->T_final, &c->n_contrib,
                 &c->dl_rgb, &c->dl_depth, &c->dl_ins, &c->counters, &c->sort_err, &c->tile_sched};
   for (Buf* b : all)
     if (b->p) cudaFree(b->p);
   dqo_ctx::Batch& B = c->b;
-  Buf* ball[] = {&B.p0, &B.p1, &B.p2, &B.rect, &B.ntiles, &B.zkey_a, &B.zkey_b, &B.zval_a, &B.zval_b, &B.rank,
+  Buf* ball[] = {&B.p0, &B.p1, &B.p2, &B.rect, &B.ntiles, &B.zkey_a, &B.zkey_b, &B.zval_a, &B.zval_b,
                  &B.gid, &B.offsets, &B.grad2d, &B.scan_scratch, &B.depth_scan_scratch, &B.depth_hist, &B.hist,
                  &B.pair_a, &B.pair_b, &B.list, &B.ranges, &B.loss_part, &B.T_final, &B.n_contrib, &B.dl_rgb,
                  &B.dl_depth, &B.dl_ins, &B.counters, &B.tile_sched, &c->mlp_work};
@@ -318,7 +318,6 @@ dqo_status dqo_render_forward(dqo_ctx* c, const dqo_settings* s, const dqo_gauss
   DQO_CUDA(c, ensure(c->zkey_b, 4 * n));
   DQO_CUDA(c, ensure(c->zval_a, 4 * n));
   DQO_CUDA(c, ensure(c->zval_b, 4 * n));
-  DQO_CUDA(c, ensure(c->rank, 4 * n));
   DQO_CUDA(c, ensure(c->gid, 4 * n));
   DQO_CUDA(c, ensure(c->offsets, 4 * n));
   DQO_CUDA(c, ensure(c->ranges, 8 * (size_t)tiles));
@@ -357,23 +356,24 @@ dqo_status dqo_render_forward(dqo_ctx* c, const dqo_settings* s, const dqo_gauss
   }
   c->launches += nb_launch;
 
-  // ---- K2 scan of tiles per Gaussian; the pair count goes to the host while the depth
-  // sort runs (the host waits on that copy only, not on the sort)
+  // ---- K4a depth order, then K2: the scan of tiles per Gaussian in depth order (pair
+  // offsets by rank); the pair count goes to the host
   int sel = 0;
+  const uint32_t* order = nullptr;
   {
     PhaseTimer pt(c, DQO_PHASE_DEPTH_SORT, s_);
+    DQO_CUDA(c, radix_sort_u32(as<uint32_t>(c->zkey_a), as<uint32_t>(c->zkey_b), as<uint32_t>(c->zval_a),
+                               as<uint32_t>(c->zval_b), n, 32, as<uint32_t>(c->depth_hist), &sel, s_, nullptr,
+                               as<uint32_t>(c->sort_err)));
+    order = sel ? as<uint32_t>(c->zval_b) : as<uint32_t>(c->zval_a);
     DQO_CUDA(c, launch_exclusive_scan(as<uint32_t>(c->ntiles), as<uint32_t>(c->offsets), n,
-                                      as<uint64_t>(c->scan_scratch), d_total, s_, as<uint32_t>(c->sort_err)));
+                                      as<uint64_t>(c->scan_scratch), d_total, s_, as<uint32_t>(c->sort_err), order));
     DQO_CUDA(c, cudaMemcpyAsync(c->host_counters, c->counters.p, 16, cudaMemcpyDeviceToHost, s_));
     DQO_CUDA(c, cudaMemcpyAsync(c->host_counters + 2, c->sort_err.p, 4, cudaMemcpyDeviceToHost, s_));
     DQO_CUDA(c, cudaEventRecord(c->count_ready, s_));
-    DQO_CUDA(c, radix_sort_u32(as<uint32_t>(c->zkey_a), as<uint32_t>(c->zkey_b), as<uint32_t>(c->zval_a),
-                               as<uint32_t>(c->zval_b), n, 32, as<uint32_t>(c->depth_hist), &sel, s_,
-                               as<uint32_t>(c->rank), as<uint32_t>(c->sort_err)));
   }
-  const uint32_t* order = sel ? as<uint32_t>(c->zval_b) : as<uint32_t>(c->zval_a);
   c->order_sel = sel;
-  c->launches += scan_launches(n) + radix_sort_launches(n, 32) + (n == 1 ? 1 : 0);
+  c->launches += scan_launches(n) + radix_sort_launches(n, 32);
 
   // ---- pair count on the host (the one wait of the forward)
   DQO_CUDA(c, cudaEventSynchronize(c->count_ready));
@@ -401,19 +401,21 @@ dqo_status dqo_render_forward(dqo_ctx* c, const dqo_settings* s, const dqo_gauss
     DQO_CUDA(c, ensure(c->hist, 4 * radix_scratch_words((int64_t)m)));
     DQO_CUDA(c, ensure(c->scan_scratch, 8 * scan_scratch_words(radix_scratch_words((int64_t)m))));
     int psel = 0;
-    c->launches += 2 + radix_sort_launches((int64_t)m, end_bit);
+    // pairs come out in depth-rank order: a stable sort on the tile bits finishes the job
+    c->launches += 2 + radix_sort_launches((int64_t)m, end_bit, rank_bits);
     if (k32) {
-      DQO_CUDA(c, launch_emit_pairs_u32(as<ushort4>(c->rect), as<uint32_t>(c->offsets), as<uint32_t>(c->rank), n,
-                                        rp.ntx, rank_bits, as<uint32_t>(c->pair_a), s_));
+      DQO_CUDA(c, launch_emit_pairs_u32(as<ushort4>(c->rect), as<uint32_t>(c->offsets), order, n, rp.ntx, rank_bits,
+                                        as<uint32_t>(c->pair_a), s_));
       DQO_CUDA(c, radix_sort_u32(as<uint32_t>(c->pair_a), as<uint32_t>(c->pair_b), nullptr, nullptr, (int64_t)m,
-                                 end_bit, as<uint32_t>(c->hist), &psel, s_, nullptr, as<uint32_t>(c->sort_err)));
+                                 end_bit, as<uint32_t>(c->hist), &psel, s_, nullptr, as<uint32_t>(c->sort_err),
+                                 rank_bits));
       DQO_CUDA(c, launch_tile_ranges_u32(psel ? as<uint32_t>(c->pair_b) : as<uint32_t>(c->pair_a), (int64_t)m,
                                          rank_bits, order, as<uint2>(c->ranges), as<uint32_t>(c->list), s_));
     } else {
-      DQO_CUDA(c, launch_emit_pairs_u64(as<ushort4>(c->rect), as<uint32_t>(c->offsets), as<uint32_t>(c->rank), n,
-                                        rp.ntx, rank_bits, as<uint64_t>(c->pair_a), s_));
+      DQO_CUDA(c, launch_emit_pairs_u64(as<ushort4>(c->rect), as<uint32_t>(c->offsets), order, n, rp.ntx, rank_bits,
+                                        as<uint64_t>(c->pair_a), s_));
       DQO_CUDA(c, radix_sort_u64(as<uint64_t>(c->pair_a), as<uint64_t>(c->pair_b), (int64_t)m, end_bit,
-                                 as<uint32_t>(c->hist), &psel, s_, nullptr, as<uint32_t>(c->sort_err)));
+                                 as<uint32_t>(c->hist), &psel, s_, nullptr, as<uint32_t>(c->sort_err), rank_bits));
       DQO_CUDA(c, launch_tile_ranges_u64(psel ? as<uint64_t>(c->pair_b) : as<uint64_t>(c->pair_a), (int64_t)m,
                                          rank_bits, order, as<uint2>(c->ranges), as<uint32_t>(c->list), s_));
     }
@@ -744,7 +746,6 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
     DQO_CUDA(c, ensure(B.zkey_b, 4 * N));
     DQO_CUDA(c, ensure(B.zval_a, 4 * N));
     DQO_CUDA(c, ensure(B.zval_b, 4 * N));
-    DQO_CUDA(c, ensure(B.rank, 4 * N));
     DQO_CUDA(c, ensure(B.gid, 4 * N));
     DQO_CUDA(c, ensure(B.offsets, 4 * N));
     DQO_CUDA(c, ensure(B.grad2d, 48 * N));
@@ -814,19 +815,20 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
     DQO_CUDA(c, launch_preprocess_batch(pt, nkf, max_n, pb, s_));
     launches += 1;
   }
-  // ---- pair offsets, depth order (one sort over all keyframes: ranks keep each
-  // keyframe's (depth, index) order because its indices are contiguous)
+  // ---- depth order (one sort over all keyframes: the order restricted to a keyframe is
+  // its (depth, index) order because its indices are contiguous), then pair offsets by
+  // depth rank
   int sel = 0;
   const uint32_t* order = nullptr;
   {
     PhaseTimer timer(c, DQO_PHASE_DEPTH_SORT, s_);
-    DQO_CUDA(c, launch_exclusive_scan(as<uint32_t>(B.ntiles), as<uint32_t>(B.offsets), N,
-                                      as<uint64_t>(B.scan_scratch), d_total, s_, d_sort_err));
     DQO_CUDA(c, radix_sort_u32(as<uint32_t>(B.zkey_a), as<uint32_t>(B.zkey_b), as<uint32_t>(B.zval_a),
-                               as<uint32_t>(B.zval_b), N, 32, as<uint32_t>(B.depth_hist), &sel, s_,
-                               as<uint32_t>(B.rank), d_sort_err));
+                               as<uint32_t>(B.zval_b), N, 32, as<uint32_t>(B.depth_hist), &sel, s_, nullptr,
+                               d_sort_err));
     order = sel ? as<uint32_t>(B.zval_b) : as<uint32_t>(B.zval_a);
-    launches += scan_launches(N) + radix_sort_launches(N, 32) + (N == 1 ? 1 : 0);
+    DQO_CUDA(c, launch_exclusive_scan(as<uint32_t>(B.ntiles), as<uint32_t>(B.offsets), N,
+                                      as<uint64_t>(B.scan_scratch), d_total, s_, d_sort_err, order));
+    launches += scan_launches(N) + radix_sort_launches(N, 32);
   }
 
   if (sizing) {
@@ -857,23 +859,23 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
       et.kf[k].ntx = rp[k].ntx;
     }
     const bool k32 = end_bit <= 32;
-    DQO_CUDA(c, launch_emit_pairs_batch(et, nkf, max_n, as<ushort4>(B.rect), as<uint32_t>(B.offsets),
-                                        as<uint32_t>(B.rank), rank_bits, cap, B.pair_a.p, k32, d_overflow, s_));
+    DQO_CUDA(c, launch_emit_pairs_batch(et, nkf, N, as<ushort4>(B.rect), as<uint32_t>(B.offsets), order, rank_bits,
+                                        cap, B.pair_a.p, k32, d_overflow, s_));
     int psel = 0;
     if (k32) {
       DQO_CUDA(c, radix_sort_u32_dev(as<uint32_t>(B.pair_a), as<uint32_t>(B.pair_b), (int64_t)cap, end_bit,
-                                     as<uint32_t>(B.hist), &psel, s_, d_total, d_sort_err));
+                                     as<uint32_t>(B.hist), &psel, s_, d_total, d_sort_err, rank_bits));
       DQO_CUDA(c, launch_tile_ranges_u32(psel ? as<uint32_t>(B.pair_b) : as<uint32_t>(B.pair_a), (int64_t)cap,
                                          rank_bits, order, as<uint2>(B.ranges), as<uint32_t>(B.list), s_,
                                          d_total));
     } else {
       DQO_CUDA(c, radix_sort_u64(as<uint64_t>(B.pair_a), as<uint64_t>(B.pair_b), (int64_t)cap, end_bit,
-                                 as<uint32_t>(B.hist), &psel, s_, d_total, d_sort_err));
+                                 as<uint32_t>(B.hist), &psel, s_, d_total, d_sort_err, rank_bits));
       DQO_CUDA(c, launch_tile_ranges_u64(psel ? as<uint64_t>(B.pair_b) : as<uint64_t>(B.pair_a), (int64_t)cap,
                                          rank_bits, order, as<uint2>(B.ranges), as<uint32_t>(B.list), s_,
                                          d_total));
     }
-    launches += 2 + radix_sort_launches((int64_t)cap, end_bit);
+    launches += 2 + radix_sort_launches((int64_t)cap, end_bit, rank_bits);
   }
 
   // ---- persistent forward + backward over all tiles, losses, projection adjoint

@@ -177,14 +177,15 @@ cudaError_t launch_preprocess_batch(const PreTable& t, int nkf, int64_t max_n, c
                                     cudaStream_t s);
 cudaError_t launch_preprocess_backward_batch(const PreBwdTable& t, int nkf, int64_t max_n, cudaStream_t s);
 
-// Exclusive scan of n uint32 values (one kernel, decoupled look-back); total (uint64)
-// written to *total.  scratch must hold scan_scratch_words(n) uint64 words.  err
-// (optional): set to 1 if a look-back wait gave up.
+// Exclusive scan of n uint32 values in[i] (in[gather[i]] when gather is given; one kernel,
+// decoupled look-back); total (uint64) written to *total.  scratch must hold
+// scan_scratch_words(n) uint64 words.  err (optional): set to 1 if a look-back wait gave up.
 size_t scan_scratch_words(int64_t n);
 cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint64_t* scratch,
-                                  uint64_t* total, cudaStream_t s, uint32_t* err = nullptr);
+                                  uint64_t* total, cudaStream_t s, uint32_t* err = nullptr,
+                                  const uint32_t* gather = nullptr);
 
-// Stable LSD radix sort of n keys (bits [0, end_bit)), optional uint32 values: one kernel
+// Stable LSD radix sort of n keys on bits [begin_bit, end_bit), optional uint32 values: one kernel
 // counts all digits, then one kernel per 8-bit digit with decoupled look-back.  Results
 // land in whichever of the double buffers *sel says (0: *_a, 1: *_b).  scratch holds
 // radix_scratch_words(n) uint32 words (histograms, look-back status, counters).  rank
@@ -193,19 +194,23 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, 
 // err (optional): set to 1 if a look-back wait gave up (about a second); NULL keeps the
 // flag inside scratch.
 size_t radix_scratch_words(int64_t n);
-int64_t radix_sort_launches(int64_t n, int end_bit);
+int64_t radix_sort_launches(int64_t n, int end_bit, int begin_bit = 0);
 cudaError_t radix_sort_u32(uint32_t* keys_a, uint32_t* keys_b, uint32_t* vals_a, uint32_t* vals_b, int64_t n,
                            int end_bit, uint32_t* scratch, int* sel, cudaStream_t s, uint32_t* rank = nullptr,
-                           uint32_t* err = nullptr);
+                           uint32_t* err = nullptr, int begin_bit = 0);
 cudaError_t radix_sort_u64(uint64_t* keys_a, uint64_t* keys_b, int64_t n, int end_bit, uint32_t* scratch, int* sel,
-                           cudaStream_t s, const uint64_t* n_dev = nullptr, uint32_t* err = nullptr);
+                           cudaStream_t s, const uint64_t* n_dev = nullptr, uint32_t* err = nullptr,
+                           int begin_bit = 0);
 cudaError_t radix_sort_u32_dev(uint32_t* keys_a, uint32_t* keys_b, int64_t n, int end_bit, uint32_t* scratch,
-                               int* sel, cudaStream_t s, const uint64_t* n_dev, uint32_t* err = nullptr);
+                               int* sel, cudaStream_t s, const uint64_t* n_dev, uint32_t* err = nullptr,
+                               int begin_bit = 0);
 
 cudaError_t launch_rank_scatter(const uint32_t* order, int64_t n, uint32_t* rank, cudaStream_t s);
-cudaError_t launch_emit_pairs_u32(const ushort4* rect, const uint32_t* offsets, const uint32_t* rank,
+// Pairs (tile << rank_bits | depth rank) of the Gaussians in depth order: rank r's Gaussian
+// order[r] writes its tiles' keys from offsets[r] (tile counts scanned in rank order).
+cudaError_t launch_emit_pairs_u32(const ushort4* rect, const uint32_t* offsets, const uint32_t* order,
                                   int64_t n, int ntx, int rank_bits, uint32_t* keys, cudaStream_t s);
-cudaError_t launch_emit_pairs_u64(const ushort4* rect, const uint32_t* offsets, const uint32_t* rank,
+cudaError_t launch_emit_pairs_u64(const ushort4* rect, const uint32_t* offsets, const uint32_t* order,
                                   int64_t n, int ntx, int rank_bits, uint64_t* keys, cudaStream_t s);
 cudaError_t launch_tile_ranges_u32(const uint32_t* keys, int64_t m, int rank_bits, const uint32_t* order,
                                    uint2* ranges, uint32_t* list, cudaStream_t s, const uint64_t* m_dev = nullptr);
@@ -224,9 +229,10 @@ struct EmitKf {
 struct EmitTable {
   EmitKf kf[16];
 };
-// keys: uint32_t[capacity] if k32 (tile and rank bits fit 32), else uint64_t[capacity].
-cudaError_t launch_emit_pairs_batch(const EmitTable& t, int nkf, int64_t max_n, const ushort4* rect,
-                                    const uint32_t* offsets, const uint32_t* rank, int rank_bits, uint64_t capacity,
+// The same over a batch's n joint Gaussians in joint depth order.  keys: uint32_t[capacity]
+// if k32 (tile and rank bits fit 32), else uint64_t[capacity].
+cudaError_t launch_emit_pairs_batch(const EmitTable& t, int nkf, int64_t n, const ushort4* rect,
+                                    const uint32_t* offsets, const uint32_t* order, int rank_bits, uint64_t capacity,
                                     void* keys, bool k32, uint32_t* overflow, cudaStream_t s);
 
 cudaError_t launch_blend_forward(const BlendFwdArgs& a, bool with_id, cudaStream_t s);

@@ -59,6 +59,7 @@ __device__ __forceinline__ uint64_t scan_ns() {
 constexpr uint64_t kScanAgg = 1ull << 62, kScanInc = 2ull << 62, kScanMask = (1ull << 62) - 1;
 
 __global__ void __launch_bounds__(kThreads) k_scan_lookback(const uint32_t* __restrict__ in,
+                                                            const uint32_t* __restrict__ gather,
                                                             uint32_t* __restrict__ out, int64_t n,
                                                             uint64_t* __restrict__ status,
                                                             uint32_t* __restrict__ counter,
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(kThreads) k_scan_lookback(const uint32_t* __re
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
     const int64_t i = base + k * kThreads + threadIdx.x;
-    tile_s[k * kThreads + threadIdx.x] = i < n ? in[i] : 0u;
+    tile_s[k * kThreads + threadIdx.x] = i < n ? in[gather ? gather[i] : i] : 0u;
   }
   __syncthreads();
   uint32_t v[kSortItems];
@@ -151,8 +152,8 @@ constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kCountMask = (1u <<
 
 template <typename K, int IPT>
 __global__ void __launch_bounds__(kThreads) k_onesweep_hist(const K* __restrict__ keys, int64_t n_cap,
-                                                            const uint64_t* __restrict__ n_dev, int passes,
-                                                            uint32_t* __restrict__ ghist) {
+                                                            const uint64_t* __restrict__ n_dev, int begin_bit,
+                                                            int passes, uint32_t* __restrict__ ghist) {
   __shared__ uint32_t h[kMaxRadixPasses][kRadixBins];
   for (int i = threadIdx.x; i < passes * kRadixBins; i += kThreads) (&h[0][0])[i] = 0;
   __syncthreads();
@@ -163,7 +164,8 @@ __global__ void __launch_bounds__(kThreads) k_onesweep_hist(const K* __restrict_
     const int64_t i = base + k * kThreads + threadIdx.x;
     if (i < n) {
       const K key = keys[i];
-      for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(uint32_t)(key >> (p * kRadixBits)) & (kRadixBins - 1)], 1u);
+      for (int p = 0; p < passes; ++p)
+        atomicAdd(&h[p][(uint32_t)(key >> (begin_bit + p * kRadixBits)) & (kRadixBins - 1)], 1u);
     }
   }
   __syncthreads();
@@ -301,65 +303,68 @@ __device__ __forceinline__ void warp_emit(const ushort4 r, const uint64_t o, con
     const uint32_t y0 = __shfl_sync(0xFFFFFFFFu, (uint32_t)r.y, j);
     const uint32_t w = __shfl_sync(0xFFFFFFFFu, (uint32_t)(r.z - r.x), j);
     const K rj = __shfl_sync(0xFFFFFFFFu, rk, j);
+    const uint32_t toj = __shfl_sync(0xFFFFFFFFu, tile_off, j);   // the Gaussian's keyframe
+    const uint32_t ntxj = __shfl_sync(0xFFFFFFFFu, (uint32_t)ntx, j);
     for (uint32_t k = lane; k < c; k += 32) {
       const uint32_t ty = y0 + k / w, tx = x0 + k % w;
-      keys[oj + k] = ((K)(tile_off + ty * (uint32_t)ntx + tx) << rank_bits) | rj;
+      keys[oj + k] = ((K)(toj + ty * ntxj + tx) << rank_bits) | rj;
     }
   }
 }
 
+// Pairs in depth order: thread r emits the pairs of the Gaussian of depth rank r,
+// i = order[r], at offsets[r] (the exclusive scan of tile counts in rank order).  Pairs
+// thus come out ordered by rank, and a stable sort on the tile bits alone groups them by
+// tile with each tile's Gaussians front to back.
 template <typename K>
 __global__ void __launch_bounds__(kThreads) k_emit_pairs(const ushort4* __restrict__ rect,
                                                          const uint32_t* __restrict__ offsets,
-                                                         const uint32_t* __restrict__ rank, int64_t n, int ntx,
+                                                         const uint32_t* __restrict__ order, int64_t n, int ntx,
                                                          int rank_bits, K* __restrict__ keys) {
-  const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-  ushort4 r = make_ushort4(0, 0, 0, 0);
+  const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  ushort4 q = make_ushort4(0, 0, 0, 0);
   uint64_t o = 0;
   uint32_t cnt = 0;
-  K rk = 0;
-  if (i < n) {
-    r = rect[i];
-    if (r.z > r.x && r.w > r.y) {
-      o = offsets[i];
-      cnt = (uint32_t)(r.z - r.x) * (uint32_t)(r.w - r.y);
-      rk = (K)rank[i];
+  if (r < n) {
+    q = rect[order[r]];
+    if (q.z > q.x && q.w > q.y) {
+      o = offsets[r];
+      cnt = (uint32_t)(q.z - q.x) * (uint32_t)(q.w - q.y);
     }
   }
-  warp_emit<K>(r, o, cnt, rk, 0u, ntx, rank_bits, keys);
+  warp_emit<K>(q, o, cnt, (K)r, 0u, ntx, rank_bits, keys);
 }
 
-// Pairs of a batch of keyframes: Gaussian i of keyframe blockIdx.y (global index
-// base + i) covers tiles tile_off + ty * ntx + tx of the batch's joint tile numbering.
-// Pairs past `capacity` are not written; *overflow is set instead.
+// The same over a batch of keyframes (joint rank r of all keyframes' Gaussians; the
+// Gaussian's keyframe k is found from the global index ranges [base, base + n)); its
+// tiles are tile_off + ty * ntx + tx of the batch's joint tile numbering.  Pairs past
+// `capacity` are not written; *overflow is set instead.
 template <typename K>
-__global__ void __launch_bounds__(kThreads) k_emit_pairs_batch(const __grid_constant__ EmitTable t,
+__global__ void __launch_bounds__(kThreads) k_emit_pairs_batch(const __grid_constant__ EmitTable t, int nkf,
                                                                const ushort4* __restrict__ rect,
                                                                const uint32_t* __restrict__ offsets,
-                                                               const uint32_t* __restrict__ rank, int rank_bits,
-                                                               uint64_t capacity, K* __restrict__ keys,
+                                                               const uint32_t* __restrict__ order, int64_t n,
+                                                               int rank_bits, uint64_t capacity, K* __restrict__ keys,
                                                                uint32_t* __restrict__ overflow) {
-  const EmitKf& kf = t.kf[blockIdx.y];
-  if ((int64_t)blockIdx.x * kThreads >= kf.n) return;  // uniform over the block
-  const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-  ushort4 r = make_ushort4(0, 0, 0, 0);
+  const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  ushort4 q = make_ushort4(0, 0, 0, 0);
   uint64_t o = 0;
   uint32_t cnt = 0;
-  K rk = 0;
-  if (i < kf.n) {
-    const int64_t gi = kf.base + i;
-    r = rect[gi];
-    if (r.z > r.x && r.w > r.y) {
-      o = offsets[gi];
-      cnt = (uint32_t)(r.z - r.x) * (uint32_t)(r.w - r.y);
-      rk = (K)rank[gi];
+  int k = 0;
+  if (r < n) {
+    const int64_t gi = order[r];
+    while (k + 1 < nkf && t.kf[k + 1].base <= gi) ++k;
+    q = rect[gi];
+    if (q.z > q.x && q.w > q.y) {
+      o = offsets[r];
+      cnt = (uint32_t)(q.z - q.x) * (uint32_t)(q.w - q.y);
       if (o + cnt > capacity) {
         atomicExch(overflow, 1u);
         cnt = 0;
       }
     }
   }
-  warp_emit<K>(r, o, cnt, rk, kf.tile_off, kf.ntx, rank_bits, keys);
+  warp_emit<K>(q, o, cnt, (K)r, t.kf[k].tile_off, t.kf[k].ntx, rank_bits, keys);
 }
 
 template <typename K>
@@ -389,21 +394,23 @@ inline size_t onesweep_words(int64_t tiles, int passes) {
 }
 
 template <typename K, bool kVals, int IPT>
-cudaError_t radix_passes(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n, int end_bit, uint32_t* scratch,
-                         int* sel, cudaStream_t s, const uint64_t* n_dev, uint32_t* rank, uint32_t* err_out) {
+cudaError_t radix_passes(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n, int begin_bit, int end_bit,
+                         uint32_t* scratch, int* sel, cudaStream_t s, const uint64_t* n_dev, uint32_t* rank,
+                         uint32_t* err_out) {
   const unsigned nb = grid_for(n, kThreads * IPT);
-  const int passes = (end_bit + kRadixBits - 1) / kRadixBits;
+  const int passes = (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;
   uint32_t* ghist = scratch;
   uint32_t* status = ghist + (size_t)passes * kRadixBins;
   uint32_t* counters = status + (size_t)passes * nb * kRadixBins;
   uint32_t* err = err_out ? err_out : counters + passes;
   cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * onesweep_words(nb, passes), s);
   if (e != cudaSuccess) return e;
-  k_onesweep_hist<K, IPT><<<nb, kThreads, 0, s>>>(ka, n, n_dev, passes, ghist);
+  k_onesweep_hist<K, IPT><<<nb, kThreads, 0, s>>>(ka, n, n_dev, begin_bit, passes, ghist);
   K* kin = ka; K* kout = kb;
   uint32_t* vin = va; uint32_t* vout = vb;
   for (int p = 0; p < passes; ++p) {
-    k_onesweep_pass<K, kVals, IPT><<<nb, kThreads, 0, s>>>(kin, kout, vin, vout, n, n_dev, p * kRadixBits,
+    k_onesweep_pass<K, kVals, IPT><<<nb, kThreads, 0, s>>>(kin, kout, vin, vout, n, n_dev,
+                                                           begin_bit + p * kRadixBits,
                                                            ghist + p * kRadixBins,
                                                            status + (size_t)p * nb * kRadixBins, counters + p,
                                                            p == passes - 1 ? rank : nullptr, err);
@@ -417,16 +424,17 @@ cudaError_t radix_passes(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n, in
 template <typename K, bool kVals>
 cudaError_t radix_sort_impl(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n, int end_bit, uint32_t* hist,
                             int* sel, cudaStream_t s, const uint64_t* n_dev = nullptr, uint32_t* rank = nullptr,
-                            uint32_t* err = nullptr) {
+                            uint32_t* err = nullptr, int begin_bit = 0) {
   *sel = 0;
-  if (n <= 1 || end_bit <= 0) {  // already in order: ranks from the values as they stand
+  if (begin_bit < 0 || end_bit > (int)(8 * sizeof(K))) return cudaErrorInvalidValue;
+  if (n <= 1 || end_bit <= begin_bit) {  // already in order: ranks from the values as they stand
     if (rank && va && n > 0) k_rank_scatter<<<grid_for(n, kThreads), kThreads, 0, s>>>(va, n, rank);
     return cudaGetLastError();
   }
-  if (end_bit > kMaxRadixPasses * kRadixBits) return cudaErrorInvalidValue;
+  if (end_bit - begin_bit > kMaxRadixPasses * kRadixBits) return cudaErrorInvalidValue;
   if (sort_items(n) == 8)
-    return radix_passes<K, kVals, 8>(ka, kb, va, vb, n, end_bit, hist, sel, s, n_dev, rank, err);
-  return radix_passes<K, kVals, 16>(ka, kb, va, vb, n, end_bit, hist, sel, s, n_dev, rank, err);
+    return radix_passes<K, kVals, 8>(ka, kb, va, vb, n, begin_bit, end_bit, hist, sel, s, n_dev, rank, err);
+  return radix_passes<K, kVals, 16>(ka, kb, va, vb, n, begin_bit, end_bit, hist, sel, s, n_dev, rank, err);
 }
 
 }  // namespace
@@ -435,7 +443,7 @@ cudaError_t radix_sort_impl(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n,
 size_t scan_scratch_words(int64_t n) { return (size_t)grid_for(n > 0 ? n : 1, kSortTile) + 2; }
 
 cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint64_t* scratch, uint64_t* total,
-                                  cudaStream_t s, uint32_t* err) {
+                                  cudaStream_t s, uint32_t* err, const uint32_t* gather) {
   if (n <= 0) {
     if (total) return cudaMemsetAsync(total, 0, sizeof(uint64_t), s);
     return cudaSuccess;
@@ -444,7 +452,7 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, 
   cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(uint64_t) * (nb + 2), s);
   if (e != cudaSuccess) return e;
   uint32_t* counter = reinterpret_cast<uint32_t*>(scratch + nb);
-  k_scan_lookback<<<nb, kThreads, 0, s>>>(in, out, n, scratch, counter,
+  k_scan_lookback<<<nb, kThreads, 0, s>>>(in, gather, out, n, scratch, counter,
                                           err ? err : reinterpret_cast<uint32_t*>(scratch + nb + 1), total);
   return cudaGetLastError();
 }
@@ -454,24 +462,25 @@ size_t radix_scratch_words(int64_t n) {
   return onesweep_words(grid_for(m, kThreads * sort_items(m)), kMaxRadixPasses);
 }
 
-int64_t radix_sort_launches(int64_t n, int end_bit) {
-  if (n <= 1 || end_bit <= 0) return 0;
-  return 1 + (end_bit + kRadixBits - 1) / kRadixBits;  // histograms, one kernel per pass
+int64_t radix_sort_launches(int64_t n, int end_bit, int begin_bit) {
+  if (n <= 1 || end_bit <= begin_bit) return 0;
+  return 1 + (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;  // histograms, one kernel per pass
 }
 
 cudaError_t radix_sort_u32(uint32_t* keys_a, uint32_t* keys_b, uint32_t* vals_a, uint32_t* vals_b, int64_t n,
-                           int end_bit, uint32_t* scratch, int* sel, cudaStream_t s, uint32_t* rank, uint32_t* err) {
+                           int end_bit, uint32_t* scratch, int* sel, cudaStream_t s, uint32_t* rank, uint32_t* err,
+                           int begin_bit) {
   if (vals_a)
     return radix_sort_impl<uint32_t, true>(keys_a, keys_b, vals_a, vals_b, n, end_bit, scratch, sel, s, nullptr,
-                                           rank, err);
+                                           rank, err, begin_bit);
   return radix_sort_impl<uint32_t, false>(keys_a, keys_b, nullptr, nullptr, n, end_bit, scratch, sel, s, nullptr,
-                                          nullptr, err);
+                                          nullptr, err, begin_bit);
 }
 
 cudaError_t radix_sort_u64(uint64_t* keys_a, uint64_t* keys_b, int64_t n, int end_bit, uint32_t* scratch, int* sel,
-                           cudaStream_t s, const uint64_t* n_dev, uint32_t* err) {
+                           cudaStream_t s, const uint64_t* n_dev, uint32_t* err, int begin_bit) {
   return radix_sort_impl<uint64_t, false>(keys_a, keys_b, nullptr, nullptr, n, end_bit, scratch, sel, s, n_dev,
-                                          nullptr, err);
+                                          nullptr, err, begin_bit);
 }
 
 cudaError_t launch_rank_scatter(const uint32_t* order, int64_t n, uint32_t* rank, cudaStream_t s) {
@@ -480,17 +489,17 @@ cudaError_t launch_rank_scatter(const uint32_t* order, int64_t n, uint32_t* rank
   return cudaGetLastError();
 }
 
-cudaError_t launch_emit_pairs_u32(const ushort4* rect, const uint32_t* offsets, const uint32_t* rank, int64_t n,
+cudaError_t launch_emit_pairs_u32(const ushort4* rect, const uint32_t* offsets, const uint32_t* order, int64_t n,
                                   int ntx, int rank_bits, uint32_t* keys, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_emit_pairs<uint32_t><<<grid_for(n, kThreads), kThreads, 0, s>>>(rect, offsets, rank, n, ntx, rank_bits, keys);
+  k_emit_pairs<uint32_t><<<grid_for(n, kThreads), kThreads, 0, s>>>(rect, offsets, order, n, ntx, rank_bits, keys);
   return cudaGetLastError();
 }
 
-cudaError_t launch_emit_pairs_u64(const ushort4* rect, const uint32_t* offsets, const uint32_t* rank, int64_t n,
+cudaError_t launch_emit_pairs_u64(const ushort4* rect, const uint32_t* offsets, const uint32_t* order, int64_t n,
                                   int ntx, int rank_bits, uint64_t* keys, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_emit_pairs<uint64_t><<<grid_for(n, kThreads), kThreads, 0, s>>>(rect, offsets, rank, n, ntx, rank_bits, keys);
+  k_emit_pairs<uint64_t><<<grid_for(n, kThreads), kThreads, 0, s>>>(rect, offsets, order, n, ntx, rank_bits, keys);
   return cudaGetLastError();
 }
 
@@ -510,24 +519,24 @@ cudaError_t launch_tile_ranges_u64(const uint64_t* keys, int64_t m, int rank_bit
   return cudaGetLastError();
 }
 
-cudaError_t launch_emit_pairs_batch(const EmitTable& t, int nkf, int64_t max_n, const ushort4* rect,
-                                    const uint32_t* offsets, const uint32_t* rank, int rank_bits, uint64_t capacity,
+cudaError_t launch_emit_pairs_batch(const EmitTable& t, int nkf, int64_t n, const ushort4* rect,
+                                    const uint32_t* offsets, const uint32_t* order, int rank_bits, uint64_t capacity,
                                     void* keys, bool k32, uint32_t* overflow, cudaStream_t s) {
-  if (nkf == 0 || max_n == 0) return cudaSuccess;
-  const dim3 grid(grid_for(max_n, kThreads), (unsigned)nkf);
+  if (nkf == 0 || n == 0) return cudaSuccess;
+  const unsigned grid = grid_for(n, kThreads);
   if (k32)
-    k_emit_pairs_batch<uint32_t><<<grid, kThreads, 0, s>>>(t, rect, offsets, rank, rank_bits, capacity,
+    k_emit_pairs_batch<uint32_t><<<grid, kThreads, 0, s>>>(t, nkf, rect, offsets, order, n, rank_bits, capacity,
                                                            static_cast<uint32_t*>(keys), overflow);
   else
-    k_emit_pairs_batch<uint64_t><<<grid, kThreads, 0, s>>>(t, rect, offsets, rank, rank_bits, capacity,
+    k_emit_pairs_batch<uint64_t><<<grid, kThreads, 0, s>>>(t, nkf, rect, offsets, order, n, rank_bits, capacity,
                                                            static_cast<uint64_t*>(keys), overflow);
   return cudaGetLastError();
 }
 
 cudaError_t radix_sort_u32_dev(uint32_t* keys_a, uint32_t* keys_b, int64_t n, int end_bit, uint32_t* scratch,
-                               int* sel, cudaStream_t s, const uint64_t* n_dev, uint32_t* err) {
+                               int* sel, cudaStream_t s, const uint64_t* n_dev, uint32_t* err, int begin_bit) {
   return radix_sort_impl<uint32_t, false>(keys_a, keys_b, nullptr, nullptr, n, end_bit, scratch, sel, s, n_dev,
-                                          nullptr, err);
+                                          nullptr, err, begin_bit);
 }
 
 }  // namespace dqo
