@@ -185,7 +185,7 @@ __device__ __forceinline__ uint64_t global_ns() {
 // before the pass; counter: this pass's tile counter, zero before the pass.  rank (optional,
 // with values): rank[value] = destination.  err: set to 1 if a look-back wait gave up.
 template <typename K, bool kVals, int IPT>
-__global__ void __launch_bounds__(kThreads) k_onesweep_pass(const K* __restrict__ kin, K* __restrict__ kout,
+__global__ void __launch_bounds__(kThreads, 3) k_onesweep_pass(const K* __restrict__ kin, K* __restrict__ kout,
                                                             const uint32_t* __restrict__ vin,
                                                             uint32_t* __restrict__ vout, int64_t n_cap,
                                                             const uint64_t* __restrict__ n_dev, int shift,
@@ -194,7 +194,9 @@ __global__ void __launch_bounds__(kThreads) k_onesweep_pass(const K* __restrict_
                                                             uint32_t* __restrict__ counter,
                                                             uint32_t* __restrict__ rank, uint32_t* __restrict__ err) {
   __shared__ uint32_t cnt[kThreads / 32][kRadixBins];
-  __shared__ uint32_t s_base[kRadixBins];
+  __shared__ uint32_t s_base[kRadixBins], s_lstart[kRadixBins];
+  __shared__ K s_key[kThreads * IPT];
+  __shared__ uint32_t s_val[kVals ? kThreads * IPT : 1];
   __shared__ uint32_t s_tile;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, t = threadIdx.x;
   if (t == 0) s_tile = atomicAdd(counter, 1u);
@@ -239,6 +241,9 @@ __global__ void __launch_bounds__(kThreads) k_onesweep_pass(const K* __restrict_
   }
   volatile uint32_t* st = status;
   st[(int64_t)tile * kRadixBins + t] = (tile == 0 ? kFlagInc : kFlagAgg) | total;
+  // the digit's start within the tile (keys of the tile in digit order)
+  uint32_t tile_n;
+  s_lstart[t] = block_exclusive_scan<uint32_t>(total, tile_n);
   // the digit's global start: exclusive scan of the pass's histogram over digits
   uint32_t gtot;
   const uint32_t gex = block_exclusive_scan<uint32_t>(ghist[t], gtot);
@@ -265,15 +270,26 @@ __global__ void __launch_bounds__(kThreads) k_onesweep_pass(const K* __restrict_
   }
   s_base[t] = gex + excl;
   __syncthreads();
+  // stage the tile's keys in digit order, then write each digit's run out contiguously
+  // (consecutive threads, consecutive addresses) instead of one scattered key per lane
 #pragma unroll
   for (int r = 0; r < IPT; ++r) {
     if (pos[r] == 0xFFFFFFFFu) continue;
     const uint32_t d = (uint32_t)(key[r] >> shift) & (kRadixBins - 1);
-    const uint32_t dst = s_base[d] + cnt[warp][d] + pos[r];
-    kout[dst] = key[r];
+    const uint32_t li = s_lstart[d] + cnt[warp][d] + pos[r];
+    s_key[li] = key[r];
+    if (kVals) s_val[li] = val[r];
+  }
+  __syncthreads();
+  for (uint32_t j = t; j < tile_n; j += kThreads) {
+    const K k = s_key[j];
+    const uint32_t d = (uint32_t)(k >> shift) & (kRadixBins - 1);
+    const uint32_t dst = s_base[d] + (j - s_lstart[d]);
+    kout[dst] = k;
     if (kVals) {
-      vout[dst] = val[r];
-      if (rank) rank[val[r]] = dst;
+      const uint32_t v = s_val[j];
+      vout[dst] = v;
+      if (rank) rank[v] = dst;
     }
   }
 }
