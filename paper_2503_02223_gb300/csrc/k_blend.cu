@@ -482,23 +482,49 @@ __device__ __forceinline__ int sched_bucket(uint32_t x) {
   return min(kSchedBuckets - 1, lz * 4 + (int)frac + 1);
 }
 
-// One CTA: counting sort of the tiles by decreasing bucket.
+// One CTA of kSchedThreads: counting sort of the tiles by decreasing bucket.  Each round
+// takes kSchedThreads * kSchedPer tiles with all their cost loads in flight; a warp's
+// lanes with equal buckets add to the bucket's counter once (match_any).
+constexpr int kSchedThreads = 1024, kSchedPer = 8;
+
 __device__ __forceinline__ void schedule_tiles(const uint2* __restrict__ ranges, const uint32_t* __restrict__ cost,
                                                int tiles, uint32_t* __restrict__ order) {
   __shared__ uint32_t s_h[kSchedBuckets];
-  auto cost_of = [&](int t) -> uint32_t {
-    if (cost) return cost[t];
-    const uint2 r = ranges[t];
-    return r.y > r.x ? r.y - r.x : 0u;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const uint32_t lt = lanemask_lt();
+  auto buckets = [&](int base, int (&b)[kSchedPer]) {
+    uint32_t c[kSchedPer];
+#pragma unroll
+    for (int j = 0; j < kSchedPer; ++j) {
+      const int t = base + j * kSchedThreads + tid;
+      c[j] = 0u;
+      if (t < tiles) {
+        if (cost) {
+          c[j] = cost[t];
+        } else {
+          const uint2 r = ranges[t];
+          c[j] = r.y > r.x ? r.y - r.x : 0u;
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kSchedPer; ++j) b[j] = base + j * kSchedThreads + tid < tiles ? sched_bucket(c[j]) : -1;
   };
-  for (int b = threadIdx.x; b < kSchedBuckets; b += blockDim.x) s_h[b] = 0u;
+  for (int b = tid; b < kSchedBuckets; b += kSchedThreads) s_h[b] = 0u;
   __syncthreads();
-  for (int t = threadIdx.x; t < tiles; t += blockDim.x) atomicAdd(&s_h[sched_bucket(cost_of(t))], 1u);
+  for (int base = 0; base < tiles; base += kSchedThreads * kSchedPer) {
+    int b[kSchedPer];
+    buckets(base, b);
+#pragma unroll
+    for (int j = 0; j < kSchedPer; ++j) {
+      const uint32_t peers = __match_any_sync(kFull, b[j]);
+      if (b[j] >= 0 && lane == __ffs(peers) - 1) atomicAdd(&s_h[b[j]], (uint32_t)__popc(peers));
+    }
+  }
   __syncthreads();
-  if (threadIdx.x < 32) {
+  if (tid < 32) {
     // exclusive scan in decreasing bucket order: lane l owns buckets 127-4l .. 124-4l
     constexpr int kPer = kSchedBuckets / 32;
-    const int lane = threadIdx.x;
     uint32_t v[kPer], sum = 0;
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
@@ -519,12 +545,24 @@ __device__ __forceinline__ void schedule_tiles(const uint2* __restrict__ ranges,
     }
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < tiles; t += blockDim.x) order[atomicAdd(&s_h[sched_bucket(cost_of(t))], 1u)] = t;
+  for (int base = 0; base < tiles; base += kSchedThreads * kSchedPer) {
+    int b[kSchedPer];
+    buckets(base, b);
+#pragma unroll
+    for (int j = 0; j < kSchedPer; ++j) {
+      const uint32_t peers = __match_any_sync(kFull, b[j]);
+      const int leader = __ffs(peers) - 1;
+      uint32_t p0 = 0u;
+      if (b[j] >= 0 && lane == leader) p0 = atomicAdd(&s_h[b[j]], (uint32_t)__popc(peers));
+      p0 = __shfl_sync(kFull, p0, leader);
+      if (b[j] >= 0) order[p0 + __popc(peers & lt)] = (uint32_t)(base + j * kSchedThreads + tid);
+    }
+  }
 }
 
-__global__ void __launch_bounds__(kThreads) k_tile_schedule(const uint2* __restrict__ ranges,
-                                                            const uint32_t* __restrict__ cost, int tiles,
-                                                            uint32_t* __restrict__ order) {
+__global__ void __launch_bounds__(kSchedThreads) k_tile_schedule(const uint2* __restrict__ ranges,
+                                                                 const uint32_t* __restrict__ cost, int tiles,
+                                                                 uint32_t* __restrict__ order) {
   schedule_tiles(ranges, cost, tiles, order);
 }
 
@@ -825,7 +863,7 @@ cudaError_t launch_blend_forward(const BlendFwdArgs& a, bool with_id, cudaStream
 cudaError_t launch_tile_schedule(const uint2* ranges, const uint32_t* cost, int tiles, uint32_t* order,
                                  cudaStream_t s) {
   if (tiles <= 0) return cudaSuccess;
-  k_tile_schedule<<<1, kThreads, 0, s>>>(ranges, cost, tiles, order);
+  k_tile_schedule<<<1, kSchedThreads, 0, s>>>(ranges, cost, tiles, order);
   return cudaGetLastError();
 }
 
@@ -865,7 +903,8 @@ unsigned persistent_grid(Kernel k, int ctas_per_sm, int sms, uint32_t total, cud
 
 // One CTA per keyframe of a step table: which = 0 orders t.f[k]'s tiles by list length
 // into t.f[k].tile_order, which = 1 by t.f[k].tile_cost into t.b[k].tile_order.
-__global__ void __launch_bounds__(kThreads) k_tile_schedule_batch(const __grid_constant__ StepTable t, int which) {
+__global__ void __launch_bounds__(kSchedThreads) k_tile_schedule_batch(const __grid_constant__ StepTable t,
+                                                                       int which) {
   const int k = blockIdx.x;
   const int tiles = (int)(t.tile_off[k + 1] - t.tile_off[k]);
   if (which == 0)
@@ -891,19 +930,19 @@ cudaError_t step_tw(const StepTable& t, const BlendCommon& cm, uint32_t* queue, 
   if (schedule == 0) {
     const unsigned grid = persistent_grid(k_blend_step<TW, kId>, ctas_per_sm, sms, total, &e);
     if (e != cudaSuccess) return e;
-    if (sched) k_tile_schedule<<<1, kThreads, 0, s>>>(t.f[0].ranges, nullptr, (int)total, f_order);
+    if (sched) k_tile_schedule<<<1, kSchedThreads, 0, s>>>(t.f[0].ranges, nullptr, (int)total, f_order);
     k_blend_step<TW, kId><<<grid, kThreads, 0, s>>>(t, cm, queue, f_order);
   } else if (schedule == 1) {
     unsigned grid = persistent_grid(k_blend_fwd_queue<TW, kId>, ctas_per_sm, sms, total, &e);
     if (e != cudaSuccess) return e;
-    if (sched) k_tile_schedule<<<1, kThreads, 0, s>>>(t.f[0].ranges, nullptr, (int)total, f_order);
+    if (sched) k_tile_schedule<<<1, kSchedThreads, 0, s>>>(t.f[0].ranges, nullptr, (int)total, f_order);
     k_blend_fwd_queue<TW, kId><<<grid, kThreads, 0, s>>>(t, cm, queue, f_order);
     grid = persistent_grid(k_blend_bwd_queue<TW>, ctas_per_sm, sms, total, &e);
     if (e != cudaSuccess) return e;
-    if (sched) k_tile_schedule<<<1, kThreads, 0, s>>>(nullptr, t.f[0].tile_cost, (int)total, b_order);
+    if (sched) k_tile_schedule<<<1, kSchedThreads, 0, s>>>(nullptr, t.f[0].tile_cost, (int)total, b_order);
     k_blend_bwd_queue<TW><<<grid, kThreads, 0, s>>>(t, cm, queue + 1, b_order);
   } else {
-    if (sched) k_tile_schedule_batch<<<(unsigned)t.nkf, kThreads, 0, s>>>(t, 0);
+    if (sched) k_tile_schedule_batch<<<(unsigned)t.nkf, kSchedThreads, 0, s>>>(t, 0);
     for (int k = 0; k < t.nkf; ++k) {
       const unsigned tiles = t.tile_off[k + 1] - t.tile_off[k];
       if (tiles == 0) continue;
@@ -915,7 +954,7 @@ cudaError_t step_tw(const StepTable& t, const BlendCommon& cm, uint32_t* queue, 
       f.list = cm.list;
       k_blend_forward<TW, kId><<<tiles, kThreads, 0, s>>>(f);
     }
-    if (sched) k_tile_schedule_batch<<<(unsigned)t.nkf, kThreads, 0, s>>>(t, 1);
+    if (sched) k_tile_schedule_batch<<<(unsigned)t.nkf, kSchedThreads, 0, s>>>(t, 1);
     for (int k = 0; k < t.nkf; ++k) {
       const unsigned tiles = t.tile_off[k + 1] - t.tile_off[k];
       if (tiles == 0) continue;
