@@ -57,9 +57,10 @@ __device__ __forceinline__ bool eval_alpha(const float4& p0, const float4& p1, f
 }
 
 template <int TW>
-__device__ __forceinline__ void pixel_of(int tile_x0, int tile_y0, int& px, int& py, float& wx0, float& wy0) {
+__device__ __forceinline__ void pixel_of(int tile_x0, int tile_y0, int& px, int& py, float& wx0, float& wy0,
+                                         int warp = threadIdx.x >> 5) {
   constexpr int WX = TW / 8;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const int bx = tile_x0 + (warp % WX) * 8, by = tile_y0 + (warp / WX) * 4;
   px = bx + (lane & 7);
   py = by + (lane >> 3);
@@ -611,22 +612,23 @@ __device__ __forceinline__ float warp_transpose_sum10(const float v[10]) {
 // atomics instead of a warp sum.
 constexpr int kFewLanes = 12;
 
-// Backward of one tile (local tile index); warp-autonomous, no block barrier.
-template <int TW>
-__device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const BlendCommon& cm, const int tile) {
-  constexpr int NW = kThreads / 32;
+// Backward of one tile's warp-blocks (local tile index); warp-autonomous, no block barrier.
+// The CTA holds NW warps; its warp w covers the tile's 8x4 block w0 + w.
+template <int TW, int NW = kThreads / 32>
+__device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const BlendCommon& cm, const int tile,
+                                               const int w0 = 0) {
   __shared__ float4 s_q0[NW][32], s_q1[NW][32], s_q2[NW][32];
   __shared__ uint32_t s_g[NW][32];
 
   const RasterParams& rp = a.rp;
   const int tx = tile % rp.ntx, ty = tile / rp.ntx;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int px, py;
   float wx0, wy0;
-  pixel_of<TW>(tx * rp.tile_w, ty * rp.tile_h, px, py, wx0, wy0);
+  pixel_of<TW>(tx * rp.tile_w, ty * rp.tile_h, px, py, wx0, wy0, w0 + warp);
   const bool inside = px < rp.W && py < rp.H;
   const int64_t pix = (int64_t)py * rp.W + px;
   const int start = (int)a.ranges[tile].x;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   uint32_t nc = 0;
   float T = 1.f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gD = 0.f, gA = 0.f, gI = 0.f;
@@ -757,11 +759,19 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const Blen
   }
 }
 
+// The backward kernel's CTAs hold kBwdWarps warps (a part of a tile): a CTA's resources
+// are freed only when its last warp ends, and the warps of one tile walk lists of very
+// different lengths.  CTA b covers part b % kBwdParts of the b / kBwdParts-th scheduled tile.
+constexpr int kBwdWarps = 4;
+constexpr int kBwdParts = kThreads / 32 / kBwdWarps;
+
 template <int TW>
-__global__ void __launch_bounds__(kThreads, 3) k_blend_backward(BlendBwdArgs a) {
+__global__ void __launch_bounds__(32 * kBwdWarps, 24 / kBwdWarps) k_blend_backward(BlendBwdArgs a) {
   const BlendCommon cm{a.p0, a.p1, a.p2, nullptr, a.list, a.grad2d, a.rp.alpha_clamp, a.rp.alpha_min, 0.f,
                        a.rp.og_filter};
-  blend_bwd_tile<TW>(a, cm, a.tile_order ? (int)a.tile_order[blockIdx.x] : (int)blockIdx.x);
+  const int u = (int)(blockIdx.x / kBwdParts);
+  blend_bwd_tile<TW, kBwdWarps>(a, cm, a.tile_order ? (int)a.tile_order[u] : u,
+                                (int)(blockIdx.x % kBwdParts) * kBwdWarps);
 }
 
 // Persistent step over the tiles of a batch of keyframes: each CTA takes tiles from an
@@ -877,9 +887,9 @@ cudaError_t launch_blend_backward(const BlendBwdArgs& a, cudaStream_t s) {
   const unsigned tiles = (unsigned)(a.rp.ntx * a.rp.nty);
   if (tiles == 0) return cudaSuccess;
   switch (a.rp.tile_w) {
-    case 8: k_blend_backward<8><<<tiles, kThreads, 0, s>>>(a); break;
-    case 16: k_blend_backward<16><<<tiles, kThreads, 0, s>>>(a); break;
-    case 32: k_blend_backward<32><<<tiles, kThreads, 0, s>>>(a); break;
+    case 8: k_blend_backward<8><<<tiles * kBwdParts, 32 * kBwdWarps, 0, s>>>(a); break;
+    case 16: k_blend_backward<16><<<tiles * kBwdParts, 32 * kBwdWarps, 0, s>>>(a); break;
+    case 32: k_blend_backward<32><<<tiles * kBwdParts, 32 * kBwdWarps, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -964,7 +974,7 @@ cudaError_t step_tw(const StepTable& t, const BlendCommon& cm, uint32_t* queue, 
       b.p2 = cm.p2;
       b.list = cm.list;
       b.grad2d = cm.grad2d;
-      k_blend_backward<TW><<<tiles, kThreads, 0, s>>>(b);
+      k_blend_backward<TW><<<tiles * kBwdParts, 32 * kBwdWarps, 0, s>>>(b);
     }
   }
   return cudaGetLastError();
