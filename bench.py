@@ -53,16 +53,17 @@ MLP_FLOPS_PER_SAMPLE = 2 * (128 * 128 + 128 * 128 + 9 * 128) + 2 * (2 * 9 * 128 
 # Bytes each HBM-bound phase of the step moves (design bytes, counted from the kernels):
 # projection: reads means 12, log-scales 12, quaternion 16, logit 4, rgb 12, id 4, flags 1;
 #   writes 3 x float4 48, rect 8, tiles 4, depth key 4, value 4, id 4        -> 133 B/Gaussian
-# depth sort: scan of tiles per Gaussian (read 4, write 4, read 4); 4 radix passes of
-#   (histogram read 4 + scatter read 8, write 8) on key+value; ranks written 4 -> 92 B/Gaussian
-# binning: emission reads rect 8, offset 4, rank 4 per Gaussian and writes 4 per pair; 4
-#   passes of (histogram read 4 + scatter read 4, write 4) per pair; ranges read key 4 and
-#   the order 4, write the list 4 per pair                                   -> 16 B/Gaussian + 64 B/pair
+# depth sort: one histogram kernel reads the keys 4; 4 radix passes read key+value 8 and
+#   write 8; the scan of tiles per Gaussian in depth order reads the order 4 and the count
+#   4 and writes the offset 4                                                -> 80 B/Gaussian
+# binning: emission reads order 4, rect 8, offset 4 per Gaussian and writes 4 per pair; the
+#   pair sort covers the tile bits only: histogram read 4 + 2 passes of (read 4, write 4);
+#   ranges read key 4 and the order 4, write the list 4 per pair             -> 16 B/Gaussian + 36 B/pair
 #   (the algorithmic minimum: write each pair's value once and read it once in the blend,
 #   8 B/pair, plus 16 B/Gaussian)
 # projection adjoint: reads the 10 inputs 61, tiles 4, moment record 48; read-modify-write of
 #   the 14 gradient floats 112                                              -> 225 B/Gaussian
-HBM_BYTES = {"project": (133, 0), "depth_sort": (92, 0), "binning": (16, 64), "project_bwd": (225, 0)}
+HBM_BYTES = {"project": (133, 0), "depth_sort": (80, 0), "binning": (16, 36), "project_bwd": (225, 0)}
 SORT_MIN_BYTES = (16, 8)
 MLP_TRAIN_SAMPLES = 1 << 20
 MLP_EPOCHS = 10
