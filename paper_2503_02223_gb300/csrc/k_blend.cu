@@ -766,7 +766,7 @@ constexpr int kBwdWarps = 4;
 constexpr int kBwdParts = kThreads / 32 / kBwdWarps;
 
 template <int TW>
-__global__ void __launch_bounds__(32 * kBwdWarps, 24 / kBwdWarps) k_blend_backward(BlendBwdArgs a) {
+__global__ void __launch_bounds__(32 * kBwdWarps, 28 / kBwdWarps) k_blend_backward(BlendBwdArgs a) {
   const BlendCommon cm{a.p0, a.p1, a.p2, nullptr, a.list, a.grad2d, a.rp.alpha_clamp, a.rp.alpha_min, 0.f,
                        a.rp.og_filter};
   const int u = (int)(blockIdx.x / kBwdParts);
