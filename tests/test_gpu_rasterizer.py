@@ -57,11 +57,29 @@ def test_tile_lists_bit_exact(tile):
     g, cam, t = tiny_case(width=333, height=251)
     r = Render(g, cam, 4, t, tile_w=tile[0], tile_h=tile[1])
     r.forward()
+    _check_tile_lists(r, 333, 251, tile)
+    r.close()
+
+
+def test_tile_lists_bit_exact_wide_keys():
+    """Depth-rank bits + tile bits above 32 (140k Gaussians, 49152 tiles): the pair keys are
+    64-bit and the pair sort still covers only the tile bits."""
+    g = synth.tiny_gaussians(1101, n=140000)
+    cam = synth.tiny_camera(width=4096, height=3072, f=3000.0)
+    r = Render(g, cam, 4, None)
+    r.forward()
+    m, nvis, ntiles = dqo.dqo_get_counts(r.ctx)
+    assert ntiles == 256 * 192 and int(nvis).bit_length() + int(ntiles - 1).bit_length() > 32
+    _check_tile_lists(r, 4096, 3072, (16, 16))
+    r.close()
+
+
+def _check_tile_lists(r, W, H, tile):
     P = r.proj()
     rect = r.buffer(dqo.DQO_BUF_RECT, np.uint16).reshape(-1, 4).astype(np.int32)
     vis = (rect[:, 2] > rect[:, 0]) & (rect[:, 3] > rect[:, 1])
     zbits = P[1, :, 2].copy().view(np.uint32)
-    ntx, nty = -(-333 // tile[0]), -(-251 // tile[1])
+    ntx, nty = -(-W // tile[0]), -(-H // tile[1])
     ranges_ref, list_ref = oracle.bin_tiles(rect, zbits, vis.astype(np.uint8), ntx, nty)
     ranges = r.buffer(dqo.DQO_BUF_TILE_RANGES, np.uint32).reshape(-1, 2).astype(np.int64)
     lst = r.buffer(dqo.DQO_BUF_TILE_LIST, np.uint32).astype(np.int64)
@@ -75,7 +93,6 @@ def test_tile_lists_bit_exact(tile):
     order = r.buffer(dqo.DQO_BUF_DEPTH_ORDER, np.uint32).astype(np.int64)
     key = np.where(vis, zbits, np.uint32(0xFFFFFFFF))
     assert np.array_equal(order, np.lexsort((np.arange(len(key)), key)))
-    r.close()
 
 
 def _forward_parity(g, cam, t, nobj, st_kw=None, id_check=True, min_ok=0.97):
