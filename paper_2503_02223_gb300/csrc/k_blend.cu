@@ -152,9 +152,31 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const Blen
   if (kId) {
     for (int t = tid; t < nw; t += kThreads) s_mask[t] = 0u;
     __syncthreads();
-    for (int i = start + tid; i < end; i += kThreads) {
-      const uint32_t id = cm.gid[cm.list[i]];
-      if (id != 0xFFFFFFFFu) atomicOr(&s_mask[id >> 5], 1u << (id & 31));
+    // four list entries per thread with their loads in flight; a warp whose ids all fall
+    // in one mask word ORs them together and adds them with one atomic
+    constexpr int kPre = 4;
+    for (int b = start; b < end; b += kPre * kThreads) {  // uniform trip count: warp intrinsics below
+      uint32_t id[kPre];
+#pragma unroll
+      for (int j = 0; j < kPre; ++j) {
+        const int i = b + j * kThreads + tid;
+        id[j] = i < end ? cm.list[i] : 0xFFFFFFFFu;
+      }
+#pragma unroll
+      for (int j = 0; j < kPre; ++j) id[j] = id[j] != 0xFFFFFFFFu ? cm.gid[id[j]] : 0xFFFFFFFFu;
+#pragma unroll
+      for (int j = 0; j < kPre; ++j) {
+        const bool has = id[j] != 0xFFFFFFFFu;
+        const uint32_t word = has ? id[j] >> 5 : 0u, bit = has ? 1u << (id[j] & 31) : 0u;
+        int same;
+        __match_all_sync(kFull, word, &same);
+        if (same) {
+          const uint32_t m = __reduce_or_sync(kFull, bit);
+          if (lane == 0 && m) atomicOr(&s_mask[word], m);
+        } else if (has) {
+          atomicOr(&s_mask[word], bit);
+        }
+      }
     }
     __syncthreads();
     if (tid < 32) {
