@@ -779,7 +779,6 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
 
   DQO_CUDA(c, cudaMemsetAsync(B.counters.p, 0, 64, s_));
   DQO_CUDA(c, cudaMemsetAsync(B.ranges.p, 0, 8 * T, s_));
-  DQO_CUDA(c, cudaMemsetAsync(B.grad2d.p, 0, 48 * (size_t)N, s_));
 
   // ---- quadric fits on the side stream, concurrent with the keyframes
   const bool run_fits = fits && fits->nq > 0;
@@ -804,6 +803,7 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
   pb.zval = as<uint32_t>(B.zval_a);
   pb.gid = as<uint32_t>(B.gid);
   pb.n_visible = d_nvis;
+  pb.grad2d = as<float4>(B.grad2d);  // zeroed by the projection, for binned Gaussians only
   {
     PhaseTimer timer(c, DQO_PHASE_PROJECT, s_);
     PreTable pt;

@@ -86,6 +86,7 @@ struct ProjBuffers {
   uint32_t* zval;    // depth sort values: Gaussian index
   uint32_t* gid;     // object id (kNoObject if none) for the id-map prepass
   uint32_t* n_visible;
+  float4* grad2d = nullptr;  // if set: each binned Gaussian's backward moment record is zeroed
 };
 
 struct BlendFwdArgs {

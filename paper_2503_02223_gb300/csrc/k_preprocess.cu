@@ -187,6 +187,12 @@ __device__ __forceinline__ void preprocess_item(const RasterParams& rp, const dq
     o.zkey[j] = f.visible ? __float_as_uint(f.pc[2]) : 0xFFFFFFFFu;
     o.zval[j] = (uint32_t)j;
     o.gid[j] = has_obj ? (uint32_t)id : 0xFFFFFFFFu;
+    if (o.grad2d && f.ntiles > 0) {  // only binned Gaussians receive (and are read for) moments
+      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      o.grad2d[3 * j] = z;
+      o.grad2d[3 * j + 1] = z;
+      o.grad2d[3 * j + 2] = z;
+    }
   }
   const uint32_t vis = __ballot_sync(0xFFFFFFFFu, in && f.visible);
   if (lane == 0 && vis) atomicAdd(o.n_visible, (uint32_t)__popc(vis));
