@@ -235,12 +235,13 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const Blen
   // Stages, in list order, the Gaussians of list chunk [c, c+32) that can reach this warp's
   // pixels and sit before list position `lim`; returns how many.  q1.w holds the key and
   // q2.w the list position (both consumed at staging otherwise).
-  auto stage = [&](int c, int lim) -> int {
+  // gi: list entry c + lane, already loaded by the caller (read only below lim).
+  auto stage = [&](int c, int lim, uint32_t gi) -> int {
     const int i = c + lane;
     bool hit = false;
     float4 q0, q1, q2;
     if (i < lim) {
-      const uint32_t g = cm.list[i];
+      const uint32_t g = gi;
       q0 = cm.p0[g];
       q1 = cm.p1[g];
       q2 = cm.p2[g];
@@ -289,9 +290,12 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const Blen
   // ---- front to back, each warp on its own: no block-wide barrier inside the walk.  kFwdIlp
   // staged Gaussians per iteration: their exponentials are independent, only the blending
   // is sequential.
+  // the next chunk's list entries are loaded while the current chunk is blended
+  uint32_t gnext = start + lane < end ? cm.list[start + lane] : 0u;
   for (int c = start; c < end; c += 32) {
     if (__all_sync(kFull, done)) break;
-    const int nh = stage(c, end);
+    const int nh = stage(c, end, gnext);
+    if (c + 32 + lane < end) gnext = cm.list[c + 32 + lane];
     for (int h = 0; h < nh; h += kFwdIlp) {
       if (done) continue;
       // slots h .. h + kFwdIlp - 1 <= 31 are inside the staging arrays even past nh
@@ -337,7 +341,7 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const Blen
         __syncthreads();
         float Tr = 1.f;
         for (int c = start; c < start + wlast; c += 32) {
-          const int nh = stage(c, start + wlast);
+          const int nh = stage(c, start + wlast, c + lane < start + wlast ? cm.list[c + lane] : 0u);
           for (int h = 0; h < nh; ++h) {
             if (__float_as_int(s_q2[warp][h].w) >= last) continue;
             float alpha, G, dx, dy;
@@ -683,13 +687,16 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const Blen
   const int src2 = lane == 1 ? 20 : 8;
   const int src3 = lane == 1 ? 24 : 12;
 
-  for (int c = (wmax - 1) & ~31; c >= 0 && wmax > 0; c -= 32) {
+  // the next (earlier) chunk's list entries are loaded while the current one is processed
+  const int c0 = (wmax - 1) & ~31;
+  uint32_t gnext = wmax > 0 && c0 + lane < wmax ? cm.list[start + c0 + lane] : 0u;
+  for (int c = c0; c >= 0 && wmax > 0; c -= 32) {
     const int jl = c + lane;
     bool hit = false;
     float4 q0, q1, q2;
     uint32_t g = 0;
     if (jl < wmax) {
-      g = cm.list[start + jl];
+      g = gnext;
       q0 = cm.p0[g];
       q1 = cm.p1[g];
       q2 = cm.p2[g];
@@ -707,6 +714,7 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const Blen
       s_g[warp][k] = g;
     }
     __syncwarp();
+    if (c >= 32) gnext = cm.list[start + c - 32 + lane];  // below c <= wmax - 1: in the list
     // staged slots [0, hlim) hold this lane's contributors (list positions below nc): the
     // slots are in list order and slot k came from chunk lane k's position c + k
     const int below = (int)nc - c;
