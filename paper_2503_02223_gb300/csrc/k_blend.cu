@@ -451,6 +451,8 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const Blen
 
 template <int TW, bool kId>
 __global__ void __launch_bounds__(kThreads) k_blend_forward(BlendFwdArgs a) {
+  pdl_wait();
+  pdl_trigger();
   const BlendCommon cm{a.p0, a.p1, a.p2, a.gid, a.list, nullptr, a.rp.alpha_clamp, a.rp.alpha_min, a.rp.t_stop,
                        a.rp.og_filter};
   blend_fwd_tile<TW, kId>(a, cm, a.tile_order ? (int)a.tile_order[blockIdx.x] : (int)blockIdx.x);
@@ -484,11 +486,15 @@ __device__ __forceinline__ void loss_reduce(const float* __restrict__ part, int 
 
 __global__ void k_loss_reduce(const float* __restrict__ part, int tiles, float lambda_ins, float scale,
                               float* __restrict__ loss) {
+  pdl_wait();
+  pdl_trigger();
   loss_reduce(part, tiles, lambda_ins, scale, loss);
 }
 
 // One block per keyframe of a batch.
 __global__ void k_loss_reduce_batch(const __grid_constant__ LossTable t) {
+  pdl_wait();
+  pdl_trigger();
   const LossKf& k = t.kf[blockIdx.x];
   if (k.loss) loss_reduce(k.part, k.tiles, k.lambda_ins, k.scale, k.loss);
 }
@@ -590,6 +596,8 @@ __device__ __forceinline__ void schedule_tiles(const uint2* __restrict__ ranges,
 __global__ void __launch_bounds__(kSchedThreads) k_tile_schedule(const uint2* __restrict__ ranges,
                                                                  const uint32_t* __restrict__ cost, int tiles,
                                                                  uint32_t* __restrict__ order) {
+  pdl_wait();
+  pdl_trigger();
   schedule_tiles(ranges, cost, tiles, order);
 }
 
@@ -797,6 +805,8 @@ constexpr int kBwdParts = kThreads / 32 / kBwdWarps;
 
 template <int TW>
 __global__ void __launch_bounds__(32 * kBwdWarps, 28 / kBwdWarps) k_blend_backward(BlendBwdArgs a) {
+  pdl_wait();
+  pdl_trigger();
   const BlendCommon cm{a.p0, a.p1, a.p2, nullptr, a.list, a.grad2d, a.rp.alpha_clamp, a.rp.alpha_min, 0.f,
                        a.rp.og_filter};
   const int u = (int)(blockIdx.x / kBwdParts);
@@ -815,6 +825,8 @@ template <int TW, bool kId>
 __global__ void __launch_bounds__(kThreads, 4) k_blend_step(const __grid_constant__ StepTable t, BlendCommon cm,
                                                             uint32_t* __restrict__ queue,
                                                             const uint32_t* __restrict__ order) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t s_item;
   const uint32_t total = t.tile_off[t.nkf];
   for (;;) {
@@ -840,6 +852,8 @@ template <int TW, bool kId>
 __global__ void __launch_bounds__(kThreads) k_blend_fwd_queue(const __grid_constant__ StepTable t, BlendCommon cm,
                                                               uint32_t* __restrict__ queue,
                                                               const uint32_t* __restrict__ order) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t s_item;
   const uint32_t total = t.tile_off[t.nkf];
   for (;;) {
@@ -861,6 +875,8 @@ template <int TW>
 __global__ void __launch_bounds__(kThreads, 4) k_blend_bwd_queue(const __grid_constant__ StepTable t, BlendCommon cm,
                                                               uint32_t* __restrict__ queue,
                                                               const uint32_t* __restrict__ order) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t s_item;
   const uint32_t total = t.tile_off[t.nkf];
   for (;;) {
@@ -882,9 +898,9 @@ template <int TW>
 cudaError_t launch_fwd_tw(const BlendFwdArgs& a, bool with_id, cudaStream_t s) {
   const unsigned tiles = (unsigned)(a.rp.ntx * a.rp.nty);
   if (with_id)
-    k_blend_forward<TW, true><<<tiles, kThreads, 0, s>>>(a);
+    launch_dep(k_blend_forward<TW, true>, dim3(tiles), dim3(kThreads), s, a);
   else
-    k_blend_forward<TW, false><<<tiles, kThreads, 0, s>>>(a);
+    launch_dep(k_blend_forward<TW, false>, dim3(tiles), dim3(kThreads), s, a);
   return cudaGetLastError();
 }
 
@@ -903,13 +919,13 @@ cudaError_t launch_blend_forward(const BlendFwdArgs& a, bool with_id, cudaStream
 cudaError_t launch_tile_schedule(const uint2* ranges, const uint32_t* cost, int tiles, uint32_t* order,
                                  cudaStream_t s) {
   if (tiles <= 0) return cudaSuccess;
-  k_tile_schedule<<<1, kSchedThreads, 0, s>>>(ranges, cost, tiles, order);
+  launch_dep(k_tile_schedule, dim3(1), dim3(kSchedThreads), s, ranges, cost, tiles, order);
   return cudaGetLastError();
 }
 
 cudaError_t launch_loss_reduce(const float* part, int tiles, float lambda_ins, float scale, float* loss,
                                cudaStream_t s) {
-  k_loss_reduce<<<1, kThreads, 0, s>>>(part, tiles, lambda_ins, scale, loss);
+  launch_dep(k_loss_reduce, dim3(1), dim3(kThreads), s, part, tiles, lambda_ins, scale, loss);
   return cudaGetLastError();
 }
 
@@ -917,9 +933,9 @@ cudaError_t launch_blend_backward(const BlendBwdArgs& a, cudaStream_t s) {
   const unsigned tiles = (unsigned)(a.rp.ntx * a.rp.nty);
   if (tiles == 0) return cudaSuccess;
   switch (a.rp.tile_w) {
-    case 8: k_blend_backward<8><<<tiles * kBwdParts, 32 * kBwdWarps, 0, s>>>(a); break;
-    case 16: k_blend_backward<16><<<tiles * kBwdParts, 32 * kBwdWarps, 0, s>>>(a); break;
-    case 32: k_blend_backward<32><<<tiles * kBwdParts, 32 * kBwdWarps, 0, s>>>(a); break;
+    case 8: launch_dep(k_blend_backward<8>, dim3(tiles * kBwdParts), dim3(32 * kBwdWarps), s, a); break;
+    case 16: launch_dep(k_blend_backward<16>, dim3(tiles * kBwdParts), dim3(32 * kBwdWarps), s, a); break;
+    case 32: launch_dep(k_blend_backward<32>, dim3(tiles * kBwdParts), dim3(32 * kBwdWarps), s, a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -945,6 +961,8 @@ unsigned persistent_grid(Kernel k, int ctas_per_sm, int sms, uint32_t total, cud
 // into t.f[k].tile_order, which = 1 by t.f[k].tile_cost into t.b[k].tile_order.
 __global__ void __launch_bounds__(kSchedThreads) k_tile_schedule_batch(const __grid_constant__ StepTable t,
                                                                        int which) {
+  pdl_wait();
+  pdl_trigger();
   const int k = blockIdx.x;
   const int tiles = (int)(t.tile_off[k + 1] - t.tile_off[k]);
   if (which == 0)
@@ -970,19 +988,22 @@ cudaError_t step_tw(const StepTable& t, const BlendCommon& cm, uint32_t* queue, 
   if (schedule == 0) {
     const unsigned grid = persistent_grid(k_blend_step<TW, kId>, ctas_per_sm, sms, total, &e);
     if (e != cudaSuccess) return e;
-    if (sched) k_tile_schedule<<<1, kSchedThreads, 0, s>>>(t.f[0].ranges, nullptr, (int)total, f_order);
+    if (sched)
+      launch_dep(k_tile_schedule, dim3(1), dim3(kSchedThreads), s, t.f[0].ranges, nullptr, (int)total, f_order);
     k_blend_step<TW, kId><<<grid, kThreads, 0, s>>>(t, cm, queue, f_order);
   } else if (schedule == 1) {
     unsigned grid = persistent_grid(k_blend_fwd_queue<TW, kId>, ctas_per_sm, sms, total, &e);
     if (e != cudaSuccess) return e;
-    if (sched) k_tile_schedule<<<1, kSchedThreads, 0, s>>>(t.f[0].ranges, nullptr, (int)total, f_order);
+    if (sched)
+      launch_dep(k_tile_schedule, dim3(1), dim3(kSchedThreads), s, t.f[0].ranges, nullptr, (int)total, f_order);
     k_blend_fwd_queue<TW, kId><<<grid, kThreads, 0, s>>>(t, cm, queue, f_order);
     grid = persistent_grid(k_blend_bwd_queue<TW>, ctas_per_sm, sms, total, &e);
     if (e != cudaSuccess) return e;
-    if (sched) k_tile_schedule<<<1, kSchedThreads, 0, s>>>(nullptr, t.f[0].tile_cost, (int)total, b_order);
+    if (sched)
+      launch_dep(k_tile_schedule, dim3(1), dim3(kSchedThreads), s, nullptr, t.f[0].tile_cost, (int)total, b_order);
     k_blend_bwd_queue<TW><<<grid, kThreads, 0, s>>>(t, cm, queue + 1, b_order);
   } else {
-    if (sched) k_tile_schedule_batch<<<(unsigned)t.nkf, kSchedThreads, 0, s>>>(t, 0);
+    if (sched) launch_dep(k_tile_schedule_batch, dim3((unsigned)t.nkf), dim3(kSchedThreads), s, t, 0);
     for (int k = 0; k < t.nkf; ++k) {
       const unsigned tiles = t.tile_off[k + 1] - t.tile_off[k];
       if (tiles == 0) continue;
@@ -992,9 +1013,9 @@ cudaError_t step_tw(const StepTable& t, const BlendCommon& cm, uint32_t* queue, 
       f.p2 = cm.p2;
       f.gid = cm.gid;
       f.list = cm.list;
-      k_blend_forward<TW, kId><<<tiles, kThreads, 0, s>>>(f);
+      launch_dep(k_blend_forward<TW, kId>, dim3(tiles), dim3(kThreads), s, f);
     }
-    if (sched) k_tile_schedule_batch<<<(unsigned)t.nkf, kSchedThreads, 0, s>>>(t, 1);
+    if (sched) launch_dep(k_tile_schedule_batch, dim3((unsigned)t.nkf), dim3(kSchedThreads), s, t, 1);
     for (int k = 0; k < t.nkf; ++k) {
       const unsigned tiles = t.tile_off[k + 1] - t.tile_off[k];
       if (tiles == 0) continue;
@@ -1004,7 +1025,7 @@ cudaError_t step_tw(const StepTable& t, const BlendCommon& cm, uint32_t* queue, 
       b.p2 = cm.p2;
       b.list = cm.list;
       b.grad2d = cm.grad2d;
-      k_blend_backward<TW><<<tiles * kBwdParts, 32 * kBwdWarps, 0, s>>>(b);
+      launch_dep(k_blend_backward<TW>, dim3(tiles * kBwdParts), dim3(32 * kBwdWarps), s, b);
     }
   }
   return cudaGetLastError();
@@ -1027,7 +1048,7 @@ cudaError_t launch_blend_step(const StepTable& t, const BlendCommon& cm, uint32_
 
 cudaError_t launch_loss_reduce_batch(const LossTable& t, int nkf, cudaStream_t s) {
   if (nkf == 0) return cudaSuccess;
-  k_loss_reduce_batch<<<(unsigned)nkf, kThreads, 0, s>>>(t);
+  launch_dep(k_loss_reduce_batch, dim3((unsigned)nkf), dim3(kThreads), s, t);
   return cudaGetLastError();
 }
 

@@ -205,6 +205,8 @@ __global__ void __launch_bounds__(kThreads) k_preprocess(RasterParams rp, dqo_ga
 
 // Keyframe blockIdx.y of a batch.
 __global__ void __launch_bounds__(kThreads) k_preprocess_batch(const __grid_constant__ PreTable t, ProjBuffers o) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ float stage[kThreads / 32][96];
   const PreKf& kf = t.kf[blockIdx.y];
   if ((int64_t)blockIdx.x * kThreads >= kf.g.n) return;  // uniform over the block
@@ -319,6 +321,8 @@ __global__ void __launch_bounds__(kThreads) k_preprocess_backward(PreBwdArgs a) 
 // Keyframe blockIdx.y of a batch (its ntiles and grad2d pointers already offset to its
 // first Gaussian); gradients added atomically.
 __global__ void __launch_bounds__(kThreads) k_preprocess_backward_batch(const __grid_constant__ PreBwdTable t) {
+  pdl_wait();
+  pdl_trigger();
   preprocess_backward_item<true>(t.kf[blockIdx.y], (int64_t)blockIdx.x * kThreads + threadIdx.x);
 }
 
@@ -336,14 +340,14 @@ cudaError_t launch_preprocess_batch(const PreTable& t, int nkf, int64_t max_n, c
                                     cudaStream_t s) {
   if (nkf == 0 || max_n == 0) return cudaSuccess;
   const dim3 grid((unsigned)((max_n + kThreads - 1) / kThreads), (unsigned)nkf);
-  k_preprocess_batch<<<grid, kThreads, 0, s>>>(t, out);
+  launch_dep(k_preprocess_batch, dim3(grid), dim3(kThreads), s, t, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_preprocess_backward_batch(const PreBwdTable& t, int nkf, int64_t max_n, cudaStream_t s) {
   if (nkf == 0 || max_n == 0) return cudaSuccess;
   const dim3 grid((unsigned)((max_n + kThreads - 1) / kThreads), (unsigned)nkf);
-  k_preprocess_backward_batch<<<grid, kThreads, 0, s>>>(t);
+  launch_dep(k_preprocess_backward_batch, dim3(grid), dim3(kThreads), s, t);
   return cudaGetLastError();
 }
 

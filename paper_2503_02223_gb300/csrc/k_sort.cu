@@ -64,6 +64,8 @@ __global__ void __launch_bounds__(kThreads) k_scan_lookback(const uint32_t* __re
                                                             uint64_t* __restrict__ status,
                                                             uint32_t* __restrict__ counter,
                                                             uint32_t* __restrict__ err, uint64_t* __restrict__ total) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t tile_s[kSortTile];
   __shared__ uint32_t s_tile;
   __shared__ uint64_t s_prefix;
@@ -154,6 +156,8 @@ template <typename K, int IPT>
 __global__ void __launch_bounds__(kThreads) k_onesweep_hist(const K* __restrict__ keys, int64_t n_cap,
                                                             const uint64_t* __restrict__ n_dev, int begin_bit,
                                                             int passes, uint32_t* __restrict__ ghist) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t h[kMaxRadixPasses][kRadixBins];
   for (int i = threadIdx.x; i < passes * kRadixBins; i += kThreads) (&h[0][0])[i] = 0;
   __syncthreads();
@@ -193,6 +197,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep_pass(const K* __restri
                                                             uint32_t* __restrict__ status,
                                                             uint32_t* __restrict__ counter,
                                                             uint32_t* __restrict__ rank, uint32_t* __restrict__ err) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t cnt[kThreads / 32][kRadixBins];
   __shared__ uint32_t s_base[kRadixBins], s_lstart[kRadixBins];
   __shared__ K s_key[kThreads * IPT];
@@ -337,6 +343,8 @@ __global__ void __launch_bounds__(kThreads) k_emit_pairs(const ushort4* __restri
                                                          const uint32_t* __restrict__ offsets,
                                                          const uint32_t* __restrict__ order, int64_t n, int ntx,
                                                          int rank_bits, K* __restrict__ keys) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   ushort4 q = make_ushort4(0, 0, 0, 0);
   uint64_t o = 0;
@@ -362,6 +370,8 @@ __global__ void __launch_bounds__(kThreads) k_emit_pairs_batch(const __grid_cons
                                                                const uint32_t* __restrict__ order, int64_t n,
                                                                int rank_bits, uint64_t capacity, K* __restrict__ keys,
                                                                uint32_t* __restrict__ overflow) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   ushort4 q = make_ushort4(0, 0, 0, 0);
   uint64_t o = 0;
@@ -388,6 +398,8 @@ __global__ void __launch_bounds__(kThreads) k_tile_ranges(const K* __restrict__ 
                                                           const uint64_t* __restrict__ m_dev, int rank_bits,
                                                           const uint32_t* __restrict__ order,
                                                           uint2* __restrict__ ranges, uint32_t* __restrict__ list) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t m = live_count(m_cap, m_dev);
   const int64_t p = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (p >= m) return;
@@ -421,11 +433,11 @@ cudaError_t radix_passes(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n, in
   uint32_t* err = err_out ? err_out : counters + passes;
   cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * onesweep_words(nb, passes), s);
   if (e != cudaSuccess) return e;
-  k_onesweep_hist<K, IPT><<<nb, kThreads, 0, s>>>(ka, n, n_dev, begin_bit, passes, ghist);
+  launch_dep(k_onesweep_hist<K, IPT>, dim3(nb), dim3(kThreads), s, ka, n, n_dev, begin_bit, passes, ghist);
   K* kin = ka; K* kout = kb;
   uint32_t* vin = va; uint32_t* vout = vb;
   for (int p = 0; p < passes; ++p) {
-    k_onesweep_pass<K, kVals, IPT><<<nb, kThreads, 0, s>>>(kin, kout, vin, vout, n, n_dev,
+    launch_dep(k_onesweep_pass<K, kVals, IPT>, dim3(nb), dim3(kThreads), s, kin, kout, vin, vout, n, n_dev,
                                                            begin_bit + p * kRadixBits,
                                                            ghist + p * kRadixBins,
                                                            status + (size_t)p * nb * kRadixBins, counters + p,
@@ -468,7 +480,7 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, 
   cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(uint64_t) * (nb + 2), s);
   if (e != cudaSuccess) return e;
   uint32_t* counter = reinterpret_cast<uint32_t*>(scratch + nb);
-  k_scan_lookback<<<nb, kThreads, 0, s>>>(in, gather, out, n, scratch, counter,
+  launch_dep(k_scan_lookback, dim3(nb), dim3(kThreads), s, in, gather, out, n, scratch, counter,
                                           err ? err : reinterpret_cast<uint32_t*>(scratch + nb + 1), total);
   return cudaGetLastError();
 }
@@ -508,21 +520,24 @@ cudaError_t launch_rank_scatter(const uint32_t* order, int64_t n, uint32_t* rank
 cudaError_t launch_emit_pairs_u32(const ushort4* rect, const uint32_t* offsets, const uint32_t* order, int64_t n,
                                   int ntx, int rank_bits, uint32_t* keys, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_emit_pairs<uint32_t><<<grid_for(n, kThreads), kThreads, 0, s>>>(rect, offsets, order, n, ntx, rank_bits, keys);
+  launch_dep(k_emit_pairs<uint32_t>, dim3(grid_for(n, kThreads)), dim3(kThreads), s, rect, offsets, order, n, ntx,
+             rank_bits, keys);
   return cudaGetLastError();
 }
 
 cudaError_t launch_emit_pairs_u64(const ushort4* rect, const uint32_t* offsets, const uint32_t* order, int64_t n,
                                   int ntx, int rank_bits, uint64_t* keys, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_emit_pairs<uint64_t><<<grid_for(n, kThreads), kThreads, 0, s>>>(rect, offsets, order, n, ntx, rank_bits, keys);
+  launch_dep(k_emit_pairs<uint64_t>, dim3(grid_for(n, kThreads)), dim3(kThreads), s, rect, offsets, order, n, ntx,
+             rank_bits, keys);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tile_ranges_u32(const uint32_t* keys, int64_t m, int rank_bits, const uint32_t* order,
                                    uint2* ranges, uint32_t* list, cudaStream_t s, const uint64_t* m_dev) {
   if (m == 0) return cudaSuccess;
-  k_tile_ranges<uint32_t><<<grid_for(m, kThreads), kThreads, 0, s>>>(keys, m, m_dev, rank_bits, order, ranges,
+  launch_dep(k_tile_ranges<uint32_t>, dim3(grid_for(m, kThreads)), dim3(kThreads), s, keys, m, m_dev, rank_bits, order,
+             ranges,
                                                                        list);
   return cudaGetLastError();
 }
@@ -530,7 +545,8 @@ cudaError_t launch_tile_ranges_u32(const uint32_t* keys, int64_t m, int rank_bit
 cudaError_t launch_tile_ranges_u64(const uint64_t* keys, int64_t m, int rank_bits, const uint32_t* order,
                                    uint2* ranges, uint32_t* list, cudaStream_t s, const uint64_t* m_dev) {
   if (m == 0) return cudaSuccess;
-  k_tile_ranges<uint64_t><<<grid_for(m, kThreads), kThreads, 0, s>>>(keys, m, m_dev, rank_bits, order, ranges,
+  launch_dep(k_tile_ranges<uint64_t>, dim3(grid_for(m, kThreads)), dim3(kThreads), s, keys, m, m_dev, rank_bits, order,
+             ranges,
                                                                        list);
   return cudaGetLastError();
 }
@@ -541,10 +557,12 @@ cudaError_t launch_emit_pairs_batch(const EmitTable& t, int nkf, int64_t n, cons
   if (nkf == 0 || n == 0) return cudaSuccess;
   const unsigned grid = grid_for(n, kThreads);
   if (k32)
-    k_emit_pairs_batch<uint32_t><<<grid, kThreads, 0, s>>>(t, nkf, rect, offsets, order, n, rank_bits, capacity,
+    launch_dep(k_emit_pairs_batch<uint32_t>, dim3(grid), dim3(kThreads), s, t, nkf, rect, offsets, order, n, rank_bits,
+               capacity,
                                                            static_cast<uint32_t*>(keys), overflow);
   else
-    k_emit_pairs_batch<uint64_t><<<grid, kThreads, 0, s>>>(t, nkf, rect, offsets, order, n, rank_bits, capacity,
+    launch_dep(k_emit_pairs_batch<uint64_t>, dim3(grid), dim3(kThreads), s, t, nkf, rect, offsets, order, n, rank_bits,
+               capacity,
                                                            static_cast<uint64_t*>(keys), overflow);
   return cudaGetLastError();
 }
