@@ -63,7 +63,7 @@ MLP_FLOPS_PER_SAMPLE = 2 * (128 * 128 + 128 * 128 + 9 * 128) + 2 * (2 * 9 * 128 
 #   8 B/pair, plus 16 B/Gaussian)
 # projection adjoint: reads the 10 inputs 61, tiles 4, moment record 48; read-modify-write of
 #   the 14 gradient floats 112                                              -> 225 B/Gaussian
-REF_BUDGET_S = 150.0   # the reference arm's K + W steps take about this long
+REF_BUDGET_S = 240.0   # the reference arm's K + W steps take about this long
 HBM_BYTES = {"project": (133, 0), "depth_sort": (80, 0), "binning": (16, 36), "project_bwd": (225, 0)}
 SORT_MIN_BYTES = (16, 8)
 MLP_TRAIN_SAMPLES = 1 << 20
