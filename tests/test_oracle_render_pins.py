@@ -1,7 +1,7 @@
 """Pins of the FP64 rasterizer oracle against facts fixed outside the oracle itself:
 closed-form Gaussian integrals and moments, a numerically differentiated pinhole map,
 scipy's quaternion rotation, invariants of alpha compositing, brute force, and
-central finite differences of every gradient (SURVEY-free: each test states the fact).
+central finite differences of every gradient; each test states the fact it checks.
 """
 import numpy as np
 import pytest
