@@ -284,3 +284,22 @@ def test_update_masks_eq11():
     assert (ref["update_mask"] & 1).any() and (ref["update_mask"] & 2).any() and (ref["update_mask"] == 0).any()
     assert np.all(out["update_mask"][t["gt_id"] < 0] == 0)
     r.close()
+
+
+def test_update_masks_golden_cases():
+    # the CUDA path on the cases of tests/golden/eq11_update_masks.txt (Eq. 11, thresholds
+    # as printed after it), against the fixture's expected bits
+    from golden_cases import eq11_case, read_fixture
+    consts, rows = read_fixture("eq11_update_masks.txt")
+    st_kw = dict(theta_alpha=consts["theta_alpha"], theta_d=consts["theta_d"], theta_c=consts["theta_c"])
+    default = dqo.settings()
+    assert abs(default.theta_d - consts["theta_d"]) < 1e-7 and abs(default.theta_c - consts["theta_c"]) < 1e-7
+    for a, dd, dc, geo, rgb in rows:
+        g, cam, t, (y, x) = eq11_case(a, dd, dc)
+        r = Render(g, cam, 4, t, **st_kw)
+        r.out["update_mask"] = torch.empty(cam["height"], cam["width"], dtype=torch.uint8, device="cuda")
+        out = r.forward()
+        assert abs(out["ins"][y, x] - a) < 1e-6
+        assert out["update_mask"][y, x] == int(geo) | (int(rgb) << 1), (a, dd, dc)
+        assert np.all(out["update_mask"][t["gt_id"] < 0] == 0)
+        r.close()

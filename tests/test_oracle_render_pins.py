@@ -269,3 +269,20 @@ def test_render_backward_finite_differences_fused_loss_with_background():
 
     b = oracle.render_backward(g, cam, st, tg)
     _fd_check(g, cam, st, value, b)
+
+
+def test_eq11_update_masks_golden_cases():
+    # Eq. 11's masks at one labelled pixel for the cases of tests/golden/eq11_update_masks.txt
+    # (thresholds theta_d = theta_c = 0.1 as printed after Eq. 11), and the oracle's default
+    # thresholds are the printed ones
+    from golden_cases import eq11_case, read_fixture
+    consts, rows = read_fixture("eq11_update_masks.txt")
+    assert oracle.DEFAULTS["theta_d"] == consts["theta_d"] and oracle.DEFAULTS["theta_c"] == consts["theta_c"]
+    st = oracle.settings(num_objects=4, theta_d=consts["theta_d"], theta_c=consts["theta_c"],
+                         theta_alpha=consts["theta_alpha"])
+    for a, dd, dc, geo, rgb in rows:
+        g, cam, t, (y, x) = eq11_case(a, dd, dc)
+        r = oracle.render(g, cam, st, t)
+        assert abs(r["ins"][y, x] - a) < 1e-12            # the case's premise: ins = alpha
+        assert r["update_mask"][y, x] == int(geo) | (int(rgb) << 1), (a, dd, dc)
+        assert np.all(r["update_mask"][t["gt_id"] < 0] == 0)
