@@ -160,6 +160,25 @@ def make_workload():
     return kf, targets
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest of the ranks' values of x (the job lasts as long as its slowest rank);
+    x itself on one rank.  device: where the process group's backend reduces (cuda for
+    NCCL, cpu for gloo)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps: int, total_ms: float) -> float:
+    """Whole-job units per second: every rank runs `steps` steps of one unit (weak
+    scaling), the job taking total_ms (the slowest rank's time)."""
+    return world * steps / (total_ms / 1e3)
+
+
 def oracle_full_parallel(kf, targets, threads: int, bands=None) -> tuple[float, int]:
     """FP64 oracle forward + backward of the whole image (or of the given (first row, rows)
     bands) with its rows split into bands of whole tile rows run concurrently on `threads`
@@ -400,13 +419,9 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    total_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1e3)
+    value = job_throughput(world, args.steps, total_ms)
     phases = {k: v / args.steps for k, v in phase_sum.items() if v > 0}
     phase_source = "event-record nodes of the replayed graph"
     if not graph_timing:
@@ -543,12 +558,8 @@ def run_ours(args, rank, world, local_rank):
     run_e2e(e_steps)
     e1.record(stream)
     torch.cuda.synchronize()
-    e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([e_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e_ms = float(tt.item())
-    e2e_val = world * e_steps / (e_ms / 1e3)
+    e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    e2e_val = job_throughput(world, e_steps, e_ms)
 
     # ---- roofline of the dominant kernel (FP32 pipe): the persistent forward + backward
     # blend (its phase also holds the per-keyframe loss sum, a few microseconds)
