@@ -296,6 +296,7 @@ def test_update_masks_golden_cases():
     assert abs(default.theta_d - consts["theta_d"]) < 1e-7 and abs(default.theta_c - consts["theta_c"]) < 1e-7
     for a, dd, dc, geo, rgb in rows:
         g, cam, t, (y, x) = eq11_case(a, dd, dc)
+        g = {k: v.astype(np.float32) if v.dtype == np.float64 else v for k, v in g.items()}
         r = Render(g, cam, 4, t, **st_kw)
         r.out["update_mask"] = torch.empty(cam["height"], cam["width"], dtype=torch.uint8, device="cuda")
         out = r.forward()
