@@ -179,8 +179,9 @@ DQO_API int dqo_version(void);
  *   L_depth = 1/(HW) sum_{p: gt(p) >= 0, D^(p) > 0} |D(p) - D^(p)|
  *   L_ins   = 1/(HW) sum_{p: gt(p) >= 0} |ins(p) - 1|
  *   L_total = L_rgb + L_depth + lambda_ins L_ins
- * Stages: projection, depth radix sort, tile binning + pair radix sort, tile ranges,
- * blend + fused loss.  With targets, dL/d(pixel) is kept in the context for the
+ * Stages: projection, depth radix sort, scan of tiles per Gaussian in depth order, pair
+ * emission in depth order + a radix sort on the tile bits, tile ranges, tile schedule
+ * (heaviest tiles first), blend + fused loss.  With targets, dL/d(pixel) is kept in the context for the
  * backward.  out->loss requires targets (DQO_EINVAL otherwise).
  * Errors: DQO_EINVAL (NULL ctx/settings/gaussians/camera/out, settings out of range,
  * n > 0 with a NULL input array, targets without gt_id or rgb), DQO_ENOMEM, DQO_ECUDA. */
@@ -191,8 +192,9 @@ DQO_API dqo_status dqo_render_forward(dqo_ctx* ctx, const dqo_settings* settings
 /* Backward of the last forward on this context (same settings, Gaussians, camera and
  * targets).  Upstream pixel gradients: `pixel_grads` if non-NULL, else the gradient of
  * L_total saved by the forward (which then must have had targets).  Per pixel it walks
- * the blended Gaussians back to front from the saved T_final / n_contrib, reduces
- * per-Gaussian partials over the warp and the CTA, then adds them to a per-Gaussian
+ * the blended Gaussians back to front from the saved T_final / n_contrib, sums
+ * per-Gaussian partials over each warp (or per lane when few lanes contribute), then adds
+ * them to a per-Gaussian
  * moment record (DQO_BUF_GRAD2D: sum over pixels of g dx, g dy, g dx^2, g dx dy, g dy^2
  * with g = dL/d(exponent), then dL/dopacity, dL/drgb (3), dL/dz), and chains the record
  * through the projection to the parameters, ACCUMULATING into `grads`.
@@ -212,13 +214,13 @@ DQO_API dqo_status dqo_get_buffer(dqo_ctx* ctx, dqo_buffer which, void* dst, siz
 /* Phases timed by dqo_set_timing / dqo_get_timings. */
 typedef enum {
   DQO_PHASE_PROJECT = 0,     /* K1 projection */
-  DQO_PHASE_DEPTH_SORT = 1,  /* scan of tiles per Gaussian, depth radix sort, depth ranks */
+  DQO_PHASE_DEPTH_SORT = 1,  /* depth radix sort, scan of tiles per Gaussian in depth order */
   DQO_PHASE_BINNING = 2,     /* pair emission, pair radix sort, tile ranges (after the host sync) */
-  DQO_PHASE_BLEND_FWD = 3,   /* K6 blend + fused losses (+ loss reduction) */
-  DQO_PHASE_BLEND_BWD = 4,   /* K7 blend backward */
+  DQO_PHASE_BLEND_FWD = 3,   /* tile schedule, K6 blend + fused losses (+ loss reduction) */
+  DQO_PHASE_BLEND_BWD = 4,   /* tile schedule, K7 blend backward */
   DQO_PHASE_PROJECT_BWD = 5, /* K8 projection backward */
   DQO_PHASE_QUADRIC = 6,     /* dual-quadric projection or bbox loss */
-  DQO_PHASE_BLEND_STEP = 7,  /* dqo_batch_step: persistent forward + backward blend, loss sums */
+  DQO_PHASE_BLEND_STEP = 7,  /* dqo_batch_step: tile schedules, forward + backward blend, loss sums */
   DQO_PHASE_COUNT = 8
 } dqo_phase;
 
@@ -363,10 +365,9 @@ typedef struct dqo_fit_batch {
  * gradients = the saved loss derivatives) on each keyframe alone; images are bitwise the
  * same, gradients up to the order of floating-point additions.  The fits run concurrently
  * on a second stream of the context, joined into `stream` before the call's work ends.
- *   Phases: projection, scan, depth sort, pair emission, pair sort and tile ranges each
- *   run once over all keyframes; the blend runs as one persistent kernel whose CTAs take
- *   tiles of all keyframes from an atomic work queue, each tile's forward followed at once
- *   by its backward; then the per-keyframe loss sums and the projection adjoint.
+ *   Phases: projection, depth sort, scan, pair emission, pair sort and tile ranges each
+ *   run once over all keyframes; the blend as `schedule` says, tiles heaviest first; then
+ *   the per-keyframe loss sums and the projection adjoint.
  * Sizing: the first call, and any call whose batch layout (keyframe count, Gaussian
  * counts, image sizes, tile shape) differs from the previous one, waits once on the host
  * for the pair count and sizes the pair buffers with 25% headroom; other calls do not
