@@ -278,6 +278,8 @@ __global__ void __launch_bounds__(kGemmThreads) k_mlp_gemm(GemmArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tslot;
+  pdl_wait();  // before any memory access or tensor-memory allocation
+  pdl_trigger();
   const int t = threadIdx.x, w = t >> 5;
   const int m0 = blockIdx.x * kTileM;
   const int64_t k0 = (int64_t)blockIdx.y * a.K;
@@ -414,6 +416,8 @@ __global__ void k_mlp_features(int nq, int nv, const float* __restrict__ Pm, con
 // on a cosine schedule from lr to lr_final over total_steps), gradient reset to zero, and
 // the BF16 operand copies of the weights (W and, for W2 and W3, W^T) rewritten.
 __global__ void k_mlp_adam(MlpState st, dqo_mlp_hparams hp) {
+  pdl_wait();
+  pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kMlpParams) return;
   const int step = *st.step;
@@ -481,8 +485,7 @@ template <int EPI>
 cudaError_t gemm(const GemmArgs& a, dim3 grid, cudaStream_t s) {
   // every launch takes the full shared-memory budget: at most three CTAs share an SM, so
   // their tensor-memory allocations (128 columns each) always fit in its 512 columns
-  k_mlp_gemm<EPI><<<grid, kGemmThreads, kGemmSmem, s>>>(a);
-  return cudaGetLastError();
+  return launch_dep_smem(k_mlp_gemm<EPI>, grid, dim3(kGemmThreads), kGemmSmem, s, a);
 }
 
 GemmArgs base(const __nv_bfloat16* A, int64_t lda, int M, const __nv_bfloat16* B, int64_t ldb, int N, int K,
@@ -518,8 +521,7 @@ cudaError_t launch_mlp_set(const MlpState& st, const float* params, cudaStream_t
 }
 
 cudaError_t launch_mlp_adam(const MlpState& st, const dqo_mlp_hparams& hp, cudaStream_t s) {
-  k_mlp_adam<<<(kMlpParams + 255) / 256, 256, 0, s>>>(st, hp);
-  return cudaGetLastError();
+  return launch_dep(k_mlp_adam, dim3((kMlpParams + 255) / 256), dim3(256), s, st, hp);
 }
 
 // Inference: X [n][128] -> y [n][9]; three launches.
