@@ -1,16 +1,17 @@
 // K6 (blend forward + fused losses) and K7 (blend backward) of the rasterizer.
 //
-// One CTA of 256 threads per screen tile (16x16, 8x32 or 32x8 pixels), one pixel per
-// thread; each warp covers an 8x4 pixel block.  The tile's depth-ordered Gaussian list
-// is staged through shared memory in batches.
+// Forward: one CTA of 256 threads per screen tile (16x16, 8x32 or 32x8 pixels); backward:
+// one CTA of 128 threads per half tile.  One pixel per thread; each warp covers an 8x4
+// pixel block and walks the tile's depth-ordered Gaussian list in chunks of 32, staging
+// in shared memory the Gaussians that can reach its block.  Tiles (and backward half
+// tiles) are taken heaviest first, in the order a one-CTA counting sort writes.
 //
 // Forward, per pixel, front to back (3DGS blending; Eq. 15 for ins; Eq. 7-10 losses):
 //   alpha = min(clamp, o G), skipped if < alpha_min; stop before T (1 - alpha) < t_stop;
 //   w = alpha T: C += w c, D += w z, ins += w if the Gaussian is opaque (or og_filter is
 //   off) and its id equals the pixel's labelled id; W_k += w for the id map.
 // Each warp walks the list on its own (no barrier inside the walk) and leaves it once
-// all its pixels have stopped.  Per-object weights live in
-// shared memory per tile: the tile's distinct ids are found first and mapped to dense
+// all its pixels have stopped.  Per-object weights live in shared memory per tile: the tile's distinct ids are found first and mapped to dense
 // slots, 16 slots per round (extra rounds re-walk the list only for tiles with more
 // than 16 objects).  The loss terms and dL/d(pixel) are computed in the epilogue.
 //
