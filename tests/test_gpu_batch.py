@@ -235,3 +235,47 @@ def test_batch_invalid_arguments():
     with pytest.raises(dqo.DqoError):                          # no targets
         dqo.dqo_batch_step(bt.ctx, bt.st, [k2])
     bt.ctx.close()
+
+
+def test_indoor_keyframe_batch_step_full_size_parity():
+    # The bench's timed configuration (dqo_batch_step on the 300k-Gaussian indoor keyframe,
+    # per-keyframe blend schedule, 16x16 tiles): images bitwise those of the single-keyframe
+    # calls (whose full-size image parity with the oracle the rasterizer tests check), and
+    # every Gaussian gradient against the FP64 oracle with the rasterizer tests' criterion
+    # (relative 1e-3 plus the oracle's per-element decision and rounding bound).
+    from gpu_util import assert_grads_close, condition_targets
+    kf = synth.indoor_keyframe(1002)
+    g, cam = kf["gaussians"], kf["camera"]
+    st_o = oracle_settings(31)
+    t = condition_targets(g, cam, synth.raycast_targets(kf), st_o)
+    outs_ref, _ = _single_n(g, cam, t, 31)
+    ctx = dqo.Context()
+    gd, td = dqo.to_device(g), dqo.to_device(t)
+    out = dqo.alloc_outputs(cam["width"], cam["height"], mask=True)
+    gr = dqo.alloc_grads(g["means"].shape[0])
+    kf_b = dqo.keyframe(gd, 31, cam, td, out, gr)
+    dqo.dqo_batch_step(ctx, dqo.settings(), [kf_b], None, 0, dqo.SCHEDULE_PER_KEYFRAME)
+    torch.cuda.synchronize()
+    pairs, over = dqo.dqo_batch_check(ctx)
+    assert pairs > 1_000_000 and not over
+    for name in IMG_KEYS:
+        assert np.array_equal(out[name].cpu().numpy(), outs_ref[name]), name
+    refb = oracle.render_backward(g, cam, st_o, t)
+    report = {}
+    assert_grads_close({k: v.cpu().numpy() for k, v in gr.items()}, refb, report=report)
+    assert all(v["widened"] < 0.05 for v in report.values()), report
+    ctx.close()
+
+
+def _single_n(g, cam, t, nobj, **st):
+    ctx = dqo.Context()
+    gd, td = dqo.to_device(g), dqo.to_device(t)
+    out = dqo.alloc_outputs(cam["width"], cam["height"], mask=True)
+    grads = dqo.alloc_grads(g["means"].shape[0])
+    s = dqo.settings(**st)
+    dqo.dqo_render_forward(ctx, s, dqo.gaussians(gd, nobj), dqo.camera(cam), dqo.targets(td), dqo.render_out(out))
+    dqo.dqo_render_backward(ctx, s, dqo.gaussians(gd, nobj), dqo.camera(cam), dqo.targets(td), None,
+                            dqo.gaussian_grads(grads))
+    torch.cuda.synchronize()
+    ctx.close()
+    return {k: v.cpu().numpy() for k, v in out.items()}, {k: v.cpu().numpy() for k, v in grads.items()}
