@@ -30,7 +30,7 @@ struct dqo_ctx {
   Buf scan_scratch, depth_scan_scratch, hist, depth_hist, pair_a, pair_b, list;
   // per-tile / per-pixel
   Buf ranges, loss_part, T_final, n_contrib, dl_rgb, dl_depth, dl_ins;
-  Buf tile_sched;           // [3][tiles] uint32: forward tile order, tile costs, backward tile order
+  Buf tile_sched;           // uint32 [tiles] forward order, [tiles * kTileParts] part costs, backward order
   Buf counters;             // device: [0] uint64 total pairs, [1] uint32 n_visible
   Buf sort_err;             // device uint32: a radix sort's look-back wait gave up (sticky until read)
   uint64_t* host_counters = nullptr;  // pinned mirror
@@ -321,7 +321,7 @@ dqo_status dqo_render_forward(dqo_ctx* c, const dqo_settings* s, const dqo_gauss
   DQO_CUDA(c, ensure(c->gid, 4 * n));
   DQO_CUDA(c, ensure(c->offsets, 4 * n));
   DQO_CUDA(c, ensure(c->ranges, 8 * (size_t)tiles));
-  DQO_CUDA(c, ensure(c->tile_sched, 12 * (size_t)tiles));
+  DQO_CUDA(c, ensure(c->tile_sched, 4 * (1 + 2 * kTileParts) * (size_t)tiles));
   DQO_CUDA(c, ensure(c->loss_part, 12 * (size_t)tiles));
   DQO_CUDA(c, ensure(c->T_final, 4 * HW));
   DQO_CUDA(c, ensure(c->n_contrib, 4 * HW));
@@ -517,7 +517,7 @@ dqo_status dqo_render_backward(dqo_ctx* c, const dqo_settings* s, const dqo_gaus
   }
   a.grad2d = as<float>(c->grad2d);
   const int tiles = c->ntx * c->nty;
-  a.tile_order = as<uint32_t>(c->tile_sched) + 2 * (size_t)tiles;
+  a.tile_order = as<uint32_t>(c->tile_sched) + (1 + kTileParts) * (size_t)tiles;
   {
     PhaseTimer pt(c, DQO_PHASE_BLEND_BWD, s_);
     DQO_CUDA(c, launch_tile_schedule(nullptr, as<uint32_t>(c->tile_sched) + tiles, tiles,
@@ -750,7 +750,7 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
     DQO_CUDA(c, ensure(B.offsets, 4 * N));
     DQO_CUDA(c, ensure(B.grad2d, 48 * N));
     DQO_CUDA(c, ensure(B.ranges, 8 * T));
-    DQO_CUDA(c, ensure(B.tile_sched, 12 * T));
+    DQO_CUDA(c, ensure(B.tile_sched, 4 * (1 + 2 * kTileParts) * T));
     DQO_CUDA(c, ensure(B.loss_part, 12 * T));
     DQO_CUDA(c, ensure(B.T_final, 4 * P));
     DQO_CUDA(c, ensure(B.n_contrib, 4 * P));
@@ -910,7 +910,7 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
       a.loss_part = as<float>(B.loss_part) + 3 * (int64_t)toff[k];
       a.o_mask = kf.out.update_mask;
       a.tile_order = as<uint32_t>(B.tile_sched) + toff[k];
-      a.tile_cost = as<uint32_t>(B.tile_sched) + T + toff[k];
+      a.tile_cost = as<uint32_t>(B.tile_sched) + T + kTileParts * (uint64_t)toff[k];
       BlendBwdArgs& bb = tt.b[k];
       bb.rp = rp[k];
       bb.p0 = pb.p0;
@@ -926,7 +926,7 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
       bb.g_alpha = nullptr;
       bb.g_ins = a.dl_ins;
       bb.grad2d = as<float>(B.grad2d);
-      bb.tile_order = as<uint32_t>(B.tile_sched) + 2 * T + toff[k];
+      bb.tile_order = as<uint32_t>(B.tile_sched) + (1 + kTileParts) * T + kTileParts * (uint64_t)toff[k];
       tt.tile_off[k] = toff[k];
       lt.kf[k].part = a.loss_part;
       lt.kf[k].tiles = (int)(toff[k + 1] - toff[k]);

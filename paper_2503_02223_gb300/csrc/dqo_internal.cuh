@@ -142,7 +142,7 @@ struct BlendFwdArgs {
   float* loss_part;  // [T*3] per-tile loss sums
   uint8_t* o_mask;   // [H*W] Eq. 11 update masks (with targets)
   const uint32_t* tile_order = nullptr;  // [T] block b blends tile tile_order[b] (null: tile b)
-  uint32_t* tile_cost = nullptr;         // [T] out: longest blended prefix of the tile's pixels
+  uint32_t* tile_cost = nullptr;         // [T * kTileParts] out: longest blended prefix per tile part
 };
 
 struct BlendBwdArgs {
@@ -269,6 +269,9 @@ cudaError_t launch_blend_forward(const BlendFwdArgs& a, bool with_id, cudaStream
 // Tile schedule: order[0..tiles) lists the tiles by decreasing cost (cost[t], or the
 // tile's list length ranges[t].y - ranges[t].x when cost is null), on a log scale of four
 // buckets per octave; tiles of one bucket come in no fixed order.  One CTA.
+// The backward walks a tile in kTileParts parts of kTileWarps / kTileParts warps (8x4
+// blocks); the forward reports each part's cost.
+constexpr int kTileParts = 2;
 cudaError_t launch_tile_schedule(const uint2* ranges, const uint32_t* cost, int tiles, uint32_t* order,
                                  cudaStream_t s);
 cudaError_t launch_loss_reduce(const float* part, int tiles, float lambda_ins, float scale, float* loss,

@@ -441,11 +441,13 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const Blen
       for (int w = 0; w < kThreads / 32; ++w) s += s_red[tid][w];
       a.loss_part[3 * tile + tid] = s;
     }
-    if (a.tile_cost && tid == 32) {
+    if (a.tile_cost && tid >= 32 && tid < 32 + kTileParts) {  // each part's longest prefix
+      constexpr int kPartWarps = kThreads / 32 / kTileParts;
+      const int p = tid - 32;
       uint32_t m = 0;
 #pragma unroll
-      for (int w = 0; w < kThreads / 32; ++w) m = max(m, s_wlast[w]);
-      a.tile_cost[tile] = m;
+      for (int w = 0; w < kPartWarps; ++w) m = max(m, s_wlast[p * kPartWarps + w]);
+      a.tile_cost[tile * kTileParts + p] = m;
     }
   }
 }
@@ -521,8 +523,10 @@ __device__ __forceinline__ int sched_bucket(uint32_t x) {
 // lanes with equal buckets add to the bucket's counter once (match_any).
 constexpr int kSchedThreads = 1024, kSchedPer = 8;
 
+// Item i's cost: tile i's list length (ranges), else the largest of cost[i * group + j],
+// j < group (a tile's parts, or one part).
 __device__ __forceinline__ void schedule_tiles(const uint2* __restrict__ ranges, const uint32_t* __restrict__ cost,
-                                               int tiles, uint32_t* __restrict__ order) {
+                                               int group, int tiles, uint32_t* __restrict__ order) {
   __shared__ uint32_t s_h[kSchedBuckets];
   const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t lt = lanemask_lt();
@@ -534,7 +538,7 @@ __device__ __forceinline__ void schedule_tiles(const uint2* __restrict__ ranges,
       c[j] = 0u;
       if (t < tiles) {
         if (cost) {
-          c[j] = cost[t];
+          for (int g = 0; g < group; ++g) c[j] = max(c[j], cost[(int64_t)t * group + g]);
         } else {
           const uint2 r = ranges[t];
           c[j] = r.y > r.x ? r.y - r.x : 0u;
@@ -595,11 +599,11 @@ __device__ __forceinline__ void schedule_tiles(const uint2* __restrict__ ranges,
 }
 
 __global__ void __launch_bounds__(kSchedThreads) k_tile_schedule(const uint2* __restrict__ ranges,
-                                                                 const uint32_t* __restrict__ cost, int tiles,
-                                                                 uint32_t* __restrict__ order) {
+                                                                 const uint32_t* __restrict__ cost, int group,
+                                                                 int tiles, uint32_t* __restrict__ order) {
   pdl_wait();
   pdl_trigger();
-  schedule_tiles(ranges, cost, tiles, order);
+  schedule_tiles(ranges, cost, group, tiles, order);
 }
 
 // Sum over the warp of 10 per-lane values, transposing as it halves: stage 1 (lanes l and
@@ -803,6 +807,7 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const Blen
 // different lengths.  CTA b covers part b % kBwdParts of the b / kBwdParts-th scheduled tile.
 constexpr int kBwdWarps = 4;
 constexpr int kBwdParts = kThreads / 32 / kBwdWarps;
+static_assert(kBwdParts == kTileParts, "tile parts of the backward and of the cost records");
 
 template <int TW>
 __global__ void __launch_bounds__(32 * kBwdWarps, 28 / kBwdWarps) k_blend_backward(BlendBwdArgs a) {
@@ -872,25 +877,28 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd_queue(const __grid_const
   }
 }
 
+// The backward on a work queue of tile parts (CTAs of kBwdWarps warps, like the
+// one-keyframe backward): item u is part u % kBwdParts of joint tile u / kBwdParts.
 template <int TW>
-__global__ void __launch_bounds__(kThreads, 4) k_blend_bwd_queue(const __grid_constant__ StepTable t, BlendCommon cm,
-                                                              uint32_t* __restrict__ queue,
-                                                              const uint32_t* __restrict__ order) {
+__global__ void __launch_bounds__(32 * kBwdWarps, 28 / kBwdWarps)
+    k_blend_bwd_queue(const __grid_constant__ StepTable t, BlendCommon cm, uint32_t* __restrict__ queue,
+                      const uint32_t* __restrict__ order) {
   pdl_wait();
   pdl_trigger();
   __shared__ uint32_t s_item;
-  const uint32_t total = t.tile_off[t.nkf];
+  const uint32_t total = t.tile_off[t.nkf] * kBwdParts;
   for (;;) {
     if (threadIdx.x == 0) {
       const uint32_t q = atomicAdd(queue, 1u);
       s_item = q < total && order ? order[q] : q;
     }
     __syncthreads();
-    const uint32_t it = s_item;
-    if (it >= total) break;
+    const uint32_t u = s_item;
+    if (u >= total) break;
+    const uint32_t jt = u / kBwdParts;
     int k = 0;
-    while (k + 1 < t.nkf && t.tile_off[k + 1] <= it) ++k;
-    blend_bwd_tile<TW>(t.b[k], cm, (int)(it - t.tile_off[k]));
+    while (k + 1 < t.nkf && t.tile_off[k + 1] <= jt) ++k;
+    blend_bwd_tile<TW, kBwdWarps>(t.b[k], cm, (int)(jt - t.tile_off[k]), (int)(u % kBwdParts) * kBwdWarps);
     __syncthreads();
   }
 }
@@ -920,7 +928,7 @@ cudaError_t launch_blend_forward(const BlendFwdArgs& a, bool with_id, cudaStream
 cudaError_t launch_tile_schedule(const uint2* ranges, const uint32_t* cost, int tiles, uint32_t* order,
                                  cudaStream_t s) {
   if (tiles <= 0) return cudaSuccess;
-  launch_dep(k_tile_schedule, dim3(1), dim3(kSchedThreads), s, ranges, cost, tiles, order);
+  launch_dep(k_tile_schedule, dim3(1), dim3(kSchedThreads), s, ranges, cost, kTileParts, tiles, order);
   return cudaGetLastError();
 }
 
@@ -948,9 +956,10 @@ namespace dqo {
 namespace {
 
 template <typename Kernel>
-unsigned persistent_grid(Kernel k, int ctas_per_sm, int sms, uint32_t total, cudaError_t* e) {
+unsigned persistent_grid(Kernel k, int ctas_per_sm, int sms, uint32_t total, cudaError_t* e,
+                         int threads = kThreads) {
   int occ = 0;
-  *e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kThreads, 0);
+  *e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, 0);
   if (*e != cudaSuccess) return 0;
   if (occ < 1) occ = 1;
   const int per = ctas_per_sm > 0 ? (ctas_per_sm < occ ? ctas_per_sm : occ) : occ;
@@ -967,9 +976,9 @@ __global__ void __launch_bounds__(kSchedThreads) k_tile_schedule_batch(const __g
   const int k = blockIdx.x;
   const int tiles = (int)(t.tile_off[k + 1] - t.tile_off[k]);
   if (which == 0)
-    schedule_tiles(t.f[k].ranges, nullptr, tiles, const_cast<uint32_t*>(t.f[k].tile_order));
+    schedule_tiles(t.f[k].ranges, nullptr, 1, tiles, const_cast<uint32_t*>(t.f[k].tile_order));
   else
-    schedule_tiles(nullptr, t.f[k].tile_cost, tiles, const_cast<uint32_t*>(t.b[k].tile_order));
+    schedule_tiles(nullptr, t.f[k].tile_cost, kTileParts, tiles, const_cast<uint32_t*>(t.b[k].tile_order));
 }
 
 // Blend schedules of a batch: 0 = fused queue kernel, 1 = forward and backward queue
@@ -990,19 +999,22 @@ cudaError_t step_tw(const StepTable& t, const BlendCommon& cm, uint32_t* queue, 
     const unsigned grid = persistent_grid(k_blend_step<TW, kId>, ctas_per_sm, sms, total, &e);
     if (e != cudaSuccess) return e;
     if (sched)
-      launch_dep(k_tile_schedule, dim3(1), dim3(kSchedThreads), s, t.f[0].ranges, nullptr, (int)total, f_order);
+      launch_dep(k_tile_schedule, dim3(1), dim3(kSchedThreads), s, t.f[0].ranges, nullptr, 1, (int)total, f_order);
     k_blend_step<TW, kId><<<grid, kThreads, 0, s>>>(t, cm, queue, f_order);
   } else if (schedule == 1) {
     unsigned grid = persistent_grid(k_blend_fwd_queue<TW, kId>, ctas_per_sm, sms, total, &e);
     if (e != cudaSuccess) return e;
     if (sched)
-      launch_dep(k_tile_schedule, dim3(1), dim3(kSchedThreads), s, t.f[0].ranges, nullptr, (int)total, f_order);
+      launch_dep(k_tile_schedule, dim3(1), dim3(kSchedThreads), s, t.f[0].ranges, nullptr, 1, (int)total, f_order);
     k_blend_fwd_queue<TW, kId><<<grid, kThreads, 0, s>>>(t, cm, queue, f_order);
-    grid = persistent_grid(k_blend_bwd_queue<TW>, ctas_per_sm, sms, total, &e);
+    // the backward's CTAs are tile parts: as many warps per SM as ctas_per_sm whole tiles
+    grid = persistent_grid(k_blend_bwd_queue<TW>, ctas_per_sm > 0 ? ctas_per_sm * kBwdParts : 0, sms,
+                           total * kBwdParts, &e, 32 * kBwdWarps);
     if (e != cudaSuccess) return e;
     if (sched)
-      launch_dep(k_tile_schedule, dim3(1), dim3(kSchedThreads), s, nullptr, t.f[0].tile_cost, (int)total, b_order);
-    k_blend_bwd_queue<TW><<<grid, kThreads, 0, s>>>(t, cm, queue + 1, b_order);
+      launch_dep(k_tile_schedule, dim3(1), dim3(kSchedThreads), s, nullptr, t.f[0].tile_cost, 1,
+                 (int)(total * kBwdParts), b_order);
+    k_blend_bwd_queue<TW><<<grid, 32 * kBwdWarps, 0, s>>>(t, cm, queue + 1, b_order);
   } else {
     if (sched) launch_dep(k_tile_schedule_batch, dim3((unsigned)t.nkf), dim3(kSchedThreads), s, t, 0);
     for (int k = 0; k < t.nkf; ++k) {
