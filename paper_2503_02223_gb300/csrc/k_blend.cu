@@ -878,7 +878,9 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd_queue(const __grid_const
 }
 
 // The backward on a work queue of tile parts (CTAs of kBwdWarps warps, like the
-// one-keyframe backward): item u is part u % kBwdParts of joint tile u / kBwdParts.
+// one-keyframe backward): queue entry q is part q % kBwdParts of the (q / kBwdParts)-th
+// tile of the order (a tile's parts run next to each other, which measured faster than
+// ordering the parts on their own).
 template <int TW>
 __global__ void __launch_bounds__(32 * kBwdWarps, 28 / kBwdWarps)
     k_blend_bwd_queue(const __grid_constant__ StepTable t, BlendCommon cm, uint32_t* __restrict__ queue,
@@ -890,7 +892,7 @@ __global__ void __launch_bounds__(32 * kBwdWarps, 28 / kBwdWarps)
   for (;;) {
     if (threadIdx.x == 0) {
       const uint32_t q = atomicAdd(queue, 1u);
-      s_item = q < total && order ? order[q] : q;
+      s_item = q < total && order ? order[q / kBwdParts] * kBwdParts + q % kBwdParts : q;
     }
     __syncthreads();
     const uint32_t u = s_item;
@@ -1012,8 +1014,8 @@ cudaError_t step_tw(const StepTable& t, const BlendCommon& cm, uint32_t* queue, 
                            total * kBwdParts, &e, 32 * kBwdWarps);
     if (e != cudaSuccess) return e;
     if (sched)
-      launch_dep(k_tile_schedule, dim3(1), dim3(kSchedThreads), s, nullptr, t.f[0].tile_cost, 1,
-                 (int)(total * kBwdParts), b_order);
+      launch_dep(k_tile_schedule, dim3(1), dim3(kSchedThreads), s, nullptr, t.f[0].tile_cost, kTileParts,
+                 (int)total, b_order);
     k_blend_bwd_queue<TW><<<grid, 32 * kBwdWarps, 0, s>>>(t, cm, queue + 1, b_order);
   } else {
     if (sched) launch_dep(k_tile_schedule_batch, dim3((unsigned)t.nkf), dim3(kSchedThreads), s, t, 0);
