@@ -235,7 +235,6 @@ cudaError_t radix_sort_u32_dev(uint32_t* keys_a, uint32_t* keys_b, int64_t n, in
                                int* sel, cudaStream_t s, const uint64_t* n_dev, uint32_t* err = nullptr,
                                int begin_bit = 0);
 
-cudaError_t launch_rank_scatter(const uint32_t* order, int64_t n, uint32_t* rank, cudaStream_t s);
 // Pairs (tile << rank_bits | depth rank) of the Gaussians in depth order: rank r's Gaussian
 // order[r] writes its tiles' keys from offsets[r] (tile counts scanned in rank order).
 cudaError_t launch_emit_pairs_u32(const ushort4* rect, const uint32_t* offsets, const uint32_t* order,

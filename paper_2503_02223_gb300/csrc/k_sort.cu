@@ -511,12 +511,6 @@ cudaError_t radix_sort_u64(uint64_t* keys_a, uint64_t* keys_b, int64_t n, int en
                                           nullptr, err, begin_bit);
 }
 
-cudaError_t launch_rank_scatter(const uint32_t* order, int64_t n, uint32_t* rank, cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
-  k_rank_scatter<<<grid_for(n, kThreads), kThreads, 0, s>>>(order, n, rank);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_emit_pairs_u32(const ushort4* rect, const uint32_t* offsets, const uint32_t* order, int64_t n,
                                   int ntx, int rank_bits, uint32_t* keys, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
