@@ -231,6 +231,24 @@ def traffic_for(kernel: str):
 
 # ----------------------------------------------------------------------------- arms
 
+def image_slices(H: int, h: int, cores: int) -> list:
+    """The image's rows as bands of h rows (the last one shorter), grouped `cores` bands to
+    a slice: a slice is one reference step (its bands run concurrently)."""
+    bands = [(r0, min(h, H - r0)) for r0 in range(0, H, h)]
+    return [bands[i:i + cores] for i in range(0, len(bands), cores)]
+
+
+def reference_band_rows(t1: float, t16: float, steps: int, warmup: int, budget_s: float) -> int:
+    """The largest band height of 16, 8, 4, 2 whose step time, interpolated between the
+    measured 1-row (t1) and 16-row (t16) steps, keeps steps + warmup steps within budget_s
+    seconds; 1 when none does."""
+    per_step = budget_s / max(1, steps + warmup)
+    for cand in (16, 8, 4, 2):
+        if t1 + (t16 - t1) * (cand - 1) / 15.0 <= per_step:
+            return cand
+    return 1
+
+
 def run_reference(args, rank, world):
     """The FP64 CPU oracle on this host's cores (the reference arm of this workload): the
     whole keyframe per step, rows split into bands run concurrently on every core."""
@@ -244,19 +262,10 @@ def run_reference(args, rank, world):
     # band's time is a fixed part plus a part per row: the first two warm-up steps measure
     # bands of 1 and 16 rows, and h (16, 8, 4, 2 or 1) is the largest that keeps the
     # K + W steps near REF_BUDGET_S seconds.
-    def slices_of(h):
-        bands = [(r0, min(h, H - r0)) for r0 in range(0, H, h)]
-        return [bands[i:i + cores] for i in range(0, len(bands), cores)]
-
-    t1, _ = oracle_full_parallel(kf, targets, cores, slices_of(1)[0])
-    t16, _ = oracle_full_parallel(kf, targets, cores, slices_of(16)[0])
-    per_step = REF_BUDGET_S / max(1, args.steps + args.warmup)
-    h = 1
-    for cand in (16, 8, 4, 2):
-        if t1 + (t16 - t1) * (cand - 1) / 15.0 <= per_step:
-            h = cand
-            break
-    slices = slices_of(h)
+    t1, _ = oracle_full_parallel(kf, targets, cores, image_slices(H, 1, cores)[0])
+    t16, _ = oracle_full_parallel(kf, targets, cores, image_slices(H, 16, cores)[0])
+    h = reference_band_rows(t1, t16, args.steps, args.warmup, REF_BUDGET_S)
+    slices = image_slices(H, h, cores)
     for w in range(max(0, args.warmup - 2)):
         oracle_full_parallel(kf, targets, cores, slices[w % len(slices)])
     times, rows_done = [], 0

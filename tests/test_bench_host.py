@@ -1,6 +1,6 @@
-"""The multi-rank path of bench.py on CPU: two gloo ranks with different step times agree
-on the slowest rank's time, and the whole-job throughput counts both ranks' units
-(replicas, weak scaling)."""
+"""Host logic of bench.py on CPU: the multi-rank path (two gloo ranks with different step
+times agree on the slowest rank's time, and the whole-job throughput counts both ranks'
+units: replicas, weak scaling) and the reference arm's sampling of the image."""
 import os
 import socket
 
@@ -51,3 +51,21 @@ def test_two_gloo_ranks_take_the_slowest_time():
 def test_one_rank_needs_no_process_group():
     assert bench.max_over_ranks(7.5, 1, "cpu") == 7.5
     assert bench.job_throughput(1, 4, 2000.0) == pytest.approx(2.0)
+
+
+def test_reference_slices_cover_every_row_once_per_cycle():
+    for H, h, cores in ((680, 16, 15), (680, 1, 16), (680, 8, 4), (17, 16, 3)):
+        slices = bench.image_slices(H, h, cores)
+        rows = [r for sl in slices for r0, nr in sl for r in range(r0, r0 + nr)]
+        assert rows == list(range(H))
+        assert all(1 <= len(sl) <= cores for sl in slices) and all(len(sl) == cores for sl in slices[:-1])
+        assert all(nr == h for sl in slices for r0, nr in sl[:-1])
+
+
+def test_reference_band_height_fits_the_budget():
+    # 1-row steps 0.5 s, 16-row steps 2 s, so 8, 4 and 2 rows take 1.2, 0.8 and 0.6 s: the
+    # tallest band whose step fits budget / (steps + warm-up) is chosen
+    assert bench.reference_band_rows(0.5, 2.0, 10, 2, 240.0) == 16      # 20 s per step
+    assert bench.reference_band_rows(0.5, 2.0, 200, 10, 240.0) == 4     # 1.14 s per step
+    assert bench.reference_band_rows(0.5, 2.0, 300, 10, 240.0) == 2     # 0.77 s per step
+    assert bench.reference_band_rows(0.5, 2.0, 1000, 10, 240.0) == 1    # 0.24 s per step
