@@ -31,6 +31,7 @@ struct dqo_ctx {
   // per-tile / per-pixel
   Buf ranges, loss_part, T_final, n_contrib, dl_rgb, dl_depth, dl_ins;
   Buf tile_sched;           // uint32 [tiles] forward order, [tiles * kTileParts] part costs, backward order
+  Buf hitrec;               // uint32 [8 (pairs / 32 + tiles + 1)]: the forward's hit ballots for the backward
   Buf counters;             // device: [0] uint64 total pairs, [1] uint32 n_visible
   Buf sort_err;             // device uint32: a radix sort's look-back wait gave up (sticky until read)
   uint64_t* host_counters = nullptr;  // pinned mirror
@@ -52,7 +53,7 @@ struct dqo_ctx {
   struct Batch {
     Buf p0, p1, p2, rect, ntiles, zkey_a, zkey_b, zval_a, zval_b, gid, offsets, grad2d;
     Buf scan_scratch, depth_scan_scratch, depth_hist, hist, pair_a, pair_b, list, ranges, loss_part;
-    Buf T_final, n_contrib, dl_rgb, dl_depth, dl_ins, counters, tile_sched;
+    Buf T_final, n_contrib, dl_rgb, dl_depth, dl_ins, counters, tile_sched, hitrec;
     uint64_t* host = nullptr;  // pinned: pair count of a sizing call
     std::vector<int64_t> sig;  // layout of the last sizing call
     uint64_t capacity = 0;
@@ -108,6 +109,9 @@ template <typename T>
 T* as(const Buf& b) {
   return reinterpret_cast<T*>(b.p);
 }
+
+// Words of the blend's hit record: 8 warp-blocks x (pairs / 32 + tiles + 1) list chunks.
+size_t hit_record_words(uint64_t pairs, uint64_t tiles) { return 8 * (size_t)(pairs / 32 + tiles + 1); }
 
 int bits_for(uint64_t v) {  // smallest b with v <= 2^b (at least 1)
   int b = 1;
@@ -267,14 +271,14 @@ void dqo_destroy(dqo_ctx* c) {
                 &c->zval_b, &c->gid, &c->offsets, &c->grad2d, &c->scan_scratch,
                 &c->depth_scan_scratch, &c->hist, &c->depth_hist,
                 &c->pair_a, &c->pair_b, &c->list, &c->ranges, &c->loss_part, &c->T_final, &c->n_contrib,
-                &c->dl_rgb, &c->dl_depth, &c->dl_ins, &c->counters, &c->sort_err, &c->tile_sched};
+                &c->dl_rgb, &c->dl_depth, &c->dl_ins, &c->counters, &c->sort_err, &c->tile_sched, &c->hitrec};
   for (Buf* b : all)
     if (b->p) cudaFree(b->p);
   dqo_ctx::Batch& B = c->b;
   Buf* ball[] = {&B.p0, &B.p1, &B.p2, &B.rect, &B.ntiles, &B.zkey_a, &B.zkey_b, &B.zval_a, &B.zval_b,
                  &B.gid, &B.offsets, &B.grad2d, &B.scan_scratch, &B.depth_scan_scratch, &B.depth_hist, &B.hist,
                  &B.pair_a, &B.pair_b, &B.list, &B.ranges, &B.loss_part, &B.T_final, &B.n_contrib, &B.dl_rgb,
-                 &B.dl_depth, &B.dl_ins, &B.counters, &B.tile_sched, &c->mlp_work};
+                 &B.dl_depth, &B.dl_ins, &B.counters, &B.tile_sched, &B.hitrec, &c->mlp_work};
   for (Buf* b : ball)
     if (b->p) cudaFree(b->p);
   if (B.host) cudaFreeHost(B.host);
@@ -450,6 +454,8 @@ dqo_status dqo_render_forward(dqo_ctx* c, const dqo_settings* s, const dqo_gauss
   a.o_mask = out->update_mask;
   a.tile_order = as<uint32_t>(c->tile_sched);
   a.tile_cost = as<uint32_t>(c->tile_sched) + tiles;
+  DQO_CUDA(c, ensure(c->hitrec, 4 * hit_record_words(m, tiles)));
+  a.hitmask = as<uint32_t>(c->hitrec);
   {
     PhaseTimer pt(c, DQO_PHASE_BLEND_FWD, s_);
     DQO_CUDA(c, launch_tile_schedule(a.ranges, nullptr, tiles, const_cast<uint32_t*>(a.tile_order), s_));
@@ -518,6 +524,7 @@ dqo_status dqo_render_backward(dqo_ctx* c, const dqo_settings* s, const dqo_gaus
   a.grad2d = as<float>(c->grad2d);
   const int tiles = c->ntx * c->nty;
   a.tile_order = as<uint32_t>(c->tile_sched) + (1 + kTileParts) * (size_t)tiles;
+  a.hitmask = as<uint32_t>(c->hitrec);
   {
     PhaseTimer pt(c, DQO_PHASE_BLEND_BWD, s_);
     DQO_CUDA(c, launch_tile_schedule(nullptr, as<uint32_t>(c->tile_sched) + tiles, tiles,
@@ -843,6 +850,7 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
     DQO_CUDA(c, ensure(B.hist, 4 * radix_scratch_words((int64_t)cap)));
     DQO_CUDA(c, ensure(B.scan_scratch, 8 * std::max(scan_scratch_words(N),
                                                     scan_scratch_words(radix_scratch_words((int64_t)cap)))));
+    DQO_CUDA(c, ensure(B.hitrec, 4 * hit_record_words(cap, T)));
     B.capacity = cap;
     B.sig = sig;
   }
@@ -911,6 +919,7 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
       a.o_mask = kf.out.update_mask;
       a.tile_order = as<uint32_t>(B.tile_sched) + toff[k];
       a.tile_cost = as<uint32_t>(B.tile_sched) + T + kTileParts * (uint64_t)toff[k];
+      a.hitmask = as<uint32_t>(B.hitrec) + 8 * (uint64_t)toff[k];  // joint tile numbering
       BlendBwdArgs& bb = tt.b[k];
       bb.rp = rp[k];
       bb.p0 = pb.p0;
@@ -927,6 +936,7 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
       bb.g_ins = a.dl_ins;
       bb.grad2d = as<float>(B.grad2d);
       bb.tile_order = as<uint32_t>(B.tile_sched) + (1 + kTileParts) * T + kTileParts * (uint64_t)toff[k];
+      bb.hitmask = a.hitmask;
       tt.tile_off[k] = toff[k];
       lt.kf[k].part = a.loss_part;
       lt.kf[k].tiles = (int)(toff[k + 1] - toff[k]);

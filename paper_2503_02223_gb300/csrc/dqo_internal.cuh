@@ -143,6 +143,8 @@ struct BlendFwdArgs {
   uint8_t* o_mask;   // [H*W] Eq. 11 update masks (with targets)
   const uint32_t* tile_order = nullptr;  // [T] block b blends tile tile_order[b] (null: tile b)
   uint32_t* tile_cost = nullptr;         // [T * kTileParts] out: longest blended prefix per tile part
+  uint32_t* hitmask = nullptr;           // [8 * (M/32 + T + 1)] out: per warp-block and list chunk, the
+                                         // ballot of the entries that can reach the block (null: none)
 };
 
 struct BlendBwdArgs {
@@ -161,6 +163,7 @@ struct BlendBwdArgs {
   const float* g_ins;
   float* grad2d;     // [n*12] moment records (accumulated with atomics)
   const uint32_t* tile_order = nullptr;  // [T] block b walks tile tile_order[b] (null: tile b)
+  const uint32_t* hitmask = nullptr;     // the forward's hit record (null: test again)
 };
 
 struct PreBwdArgs {

@@ -103,6 +103,16 @@ __device__ __forceinline__ bool ellipse_hits(const float4& p0, const float4& p1,
   return m <= lvl;
 }
 
+// Word of the hit record for the warp-block `wblock` of tile `tile` and the list chunk
+// starting at position c of the tile's list [start, ..): the forward stores there the
+// ballot of which chunk entries can reach the block, the backward reads it instead of
+// testing again.  Words (floor(start / 32) + tile + chunk) * 8 + wblock never collide
+// between tiles (a tile's chunks number at most floor(length / 32) + 1), so a record of
+// 8 * (pairs / 32 + tiles + 1) words holds all.
+__device__ __forceinline__ int64_t hit_word(int start, int c, int tile, int wblock) {
+  return ((int64_t)(start >> 5) + tile + ((c - start) >> 5)) * 8 + wblock;
+}
+
 // Fills s_slot_id[s - first] with the object id of dense slot s for s in [first, first+kIdSlots).
 __device__ __forceinline__ void slot_ids_for_round(const uint32_t* s_mask, const uint32_t* s_pref, int nw, int first,
                                                    int32_t* s_slot_id) {
@@ -237,7 +247,7 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const Blen
   // pixels and sit before list position `lim`; returns how many.  q1.w holds the key and
   // q2.w the list position (both consumed at staging otherwise).
   // gi: list entry c + lane, already loaded by the caller (read only below lim).
-  auto stage = [&](int c, int lim, uint32_t gi) -> int {
+  auto stage = [&](int c, int lim, uint32_t gi, bool record) -> int {
     const int i = c + lane;
     bool hit = false;
     float4 q0, q1, q2;
@@ -249,6 +259,7 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const Blen
       hit = ellipse_hits(q0, q1, q2, wx0, wy0, 7.f, 3.f);
     }
     const uint32_t m = __ballot_sync(kFull, hit);
+    if (record && a.hitmask && lane == 0) a.hitmask[hit_word(start, c, tile, warp)] = m;
     if (hit) {
       const int k = __popc(m & lt);
       q1.w = __uint_as_float(key_of(__float_as_uint(q1.w)));
@@ -295,7 +306,7 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const Blen
   uint32_t gnext = start + lane < end ? cm.list[start + lane] : 0u;
   for (int c = start; c < end; c += 32) {
     if (__all_sync(kFull, done)) break;
-    const int nh = stage(c, end, gnext);
+    const int nh = stage(c, end, gnext, true);
     if (c + 32 + lane < end) gnext = cm.list[c + 32 + lane];
     for (int h = 0; h < nh; h += kFwdIlp) {
       if (done) continue;
@@ -342,7 +353,7 @@ __device__ __forceinline__ void blend_fwd_tile(const BlendFwdArgs& a, const Blen
         __syncthreads();
         float Tr = 1.f;
         for (int c = start; c < start + wlast; c += 32) {
-          const int nh = stage(c, start + wlast, c + lane < start + wlast ? cm.list[c + lane] : 0u);
+          const int nh = stage(c, start + wlast, c + lane < start + wlast ? cm.list[c + lane] : 0u, false);
           for (int h = 0; h < nh; ++h) {
             if (__float_as_int(s_q2[warp][h].w) >= last) continue;
             float alpha, G, dx, dy;
@@ -708,12 +719,15 @@ __device__ __forceinline__ void blend_bwd_tile(const BlendBwdArgs& a, const Blen
     bool hit = false;
     float4 q0, q1, q2;
     uint32_t g = 0;
-    if (jl < wmax) {
+    // the forward's ballot for this chunk and block, when recorded: the same test on the
+    // same records, so only its hits are loaded and nothing is tested again
+    const uint32_t rec = a.hitmask ? a.hitmask[hit_word(start, start + c, tile, w0 + warp)] : kFull;
+    if (jl < wmax && ((rec >> lane) & 1u)) {
       g = gnext;
       q0 = cm.p0[g];
       q1 = cm.p1[g];
       q2 = cm.p2[g];
-      hit = ellipse_hits(q0, q1, q2, wx0, wy0, 7.f, 3.f);
+      hit = a.hitmask ? true : ellipse_hits(q0, q1, q2, wx0, wy0, 7.f, 3.f);
     }
     const uint32_t m = __ballot_sync(kFull, hit);
     if (hit) {
