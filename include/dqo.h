@@ -2,7 +2,7 @@
  * hot path (arXiv 2503.02223):
  *
  *   - the differentiable 3D Gaussian Splatting tile rasterizer the paper optimises its
- *     object Gaussians with ("CUDA kernels for rasterization and back propagation",
+ *     object Gaussians with (implemented, like its backward pass, as CUDA kernels per
  *     Sec. IV, implementation details): EWA projection, tile binning + depth radix
  *     sort, front-to-back blending of colour, depth, alpha, the instance channel
  *     ins (Eq. 15) and the object-id argmax map; the colour, depth and instance

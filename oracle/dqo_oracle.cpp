@@ -11,7 +11,7 @@
 //     sum (1 - IoU(BBox(C*), BBox_obs)).
 //   * Sec. III-D Eq. 7-10, 15: colour, depth and instance losses of the Gaussian-splatting
 //     render; ins = sum of blend weights of the pixel's own object's opaque Gaussians.
-//   * Sec. IV (impl.): "CUDA kernels for rasterization and back propagation" -- the
+//   * Sec. IV (impl.): rasterization and its backward pass run as CUDA kernels -- the
 //     rasterizer is the 3D Gaussian Splatting one the paper builds on (Sec. I, II-B);
 //     its unstated constants are the settings struct below.
 //
