@@ -69,3 +69,9 @@ def test_reference_band_height_fits_the_budget():
     assert bench.reference_band_rows(0.5, 2.0, 200, 10, 240.0) == 4     # 1.14 s per step
     assert bench.reference_band_rows(0.5, 2.0, 300, 10, 240.0) == 2     # 0.77 s per step
     assert bench.reference_band_rows(0.5, 2.0, 1000, 10, 240.0) == 1    # 0.24 s per step
+
+
+def test_peaks_fall_back_without_the_measured_file(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    peaks, src = bench.measured_peaks()
+    assert src == "fallback" and peaks["hbm_gbs"] == 6800.0 and peaks["bf16_tflops_sustained"] == 1700.0
