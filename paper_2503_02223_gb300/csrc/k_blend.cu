@@ -19,7 +19,7 @@
 // dL/da_j = T_j U_j - R_j / (1 - a_j) with U_j = dC.c_j + dD z_j + dA + dins [j counts]
 // and R_j = sum_{k>j} w_k U_k + T_final dC.bg.  The ten per-Gaussian partials are
 // summed over the warp by a transposing reduction (12 shuffles) and added to the global
-// per-Gaussian record with vector atomics once per (warp, Gaussian); when at most twelve
+// per-Gaussian record with vector atomics once per (warp, Gaussian); when at most sixteen
 // lanes contribute, each adds its own partials instead.
 #include "dqo_internal.cuh"
 
@@ -660,7 +660,7 @@ __device__ __forceinline__ float warp_transpose_sum10(const float v[10]) {
 
 // Up to this many contributing lanes a (warp, Gaussian) adds its partials with per-lane
 // atomics instead of a warp sum.
-constexpr int kFewLanes = 12;
+constexpr int kFewLanes = 16;
 
 // Backward of one tile's warp-blocks (local tile index); warp-autonomous, no block barrier.
 // The CTA holds NW warps; its warp w covers the tile's 8x4 block w0 + w.
