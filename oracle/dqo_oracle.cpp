@@ -275,9 +275,9 @@ struct PixelResult {
     int32_t id = -1;
     double id_margin = 0;
     uint8_t amb = 0;        // bit0 threshold, bit2 tile membership, bit3 loss kink
-    int64_t amb_pos = -1;   // first list position with a threshold decision near its threshold
-    int amb_kind = 0;       // which decision there: 1 alpha_min skip, 2 clamp, 3 stop
-    std::vector<std::pair<int64_t, int>> near;  // every (position, kind) near its threshold
+    // every (Gaussian, kind) whose decision is near its threshold here; kind 1 alpha_min
+    // skip, 2 clamp, 3 stop
+    std::vector<std::pair<int64_t, int>> near;
     int64_t stop_pos = -1;  // list position where the walk stopped (-1: ran to the end)
     std::vector<int64_t> amb_rect;  // Gaussians whose uncertain tile membership matters here
     std::vector<Contrib> contribs;
@@ -288,11 +288,17 @@ const int FLIP_SKIP = 1, FLIP_CLAMP = 2, FLIP_STOP = 3;
 
 bool near_rel(double a, double b, double rel) { return std::fabs(a - b) <= rel * std::fabs(b); }
 
-// Front-to-back blend of one pixel over the tile list L.  flip_pos / flip_kind invert one
-// decision (used to measure how much a decision near its threshold matters).
+// A decision taken the other way: Gaussian g's alpha_min skip, clamp or stop decision.
+struct Flip {
+    int64_t g;
+    int kind;
+};
+
+// Front-to-back blend of one pixel over the tile list L.  `flips` inverts the listed
+// decisions (used to measure how much decisions near their thresholds matter).
 PixelResult blend_pixel(const OSettings& st, const Inputs& in, const std::vector<Proj>& pr,
                         const std::vector<int64_t>& L, int px, int py, int32_t gt, bool keep,
-                        int64_t flip_pos = -1, int flip_kind = 0) {
+                        const std::vector<Flip>& flips = {}) {
     PixelResult R;
     std::vector<double> Wk(st.num_objects > 0 ? st.num_objects : 0, 0.0);
     double T = 1.0;
@@ -312,22 +318,25 @@ PixelResult blend_pixel(const OSettings& st, const Inputs& in, const std::vector
         const double ea = 0.5 * (std::fabs(P.conic[0] * dx + P.conic[1] * dy) * ulpx +
                                  std::fabs(P.conic[1] * dx + P.conic[2] * dy) * ulpy) + 1e-6;
         const double marg = std::max(st.amb_rel, 4 * ea);
-        const bool flip = (int64_t)j == flip_pos;
+        auto flipped = [&](int kind) {
+            for (const Flip& f : flips)
+                if (f.g == g && f.kind == kind) return true;
+            return false;
+        };
         bool clamped = oG > st.alpha_clamp;
-        if (flip && flip_kind == FLIP_CLAMP) clamped = !clamped;
+        if (flipped(FLIP_CLAMP)) clamped = !clamped;
         const double alpha = clamped ? st.alpha_clamp : oG;
         auto mark = [&](int kind) {
             R.amb |= AMB_THRESH;
-            if (R.amb_pos < 0) { R.amb_pos = (int64_t)j; R.amb_kind = kind; }
-            R.near.push_back({(int64_t)j, kind});
+            R.near.push_back({g, kind});
         };
         if (near_rel(oG, st.alpha_clamp, marg)) mark(FLIP_CLAMP);
         else if (near_rel(alpha, st.alpha_min, marg)) mark(FLIP_SKIP);
-        if ((alpha < st.alpha_min) != (flip && flip_kind == FLIP_SKIP)) continue;
+        if ((alpha < st.alpha_min) != flipped(FLIP_SKIP)) continue;
         const double Tn = T * (1 - alpha);
         eT += (clamped ? 0.0 : alpha * ea / (1 - alpha)) + 1e-7;
         if (near_rel(Tn, st.t_stop, std::max(st.amb_rel, 4 * eT))) mark(FLIP_STOP);
-        if ((Tn < st.t_stop) != (flip && flip_kind == FLIP_STOP)) {
+        if ((Tn < st.t_stop) != flipped(FLIP_STOP)) {
             R.stop_pos = (int64_t)j;
             break;
         }
@@ -594,17 +603,20 @@ int oracle_preprocess(const OSettings* st, const OCamera* cam, int64_t n, const 
 // Gaussians in (depth key, index) order.  Targets may be NULL (then no loss / pixel gradients).
 // Outputs (each may be NULL): rgb[H*W*3], depth, alpha, ins, id_map, T_final, n_contrib,
 // amb[H*W] (flag bits), id_margin[H*W], loss[4] (rgb, depth, ins, total),
-// dl[H*W*6] (dC r,g,b, dD, dA, dins).
+// dl[H*W*6] (dC r,g,b, dD, dA, dins).  Only pixel rows y0 <= v < y1 are rendered (y1 <= 0:
+// every row); other rows' outputs are left as they are and add nothing to the losses.
 int oracle_render(const OSettings* st, const OCamera* cam, int64_t n, const double* means,
                   const double* log_scales, const double* quats, const double* opacity_logit,
                   const double* rgb, const int32_t* obj_id, const uint8_t* flags,
                   const double* t_rgb, const double* t_depth, const int32_t* t_gt, int mode,
                   double* o_rgb, double* o_depth, double* o_alpha, double* o_ins, int32_t* o_id,
                   double* o_T, int64_t* o_ncontrib, uint8_t* o_amb, double* o_margin, double* o_loss,
-                  double* o_dl, uint8_t* o_mask, uint8_t* o_mask_amb) {
+                  double* o_dl, uint8_t* o_mask, uint8_t* o_mask_amb, int32_t y0, int32_t y1) {
     const Inputs in = make_inputs(n, means, log_scales, quats, opacity_logit, rgb, obj_id, flags);
     const int W = cam->width, H = cam->height;
     if (W <= 0 || H <= 0 || st->tile_w <= 0 || st->tile_h <= 0) return 1;
+    if (y1 <= 0 || y1 > H) y1 = H;
+    if (y0 < 0) y0 = 0;
     const int ntx = (W + st->tile_w - 1) / st->tile_w, nty = (H + st->tile_h - 1) / st->tile_h;
     std::vector<Proj> pr = project_all(*st, *cam, in);
     const std::vector<std::vector<int64_t>> tile_amb = rect_ambiguity(pr, ntx, nty);
@@ -615,11 +627,11 @@ int oracle_render(const OSettings* st, const OCamera* cam, int64_t n, const doub
     }
     double loss[3] = {0, 0, 0};
     const double inv_hw = 1.0 / ((double)W * H);
-    for (int ty = 0; ty < nty; ++ty)
+    for (int ty = y0 / st->tile_h; ty < nty && ty * st->tile_h < y1; ++ty)
         for (int tx = 0; tx < ntx; ++tx) {
             std::vector<int64_t> L;
             if (mode == 0) L = tile_list(pr, tx, ty);
-            for (int py = ty * st->tile_h; py < std::min(H, (ty + 1) * st->tile_h); ++py)
+            for (int py = std::max(y0, ty * st->tile_h); py < std::min(y1, (ty + 1) * st->tile_h); ++py)
                 for (int px = tx * st->tile_w; px < std::min(W, (tx + 1) * st->tile_w); ++px) {
                     const size_t p = (size_t)py * W + px;
                     const int32_t gt = t_gt ? t_gt[p] : -1;
@@ -705,11 +717,95 @@ int oracle_render_pixels(const OSettings* st, const OCamera* cam, int64_t n, con
     return 0;
 }
 
+// The outcomes a correct single-precision render may produce at selected pixels.  A pixel
+// whose result hangs on decisions within rounding distance of their thresholds (alpha_min
+// skip, clamp, transmittance stop; tile membership of a Gaussian whose rect edge is
+// uncertain) is re-rendered with each subset of those decisions taken the other way: every
+// subset when there are at most `full_items` of them, else the subsets of one or two.
+// Alternative 0 is the render as it stands.  px[npix*2] = (u, v).  Outputs per (pixel k,
+// alternative a), index k*max_alt + a: vals[*7] = (r, g, b, depth, alpha, ins, T_final),
+// n_contrib, id, id_margin; count[k] = alternatives written (at most max_alt).
+int oracle_render_alternatives(const OSettings* st, const OCamera* cam, int64_t n, const double* means,
+                               const double* log_scales, const double* quats, const double* opacity_logit,
+                               const double* rgb, const int32_t* obj_id, const uint8_t* flags,
+                               const int32_t* t_gt, int64_t npix, const int32_t* pxy, int32_t max_alt,
+                               int32_t full_items, int32_t* o_count, double* o_vals, int64_t* o_ncontrib,
+                               int32_t* o_id, double* o_margin) {
+    const Inputs in = make_inputs(n, means, log_scales, quats, opacity_logit, rgb, obj_id, flags);
+    const int W = cam->width, H = cam->height;
+    if (W <= 0 || H <= 0 || max_alt < 1) return 1;
+    const int ntx = (W + st->tile_w - 1) / st->tile_w, nty = (H + st->tile_h - 1) / st->tile_h;
+    std::vector<Proj> pr = project_all(*st, *cam, in);
+    const std::vector<std::vector<int64_t>> tile_amb = rect_ambiguity(pr, ntx, nty);
+    std::map<int64_t, std::vector<int64_t>> lists;  // tile lists of the tiles asked for
+    for (int64_t k = 0; k < npix; ++k) {
+        const int px = pxy[2 * k], py = pxy[2 * k + 1];
+        if (px < 0 || px >= W || py < 0 || py >= H) return 1;
+        const int tx = px / st->tile_w, ty = py / st->tile_h;
+        const int64_t tile = (int64_t)ty * ntx + tx;
+        auto it = lists.find(tile);
+        if (it == lists.end()) it = lists.emplace(tile, tile_list(pr, tx, ty)).first;
+        const std::vector<int64_t>& L = it->second;
+        const int32_t gt = t_gt ? t_gt[(size_t)py * W + px] : -1;
+        PixelResult R = blend_pixel(*st, in, pr, L, px, py, gt, false);
+        rect_check(*st, pr, tile_amb[(size_t)tile], px, py, R);
+        // the uncertain items: decision flips, then membership toggles (each Gaussian once)
+        std::vector<Flip> fl(R.near.size());
+        for (size_t i = 0; i < R.near.size(); ++i) fl[i] = Flip{R.near[i].first, R.near[i].second};
+        std::vector<int64_t> tog = R.amb_rect;
+        std::sort(tog.begin(), tog.end());
+        tog.erase(std::unique(tog.begin(), tog.end()), tog.end());
+        const int items = (int)(fl.size() + tog.size());
+        std::vector<std::vector<int>> subsets{{}};
+        if (items <= full_items) {
+            for (int mask = 1; mask < (1 << items); ++mask) {
+                std::vector<int> sub;
+                for (int i = 0; i < items; ++i)
+                    if (mask >> i & 1) sub.push_back(i);
+                subsets.push_back(sub);
+            }
+        } else {
+            for (int i = 0; i < items; ++i) subsets.push_back({i});
+            for (int i = 0; i < items; ++i)
+                for (int j = i + 1; j < items; ++j) subsets.push_back({i, j});
+        }
+        int a = 0;
+        for (const std::vector<int>& sub : subsets) {
+            if (a >= max_alt) break;
+            std::vector<Flip> f;
+            std::vector<int64_t> L1 = L;
+            bool changed_list = false;
+            for (int i : sub) {
+                if (i < (int)fl.size()) { f.push_back(fl[(size_t)i]); continue; }
+                const int64_t ga = tog[(size_t)i - fl.size()];
+                auto pos = std::find(L1.begin(), L1.end(), ga);
+                if (pos != L1.end()) L1.erase(pos);
+                else { L1.push_back(ga); changed_list = true; }
+            }
+            if (changed_list)
+                std::stable_sort(L1.begin(), L1.end(), [&](int64_t x, int64_t y) { return depth_less(pr, x, y); });
+            const PixelResult R1 = sub.empty() ? R : blend_pixel(*st, in, pr, L1, px, py, gt, false, f);
+            const size_t o = (size_t)k * max_alt + a;
+            double* v = o_vals + 7 * o;
+            v[0] = R1.C[0]; v[1] = R1.C[1]; v[2] = R1.C[2]; v[3] = R1.D; v[4] = R1.A; v[5] = R1.ins; v[6] = R1.T;
+            o_ncontrib[o] = R1.n_contrib;
+            o_id[o] = R1.id;
+            o_margin[o] = R1.id_margin;
+            ++a;
+        }
+        o_count[k] = a;
+    }
+    return 0;
+}
+
 // Backward of the render.  Pixel gradients: if dl (H*W*6 = dC rgb, dD, dA, dins) is NULL the
 // fused L1 losses against the targets are differentiated.  Outputs (accumulated +=, each may be
 // NULL): g2[n*10] (dxy, dconic a b c, dopac, drgb, dz), and parameter gradients.
 // g_amb[n]: bit0 the Gaussian's alpha decision is near a threshold somewhere, bit2 its tile
-// membership is uncertain somewhere, bit3 it feeds a pixel at an L1 kink.
+// membership is uncertain somewhere, bit3 it feeds a pixel at an L1 kink.  A pixel whose
+// upstream gradient is zero (all six dl entries zero, or, for the fused losses, an
+// unlabelled pixel) adds exactly zero to every gradient and every bound, so it is skipped
+// and sets no flag.
 // unc[n*14]: per parameter (means, log_scales, quats, logit, rgb) the summed absolute change
 // of the gradient when each near-threshold decision or uncertain membership is taken the
 // other way, pixel by pixel, plus a bound on single-precision rounding of the gradient's
@@ -763,12 +859,27 @@ int oracle_render_backward(const OSettings* st, const OCamera* cam, int64_t n, c
             for (int k = 0; k < 3; ++k) u[11 + k] += std::fabs(dc[k]);
         }
     };
+    // upstream gradient of pixel p is zero (see above)
+    auto inactive = [&](size_t p) {
+        if (dl) {
+            for (int k = 0; k < 6; ++k)
+                if (dl[6 * p + k] != 0) return false;
+            return true;
+        }
+        return !t_gt || t_gt[p] < 0;
+    };
     for (int ty = 0; ty < nty; ++ty)
         for (int tx = 0; tx < ntx; ++tx) {
+            bool any = false;
+            for (int py = ty * st->tile_h; py < std::min(H, (ty + 1) * st->tile_h) && !any; ++py)
+                for (int px = tx * st->tile_w; px < std::min(W, (tx + 1) * st->tile_w) && !any; ++px)
+                    any = !inactive((size_t)py * W + px);
+            if (!any) continue;
             std::vector<int64_t> L = tile_list(pr, tx, ty);
             for (int py = ty * st->tile_h; py < std::min(H, (ty + 1) * st->tile_h); ++py)
                 for (int px = tx * st->tile_w; px < std::min(W, (tx + 1) * st->tile_w); ++px) {
                     const size_t p = (size_t)py * W + px;
+                    if (inactive(p)) continue;
                     const int32_t gt = t_gt ? t_gt[p] : -1;
                     PixelResult R = blend_pixel(*st, in, pr, L, px, py, gt, true);
                     rect_check(*st, pr, tile_amb[(size_t)ty * ntx + tx], px, py, R);
@@ -807,11 +918,11 @@ int oracle_render_backward(const OSettings* st, const OCamera* cam, int64_t n, c
                         pixel_backward(*st, in, pr, R, pg, gt, sparse_acc(m0));
                         for (const auto& nk : R.near) {
                             // the same pixel with one near-threshold decision taken the other way
-                            PixelResult R1 = blend_pixel(*st, in, pr, L, px, py, gt, true, nk.first, nk.second);
+                            PixelResult R1 = blend_pixel(*st, in, pr, L, px, py, gt, true, {Flip{nk.first, nk.second}});
                             Sparse m1;
                             pixel_backward(*st, in, pr, R1, pg, gt, sparse_acc(m1));
                             add_uncertainty(m0, m1);
-                            if (g_amb) g_amb[L[(size_t)nk.first]] |= AMB_THRESH;
+                            if (g_amb) g_amb[nk.first] |= AMB_THRESH;
                         }
                         std::vector<int64_t> cand = R.amb_rect;
                         std::sort(cand.begin(), cand.end());
