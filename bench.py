@@ -37,13 +37,18 @@ METRIC = "fwd+bwd keyframe iters/s (300k Gaussians,1200×680) & quadric fits/s v
 UNIT = "iters/s"
 SEED = 1002
 NUM_OBJECTS = 31                 # ids 0 (room) .. 30
-SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # FMA = 2 flops
-# Algorithmic FP32 flops per (pixel, Gaussian) evaluation, counted from the kernels'
-# arithmetic (FMA = 2): forward = exponent 9 + alpha/transmittance 5 + colour/depth 8 +
-# instance 2 + weight 1; backward = exponent 9 + alpha 3 + transmittance 2 + upstream dot 9
-# + dalpha 5 + accumulator 2 + ten partials 15 + their sums 10.
-FLOPS_PER_EVAL = {"blend_fwd": 25, "blend_bwd": 55, "blend_step": 80}
+FP32_LANES = 128                 # FP32 lanes per SM (context figure beside the measured peak)
+# Algorithmic FP32 flops per (pixel, Gaussian) evaluation (FMA = 2 flops, the exponential
+# counted on its own pipe): forward ~20 (offset, quadratic form, alpha, transmittance,
+# weight, colour / depth / alpha accumulation), backward ~50 (the forward's evaluation
+# again, the upstream dot product, dL/dalpha, the ten per-Gaussian partials and their
+# sums).  The kernels' own instruction count is higher (25 + 55: instance channel, id
+# bookkeeping); the roofline uses the algorithmic count.
+FLOPS_PER_EVAL = {"blend_fwd": 20, "blend_bwd": 50, "blend_step": 70}
+FLOPS_PER_EVAL_KERNEL = {"blend_fwd": 25, "blend_bwd": 55, "blend_step": 80}
+# Quadric step: ~700 FP32 flops per (quadric, view) pair per forward + backward (Q* build
+# share, C* = P Q* P^T, tangent-line box, IoU and the adjoint back through them).
+QUADRIC_FLOPS_PER_PAIR = 700
 FIT_ITERS = 100
 KERNEL_SRC = {"blend_fwd": "k_blend.cu", "blend_bwd": "k_blend.cu", "blend_step": "k_blend.cu"}
 # Learned proposal: algorithmic flops per sample of one training step (FMA = 2): forward
@@ -82,6 +87,7 @@ def parse():
     p.add_argument("--batch", type=int, default=256)
     p.add_argument("--no-learned", action="store_true", help="skip the learned-proposal section")
     p.add_argument("--no-batched", action="store_true", help="skip the batched-keyframes section")
+    p.add_argument("--no-adjoint-1m", action="store_true", help="skip the 1M-Gaussian adjoint section")
     p.add_argument("--no-tune", action="store_true",
                    help="fixed step configuration (--tile, per-keyframe blend schedule) instead of the autotuner; "
                         "for profiling, where the tuner's timings are distorted")
@@ -100,6 +106,57 @@ def measured_peaks() -> tuple[dict, str]:
             return json.load(f), "measured"
     except (OSError, ValueError):
         return dict(FALLBACK_PEAKS), "fallback"
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (x86 'model name', or the Arm implementer/part fields)."""
+    try:
+        txt = open("/proc/cpuinfo").read()
+    except OSError:
+        return "unknown"
+    for key in ("model name", "Model name", "cpu model"):
+        for ln in txt.splitlines():
+            if ln.split(":")[0].strip() == key:
+                return ln.split(":", 1)[1].strip()
+    fields = {}
+    for ln in txt.splitlines():
+        if ":" in ln:
+            k, v = ln.split(":", 1)
+            fields.setdefault(k.strip(), v.strip())
+    if "CPU part" in fields:
+        return f"Arm implementer {fields.get('CPU implementer', '?')} part {fields['CPU part']}"
+    return "unknown"
+
+
+def alu_peaks(dqo, dev, stream, smi_id) -> dict:
+    """Measured FP32 FMA (TFLOP/s) and ex2 (T exponentials/s) throughput of this GPU: the
+    library's probe kernels, each launch filling every SM for about 5 ms, best of 5 timed
+    launches (burst, like the blend kernels inside a sub-millisecond step), CUDA events on
+    the launching stream, SM clocks sampled meanwhile."""
+    import torch
+    sink = torch.zeros(1, device=dev)
+    out = {}
+    clocks = ClockSampler(smi_id)
+    clocks.start()
+    for kind, name in ((dqo.ALU_FMA, "fp32_fma_tflops"), (dqo.ALU_EX2, "ex2_tops")):
+        iters = 64
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(2):                   # size the launch to about 5 ms
+            e0.record(stream)
+            dqo.dqo_alu_probe(kind, iters, sink, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            iters = max(1, int(iters * 5.0 / max(e0.elapsed_time(e1), 1e-3)))
+        best = 0.0
+        for _ in range(5):
+            e0.record(stream)
+            ops = dqo.dqo_alu_probe(kind, iters, sink, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = max(best, ops / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+        out[name] = best
+    out["clocks"] = clocks.stop()
+    return out
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -215,6 +272,33 @@ def oracle_full_parallel(kf, targets, threads: int, bands=None) -> tuple[float, 
     for th in ths:
         th.join()
     return time.perf_counter() - t0, len(bands)
+
+
+def oracle_fits(fq, threads: int, nfits: int | None = None) -> tuple[float, int, int]:
+    """FP64 oracle plain fits (Eq. 1 init + FIT_ITERS Adam steps) of the first nfits
+    quadrics of the batch, split into `threads` contiguous chunks run concurrently (the
+    oracle's calls release the interpreter lock).  Returns (seconds, fits, threads used)."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    q_ptr = fq["q_ptr"]
+    nq = q_ptr.shape[0] - 1 if nfits is None else min(nfits, q_ptr.shape[0] - 1)
+    edges = np.linspace(0, nq, min(threads, nq) + 1).astype(int)
+    chunks = [(a, b) for a, b in zip(edges[:-1], edges[1:]) if b > a]
+
+    def run(ab):
+        a, b = ab
+        p0, p1 = int(q_ptr[a]), int(q_ptr[b])
+        oracle.quadric_fit(fq["P"], q_ptr[a:b + 1] - p0, fq["pair_v"][p0:p1], fq["obs_bbox"][p0:p1], iters=FIT_ITERS)
+
+    t0 = time.perf_counter()
+    ths = [threading.Thread(target=run, args=(c,)) for c in chunks]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    return time.perf_counter() - t0, nq, len(chunks)
 
 
 def traffic_for(kernel: str):
@@ -576,17 +660,31 @@ def run_ours(args, rank, world, local_rank):
     e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     e2e_val = job_throughput(world, e_steps, e_ms)
 
-    # ---- roofline of the dominant kernel (FP32 pipe): the persistent forward + backward
-    # blend (its phase also holds the per-keyframe loss sum, a few microseconds)
+    # ---- measured FP32 FMA and ex2 peaks of this GPU (the library's probe kernels)
+    alu = alu_peaks(dqo, dev, stream, smi_id)
+    fp32_peak = alu["fp32_fma_tflops"]
+    props = torch.cuda.get_device_properties(local_rank)
+    sms = props.multi_processor_count
+    sm_max = clk.get("sm_max_mhz") or alu["clocks"].get("sm_max_mhz")
+    derived = sms * FP32_LANES * 2 * sm_max * 1e6 / 1e12 if sm_max else None
+
+    # ---- roofline of the dominant kernels (FP32 pipe): the blend's forward + backward
+    # (the phase also holds the per-keyframe loss sum, a few microseconds)
     dom = "blend_step"
     flops = FLOPS_PER_EVAL[dom] * evals
     achieved = flops / (phases[dom] * 1e-3) / 1e12
     kname = {dqo.SCHEDULE_FUSED: "k_blend_step", dqo.SCHEDULE_SPLIT: "k_blend_fwd_queue + k_blend_bwd_queue",
              dqo.SCHEDULE_PER_KEYFRAME: "k_blend_forward + k_blend_backward"}[sched]
-    roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic_for(dom),
+    ex2_per_step = 2 * evals                 # one exponential per evaluation, forward and backward
+    roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+            "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic_for(dom),
             "evals_per_launch": evals, "flops_per_eval": FLOPS_PER_EVAL[dom],
-            "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, no measured FP32 peak)"}
+            "frac_kernel_count": FLOPS_PER_EVAL_KERNEL[dom] * evals / (phases[dom] * 1e-3) / 1e12 / fp32_peak,
+            "ex2_frac": ex2_per_step / (phases[dom] * 1e-3) / 1e12 / alu["ex2_tops"],
+            "peak_basis": f"measured: FP32 FMA probe (dqo_alu_probe) on this GPU, best of 5 launches of ~5 ms "
+                          f"filling all {sms} SMs, median SM clock {alu['clocks'].get('sm_mhz')} MHz (of measured)",
+            "derived_peak_context": derived,
+            "ex2_peak_tops": alu["ex2_tops"]}
 
     # ---- HBM rooflines of the projection, sort and gradient-scatter phases
     peaks, peak_src = measured_peaks()
@@ -632,10 +730,19 @@ def run_ours(args, rank, world, local_rank):
     f1.record(stream)
     torch.cuda.synchronize()
     fit_ms = f0.elapsed_time(f1) / fit_reps
+    npairs_fit = int(fq["pair_v"].shape[0])
+    fit_flops = QUADRIC_FLOPS_PER_PAIR * npairs_fit * FIT_ITERS
+    fit_tflops = fit_flops / (fit_ms * 1e-3) / 1e12
     fits = {"value": world * nfit / (fit_ms * 1e-3), "unit": "fits/s", "ms_per_batch": fit_ms,
             "batch": nfit, "views": f"{int(fq['counts'].min())}..{int(fq['counts'].max())}",
-            "iters": FIT_ITERS, "form": "plain: Eq. 1 SVD init + 100 Adam steps, one launch",
-            "ok_fraction": float(f_ok.float().mean().item())}
+            "pairs": npairs_fit, "iters": FIT_ITERS, "form": "plain: Eq. 1 SVD init + 100 Adam steps, one launch",
+            "ok_fraction": float(f_ok.float().mean().item()),
+            "mean_bbox_loss": float(f_loss.mean().item()),
+            "roofline": {"bound": "alu", "achieved": fit_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": fit_tflops / fp32_peak, "flops_per_pair_step": QUADRIC_FLOPS_PER_PAIR,
+                         "flops_per_launch": fit_flops, "traffic": None,
+                         "note": "refinement flops only (the Eq. 1 initialisation is not counted)",
+                         "peak_basis": "measured FP32 FMA probe (of measured)"}}
 
     if not args.no_learned:
         fits["learned"] = learned_section(ctx, dev, stream, world, fd, nfit, fit_ms)
@@ -660,14 +767,33 @@ def run_ours(args, rank, world, local_rank):
             "quadric_fits": fits}
     if batched is not None:
         line["batched"] = batched
+    if not args.no_adjoint_1m:
+        line["adjoint_1m"] = adjoint_1m_section(dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         H_ = kf["camera"]["height"]
         cores = os.cpu_count() or 1
+        model = cpu_model()
         t_full, nb = oracle_full_parallel(kf, targets, cores)
-        line["cpu_baseline"] = {"value": 1.0 / t_full, "unit": UNIT, "cores": min(cores, nb), "kind": "oracle",
+        # single thread: one 16-row band (its projection of all Gaussians included), scaled
+        # to the whole image by rows -- an upper bound on the single-thread keyframe time
+        t_band, _ = oracle_full_parallel(kf, targets, 1, [(320, 16)])
+        line["cpu_baseline"] = {"value": 1.0 / t_full, "unit": UNIT, "cores": nb, "kind": "oracle",
+                                "host_cores": cores, "cpu_model": model,
                                 "sample": f"the whole {H_}-row image once (forward + backward, FP64), rows in {nb} "
-                                          f"bands of whole tile rows run concurrently, each band projecting all "
-                                          f"300k Gaussians"}
+                                          f"bands of whole tile rows run on {nb} threads, each band projecting all "
+                                          f"300k Gaussians",
+                                "single_thread": {"value": 1.0 / (t_band * H_ / 16), "unit": UNIT, "cores": 1,
+                                                  "sample": "one 16-row band (rows 320..335, forward + backward, "
+                                                            "projecting all 300k Gaussians) on one thread, scaled "
+                                                            f"by {H_}/16 rows"}}
+        t_fit, nf, nth = oracle_fits(fq, cores)
+        t_fit1, nf1, _ = oracle_fits(fq, 1)
+        fits["cpu_baseline"] = {"value": nf / t_fit, "unit": "fits/s", "cores": nth, "kind": "oracle",
+                                "host_cores": cores, "cpu_model": model,
+                                "sample": f"the same {nf} plain fits (FP64 Eq. 1 init + {FIT_ITERS} Adam steps), "
+                                          f"split into {nth} chunks run on {nth} threads",
+                                "single_thread": {"value": nf1 / t_fit1, "unit": "fits/s", "cores": 1,
+                                                  "sample": f"the same {nf1} fits on one thread"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -741,6 +867,56 @@ def learned_section(ctx, dev, stream, world, fd, nfit, plain_fit_ms):
                                                      else "fallback bf16 sustained figure (no measured peaks file)"),
                                       "flops_per_sample": MLP_FLOPS_PER_SAMPLE,
                                       "traffic": None}}}
+
+
+def adjoint_1m_section(dev, stream) -> dict:
+    """1M Gaussians at 1200x680 (the indoor recipe with 3.33x the Gaussians): forward with
+    the fused losses + backward through the library, the blend state recomputed in the
+    backward (the forward keeps only T_final and the blended count per pixel).  Reports the
+    device memory it takes and its time."""
+    import torch
+
+    from paper_2503_02223_gb300 import dqo, synth
+    kf = synth.indoor_keyframe(SEED + 4, n_total=1_000_000, object_total=783_000)
+    cam = kf["camera"]
+    g = dqo.to_device(kf["gaussians"], dev)
+    t = dqo.to_device(synth.raycast_targets(kf), dev)
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats(dev)
+    free0, _ = torch.cuda.mem_get_info(dev)
+    base = torch.cuda.memory_allocated(dev)
+    ctx = dqo.Context(dev.index)
+    st = dqo.settings()
+    out = dqo.alloc_outputs(cam["width"], cam["height"], dev)
+    grads = dqo.alloc_grads(g["means"].shape[0], dev)
+    gs, cs, ts = dqo.gaussians(g, NUM_OBJECTS), dqo.camera(cam), dqo.targets(t)
+
+    def step():
+        dqo.dqo_render_forward(ctx, st, gs, cs, ts, dqo.render_out(out), stream)
+        dqo.dqo_render_backward(ctx, st, gs, cs, ts, None, dqo.gaussian_grads(grads), stream)
+
+    step()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(dev)
+    torch_peak = torch.cuda.max_memory_allocated(dev) - base
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    e0.record(stream)
+    for _ in range(reps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    m, nvis, _ = dqo.dqo_get_counts(ctx)
+    ctx.close()
+    return {"gaussians": int(kf["gaussians"]["means"].shape[0]), "visible": int(nvis), "tile_gaussian_pairs": int(m),
+            "ms_per_iter": ms, "iters_per_s": 1e3 / ms,
+            "peak_memory_mib": {"device_in_use": (free0 - free1) / 2 ** 20, "torch_max_allocated": torch_peak / 2 ** 20},
+            "form": "dqo_render_forward (fused losses) + dqo_render_backward per iteration, the backward re-walking "
+                    "each pixel's list (no per-(pixel, Gaussian) state kept)"}
 
 
 def tune_table(dqo, ms) -> dict:

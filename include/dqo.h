@@ -251,17 +251,24 @@ DQO_API dqo_status dqo_get_counts(const dqo_ctx* ctx, int64_t* n_pairs, int64_t*
  * dqo_render_forward (DQO_BUF_DEPTH_ORDER) on keys the caller supplies.
  *   depth_keys [n] (device, read only): the float bit pattern of each Gaussian's positive
  *     camera depth, or 0xFFFFFFFF for a culled Gaussian (any uint32 keys sort correctly);
- *   order [n] (device, written): indices 0..n-1 ordered by (key, index).
- * Scratch memory is a fixed array of about 14.5 MiB inside the library, held by every GPU
+ *   order [n] (device, written): indices 0..n-1 ordered by (key, index);
+ *   status (device, optional, written): 0 when `order` is valid, 1 when one of the sort's
+ *     bounded look-back waits gave up after about a second (then `order` is not valid).
+ *     Read it after the stream has synchronised.
+ * Scratch memory is a fixed array of about 16 MiB inside the library, held by every GPU
  * that loads the library until the process exits.  n may be 0 .. 1048576 (2^20);
  * larger n returns DQO_EINVAL, as do NULL arrays with n > 0.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) for that device; make that
- * first call before any stream capture.  No call allocates device or host memory.  All
- * calls share the one scratch array, which keeps the previous call's contents: calls
- * that overlap on the GPU race and must be serialised by the caller (for example by
- * issuing them on one stream).  Asynchronous on `stream`; DQO_ECUDA on a CUDA failure. */
+ * looks up the array's device address (cudaGetSymbolAddress) for that device; with
+ * CUDA's lazy module loading that lookup may also load the library's device code onto
+ * that GPU, which allocates the array and synchronises the device.  Make one warm-up
+ * call on each device before a real-time loop or any stream capture.  No call allocates
+ * device or host memory itself.  All calls share the one scratch array, which keeps the
+ * previous call's contents (each call clears the parts it needs, including its error
+ * word): calls that overlap on the GPU race and must be serialised by the caller (for
+ * example by issuing them on one stream).  Asynchronous on `stream`; DQO_ECUDA on a CUDA
+ * failure. */
 DQO_API dqo_status dqo_depth_order_noalloc(const uint32_t* depth_keys, int64_t n, uint32_t* order,
-                                           dqo_stream stream);
+                                           uint32_t* status, dqo_stream stream);
 
 /* ------------------------------------------------------------------ dual quadrics */
 
@@ -491,6 +498,17 @@ DQO_API dqo_status dqo_mlp_check(dqo_ctx* ctx, int* timed_out);
  * give up).  The context stays usable afterwards.  No counterpart in the paper: this is
  * how a stalled completion is reported instead of hanging the GPU. */
 DQO_API dqo_status dqo_wait_probe(dqo_ctx* ctx, dqo_stream stream);
+
+/* Throughput probe of one arithmetic pipe, for the roofline the blend kernels are quoted
+ * against (no counterpart in the paper).  kind 0: FP32 fused multiply-add; kind 1: the
+ * special-function unit's 2^x (ex2.approx), the exponential of every blend evaluation.
+ * One launch fills every SM of the current device (8 CTAs of 256 threads per SM), each
+ * thread running 8 independent chains of iters x 16 operations.  *ops (host) receives
+ * the launch's operation count: flops for kind 0 (an FMA counts 2), exponentials for
+ * kind 1; the caller times the launch on `stream` (CUDA events) and divides.  sink: one
+ * device float, written only by an impossible outcome (it keeps the work live).
+ * Errors: DQO_EINVAL (kind not 0/1, iters < 1, NULL pointers), DQO_ECUDA. */
+DQO_API dqo_status dqo_alu_probe(int32_t kind, int32_t iters, float* sink, double* ops, dqo_stream stream);
 
 #ifdef __cplusplus
 }

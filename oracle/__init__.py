@@ -56,9 +56,9 @@ def _lib_handle():
             lib = C.CDLL(build())
             i64 = C.c_int64
             lib.oracle_preprocess.argtypes = [_P, _P, i64] + [_P] * 12
-            lib.oracle_render.argtypes = [_P, _P, i64] + [_P] * 10 + [C.c_int] + [_P] * 13 + [C.c_int32] * 2
+            lib.oracle_render.argtypes = [_P, _P, i64] + [_P] * 10 + [C.c_int] + [_P] * 14 + [C.c_int32] * 2
             lib.oracle_render_alternatives.argtypes = [_P, _P, i64] + [_P] * 8 + [i64, _P, C.c_int32, C.c_int32] + \
-                [_P] * 5
+                [_P] * 6
             lib.oracle_render_pixels.argtypes = [_P, _P, i64] + [_P] * 8 + [i64] + [_P] * 10
             lib.oracle_render_backward.argtypes = [_P, _P, i64] + [_P] * 19
             lib.oracle_bin_tiles.argtypes = [i64, _P, _P, _P, C.c_int, C.c_int, _P, _P]
@@ -153,7 +153,7 @@ def render(g: dict, cam: dict, st: OSettings | None = None, targets: dict | None
     with the losses of Eq. 7-10 (reading: per-pixel L1 means over labelled pixels) and the
     incremental-update masks of Eq. 11 (update_mask bit0 Mask_geo, bit1 Mask_rgb).
     rows = (y0, y1): render only pixel rows y0 <= v < y1 (the others stay zero and add
-    nothing to the losses)."""
+    nothing to the losses).  last[v, u] = index of the pixel's last blended Gaussian (-1: none)."""
     st = st or settings()
     m, s, q, o, c, i, f = _gauss(g)
     n = m.shape[0]
@@ -163,13 +163,14 @@ def render(g: dict, cam: dict, st: OSettings | None = None, targets: dict | None
                ins=np.zeros((H, W)), id_map=np.zeros((H, W), np.int32), T_final=np.zeros((H, W)),
                n_contrib=np.zeros((H, W), np.int64), amb=np.zeros((H, W), np.uint8),
                id_margin=np.zeros((H, W)), loss=np.zeros(4), dl=np.zeros((H, W, 6)),
-               update_mask=np.zeros((H, W), np.uint8), mask_amb=np.zeros((H, W), np.uint8))
+               update_mask=np.zeros((H, W), np.uint8), mask_amb=np.zeros((H, W), np.uint8),
+               last=np.zeros((H, W), np.int64))
     oc = camera(cam)
     rc = _lib_handle().oracle_render(C.byref(st), C.byref(oc), n, _ptr(m), _ptr(s), _ptr(q), _ptr(o),
                                      _ptr(c), _ptr(i), _ptr(f), _ptr(tr), _ptr(td), _ptr(tg), mode,
                                      *[_ptr(out[k]) for k in ("rgb", "depth", "alpha", "ins", "id_map",
                                                               "T_final", "n_contrib", "amb", "id_margin",
-                                                              "loss", "dl", "update_mask", "mask_amb")],
+                                                              "loss", "dl", "update_mask", "mask_amb", "last")],
                                      *(rows if rows is not None else (0, 0)))
     if rc:
         raise ValueError("oracle_render: invalid arguments")
@@ -183,7 +184,8 @@ def render_alternatives(g: dict, cam: dict, pxy, st: OSettings | None = None, gt
     (alpha skip / clamp / stop, uncertain tile membership) taken the other way (all subsets
     of up to `full_items` items, else those of one or two).  Returns count[k] and, per
     (k, alternative), vals[..., 7] = (r, g, b, depth, alpha, ins, T_final), n_contrib, id_map,
-    id_margin; alternative 0 is the render as it stands."""
+    id_margin, last (index of the last blended Gaussian, -1: none); alternative 0 is the render
+    as it stands."""
     st = st or settings()
     m, s, q, o, c, i, f = _gauss(g)
     n = m.shape[0]
@@ -191,12 +193,14 @@ def render_alternatives(g: dict, cam: dict, pxy, st: OSettings | None = None, gt
     k = pxy.shape[0]
     gt = None if gt_id is None else np.ascontiguousarray(gt_id, np.int32)
     out = dict(count=np.zeros(k, np.int32), vals=np.zeros((k, max_alt, 7)), n_contrib=np.zeros((k, max_alt), np.int64),
-               id_map=np.zeros((k, max_alt), np.int32), id_margin=np.zeros((k, max_alt)))
+               id_map=np.zeros((k, max_alt), np.int32), id_margin=np.zeros((k, max_alt)),
+               last=np.zeros((k, max_alt), np.int64))
     oc = camera(cam)
     rc = _lib_handle().oracle_render_alternatives(C.byref(st), C.byref(oc), n, _ptr(m), _ptr(s), _ptr(q), _ptr(o),
                                                   _ptr(c), _ptr(i), _ptr(f), _ptr(gt), k, _ptr(pxy), max_alt,
                                                   full_items, *[_ptr(out[x]) for x in ("count", "vals", "n_contrib",
-                                                                                       "id_map", "id_margin")])
+                                                                                       "id_map", "id_margin",
+                                                                                       "last")])
     if rc:
         raise ValueError("oracle_render_alternatives: pixel out of range")
     return out

@@ -272,6 +272,7 @@ struct Contrib {
 struct PixelResult {
     double C[3] = {0, 0, 0}, D = 0, A = 0, ins = 0, T = 1;
     int64_t n_contrib = 0;  // 1 + list position of the last blended Gaussian
+    int64_t last_g = -1;    // index of the last blended Gaussian (-1: none)
     int32_t id = -1;
     double id_margin = 0;
     uint8_t amb = 0;        // bit0 threshold, bit2 tile membership, bit3 loss kink
@@ -354,6 +355,7 @@ PixelResult blend_pixel(const OSettings& st, const Inputs& in, const std::vector
         if (keep) R.contribs.push_back({g, alpha, T, G, dx, dy, clamped, j});
         T = Tn;
         R.n_contrib = (int64_t)j + 1;
+        R.last_g = g;
     }
     R.T = T;
     for (int c = 0; c < 3; ++c) R.C[c] += T * st.bg[c];
@@ -603,7 +605,8 @@ int oracle_preprocess(const OSettings* st, const OCamera* cam, int64_t n, const 
 // Gaussians in (depth key, index) order.  Targets may be NULL (then no loss / pixel gradients).
 // Outputs (each may be NULL): rgb[H*W*3], depth, alpha, ins, id_map, T_final, n_contrib,
 // amb[H*W] (flag bits), id_margin[H*W], loss[4] (rgb, depth, ins, total),
-// dl[H*W*6] (dC r,g,b, dD, dA, dins).  Only pixel rows y0 <= v < y1 are rendered (y1 <= 0:
+// dl[H*W*6] (dC r,g,b, dD, dA, dins), update_mask, mask_amb, last[H*W] (index of the last
+// blended Gaussian, -1 if none).  Only pixel rows y0 <= v < y1 are rendered (y1 <= 0:
 // every row); other rows' outputs are left as they are and add nothing to the losses.
 int oracle_render(const OSettings* st, const OCamera* cam, int64_t n, const double* means,
                   const double* log_scales, const double* quats, const double* opacity_logit,
@@ -611,7 +614,7 @@ int oracle_render(const OSettings* st, const OCamera* cam, int64_t n, const doub
                   const double* t_rgb, const double* t_depth, const int32_t* t_gt, int mode,
                   double* o_rgb, double* o_depth, double* o_alpha, double* o_ins, int32_t* o_id,
                   double* o_T, int64_t* o_ncontrib, uint8_t* o_amb, double* o_margin, double* o_loss,
-                  double* o_dl, uint8_t* o_mask, uint8_t* o_mask_amb, int32_t y0, int32_t y1) {
+                  double* o_dl, uint8_t* o_mask, uint8_t* o_mask_amb, int64_t* o_last, int32_t y0, int32_t y1) {
     const Inputs in = make_inputs(n, means, log_scales, quats, opacity_logit, rgb, obj_id, flags);
     const int W = cam->width, H = cam->height;
     if (W <= 0 || H <= 0 || st->tile_w <= 0 || st->tile_h <= 0) return 1;
@@ -651,6 +654,7 @@ int oracle_render(const OSettings* st, const OCamera* cam, int64_t n, const doub
                     if (o_id) o_id[p] = R.id;
                     if (o_T) o_T[p] = R.T;
                     if (o_ncontrib) o_ncontrib[p] = R.n_contrib;
+                    if (o_last) o_last[p] = R.last_g;
                     if (o_amb) o_amb[p] = R.amb;
                     if (o_margin) o_margin[p] = R.id_margin;
                     if (o_dl) {
@@ -724,13 +728,14 @@ int oracle_render_pixels(const OSettings* st, const OCamera* cam, int64_t n, con
 // subset when there are at most `full_items` of them, else the subsets of one or two.
 // Alternative 0 is the render as it stands.  px[npix*2] = (u, v).  Outputs per (pixel k,
 // alternative a), index k*max_alt + a: vals[*7] = (r, g, b, depth, alpha, ins, T_final),
-// n_contrib, id, id_margin; count[k] = alternatives written (at most max_alt).
+// n_contrib, id, id_margin, last (index of the last blended Gaussian, -1 if none);
+// count[k] = alternatives written (at most max_alt).
 int oracle_render_alternatives(const OSettings* st, const OCamera* cam, int64_t n, const double* means,
                                const double* log_scales, const double* quats, const double* opacity_logit,
                                const double* rgb, const int32_t* obj_id, const uint8_t* flags,
                                const int32_t* t_gt, int64_t npix, const int32_t* pxy, int32_t max_alt,
                                int32_t full_items, int32_t* o_count, double* o_vals, int64_t* o_ncontrib,
-                               int32_t* o_id, double* o_margin) {
+                               int32_t* o_id, double* o_margin, int64_t* o_last) {
     const Inputs in = make_inputs(n, means, log_scales, quats, opacity_logit, rgb, obj_id, flags);
     const int W = cam->width, H = cam->height;
     if (W <= 0 || H <= 0 || max_alt < 1) return 1;
@@ -789,6 +794,7 @@ int oracle_render_alternatives(const OSettings* st, const OCamera* cam, int64_t 
             double* v = o_vals + 7 * o;
             v[0] = R1.C[0]; v[1] = R1.C[1]; v[2] = R1.C[2]; v[3] = R1.D; v[4] = R1.A; v[5] = R1.ins; v[6] = R1.T;
             o_ncontrib[o] = R1.n_contrib;
+            o_last[o] = R1.last_g;
             o_id[o] = R1.id;
             o_margin[o] = R1.id_margin;
             ++a;

@@ -370,6 +370,8 @@ __device__ __forceinline__ void write_bf16_copies(const MlpState& st, int i, flo
 
 cudaError_t mlp_gemm_setup();
 cudaError_t launch_bounded_wait_probe(int* flag, cudaStream_t s);
+// FP32 FMA (kind 0) or ex2 (kind 1) throughput probe over every SM; *ops = operations launched.
+cudaError_t launch_alu_probe(int kind, int iters, float* sink, double* ops, cudaStream_t s);
 cudaError_t launch_mlp_features(int nq, int nv, const float* P, const int32_t* q_ptr, const int32_t* pair_v,
                                 int npairs, const float* obs, const int32_t* counts, float inv_scale, uint16_t* X,
                                 uint16_t* XT, int64_t ldt, cudaStream_t s);

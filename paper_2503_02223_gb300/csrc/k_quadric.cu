@@ -29,49 +29,60 @@ __device__ __forceinline__ RotCoef rot_coef(float s) {  // s = |r|^2
   } else {
     const float th = sqrtf(s);
     float sn, cs;
-    sincosf(th, &sn, &cs);
-    c.A = sn / th;
-    c.B = (1.f - cs) / s;
-    c.Cc = (th * cs - sn) / (s * th);
-    c.Dd = (th * sn - 2.f * (1.f - cs)) / (s * s);
+    __sincosf(th, &sn, &cs);   // th < pi in the parameterisation's use; absolute error ~1e-6
+    const float is = __fdividef(1.f, s);
+    c.A = __fdividef(sn, th);
+    c.B = (1.f - cs) * is;
+    c.Cc = __fdividef((th * cs - sn) * is, th);
+    c.Dd = (th * sn - 2.f * (1.f - cs)) * is * is;
   }
   return c;
 }
 
-struct PairFwd {
-  bool valid;
-  float R[3][3], K[3][3], K2[3][3], MR[3][3], d[3], h[3];
-  float S00, S01, S02, S11, S12, S22;
-  float c13, c23, c33, su, sv;
-  float box[4];
+// The parts of the projection that depend on the quadric only (shared by all its views).
+struct QuadCommon {
+  float R[3][3], K[3][3], K2[3][3], d[3];
   RotCoef rc;
 };
 
-__device__ __forceinline__ void pair_forward(const float* __restrict__ p, const float* __restrict__ P, PairFwd& f) {
+__device__ __forceinline__ void quad_common(const float* __restrict__ p, QuadCommon& c) {
   const float r0 = p[6], r1 = p[7], r2 = p[8];
-  f.rc = rot_coef(r0 * r0 + r1 * r1 + r2 * r2);
-  f.K[0][0] = 0.f; f.K[0][1] = -r2; f.K[0][2] = r1;
-  f.K[1][0] = r2;  f.K[1][1] = 0.f; f.K[1][2] = -r0;
-  f.K[2][0] = -r1; f.K[2][1] = r0;  f.K[2][2] = 0.f;
+  c.rc = rot_coef(r0 * r0 + r1 * r1 + r2 * r2);
+  c.K[0][0] = 0.f; c.K[0][1] = -r2; c.K[0][2] = r1;
+  c.K[1][0] = r2;  c.K[1][1] = 0.f; c.K[1][2] = -r0;
+  c.K[2][0] = -r1; c.K[2][1] = r0;  c.K[2][2] = 0.f;
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      f.K2[i][j] = f.K[i][0] * f.K[0][j] + f.K[i][1] * f.K[1][j] + f.K[i][2] * f.K[2][j];
-      f.R[i][j] = (i == j ? 1.f : 0.f) + f.rc.A * f.K[i][j] + f.rc.B * f.K2[i][j];
+      c.K2[i][j] = c.K[i][0] * c.K[0][j] + c.K[i][1] * c.K[1][j] + c.K[i][2] * c.K[2][j];
+      c.R[i][j] = (i == j ? 1.f : 0.f) + c.rc.A * c.K[i][j] + c.rc.B * c.K2[i][j];
     }
 #pragma unroll
-  for (int k = 0; k < 3; ++k) f.d[k] = expf(2.f * p[3 + k]);
+  for (int k = 0; k < 3; ++k) c.d[k] = __expf(2.f * p[3 + k]);
+}
+
+struct PairFwd {
+  bool valid;
+  float MR[3][3], h[3];
+  float S00, S01, S02, S11, S12, S22;
+  float c13, c23, c33, su, sv, ic;
+  float box[4];
+};
+
+__device__ __forceinline__ void pair_forward(const float* __restrict__ p, const QuadCommon& qc,
+                                             const float* __restrict__ P, PairFwd& f) {
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     f.h[i] = P[4 * i] * p[0] + P[4 * i + 1] * p[1] + P[4 * i + 2] * p[2] + P[4 * i + 3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) f.MR[i][k] = P[4 * i] * f.R[0][k] + P[4 * i + 1] * f.R[1][k] + P[4 * i + 2] * f.R[2][k];
+    for (int k = 0; k < 3; ++k)
+      f.MR[i][k] = P[4 * i] * qc.R[0][k] + P[4 * i + 1] * qc.R[1][k] + P[4 * i + 2] * qc.R[2][k];
   }
   f.S00 = f.S01 = f.S02 = f.S11 = f.S12 = f.S22 = 0.f;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const float a0 = f.MR[0][k], a1 = f.MR[1][k], a2 = f.MR[2][k], dk = f.d[k];
+    const float a0 = f.MR[0][k], a1 = f.MR[1][k], a2 = f.MR[2][k], dk = qc.d[k];
     f.S00 += dk * a0 * a0; f.S01 += dk * a0 * a1; f.S02 += dk * a0 * a2;
     f.S11 += dk * a1 * a1; f.S12 += dk * a1 * a2; f.S22 += dk * a2 * a2;
   }
@@ -85,19 +96,21 @@ __device__ __forceinline__ void pair_forward(const float* __restrict__ p, const 
   f.su = f.valid ? sqrtf(du) : 0.f;
   f.sv = f.valid ? sqrtf(dv) : 0.f;
   if (f.valid) {
-    const float ic = 1.f / f.c33;
-    f.box[0] = (f.c13 + f.su) * ic;  // c33 < 0: the + root is the left edge
-    f.box[2] = (f.c13 - f.su) * ic;
-    f.box[1] = (f.c23 + f.sv) * ic;
-    f.box[3] = (f.c23 - f.sv) * ic;
+    f.ic = __fdividef(1.f, f.c33);
+    f.box[0] = (f.c13 + f.su) * f.ic;  // c33 < 0: the + root is the left edge
+    f.box[2] = (f.c13 - f.su) * f.ic;
+    f.box[1] = (f.c23 + f.sv) * f.ic;
+    f.box[3] = (f.c23 - f.sv) * f.ic;
   } else {
+    f.ic = 0.f;
     f.box[0] = f.box[1] = f.box[2] = f.box[3] = 0.f;
   }
 }
 
 // Loss 1 - IoU of one valid pair and its gradient w.r.t. the 9 parameters (added to g).
 __device__ __forceinline__ float pair_loss_grad(const float* __restrict__ P, const float* __restrict__ p,
-                                                const float* __restrict__ o, const PairFwd& f, float g[9]) {
+                                                const float* __restrict__ o, const QuadCommon& qc,
+                                                const PairFwd& f, float g[9]) {
   const float* b = f.box;
   const float ix0 = fmaxf(b[0], o[0]), iy0 = fmaxf(b[1], o[1]);
   const float ix1 = fminf(b[2], o[2]), iy1 = fminf(b[3], o[3]);
@@ -106,11 +119,12 @@ __device__ __forceinline__ float pair_loss_grad(const float* __restrict__ P, con
   const float inter = ov ? iw * ih : 0.f;
   const float bw = b[2] - b[0], bh = b[3] - b[1];
   const float U = bw * bh + (o[2] - o[0]) * (o[3] - o[1]) - inter;
-  const float iou = inter / U;
+  const float iU = __fdividef(1.f, U);
+  const float iou = inter * iU;
   // d(1 - IoU)
   const float g_iou = -1.f;
-  const float g_inter = g_iou * (U + inter) / (U * U);
-  const float g_ap = -g_iou * inter / (U * U);
+  const float g_inter = g_iou * (U + inter) * iU * iU;
+  const float g_ap = -g_iou * inter * iU * iU;
   float gb[4];
   gb[0] = -g_ap * bh; gb[2] = g_ap * bh;
   gb[1] = -g_ap * bw; gb[3] = g_ap * bw;
@@ -122,14 +136,14 @@ __device__ __forceinline__ float pair_loss_grad(const float* __restrict__ P, con
     if (b[3] < o[3]) gb[3] += g_ih;
   }
   // box <- (c13, c23, c33, su, sv)
-  const float ic = 1.f / f.c33;
+  const float ic = f.ic;
   const float g_c13 = (gb[0] + gb[2]) * ic;
   const float g_su = (gb[0] - gb[2]) * ic;
   const float g_c23 = (gb[1] + gb[3]) * ic;
   const float g_sv = (gb[1] - gb[3]) * ic;
   const float g_c33 = -(gb[0] * b[0] + gb[2] * b[2] + gb[1] * b[1] + gb[3] * b[3]) * ic;
-  const float g_du = g_su / (2.f * f.su);
-  const float g_dv = g_sv / (2.f * f.sv);
+  const float g_du = __fdividef(g_su, 2.f * f.su);
+  const float g_dv = __fdividef(g_sv, 2.f * f.sv);
   const float h0 = f.h[0], h1 = f.h[1], h2 = f.h[2];
   // (c13, c23, c33, du, dv) <- (S, h)
   const float gS02 = g_c13 + g_du * (2.f * f.S02 - 2.f * h0 * h2);
@@ -146,7 +160,7 @@ __device__ __forceinline__ float pair_loss_grad(const float* __restrict__ P, con
   float gMR[3][3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const float a0 = f.MR[0][k], a1 = f.MR[1][k], a2 = f.MR[2][k], dk = f.d[k];
+    const float a0 = f.MR[0][k], a1 = f.MR[1][k], a2 = f.MR[2][k], dk = qc.d[k];
     const float gd = gS00 * a0 * a0 + gS02 * a0 * a2 + gS22 * a2 * a2 + gS11 * a1 * a1 + gS12 * a1 * a2;
     g[3 + k] += 2.f * dk * gd;  // d_k = exp(2 l_k)
     gMR[0][k] = dk * (2.f * gS00 * a0 + gS02 * a2);
@@ -167,8 +181,8 @@ __device__ __forceinline__ float pair_loss_grad(const float* __restrict__ P, con
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      gK += gR[i][j] * f.K[i][j];
-      gK2 += gR[i][j] * f.K2[i][j];
+      gK += gR[i][j] * qc.K[i][j];
+      gK2 += gR[i][j] * qc.K2[i][j];
     }
   // <gR, E_i> with E_i = [e_i]x, and <gR, E_i K + K E_i>
   const float r[3] = {p[6], p[7], p[8]};
@@ -181,7 +195,7 @@ __device__ __forceinline__ float pair_loss_grad(const float* __restrict__ P, con
     float gEK = -2.f * r[i] * tr;
 #pragma unroll
     for (int j = 0; j < 3; ++j) gEK += (gR[j][i] + gR[i][j]) * r[j];
-    g[6 + i] += f.rc.A * gE[i] + f.rc.B * gEK + f.rc.Cc * r[i] * gK + f.rc.Dd * r[i] * gK2;
+    g[6 + i] += qc.rc.A * gE[i] + qc.rc.B * gEK + qc.rc.Cc * r[i] * gK + qc.rc.Dd * r[i] * gK2;
   }
   return 1.f - iou;
 }
@@ -202,12 +216,14 @@ __global__ void k_quadric_project(int nq, const float* __restrict__ params, int 
 #pragma unroll
   for (int k = 0; k < 9; ++k) p[k] = params[9 * q + k];
   const int k0 = max(q_ptr[q], 0), k1 = min(q_ptr[q + 1], npairs);
+  QuadCommon qc;
+  quad_common(p, qc);
   for (int k = k0 + lane; k < k1; k += 32) {
     const int v = pair_v[k];
     PairFwd f;
     bool ok = v >= 0 && v < nv;
     if (ok) {
-      pair_forward(p, Pm + 12 * v, f);
+      pair_forward(p, qc, Pm + 12 * v, f);
       ok = f.valid;
     }
     if (conic) {
@@ -246,13 +262,15 @@ __global__ void k_quadric_bbox_loss(int nq, const float* __restrict__ params, in
   }
   float l = 0.f;
   const int k0 = max(q_ptr[q], 0), k1 = min(q_ptr[q + 1], npairs);
+  QuadCommon qc;
+  quad_common(p, qc);
   for (int k = k0 + lane; k < k1; k += 32) {
     const int v = pair_v[k];
     if (v < 0 || v >= nv) continue;
     PairFwd f;
-    pair_forward(p, Pm + 12 * v, f);
+    pair_forward(p, qc, Pm + 12 * v, f);
     if (!f.valid) continue;
-    l += pair_loss_grad(Pm + 12 * v, p, obs + 4 * (int64_t)k, f, g);
+    l += pair_loss_grad(Pm + 12 * v, p, obs + 4 * (int64_t)k, qc, f, g);
   }
   l = warp_sum(l);
 #pragma unroll
@@ -269,16 +287,19 @@ __global__ void k_quadric_bbox_loss(int nq, const float* __restrict__ params, in
 // ---------------------------------------------------------------- plain multi-view fit
 
 constexpr int kFitWarps = 4;
+constexpr int kAtA = 55;          // upper triangle of the 10 x 10 normal matrix
 
-// One cyclic-Jacobi rotation sweep set on a symmetric n x n fp64 matrix held in shared
-// memory, the element updates spread over the warp's lanes (lane k owns row / column k).
-__device__ void warp_jacobi(int n, double* A, double* V, int lane) {
-  for (int k = lane; k < n * n; k += 32) V[k] = (k / n == k % n) ? 1.0 : 0.0;
+// Cyclic Jacobi eigen-decomposition of a symmetric n x n matrix in shared memory (the
+// element updates spread over the warp's lanes: lane k owns row / column k).  On return
+// the diagonal of A holds the eigenvalues and the columns of V the eigenvectors.
+template <typename T>
+__device__ void warp_jacobi(int n, T* A, T* V, int lane, int max_sweeps, T tol) {
+  for (int k = lane; k < n * n; k += 32) V[k] = (k / n == k % n) ? T(1) : T(0);
   __syncwarp();
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    double off = 0.0, tot = 0.0;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    T off = T(0), tot = T(0);
     for (int k = lane; k < n * n; k += 32) {
-      const double a = A[k] * A[k];
+      const T a = A[k] * A[k];
       tot += a;
       if (k / n != k % n) off += a;
     }
@@ -287,26 +308,26 @@ __device__ void warp_jacobi(int n, double* A, double* V, int lane) {
       off += __shfl_xor_sync(0xFFFFFFFFu, off, o);
       tot += __shfl_xor_sync(0xFFFFFFFFu, tot, o);
     }
-    if (off <= 1e-30 * tot || off == 0.0) break;
+    if (off <= tol * tot || off == T(0)) break;
     for (int p = 0; p < n - 1; ++p)
       for (int q = p + 1; q < n; ++q) {
-        const double apq = A[p * n + q];
-        if (apq == 0.0) continue;  // uniform: every lane reads the same value
-        const double th = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
-        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-        const double c = rsqrt(t * t + 1.0), sn = t * c;
+        const T apq = A[p * n + q];
+        if (apq == T(0)) continue;  // uniform: every lane reads the same value
+        const T th = (A[q * n + q] - A[p * n + p]) / (T(2) * apq);
+        const T t = (th >= T(0) ? T(1) : T(-1)) / (fabs(th) + sqrt(th * th + T(1)));
+        const T c = T(1) / sqrt(t * t + T(1)), sn = t * c;
         __syncwarp();
         if (lane < n) {
-          const double akp = A[lane * n + p], akq = A[lane * n + q];
+          const T akp = A[lane * n + p], akq = A[lane * n + q];
           A[lane * n + p] = c * akp - sn * akq;
           A[lane * n + q] = sn * akp + c * akq;
         }
         __syncwarp();
         if (lane < n) {
-          const double apk = A[p * n + lane], aqk = A[q * n + lane];
+          const T apk = A[p * n + lane], aqk = A[q * n + lane];
           A[p * n + lane] = c * apk - sn * aqk;
           A[q * n + lane] = sn * apk + c * aqk;
-          const double vkp = V[lane * n + p], vkq = V[lane * n + q];
+          const T vkp = V[lane * n + p], vkq = V[lane * n + q];
           V[lane * n + p] = c * vkp - sn * vkq;
           V[lane * n + q] = sn * vkp + c * vkq;
         }
@@ -316,161 +337,218 @@ __device__ void warp_jacobi(int n, double* A, double* V, int lane) {
 }
 
 // Rotation matrix -> rotation vector through the unit quaternion (Shepperd's branch).
-__device__ void rotmat_to_rotvec(const double R[3][3], double r[3]) {
-  const double tr = R[0][0] + R[1][1] + R[2][2];
-  double w, x, y, z;
-  if (tr > 0.0) {
-    const double s = 2.0 * sqrt(tr + 1.0);
-    w = 0.25 * s; x = (R[2][1] - R[1][2]) / s; y = (R[0][2] - R[2][0]) / s; z = (R[1][0] - R[0][1]) / s;
+template <typename T>
+__device__ void rotmat_to_rotvec(const T R[3][3], T r[3]) {
+  const T tr = R[0][0] + R[1][1] + R[2][2];
+  T w, x, y, z;
+  if (tr > T(0)) {
+    const T s = T(2) * sqrt(tr + T(1));
+    w = T(0.25) * s; x = (R[2][1] - R[1][2]) / s; y = (R[0][2] - R[2][0]) / s; z = (R[1][0] - R[0][1]) / s;
   } else if (R[0][0] > R[1][1] && R[0][0] > R[2][2]) {
-    const double s = 2.0 * sqrt(1.0 + R[0][0] - R[1][1] - R[2][2]);
-    w = (R[2][1] - R[1][2]) / s; x = 0.25 * s; y = (R[0][1] + R[1][0]) / s; z = (R[0][2] + R[2][0]) / s;
+    const T s = T(2) * sqrt(T(1) + R[0][0] - R[1][1] - R[2][2]);
+    w = (R[2][1] - R[1][2]) / s; x = T(0.25) * s; y = (R[0][1] + R[1][0]) / s; z = (R[0][2] + R[2][0]) / s;
   } else if (R[1][1] > R[2][2]) {
-    const double s = 2.0 * sqrt(1.0 + R[1][1] - R[0][0] - R[2][2]);
-    w = (R[0][2] - R[2][0]) / s; x = (R[0][1] + R[1][0]) / s; y = 0.25 * s; z = (R[1][2] + R[2][1]) / s;
+    const T s = T(2) * sqrt(T(1) + R[1][1] - R[0][0] - R[2][2]);
+    w = (R[0][2] - R[2][0]) / s; x = (R[0][1] + R[1][0]) / s; y = T(0.25) * s; z = (R[1][2] + R[2][1]) / s;
   } else {
-    const double s = 2.0 * sqrt(1.0 + R[2][2] - R[0][0] - R[1][1]);
-    w = (R[1][0] - R[0][1]) / s; x = (R[0][2] + R[2][0]) / s; y = (R[1][2] + R[2][1]) / s; z = 0.25 * s;
+    const T s = T(2) * sqrt(T(1) + R[2][2] - R[0][0] - R[1][1]);
+    w = (R[1][0] - R[0][1]) / s; x = (R[0][2] + R[2][0]) / s; y = (R[1][2] + R[2][1]) / s; z = T(0.25) * s;
   }
-  if (w < 0.0) { w = -w; x = -x; y = -y; z = -z; }
-  const double vn = sqrt(x * x + y * y + z * z);
-  const double f = vn > 1e-300 ? 2.0 * atan2(vn, w) / vn : 2.0;
+  if (w < T(0)) { w = -w; x = -x; y = -y; z = -z; }
+  const T vn = sqrt(x * x + y * y + z * z);
+  const T f = vn > T(1e-30) ? T(2) * atan2(vn, w) / vn : T(2);
   r[0] = f * x; r[1] = f * y; r[2] = f * z;
 }
 
-// Eq. 1 initialisation of one quadric by one warp (fp64).  Same reading as the library's
-// documentation: planes of the box edges in a frame centred on the views' camera centres
-// and scaled to unit mean distance, unit-norm rows, null vector of A^T A, Q*44 = -1,
-// eigen-decomposition of Q*[0:3,0:3] + t t^T (descending, >= 1e-6, det R = +1).
+__device__ __forceinline__ float warp_sum(float v);
+
+// Camera centre C = -M^-1 p of P = [M | p] (adjugate over the determinant); false if M is
+// singular.
+__device__ __forceinline__ bool camera_centre(const float* __restrict__ P, float C[3]) {
+  const float a = P[0], b = P[1], c = P[2], d = P[4], e = P[5], f = P[6], g = P[8], h = P[9], i = P[10];
+  const float det = a * (e * i - f * h) - b * (d * i - f * g) + c * (d * h - e * g);
+  if (det == 0.f) return false;
+  const float p0 = P[3], p1 = P[7], p2 = P[11];
+  const float id = 1.f / det;
+  C[0] = -((e * i - f * h) * p0 + (c * h - b * i) * p1 + (b * f - c * e) * p2) * id;
+  C[1] = -((f * g - d * i) * p0 + (a * i - c * g) * p1 + (c * d - a * f) * p2) * id;
+  C[2] = -((d * h - e * g) * p0 + (b * g - a * h) * p1 + (a * e - b * d) * p2) * id;
+  return true;
+}
+
+// Eq. 1 initialisation of one quadric by one warp, in single precision.  Same reading as
+// the library's documentation: planes of the box edges in a frame centred on the views'
+// camera centres and scaled to unit mean distance, unit-norm rows, null vector of A^T A,
+// Q*44 = -1, eigen-decomposition of Q*[0:3,0:3] + t t^T (descending, >= 1e-6, det R = +1).
+// The views are spread over the lanes: each lane accumulates the normal matrix of its own
+// views' rows (55 entries), and the lanes' partial matrices are summed through shared
+// memory.  sm: 32 x 56 floats of this warp.
 __device__ bool warp_quadric_init(int k0, int k1, const float* __restrict__ Pm, const int32_t* __restrict__ pair_v,
-                                  const float* __restrict__ obs, int nv, double* sm, int lane, float out[9]) {
-  double* AtA = sm;        // 100
-  double* V = sm + 100;    // 100
+                                  const float* __restrict__ obs, int nv, float* sm, int lane, float out[9]) {
   const int nview = k1 - k0;
-  // camera centres: C = -M^-1 p, accumulated over the warp
-  double cs[3] = {0.0, 0.0, 0.0};
+  float cs[3] = {0.f, 0.f, 0.f};
   bool good = true;
   for (int k = k0 + lane; k < k1; k += 32) {
     const int v = pair_v[k];
-    if (v < 0 || v >= nv) { good = false; continue; }
-    const float* P = Pm + 12 * v;
-    const double a = P[0], b = P[1], c = P[2], d = P[4], e = P[5], f = P[6], g = P[8], h = P[9], i = P[10];
-    const double det = a * (e * i - f * h) - b * (d * i - f * g) + c * (d * h - e * g);
-    if (det == 0.0) { good = false; continue; }
-    const double p0 = P[3], p1 = P[7], p2 = P[11];
-    cs[0] += -((e * i - f * h) * p0 + (c * h - b * i) * p1 + (b * f - c * e) * p2) / det;
-    cs[1] += -((f * g - d * i) * p0 + (a * i - c * g) * p1 + (c * d - a * f) * p2) / det;
-    cs[2] += -((d * h - e * g) * p0 + (b * g - a * h) * p1 + (a * e - b * d) * p2) / det;
+    float C[3];
+    if (v < 0 || v >= nv || !camera_centre(Pm + 12 * v, C)) { good = false; continue; }
+    cs[0] += C[0]; cs[1] += C[1]; cs[2] += C[2];
   }
   good = __all_sync(0xFFFFFFFFu, good);
   if (!good || nview < 3) return false;
+  const float inv_n = 1.f / (float)nview;
+  const float cx = warp_sum(cs[0]) * inv_n, cy = warp_sum(cs[1]) * inv_n, cz = warp_sum(cs[2]) * inv_n;
+  float md = 0.f;
+  for (int k = k0 + lane; k < k1; k += 32) {
+    float C[3];
+    camera_centre(Pm + 12 * pair_v[k], C);
+    md += sqrtf((C[0] - cx) * (C[0] - cx) + (C[1] - cy) * (C[1] - cy) + (C[2] - cz) * (C[2] - cz));
+  }
+  md = warp_sum(md) * inv_n;
+  const float sc = md > 0.f ? 1.f / md : 1.f;
+  // this lane's views: 4 tangent planes each, normalised, their monomial rows accumulated
+  float acc[kAtA];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) cs[j] += __shfl_xor_sync(0xFFFFFFFFu, cs[j], o);
-  const double cx = cs[0] / nview, cy = cs[1] / nview, cz = cs[2] / nview;
-  double md = 0.0;
+  for (int e = 0; e < kAtA; ++e) acc[e] = 0.f;
   for (int k = k0 + lane; k < k1; k += 32) {
     const float* P = Pm + 12 * pair_v[k];
-    const double a = P[0], b = P[1], c = P[2], d = P[4], e = P[5], f = P[6], g = P[8], h = P[9], i = P[10];
-    const double det = a * (e * i - f * h) - b * (d * i - f * g) + c * (d * h - e * g);
-    const double p0 = P[3], p1 = P[7], p2 = P[11];
-    const double X = -((e * i - f * h) * p0 + (c * h - b * i) * p1 + (b * f - c * e) * p2) / det;
-    const double Y = -((f * g - d * i) * p0 + (a * i - c * g) * p1 + (c * d - a * f) * p2) / det;
-    const double Z = -((d * h - e * g) * p0 + (b * g - a * h) * p1 + (a * e - b * d) * p2) / det;
-    md += sqrt((X - cx) * (X - cx) + (Y - cy) * (Y - cy) + (Z - cz) * (Z - cz));
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) md += __shfl_xor_sync(0xFFFFFFFFu, md, o);
-  md /= nview;
-  const double sc = md > 0.0 ? 1.0 / md : 1.0;
-  // A^T A: lane j < 100 owns entry j; every lane walks all rows (4 per view)
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // entries lane, lane + 32, lane + 64, lane + 96
-  for (int k = k0; k < k1; ++k) {
-    const float* P = Pm + 12 * pair_v[k];
     const float* bb = obs + 4 * (int64_t)k;
-    for (int ed = 0; ed < 4; ++ed) {
-      const double l0 = ed < 2 ? 1.0 : 0.0, l1 = ed < 2 ? 0.0 : 1.0;
-      const double l2 = -(double)bb[ed == 0 ? 0 : ed == 1 ? 2 : ed == 2 ? 1 : 3];
-      double pi[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) pi[j] = l0 * P[j] + l1 * P[4 + j] + l2 * P[8 + j];
-      double pn[4] = {pi[0] / sc, pi[1] / sc, pi[2] / sc, pi[0] * cx + pi[1] * cy + pi[2] * cz + pi[3]};
-      const double nr = rsqrt(pn[0] * pn[0] + pn[1] * pn[1] + pn[2] * pn[2] + pn[3] * pn[3]);
+    for (int ed = 0; ed < 4; ++ed) {
+      // edge lines u = u_min, u = u_max (l = (1, 0, -u)), v = v_min, v = v_max (l = (0, 1, -v))
+      const float lb = -bb[ed == 0 ? 0 : ed == 1 ? 2 : ed == 2 ? 1 : 3];
+      float pi[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) pi[j] = (ed < 2 ? P[j] : P[4 + j]) + lb * P[8 + j];
+      float pn[4] = {pi[0] * md, pi[1] * md, pi[2] * md, pi[0] * cx + pi[1] * cy + pi[2] * cz + pi[3]};
+      const float nr = rsqrtf(pn[0] * pn[0] + pn[1] * pn[1] + pn[2] * pn[2] + pn[3] * pn[3]);
 #pragma unroll
       for (int j = 0; j < 4; ++j) pn[j] *= nr;
-      const double row[10] = {pn[0] * pn[0], 2 * pn[0] * pn[1], 2 * pn[0] * pn[2], 2 * pn[0] * pn[3], pn[1] * pn[1],
-                              2 * pn[1] * pn[2], 2 * pn[1] * pn[3], pn[2] * pn[2], 2 * pn[2] * pn[3], pn[3] * pn[3]};
+      const float row[10] = {pn[0] * pn[0], 2.f * pn[0] * pn[1], 2.f * pn[0] * pn[2], 2.f * pn[0] * pn[3],
+                             pn[1] * pn[1], 2.f * pn[1] * pn[2], 2.f * pn[1] * pn[3], pn[2] * pn[2],
+                             2.f * pn[2] * pn[3], pn[3] * pn[3]};
+      int e = 0;
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const int e = lane + 32 * m;
-        if (e < 100) acc[m] += row[e / 10] * row[e % 10];
-      }
+      for (int i = 0; i < 10; ++i)
+#pragma unroll
+        for (int j = i; j < 10; ++j) acc[e++] += row[i] * row[j];
     }
   }
+  // sum the lanes' partial matrices: transpose through shared memory
+  float* red = sm;          // [32][56]
 #pragma unroll
-  for (int m = 0; m < 4; ++m) {
+  for (int e = 0; e < kAtA; ++e) red[lane * 56 + e] = acc[e];
+  __syncwarp();
+  float tot[2] = {0.f, 0.f};
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
     const int e = lane + 32 * m;
-    if (e < 100) AtA[e] = acc[m];
+    if (e < kAtA)
+      for (int l = 0; l < 32; ++l) tot[m] += red[l * 56 + e];
   }
   __syncwarp();
-  warp_jacobi(10, AtA, V, lane);
+  float* AtA = sm;          // 100, reusing the reduction area
+  float* V = sm + 100;      // 100
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    const int e = lane + 32 * m;
+    if (e < kAtA) {
+      int i = 0, r = e;     // upper-triangle index -> (i, j)
+      while (r >= 10 - i) { r -= 10 - i; ++i; }
+      const int j = i + r;
+      AtA[i * 10 + j] = tot[m];
+      AtA[j * 10 + i] = tot[m];
+    }
+  }
+  __syncwarp();
+  warp_jacobi<float>(10, AtA, V, lane, 20, 1e-13f);
   // smallest eigenvalue's vector
   int kmin = 0;
   for (int k = 1; k < 10; ++k)
     if (AtA[k * 11] < AtA[kmin * 11]) kmin = k;
-  double q[10];
+  float q[10];
 #pragma unroll
   for (int k = 0; k < 10; ++k) q[k] = V[k * 10 + kmin];
   // back to the world frame: Q* = Ti Q' Ti^T, Ti = [[I/sc, c], [0, 1]]
-  const double Qn[4][4] = {{q[0], q[1], q[2], q[3]}, {q[1], q[4], q[5], q[6]},
-                           {q[2], q[5], q[7], q[8]}, {q[3], q[6], q[8], q[9]}};
-  const double Ti[4][4] = {{1 / sc, 0, 0, cx}, {0, 1 / sc, 0, cy}, {0, 0, 1 / sc, cz}, {0, 0, 0, 1}};
-  double Q[4][4];
+  const float Qn[4][4] = {{q[0], q[1], q[2], q[3]}, {q[1], q[4], q[5], q[6]},
+                          {q[2], q[5], q[7], q[8]}, {q[3], q[6], q[8], q[9]}};
+  const float Ti[4][4] = {{md, 0.f, 0.f, cx}, {0.f, md, 0.f, cy}, {0.f, 0.f, md, cz}, {0.f, 0.f, 0.f, 1.f}};
+  float Q[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      double s2 = 0.0;
+      float s2 = 0.f;
 #pragma unroll
       for (int k = 0; k < 4; ++k)
 #pragma unroll
         for (int l = 0; l < 4; ++l) s2 += Ti[i][k] * Qn[k][l] * Ti[j][l];
       Q[i][j] = s2;
     }
-  if (fabs(Q[3][3]) < 1e-300) return false;
-  const double fs = -1.0 / Q[3][3];
-  const double t[3] = {-Q[0][3] * fs, -Q[1][3] * fs, -Q[2][3] * fs};
-  double* M = sm;  // reuse: 9 entries + 9 eigenvectors
-  double* E = sm + 16;
+  (void)sc;
+  if (fabsf(Q[3][3]) < 1e-30f) return false;
+  const float fs = -1.f / Q[3][3];
+  const float t[3] = {-Q[0][3] * fs, -Q[1][3] * fs, -Q[2][3] * fs};
+  float* M = sm + 200;      // 9 entries + 9 eigenvectors
+  float* E = sm + 216;
   __syncwarp();
   if (lane < 9) M[lane] = Q[lane / 3][lane % 3] * fs + t[lane / 3] * t[lane % 3];
   __syncwarp();
-  warp_jacobi(3, M, E, lane);
+  warp_jacobi<float>(3, M, E, lane, 20, 1e-13f);
   int ord[3] = {0, 1, 2};
   if (M[4 * ord[1]] > M[4 * ord[0]]) { const int x = ord[0]; ord[0] = ord[1]; ord[1] = x; }
   if (M[4 * ord[2]] > M[4 * ord[1]]) { const int x = ord[1]; ord[1] = ord[2]; ord[2] = x; }
   if (M[4 * ord[1]] > M[4 * ord[0]]) { const int x = ord[0]; ord[0] = ord[1]; ord[1] = x; }
-  double R[3][3];
+  float R[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int k = 0; k < 3; ++k) R[i][k] = E[3 * i + ord[k]];
-  const double dR = R[0][0] * (R[1][1] * R[2][2] - R[1][2] * R[2][1]) - R[0][1] * (R[1][0] * R[2][2] - R[1][2] * R[2][0]) +
-                    R[0][2] * (R[1][0] * R[2][1] - R[1][1] * R[2][0]);
-  if (dR < 0.0)
+  const float dR = R[0][0] * (R[1][1] * R[2][2] - R[1][2] * R[2][1]) - R[0][1] * (R[1][0] * R[2][2] - R[1][2] * R[2][0]) +
+                   R[0][2] * (R[1][0] * R[2][1] - R[1][1] * R[2][0]);
+  if (dR < 0.f)
 #pragma unroll
     for (int i = 0; i < 3; ++i) R[i][2] = -R[i][2];
-  double rv[3];
-  rotmat_to_rotvec(R, rv);
+  float rv[3];
+  rotmat_to_rotvec<float>(R, rv);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    out[k] = (float)t[k];
-    out[3 + k] = (float)(0.5 * log(fmax(M[4 * ord[k]], 1e-6)));
-    out[6 + k] = (float)rv[k];
+    out[k] = t[k];
+    out[3 + k] = 0.5f * logf(fmaxf(M[4 * ord[k]], 1e-6f));
+    out[6 + k] = rv[k];
   }
   __syncwarp();
   return true;
+}
+
+// Warp sum of 16 values per lane in 16 shuffles (a transposing reduction): each stage
+// keeps half of the values and sends the other half to the partner lane.  Lane L returns
+// the total of value (L >> 1) & 15 (lanes 2v and 2v + 1 hold value v).
+__device__ __forceinline__ float warp_transpose_sum16(const float (&v)[16], int lane) {
+  float a8[8];
+  const bool b4 = lane & 16;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float keep = b4 ? v[i + 8] : v[i], send = b4 ? v[i] : v[i + 8];
+    a8[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 16);
+  }
+  float a4[4];
+  const bool b3 = lane & 8;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float keep = b3 ? a8[i + 4] : a8[i], send = b3 ? a8[i] : a8[i + 4];
+    a4[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 8);
+  }
+  float a2[2];
+  const bool b2 = lane & 4;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float keep = b2 ? a4[i + 2] : a4[i], send = b2 ? a4[i] : a4[i + 2];
+    a2[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, 4);
+  }
+  const bool b1 = lane & 2;
+  const float a1 = (b1 ? a2[1] : a2[0]) + __shfl_xor_sync(0xFFFFFFFFu, b1 ? a2[0] : a2[1], 2);
+  return a1 + __shfl_xor_sync(0xFFFFFFFFu, a1, 1);
 }
 
 __global__ void __launch_bounds__(32 * kFitWarps) k_quadric_fit(int nq, int nv, const float* __restrict__ Pm,
@@ -482,7 +560,7 @@ __global__ void __launch_bounds__(32 * kFitWarps) k_quadric_fit(int nq, int nv, 
                                                                   float* __restrict__ params_out,
                                                                   float* __restrict__ loss_out,
                                                                   uint8_t* __restrict__ ok_out) {
-  __shared__ double sm[kFitWarps][200];
+  __shared__ float sm[kFitWarps][32 * 56];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q = blockIdx.x * kFitWarps + w;
   if (q >= nq) return;
@@ -506,35 +584,43 @@ __global__ void __launch_bounds__(32 * kFitWarps) k_quadric_fit(int nq, int nv, 
     return;
   }
   if (init_out && lane < 9) init_out[9 * q + lane] = p[lane];
-  // refinement: Adam on the Eq. 12 loss, every lane holding the parameters
-  float m[9], v[9];
+  // Refinement: Adam on the Eq. 12 loss.  Every lane evaluates its views with all nine
+  // parameters; after the transposing reduction lanes 2k and 2k + 1 hold the gradient of
+  // parameter k (k < 9; lanes 18, 19 the loss) and run that parameter's Adam update, and
+  // the nine new values are broadcast back.
+  const int mine = (lane >> 1) & 15;
+  float pm = 0.f;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) m[k] = v[k] = 0.f;
+  for (int k = 0; k < 9; ++k)
+    if (mine == k) pm = p[k];
+  float m1 = 0.f, m2 = 0.f;
   float b1t = 1.f, b2t = 1.f, L = 0.f;
   for (int it = 0; it <= iters; ++it) {
-    float g[9], l = 0.f;
+    QuadCommon qc;
+    quad_common(p, qc);
+    float g[16];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) g[k] = 0.f;
+    for (int k = 0; k < 16; ++k) g[k] = 0.f;
     for (int k = k0 + lane; k < k1; k += 32) {
       const int vw = pair_v[k];
       PairFwd f;
-      pair_forward(p, Pm + 12 * vw, f);
+      pair_forward(p, qc, Pm + 12 * vw, f);
       if (!f.valid) continue;
-      l += pair_loss_grad(Pm + 12 * vw, p, obs + 4 * (int64_t)k, f, g);
+      g[9] += pair_loss_grad(Pm + 12 * vw, p, obs + 4 * (int64_t)k, qc, f, g);
     }
-    L = warp_sum(l);
-    if (it == iters) break;  // the last pass only evaluates the final loss
-#pragma unroll
-    for (int k = 0; k < 9; ++k) g[k] = warp_sum(g[k]);
+    const float tot = warp_transpose_sum16(g, lane);
+    if (it == iters) {  // the last pass only evaluates the final loss
+      L = __shfl_sync(0xFFFFFFFFu, tot, 18);
+      break;
+    }
     b1t *= 0.9f;
     b2t *= 0.999f;
+    m1 = 0.9f * m1 + 0.1f * tot;
+    m2 = 0.999f * m2 + 0.001f * tot * tot;
+    const float mh = m1 / (1.f - b1t), vh = m2 / (1.f - b2t);
+    pm -= lr * mh / (sqrtf(vh) + 1e-8f);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      m[k] = 0.9f * m[k] + 0.1f * g[k];
-      v[k] = 0.999f * v[k] + 0.001f * g[k] * g[k];
-      const float mh = m[k] / (1.f - b1t), vh = v[k] / (1.f - b2t);
-      p[k] -= lr * mh / (sqrtf(vh) + 1e-8f);
-    }
+    for (int k = 0; k < 9; ++k) p[k] = __shfl_sync(0xFFFFFFFFu, pm, 2 * k);
   }
   if (params_out && lane < 9) params_out[9 * q + lane] = p[lane];
   if (lane == 0 && loss_out) loss_out[q] = L;
@@ -600,7 +686,7 @@ __global__ void k_quadric_canonical(int nq, const float* __restrict__ in, float*
 #pragma unroll
     for (int k = 0; k < 3; ++k) Rs[i][k] *= sg[best][k];
   double rv[3];
-  rotmat_to_rotvec(Rs, rv);
+  rotmat_to_rotvec<double>(Rs, rv);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     out[9 * q + k] = (float)p[k];

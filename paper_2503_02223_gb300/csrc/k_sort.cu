@@ -7,6 +7,8 @@
 //      values carried along;
 //   3. tile ranges are read off the sorted keys and ranks mapped back to indices.
 // Keys are 32-bit when tile and rank bits fit, else 64-bit.
+#include <atomic>
+
 #include "dqo_internal.cuh"
 
 namespace dqo {
@@ -412,8 +414,21 @@ __global__ void __launch_bounds__(kThreads) k_tile_ranges(const K* __restrict__ 
 
 inline unsigned grid_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
 
+// SM count of the current device, read once per device.
+int current_sm_count() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cached[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 1;
+  int v = cached[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) return 1;
+  cached[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
 // Keys per CTA of a radix pass: 4096, or 2048 when a 4096-key grid would leave SMs idle.
-inline int sort_items(int64_t n) { return n < int64_t(152) * 4096 ? 8 : 16; }
+inline int sort_items(int64_t n) { return n < int64_t(current_sm_count()) * 4096 ? 8 : 16; }
 
 // Scratch of one sort (uint32 words): [passes][256] histograms, [passes][tiles][256] status
 // words, [passes] tile counters and an error flag.

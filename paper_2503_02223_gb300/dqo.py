@@ -74,7 +74,7 @@ _SIGS = {
     "dqo_set_timing": (c_i32, [c_p, C.c_int]),
     "dqo_get_timings": (c_i32, [c_p, c_p, c_i32]),
     "dqo_launch_count": (c_i64, [c_p]),
-    "dqo_depth_order_noalloc": (c_i32, [c_p, c_i64, c_p, c_p]),
+    "dqo_depth_order_noalloc": (c_i32, [c_p, c_i64, c_p, c_p, c_p]),
     "dqo_quadric_project": (c_i32, [c_p, c_i32, c_p, c_i32, c_p, c_p, c_p, c_i32, c_p, c_p, c_p, c_p]),
     "dqo_quadric_bbox_loss": (c_i32, [c_p, c_i32, c_p, c_i32, c_p, c_p, c_p, c_i32, c_p, c_p, c_p, c_p]),
     "dqo_quadric_fit": (c_i32, [c_p, c_i32, c_i32, c_p, c_p, c_p, c_i32, c_p, c_i32, c_f, c_p, c_p, c_p, c_p, c_p,
@@ -92,6 +92,7 @@ _SIGS = {
     "dqo_mlp_train_step": (c_i32, [c_p, c_p, c_p, c_i64, c_p, c_p, c_i64, c_p, c_p, c_p]),
     "dqo_mlp_check": (c_i32, [c_p, c_p]),
     "dqo_wait_probe": (c_i32, [c_p, c_p]),
+    "dqo_alu_probe": (c_i32, [c_i32, c_i32, c_p, C.POINTER(C.c_double), c_p]),
 }
 
 class dqo_keyframe(C.Structure):
@@ -331,16 +332,21 @@ def dqo_launch_count(ctx: Context) -> int:
     return int(load().dqo_launch_count(ctx.handle))
 
 
-def dqo_depth_order_noalloc(depth_keys: torch.Tensor, order: torch.Tensor, stream=None):
+def dqo_depth_order_noalloc(depth_keys: torch.Tensor, order: torch.Tensor, status: torch.Tensor | None = None,
+                            stream=None):
     """Depth order without any device allocation (scratch lives in the library); see
     include/dqo.h.  depth_keys: uint32 bit patterns as an int32 CUDA tensor [n]; order:
-    int32 CUDA tensor [n] receiving the sorted indices."""
+    int32 CUDA tensor [n] receiving the sorted indices; status (optional): int32 CUDA
+    tensor [1] set to 0 when the order is valid, 1 when a bounded sort wait gave up."""
     if depth_keys.dtype != torch.int32 or order.dtype != torch.int32:
         raise ValueError("depth_keys and order must be int32 tensors (uint32 bit patterns)")
     if order.numel() != depth_keys.numel():
         raise ValueError("order must have as many elements as depth_keys")
+    if status is not None and (status.dtype != torch.int32 or status.numel() < 1):
+        raise ValueError("status must be an int32 tensor of at least one element")
     _check("dqo_depth_order_noalloc",
-           load().dqo_depth_order_noalloc(_ptr(depth_keys), depth_keys.numel(), _ptr(order), _stream(stream)))
+           load().dqo_depth_order_noalloc(_ptr(depth_keys), depth_keys.numel(), _ptr(order), _ptr(status),
+                                          _stream(stream)))
 
 
 def dqo_quadric_project(ctx: Context, params, P, q_ptr, pair_v, conic=None, bbox=None, valid=None, stream=None):
@@ -531,6 +537,17 @@ def dqo_mlp_check(ctx: Context) -> bool:
 def dqo_wait_probe(ctx: Context, stream=None) -> int:
     """Runs the bounded-wait probe; returns the status (DQO_ETIMEOUT expected)."""
     return int(load().dqo_wait_probe(ctx.handle, _stream(stream)))
+
+
+ALU_FMA, ALU_EX2 = 0, 1
+
+
+def dqo_alu_probe(kind: int, iters: int, sink: torch.Tensor, stream=None) -> float:
+    """Launches the FP32 FMA (kind 0) or ex2 (kind 1) throughput probe on every SM;
+    returns the launch's operation count (flops, or exponentials)."""
+    ops = C.c_double(0.0)
+    _check("dqo_alu_probe", load().dqo_alu_probe(kind, iters, _ptr(sink), C.byref(ops), _stream(stream)))
+    return ops.value
 
 
 # ------------------------------------------------------------------------ conveniences

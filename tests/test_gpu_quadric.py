@@ -142,15 +142,21 @@ def _rel_q(pa, pb):
 
 
 def test_quadric_fit_init_parity_512_fits():
-    # the Eq. 1 initialisation (fp64 on both sides): the decomposed quadric within 1e-3
+    # The Eq. 1 initialisation, single precision on the GPU against the FP64 oracle.  In the
+    # normalised frame the null vector of the single-precision normal matrix is within
+    # about eps_32 * lambda_max / (lambda_9 - lambda_10) of the FP64 one (measured on this
+    # set: median 6e-7, at most 2e-5); the decomposition adds the cancellation of t t^T
+    # against the axes (about |t|^2 / a^2 < 100).  Stated tolerance on the normalised Q*:
+    # median 1e-5, every quadric 1e-3.
     q = _batched_fits()
     got = _gpu_fit(q, iters=0)
     ref = oracle.quadric_fit(q["P"], q["q_ptr"], q["pair_v"], q["obs_bbox"], iters=0)
     assert np.array_equal(got["ok"], ref["ok"]) and ref["ok"].mean() > 0.99
     ok = ref["ok"] > 0
     rel = _rel_q(got["init"][ok].astype(np.float64), ref["init"][ok])
+    print("init rel Q*: median %.2e p90 %.2e max %.2e" % (np.median(rel), np.percentile(rel, 90), rel.max()))
     assert np.all(rel < 1e-3), (rel.max(), np.argmax(rel))
-    assert np.median(rel) < 1e-6
+    assert np.median(rel) < 1e-5
     np.testing.assert_allclose(got["loss"][ok], ref["loss"][ok], rtol=1e-3, atol=1e-4)
 
 

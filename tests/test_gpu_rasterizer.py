@@ -2,19 +2,22 @@
 
 Tolerances: rendered colour / depth / alpha / ins within 1e-4 absolute; tile lists and
 the depth order bit-exact given the GPU's own FP32 projections; the object-id map exact
-on pixels whose FP64 top-2 weight margin exceeds 1e-5; gradients within 1e-3 relative
-per Gaussian parameter vector (floor 1e-2 of the tensor's largest vector) and per tensor.  Pixels the
-oracle flags as within rounding distance of a discrete decision (alpha skip / clamp /
-stop thresholds, tile-membership edges) are left out of the image comparison and must be
-rare; for gradients the oracle instead bounds the change such a decision can cause and
-the per-element tolerance is widened by that bound.
+on pixels whose FP64 top-2 weight margin exceeds 1e-5 (pixels under that margin at most
+0.01% of the image); gradients within 1e-3 relative per element (floor 1e-3 of the
+tensor's largest |g|) and per tensor.  A pixel the oracle flags as within rounding
+distance of a discrete decision (alpha skip / clamp / stop thresholds, tile-membership
+edges) must match one of the outcomes the oracle gives with those decisions taken the
+other way; flagged pixels must be rare.  For gradients the oracle bounds the change such
+a decision (or FP32 rounding of the gradient sums) can cause, and only the Gaussians it
+flags have their per-element tolerance widened by that bound.
 """
 import numpy as np
 import pytest
 import torch
 
 import oracle
-from gpu_util import (TOL_IMG, Render, assert_grads_close, condition_targets, oracle_settings, tiny_case)
+from gpu_util import (ID_MARGIN, TOL_IMG, Render, assert_grads_close, check_flagged_pixels, condition_targets,
+                      oracle_settings, tiny_case)
 from paper_2503_02223_gb300 import dqo, synth
 
 pytestmark = pytest.mark.gpu
@@ -95,24 +98,37 @@ def _check_tile_lists(r, W, H, tile):
     assert np.array_equal(order, np.lexsort((np.arange(len(key)), key)))
 
 
-def _forward_parity(g, cam, t, nobj, st_kw=None, id_check=True, min_ok=0.97):
+def _near_ties(ref):
+    """Non-empty pixels whose FP64 top-2 object weight margin is within ID_MARGIN."""
+    return int(((ref["id_margin"] <= ID_MARGIN) & (ref["id_map"] != -1)).sum())
+
+
+def _forward_parity(g, cam, t, nobj, st_kw=None, id_check=True, max_flagged=0.01, max_ties=1e-4, report=None):
     st_kw = st_kw or {}
     r = Render(g, cam, nobj, t, **st_kw)
     out = r.forward()
     st_o = oracle_settings(nobj, **{k: v for k, v in st_kw.items() if k not in ("batch",)})
     ref = oracle.render(g, cam, st_o, t)
     ok = ref["amb"] == 0
-    assert ok.mean() > min_ok, ok.mean()
+    assert 1 - ok.mean() <= max_flagged, 1 - ok.mean()
     _img_compare(out, ref, ok)
-    Tf = r.buffer(dqo.DQO_BUF_T_FINAL, np.float32).reshape(cam["height"], cam["width"])
-    nc = r.buffer(dqo.DQO_BUF_N_CONTRIB, np.uint32).reshape(cam["height"], cam["width"])
+    H, W = cam["height"], cam["width"]
+    Tf = r.buffer(dqo.DQO_BUF_T_FINAL, np.float32).reshape(H, W)
+    last = r.last_blended()
     assert np.abs(Tf - ref["T_final"])[ok].max(initial=0) < TOL_IMG
-    assert np.array_equal(nc[ok], ref["n_contrib"][ok])
+    assert np.array_equal(last[ok], ref["last"][ok])
     if id_check:
         # an empty pixel (id -1) is certain; otherwise the top-2 weight margin must exceed 1e-5
-        sure = ok & ((ref["id_margin"] > 1e-5) | (ref["id_map"] == -1))
-        assert sure.mean() > min_ok
+        sure = ok & ((ref["id_margin"] > ID_MARGIN) | (ref["id_map"] == -1))
         assert np.array_equal(out["id_map"][sure], ref["id_map"][sure])
+        ties = _near_ties(ref)
+        assert ties <= max(max_ties * H * W, 2), (ties, H * W)
+        if report is not None:
+            report["near_ties"] = ties
+    else:
+        out = {k: v for k, v in out.items() if k != "id_map"}
+    # every flagged pixel is one of the outcomes of its uncertain decisions
+    check_flagged_pixels(g, cam, st_o, t, ref, out, Tf, last, report=report)
     if t is not None:
         np.testing.assert_allclose(out["loss"], ref["loss"], rtol=2e-5, atol=1e-6)
     return r, out, ref
@@ -256,16 +272,26 @@ def test_indoor_keyframe_full_size_parity():
     got = r.backward()
     ref = oracle.render(g, cam, st_o, t)
     ok = ref["amb"] == 0
-    assert ok.mean() > 0.9, ok.mean()
+    # flagged pixels (decisions within rounding distance of a threshold) are at most 1%
+    assert ok.mean() >= 0.99, ok.mean()
     _img_compare(out, ref, ok)
-    sure = ok & ((ref["id_margin"] > 1e-5) | (ref["id_map"] == -1))
+    H, W = cam["height"], cam["width"]
+    Tf = r.buffer(dqo.DQO_BUF_T_FINAL, np.float32).reshape(H, W)
+    last = r.last_blended()
+    assert np.abs(Tf - ref["T_final"])[ok].max(initial=0) < TOL_IMG
+    assert np.array_equal(last[ok], ref["last"][ok])
+    sure = ok & ((ref["id_margin"] > ID_MARGIN) | (ref["id_map"] == -1))
     assert np.array_equal(out["id_map"][sure], ref["id_map"][sure])
+    # id-map near ties are at most 0.01% of the pixels
+    assert _near_ties(ref) <= 1e-4 * H * W, _near_ties(ref)
+    # every flagged pixel matches one of the outcomes of its uncertain decisions
+    rep_px = {}
+    check_flagged_pixels(g, cam, st_o, t, ref, out, Tf, last, report=rep_px)
     np.testing.assert_allclose(out["loss"], ref["loss"], rtol=2e-5, atol=1e-6)
     refb = oracle.render_backward(g, cam, st_o, t)
     report = {}
     assert_grads_close(got, refb, report=report)
-    # the uncertainty allowance widens the tolerance of few elements
-    assert all(v["widened"] < 0.05 for v in report.values()), report
+    print("flagged pixels", rep_px, "near ties", _near_ties(ref), "gradients", report)
     r.close()
 
 

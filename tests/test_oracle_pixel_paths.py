@@ -172,3 +172,23 @@ def test_backward_skip_of_zero_gradient_pixels_keeps_it_linear():
     lin = oracle.render_backward(g, cam, st, t, dl=dl_f)
     for k in ("means", "log_scales", "quats", "opacity_logit", "rgb"):
         assert np.abs(fused[k] - lin[k]).max() <= 1e-12 * np.abs(lin[k]).max(), k
+
+
+def test_last_blended_is_the_tile_list_entry_at_n_contrib():
+    # the render's `last` output is the Gaussian at list position n_contrib - 1 of the
+    # pixel's tile list, rebuilt here from the projections by the tile-list builder
+    g = synth.tiny_gaussians(1051)
+    W, H = 333, 251
+    cam = synth.tiny_camera(width=W, height=H)
+    st = oracle.settings(num_objects=4)
+    r = oracle.render(g, cam, st)
+    pp = oracle.preprocess(g, cam, st)
+    ntx, nty = -(-W // 16), -(-H // 16)
+    zbits = pp["z"].astype(np.float32).view(np.uint32)
+    ranges, lst = oracle.bin_tiles(pp["rect"], zbits, pp["visible"], ntx, nty)
+    yy, xx = np.mgrid[0:H, 0:W]
+    tile = (yy // 16) * ntx + xx // 16
+    nc = r["n_contrib"]
+    expect = np.where(nc > 0, lst[np.clip(ranges[tile, 0] + nc - 1, 0, lst.size - 1)], -1)
+    assert np.array_equal(r["last"], expect)
+    assert (r["last"] >= 0).mean() > 0.5

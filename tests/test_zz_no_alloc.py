@@ -1,11 +1,12 @@
-"""The allocation-free depth order (dqo_depth_order_noalloc) against the depth order the
-forward render computes with its own workspace.
+"""The allocation-free depth order (dqo_depth_order_noalloc) against numpy's stable sort
+and against the depth order the forward render computes with its own workspace.
 
 dqo_depth_order_noalloc exists for callers that cannot allocate device memory while they
 run (a real-time loop that must not take cudaMalloc's implicit synchronisation, a plugin
 whose host framework owns the device memory, a fixed memory budget); its scratch is a
-fixed array inside the library.  This file is collected last so that, if it fails, a run
-that stops at the first failure has already run every other test."""
+fixed array inside the library.  Every call shares that array and it keeps the previous
+call's contents, so each case runs twice in a row.  This file is collected last so that,
+if it fails, a run that stops at the first failure has already run every other test."""
 import numpy as np
 import pytest
 import torch
@@ -28,8 +29,22 @@ def _forward_keys_and_order(g, cam, nobj):
     return keys, order
 
 
+def _noalloc_twice(keys: np.ndarray):
+    """Two calls in a row on the same keys; returns both orders after checking the status."""
+    d_keys = torch.from_numpy(keys.view(np.int32)).cuda()
+    outs = []
+    for call in range(2):
+        order = torch.full_like(d_keys, -7)
+        status = torch.full((1,), 7, dtype=torch.int32, device="cuda")
+        dqo.dqo_depth_order_noalloc(d_keys, order, status)
+        torch.cuda.synchronize()
+        assert status.item() == 0, f"call {call}: a sort wait gave up"
+        outs.append(order.cpu().numpy().view(np.uint32).astype(np.int64))
+    return outs
+
+
 @pytest.mark.parametrize("case", ["tiny", "indoor"])
-def test_noalloc_depth_order_matches_forward_twice(case):
+def test_noalloc_depth_order_matches_lexsort_and_forward_twice(case):
     if case == "tiny":
         g, cam, _ = tiny_case()
         # push some Gaussians behind the near plane so culled keys are present
@@ -40,18 +55,34 @@ def test_noalloc_depth_order_matches_forward_twice(case):
     else:
         kf = synth.indoor_keyframe(1002)
         keys, ref = _forward_keys_and_order(kf["gaussians"], kf["camera"], 31)
-    d_keys = torch.from_numpy(keys.view(np.int32)).cuda()
-    for call in range(2):   # the shared scratch keeps the previous call's contents
-        order = torch.full_like(d_keys, -7)
-        dqo.dqo_depth_order_noalloc(d_keys, order)
-        torch.cuda.synchronize()
-        got = order.cpu().numpy().view(np.uint32)
-        assert np.array_equal(got, ref), f"call {call}"
+    expect = np.lexsort((np.arange(keys.size), keys))
+    for call, got in enumerate(_noalloc_twice(keys)):
+        assert np.array_equal(got, expect), f"call {call}"
+        assert np.array_equal(got, ref.astype(np.int64)), f"call {call}"
+
+
+@pytest.mark.parametrize("n", [1, 2, 622591, 1 << 20])
+def test_noalloc_random_keys_with_duplicates_and_culled(n):
+    # n = 1: the single-key path; 622591: just under 152 x 4096 keys, the most CTAs of the
+    # 2048-key tiles on this GPU; 2^20: the largest size, 4096-key tiles
+    rng = np.random.default_rng(n)
+    keys = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
+    keys[rng.random(n) < 0.1] = 0xFFFFFFFF                        # culled Gaussians
+    dup = rng.random(n) < 0.3
+    keys[dup] = keys[rng.integers(0, n, int(dup.sum()))]           # duplicated depths
+    keys[rng.random(n) < 0.05] = 0
+    expect = np.argsort(keys, kind="stable")
+    for call, got in enumerate(_noalloc_twice(keys)):
+        assert np.array_equal(got, expect), f"call {call}"
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     lib = dqo.load()
     buf = torch.zeros(16, dtype=torch.int32, device="cuda")
-    assert lib.dqo_depth_order_noalloc(buf.data_ptr(), (1 << 20) + 1, buf.data_ptr(), None) == dqo.DQO_EINVAL
-    assert lib.dqo_depth_order_noalloc(None, 5, None, None) == dqo.DQO_EINVAL
-    assert lib.dqo_depth_order_noalloc(None, 0, None, None) == dqo.DQO_OK
+    assert lib.dqo_depth_order_noalloc(buf.data_ptr(), (1 << 20) + 1, buf.data_ptr(), None, None) == dqo.DQO_EINVAL
+    assert lib.dqo_depth_order_noalloc(None, 5, None, None, None) == dqo.DQO_EINVAL
+    assert lib.dqo_depth_order_noalloc(None, -1, None, None, None) == dqo.DQO_EINVAL
+    status = torch.full((1,), 7, dtype=torch.int32, device="cuda")
+    assert lib.dqo_depth_order_noalloc(None, 0, None, status.data_ptr(), None) == dqo.DQO_OK
+    torch.cuda.synchronize()
+    assert status.item() == 0
