@@ -406,7 +406,8 @@ def run_ours(args, rank, world, local_rank):
     W, H = cam["width"], cam["height"]
     tw, th = (int(x) for x in args.tile.split("x"))
     ctx = dqo.Context(local_rank)
-    st = dqo.settings(tile_w=tw, tile_h=th, batch=args.batch)
+    # gradients overwritten by the adjoint (no separate clearing of the buffers per step)
+    st = dqo.settings(tile_w=tw, tile_h=th, batch=args.batch, grads_zero=1)
     g = dqo.to_device(kf["gaussians"], dev)
     t = dqo.to_device(targets, dev)
     q = dqo.to_device({k: kf["quadrics"][k] for k in ("params", "P", "q_ptr", "pair_v", "obs_bbox")}, dev)
@@ -421,8 +422,6 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
 
     def step():
-        for v in grads.values():
-            v.zero_()
         dqo.dqo_render_forward(ctx, st, gs, cs, ts, outs, stream)
         dqo.dqo_render_backward(ctx, st, gs, cs, ts, None, gg, stream)
         dqo.dqo_quadric_bbox_loss(ctx, q["params"], q["P"], q["q_ptr"], q["pair_v"], q["obs_bbox"], qloss, qgrad,
@@ -446,7 +445,7 @@ def run_ours(args, rank, world, local_rank):
     bctx = dqo.Context(local_rank)
     kfb = dqo.keyframe(g, NUM_OBJECTS, cam, t, out, grads)
 
-    bst = dqo.settings(tile_w=tw, tile_h=th, batch=args.batch)
+    bst = dqo.settings(tile_w=tw, tile_h=th, batch=args.batch, grads_zero=1)
     if args.no_tune:
         cps, sched, tune_ms = 0, dqo.SCHEDULE_PER_KEYFRAME, []
     else:
@@ -461,8 +460,6 @@ def run_ours(args, rank, world, local_rank):
         with torch.cuda.stream(qside):
             dqo.dqo_quadric_bbox_loss(bctx, q["params"], q["P"], q["q_ptr"], q["pair_v"], q["obs_bbox"], qloss,
                                       qgrad)
-        for v in grads.values():
-            v.zero_()
         dqo.dqo_batch_step(bctx, bst, [kfb], None, cps, sched)
         main.wait_stream(qside)
 
@@ -590,8 +587,6 @@ def run_ours(args, rank, world, local_rank):
         with torch.cuda.stream(qside):
             dqo.dqo_quadric_bbox_loss(bctx, q2["params"], q2["P"], q2["q_ptr"], q2["pair_v"], q2["obs_bbox"],
                                       qloss2, qgrad2)
-        for v in grads2.values():
-            v.zero_()
         dqo.dqo_batch_step(bctx, bst, [kfb2], None, cps, sched)
         main.wait_stream(qside)
 

@@ -74,6 +74,9 @@ typedef struct {
   float theta_alpha;      /* Eq. 11 instance threshold of Mask_geo (not given in the paper)    (0.5)   */
   float theta_d;          /* Eq. 11 depth threshold of Mask_geo (m)                            (0.1)   */
   float theta_c;          /* Eq. 11 colour threshold of Mask_rgb                               (0.1)   */
+  int32_t grads_zero;     /* 0: Gaussian gradients are added (+=) to the caller's buffers; 1: the
+                             call overwrites them with its own gradients (zero for culled Gaussians),
+                             so the caller need not clear them first                      (0)     */
 } dqo_settings;
 
 typedef struct {
@@ -126,7 +129,8 @@ typedef struct {
   const float* ins;    /* [H,W] */
 } dqo_pixel_grads;
 
-/* Parameter gradients, ACCUMULATED (+=) into caller buffers (each may be NULL). */
+/* Parameter gradients, ACCUMULATED (+=) into caller buffers, or overwritten when
+ * dqo_settings.grads_zero is 1 (each may be NULL). */
 typedef struct {
   float* means;          /* [n,3] */
   float* log_scales;     /* [n,3] */
@@ -343,7 +347,11 @@ DQO_API dqo_status dqo_quadric_canonical(int32_t nq, const float* params, float*
 /* One keyframe of a batch: its scene, camera, targets (required: the step optimises the
  * fused losses), outputs (as dqo_render_forward; NULL members are skipped) and the
  * gradient buffers its step ADDS to (several keyframes may share a scene and its
- * gradient buffers: additions are atomic). */
+ * gradient buffers: additions are atomic).  With dqo_settings.grads_zero = 1 the step
+ * overwrites each keyframe's gradient buffers instead: buffers no other keyframe of the
+ * batch uses are written once by the adjoint, shared ones (the same array pointer) are
+ * cleared at the start of the step and then added to; buffers that overlap without being
+ * the same array are not supported in that mode. */
 typedef struct dqo_keyframe {
   dqo_gaussians gaussians;
   dqo_camera camera;

@@ -441,17 +441,36 @@ void pixel_backward(const OSettings& st, const Inputs& in, const std::vector<Pro
     }
 }
 
-// Chain a Gaussian's 2D gradient record back to its parameters.
+// Magnitude arithmetic: every value is replaced by its absolute value and every sum or
+// difference by the sum of the absolute values, so that a chain of operations evaluated
+// on Mag gives the sum of the magnitudes of all the terms it combines (the quantity a
+// first-order bound on its floating-point rounding is proportional to).
+struct Mag {
+    double v = 0;
+    Mag() = default;
+    Mag(double x) : v(std::fabs(x)) {}
+    Mag& operator+=(const Mag& o) { v += o.v; return *this; }
+    Mag& operator-=(const Mag& o) { v += o.v; return *this; }
+};
+Mag operator+(const Mag& a, const Mag& b) { return Mag(a.v + b.v); }
+Mag operator-(const Mag& a, const Mag& b) { return Mag(a.v + b.v); }
+Mag operator-(const Mag& a) { return a; }
+Mag operator*(const Mag& a, double b) { return Mag(a.v * std::fabs(b)); }
+Mag operator*(double a, const Mag& b) { return Mag(std::fabs(a) * b.v); }
+Mag operator/(const Mag& a, double b) { return Mag(a.v / std::fabs(b)); }
+
+// Chain a Gaussian's 2D gradient record back to its parameters (T = double; T = Mag
+// evaluates the same chain on magnitudes).
+template <class T>
 void preprocess_backward(const OSettings& st, const OCamera& cam, const Proj& P, double opacity_logit,
-                         const double* g2, double* dmean, double* dlog_scale, double* dquat,
-                         double* dlogit, double* drgb) {
+                         const T* g2, T* dmean, T* dlog_scale, T* dquat, T* dlogit, T* drgb) {
     (void)st;
     for (int c = 0; c < 3; ++c) drgb[c] += g2[6 + c];
     *dlogit += g2[5] * P.opac * (1 - P.opac);
     (void)opacity_logit;
     const double x = P.pc[0], y = P.pc[1], z = P.pc[2];
     const double* V = cam.viewmat;
-    double dpc[3] = {0, 0, 0};
+    T dpc[3] = {0, 0, 0};
     // 2D mean
     dpc[0] += g2[0] * cam.fx / z;
     dpc[1] += g2[1] * cam.fy / z;
@@ -460,36 +479,36 @@ void preprocess_backward(const OSettings& st, const OCamera& cam, const Proj& P,
     dpc[2] += g2[9];
     // conic = inverse(Sigma'): dL/dSigma' = -M^-1 Gm M^-1 with Gm the matrix gradient of the conic
     const double M[2][2] = {{P.conic[0], P.conic[1]}, {P.conic[1], P.conic[2]}};
-    const double Gm[2][2] = {{g2[2], 0.5 * g2[3]}, {0.5 * g2[3], g2[4]}};
-    double GS[2][2];
+    const T Gm[2][2] = {{g2[2], 0.5 * g2[3]}, {0.5 * g2[3], g2[4]}};
+    T GS[2][2];
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) {
-            double acc = 0;
+            T acc = 0;
             for (int k = 0; k < 2; ++k)
                 for (int l = 0; l < 2; ++l) acc += M[i][k] * Gm[k][l] * M[l][j];
             GS[i][j] = -acc;
         }
     // Sigma' = T2 S3 T2^T + lowpass I;  dL/dS3 = T2^T GS T2;  dL/dT2 = 2 GS T2 S3
-    double dS3[3][3], dT2[2][3];
+    T dS3[3][3], dT2[2][3];
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
-            double acc = 0;
+            T acc = 0;
             for (int k = 0; k < 2; ++k)
                 for (int l = 0; l < 2; ++l) acc += P.T2[k][i] * GS[k][l] * P.T2[l][j];
             dS3[i][j] = acc;
         }
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 3; ++j) {
-            double acc = 0;
+            T acc = 0;
             for (int k = 0; k < 2; ++k)
                 for (int l = 0; l < 3; ++l) acc += GS[i][k] * P.T2[k][l] * P.S3[l][j];
             dT2[i][j] = 2 * acc;
         }
     // T2 = J W  ->  dL/dJ = dT2 W^T
-    double dJ[2][3];
+    T dJ[2][3];
     for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 3; ++j) {
-            double acc = 0;
+            T acc = 0;
             for (int k = 0; k < 3; ++k) acc += dT2[i][k] * V[4 * j + k];
             dJ[i][j] = acc;
         }
@@ -504,16 +523,16 @@ void preprocess_backward(const OSettings& st, const OCamera& cam, const Proj& P,
     double Mm[3][3];
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) Mm[i][j] = P.Rq[i][j] * P.s[j];
-    double dM[3][3];
+    T dM[3][3];
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
-            double acc = 0;
+            T acc = 0;
             for (int k = 0; k < 3; ++k) acc += (dS3[i][k] + dS3[k][i]) * Mm[k][j];
             dM[i][j] = acc;
         }
-    double dR[3][3];
+    T dR[3][3];
     for (int j = 0; j < 3; ++j) {
-        double ds = 0;
+        T ds = 0;
         for (int i = 0; i < 3; ++i) {
             ds += dM[i][j] * P.Rq[i][j];
             dR[i][j] = dM[i][j] * P.s[j];
@@ -522,7 +541,7 @@ void preprocess_backward(const OSettings& st, const OCamera& cam, const Proj& P,
     }
     // R(q) for the normalised quaternion (w,x,y,z)
     const double w = P.qn[0], qx = P.qn[1], qy = P.qn[2], qz = P.qn[3];
-    double dqn[4];
+    T dqn[4];
     dqn[0] = 2 * (-qz * dR[0][1] + qy * dR[0][2] + qz * dR[1][0] - qx * dR[1][2] - qy * dR[2][0] + qx * dR[2][1]);
     dqn[1] = 2 * (qy * dR[0][1] + qz * dR[0][2] + qy * dR[1][0] - 2 * qx * dR[1][1] - w * dR[1][2] +
                   qz * dR[2][0] + w * dR[2][1] - 2 * qx * dR[2][2]);
@@ -531,7 +550,7 @@ void preprocess_backward(const OSettings& st, const OCamera& cam, const Proj& P,
     dqn[3] = 2 * (-2 * qz * dR[0][0] - w * dR[0][1] + qx * dR[0][2] + w * dR[1][0] - 2 * qz * dR[1][1] +
                   qy * dR[1][2] + qx * dR[2][0] + qy * dR[2][1]);
     // normalisation q / |q|
-    double dot = 0;
+    T dot = 0;
     for (int k = 0; k < 4; ++k) dot += dqn[k] * P.qn[k];
     for (int k = 0; k < 4; ++k) dquat[k] += (dqn[k] - P.qn[k] * dot) / P.qnorm;
 }
@@ -815,7 +834,8 @@ int oracle_render_alternatives(const OSettings* st, const OCamera* cam, int64_t 
 // unc[n*14]: per parameter (means, log_scales, quats, logit, rgb) the summed absolute change
 // of the gradient when each near-threshold decision or uncertain membership is taken the
 // other way, pixel by pixel, plus a bound on single-precision rounding of the gradient's
-// sum -- the amount by which a correct single-precision evaluation may differ from this one.
+// sum and of the projection adjoint's chain -- the amount by which a correct
+// single-precision evaluation may differ from this one.
 int oracle_render_backward(const OSettings* st, const OCamera* cam, int64_t n, const double* means,
                            const double* log_scales, const double* quats, const double* opacity_logit,
                            const double* rgb, const int32_t* obj_id, const uint8_t* flags,
@@ -979,6 +999,25 @@ int oracle_render_backward(const OSettings* st, const OCamera* cam, int64_t n, c
             uu[10] += std::fabs(dlg) * bound2d[k];
             for (int j = 0; j < 3; ++j) uu[11 + j] += std::fabs(dc[j]) * bound2d[k];
         }
+    }
+    // Single-precision evaluation of the projection adjoint itself: to first order its
+    // rounding error is at most a few tens of unit roundoffs (the chain is ~40 operations
+    // deep, its coefficients -- conic, Jacobian, rotation, scales -- are themselves rounded)
+    // times the magnitude sum of every term it combines, the same chain evaluated on
+    // magnitudes; 64u of that.  It matters only where the chain cancels, e.g. a Gaussian
+    // just beyond the near plane whose footprint covers the image.
+    for (int64_t i = 0; unc && i < n; ++i) {
+        if (!pr[i].visible) continue;
+        Mag m2[G2], mm[3], ms[3], mq[4], ml, mc[3];
+        for (int k = 0; k < G2; ++k) m2[k] = Mag(g2[G2 * i + k]);
+        preprocess_backward<Mag>(*st, *cam, pr[i], opacity_logit[i], m2, mm, ms, mq, &ml, mc);
+        const double cu = 64 * u;
+        double* uu = unc + 14 * i;
+        for (int j = 0; j < 3; ++j) uu[j] += cu * mm[j].v;
+        for (int j = 0; j < 3; ++j) uu[3 + j] += cu * ms[j].v;
+        for (int j = 0; j < 4; ++j) uu[6 + j] += cu * mq[j].v;
+        uu[10] += cu * ml.v;
+        for (int j = 0; j < 3; ++j) uu[11 + j] += cu * mc[j].v;
     }
     for (int64_t i = 0; i < n; ++i) {
         const double* r = g2.data() + G2 * i;

@@ -124,6 +124,7 @@ dqo_status check_settings(const dqo_settings* s) {
   if (!(s->tile_w == 8 || s->tile_w == 16 || s->tile_w == 32) || s->tile_w * s->tile_h != kThreads)
     return DQO_EINVAL;
   if (s->batch < 32 || s->batch > 256 || (s->batch & 31)) return DQO_EINVAL;
+  if (s->grads_zero != 0 && s->grads_zero != 1) return DQO_EINVAL;
   if (!(s->alpha_clamp > 0.f) || !(s->alpha_min >= 0.f) || !(s->t_stop >= 0.f) || !(s->znear > 0.f) ||
       !(s->lowpass >= 0.f) || !(s->radius_sigma > 0.f) || !(s->lambda_ins >= 0.f))
     return DQO_EINVAL;
@@ -225,6 +226,7 @@ void dqo_settings_default(dqo_settings* s) {
   s->theta_alpha = 0.5f;
   s->theta_d = 0.1f;
   s->theta_c = 0.1f;
+  s->grads_zero = 0;
 }
 
 int dqo_version(void) { return 100; }
@@ -547,6 +549,7 @@ dqo_status dqo_render_backward(dqo_ctx* c, const dqo_settings* s, const dqo_gaus
   b.d_quats = grads->quats;
   b.d_logit = grads->opacity_logit;
   b.d_rgb = grads->rgb;
+  b.mode = s->grads_zero ? kGradStore : kGradAdd;
   {
     PhaseTimer pt(c, DQO_PHASE_PROJECT_BWD, s_);
     DQO_CUDA(c, launch_preprocess_backward(b, s_));
@@ -699,6 +702,16 @@ dqo_status check_fits(const dqo_fit_batch* f) {
 
 }  // namespace
 
+// Two keyframes' gradient buffers are shared if any of their five arrays coincide.
+bool grads_share(const dqo_gaussian_grads& a, const dqo_gaussian_grads& b) {
+  const float* pa[5] = {a.means, a.log_scales, a.quats, a.opacity_logit, a.rgb};
+  const float* pb[5] = {b.means, b.log_scales, b.quats, b.opacity_logit, b.rgb};
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j)
+      if (pa[i] && pa[i] == pb[j]) return true;
+  return false;
+}
+
 dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const dqo_keyframe* kfs,
                           const dqo_fit_batch* fits, int32_t ctas_per_sm, int32_t schedule, dqo_stream stream_) {
   if (!c || !kfs || nkf < 1 || nkf > kMaxBatch || schedule < 0 || schedule > 2) return DQO_EINVAL;
@@ -786,6 +799,26 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
 
   DQO_CUDA(c, cudaMemsetAsync(B.counters.p, 0, 64, s_));
   DQO_CUDA(c, cudaMemsetAsync(B.ranges.p, 0, 8 * T, s_));
+  if (s->grads_zero) {
+    // gradient buffers shared by several keyframes take atomic additions: clear them first
+    // (once per buffer set); unshared ones are overwritten by the adjoint
+    for (int k = 0; k < nkf; ++k) {
+      bool shared = false, first = true;
+      for (int j = 0; j < nkf; ++j) {
+        if (j == k || !grads_share(kfs[j].grads, kfs[k].grads)) continue;
+        shared = true;
+        if (j < k) first = false;
+      }
+      if (!shared || !first) continue;
+      const dqo_gaussian_grads& gr = kfs[k].grads;
+      const size_t n = (size_t)kfs[k].gaussians.n;
+      if (gr.means) DQO_CUDA(c, cudaMemsetAsync(gr.means, 0, 12 * n, s_));
+      if (gr.log_scales) DQO_CUDA(c, cudaMemsetAsync(gr.log_scales, 0, 12 * n, s_));
+      if (gr.quats) DQO_CUDA(c, cudaMemsetAsync(gr.quats, 0, 16 * n, s_));
+      if (gr.opacity_logit) DQO_CUDA(c, cudaMemsetAsync(gr.opacity_logit, 0, 4 * n, s_));
+      if (gr.rgb) DQO_CUDA(c, cudaMemsetAsync(gr.rgb, 0, 12 * n, s_));
+    }
+  }
 
   // ---- quadric fits on the side stream, concurrent with the keyframes
   const bool run_fits = fits && fits->nq > 0;
@@ -957,6 +990,13 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
       pa.d_quats = kf.grads.quats;
       pa.d_logit = kf.grads.opacity_logit;
       pa.d_rgb = kf.grads.rgb;
+      // gradients are added atomically (keyframes may share buffers); with grads_zero a
+      // keyframe whose buffers no other keyframe uses overwrites them, shared ones were
+      // cleared at the start
+      bool shared = false;
+      for (int j = 0; j < nkf; ++j)
+        if (j != k && grads_share(kfs[j].grads, kf.grads)) shared = true;
+      pa.mode = s->grads_zero && !shared ? kGradStore : kGradAtomic;
     }
     tt.tile_off[nkf] = toff[nkf];
     tt.nkf = nkf;

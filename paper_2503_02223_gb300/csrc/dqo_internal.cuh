@@ -180,7 +180,11 @@ struct PreBwdArgs {
   float* d_quats;
   float* d_logit;
   float* d_rgb;
+  int32_t mode;        // kGradAdd, kGradAtomic or kGradStore
 };
+constexpr int32_t kGradAdd = 0;     // gradients += (one keyframe)
+constexpr int32_t kGradAtomic = 1;  // gradients added atomically (buffers shared by keyframes)
+constexpr int32_t kGradStore = 2;   // gradients overwritten, zero for Gaussians never binned
 
 // ---------------------------------------------------------------- launchers (return cudaGetLastError)
 

@@ -213,18 +213,31 @@ __global__ void __launch_bounds__(kThreads) k_preprocess_batch(const __grid_cons
   preprocess_item(kf.rp, kf.g, o, (int64_t)blockIdx.x * kThreads + threadIdx.x, kf.base, stage);
 }
 
-template <bool kAtomic>
-__device__ __forceinline__ void add_grad(float* p, float v) {
-  if (kAtomic) atomicAdd(p, v);
+// Writes one gradient element in the call's mode: +=, atomic +=, or =.
+__device__ __forceinline__ void put_grad(int mode, float* p, float v) {
+  if (mode == kGradAtomic) atomicAdd(p, v);
+  else if (mode == kGradStore) *p = v;
   else *p += v;
 }
 
-// Adjoint of Gaussian i (gradients added to a's parameter gradients; atomically when
-// several keyframes of a batch may share them).
-template <bool kAtomic>
+// Zero gradient of a Gaussian that was never binned (written only when overwriting).
+__device__ __forceinline__ void zero_grads(const PreBwdArgs& a, int64_t i) {
+  if (a.mode != kGradStore) return;
+  if (a.d_rgb) a.d_rgb[3 * i] = a.d_rgb[3 * i + 1] = a.d_rgb[3 * i + 2] = 0.f;
+  if (a.d_logit) a.d_logit[i] = 0.f;
+  if (a.d_means) a.d_means[3 * i] = a.d_means[3 * i + 1] = a.d_means[3 * i + 2] = 0.f;
+  if (a.d_log_scales) a.d_log_scales[3 * i] = a.d_log_scales[3 * i + 1] = a.d_log_scales[3 * i + 2] = 0.f;
+  if (a.d_quats) a.d_quats[4 * i] = a.d_quats[4 * i + 1] = a.d_quats[4 * i + 2] = a.d_quats[4 * i + 3] = 0.f;
+}
+
+// Adjoint of Gaussian i, written to a's parameter gradients in mode a.mode (atomically
+// when several keyframes of a batch share them).
 __device__ __forceinline__ void preprocess_backward_item(const PreBwdArgs& a, int64_t i) {
   if (i >= a.n) return;
-  if (a.ntiles[i] == 0) return;  // culled: never blended, zero gradient
+  if (a.ntiles[i] == 0) {  // culled: never blended, zero gradient
+    zero_grads(a, i);
+    return;
+  }
   const RasterParams& rp = a.rp;
   const float mean[3] = {a.means[3 * i], a.means[3 * i + 1], a.means[3 * i + 2]};
   const float ls[3] = {a.log_scales[3 * i], a.log_scales[3 * i + 1], a.log_scales[3 * i + 2]};
@@ -232,7 +245,11 @@ __device__ __forceinline__ void preprocess_backward_item(const PreBwdArgs& a, in
   const float logit = a.opacity_logit[i];
   Footprint f;
   footprint(rp, mean, ls, q, logit, f);
-  if (!f.visible) return;
+  if (!f.visible) {
+    zero_grads(a, i);
+    return;
+  }
+  const int mode = a.mode;
   const float4 r0 = reinterpret_cast<const float4*>(a.grad2d)[3 * i + 0];  // m_x m_y m_xx m_xy
   const float4 r1 = reinterpret_cast<const float4*>(a.grad2d)[3 * i + 1];  // m_yy d_opac d_r d_g
   const float4 r2 = reinterpret_cast<const float4*>(a.grad2d)[3 * i + 2];  // d_b d_z - -
@@ -242,11 +259,11 @@ __device__ __forceinline__ void preprocess_backward_item(const PreBwdArgs& a, in
   const float gy = cb * r0.x + cc * r0.y;
   const float ga = -0.5f * r0.z, gb = -r0.w, gc = -0.5f * r1.x;
   if (a.d_rgb) {
-    add_grad<kAtomic>(a.d_rgb + 3 * i + 0, r1.z);
-    add_grad<kAtomic>(a.d_rgb + 3 * i + 1, r1.w);
-    add_grad<kAtomic>(a.d_rgb + 3 * i + 2, r2.x);
+    put_grad(mode, a.d_rgb + 3 * i + 0, r1.z);
+    put_grad(mode, a.d_rgb + 3 * i + 1, r1.w);
+    put_grad(mode, a.d_rgb + 3 * i + 2, r2.x);
   }
-  if (a.d_logit) add_grad<kAtomic>(a.d_logit + i, r1.y * f.opac * (1.f - f.opac));
+  if (a.d_logit) put_grad(mode, a.d_logit + i, r1.y * f.opac * (1.f - f.opac));
   // dL/dSigma' = -Cn Gm Cn, Cn = [[a, b], [b, c]], Gm = [[ga, gb/2], [gb/2, gc]]
   const float m00 = ca * ga + cb * 0.5f * gb, m01 = ca * 0.5f * gb + cb * gc;
   const float m10 = cb * ga + cc * 0.5f * gb, m11 = cb * 0.5f * gb + cc * gc;
@@ -292,11 +309,11 @@ __device__ __forceinline__ void preprocess_backward_item(const PreBwdArgs& a, in
                dJ02 * (2.f * rp.fx * x * iz3) + dJ11 * (-rp.fy * iz2) + dJ12 * (2.f * rp.fy * y * iz3);
   if (a.d_means) {
 #pragma unroll
-    for (int j = 0; j < 3; ++j) add_grad<kAtomic>(a.d_means + 3 * i + j, W[j] * dpc0 + W[4 + j] * dpc1 + W[8 + j] * dpc2);
+    for (int j = 0; j < 3; ++j) put_grad(mode, a.d_means + 3 * i + j, W[j] * dpc0 + W[4 + j] * dpc1 + W[8 + j] * dpc2);
   }
   if (a.d_log_scales) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) add_grad<kAtomic>(a.d_log_scales + 3 * i + k, ds[k] * f.s[k]);
+    for (int k = 0; k < 3; ++k) put_grad(mode, a.d_log_scales + 3 * i + k, ds[k] * f.s[k]);
   }
   if (a.d_quats) {
     const float w = f.qn[0], qx = f.qn[1], qy = f.qn[2], qz = f.qn[3];
@@ -310,20 +327,20 @@ __device__ __forceinline__ void preprocess_backward_item(const PreBwdArgs& a, in
                    qy * dR[1][2] + qx * dR[2][0] + qy * dR[2][1]);
     const float dot = dq[0] * w + dq[1] * qx + dq[2] * qy + dq[3] * qz;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) add_grad<kAtomic>(a.d_quats + 4 * i + k, (dq[k] - f.qn[k] * dot) * f.qinv);
+    for (int k = 0; k < 4; ++k) put_grad(mode, a.d_quats + 4 * i + k, (dq[k] - f.qn[k] * dot) * f.qinv);
   }
 }
 
 __global__ void __launch_bounds__(kThreads) k_preprocess_backward(PreBwdArgs a) {
-  preprocess_backward_item<false>(a, (int64_t)blockIdx.x * kThreads + threadIdx.x);
+  preprocess_backward_item(a, (int64_t)blockIdx.x * kThreads + threadIdx.x);
 }
 
 // Keyframe blockIdx.y of a batch (its ntiles and grad2d pointers already offset to its
-// first Gaussian); gradients added atomically.
+// first Gaussian); each keyframe in its own mode (atomic where keyframes share buffers).
 __global__ void __launch_bounds__(kThreads) k_preprocess_backward_batch(const __grid_constant__ PreBwdTable t) {
   pdl_wait();
   pdl_trigger();
-  preprocess_backward_item<true>(t.kf[blockIdx.y], (int64_t)blockIdx.x * kThreads + threadIdx.x);
+  preprocess_backward_item(t.kf[blockIdx.y], (int64_t)blockIdx.x * kThreads + threadIdx.x);
 }
 
 }  // namespace

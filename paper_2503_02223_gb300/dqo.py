@@ -29,7 +29,8 @@ PHASES = ("project", "depth_sort", "binning", "blend_fwd", "blend_bwd", "project
 class dqo_settings(C.Structure):
     _fields_ = [("tile_w", c_i32), ("tile_h", c_i32), ("alpha_clamp", c_f), ("alpha_min", c_f), ("t_stop", c_f),
                 ("znear", c_f), ("lowpass", c_f), ("radius_sigma", c_f), ("lambda_ins", c_f), ("bg", c_f * 3),
-                ("og_filter", c_i32), ("batch", c_i32), ("theta_alpha", c_f), ("theta_d", c_f), ("theta_c", c_f)]
+                ("og_filter", c_i32), ("batch", c_i32), ("theta_alpha", c_f), ("theta_d", c_f), ("theta_c", c_f),
+                ("grads_zero", c_i32)]
 
 
 class dqo_camera(C.Structure):

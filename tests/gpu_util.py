@@ -112,17 +112,18 @@ def condition_targets(g, cam, t, st_o):
 
 def assert_grads_close(got: dict, ref: dict, keys=("means", "log_scales", "quats", "opacity_logit", "rgb"),
                        rel=TOL_GRAD_REL, floor=TOL_GRAD_FLOOR, report=None, sel=None, max_over=1e-3):
-    """Per element: |g - g_ref| <= rel * max(|g_ref|, floor * max |g_ref| over the tensor), and
-    per tensor ||g - g_ref|| <= rel ||g_ref||.  At most a fraction `max_over` of the compared
-    Gaussians may exceed that per-element tolerance, and each of them must be one the
-    oracle flags -- one of its decisions (alpha skip / clamp / stop, tile membership) lies
-    within rounding distance of its threshold at a pixel with a gradient (ref["amb"] bits 0,
-    2), or the oracle's bound on single-precision rounding of its gradient sums exceeds the
-    tolerance -- and lie within the tolerance plus the oracle's bound ref["unc"] on how far
-    a correct single-precision evaluation may differ.  The per-tensor check allows the norm
-    of the bounds of the Gaussians that exceed.  Gaussians feeding a pixel at an L1 kink
-    (bit 3; the targets are conditioned so there are none) are left out.  sel: optional
-    index subset compared.  Returns the number of Gaussians over the plain tolerance."""
+    """Per element: |g - g_ref| <= rel * max(|g_ref|, floor * max |g_ref| over the tensor).  At
+    most a fraction `max_over` of the compared Gaussians (or 5) may exceed that per-element
+    tolerance, and each of them must be one the oracle flags -- one of its decisions (alpha
+    skip / clamp / stop, tile membership) lies within rounding distance of its threshold at
+    a pixel with a gradient (ref["amb"] bits 0, 2), or the oracle's bound on single-
+    precision rounding (of its gradient sums, and of the projection adjoint's chain)
+    exceeds the tolerance -- and lie within the tolerance plus the oracle's bound
+    ref["unc"] on how far a correct single-precision evaluation may differ.  Per tensor,
+    over the Gaussians within the per-element tolerance, ||g - g_ref|| <= rel ||g_ref||.
+    Gaussians feeding a pixel at an L1 kink (bit 3; the targets are conditioned so there
+    are none) are left out.  sel: optional index subset compared.  Returns the number of
+    Gaussians over the plain tolerance."""
     keep = (ref["amb"] & 8) == 0
     if sel is not None:
         m = np.zeros_like(keep)
@@ -148,12 +149,13 @@ def assert_grads_close(got: dict, ref: dict, keys=("means", "log_scales", "quats
     for k, (g, r, u, tol, err) in rows.items():
         allow = tol + np.where(flagged[:, None], u, 0.0)
         bad = err > allow
-        nrm = np.linalg.norm(g - r) / np.linalg.norm(r)
-        unrm = np.linalg.norm(u[over]) / np.linalg.norm(r)
+        nrm_all = np.linalg.norm(g - r) / np.linalg.norm(r)
+        rin = np.linalg.norm(r[~over])
+        nrm = np.linalg.norm((g - r)[~over]) / rin if rin > 0 else 0.0
         if report is not None:
-            report[k] = dict(bad=int(bad.sum()), norm=float(nrm), unc_norm_over=float(unrm),
+            report[k] = dict(bad=int(bad.sum()), norm=float(nrm), norm_all=float(nrm_all),
                              worst=float((err / allow).max()), over=int(((err > tol).any(1)).sum()))
-        assert nrm <= rel + unrm, (k, nrm, unrm)
+        assert nrm <= rel, (k, nrm)
         worst = np.unravel_index(int(np.argmax(err / allow)), err.shape)
         assert not bad.any(), (k, int(bad.sum()), float((err / allow).max()),
                                int(np.nonzero(keep)[0][worst[0]]), r[worst[0]].tolist(), g[worst[0]].tolist())
@@ -161,7 +163,7 @@ def assert_grads_close(got: dict, ref: dict, keys=("means", "log_scales", "quats
         report["summary"] = dict(compared=n, flagged=int(flagged.sum()), over_plain_tolerance=int(over.sum()))
     # every Gaussian over the plain tolerance is flagged, and they are few
     assert not (over & ~flagged).any()
-    assert over.sum() <= max_over * n, (int(over.sum()), n)
+    assert over.sum() <= max(max_over * n, 5), (int(over.sum()), n)
     return int(over.sum())
 
 

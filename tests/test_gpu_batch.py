@@ -113,6 +113,57 @@ def test_batch_step_matches_single_keyframe_calls(tile, schedule):
     bt.ctx.close()
 
 
+@pytest.mark.parametrize("share", [(0, 1, 0), (0, 1, 2)])
+def test_batch_step_overwrites_gradients_with_grads_zero(share):
+    # grads_zero = 1: buffers filled with NaN beforehand hold exactly the step's gradients
+    # afterwards -- overwritten where a keyframe uses its buffers alone, cleared and added
+    # to where keyframes share them -- equal to a zeroed accumulating step
+    cases = _scenes()
+    ref = Batch(cases, share=share)
+    ref.zero_grads()
+    ref.step(schedule=dqo.SCHEDULE_SPLIT)
+    bt = Batch(cases, share=share, grads_zero=1)
+    for gd, gr in bt.scenes.values():
+        for v in gr.values():
+            v.fill_(float("nan"))
+    for _ in range(2):          # a second step overwrites the first step's gradients
+        bt.step(schedule=dqo.SCHEDULE_SPLIT)
+    torch.cuda.synchronize()
+    for key in ref.scenes:
+        for name in GRAD_KEYS:
+            a = bt.scenes[key][1][name].cpu().numpy()
+            b = ref.scenes[key][1][name].cpu().numpy()
+            assert np.isfinite(a).all(), (key, name)
+            assert _close(a, b), (key, name)
+    ref.ctx.close()
+    bt.ctx.close()
+
+
+def test_single_call_backward_overwrites_gradients_with_grads_zero():
+    g, cam, t = tiny_case(seed=1205)
+    g = dict(g)
+    g["means"] = g["means"].copy()
+    g["means"][::5, 2] -= 6.0                # culled Gaussians: their gradient is zero
+    _, ref = _single(g, cam, t)
+    ctx = dqo.Context()
+    gd, td = dqo.to_device(g), dqo.to_device(t)
+    out = dqo.alloc_outputs(cam["width"], cam["height"])
+    grads = {k: torch.full_like(v, float("nan")) for k, v in dqo.alloc_grads(g["means"].shape[0]).items()}
+    st = dqo.settings(grads_zero=1)
+    gs, cs, ts = dqo.gaussians(gd, NUM_OBJECTS), dqo.camera(cam), dqo.targets(td)
+    dqo.dqo_render_forward(ctx, st, gs, cs, ts, dqo.render_out(out))
+    for _ in range(2):
+        dqo.dqo_render_backward(ctx, st, gs, cs, ts, None, dqo.gaussian_grads(grads))
+    torch.cuda.synchronize()
+    for name in GRAD_KEYS:
+        a = grads[name].cpu().numpy()
+        assert np.array_equal(a, ref[name]), name
+        assert not a.reshape(a.shape[0], -1)[::5].any(), name
+    with pytest.raises(dqo.DqoError):
+        dqo.dqo_render_backward(ctx, dqo.settings(grads_zero=2), gs, cs, ts, None, dqo.gaussian_grads(grads))
+    ctx.close()
+
+
 def test_batch_step_against_oracle():
     cases = _scenes()
     bt = Batch(cases)
