@@ -52,7 +52,7 @@ struct dqo_ctx {
   // batched step: joint buffers of all keyframes of a batch, pair capacity, side stream
   struct Batch {
     Buf p0, p1, p2, rect, ntiles, zkey_a, zkey_b, zval_a, zval_b, gid, offsets, grad2d;
-    Buf scan_scratch, depth_scan_scratch, depth_hist, hist, pair_a, pair_b, list, ranges, loss_part;
+    Buf scan_scratch, depth_scan_scratch, depth_hist, hist, pair_a, pair_b, list, ranges, tile_count, loss_part;
     Buf T_final, n_contrib, dl_rgb, dl_depth, dl_ins, counters, tile_sched, hitrec;
     uint64_t* host = nullptr;  // pinned: pair count of a sizing call
     std::vector<int64_t> sig;  // layout of the last sizing call
@@ -770,6 +770,7 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
     DQO_CUDA(c, ensure(B.offsets, 4 * N));
     DQO_CUDA(c, ensure(B.grad2d, 48 * N));
     DQO_CUDA(c, ensure(B.ranges, 8 * T));
+    DQO_CUDA(c, ensure(B.tile_count, 4 * T));
     DQO_CUDA(c, ensure(B.tile_sched, 4 * (1 + 2 * kTileParts) * T));
     DQO_CUDA(c, ensure(B.loss_part, 12 * T));
     DQO_CUDA(c, ensure(B.T_final, 4 * P));
@@ -792,13 +793,15 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
   uint32_t* d_overflow = d_nvis + 1;
   uint32_t* d_queue = reinterpret_cast<uint32_t*>(d_total + 2);
   uint32_t* d_sort_err = d_queue + 2;  // byte 24: a sort's look-back wait gave up
+  uint64_t* d_live = d_total + 4;      // byte 32: pairs the pair sort reads (all ones before the emission)
   const int rank_bits = bits_for((uint64_t)N);  // static bounds, so the step captures
   const int tile_bits = bits_for(T);
   const int end_bit = rank_bits + tile_bits;
   int64_t launches = 0;
 
-  DQO_CUDA(c, cudaMemsetAsync(B.counters.p, 0, 64, s_));
-  DQO_CUDA(c, cudaMemsetAsync(B.ranges.p, 0, 8 * T, s_));
+  DQO_CUDA(c, cudaMemsetAsync(B.counters.p, 0, 32, s_));
+  DQO_CUDA(c, cudaMemsetAsync(d_live, 0xFF, 8, s_));
+  DQO_CUDA(c, cudaMemsetAsync(B.tile_count.p, 0, 4 * T, s_));   // the ranges are written from these
   if (s->grads_zero) {
     // gradient buffers shared by several keyframes take atomic additions: clear them first
     // (once per buffer set); unshared ones are overwritten by the adjoint
@@ -900,23 +903,24 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
       et.kf[k].ntx = rp[k].ntx;
     }
     const bool k32 = end_bit <= 32;
+    // the emission counts the pair sort's digit histograms; the sort's last pass writes
+    // the tile list and each tile's pair count, from which the forward's tile schedule
+    // writes the ranges
+    uint32_t* ghist = nullptr;
+    DQO_CUDA(c, radix_clear_scratch(as<uint32_t>(B.hist), (int64_t)cap, rank_bits, end_bit, &ghist, s_));
     DQO_CUDA(c, launch_emit_pairs_batch(et, nkf, N, as<ushort4>(B.rect), as<uint32_t>(B.offsets), order, rank_bits,
-                                        cap, B.pair_a.p, k32, d_overflow, s_));
+                                        cap, B.pair_a.p, k32, d_overflow, d_total, d_live, ghist,
+                                        (end_bit - rank_bits + kRadixBits - 1) / kRadixBits, s_));
+    const PairOut po{order, as<uint32_t>(B.list), as<uint32_t>(B.tile_count), rank_bits, (uint32_t)T,
+                     (uint32_t)N};
     int psel = 0;
-    if (k32) {
-      DQO_CUDA(c, radix_sort_u32_dev(as<uint32_t>(B.pair_a), as<uint32_t>(B.pair_b), (int64_t)cap, end_bit,
-                                     as<uint32_t>(B.hist), &psel, s_, d_total, d_sort_err, rank_bits));
-      DQO_CUDA(c, launch_tile_ranges_u32(psel ? as<uint32_t>(B.pair_b) : as<uint32_t>(B.pair_a), (int64_t)cap,
-                                         rank_bits, order, as<uint2>(B.ranges), as<uint32_t>(B.list), s_,
-                                         d_total));
-    } else {
-      DQO_CUDA(c, radix_sort_u64(as<uint64_t>(B.pair_a), as<uint64_t>(B.pair_b), (int64_t)cap, end_bit,
-                                 as<uint32_t>(B.hist), &psel, s_, d_total, d_sort_err, rank_bits));
-      DQO_CUDA(c, launch_tile_ranges_u64(psel ? as<uint64_t>(B.pair_b) : as<uint64_t>(B.pair_a), (int64_t)cap,
-                                         rank_bits, order, as<uint2>(B.ranges), as<uint32_t>(B.list), s_,
-                                         d_total));
-    }
-    launches += 2 + radix_sort_launches((int64_t)cap, end_bit, rank_bits);
+    if (k32)
+      DQO_CUDA(c, radix_sort_pairs_u32(as<uint32_t>(B.pair_a), as<uint32_t>(B.pair_b), (int64_t)cap, end_bit,
+                                       as<uint32_t>(B.hist), &psel, s_, d_live, d_sort_err, rank_bits, po));
+    else
+      DQO_CUDA(c, radix_sort_pairs_u64(as<uint64_t>(B.pair_a), as<uint64_t>(B.pair_b), (int64_t)cap, end_bit,
+                                       as<uint32_t>(B.hist), &psel, s_, d_live, d_sort_err, rank_bits, po));
+    launches += 1 + radix_pair_sort_launches((int64_t)cap, end_bit, rank_bits);
   }
 
   // ---- persistent forward + backward over all tiles, losses, projection adjoint
@@ -976,6 +980,7 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
       lt.kf[k].lambda_ins = rp[k].lambda_ins;
       lt.kf[k].scale = (float)(1.0 / ((double)rp[k].W * (double)rp[k].H));
       lt.kf[k].loss = kf.out.loss;
+      tt.loss[k] = kf.out.loss;
       PreBwdArgs& pa = bt.kf[k];
       pa.rp = rp[k];
       pa.n = kf.gaussians.n;
@@ -1000,18 +1005,19 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
     }
     tt.tile_off[nkf] = toff[nkf];
     tt.nkf = nkf;
+    tt.tile_count = as<uint32_t>(B.tile_count);
     {
       PhaseTimer timer(c, DQO_PHASE_BLEND_STEP, s_);
       const BlendCommon cm{pb.p0, pb.p1, pb.p2, pb.gid, as<uint32_t>(B.list), as<float>(B.grad2d), s->alpha_clamp,
                            s->alpha_min, s->t_stop, s->og_filter ? 1 : 0};
       DQO_CUDA(c, launch_blend_step(tt, cm, d_queue, s->tile_w, with_id, ctas_per_sm, B.sms, schedule, s_));
-      DQO_CUDA(c, launch_loss_reduce_batch(lt, nkf, s_));
+      if (!blend_step_sums_losses(schedule)) DQO_CUDA(c, launch_loss_reduce_batch(lt, nkf, s_));
     }
     {
       PhaseTimer timer(c, DQO_PHASE_PROJECT_BWD, s_);
       DQO_CUDA(c, launch_preprocess_backward_batch(bt, nkf, max_n, s_));
     }
-    launches += 2 + (schedule == 0 ? 2 : schedule == 1 ? 4 : 2 * nkf + 2);
+    launches += (blend_step_sums_losses(schedule) ? 1 : 2) + (schedule == 0 ? 2 : schedule == 1 ? 4 : 2 * nkf + 2);
   }
   if (run_fits) DQO_CUDA(c, cudaStreamWaitEvent(s_, B.join, 0));
   c->launches += launches;

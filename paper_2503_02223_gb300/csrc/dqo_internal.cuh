@@ -266,10 +266,41 @@ struct EmitTable {
   EmitKf kf[16];
 };
 // The same over a batch's n joint Gaussians in joint depth order.  keys: uint32_t[capacity]
-// if k32 (tile and rank bits fit 32), else uint64_t[capacity].
+// if k32 (tile and rank bits fit 32), else uint64_t[capacity].  The emission also counts
+// the pair sort's digit histograms (8-bit digits of the tile bits) into ghist[passes][256]
+// (zeroed by radix_clear_scratch before).  A Gaussian whose pairs do not fit the capacity
+// sets *overflow; *live (all ones before) becomes min(*total, first pair not written), the
+// count the pair sort then reads.
 cudaError_t launch_emit_pairs_batch(const EmitTable& t, int nkf, int64_t n, const ushort4* rect,
                                     const uint32_t* offsets, const uint32_t* order, int rank_bits, uint64_t capacity,
-                                    void* keys, bool k32, uint32_t* overflow, cudaStream_t s);
+                                    void* keys, bool k32, uint32_t* overflow, const uint64_t* total, uint64_t* live,
+                                    uint32_t* ghist, int hist_passes, cudaStream_t s);
+
+// What the last pass of a pair sort writes besides the keys: the tile list (list[p] =
+// order[rank of key p]) and each tile's pair count (added to counts[tile], zero before).
+// Keys whose tile or rank is out of range (stale keys after an overflowed emission) are
+// skipped, and so are positions at or past the live count.
+struct PairOut {
+  const uint32_t* order;
+  uint32_t* list;
+  uint32_t* counts;
+  int rank_bits;
+  uint32_t tiles;
+  uint32_t n_order;
+};
+// Zeroes a pair sort's scratch (histograms, look-back status, counters) for n keys on bits
+// [begin_bit, end_bit) and returns its histogram area (passes x 256 words) in *ghist.
+cudaError_t radix_clear_scratch(uint32_t* scratch, int64_t n, int begin_bit, int end_bit, uint32_t** ghist,
+                                cudaStream_t s);
+// Pair sorts whose histograms the emission counted (radix_clear_scratch, then emission),
+// the last pass writing the tile list and counts (po).
+cudaError_t radix_sort_pairs_u32(uint32_t* keys_a, uint32_t* keys_b, int64_t n, int end_bit, uint32_t* scratch,
+                                 int* sel, cudaStream_t s, const uint64_t* n_dev, uint32_t* err, int begin_bit,
+                                 const PairOut& po);
+cudaError_t radix_sort_pairs_u64(uint64_t* keys_a, uint64_t* keys_b, int64_t n, int end_bit, uint32_t* scratch,
+                                 int* sel, cudaStream_t s, const uint64_t* n_dev, uint32_t* err, int begin_bit,
+                                 const PairOut& po);
+int64_t radix_pair_sort_launches(int64_t n, int end_bit, int begin_bit);
 
 cudaError_t launch_blend_forward(const BlendFwdArgs& a, bool with_id, cudaStream_t s);
 // Tile schedule: order[0..tiles) lists the tiles by decreasing cost (cost[t], or the
@@ -289,6 +320,8 @@ cudaError_t launch_blend_backward(const BlendBwdArgs& a, cudaStream_t s);
 struct StepTable {
   BlendFwdArgs f[16];
   BlendBwdArgs b[16];
+  float* loss[16];        // keyframe k's loss output [4] (NULL: none)
+  const uint32_t* tile_count;  // pairs per joint tile; the forward schedule turns them into ranges
   uint32_t tile_off[17];  // keyframe k owns joint tiles [tile_off[k], tile_off[k+1])
   int nkf;
 };
@@ -321,6 +354,9 @@ struct LossTable {
   LossKf kf[16];
 };
 cudaError_t launch_loss_reduce_batch(const LossTable& t, int nkf, cudaStream_t s);
+// True when launch_blend_step sums the keyframes' losses itself (the per-keyframe schedule
+// folds the sums into its backward tile-schedule launch).
+inline bool blend_step_sums_losses(int schedule) { return schedule == 2; }
 
 cudaError_t launch_quadric_project(int nq, const float* params, int nv, const float* P, const int32_t* q_ptr,
                                    const int32_t* pair_v, int npairs, float* conic, float* bbox, uint8_t* valid,

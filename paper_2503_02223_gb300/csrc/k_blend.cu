@@ -472,16 +472,20 @@ __global__ void __launch_bounds__(kThreads) k_blend_forward(BlendFwdArgs a) {
   blend_fwd_tile<TW, kId>(a, cm, a.tile_order ? (int)a.tile_order[blockIdx.x] : (int)blockIdx.x);
 }
 
-// Deterministic sum of the per-tile loss partials in double, scaled by 1/(HW).
+// Deterministic sum of the per-tile loss partials in double, scaled by 1/(HW).  The first
+// kThreads threads of the block do the arithmetic (the same order for any block size of at
+// least kThreads); every thread takes part in the barriers.
 __device__ __forceinline__ void loss_reduce(const float* __restrict__ part, int tiles, float lambda_ins, float scale,
                                             float* __restrict__ loss) {
   __shared__ double s[3][kThreads];
   double acc[3] = {0, 0, 0};
-  for (int t = threadIdx.x; t < tiles; t += kThreads)
+  if (threadIdx.x < kThreads) {
+    for (int t = threadIdx.x; t < tiles; t += kThreads)
 #pragma unroll
-    for (int k = 0; k < 3; ++k) acc[k] += (double)part[3 * t + k];
+      for (int k = 0; k < 3; ++k) acc[k] += (double)part[3 * t + k];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) s[k][threadIdx.x] = acc[k];
+    for (int k = 0; k < 3; ++k) s[k][threadIdx.x] = acc[k];
+  }
   __syncthreads();
   for (int o = kThreads / 2; o > 0; o >>= 1) {
     if ((int)threadIdx.x < o)
@@ -609,11 +613,69 @@ __device__ __forceinline__ void schedule_tiles(const uint2* __restrict__ ranges,
   }
 }
 
+// Tile ranges of the joint tiles [first, first + tiles) from the pair counts of all joint
+// tiles: ranges[t] = [base + e_t, base + e_t + counts[first + t]), e_t the exclusive prefix
+// of the slice's counts and base the pairs of the tiles before it.  One CTA of
+// kSchedThreads; ends with a barrier.
+__device__ __forceinline__ void ranges_from_counts(const uint32_t* __restrict__ counts, uint32_t first, int tiles,
+                                                   uint2* __restrict__ ranges) {
+  __shared__ uint32_t s_w[kSchedThreads / 32];
+  __shared__ uint32_t s_base;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // base: sum of the counts before the slice
+  uint32_t b = 0;
+  for (uint32_t i = tid; i < first; i += kSchedThreads) b += counts[i];
+  b = __reduce_add_sync(kFull, b);
+  if (lane == 0) s_w[warp] = b;
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < kSchedThreads / 32; ++w) t += s_w[w];
+    s_base = t;
+  }
+  __syncthreads();
+  // thread tid owns the contiguous chunk [tid * per, (tid + 1) * per) of the slice
+  const int per = (tiles + kSchedThreads - 1) / kSchedThreads;
+  const int c0 = min(tid * per, tiles), c1 = min(c0 + per, tiles);
+  uint32_t sum = 0;
+  for (int i = c0; i < c1; ++i) sum += counts[first + i];
+  uint32_t inc = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t u = __shfl_up_sync(kFull, inc, o);
+    if (lane >= o) inc += u;
+  }
+  if (lane == 31) s_w[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t v = s_w[lane];
+    uint32_t wi = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(kFull, wi, o);
+      if (lane >= o) wi += u;
+    }
+    s_w[lane] = wi - v;   // exclusive prefix of the warps' totals
+  }
+  __syncthreads();
+  uint32_t run = s_base + s_w[warp] + inc - sum;
+  for (int i = c0; i < c1; ++i) {
+    const uint32_t c = counts[first + i];
+    ranges[i] = make_uint2(run, run + c);
+    run += c;
+  }
+  __syncthreads();
+}
+
+// counts (optional): the pair counts of the tiles, from which the tile ranges are written
+// first (the batched step's pair sort counts them instead of a separate ranges kernel).
 __global__ void __launch_bounds__(kSchedThreads) k_tile_schedule(const uint2* __restrict__ ranges,
                                                                  const uint32_t* __restrict__ cost, int group,
-                                                                 int tiles, uint32_t* __restrict__ order) {
+                                                                 int tiles, uint32_t* __restrict__ order,
+                                                                 const uint32_t* __restrict__ counts) {
   pdl_wait();
   pdl_trigger();
+  if (counts) ranges_from_counts(counts, 0u, tiles, const_cast<uint2*>(ranges));
   schedule_tiles(ranges, cost, group, tiles, order);
 }
 
@@ -944,7 +1006,8 @@ cudaError_t launch_blend_forward(const BlendFwdArgs& a, bool with_id, cudaStream
 cudaError_t launch_tile_schedule(const uint2* ranges, const uint32_t* cost, int tiles, uint32_t* order,
                                  cudaStream_t s) {
   if (tiles <= 0) return cudaSuccess;
-  launch_dep(k_tile_schedule, dim3(1), dim3(kSchedThreads), s, ranges, cost, kTileParts, tiles, order);
+  launch_dep(k_tile_schedule, dim3(1), dim3(kSchedThreads), s, ranges, cost, kTileParts, tiles, order,
+             static_cast<const uint32_t*>(nullptr));
   return cudaGetLastError();
 }
 
@@ -984,15 +1047,26 @@ unsigned persistent_grid(Kernel k, int ctas_per_sm, int sms, uint32_t total, cud
 }
 
 // One CTA per keyframe of a step table: which = 0 orders t.f[k]'s tiles by list length
-// into t.f[k].tile_order, which = 1 by t.f[k].tile_cost into t.b[k].tile_order.
+// into t.f[k].tile_order, which = 1 by t.f[k].tile_cost into t.b[k].tile_order; with
+// which = 1 and 2 * nkf CTAs, CTA nkf + k sums keyframe k's loss partials.
 __global__ void __launch_bounds__(kSchedThreads) k_tile_schedule_batch(const __grid_constant__ StepTable t,
                                                                        int which) {
   pdl_wait();
   pdl_trigger();
+  if ((int)blockIdx.x >= t.nkf) {
+    const int k = (int)blockIdx.x - t.nkf;
+    const RasterParams& rp = t.f[k].rp;
+    if (t.loss[k])
+      loss_reduce(t.f[k].loss_part, (int)(t.tile_off[k + 1] - t.tile_off[k]), rp.lambda_ins,
+                  (float)(1.0 / ((double)rp.W * (double)rp.H)), t.loss[k]);
+    return;
+  }
   const int k = blockIdx.x;
   const int tiles = (int)(t.tile_off[k + 1] - t.tile_off[k]);
-  if (which == 0)
+  if (which == 0) {
+    if (t.tile_count) ranges_from_counts(t.tile_count, t.tile_off[k], tiles, const_cast<uint2*>(t.f[k].ranges));
     schedule_tiles(t.f[k].ranges, nullptr, 1, tiles, const_cast<uint32_t*>(t.f[k].tile_order));
+  }
   else
     schedule_tiles(nullptr, t.f[k].tile_cost, kTileParts, tiles, const_cast<uint32_t*>(t.b[k].tile_order));
 }
@@ -1009,19 +1083,22 @@ cudaError_t step_tw(const StepTable& t, const BlendCommon& cm, uint32_t* queue, 
   // tiles in one joint order (the per-keyframe arrays are slices of joint arrays, so
   // keyframe 0's pointers are the joint bases), the per-keyframe kernels per keyframe
   const bool sched = t.f[0].tile_order && t.f[0].tile_cost && t.b[0].tile_order && t.tile_off[0] == 0;
+  if (t.tile_count && !sched) return cudaErrorInvalidValue;   // the ranges come from the forward's schedule
   uint32_t* f_order = sched ? const_cast<uint32_t*>(t.f[0].tile_order) : nullptr;
   uint32_t* b_order = sched ? const_cast<uint32_t*>(t.b[0].tile_order) : nullptr;
   if (schedule == 0) {
     const unsigned grid = persistent_grid(k_blend_step<TW, kId>, ctas_per_sm, sms, total, &e);
     if (e != cudaSuccess) return e;
     if (sched)
-      launch_dep(k_tile_schedule, dim3(1), dim3(kSchedThreads), s, t.f[0].ranges, nullptr, 1, (int)total, f_order);
+      launch_dep(k_tile_schedule, dim3(1), dim3(kSchedThreads), s, t.f[0].ranges, nullptr, 1, (int)total, f_order,
+                 t.tile_count);
     k_blend_step<TW, kId><<<grid, kThreads, 0, s>>>(t, cm, queue, f_order);
   } else if (schedule == 1) {
     unsigned grid = persistent_grid(k_blend_fwd_queue<TW, kId>, ctas_per_sm, sms, total, &e);
     if (e != cudaSuccess) return e;
     if (sched)
-      launch_dep(k_tile_schedule, dim3(1), dim3(kSchedThreads), s, t.f[0].ranges, nullptr, 1, (int)total, f_order);
+      launch_dep(k_tile_schedule, dim3(1), dim3(kSchedThreads), s, t.f[0].ranges, nullptr, 1, (int)total, f_order,
+                 t.tile_count);
     k_blend_fwd_queue<TW, kId><<<grid, kThreads, 0, s>>>(t, cm, queue, f_order);
     // the backward's CTAs are tile parts: as many warps per SM as ctas_per_sm whole tiles
     grid = persistent_grid(k_blend_bwd_queue<TW>, ctas_per_sm > 0 ? ctas_per_sm * kBwdParts : 0, sms,
@@ -1029,7 +1106,7 @@ cudaError_t step_tw(const StepTable& t, const BlendCommon& cm, uint32_t* queue, 
     if (e != cudaSuccess) return e;
     if (sched)
       launch_dep(k_tile_schedule, dim3(1), dim3(kSchedThreads), s, nullptr, t.f[0].tile_cost, kTileParts,
-                 (int)total, b_order);
+                 (int)total, b_order, nullptr);
     k_blend_bwd_queue<TW><<<grid, 32 * kBwdWarps, 0, s>>>(t, cm, queue + 1, b_order);
   } else {
     if (sched) launch_dep(k_tile_schedule_batch, dim3((unsigned)t.nkf), dim3(kSchedThreads), s, t, 0);
@@ -1044,7 +1121,20 @@ cudaError_t step_tw(const StepTable& t, const BlendCommon& cm, uint32_t* queue, 
       f.list = cm.list;
       launch_dep(k_blend_forward<TW, kId>, dim3(tiles), dim3(kThreads), s, f);
     }
-    if (sched) launch_dep(k_tile_schedule_batch, dim3((unsigned)t.nkf), dim3(kSchedThreads), s, t, 1);
+    // the backward's schedule, and the keyframes' loss sums in extra CTAs of that launch
+    if (sched) {
+      launch_dep(k_tile_schedule_batch, dim3((unsigned)(2 * t.nkf)), dim3(kSchedThreads), s, t, 1);
+    } else {
+      LossTable lt;
+      for (int k = 0; k < t.nkf; ++k) {
+        lt.kf[k].part = t.f[k].loss_part;
+        lt.kf[k].tiles = (int)(t.tile_off[k + 1] - t.tile_off[k]);
+        lt.kf[k].lambda_ins = t.f[k].rp.lambda_ins;
+        lt.kf[k].scale = (float)(1.0 / ((double)t.f[k].rp.W * (double)t.f[k].rp.H));
+        lt.kf[k].loss = t.loss[k];
+      }
+      launch_dep(k_loss_reduce_batch, dim3((unsigned)t.nkf), dim3(kThreads), s, lt);
+    }
     for (int k = 0; k < t.nkf; ++k) {
       const unsigned tiles = t.tile_off[k + 1] - t.tile_off[k];
       if (tiles == 0) continue;

@@ -36,6 +36,32 @@ __device__ __forceinline__ void quat_rot(const float q[4], float R[3][3]) {
   R[2][0] = 2.f * (x * z - w * y);       R[2][1] = 2.f * (y * z + w * x);       R[2][2] = 1.f - 2.f * (x * x + y * y);
 }
 
+// s + err = a + b exactly (Knuth's two-sum; explicit roundings, nothing contracted).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// a0 m0 + a1 m1 + a2 m2 + t, rounded once: each product is split exactly into its rounded
+// value and its error (an FMA), the four leading terms are added with error-free two-sums
+// and the small parts are added before the single final rounding.  The sum before that
+// rounding is within about 2^-47 (relative) of the exact value, so the result is the exact
+// value correctly rounded except within that distance of a rounding boundary -- what an
+// evaluation in double precision rounded to float gives, without the double-precision
+// pipe (a small fraction of the FP32 rate on this GPU).
+__device__ __forceinline__ float dot3_plus(float a0, float m0, float a1, float m1, float a2, float m2, float t) {
+  const float p0 = __fmul_rn(a0, m0), e0 = __fmaf_rn(a0, m0, -p0);
+  const float p1 = __fmul_rn(a1, m1), e1 = __fmaf_rn(a1, m1, -p1);
+  const float p2 = __fmul_rn(a2, m2), e2 = __fmaf_rn(a2, m2, -p2);
+  float s, r1, r2, r3;
+  two_sum(p0, p1, s, r1);
+  two_sum(s, p2, s, r2);
+  two_sum(s, t, s, r3);
+  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(e0, e1), __fadd_rn(e2, r1)), __fadd_rn(r2, r3));
+  return __fadd_rn(s, lo);
+}
+
 // Same footprint computation for K1 and K8 (identical code path, identical rounding).
 __device__ __forceinline__ void footprint(const RasterParams& rp, const float mean[3], const float ls[3],
                                           const float4 q4, float logit, Footprint& f) {
@@ -43,16 +69,11 @@ __device__ __forceinline__ void footprint(const RasterParams& rp, const float me
   f.ntiles = 0;
   f.rect = make_ushort4(0, 0, 0, 0);
   const float* V = rp.vm;
-  // Camera-space mean in double, rounded once to float: products of two floats are exact
-  // in double, so z (the depth-sort key) is the correctly rounded depth of the float
-  // inputs, reproducible by any exact evaluation.
+  // Camera-space mean rounded once from its exact value, so z (the depth-sort key) is the
+  // correctly rounded depth of the float inputs, reproducible by any exact evaluation.
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    double acc = __dmul_rn((double)V[4 * i + 0], (double)mean[0]);
-    acc = __dadd_rn(acc, __dmul_rn((double)V[4 * i + 1], (double)mean[1]));
-    acc = __dadd_rn(acc, __dmul_rn((double)V[4 * i + 2], (double)mean[2]));
-    f.pc[i] = __double2float_rn(__dadd_rn(acc, (double)V[4 * i + 3]));
-  }
+  for (int i = 0; i < 3; ++i)
+    f.pc[i] = dot3_plus(V[4 * i + 0], mean[0], V[4 * i + 1], mean[1], V[4 * i + 2], mean[2], V[4 * i + 3]);
   const float x = f.pc[0], y = f.pc[1], z = f.pc[2];
   f.opac = 1.f / (1.f + expf(-logit));
   if (!(z >= rp.znear)) return;
@@ -213,11 +234,12 @@ __global__ void __launch_bounds__(kThreads) k_preprocess_batch(const __grid_cons
   preprocess_item(kf.rp, kf.g, o, (int64_t)blockIdx.x * kThreads + threadIdx.x, kf.base, stage);
 }
 
-// Writes one gradient element in the call's mode: +=, atomic +=, or =.
+// Writes one gradient element in the call's mode: +=, atomic +=, or =.  The addition is
+// rounded explicitly, so that v is formed first in every mode (0 += v gives exactly v).
 __device__ __forceinline__ void put_grad(int mode, float* p, float v) {
   if (mode == kGradAtomic) atomicAdd(p, v);
   else if (mode == kGradStore) *p = v;
-  else *p += v;
+  else *p = __fadd_rn(*p, v);
 }
 
 // Zero gradient of a Gaussian that was never binned (written only when overwriting).
