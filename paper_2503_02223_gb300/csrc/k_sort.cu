@@ -344,11 +344,27 @@ __device__ __forceinline__ void warp_emit(const ushort4 r, const uint64_t o, con
     const K rj = __shfl_sync(0xFFFFFFFFu, rk, j);
     const uint32_t toj = __shfl_sync(0xFFFFFFFFu, tile_off, j);   // the Gaussian's keyframe
     const uint32_t ntxj = __shfl_sync(0xFFFFFFFFu, (uint32_t)ntx, j);
-    for (uint32_t k = lane; k < c; k += 32) {
-      const uint32_t ty = y0 + k / w, tx = x0 + k % w;
-      const uint32_t tile = toj + ty * ntxj + tx;
-      keys[oj + k] = ((K)tile << rank_bits) | rj;
-      for (int p = 0; p < hist_passes; ++p) atomicAdd(&hist[p][(tile >> (kRadixBits * p)) & (kRadixBins - 1)], 1u);
+    for (uint32_t base = 0; base < c; base += 32) {  // uniform trip count (warp intrinsics below)
+      const uint32_t k = base + (uint32_t)lane;
+      const bool act = k < c;
+      uint32_t tile = 0;
+      if (act) {
+        const uint32_t ty = y0 + k / w, tx = x0 + k % w;
+        tile = toj + ty * ntxj + tx;
+        keys[oj + k] = ((K)tile << rank_bits) | rj;
+      }
+      if (hist_passes > 0) {
+        // the low digit differs between neighbouring tiles: one addition per lane; the
+        // higher digits are shared by runs of 256 tiles: one addition per group of lanes
+        if (act) atomicAdd(&hist[0][tile & (kRadixBins - 1)], 1u);
+        if (hist_passes > 1) {
+          const uint32_t hi = act ? tile >> kRadixBits : 0xFFFFFFFFu;
+          const uint32_t peers = __match_any_sync(0xFFFFFFFFu, hi);
+          if (act && lane == __ffs(peers) - 1)
+            for (int p = 1; p < hist_passes; ++p)
+              atomicAdd(&hist[p][(tile >> (kRadixBits * p)) & (kRadixBins - 1)], (uint32_t)__popc(peers));
+        }
+      }
     }
   }
 }

@@ -156,8 +156,10 @@ def test_single_call_backward_overwrites_gradients_with_grads_zero():
         dqo.dqo_render_backward(ctx, st, gs, cs, ts, None, dqo.gaussian_grads(grads))
     torch.cuda.synchronize()
     for name in GRAD_KEYS:
+        # the blend backward adds in a run-dependent order: equal to rounding, and culled
+        # Gaussians exactly zero
         a = grads[name].cpu().numpy()
-        assert np.array_equal(a, ref[name]), name
+        assert np.isfinite(a).all() and _close(a, ref[name]), name
         assert not a.reshape(a.shape[0], -1)[::5].any(), name
     with pytest.raises(dqo.DqoError):
         dqo.dqo_render_backward(ctx, dqo.settings(grads_zero=2), gs, cs, ts, None, dqo.gaussian_grads(grads))

@@ -247,8 +247,10 @@ def test_learned_proposal_gains_two_view_fits(trained):
 
 
 def test_learned_proposal_against_plain_fit_at_three_views(trained):
-    """With 3 views both methods run; the plain fit remains the better one there (it is the
-    fallback), the refined proposal stays within a factor of it."""
+    """With 3 views both methods run.  With boxes of 2 px noise the Eq. 1 initialisation is
+    close to the optimum and the plain fit is the more accurate one (it is the fallback and
+    the judge); the refined proposal stays within a factor of it.  The test pins that
+    order, so a change of either side shows here."""
     ctx, st, _, scale = trained
     ev = synth.proposal_samples(1108, N_EVAL)
     ref = oracle.quadric_fit(ev["P"], ev["q_ptr"], ev["pair_v"], ev["obs_bbox"], iters=100)
@@ -261,7 +263,7 @@ def test_learned_proposal_against_plain_fit_at_three_views(trained):
     e_plain = _centre_err(plain["params"].cpu().numpy().astype(np.float64), ref["params"])[ok]
     e_learn = _centre_err(refined["params"].cpu().numpy().astype(np.float64), ref["params"])[ok]
     print(f"3 views: plain centre error median {np.median(e_plain):.4f} m, learned+refined {np.median(e_learn):.4f} m")
-    assert np.median(e_learn) < 2.0 * np.median(e_plain)
+    assert np.median(e_plain) <= np.median(e_learn) < 2.0 * np.median(e_plain)
 
 
 def test_bounded_wait_gives_up_and_the_context_stays_usable():
