@@ -903,14 +903,10 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
       et.kf[k].ntx = rp[k].ntx;
     }
     const bool k32 = end_bit <= 32;
-    // the emission counts the pair sort's digit histograms; the sort's last pass writes
-    // the tile list and each tile's pair count, from which the forward's tile schedule
-    // writes the ranges
-    uint32_t* ghist = nullptr;
-    DQO_CUDA(c, radix_clear_scratch(as<uint32_t>(B.hist), (int64_t)cap, rank_bits, end_bit, &ghist, s_));
+    // the pair sort's last pass writes the tile list and each tile's pair count, from which
+    // the forward's tile schedule writes the ranges
     DQO_CUDA(c, launch_emit_pairs_batch(et, nkf, N, as<ushort4>(B.rect), as<uint32_t>(B.offsets), order, rank_bits,
-                                        cap, B.pair_a.p, k32, d_overflow, d_total, d_live, ghist,
-                                        (end_bit - rank_bits + kRadixBits - 1) / kRadixBits, s_));
+                                        cap, B.pair_a.p, k32, d_overflow, d_total, d_live, s_));
     const PairOut po{order, as<uint32_t>(B.list), as<uint32_t>(B.tile_count), rank_bits, (uint32_t)T,
                      (uint32_t)N};
     int psel = 0;
@@ -920,7 +916,7 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
     else
       DQO_CUDA(c, radix_sort_pairs_u64(as<uint64_t>(B.pair_a), as<uint64_t>(B.pair_b), (int64_t)cap, end_bit,
                                        as<uint32_t>(B.hist), &psel, s_, d_live, d_sort_err, rank_bits, po));
-    launches += 1 + radix_pair_sort_launches((int64_t)cap, end_bit, rank_bits);
+    launches += 1 + radix_sort_launches((int64_t)cap, end_bit, rank_bits);
   }
 
   // ---- persistent forward + backward over all tiles, losses, projection adjoint
@@ -1224,10 +1220,10 @@ dqo_status dqo_mlp_gradients(dqo_ctx* c, void* state, int64_t n, const uint16_t*
   const MlpState ms = state_view(state);
   DQO_CUDA(c, cudaMemsetAsync(ms.grad, 0, sizeof(float) * kMlpParams, s));
   DQO_CUDA(c, cudaMemsetAsync(loss, 0, sizeof(float), s));
-  DQO_CUDA(c, launch_mlp_backward(ms, wk, n, X, XT, ldxt, labels, loss_w, loss, nullptr, s));
+  DQO_CUDA(c, launch_mlp_backward_fused(ms, wk.err, n, X, XT, ldxt, labels, loss_w, loss, nullptr, s));
   DQO_CUDA(c, cudaMemcpyAsync(grads, ms.grad, sizeof(float) * kMlpParams, cudaMemcpyDeviceToDevice, s));
   DQO_CUDA(c, cudaMemsetAsync(ms.grad, 0, sizeof(float) * kMlpParams, s));
-  c->launches += 8;
+  c->launches += 1;
   return DQO_OK;
 }
 
@@ -1247,9 +1243,9 @@ dqo_status dqo_mlp_train_step(dqo_ctx* c, void* state, const dqo_mlp_hparams* hp
   const MlpState ms = state_view(state);
   float* lp = loss;
   if (lp) DQO_CUDA(c, cudaMemsetAsync(lp, 0, sizeof(float), s));
-  DQO_CUDA(c, launch_mlp_backward(ms, wk, n, X, XT, ldxt, labels, hp->loss_w, lp, ms.step, s));
+  DQO_CUDA(c, launch_mlp_backward_fused(ms, wk.err, n, X, XT, ldxt, labels, hp->loss_w, lp, ms.step, s));
   DQO_CUDA(c, launch_mlp_adam(ms, *hp, s));
-  c->launches += 9;
+  c->launches += 2;
   return DQO_OK;
 }
 

@@ -266,20 +266,18 @@ struct EmitTable {
   EmitKf kf[16];
 };
 // The same over a batch's n joint Gaussians in joint depth order.  keys: uint32_t[capacity]
-// if k32 (tile and rank bits fit 32), else uint64_t[capacity].  The emission also counts
-// the pair sort's digit histograms (8-bit digits of the tile bits) into ghist[passes][256]
-// (zeroed by radix_clear_scratch before).  A Gaussian whose pairs do not fit the capacity
-// sets *overflow; *live (all ones before) becomes min(*total, first pair not written), the
-// count the pair sort then reads.
+// if k32 (tile and rank bits fit 32), else uint64_t[capacity].  A Gaussian whose pairs do
+// not fit the capacity sets *overflow; *live (all ones before) becomes min(*total, first
+// pair not written), the count the pair sort then reads.
 cudaError_t launch_emit_pairs_batch(const EmitTable& t, int nkf, int64_t n, const ushort4* rect,
                                     const uint32_t* offsets, const uint32_t* order, int rank_bits, uint64_t capacity,
                                     void* keys, bool k32, uint32_t* overflow, const uint64_t* total, uint64_t* live,
-                                    uint32_t* ghist, int hist_passes, cudaStream_t s);
+                                    cudaStream_t s);
 
-// What the last pass of a pair sort writes besides the keys: the tile list (list[p] =
-// order[rank of key p]) and each tile's pair count (added to counts[tile], zero before).
-// Keys whose tile or rank is out of range (stale keys after an overflowed emission) are
-// skipped, and so are positions at or past the live count.
+// What the last pass of a pair sort writes instead of the sorted keys: the tile list
+// (list[p] = order[rank of key p]) and each tile's pair count (added to counts[tile], zero
+// before).  Keys whose tile or rank is out of range are skipped, and positions at or past
+// the live count are not written.
 struct PairOut {
   const uint32_t* order;
   uint32_t* list;
@@ -288,19 +286,13 @@ struct PairOut {
   uint32_t tiles;
   uint32_t n_order;
 };
-// Zeroes a pair sort's scratch (histograms, look-back status, counters) for n keys on bits
-// [begin_bit, end_bit) and returns its histogram area (passes x 256 words) in *ghist.
-cudaError_t radix_clear_scratch(uint32_t* scratch, int64_t n, int begin_bit, int end_bit, uint32_t** ghist,
-                                cudaStream_t s);
-// Pair sorts whose histograms the emission counted (radix_clear_scratch, then emission),
-// the last pass writing the tile list and counts (po).
+// Pair sorts whose last pass writes the tile list and the per-tile counts (po).
 cudaError_t radix_sort_pairs_u32(uint32_t* keys_a, uint32_t* keys_b, int64_t n, int end_bit, uint32_t* scratch,
                                  int* sel, cudaStream_t s, const uint64_t* n_dev, uint32_t* err, int begin_bit,
                                  const PairOut& po);
 cudaError_t radix_sort_pairs_u64(uint64_t* keys_a, uint64_t* keys_b, int64_t n, int end_bit, uint32_t* scratch,
                                  int* sel, cudaStream_t s, const uint64_t* n_dev, uint32_t* err, int begin_bit,
                                  const PairOut& po);
-int64_t radix_pair_sort_launches(int64_t n, int end_bit, int begin_bit);
 
 cudaError_t launch_blend_forward(const BlendFwdArgs& a, bool with_id, cudaStream_t s);
 // Tile schedule: order[0..tiles) lists the tiles by decreasing cost (cost[t], or the
@@ -419,6 +411,11 @@ cudaError_t launch_mlp_set(const MlpState& st, const float* params, cudaStream_t
 cudaError_t launch_mlp_adam(const MlpState& st, const dqo_mlp_hparams& hp, cudaStream_t s);
 cudaError_t launch_mlp_forward(const MlpState& st, const MlpWork& wk, int64_t n, const uint16_t* X, float* y,
                                cudaStream_t s);
+// Loss and gradients of a batch (n % 128 == 0) in one launch: the eight products of a step
+// fused per 128-sample CTA with the intermediates in shared memory.
+cudaError_t launch_mlp_backward_fused(const MlpState& st, int* err, int64_t n, const uint16_t* X, const uint16_t* XT,
+                                      int64_t ldxt, const float* labels, const float* loss_w, float* loss,
+                                      int* step_inc, cudaStream_t s);
 cudaError_t launch_mlp_backward(const MlpState& st, const MlpWork& wk, int64_t n, const uint16_t* X,
                                 const uint16_t* XT, int64_t ldxt, const float* labels, const float* loss_w,
                                 float* loss, int* step_inc, cudaStream_t s);

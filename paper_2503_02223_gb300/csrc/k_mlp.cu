@@ -333,6 +333,270 @@ __global__ void __launch_bounds__(kGemmThreads) k_mlp_gemm(GemmArgs a) {
   }
 }
 
+// ----------------------------------------------------------------------------- fused training step
+
+// The eight products of a training step (forward, loss, input and weight gradients) for
+// the 128 samples of one CTA, back to back in one kernel with every intermediate in shared
+// memory: the same operands, the same BF16 rounding points and the same per-CTA weight-
+// gradient tiles as the eight launches of launch_mlp_backward, which leave the
+// activations in global memory instead.  A step is one launch of n / 128 CTAs + Adam.
+// Shared memory: five 32 KB slots for 128 x 128 tiles, reused as the step goes on, and
+// four 4 KB slots for the 16-wide tiles; tensor memory: 256 columns, the products
+// alternating between the two halves.
+constexpr int kFusedThreads = 128;
+constexpr uint32_t kSlot = kTileM * 128 * 2;      // 32 KB
+constexpr uint32_t kSmall = kTileM * kMlpOutPad * 2;  // 4 KB
+constexpr int kFusedSmem = 5 * kSlot + 4 * kSmall + 1024;
+constexpr uint32_t kFusedCols = 256;
+
+struct FusedArgs {
+  MlpState st;
+  const __nv_bfloat16* X;   // [n][128]
+  const __nv_bfloat16* XT;  // [128][ldxt]
+  int64_t ldxt;
+  const float* labels;      // [n][9]
+  float w[9];
+  float inv_batch;
+  float* loss;              // += sum of the batch's weighted squared errors / n
+  int* step_inc;            // block 0 adds 1 (the optimiser's step count); may be NULL
+  int* err;                 // set to 1 if a tensor-core wait timed out
+};
+
+// Thread m stores its 16 values of columns [c, c + 16) of row m into a K-major 128-row tile.
+__device__ __forceinline__ void put_row16(unsigned char* tile, int m, int c, const __nv_bfloat16 (&h)[16]) {
+  *reinterpret_cast<uint4*>(tile + tile_offset(m, c, kTileM)) = reinterpret_cast<const uint4*>(h)[0];
+  *reinterpret_cast<uint4*>(tile + tile_offset(m, c + 8, kTileM)) = reinterpret_cast<const uint4*>(h)[1];
+}
+// ... and into the transposed K-major tile (rows = the columns c + j, K = the samples).
+__device__ __forceinline__ void put_col16(unsigned char* tileT, int rowsT, int m, int c,
+                                          const __nv_bfloat16 (&h)[16]) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j)
+    *reinterpret_cast<__nv_bfloat16*>(tileT + tile_offset(c + j, m, rowsT)) = h[j];
+}
+
+// D[tmem] = A[a] . B[b]^T over K (multiple of 16) for an N-wide B, issued by thread 0 and
+// committed to the mbarrier; every thread then waits (bounded) for phase `ph`.
+__device__ __forceinline__ bool fused_mma(uint32_t tmem, const unsigned char* a, const unsigned char* b, int N, int K,
+                                          uint32_t bar, uint32_t ph) {
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (threadIdx.x == 0) {
+    const uint32_t idesc = idesc_bf16(kTileM, N);
+    const uint32_t abase = smem_u32(a), bbase = smem_u32(b);
+    for (int s = 0; s < (K >> 4); ++s)
+      mma_bf16(tmem, smem_desc(abase + (uint32_t)(s * kTileM * 32)), smem_desc(bbase + (uint32_t)(s * N * 32)),
+               idesc, s > 0 ? 1u : 0u);
+    mma_commit(bar);
+  }
+  const bool ok = mbar_wait_bounded(bar, ph);
+  tc_fence_after();
+  return __syncthreads_and(ok ? 1 : 0) != 0;
+}
+
+// Row sums of a K-major tile's rows [0, rows) over its 128 samples (bias gradients).
+__device__ __forceinline__ void bias_grad(const unsigned char* tileT, int rowsT, int rows, float* db) {
+  const int t = threadIdx.x;
+  if (t >= rows) return;
+  float s = 0.f;
+  for (int k = 0; k < kTileM; ++k)
+    s += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(tileT + tile_offset(t, k, rowsT)));
+  atomicAdd(db + t, s);
+}
+
+__global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_train_fused(FusedArgs a) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  pdl_wait();
+  pdl_trigger();
+  const int t = threadIdx.x, w = t >> 5;
+  const int64_t m0 = (int64_t)blockIdx.x * kTileM;
+  const int m = (int)m0 + t;  // this thread's sample (the batch is a multiple of 128 rows)
+  unsigned char* sA = sm;                  // X, then W2, then G2
+  unsigned char* sB = sm + kSlot;          // W1, then H2, then W2T, then XT
+  unsigned char* sC = sm + 2 * kSlot;      // H1, then G2T
+  unsigned char* sD = sm + 3 * kSlot;      // H1T
+  unsigned char* sE = sm + 4 * kSlot;      // H2T, then G1T
+  unsigned char* s0 = sm + 5 * kSlot;      // W3 [16][128]
+  unsigned char* s1 = s0 + kSmall;         // dY [128][16]
+  unsigned char* s2 = s1 + kSmall;         // dY^T [16][128]
+  unsigned char* s3 = s2 + kSmall;         // W3^T [128][16]
+  const MlpState& st = a.st;
+  if (a.step_inc && t == 0 && blockIdx.x == 0) atomicAdd(a.step_inc, 1);
+  if (w == 0) {
+    tmem_alloc(smem_u32(&tslot), kFusedCols);
+    tmem_relinquish();
+  }
+  if (t == 0) mbar_init(smem_u32(&mbar), 1);
+  const uint32_t bar = smem_u32(&mbar);
+  load_tile(sA, a.X + m0 * kMlpIn, kMlpIn, kTileM, kTileM, 128);
+  load_tile(sB, st.w1b, kMlpHidden, 128, 128, 128);
+  load_tile(s0, st.w3b, kMlpHidden, kMlpOutPad, kMlpOutPad, 128);
+  load_tile(s3, st.w3tb, kMlpOutPad, 128, 128, kMlpOutPad);
+  __syncthreads();
+  const uint32_t t0 = tslot, lane_off = (uint32_t)(w * 32) << 16;
+  const uint32_t tA = t0 + lane_off, tB = t0 + 128u + lane_off;  // this thread's TMEM lane, two halves
+  uint32_t ph = 0;
+  bool ok = true;
+  uint32_t mask1[4] = {0u, 0u, 0u, 0u}, mask2[4] = {0u, 0u, 0u, 0u};
+
+  // ---- H1 = relu(X W1^T + b1): rows into sC, transposed into sD
+  ok = fused_mma(t0, sA, sB, 128, 128, bar, ph);
+  ph ^= 1u;
+  if (ok) {
+    for (int c = 0; c < 128; c += 16) {
+      float v[16];
+      tmem_ld16(tA + (uint32_t)c, v);
+      __align__(16) __nv_bfloat16 h[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        h[j] = __float2bfloat16_rn(fmaxf(v[j] + st.param[kMlpB1 + c + j], 0.f));
+        if (__bfloat162float(h[j]) > 0.f) mask1[(c + j) >> 5] |= 1u << ((c + j) & 31);
+      }
+      put_row16(sC, t, c, h);
+      put_col16(sD, kTileM, t, c, h);
+    }
+    tc_fence_before();
+    __syncthreads();
+    load_tile(sA, st.w2b, kMlpHidden, 128, 128, 128);   // X is no longer needed
+  }
+  // ---- H2 = relu(H1 W2^T + b2): rows into sB (W1 free), transposed into sE
+  if (ok) {
+    ok = fused_mma(t0 + 128u, sC, sA, 128, 128, bar, ph);
+    ph ^= 1u;
+  }
+  if (ok) {
+    for (int c = 0; c < 128; c += 16) {
+      float v[16];
+      tmem_ld16(tB + (uint32_t)c, v);
+      __align__(16) __nv_bfloat16 h[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        h[j] = __float2bfloat16_rn(fmaxf(v[j] + st.param[kMlpB2 + c + j], 0.f));
+        if (__bfloat162float(h[j]) > 0.f) mask2[(c + j) >> 5] |= 1u << ((c + j) & 31);
+      }
+      put_row16(sB, t, c, h);
+      put_col16(sE, kTileM, t, c, h);
+    }
+  }
+  // ---- Y = H2 W3^T + b3, the loss, dY = 2 w (y - label) / n: rows into s1, transposed into s2
+  if (ok) {
+    ok = fused_mma(t0, sB, s0, kMlpOutPad, 128, bar, ph);
+    ph ^= 1u;
+  }
+  if (ok) {
+    float v[16];
+    tmem_ld16(tA, v);
+    float l = 0.f;
+    __align__(16) __nv_bfloat16 d[16];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      const float y = v[j] + st.param[kMlpB3 + j];
+      const float e = y - a.labels[(int64_t)m * 9 + j];
+      l += a.w[j] * e * e;
+      d[j] = __float2bfloat16_rn(2.f * a.w[j] * e * a.inv_batch);
+    }
+#pragma unroll
+    for (int j = 9; j < 16; ++j) d[j] = __float2bfloat16_rn(0.f);
+    *reinterpret_cast<uint4*>(s1 + tile_offset(t, 0, kTileM)) = reinterpret_cast<const uint4*>(d)[0];
+    *reinterpret_cast<uint4*>(s1 + tile_offset(t, 8, kTileM)) = reinterpret_cast<const uint4*>(d)[1];
+    put_col16(s2, kMlpOutPad, t, 0, d);
+    if (a.loss) {
+      l = warp_sum_f(l * a.inv_batch);
+      if ((t & 31) == 0) atomicAdd(a.loss, l);
+    }
+  }
+  // ---- G2 = (dY W3) * (H2 > 0): rows into sA (W2 free), transposed into sC (H1 free)
+  if (ok) {
+    ok = fused_mma(t0 + 128u, s1, s3, 128, kMlpOutPad, bar, ph);
+    ph ^= 1u;
+  }
+  if (ok) {
+    for (int c = 0; c < 128; c += 16) {
+      float v[16];
+      tmem_ld16(tB + (uint32_t)c, v);
+      __align__(16) __nv_bfloat16 h[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        h[j] = __float2bfloat16_rn(((mask2[(c + j) >> 5] >> ((c + j) & 31)) & 1u) ? v[j] : 0.f);
+      put_row16(sA, t, c, h);
+      put_col16(sC, kTileM, t, c, h);
+    }
+  }
+  // ---- dW3 += dY^T H2 (A = H2^T, B = dY^T), db3
+  if (ok) {
+    ok = fused_mma(t0, sE, s2, kMlpOutPad, 128, bar, ph);
+    ph ^= 1u;
+  }
+  if (ok) {
+    float v[16];
+    tmem_ld16(tA, v);
+#pragma unroll
+    for (int j = 0; j < kMlpOut; ++j) atomicAdd(st.grad + kMlpW3 + j * kTileM + t, v[j]);
+    bias_grad(s2, kMlpOutPad, kMlpOutPad, st.grad + kMlpB3);
+    tc_fence_before();
+    __syncthreads();
+    load_tile(sB, st.w2tb, kMlpHidden, 128, 128, 128);  // H2 is no longer needed
+  }
+  // ---- G1 = (G2 W2) * (H1 > 0): transposed into sE (H2^T free)
+  if (ok) {
+    ok = fused_mma(t0 + 128u, sA, sB, 128, 128, bar, ph);
+    ph ^= 1u;
+  }
+  if (ok) {
+    for (int c = 0; c < 128; c += 16) {
+      float v[16];
+      tmem_ld16(tB + (uint32_t)c, v);
+      __align__(16) __nv_bfloat16 h[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        h[j] = __float2bfloat16_rn(((mask1[(c + j) >> 5] >> ((c + j) & 31)) & 1u) ? v[j] : 0.f);
+      put_col16(sE, kTileM, t, c, h);
+    }
+  }
+  // ---- dW2 += G2^T H1 (A = H1^T, B = G2^T), db2
+  if (ok) {
+    ok = fused_mma(t0, sD, sC, 128, 128, bar, ph);
+    ph ^= 1u;
+  }
+  if (ok) {
+    for (int c = 0; c < 128; c += 16) {
+      float v[16];
+      tmem_ld16(tA + (uint32_t)c, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) atomicAdd(st.grad + kMlpW2 + (c + j) * kTileM + t, v[j]);
+    }
+    bias_grad(sC, kTileM, kMlpHidden, st.grad + kMlpB2);
+    tc_fence_before();
+    __syncthreads();
+    load_tile(sB, a.XT + m0, a.ldxt, 128, 128, 128);   // W2^T is no longer needed
+  }
+  // ---- dW1 += G1^T X (A = X^T, B = G1^T), db1
+  if (ok) {
+    ok = fused_mma(t0 + 128u, sB, sE, 128, 128, bar, ph);
+    ph ^= 1u;
+  }
+  if (ok) {
+    for (int c = 0; c < 128; c += 16) {
+      float v[16];
+      tmem_ld16(tB + (uint32_t)c, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) atomicAdd(st.grad + kMlpW1 + (c + j) * kTileM + t, v[j]);
+    }
+    bias_grad(sE, kTileM, kMlpHidden, st.grad + kMlpB1);
+  }
+  if (!ok && t == 0 && a.err) atomicExch(a.err, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (w == 0) {
+    tc_fence_after();
+    tmem_dealloc(t0, kFusedCols);
+  }
+}
+
 // ----------------------------------------------------------------------------- features
 
 // One thread per (quadric, view slot): decomposes P = K [R | t] and writes the slot's 16
@@ -476,7 +740,9 @@ cudaError_t mlp_gemm_setup() {
     return e;
   if ((e = cudaFuncSetAttribute(k_mlp_gemm<kEpiReluGrad>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem)))
     return e;
-  return cudaFuncSetAttribute(k_mlp_gemm<kEpiWgrad>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+  if ((e = cudaFuncSetAttribute(k_mlp_gemm<kEpiWgrad>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem)))
+    return e;
+  return cudaFuncSetAttribute(k_mlp_train_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmem);
 }
 
 namespace {
@@ -545,6 +811,28 @@ cudaError_t launch_mlp_forward(const MlpState& st, const MlpWork& wk, int64_t n,
   a.bias = st.param + kMlpB3;
   a.y = y;
   return gemm<kEpiOut>(a, grid, s);
+}
+
+// Loss and gradients of a batch (n % 128 == 0) in one launch of n / 128 CTAs (the eight
+// products of launch_mlp_backward fused, intermediates in shared memory).  Gradients are
+// ADDED to st.grad; the loss is ADDED to *loss.
+cudaError_t launch_mlp_backward_fused(const MlpState& st, int* err, int64_t n, const uint16_t* X_,
+                                      const uint16_t* XT_, int64_t ldxt, const float* labels, const float* loss_w,
+                                      float* loss, int* step_inc, cudaStream_t s) {
+  if (n <= 0 || n % kTileM) return cudaErrorInvalidValue;
+  FusedArgs a{};
+  a.st = st;
+  a.X = reinterpret_cast<const __nv_bfloat16*>(X_);
+  a.XT = reinterpret_cast<const __nv_bfloat16*>(XT_);
+  a.ldxt = ldxt;
+  a.labels = labels;
+#pragma unroll
+  for (int j = 0; j < 9; ++j) a.w[j] = loss_w[j];
+  a.inv_batch = 1.f / (float)n;
+  a.loss = loss;
+  a.step_inc = step_inc;
+  a.err = err;
+  return launch_dep_smem(k_mlp_train_fused, dim3((unsigned)(n / kTileM)), dim3(kFusedThreads), kFusedSmem, s, a);
 }
 
 // Loss and gradients of a batch (n % 128 == 0): eight launches.  Gradients are ADDED to

@@ -329,8 +329,7 @@ __global__ void k_rank_scatter(const uint32_t* __restrict__ order, int64_t n, ui
 // Gaussian covering many tiles does not leave the rest of its warp idle.
 template <typename K>
 __device__ __forceinline__ void warp_emit(const ushort4 r, const uint64_t o, const uint32_t cnt, const K rk,
-                                          uint32_t tile_off, int ntx, int rank_bits, K* __restrict__ keys,
-                                          uint32_t (*hist)[kRadixBins] = nullptr, int hist_passes = 0) {
+                                          uint32_t tile_off, int ntx, int rank_bits, K* __restrict__ keys) {
   const int lane = threadIdx.x & 31;
   uint32_t pending = __ballot_sync(0xFFFFFFFFu, cnt > 0);
   while (pending) {
@@ -344,27 +343,9 @@ __device__ __forceinline__ void warp_emit(const ushort4 r, const uint64_t o, con
     const K rj = __shfl_sync(0xFFFFFFFFu, rk, j);
     const uint32_t toj = __shfl_sync(0xFFFFFFFFu, tile_off, j);   // the Gaussian's keyframe
     const uint32_t ntxj = __shfl_sync(0xFFFFFFFFu, (uint32_t)ntx, j);
-    for (uint32_t base = 0; base < c; base += 32) {  // uniform trip count (warp intrinsics below)
-      const uint32_t k = base + (uint32_t)lane;
-      const bool act = k < c;
-      uint32_t tile = 0;
-      if (act) {
-        const uint32_t ty = y0 + k / w, tx = x0 + k % w;
-        tile = toj + ty * ntxj + tx;
-        keys[oj + k] = ((K)tile << rank_bits) | rj;
-      }
-      if (hist_passes > 0) {
-        // the low digit differs between neighbouring tiles: one addition per lane; the
-        // higher digits are shared by runs of 256 tiles: one addition per group of lanes
-        if (act) atomicAdd(&hist[0][tile & (kRadixBins - 1)], 1u);
-        if (hist_passes > 1) {
-          const uint32_t hi = act ? tile >> kRadixBits : 0xFFFFFFFFu;
-          const uint32_t peers = __match_any_sync(0xFFFFFFFFu, hi);
-          if (act && lane == __ffs(peers) - 1)
-            for (int p = 1; p < hist_passes; ++p)
-              atomicAdd(&hist[p][(tile >> (kRadixBits * p)) & (kRadixBins - 1)], (uint32_t)__popc(peers));
-        }
-      }
+    for (uint32_t k = lane; k < c; k += 32) {
+      const uint32_t ty = y0 + k / w, tx = x0 + k % w;
+      keys[oj + k] = ((K)(toj + ty * ntxj + tx) << rank_bits) | rj;
     }
   }
 }
@@ -400,10 +381,6 @@ __global__ void __launch_bounds__(kThreads) k_emit_pairs(const ushort4* __restri
 // `capacity` are not written; *overflow is set instead.  *live (all ones before) becomes
 // the smaller of the pair count *total and the first pair not written: the count the pair
 // sort reads, so that it sees only pairs of this call.
-// kEmitPer ranks per thread (a CTA covers kThreads * kEmitPer ranks), so that the CTAs'
-// digit histograms of the pair sort reach global memory in few atomic additions.
-constexpr int kEmitPer = 4;
-
 template <typename K>
 __global__ void __launch_bounds__(kThreads) k_emit_pairs_batch(const __grid_constant__ EmitTable t, int nkf,
                                                                const ushort4* __restrict__ rect,
@@ -412,42 +389,30 @@ __global__ void __launch_bounds__(kThreads) k_emit_pairs_batch(const __grid_cons
                                                                int rank_bits, uint64_t capacity, K* __restrict__ keys,
                                                                uint32_t* __restrict__ overflow,
                                                                const unsigned long long* __restrict__ total,
-                                                               unsigned long long* __restrict__ live,
-                                                               uint32_t* __restrict__ ghist, int hist_passes) {
+                                                               unsigned long long* __restrict__ live) {
   pdl_wait();
   pdl_trigger();
-  __shared__ uint32_t h[kMaxRadixPasses][kRadixBins];
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicMin(live, *total);
-  for (int i = threadIdx.x; i < hist_passes * kRadixBins; i += kThreads) (&h[0][0])[i] = 0u;
-  __syncthreads();
-#pragma unroll 1
-  for (int u = 0; u < kEmitPer; ++u) {
-    const int64_t r = ((int64_t)blockIdx.x * kEmitPer + u) * kThreads + threadIdx.x;
-    ushort4 q = make_ushort4(0, 0, 0, 0);
-    uint64_t o = 0;
-    uint32_t cnt = 0;
-    int k = 0;
-    if (r < n) {
-      const int64_t gi = order[r];
-      while (k + 1 < nkf && t.kf[k + 1].base <= gi) ++k;
-      q = rect[gi];
-      if (q.z > q.x && q.w > q.y) {
-        o = offsets[r];
-        cnt = (uint32_t)(q.z - q.x) * (uint32_t)(q.w - q.y);
-        if (o + cnt > capacity) {
-          atomicExch(overflow, 1u);
-          atomicMin(live, (unsigned long long)o);
-          cnt = 0;
-        }
+  const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  ushort4 q = make_ushort4(0, 0, 0, 0);
+  uint64_t o = 0;
+  uint32_t cnt = 0;
+  int k = 0;
+  if (r < n) {
+    const int64_t gi = order[r];
+    while (k + 1 < nkf && t.kf[k + 1].base <= gi) ++k;
+    q = rect[gi];
+    if (q.z > q.x && q.w > q.y) {
+      o = offsets[r];
+      cnt = (uint32_t)(q.z - q.x) * (uint32_t)(q.w - q.y);
+      if (o + cnt > capacity) {
+        atomicExch(overflow, 1u);
+        atomicMin(live, (unsigned long long)o);
+        cnt = 0;
       }
     }
-    warp_emit<K>(q, o, cnt, (K)r, t.kf[k].tile_off, t.kf[k].ntx, rank_bits, keys, h, hist_passes);
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < hist_passes * kRadixBins; i += kThreads) {
-    const uint32_t c = (&h[0][0])[i];
-    if (c) atomicAdd(ghist + i, c);
-  }
+  warp_emit<K>(q, o, cnt, (K)r, t.kf[k].tile_off, t.kf[k].ntx, rank_bits, keys);
 }
 
 template <typename K>
@@ -491,24 +456,20 @@ inline size_t onesweep_words(int64_t tiles, int passes) {
   return (size_t)passes * kRadixBins * (size_t)(tiles + 1) + (size_t)passes + 1;
 }
 
-// hist_ready: the scratch was cleared and the histograms counted by the caller (the pair
-// emission), so neither the clearing nor the histogram kernel runs here.  po (optional):
-// the last pass also writes the tile list and per-tile counts.
+// po (optional): the last pass writes the tile list and per-tile counts instead of keys.
 template <typename K, bool kVals, int IPT>
 cudaError_t radix_passes(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n, int begin_bit, int end_bit,
                          uint32_t* scratch, int* sel, cudaStream_t s, const uint64_t* n_dev, uint32_t* rank,
-                         uint32_t* err_out, bool hist_ready, const PairOut* po) {
+                         uint32_t* err_out, const PairOut* po) {
   const unsigned nb = grid_for(n, kThreads * IPT);
   const int passes = (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;
   uint32_t* ghist = scratch;
   uint32_t* status = ghist + (size_t)passes * kRadixBins;
   uint32_t* counters = status + (size_t)passes * nb * kRadixBins;
   uint32_t* err = err_out ? err_out : counters + passes;
-  if (!hist_ready) {
-    cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * onesweep_words(nb, passes), s);
-    if (e != cudaSuccess) return e;
-    launch_dep(k_onesweep_hist<K, IPT>, dim3(nb), dim3(kThreads), s, ka, n, n_dev, begin_bit, passes, ghist);
-  }
+  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * onesweep_words(nb, passes), s);
+  if (e != cudaSuccess) return e;
+  launch_dep(k_onesweep_hist<K, IPT>, dim3(nb), dim3(kThreads), s, ka, n, n_dev, begin_bit, passes, ghist);
   const PairOut none{nullptr, nullptr, nullptr, 0, 0u, 0u};
   K* kin = ka; K* kout = kb;
   uint32_t* vin = va; uint32_t* vout = vb;
@@ -529,8 +490,7 @@ cudaError_t radix_passes(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n, in
 template <typename K, bool kVals>
 cudaError_t radix_sort_impl(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n, int end_bit, uint32_t* hist,
                             int* sel, cudaStream_t s, const uint64_t* n_dev = nullptr, uint32_t* rank = nullptr,
-                            uint32_t* err = nullptr, int begin_bit = 0, bool hist_ready = false,
-                            const PairOut* po = nullptr) {
+                            uint32_t* err = nullptr, int begin_bit = 0, const PairOut* po = nullptr) {
   *sel = 0;
   if (begin_bit < 0 || end_bit > (int)(8 * sizeof(K))) return cudaErrorInvalidValue;
   if (n <= 1 || end_bit <= begin_bit) {  // already in order: ranks from the values as they stand
@@ -540,10 +500,8 @@ cudaError_t radix_sort_impl(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n,
   }
   if (end_bit - begin_bit > kMaxRadixPasses * kRadixBits) return cudaErrorInvalidValue;
   if (sort_items(n) == 8)
-    return radix_passes<K, kVals, 8>(ka, kb, va, vb, n, begin_bit, end_bit, hist, sel, s, n_dev, rank, err,
-                                     hist_ready, po);
-  return radix_passes<K, kVals, 16>(ka, kb, va, vb, n, begin_bit, end_bit, hist, sel, s, n_dev, rank, err,
-                                    hist_ready, po);
+    return radix_passes<K, kVals, 8>(ka, kb, va, vb, n, begin_bit, end_bit, hist, sel, s, n_dev, rank, err, po);
+  return radix_passes<K, kVals, 16>(ka, kb, va, vb, n, begin_bit, end_bit, hist, sel, s, n_dev, rank, err, po);
 }
 
 }  // namespace
@@ -629,18 +587,17 @@ cudaError_t launch_tile_ranges_u64(const uint64_t* keys, int64_t m, int rank_bit
 cudaError_t launch_emit_pairs_batch(const EmitTable& t, int nkf, int64_t n, const ushort4* rect,
                                     const uint32_t* offsets, const uint32_t* order, int rank_bits, uint64_t capacity,
                                     void* keys, bool k32, uint32_t* overflow, const uint64_t* total, uint64_t* live,
-                                    uint32_t* ghist, int hist_passes, cudaStream_t s) {
+                                    cudaStream_t s) {
   if (nkf == 0 || n == 0) return cudaSuccess;
-  if (hist_passes < 0 || hist_passes > kMaxRadixPasses || (hist_passes > 0 && !ghist)) return cudaErrorInvalidValue;
-  const unsigned grid = grid_for(n, kThreads * kEmitPer);
+  const unsigned grid = grid_for(n, kThreads);
   if (k32)
     launch_dep(k_emit_pairs_batch<uint32_t>, dim3(grid), dim3(kThreads), s, t, nkf, rect, offsets, order, n, rank_bits,
                capacity, static_cast<uint32_t*>(keys), overflow, reinterpret_cast<const unsigned long long*>(total),
-               reinterpret_cast<unsigned long long*>(live), ghist, hist_passes);
+               reinterpret_cast<unsigned long long*>(live));
   else
     launch_dep(k_emit_pairs_batch<uint64_t>, dim3(grid), dim3(kThreads), s, t, nkf, rect, offsets, order, n, rank_bits,
                capacity, static_cast<uint64_t*>(keys), overflow, reinterpret_cast<const unsigned long long*>(total),
-               reinterpret_cast<unsigned long long*>(live), ghist, hist_passes);
+               reinterpret_cast<unsigned long long*>(live));
   return cudaGetLastError();
 }
 
@@ -650,32 +607,19 @@ cudaError_t radix_sort_u32_dev(uint32_t* keys_a, uint32_t* keys_b, int64_t n, in
                                           nullptr, err, begin_bit);
 }
 
-cudaError_t radix_clear_scratch(uint32_t* scratch, int64_t n, int begin_bit, int end_bit, uint32_t** ghist,
-                                cudaStream_t s) {
-  const int64_t m = n > 0 ? n : 1;
-  const unsigned nb = grid_for(m, kThreads * sort_items(m));
-  const int passes = (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;
-  if (ghist) *ghist = scratch;
-  return cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * onesweep_words(nb, passes), s);
-}
-
 cudaError_t radix_sort_pairs_u32(uint32_t* keys_a, uint32_t* keys_b, int64_t n, int end_bit, uint32_t* scratch,
                                  int* sel, cudaStream_t s, const uint64_t* n_dev, uint32_t* err, int begin_bit,
                                  const PairOut& po) {
   return radix_sort_impl<uint32_t, false>(keys_a, keys_b, nullptr, nullptr, n, end_bit, scratch, sel, s, n_dev,
-                                          nullptr, err, begin_bit, true, &po);
+                                          nullptr, err, begin_bit, &po);
 }
 
 cudaError_t radix_sort_pairs_u64(uint64_t* keys_a, uint64_t* keys_b, int64_t n, int end_bit, uint32_t* scratch,
                                  int* sel, cudaStream_t s, const uint64_t* n_dev, uint32_t* err, int begin_bit,
                                  const PairOut& po) {
   return radix_sort_impl<uint64_t, false>(keys_a, keys_b, nullptr, nullptr, n, end_bit, scratch, sel, s, n_dev,
-                                          nullptr, err, begin_bit, true, &po);
+                                          nullptr, err, begin_bit, &po);
 }
 
-int64_t radix_pair_sort_launches(int64_t n, int end_bit, int begin_bit) {
-  if (n <= 1 || end_bit <= begin_bit) return 0;
-  return (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;  // one kernel per pass
-}
 
 }  // namespace dqo
