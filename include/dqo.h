@@ -479,7 +479,10 @@ DQO_API dqo_status dqo_mlp_forward(dqo_ctx* ctx, const void* state, int64_t n, c
  * BF16 (its first n columns are this batch, XT[f][q] = X[q][f]); labels [n][9] fp32;
  * loss_w: 9 host floats.  grads (device, DQO_MLP_PARAMS) and loss (device, 1 float) are
  * OVERWRITTEN.  Backward precision: dL/dy rounded to BF16, hidden-layer gradients rounded
- * to BF16 after the ReLU derivative (the activation > 0).
+ * to BF16 after the ReLU derivative (the activation > 0).  One fused launch computes each
+ * 128-sample block's gradient (every product of the step on tensor cores, intermediates
+ * in shared memory); the blocks' gradients are summed in block order, so the result is
+ * the same on every run.
  * Errors: DQO_EINVAL, DQO_ECUDA (a tensor-core wait that ran out is reported by
  * dqo_mlp_check). */
 DQO_API dqo_status dqo_mlp_gradients(dqo_ctx* ctx, void* state, int64_t n, const uint16_t* X, const uint16_t* XT,

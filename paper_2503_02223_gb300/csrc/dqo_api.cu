@@ -1138,7 +1138,8 @@ dqo_status mlp_work(dqo_ctx* c, int64_t n, MlpWork* wk) {
   // the layout follows the largest batch seen, so the error flag keeps its place
   const int64_t nn = std::max((n + 127) / 128 * 128, c->mlp_n);
   const size_t big = align_up((size_t)nn * kMlpHidden * 2), small = align_up((size_t)nn * kMlpOutPad * 2);
-  const size_t bytes = 8 * big + 2 * small + kAlign;
+  const size_t part = align_up((size_t)(nn / 128) * kMlpParams * sizeof(float));
+  const size_t bytes = 8 * big + 2 * small + kAlign + part;
   const bool grow = nn > c->mlp_n;
   DQO_CUDA(c, ensure(c->mlp_work, bytes));
   unsigned char* b = as<unsigned char>(c->mlp_work);
@@ -1147,6 +1148,7 @@ dqo_status mlp_work(dqo_ctx* c, int64_t n, MlpWork* wk) {
   wk->dy = reinterpret_cast<__nv_bfloat16*>(b + 8 * big);
   wk->dyt = reinterpret_cast<__nv_bfloat16*>(b + 8 * big + small);
   wk->err = reinterpret_cast<int*>(b + 8 * big + 2 * small);
+  wk->gpart = reinterpret_cast<float*>(b + 8 * big + 2 * small + kAlign);
   if (grow) DQO_CUDA(c, cudaMemset(wk->err, 0, sizeof(int)));
   c->mlp_n = nn;
   return DQO_OK;
@@ -1218,12 +1220,10 @@ dqo_status dqo_mlp_gradients(dqo_ctx* c, void* state, int64_t n, const uint16_t*
   if ((st = mlp_work(c, n, &wk)) != DQO_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
   const MlpState ms = state_view(state);
-  DQO_CUDA(c, cudaMemsetAsync(ms.grad, 0, sizeof(float) * kMlpParams, s));
   DQO_CUDA(c, cudaMemsetAsync(loss, 0, sizeof(float), s));
-  DQO_CUDA(c, launch_mlp_backward_fused(ms, wk.err, n, X, XT, ldxt, labels, loss_w, loss, nullptr, s));
-  DQO_CUDA(c, cudaMemcpyAsync(grads, ms.grad, sizeof(float) * kMlpParams, cudaMemcpyDeviceToDevice, s));
-  DQO_CUDA(c, cudaMemsetAsync(ms.grad, 0, sizeof(float) * kMlpParams, s));
-  c->launches += 1;
+  DQO_CUDA(c, launch_mlp_backward_fused(ms, wk.err, wk.gpart, n, X, XT, ldxt, labels, loss_w, loss, nullptr, s));
+  DQO_CUDA(c, launch_mlp_sum_partials(wk.gpart, (int)(n / 128), grads, s));
+  c->launches += 2;
   return DQO_OK;
 }
 
@@ -1243,8 +1243,8 @@ dqo_status dqo_mlp_train_step(dqo_ctx* c, void* state, const dqo_mlp_hparams* hp
   const MlpState ms = state_view(state);
   float* lp = loss;
   if (lp) DQO_CUDA(c, cudaMemsetAsync(lp, 0, sizeof(float), s));
-  DQO_CUDA(c, launch_mlp_backward_fused(ms, wk.err, n, X, XT, ldxt, labels, hp->loss_w, lp, ms.step, s));
-  DQO_CUDA(c, launch_mlp_adam(ms, *hp, s));
+  DQO_CUDA(c, launch_mlp_backward_fused(ms, wk.err, wk.gpart, n, X, XT, ldxt, labels, hp->loss_w, lp, ms.step, s));
+  DQO_CUDA(c, launch_mlp_adam(ms, *hp, wk.gpart, (int)(n / 128), s));
   c->launches += 2;
   return DQO_OK;
 }

@@ -383,6 +383,7 @@ struct MlpWork {
   __nv_bfloat16 *h1, *h1t, *h2, *h2t, *dz1, *dz1t, *dz2, *dz2t;  // [n][128] and [128][n]
   __nv_bfloat16 *dy, *dyt;                                     // [n][16] and [16][n]
   int* err;
+  float* gpart;  // [n / 128][kMlpParams]: the fused step's per-CTA gradients
 };
 
 __device__ __forceinline__ void write_bf16_copies(const MlpState& st, int i, float p) {
@@ -408,14 +409,21 @@ cudaError_t launch_mlp_features(int nq, int nv, const float* P, const int32_t* q
                                 int npairs, const float* obs, const int32_t* counts, float inv_scale, uint16_t* X,
                                 uint16_t* XT, int64_t ldt, cudaStream_t s);
 cudaError_t launch_mlp_set(const MlpState& st, const float* params, cudaStream_t s);
-cudaError_t launch_mlp_adam(const MlpState& st, const dqo_mlp_hparams& hp, cudaStream_t s);
+// Adam on st.grad plus the fused step's partial gradients (gpart, nb CTAs; may be NULL / 0).
+cudaError_t launch_mlp_adam(const MlpState& st, const dqo_mlp_hparams& hp, const float* gpart, int nb,
+                            cudaStream_t s);
 cudaError_t launch_mlp_forward(const MlpState& st, const MlpWork& wk, int64_t n, const uint16_t* X, float* y,
                                cudaStream_t s);
 // Loss and gradients of a batch (n % 128 == 0) in one launch: the eight products of a step
 // fused per 128-sample CTA with the intermediates in shared memory.
-cudaError_t launch_mlp_backward_fused(const MlpState& st, int* err, int64_t n, const uint16_t* X, const uint16_t* XT,
-                                      int64_t ldxt, const float* labels, const float* loss_w, float* loss,
-                                      int* step_inc, cudaStream_t s);
+// Each CTA writes its gradient (all kMlpParams entries) to gpart[blockIdx][...]; the sum
+// over the n / 128 CTAs is taken by launch_mlp_adam or launch_mlp_sum_partials, in block
+// order (deterministic).
+cudaError_t launch_mlp_backward_fused(const MlpState& st, int* err, float* gpart, int64_t n, const uint16_t* X,
+                                      const uint16_t* XT, int64_t ldxt, const float* labels, const float* loss_w,
+                                      float* loss, int* step_inc, cudaStream_t s);
+// out[i] = sum over the nb CTAs of gpart[b][i].
+cudaError_t launch_mlp_sum_partials(const float* gpart, int nb, float* out, cudaStream_t s);
 cudaError_t launch_mlp_backward(const MlpState& st, const MlpWork& wk, int64_t n, const uint16_t* X,
                                 const uint16_t* XT, int64_t ldxt, const float* labels, const float* loss_w,
                                 float* loss, int* step_inc, cudaStream_t s);

@@ -360,6 +360,7 @@ struct FusedArgs {
   float* loss;              // += sum of the batch's weighted squared errors / n
   int* step_inc;            // block 0 adds 1 (the optimiser's step count); may be NULL
   int* err;                 // set to 1 if a tensor-core wait timed out
+  float* gpart;             // [gridDim.x][kMlpParams]: this CTA's gradient
 };
 
 // Thread m stores its 16 values of columns [c, c + 16) of row m into a K-major 128-row tile.
@@ -403,7 +404,7 @@ __device__ __forceinline__ void bias_grad(const unsigned char* tileT, int rowsT,
   float s = 0.f;
   for (int k = 0; k < kTileM; ++k)
     s += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(tileT + tile_offset(t, k, rowsT)));
-  atomicAdd(db + t, s);
+  db[t] = s;
 }
 
 __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_train_fused(FusedArgs a) {
@@ -425,6 +426,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_train_fused(FusedArgs 
   unsigned char* s2 = s1 + kSmall;         // dY^T [16][128]
   unsigned char* s3 = s2 + kSmall;         // W3^T [128][16]
   const MlpState& st = a.st;
+  float* const gp = a.gpart + (int64_t)blockIdx.x * kMlpParams;   // this CTA's gradient
   if (a.step_inc && t == 0 && blockIdx.x == 0) atomicAdd(a.step_inc, 1);
   if (w == 0) {
     tmem_alloc(smem_u32(&tslot), kFusedCols);
@@ -535,8 +537,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_train_fused(FusedArgs 
     float v[16];
     tmem_ld16(tA, v);
 #pragma unroll
-    for (int j = 0; j < kMlpOut; ++j) atomicAdd(st.grad + kMlpW3 + j * kTileM + t, v[j]);
-    bias_grad(s2, kMlpOutPad, kMlpOutPad, st.grad + kMlpB3);
+    for (int j = 0; j < kMlpOutPad; ++j) gp[kMlpW3 + j * kTileM + t] = j < kMlpOut ? v[j] : 0.f;
+    bias_grad(s2, kMlpOutPad, kMlpOutPad, gp + kMlpB3);
     tc_fence_before();
     __syncthreads();
     load_tile(sB, st.w2tb, kMlpHidden, 128, 128, 128);  // H2 is no longer needed
@@ -567,9 +569,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_train_fused(FusedArgs 
       float v[16];
       tmem_ld16(tA + (uint32_t)c, v);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) atomicAdd(st.grad + kMlpW2 + (c + j) * kTileM + t, v[j]);
+      for (int j = 0; j < 16; ++j) gp[kMlpW2 + (c + j) * kTileM + t] = v[j];
     }
-    bias_grad(sC, kTileM, kMlpHidden, st.grad + kMlpB2);
+    bias_grad(sC, kTileM, kMlpHidden, gp + kMlpB2);
     tc_fence_before();
     __syncthreads();
     load_tile(sB, a.XT + m0, a.ldxt, 128, 128, 128);   // W2^T is no longer needed
@@ -584,9 +586,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_train_fused(FusedArgs 
       float v[16];
       tmem_ld16(tB + (uint32_t)c, v);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) atomicAdd(st.grad + kMlpW1 + (c + j) * kTileM + t, v[j]);
+      for (int j = 0; j < 16; ++j) gp[kMlpW1 + (c + j) * kTileM + t] = v[j];
     }
-    bias_grad(sE, kTileM, kMlpHidden, st.grad + kMlpB1);
+    bias_grad(sE, kTileM, kMlpHidden, gp + kMlpB1);
   }
   if (!ok && t == 0 && a.err) atomicExch(a.err, 1);
   tc_fence_before();
@@ -679,13 +681,14 @@ __global__ void k_mlp_features(int nq, int nv, const float* __restrict__ Pm, con
 // One thread per parameter: Adam (bias-corrected, step count from the state, learning rate
 // on a cosine schedule from lr to lr_final over total_steps), gradient reset to zero, and
 // the BF16 operand copies of the weights (W and, for W2 and W3, W^T) rewritten.
-__global__ void k_mlp_adam(MlpState st, dqo_mlp_hparams hp) {
+__global__ void k_mlp_adam(MlpState st, dqo_mlp_hparams hp, const float* __restrict__ gpart, int nb) {
   pdl_wait();
   pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kMlpParams) return;
   const int step = *st.step;
-  const float g = st.grad[i];
+  float g = st.grad[i];
+  for (int b = 0; b < nb; ++b) g += gpart[(int64_t)b * kMlpParams + i];   // in block order
   st.grad[i] = 0.f;
   const float m = hp.beta1 * st.m1[i] + (1.f - hp.beta1) * g;
   const float v = hp.beta2 * st.m2[i] + (1.f - hp.beta2) * g * g;
@@ -698,6 +701,17 @@ __global__ void k_mlp_adam(MlpState st, dqo_mlp_hparams hp) {
   const float p = st.param[i] - lr * mh / (sqrtf(vh) + hp.eps);
   st.param[i] = p;
   write_bf16_copies(st, i, p);
+}
+
+// out[i] = sum over the fused step's CTAs of their gradient entry i, in block order.
+__global__ void k_mlp_sum_partials(const float* __restrict__ gpart, int nb, float* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kMlpParams) return;
+  float g = 0.f;
+  for (int b = 0; b < nb; ++b) g += gpart[(int64_t)b * kMlpParams + i];
+  out[i] = g;
 }
 
 // Parameters -> state: master copy, BF16 copies, Adam moments and step reset.
@@ -786,8 +800,13 @@ cudaError_t launch_mlp_set(const MlpState& st, const float* params, cudaStream_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_adam(const MlpState& st, const dqo_mlp_hparams& hp, cudaStream_t s) {
-  return launch_dep(k_mlp_adam, dim3((kMlpParams + 255) / 256), dim3(256), s, st, hp);
+cudaError_t launch_mlp_adam(const MlpState& st, const dqo_mlp_hparams& hp, const float* gpart, int nb,
+                            cudaStream_t s) {
+  return launch_dep(k_mlp_adam, dim3((kMlpParams + 255) / 256), dim3(256), s, st, hp, gpart, nb);
+}
+
+cudaError_t launch_mlp_sum_partials(const float* gpart, int nb, float* out, cudaStream_t s) {
+  return launch_dep(k_mlp_sum_partials, dim3((kMlpParams + 255) / 256), dim3(256), s, gpart, nb, out);
 }
 
 // Inference: X [n][128] -> y [n][9]; three launches.
@@ -814,14 +833,15 @@ cudaError_t launch_mlp_forward(const MlpState& st, const MlpWork& wk, int64_t n,
 }
 
 // Loss and gradients of a batch (n % 128 == 0) in one launch of n / 128 CTAs (the eight
-// products of launch_mlp_backward fused, intermediates in shared memory).  Gradients are
-// ADDED to st.grad; the loss is ADDED to *loss.
-cudaError_t launch_mlp_backward_fused(const MlpState& st, int* err, int64_t n, const uint16_t* X_,
+// products of launch_mlp_backward fused, intermediates in shared memory).  Each CTA's
+// gradient goes to gpart[blockIdx]; the loss is ADDED to *loss.
+cudaError_t launch_mlp_backward_fused(const MlpState& st, int* err, float* gpart, int64_t n, const uint16_t* X_,
                                       const uint16_t* XT_, int64_t ldxt, const float* labels, const float* loss_w,
                                       float* loss, int* step_inc, cudaStream_t s) {
-  if (n <= 0 || n % kTileM) return cudaErrorInvalidValue;
+  if (n <= 0 || n % kTileM || !gpart) return cudaErrorInvalidValue;
   FusedArgs a{};
   a.st = st;
+  a.gpart = gpart;
   a.X = reinterpret_cast<const __nv_bfloat16*>(X_);
   a.XT = reinterpret_cast<const __nv_bfloat16*>(XT_);
   a.ldxt = ldxt;
