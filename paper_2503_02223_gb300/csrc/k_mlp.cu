@@ -162,6 +162,28 @@ __device__ __forceinline__ void load_tile(unsigned char* dst, const __nv_bfloat1
   }
 }
 
+// The same tile with asynchronous 16-byte copies (cp.async: no register round trip, every
+// piece in flight at once); rows at or past `valid_rows` are zero-filled.  The caller
+// commits the group and waits for it (cp_async_wait_all) before the tile is read.
+__device__ __forceinline__ void load_tile_async(unsigned char* dst, const __nv_bfloat16* __restrict__ src,
+                                                int64_t ld, int rows, int valid_rows, int K) {
+  const int per_row = K >> 3;
+  const int total = rows * per_row;
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    const int r = i / per_row, kc = i - r * per_row;
+    const bool ok = r < valid_rows;
+    const __nv_bfloat16* g = src + (int64_t)(ok ? r : 0) * ld + kc * 8;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst + tile_offset(r, kc * 8, rows))),
+                 "l"(g), "r"(ok ? 16 : 0)
+                 : "memory");
+  }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// Waits until at most n of this thread's committed groups are still in flight.
+template <int n>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(n) : "memory"); }
+
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
@@ -340,13 +362,15 @@ __global__ void __launch_bounds__(kGemmThreads) k_mlp_gemm(GemmArgs a) {
 // memory: the same operands, the same BF16 rounding points and the same per-CTA weight-
 // gradient tiles as the eight launches of launch_mlp_backward, which leave the
 // activations in global memory instead.  A step is one launch of n / 128 CTAs + Adam.
-// Shared memory: five 32 KB slots for 128 x 128 tiles, reused as the step goes on, and
-// four 4 KB slots for the 16-wide tiles; tensor memory: 256 columns, the products
-// alternating between the two halves.
+// Shared memory: six 32 KB slots for 128 x 128 tiles, reused as the step goes on (the
+// operands of a later product are copied asynchronously into a free slot while the
+// current one runs), four 4 KB slots for the 16-wide tiles and the biases; tensor memory:
+// 256 columns, the products alternating between the two halves.
 constexpr int kFusedThreads = 128;
 constexpr uint32_t kSlot = kTileM * 128 * 2;      // 32 KB
 constexpr uint32_t kSmall = kTileM * kMlpOutPad * 2;  // 4 KB
-constexpr int kFusedSmem = 5 * kSlot + 4 * kSmall + 1024;
+constexpr int kBiasFloats = 2 * kMlpHidden + kMlpOutPad;
+constexpr int kFusedSmem = 6 * kSlot + 4 * kSmall + kBiasFloats * 4 + 1024;
 constexpr uint32_t kFusedCols = 256;
 
 struct FusedArgs {
@@ -416,15 +440,17 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_train_fused(FusedArgs 
   const int t = threadIdx.x, w = t >> 5;
   const int64_t m0 = (int64_t)blockIdx.x * kTileM;
   const int m = (int)m0 + t;  // this thread's sample (the batch is a multiple of 128 rows)
-  unsigned char* sA = sm;                  // X, then W2, then G2
-  unsigned char* sB = sm + kSlot;          // W1, then H2, then W2T, then XT
+  unsigned char* sA = sm;                  // X, then W2T
+  unsigned char* sB = sm + kSlot;          // W1, then H2, then XT
   unsigned char* sC = sm + 2 * kSlot;      // H1, then G2T
   unsigned char* sD = sm + 3 * kSlot;      // H1T
   unsigned char* sE = sm + 4 * kSlot;      // H2T, then G1T
-  unsigned char* s0 = sm + 5 * kSlot;      // W3 [16][128]
+  unsigned char* sF = sm + 5 * kSlot;      // W2, then G2
+  unsigned char* s0 = sm + 6 * kSlot;      // W3 [16][128]
   unsigned char* s1 = s0 + kSmall;         // dY [128][16]
   unsigned char* s2 = s1 + kSmall;         // dY^T [16][128]
   unsigned char* s3 = s2 + kSmall;         // W3^T [128][16]
+  float* sbias = reinterpret_cast<float*>(s3 + kSmall);   // b1, b2, b3
   const MlpState& st = a.st;
   float* const gp = a.gpart + (int64_t)blockIdx.x * kMlpParams;   // this CTA's gradient
   if (a.step_inc && t == 0 && blockIdx.x == 0) atomicAdd(a.step_inc, 1);
@@ -434,10 +460,19 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_train_fused(FusedArgs 
   }
   if (t == 0) mbar_init(smem_u32(&mbar), 1);
   const uint32_t bar = smem_u32(&mbar);
-  load_tile(sA, a.X + m0 * kMlpIn, kMlpIn, kTileM, kTileM, 128);
-  load_tile(sB, st.w1b, kMlpHidden, 128, 128, 128);
-  load_tile(s0, st.w3b, kMlpHidden, kMlpOutPad, kMlpOutPad, 128);
-  load_tile(s3, st.w3tb, kMlpOutPad, 128, 128, kMlpOutPad);
+  // the first product's operands, then W2 (in flight while the first product runs)
+  load_tile_async(sA, a.X + m0 * kMlpIn, kMlpIn, kTileM, kTileM, 128);
+  load_tile_async(sB, st.w1b, kMlpHidden, 128, 128, 128);
+  load_tile_async(s0, st.w3b, kMlpHidden, kMlpOutPad, kMlpOutPad, 128);
+  load_tile_async(s3, st.w3tb, kMlpOutPad, 128, 128, kMlpOutPad);
+  cp_async_commit();
+  load_tile_async(sF, st.w2b, kMlpHidden, 128, 128, 128);
+  cp_async_commit();
+  for (int i = t; i < kBiasFloats; i += kFusedThreads)
+    sbias[i] = i < kMlpHidden ? st.param[kMlpB1 + i]
+                              : (i < 2 * kMlpHidden ? st.param[kMlpB2 + i - kMlpHidden]
+                                                    : st.param[kMlpB3 + i - 2 * kMlpHidden]);
+  cp_async_wait_group<1>();
   __syncthreads();
   const uint32_t t0 = tslot, lane_off = (uint32_t)(w * 32) << 16;
   const uint32_t tA = t0 + lane_off, tB = t0 + 128u + lane_off;  // this thread's TMEM lane, two halves
@@ -455,19 +490,20 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_train_fused(FusedArgs 
       __align__(16) __nv_bfloat16 h[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        h[j] = __float2bfloat16_rn(fmaxf(v[j] + st.param[kMlpB1 + c + j], 0.f));
+        h[j] = __float2bfloat16_rn(fmaxf(v[j] + sbias[c + j], 0.f));
         if (__bfloat162float(h[j]) > 0.f) mask1[(c + j) >> 5] |= 1u << ((c + j) & 31);
       }
       put_row16(sC, t, c, h);
       put_col16(sD, kTileM, t, c, h);
     }
-    tc_fence_before();
-    __syncthreads();
-    load_tile(sA, st.w2b, kMlpHidden, 128, 128, 128);   // X is no longer needed
+    // X is no longer needed: W2^T goes there while the next products run
+    load_tile_async(sA, st.w2tb, kMlpHidden, 128, 128, 128);
+    cp_async_commit();
   }
   // ---- H2 = relu(H1 W2^T + b2): rows into sB (W1 free), transposed into sE
   if (ok) {
-    ok = fused_mma(t0 + 128u, sC, sA, 128, 128, bar, ph);
+    cp_async_wait_group<1>();   // W2
+    ok = fused_mma(t0 + 128u, sC, sF, 128, 128, bar, ph);
     ph ^= 1u;
   }
   if (ok) {
@@ -477,7 +513,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_train_fused(FusedArgs 
       __align__(16) __nv_bfloat16 h[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        h[j] = __float2bfloat16_rn(fmaxf(v[j] + st.param[kMlpB2 + c + j], 0.f));
+        h[j] = __float2bfloat16_rn(fmaxf(v[j] + sbias[kMlpHidden + c + j], 0.f));
         if (__bfloat162float(h[j]) > 0.f) mask2[(c + j) >> 5] |= 1u << ((c + j) & 31);
       }
       put_row16(sB, t, c, h);
@@ -496,7 +532,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_train_fused(FusedArgs 
     __align__(16) __nv_bfloat16 d[16];
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
-      const float y = v[j] + st.param[kMlpB3 + j];
+      const float y = v[j] + sbias[2 * kMlpHidden + j];
       const float e = y - a.labels[(int64_t)m * 9 + j];
       l += a.w[j] * e * e;
       d[j] = __float2bfloat16_rn(2.f * a.w[j] * e * a.inv_batch);
@@ -511,12 +547,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_train_fused(FusedArgs 
       if ((t & 31) == 0) atomicAdd(a.loss, l);
     }
   }
-  // ---- G2 = (dY W3) * (H2 > 0): rows into sA (W2 free), transposed into sC (H1 free)
+  // ---- G2 = (dY W3) * (H2 > 0): rows into sF (W2 free), transposed into sC (H1 free)
   if (ok) {
     ok = fused_mma(t0 + 128u, s1, s3, 128, kMlpOutPad, bar, ph);
     ph ^= 1u;
   }
   if (ok) {
+    // H2 is no longer needed: X^T goes there while the next products run
+    load_tile_async(sB, a.XT + m0, a.ldxt, 128, 128, 128);
+    cp_async_commit();
     for (int c = 0; c < 128; c += 16) {
       float v[16];
       tmem_ld16(tB + (uint32_t)c, v);
@@ -524,7 +563,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_train_fused(FusedArgs 
 #pragma unroll
       for (int j = 0; j < 16; ++j)
         h[j] = __float2bfloat16_rn(((mask2[(c + j) >> 5] >> ((c + j) & 31)) & 1u) ? v[j] : 0.f);
-      put_row16(sA, t, c, h);
+      put_row16(sF, t, c, h);
       put_col16(sC, kTileM, t, c, h);
     }
   }
@@ -539,13 +578,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_train_fused(FusedArgs 
 #pragma unroll
     for (int j = 0; j < kMlpOutPad; ++j) gp[kMlpW3 + j * kTileM + t] = j < kMlpOut ? v[j] : 0.f;
     bias_grad(s2, kMlpOutPad, kMlpOutPad, gp + kMlpB3);
-    tc_fence_before();
-    __syncthreads();
-    load_tile(sB, st.w2tb, kMlpHidden, 128, 128, 128);  // H2 is no longer needed
   }
   // ---- G1 = (G2 W2) * (H1 > 0): transposed into sE (H2^T free)
   if (ok) {
-    ok = fused_mma(t0 + 128u, sA, sB, 128, 128, bar, ph);
+    cp_async_wait_group<1>();   // W2^T (X^T may still be in flight)
+    ok = fused_mma(t0 + 128u, sF, sA, 128, 128, bar, ph);
     ph ^= 1u;
   }
   if (ok) {
@@ -572,12 +609,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_train_fused(FusedArgs 
       for (int j = 0; j < 16; ++j) gp[kMlpW2 + (c + j) * kTileM + t] = v[j];
     }
     bias_grad(sC, kTileM, kMlpHidden, gp + kMlpB2);
-    tc_fence_before();
-    __syncthreads();
-    load_tile(sB, a.XT + m0, a.ldxt, 128, 128, 128);   // W2^T is no longer needed
   }
   // ---- dW1 += G1^T X (A = X^T, B = G1^T), db1
   if (ok) {
+    cp_async_wait_all();        // X^T
     ok = fused_mma(t0 + 128u, sB, sE, 128, 128, bar, ph);
     ph ^= 1u;
   }
@@ -591,6 +626,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_train_fused(FusedArgs 
     bias_grad(sE, kTileM, kMlpHidden, gp + kMlpB1);
   }
   if (!ok && t == 0 && a.err) atomicExch(a.err, 1);
+  cp_async_wait_all();          // no copy may still target shared memory when the CTA ends
   tc_fence_before();
   __syncthreads();
   if (w == 0) {

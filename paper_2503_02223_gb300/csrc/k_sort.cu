@@ -90,32 +90,46 @@ __global__ void __launch_bounds__(kThreads) k_scan_lookback(const uint32_t* __re
   }
   uint32_t tot;
   uint32_t run = block_exclusive_scan<uint32_t>(sum, tot);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
+    // warp 0 looks back 32 predecessors at a time: lane j reads tile p - j; the words up to
+    // the nearest unpublished one are added, and the walk ends at the nearest inclusive one
+    const int lane = threadIdx.x;
     volatile uint64_t* st = status;
-    st[tile] = (tile == 0 ? kScanInc : kScanAgg) | (uint64_t)tot;
+    if (lane == 0) st[tile] = (tile == 0 ? kScanInc : kScanAgg) | (uint64_t)tot;
     uint64_t excl = 0;
     if (tile > 0) {
       int64_t p = (int64_t)tile - 1;
       const uint64_t t0 = scan_ns();
       uint32_t it = 0;
-      while (p >= 0) {
-        const uint64_t w = st[p];
+      for (;;) {
+        const uint64_t w = p - lane >= 0 ? (uint64_t)st[p - lane] : (uint64_t)kScanInc;   // before tile 0: an empty prefix
         const uint64_t f = w & ~kScanMask;
-        if (f == 0) {
-          if ((++it & 63u) == 0u && scan_ns() - t0 > 1000000000ull) {
-            atomicExch(err, 1u);
+        const uint32_t unready = __ballot_sync(0xFFFFFFFFu, f == 0);
+        const uint32_t inc = __ballot_sync(0xFFFFFFFFu, f == kScanInc);
+        const uint32_t stop = unready | inc;
+        const int first = stop ? __ffs(stop) - 1 : 32;
+        const bool finish = first < 32 && ((inc >> first) & 1u);
+        const int take = finish ? first + 1 : first;
+        uint64_t v = lane < take ? (w & kScanMask) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        excl += v;
+        if (finish) break;
+        p -= take;
+        if (take == 0 && (++it & 63u) == 0u) {
+          const bool late = __shfl_sync(0xFFFFFFFFu, lane == 0 && scan_ns() - t0 > 1000000000ull, 0);
+          if (late) {
+            if (lane == 0) atomicExch(err, 1u);
             break;
           }
-          continue;
         }
-        excl += w & kScanMask;
-        if (f == kScanInc) break;
-        --p;
       }
-      st[tile] = kScanInc | (excl + tot);
+      if (lane == 0) st[tile] = kScanInc | (excl + tot);
     }
-    s_prefix = excl;
-    if (total && base + kSortTile >= n) *total = excl + tot;
+    if (lane == 0) {
+      s_prefix = excl;
+      if (total && base + kSortTile >= n) *total = excl + tot;
+    }
   }
   __syncthreads();
   run += (uint32_t)s_prefix;
@@ -153,6 +167,7 @@ __device__ __forceinline__ int64_t live_count(int64_t n, const uint64_t* n_dev) 
 // second and raises an error flag instead of hanging.
 
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kCountMask = (1u << 30) - 1;
+constexpr int kLookBatch = 8;   // predecessors a digit's look-back reads per round trip
 
 template <typename K, int IPT>
 __global__ void __launch_bounds__(kThreads) k_onesweep_hist(const K* __restrict__ keys, int64_t n_cap,
@@ -258,22 +273,37 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep_pass(const K* __restri
   const uint32_t gex = block_exclusive_scan<uint32_t>(ghist[t], gtot);
   uint32_t excl = 0;
   if (tile > 0) {
+    // kLookBatch predecessors per round trip (independent loads in flight together): the
+    // words up to the nearest unpublished one are added, the walk ends at the nearest
+    // inclusive one
     int64_t p = (int64_t)tile - 1;
     const uint64_t t0 = global_ns();
     uint32_t it = 0;
-    while (p >= 0) {
-      const uint32_t w = st[p * kRadixBins + t];
-      const uint32_t f = w & ~kCountMask;
-      if (f == 0u) {
-        if ((++it & 63u) == 0u && global_ns() - t0 > 1000000000ull) {
-          atomicExch(err, 1u);
-          break;
+    for (;;) {
+      uint32_t w[kLookBatch];
+#pragma unroll
+      for (int k = 0; k < kLookBatch; ++k)
+        w[k] = p - k >= 0 ? (uint32_t)st[(p - k) * kRadixBins + t] : (uint32_t)kFlagInc;   // before tile 0: empty
+      int used = 0;
+      bool done = false, stalled = false;
+#pragma unroll
+      for (int k = 0; k < kLookBatch; ++k) {
+        if (done || stalled) continue;
+        const uint32_t f = w[k] & ~kCountMask;
+        if (f == 0u) {
+          stalled = true;
+          continue;
         }
-        continue;
+        excl += w[k] & kCountMask;
+        ++used;
+        done = f == kFlagInc;
       }
-      excl += w & kCountMask;
-      if (f == kFlagInc) break;
-      --p;
+      if (done) break;
+      p -= used;
+      if (used == 0 && (++it & 63u) == 0u && global_ns() - t0 > 1000000000ull) {
+        atomicExch(err, 1u);
+        break;
+      }
     }
     st[(int64_t)tile * kRadixBins + t] = kFlagInc | (excl + total);
   }
