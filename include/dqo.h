@@ -475,19 +475,18 @@ DQO_API dqo_status dqo_mlp_forward(dqo_ctx* ctx, const void* state, int64_t n, c
                                    dqo_stream stream);
 
 /* Loss L = (1/n) sum_rows sum_j loss_w[j] (y_j - labels_j)^2 of a batch and its gradient
- * w.r.t. the parameter vector.  n > 0, n % 128 == 0.  X [n][128] BF16; XT [128][ldxt]
- * BF16 (its first n columns are this batch, XT[f][q] = X[q][f]); labels [n][9] fp32;
- * loss_w: 9 host floats.  grads (device, DQO_MLP_PARAMS) and loss (device, 1 float) are
- * OVERWRITTEN.  Backward precision: dL/dy rounded to BF16, hidden-layer gradients rounded
- * to BF16 after the ReLU derivative (the activation > 0).  One fused launch computes each
- * 128-sample block's gradient (every product of the step on tensor cores, intermediates
- * in shared memory); the blocks' gradients are summed in block order, so the result is
- * the same on every run.
+ * w.r.t. the parameter vector.  n > 0, n % 128 == 0.  X [n][128] BF16 (16-byte aligned);
+ * labels [n][9] fp32 (16-byte aligned); loss_w: 9 host floats.  grads (device, DQO_MLP_PARAMS) and loss
+ * (device, 1 float) are OVERWRITTEN.  Backward precision: dL/dy rounded to BF16,
+ * hidden-layer gradients rounded to BF16 after the ReLU derivative (the activation > 0);
+ * weight and bias gradients accumulate in FP32.  One fused launch computes each 128-sample
+ * block's gradient (every product of the step on tensor cores, intermediates in shared
+ * memory, transposed operands read in place); the blocks' gradients are summed in block
+ * order, so the result is the same on every run.
  * Errors: DQO_EINVAL, DQO_ECUDA (a tensor-core wait that ran out is reported by
  * dqo_mlp_check). */
-DQO_API dqo_status dqo_mlp_gradients(dqo_ctx* ctx, void* state, int64_t n, const uint16_t* X, const uint16_t* XT,
-                                     int64_t ldxt, const float* labels, const float* loss_w, float* grads,
-                                     float* loss, dqo_stream stream);
+DQO_API dqo_status dqo_mlp_gradients(dqo_ctx* ctx, void* state, int64_t n, const uint16_t* X, const float* labels,
+                                     const float* loss_w, float* grads, float* loss, dqo_stream stream);
 
 /* One Adam step on a batch (as dqo_mlp_gradients, then the update; the learning rate
  * follows hp's cosine schedule at the state's step count).  loss (device, 1 float) is
@@ -495,8 +494,7 @@ DQO_API dqo_status dqo_mlp_gradients(dqo_ctx* ctx, void* state, int64_t n, const
  * the context has seen a batch of this size, so a sequence of steps can be captured in a
  * CUDA graph after one call.  Errors: as dqo_mlp_gradients. */
 DQO_API dqo_status dqo_mlp_train_step(dqo_ctx* ctx, void* state, const dqo_mlp_hparams* hp, int64_t n,
-                                      const uint16_t* X, const uint16_t* XT, int64_t ldxt, const float* labels,
-                                      float* loss, dqo_stream stream);
+                                      const uint16_t* X, const float* labels, float* loss, dqo_stream stream);
 
 /* Error flag of the last tensor-core kernels on this context, read synchronously and
  * cleared: *timed_out = 1 and DQO_ETIMEOUT if a tensor-core completion wait ran out (the

@@ -1106,7 +1106,7 @@ constexpr size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign;
 constexpr size_t kParamBytes = align_up(sizeof(float) * kMlpParams);
 constexpr size_t kW128Bytes = align_up(2 * kMlpHidden * kMlpHidden);
 constexpr size_t kW3Bytes = align_up(2 * kMlpOutPad * kMlpHidden);
-constexpr size_t kStateBytes = 4 * kParamBytes + 3 * kW128Bytes + 2 * kW3Bytes + kAlign;
+constexpr size_t kStateBytes = 4 * kParamBytes + 2 * kW128Bytes + kW3Bytes + kAlign;
 
 MlpState state_view(const void* state) {
   unsigned char* b = static_cast<unsigned char*>(const_cast<void*>(state));
@@ -1118,11 +1118,9 @@ MlpState state_view(const void* state) {
   b += 4 * kParamBytes;
   st.w1b = reinterpret_cast<__nv_bfloat16*>(b);
   st.w2b = reinterpret_cast<__nv_bfloat16*>(b + kW128Bytes);
-  st.w2tb = reinterpret_cast<__nv_bfloat16*>(b + 2 * kW128Bytes);
-  b += 3 * kW128Bytes;
+  b += 2 * kW128Bytes;
   st.w3b = reinterpret_cast<__nv_bfloat16*>(b);
-  st.w3tb = reinterpret_cast<__nv_bfloat16*>(b + kW3Bytes);
-  st.step = reinterpret_cast<int*>(b + 2 * kW3Bytes);
+  st.step = reinterpret_cast<int*>(b + kW3Bytes);
   return st;
 }
 
@@ -1137,26 +1135,24 @@ dqo_status mlp_work(dqo_ctx* c, int64_t n, MlpWork* wk) {
   }
   // the layout follows the largest batch seen, so the error flag keeps its place
   const int64_t nn = std::max((n + 127) / 128 * 128, c->mlp_n);
-  const size_t big = align_up((size_t)nn * kMlpHidden * 2), small = align_up((size_t)nn * kMlpOutPad * 2);
+  const size_t big = align_up((size_t)nn * kMlpHidden * 2);
   const size_t part = align_up((size_t)(nn / 128) * kMlpParams * sizeof(float));
-  const size_t bytes = 8 * big + 2 * small + kAlign + part;
+  const size_t bytes = 2 * big + kAlign + part;
   const bool grow = nn > c->mlp_n;
   DQO_CUDA(c, ensure(c->mlp_work, bytes));
   unsigned char* b = as<unsigned char>(c->mlp_work);
-  __nv_bfloat16** bigs[8] = {&wk->h1, &wk->h1t, &wk->h2, &wk->h2t, &wk->dz1, &wk->dz1t, &wk->dz2, &wk->dz2t};
-  for (int i = 0; i < 8; ++i) *bigs[i] = reinterpret_cast<__nv_bfloat16*>(b + i * big);
-  wk->dy = reinterpret_cast<__nv_bfloat16*>(b + 8 * big);
-  wk->dyt = reinterpret_cast<__nv_bfloat16*>(b + 8 * big + small);
-  wk->err = reinterpret_cast<int*>(b + 8 * big + 2 * small);
-  wk->gpart = reinterpret_cast<float*>(b + 8 * big + 2 * small + kAlign);
+  wk->h1 = reinterpret_cast<__nv_bfloat16*>(b);
+  wk->h2 = reinterpret_cast<__nv_bfloat16*>(b + big);
+  wk->err = reinterpret_cast<int*>(b + 2 * big);
+  wk->gpart = reinterpret_cast<float*>(b + 2 * big + kAlign);
   if (grow) DQO_CUDA(c, cudaMemset(wk->err, 0, sizeof(int)));
   c->mlp_n = nn;
   return DQO_OK;
 }
 
-dqo_status check_batch(int64_t n, const uint16_t* X, const uint16_t* XT, int64_t ldxt, const float* labels) {
+dqo_status check_batch(int64_t n, const uint16_t* X, const float* labels) {
   if (n <= 0 || n % 128 != 0 || n > (int64_t(1) << 30)) return DQO_EINVAL;
-  if (!X || !XT || !labels || ldxt < n || ldxt % 8 != 0 || !aligned16(X) || !aligned16(XT)) return DQO_EINVAL;
+  if (!X || !labels || !aligned16(X) || !aligned16(labels)) return DQO_EINVAL;
   return DQO_OK;
 }
 
@@ -1208,12 +1204,11 @@ dqo_status dqo_mlp_forward(dqo_ctx* c, const void* state, int64_t n, const uint1
   return DQO_OK;
 }
 
-dqo_status dqo_mlp_gradients(dqo_ctx* c, void* state, int64_t n, const uint16_t* X, const uint16_t* XT,
-                             int64_t ldxt, const float* labels, const float* loss_w, float* grads, float* loss,
-                             dqo_stream stream_) {
+dqo_status dqo_mlp_gradients(dqo_ctx* c, void* state, int64_t n, const uint16_t* X, const float* labels,
+                             const float* loss_w, float* grads, float* loss, dqo_stream stream_) {
   if (!c || !state || !loss_w || !grads || !loss || (reinterpret_cast<uintptr_t>(state) % kAlign) != 0)
     return DQO_EINVAL;
-  dqo_status st = check_batch(n, X, XT, ldxt, labels);
+  dqo_status st = check_batch(n, X, labels);
   if (st != DQO_OK) return st;
   DQO_CUDA(c, cudaSetDevice(c->device));
   MlpWork wk;
@@ -1221,20 +1216,19 @@ dqo_status dqo_mlp_gradients(dqo_ctx* c, void* state, int64_t n, const uint16_t*
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
   const MlpState ms = state_view(state);
   DQO_CUDA(c, cudaMemsetAsync(loss, 0, sizeof(float), s));
-  DQO_CUDA(c, launch_mlp_backward_fused(ms, wk.err, wk.gpart, n, X, XT, ldxt, labels, loss_w, loss, nullptr, s));
+  DQO_CUDA(c, launch_mlp_backward_fused(ms, wk.err, wk.gpart, n, X, labels, loss_w, loss, nullptr, s));
   DQO_CUDA(c, launch_mlp_sum_partials(wk.gpart, (int)(n / 128), grads, s));
   c->launches += 2;
   return DQO_OK;
 }
 
 dqo_status dqo_mlp_train_step(dqo_ctx* c, void* state, const dqo_mlp_hparams* hp, int64_t n, const uint16_t* X,
-                              const uint16_t* XT, int64_t ldxt, const float* labels, float* loss,
-                              dqo_stream stream_) {
+                              const float* labels, float* loss, dqo_stream stream_) {
   if (!c || !state || !hp || (reinterpret_cast<uintptr_t>(state) % kAlign) != 0) return DQO_EINVAL;
   if (!(hp->lr >= 0.f) || !(hp->lr_final >= 0.f) || !(hp->beta1 >= 0.f && hp->beta1 < 1.f) ||
       !(hp->beta2 >= 0.f && hp->beta2 < 1.f) || !(hp->eps > 0.f))
     return DQO_EINVAL;
-  dqo_status st = check_batch(n, X, XT, ldxt, labels);
+  dqo_status st = check_batch(n, X, labels);
   if (st != DQO_OK) return st;
   DQO_CUDA(c, cudaSetDevice(c->device));
   MlpWork wk;
@@ -1243,7 +1237,7 @@ dqo_status dqo_mlp_train_step(dqo_ctx* c, void* state, const dqo_mlp_hparams* hp
   const MlpState ms = state_view(state);
   float* lp = loss;
   if (lp) DQO_CUDA(c, cudaMemsetAsync(lp, 0, sizeof(float), s));
-  DQO_CUDA(c, launch_mlp_backward_fused(ms, wk.err, wk.gpart, n, X, XT, ldxt, labels, hp->loss_w, lp, ms.step, s));
+  DQO_CUDA(c, launch_mlp_backward_fused(ms, wk.err, wk.gpart, n, X, labels, hp->loss_w, lp, ms.step, s));
   DQO_CUDA(c, launch_mlp_adam(ms, *hp, wk.gpart, (int)(n / 128), s));
   c->launches += 2;
   return DQO_OK;

@@ -373,15 +373,14 @@ constexpr int kMlpW1 = 0, kMlpB1 = 16384, kMlpW2 = 16512, kMlpB2 = 32896, kMlpW3
 // Views into the caller-owned state buffer.
 struct MlpState {
   float *param, *grad, *m1, *m2;       // [kMlpParams] each
-  __nv_bfloat16 *w1b, *w2b, *w2tb;     // [128][128]: W1, W2, W2^T
-  __nv_bfloat16 *w3b, *w3tb;           // W3 [16][128], W3^T [128][16]
+  __nv_bfloat16 *w1b, *w2b;            // [128][128]: W1, W2
+  __nv_bfloat16* w3b;                  // W3 [16][128]
   int* step;                           // optimiser steps taken
 };
 
-// Activations and output gradients of one batch (context workspace).
+// Context workspace: the forward's activations and the training step's partial gradients.
 struct MlpWork {
-  __nv_bfloat16 *h1, *h1t, *h2, *h2t, *dz1, *dz1t, *dz2, *dz2t;  // [n][128] and [128][n]
-  __nv_bfloat16 *dy, *dyt;                                     // [n][16] and [16][n]
+  __nv_bfloat16 *h1, *h2;  // [n][128]
   int* err;
   float* gpart;  // [n / 128][kMlpParams]: the fused step's per-CTA gradients
 };
@@ -391,13 +390,9 @@ __device__ __forceinline__ void write_bf16_copies(const MlpState& st, int i, flo
   if (i < kMlpB1) {
     st.w1b[i] = b;
   } else if (i >= kMlpW2 && i < kMlpB2) {
-    const int k = i - kMlpW2;
-    st.w2b[k] = b;
-    st.w2tb[(k % kMlpHidden) * kMlpHidden + k / kMlpHidden] = b;
+    st.w2b[i - kMlpW2] = b;
   } else if (i >= kMlpW3 && i < kMlpB3) {
-    const int k = i - kMlpW3;
-    st.w3b[k] = b;
-    st.w3tb[(k % kMlpHidden) * kMlpOutPad + k / kMlpHidden] = b;
+    st.w3b[i - kMlpW3] = b;
   }
 }
 
@@ -420,12 +415,8 @@ cudaError_t launch_mlp_forward(const MlpState& st, const MlpWork& wk, int64_t n,
 // over the n / 128 CTAs is taken by launch_mlp_adam or launch_mlp_sum_partials, in block
 // order (deterministic).
 cudaError_t launch_mlp_backward_fused(const MlpState& st, int* err, float* gpart, int64_t n, const uint16_t* X,
-                                      const uint16_t* XT, int64_t ldxt, const float* labels, const float* loss_w,
-                                      float* loss, int* step_inc, cudaStream_t s);
+                                      const float* labels, const float* loss_w, float* loss, int* step_inc,
+                                      cudaStream_t s);
 // out[i] = sum over the nb CTAs of gpart[b][i].
 cudaError_t launch_mlp_sum_partials(const float* gpart, int nb, float* out, cudaStream_t s);
-cudaError_t launch_mlp_backward(const MlpState& st, const MlpWork& wk, int64_t n, const uint16_t* X,
-                                const uint16_t* XT, int64_t ldxt, const float* labels, const float* loss_w,
-                                float* loss, int* step_inc, cudaStream_t s);
-
 }  // namespace dqo

@@ -2,16 +2,12 @@
 // its Adam update.  Every product runs on the 5th-generation tensor cores: tcgen05.mma of
 // kind f16 with BF16 operands staged in shared memory and FP32 accumulators in tensor
 // memory, issued by one thread per CTA; the epilogues (bias, ReLU, the regression loss,
-// the ReLU derivative, the weight-gradient scatter) read the accumulators back with
-// tcgen05.ld and are fused into the same kernel.
+// the ReLU derivative, the gradient stores) read the accumulators back with tcgen05.ld.
 //
-// One kernel shape covers every product of a training step: a CTA computes a 128-row tile
-// D[128][N] = A[128][K] . B[N][K]^T (N = 16 or 128, K <= 128 per CTA) with both operands
-// K-contiguous in global memory.  Forward layers tile the batch (A = activations,
-// B = weights [out][in]); input gradients use the transposed weights; weight gradients
-// take the batch as the K dimension (A = activations transposed, B = output gradients
-// transposed, one CTA per 128 samples) and add their tile into the FP32 gradient with
-// coalesced atomics.
+// Inference (k_mlp_gemm, one launch per layer): a CTA computes a 128-row tile
+// D[128][N] = A[128][K] . B[N][K]^T (N = 16 or 128, K = 128) with both operands
+// K-contiguous in global memory (A = activations, B = weights [out][in]).  Training
+// (k_mlp_train_fused): the whole step of 128 samples per CTA in one kernel, then Adam.
 #include <cuda_bf16.h>
 
 #include "dqo_internal.cuh"
@@ -109,6 +105,28 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 64 consecutive FP32 accumulator columns of this thread's TMEM lane, one load and one wait.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
+  uint32_t r[64];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,"
+      "%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+        "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+        "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+        "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+        "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // ----------------------------------------------------------------------------- operand layout
 
 // Operand tiles in shared memory use the canonical K-major layout without swizzle.  A tile
@@ -162,22 +180,6 @@ __device__ __forceinline__ void load_tile(unsigned char* dst, const __nv_bfloat1
   }
 }
 
-// The same tile with asynchronous 16-byte copies (cp.async: no register round trip, every
-// piece in flight at once); rows at or past `valid_rows` are zero-filled.  The caller
-// commits the group and waits for it (cp_async_wait_all) before the tile is read.
-__device__ __forceinline__ void load_tile_async(unsigned char* dst, const __nv_bfloat16* __restrict__ src,
-                                                int64_t ld, int rows, int valid_rows, int K) {
-  const int per_row = K >> 3;
-  const int total = rows * per_row;
-  for (int i = threadIdx.x; i < total; i += blockDim.x) {
-    const int r = i / per_row, kc = i - r * per_row;
-    const bool ok = r < valid_rows;
-    const __nv_bfloat16* g = src + (int64_t)(ok ? r : 0) * ld + kc * 8;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst + tile_offset(r, kc * 8, rows))),
-                 "l"(g), "r"(ok ? 16 : 0)
-                 : "memory");
-  }
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 // Waits until at most n of this thread's committed groups are still in flight.
@@ -192,106 +194,44 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 
 // ----------------------------------------------------------------------------- the GEMM kernel
 
-enum : int { kEpiRelu = 0, kEpiOut = 1, kEpiReluGrad = 2, kEpiWgrad = 3 };
+enum : int { kEpiRelu = 0, kEpiOut = 1 };
 
 struct GemmArgs {
-  // D[m][n] = sum_k A[m0 + m][k0 + k] B[n][k0 + k], k0 = blockIdx.y * K
+  // D[m][n] = sum_k A[m0 + m][k] B[n][k]
   const __nv_bfloat16* A;
   int64_t lda;
   int M;  // valid rows of A (rows past it are zero)
   const __nv_bfloat16* B;
   int64_t ldb;
   int N;  // 16 or 128
-  int K;  // per CTA, multiple of 16, <= 128
-  // epilogue operands
-  const float* bias;              // kEpiRelu, kEpiOut: [N]
-  __nv_bfloat16* out;             // row-major [M][ldo]
+  int K;  // multiple of 16, <= 128
+  const float* bias;              // [N]
+  __nv_bfloat16* out;             // kEpiRelu: row-major [M][ldo]
   int64_t ldo;
-  __nv_bfloat16* outT;            // transposed [N][ldt]
-  int64_t ldt;
-  const __nv_bfloat16* mask;      // kEpiReluGrad: activations [M][ldm], derivative = (h > 0)
-  int64_t ldm;
   float* y;                       // kEpiOut: [M][9]
-  const float* labels;            // kEpiOut: [M][9]; NULL = inference
-  float inv_batch;
-  float w[9];
-  float* loss;                    // kEpiOut: += sum_rows sum_j w_j (y - label)^2 / batch
-  float* dw;                      // kEpiWgrad: dw[n][m] += D[m][n] for n < dw_rows
-  int dw_rows;
-  float* db;                      // kEpiWgrad: db[n] += sum_k B[n][k0 + k]
-  int* step_inc;                  // if set, block (0,0) adds 1 (the optimiser's step count)
   int* err;                       // set to 1 if the tensor-core wait timed out
 };
 
 template <int EPI>
 __device__ __forceinline__ void epilogue(const GemmArgs& a, uint32_t trow, int m, bool row_ok) {
-  if (EPI == kEpiOut) {
+  if constexpr (EPI == kEpiOut) {
     float v[16];
     tmem_ld16(trow, v);
-    float l = 0.f;
-    if (row_ok) {
-      float y[9];
+    if (row_ok)
 #pragma unroll
-      for (int j = 0; j < 9; ++j) y[j] = v[j] + a.bias[j];
-      if (a.y)
-#pragma unroll
-        for (int j = 0; j < 9; ++j) a.y[(int64_t)m * 9 + j] = y[j];
-      if (a.labels) {
-        __align__(16) __nv_bfloat16 d[16];
-#pragma unroll
-        for (int j = 0; j < 9; ++j) {
-          const float e = y[j] - a.labels[(int64_t)m * 9 + j];
-          l += a.w[j] * e * e;
-          d[j] = __float2bfloat16_rn(2.f * a.w[j] * e * a.inv_batch);
-        }
-#pragma unroll
-        for (int j = 9; j < 16; ++j) d[j] = __float2bfloat16_rn(0.f);
-        if (a.out) {
-          uint4* o = reinterpret_cast<uint4*>(a.out + (int64_t)m * a.ldo);
-          o[0] = reinterpret_cast<const uint4*>(d)[0];
-          o[1] = reinterpret_cast<const uint4*>(d)[1];
-        }
-        if (a.outT)
-#pragma unroll
-          for (int j = 0; j < 16; ++j) a.outT[(int64_t)j * a.ldt + m] = d[j];
-      }
-    }
-    if (a.labels && a.loss) {
-      l = warp_sum_f(l * a.inv_batch);
-      if ((threadIdx.x & 31) == 0) atomicAdd(a.loss, l);
-    }
-    return;
-  }
-  for (int c = 0; c < a.N; c += 16) {
-    float v[16];
-    tmem_ld16(trow + (uint32_t)c, v);
-    if (!row_ok) continue;
-    if (EPI == kEpiWgrad) {
-#pragma unroll
-      for (int j = 0; j < 16; ++j)
-        if (c + j < a.dw_rows) atomicAdd(a.dw + (int64_t)(c + j) * kTileM + m, v[j]);
-      continue;
-    }
-    __align__(16) __nv_bfloat16 h[16];
-    if (EPI == kEpiRelu) {
+      for (int j = 0; j < 9; ++j) a.y[(int64_t)m * 9 + j] = v[j] + a.bias[j];
+  } else {
+    for (int c = 0; c < a.N; c += 16) {
+      float v[16];
+      tmem_ld16(trow + (uint32_t)c, v);
+      if (!row_ok) continue;
+      __align__(16) __nv_bfloat16 h[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) h[j] = __float2bfloat16_rn(fmaxf(v[j] + a.bias[c + j], 0.f));
-    } else {  // kEpiReluGrad
-      __align__(16) __nv_bfloat16 hm[16];
-      const uint4* src = reinterpret_cast<const uint4*>(a.mask + (int64_t)m * a.ldm + c);
-      reinterpret_cast<uint4*>(hm)[0] = src[0];
-      reinterpret_cast<uint4*>(hm)[1] = src[1];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) h[j] = __float2bfloat16_rn(__bfloat162float(hm[j]) > 0.f ? v[j] : 0.f);
-    }
-    if (a.out) {
       uint4* o = reinterpret_cast<uint4*>(a.out + (int64_t)m * a.ldo + c);
       o[0] = reinterpret_cast<const uint4*>(h)[0];
       o[1] = reinterpret_cast<const uint4*>(h)[1];
     }
-    if (a.outT)
-#pragma unroll
-      for (int j = 0; j < 16; ++j) a.outT[(int64_t)(c + j) * a.ldt + m] = h[j];
   }
 }
 
@@ -304,17 +244,15 @@ __global__ void __launch_bounds__(kGemmThreads) k_mlp_gemm(GemmArgs a) {
   pdl_trigger();
   const int t = threadIdx.x, w = t >> 5;
   const int m0 = blockIdx.x * kTileM;
-  const int64_t k0 = (int64_t)blockIdx.y * a.K;
   unsigned char* sa = sm;
   unsigned char* sb = sm + kTileM * a.K * 2;
-  if (a.step_inc && t == 0 && blockIdx.x == 0 && blockIdx.y == 0) atomicAdd(a.step_inc, 1);
   if (w == 0) {
     tmem_alloc(smem_u32(&tslot), kTmemCols);
     tmem_relinquish();
   }
   if (t == 0) mbar_init(smem_u32(&mbar), 1);
-  load_tile(sa, a.A + (int64_t)m0 * a.lda + k0, a.lda, kTileM, min(kTileM, a.M - m0), a.K);
-  load_tile(sb, a.B + k0, a.ldb, a.N, a.N, a.K);
+  load_tile(sa, a.A + (int64_t)m0 * a.lda, a.lda, kTileM, min(kTileM, a.M - m0), a.K);
+  load_tile(sb, a.B, a.ldb, a.N, a.N, a.K);
   fence_proxy_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -333,17 +271,6 @@ __global__ void __launch_bounds__(kGemmThreads) k_mlp_gemm(GemmArgs a) {
   if (done) {
     const int m = m0 + t;
     epilogue<EPI>(a, tmem + ((uint32_t)(w * 32) << 16), m, m < a.M);
-    if (EPI == kEpiWgrad && a.db && t < a.N) {  // bias gradient: row sums of this CTA's B chunk
-      const __nv_bfloat16* row = a.B + (int64_t)t * a.ldb + k0;
-      float s = 0.f;
-      for (int k = 0; k < a.K; k += 8) {
-        __align__(16) __nv_bfloat16 v8[8];
-        *reinterpret_cast<uint4*>(v8) = __ldg(reinterpret_cast<const uint4*>(row + k));
-#pragma unroll
-        for (int j = 0; j < 8; ++j) s += __bfloat162float(v8[j]);
-      }
-      atomicAdd(a.db + t, s);
-    }
   } else if (t == 0 && a.err) {
     atomicExch(a.err, 1);
   }
@@ -358,26 +285,49 @@ __global__ void __launch_bounds__(kGemmThreads) k_mlp_gemm(GemmArgs a) {
 // ----------------------------------------------------------------------------- fused training step
 
 // The eight products of a training step (forward, loss, input and weight gradients) for
-// the 128 samples of one CTA, back to back in one kernel with every intermediate in shared
-// memory: the same operands, the same BF16 rounding points and the same per-CTA weight-
-// gradient tiles as the eight launches of launch_mlp_backward, which leave the
-// activations in global memory instead.  A step is one launch of n / 128 CTAs + Adam.
-// Shared memory: six 32 KB slots for 128 x 128 tiles, reused as the step goes on (the
-// operands of a later product are copied asynchronously into a free slot while the
-// current one runs), four 4 KB slots for the 16-wide tiles and the biases; tensor memory:
-// 256 columns, the products alternating between the two halves.
-constexpr int kFusedThreads = 128;
-constexpr uint32_t kSlot = kTileM * 128 * 2;      // 32 KB
-constexpr uint32_t kSmall = kTileM * kMlpOutPad * 2;  // 4 KB
+// the 128 samples of one CTA, in one kernel with every intermediate in shared memory.
+//
+// Layout: every tile [R][C] (C contiguous in global memory) is stored as a plain grid of
+// 8 x 8 core matrices, core (r / 8, c / 8) at (r / 8) * 16 C + (c / 8) * 128 bytes, each core
+// 8 rows of 16 contiguous bytes.  The same bytes are a valid tcgen05 operand both ways:
+// K-major (rows = M or N, K = the columns: leading offset 128 B between the two K cores of
+// a 16-wide K step, stride offset 16 C B between row groups, 256 B per K step) and MN-major
+// (M or N = the columns, K = the rows: stride offset 128 B between column groups, leading
+// offset 16 C B between the two K cores, 32 C B per K step; bits 15 / 16 of the instruction
+// descriptor).  So a transposed operand (H1^T, X^T, W2^T, ...) is the stored tile read the
+// other way, and no transposed copy is written.
+//
+// Bias gradients come out of the weight-gradient products: the X and H1 tiles carry 16
+// extra columns of ones (C = 144), so G1^T [X | 1] and G2^T [H1 | 1] give dW1 | db1 and
+// dW2 | db2 in one product each (column 128 of the result is the row sum); db3 is a warp
+// and block sum of dY.  Products that do not depend on each other (G2 and dW3; G1 and
+// dW2) are issued together into the two halves of a 512-column tensor-memory allocation
+// (one CTA per SM: the shared memory allows no second).
+//
+// Two warps share each 32-lane quarter of tensor memory (one accumulator row per lane):
+// warp w reads lanes 32 (w % 4) .. + 31 and the columns [64 (w / 4), + 64) of a 128-column
+// result, so every epilogue is split across 256 threads; each thread loads its 64 columns
+// with one tensor-memory load and one wait.
+//
+// Shared memory (bytes): X | 1 (36 K, all step) | H1 | 1 (36 K) | W1, then H2, then G1
+// (32 K) | W2 (32 K) | G2 (32 K) | W3 [16][128] (4 K) | dY [128][16] (4 K) | b1 b2 b3 |
+// db3 per warp | the CTA's labels [128][9].
+constexpr int kFusedThreads = 256;
+constexpr int kXC = kMlpIn + 16;        // columns of the X and H1 tiles: the values, then ones
+constexpr uint32_t kTileX = kTileM * kXC * 2;
+constexpr uint32_t kTileW = 128 * 128 * 2;
+constexpr uint32_t kTile16 = 128 * kMlpOutPad * 2;
 constexpr int kBiasFloats = 2 * kMlpHidden + kMlpOutPad;
-constexpr int kFusedSmem = 6 * kSlot + 4 * kSmall + kBiasFloats * 4 + 1024;
-constexpr uint32_t kFusedCols = 256;
+constexpr uint32_t kOffX = 0, kOffH1 = kOffX + kTileX, kOffS = kOffH1 + kTileX, kOffW2 = kOffS + kTileW,
+                   kOffG2 = kOffW2 + kTileW, kOffW3 = kOffG2 + kTileW, kOffDY = kOffW3 + kTile16,
+                   kOffBias = kOffDY + kTile16, kOffDb3 = kOffBias + kBiasFloats * 4,
+                   kOffLab = kOffDb3 + 4 * kMlpOutPad * 4, kFusedBytes = kOffLab + kTileM * 9 * 4;
+constexpr int kFusedSmem = (int)kFusedBytes + 1024;
+constexpr uint32_t kFusedCols = 512;
 
 struct FusedArgs {
   MlpState st;
   const __nv_bfloat16* X;   // [n][128]
-  const __nv_bfloat16* XT;  // [128][ldxt]
-  int64_t ldxt;
   const float* labels;      // [n][9]
   float w[9];
   float inv_batch;
@@ -387,48 +337,101 @@ struct FusedArgs {
   float* gpart;             // [gridDim.x][kMlpParams]: this CTA's gradient
 };
 
-// Thread m stores its 16 values of columns [c, c + 16) of row m into a K-major 128-row tile.
-__device__ __forceinline__ void put_row16(unsigned char* tile, int m, int c, const __nv_bfloat16 (&h)[16]) {
-  *reinterpret_cast<uint4*>(tile + tile_offset(m, c, kTileM)) = reinterpret_cast<const uint4*>(h)[0];
-  *reinterpret_cast<uint4*>(tile + tile_offset(m, c + 8, kTileM)) = reinterpret_cast<const uint4*>(h)[1];
+// Byte offset of element (r, c) of a grid-layout tile of C columns.
+__device__ __forceinline__ uint32_t grid_off(int r, int c, int C) {
+  return (uint32_t)((r >> 3) * (C >> 3) * 128 + (c >> 3) * 128 + (r & 7) * 16 + (c & 7) * 2);
 }
-// ... and into the transposed K-major tile (rows = the columns c + j, K = the samples).
-__device__ __forceinline__ void put_col16(unsigned char* tileT, int rowsT, int m, int c,
-                                          const __nv_bfloat16 (&h)[16]) {
-#pragma unroll
-  for (int j = 0; j < 16; ++j)
-    *reinterpret_cast<__nv_bfloat16*>(tileT + tile_offset(c + j, m, rowsT)) = h[j];
+// rows x K block of a row-major global matrix (ld elements, 16-byte aligned rows) into
+// columns [0, K) of a grid tile of C columns, by cp.async (committed by the caller).
+__device__ __forceinline__ void load_grid_async(unsigned char* dst, const __nv_bfloat16* __restrict__ src,
+                                                int64_t ld, int rows, int K, int C) {
+  const int per_row = K >> 3;
+  for (int i = threadIdx.x; i < rows * per_row; i += blockDim.x) {
+    const int r = i / per_row, kc = i - r * per_row;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst + grid_off(r, kc * 8, C))),
+                 "l"(src + (int64_t)r * ld + kc * 8)
+                 : "memory");
+  }
+}
+// Thread m's 16 values for columns [c, c + 16) of row m of a grid tile of C columns.
+__device__ __forceinline__ void put_grid16(unsigned char* tile, int C, int m, int c, const __nv_bfloat16 (&h)[16]) {
+  *reinterpret_cast<uint4*>(tile + grid_off(m, c, C)) = reinterpret_cast<const uint4*>(h)[0];
+  *reinterpret_cast<uint4*>(tile + grid_off(m, c + 8, C)) = reinterpret_cast<const uint4*>(h)[1];
 }
 
-// D[tmem] = A[a] . B[b]^T over K (multiple of 16) for an N-wide B, issued by thread 0 and
-// committed to the mbarrier; every thread then waits (bounded) for phase `ph`.
-__device__ __forceinline__ bool fused_mma(uint32_t tmem, const unsigned char* a, const unsigned char* b, int N, int K,
-                                          uint32_t bar, uint32_t ph) {
+// One operand of a product: a grid tile read K-major (rows = M or N) or MN-major (columns =
+// M or N, rows = K).
+struct Opnd {
+  uint32_t addr;
+  int C;
+  bool mn;
+};
+__device__ __forceinline__ uint64_t opnd_desc(const Opnd& o, int kstep) {
+  const uint32_t lbo = o.mn ? 16u * (uint32_t)o.C : 128u, sbo = o.mn ? 128u : 16u * (uint32_t)o.C;
+  const uint32_t a = o.addr + (uint32_t)kstep * (o.mn ? 32u * (uint32_t)o.C : 256u);
+  return (uint64_t)((a & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
+}
+// D[tmem][128][N] = A . B^T over K (multiple of 16); called by thread 0.
+__device__ __forceinline__ void issue_product(uint32_t tmem, const Opnd& A, const Opnd& B, int N, int K) {
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((A.mn ? 1u : 0u) << 15) | ((B.mn ? 1u : 0u) << 16) |
+                         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
+  for (int s = 0; s < (K >> 4); ++s) mma_bf16(tmem, opnd_desc(A, s), opnd_desc(B, s), idesc, s > 0 ? 1u : 0u);
+}
+// Makes the block's shared-memory writes visible to the tensor core and orders the
+// previous tensor-memory reads before the products the caller issues next.
+__device__ __forceinline__ void round_begin() {
   fence_proxy_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (threadIdx.x == 0) {
-    const uint32_t idesc = idesc_bf16(kTileM, N);
-    const uint32_t abase = smem_u32(a), bbase = smem_u32(b);
-    for (int s = 0; s < (K >> 4); ++s)
-      mma_bf16(tmem, smem_desc(abase + (uint32_t)(s * kTileM * 32)), smem_desc(bbase + (uint32_t)(s * N * 32)),
-               idesc, s > 0 ? 1u : 0u);
-    mma_commit(bar);
-  }
+}
+// Thread 0 commits the products it issued; every thread waits (bounded) for them.
+__device__ __forceinline__ bool round_end(uint32_t bar, uint32_t ph) {
+  if (threadIdx.x == 0) mma_commit(bar);
   const bool ok = mbar_wait_bounded(bar, ph);
   tc_fence_after();
   return __syncthreads_and(ok ? 1 : 0) != 0;
 }
 
-// Row sums of a K-major tile's rows [0, rows) over its 128 samples (bias gradients).
-__device__ __forceinline__ void bias_grad(const unsigned char* tileT, int rowsT, int rows, float* db) {
-  const int t = threadIdx.x;
-  if (t >= rows) return;
-  float s = 0.f;
-  for (int k = 0; k < kTileM; ++k)
-    s += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(tileT + tile_offset(t, k, rowsT)));
-  db[t] = s;
+// Epilogue of a 128-row activation tile: thread (row r, half g) turns its 64 accumulator
+// columns into BF16 values (ReLU of the sum with the bias when `bias` is set, else the
+// accumulator masked by the ReLU derivative `mask`), stores them into row r of a grid tile
+// of C columns, and (with the bias) records which are positive in `mask`.
+template <bool kRelu>
+__device__ __forceinline__ void act_epilogue(uint32_t taddr, const float* bias, uint32_t (&mask)[2],
+                                             unsigned char* tile, int C, int r, int c0) {
+  float v[64];
+  tmem_ld64(taddr, v);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    __align__(16) __nv_bfloat16 h[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int k = 16 * q + j;
+      if (kRelu) {
+        h[j] = __float2bfloat16_rn(fmaxf(v[k] + bias[c0 + k], 0.f));
+        if (__bfloat162float(h[j]) > 0.f) mask[k >> 5] |= 1u << (k & 31);
+      } else {
+        h[j] = __float2bfloat16_rn(((mask[k >> 5] >> (k & 31)) & 1u) ? v[k] : 0.f);
+      }
+    }
+    put_grid16(tile, C, r, c0 + 16 * q, h);
+  }
+}
+// Epilogue of a weight-gradient result [128][128 | ones]: thread (row r, half g) stores its
+// 64 columns into row r of the gradient block dw [128][128]; half 1 also stores column 128
+// (the row sum: the bias gradient) into db[r].
+__device__ __forceinline__ void wgrad_epilogue(uint32_t taddr, float* dw, float* db, int r, int g) {
+  float v[64];
+  tmem_ld64(taddr + (uint32_t)(64 * g), v);
+  float4* d4 = reinterpret_cast<float4*>(dw + (int64_t)r * 128 + 64 * g);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  if (g == 1) {
+    float b[16];
+    tmem_ld16(taddr + 128u, b);
+    db[r] = b[0];
+  }
 }
 
 __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_train_fused(FusedArgs a) {
@@ -437,20 +440,21 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_train_fused(FusedArgs 
   __shared__ uint32_t tslot;
   pdl_wait();
   pdl_trigger();
-  const int t = threadIdx.x, w = t >> 5;
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const int g = w >> 2;              // column half of a 128-column result
+  const int r = (w & 3) * 32 + lane; // accumulator row (TMEM lane) of this thread
+  const int c0 = 64 * g;
   const int64_t m0 = (int64_t)blockIdx.x * kTileM;
-  const int m = (int)m0 + t;  // this thread's sample (the batch is a multiple of 128 rows)
-  unsigned char* sA = sm;                  // X, then W2T
-  unsigned char* sB = sm + kSlot;          // W1, then H2, then XT
-  unsigned char* sC = sm + 2 * kSlot;      // H1, then G2T
-  unsigned char* sD = sm + 3 * kSlot;      // H1T
-  unsigned char* sE = sm + 4 * kSlot;      // H2T, then G1T
-  unsigned char* sF = sm + 5 * kSlot;      // W2, then G2
-  unsigned char* s0 = sm + 6 * kSlot;      // W3 [16][128]
-  unsigned char* s1 = s0 + kSmall;         // dY [128][16]
-  unsigned char* s2 = s1 + kSmall;         // dY^T [16][128]
-  unsigned char* s3 = s2 + kSmall;         // W3^T [128][16]
-  float* sbias = reinterpret_cast<float*>(s3 + kSmall);   // b1, b2, b3
+  unsigned char* sX = sm + kOffX;
+  unsigned char* sH1 = sm + kOffH1;
+  unsigned char* sS = sm + kOffS;    // W1, then H2, then G1
+  unsigned char* sW2 = sm + kOffW2;
+  unsigned char* sG2 = sm + kOffG2;
+  unsigned char* sW3 = sm + kOffW3;
+  unsigned char* sDY = sm + kOffDY;
+  float* sbias = reinterpret_cast<float*>(sm + kOffBias);   // b1, b2, b3
+  float* sdb3 = reinterpret_cast<float*>(sm + kOffDb3);     // [warp][16]
+  const float* slab = reinterpret_cast<const float*>(sm + kOffLab);
   const MlpState& st = a.st;
   float* const gp = a.gpart + (int64_t)blockIdx.x * kMlpParams;   // this CTA's gradient
   if (a.step_inc && t == 0 && blockIdx.x == 0) atomicAdd(a.step_inc, 1);
@@ -460,171 +464,141 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_train_fused(FusedArgs 
   }
   if (t == 0) mbar_init(smem_u32(&mbar), 1);
   const uint32_t bar = smem_u32(&mbar);
-  // the first product's operands, then W2 (in flight while the first product runs)
-  load_tile_async(sA, a.X + m0 * kMlpIn, kMlpIn, kTileM, kTileM, 128);
-  load_tile_async(sB, st.w1b, kMlpHidden, 128, 128, 128);
-  load_tile_async(s0, st.w3b, kMlpHidden, kMlpOutPad, kMlpOutPad, 128);
-  load_tile_async(s3, st.w3tb, kMlpOutPad, 128, 128, kMlpOutPad);
+  load_grid_async(sX, a.X + m0 * kMlpIn, kMlpIn, kTileM, kMlpIn, kXC);
+  load_grid_async(sS, st.w1b, kMlpIn, kMlpHidden, kMlpIn, 128);
   cp_async_commit();
-  load_tile_async(sF, st.w2b, kMlpHidden, 128, 128, 128);
+  load_grid_async(sW2, st.w2b, kMlpHidden, kMlpHidden, kMlpHidden, 128);
+  load_grid_async(sW3, st.w3b, kMlpHidden, kMlpOutPad, kMlpHidden, 128);
+  {
+    // the CTA's labels: 128 x 9 floats, contiguous and 16-byte aligned (m0 is a multiple of 128)
+    const float* lab = a.labels + m0 * 9;
+    for (int i = t; i < kTileM * 9 / 4; i += kFusedThreads)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(sm + kOffLab + 16 * i)),
+                   "l"(lab + 4 * i)
+                   : "memory");
+  }
   cp_async_commit();
+  {
+    // the ones columns [128, 144) of the X and H1 tiles: two 16-byte rows per tile row
+    const uint4 ones = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+    for (int i = t; i < 4 * kTileM; i += kFusedThreads) {
+      unsigned char* tile = (i & 2) ? sH1 : sX;
+      *reinterpret_cast<uint4*>(tile + grid_off(i >> 2, kMlpIn + 8 * (i & 1), kXC)) = ones;
+    }
+  }
   for (int i = t; i < kBiasFloats; i += kFusedThreads)
     sbias[i] = i < kMlpHidden ? st.param[kMlpB1 + i]
                               : (i < 2 * kMlpHidden ? st.param[kMlpB2 + i - kMlpHidden]
                                                     : st.param[kMlpB3 + i - 2 * kMlpHidden]);
   cp_async_wait_group<1>();
   __syncthreads();
-  const uint32_t t0 = tslot, lane_off = (uint32_t)(w * 32) << 16;
-  const uint32_t tA = t0 + lane_off, tB = t0 + 128u + lane_off;  // this thread's TMEM lane, two halves
+  const uint32_t t0 = tslot, t1 = t0 + 256u, lane_off = (uint32_t)((w & 3) * 32) << 16;
+  const uint32_t a0 = t0 + lane_off, a1 = t1 + lane_off;   // this thread's row in the two halves
+  const Opnd X{smem_u32(sX), kXC, false}, XT{smem_u32(sX), kXC, true};
+  const Opnd H1{smem_u32(sH1), kXC, false}, H1T{smem_u32(sH1), kXC, true};
+  const Opnd S{smem_u32(sS), 128, false}, ST{smem_u32(sS), 128, true};
+  const Opnd W2{smem_u32(sW2), 128, false}, W2T{smem_u32(sW2), 128, true};
+  const Opnd G2{smem_u32(sG2), 128, false}, G2T{smem_u32(sG2), 128, true};
+  const Opnd W3{smem_u32(sW3), 128, false}, W3T{smem_u32(sW3), 128, true};
+  const Opnd DY{smem_u32(sDY), kMlpOutPad, false}, DYT{smem_u32(sDY), kMlpOutPad, true};
   uint32_t ph = 0;
   bool ok = true;
-  uint32_t mask1[4] = {0u, 0u, 0u, 0u}, mask2[4] = {0u, 0u, 0u, 0u};
+  uint32_t mask1[2] = {0u, 0u}, mask2[2] = {0u, 0u};   // ReLU masks of this thread's 64 columns
 
-  // ---- H1 = relu(X W1^T + b1): rows into sC, transposed into sD
-  ok = fused_mma(t0, sA, sB, 128, 128, bar, ph);
+  // ---- H1 = relu(X W1^T + b1) [samples][h1]
+  round_begin();
+  if (t == 0) issue_product(t0, X, S, 128, kMlpIn);
+  ok = round_end(bar, ph);
   ph ^= 1u;
   if (ok) {
-    for (int c = 0; c < 128; c += 16) {
-      float v[16];
-      tmem_ld16(tA + (uint32_t)c, v);
-      __align__(16) __nv_bfloat16 h[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        h[j] = __float2bfloat16_rn(fmaxf(v[j] + sbias[c + j], 0.f));
-        if (__bfloat162float(h[j]) > 0.f) mask1[(c + j) >> 5] |= 1u << ((c + j) & 31);
-      }
-      put_row16(sC, t, c, h);
-      put_col16(sD, kTileM, t, c, h);
-    }
-    // X is no longer needed: W2^T goes there while the next products run
-    load_tile_async(sA, st.w2tb, kMlpHidden, 128, 128, 128);
-    cp_async_commit();
+    act_epilogue<true>(a0 + (uint32_t)c0, sbias, mask1, sH1, kXC, r, c0);
+    cp_async_wait_all();   // W2, W3, labels
   }
-  // ---- H2 = relu(H1 W2^T + b2): rows into sB (W1 free), transposed into sE
+  // ---- H2 = relu(H1 W2^T + b2) [samples][h2], into the W1 slot
   if (ok) {
-    cp_async_wait_group<1>();   // W2
-    ok = fused_mma(t0 + 128u, sC, sF, 128, 128, bar, ph);
+    round_begin();
+    if (t == 0) issue_product(t1, H1, W2, 128, kMlpHidden);
+    ok = round_end(bar, ph);
     ph ^= 1u;
   }
+  if (ok) act_epilogue<true>(a1 + (uint32_t)c0, sbias + kMlpHidden, mask2, sS, 128, r, c0);
+  // ---- Y = H2 W3^T + b3, the loss, dY = 2 w (y - label) / n [samples][16], db3 (warps 0-3)
   if (ok) {
-    for (int c = 0; c < 128; c += 16) {
-      float v[16];
-      tmem_ld16(tB + (uint32_t)c, v);
-      __align__(16) __nv_bfloat16 h[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        h[j] = __float2bfloat16_rn(fmaxf(v[j] + sbias[kMlpHidden + c + j], 0.f));
-        if (__bfloat162float(h[j]) > 0.f) mask2[(c + j) >> 5] |= 1u << ((c + j) & 31);
-      }
-      put_row16(sB, t, c, h);
-      put_col16(sE, kTileM, t, c, h);
-    }
-  }
-  // ---- Y = H2 W3^T + b3, the loss, dY = 2 w (y - label) / n: rows into s1, transposed into s2
-  if (ok) {
-    ok = fused_mma(t0, sB, s0, kMlpOutPad, 128, bar, ph);
+    round_begin();
+    if (t == 0) issue_product(t0, S, W3, kMlpOutPad, kMlpHidden);
+    ok = round_end(bar, ph);
     ph ^= 1u;
   }
-  if (ok) {
+  if (ok && g == 0) {
     float v[16];
-    tmem_ld16(tA, v);
+    tmem_ld16(a0, v);
     float l = 0.f;
     __align__(16) __nv_bfloat16 d[16];
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
       const float y = v[j] + sbias[2 * kMlpHidden + j];
-      const float e = y - a.labels[(int64_t)m * 9 + j];
+      const float e = y - slab[r * 9 + j];
       l += a.w[j] * e * e;
       d[j] = __float2bfloat16_rn(2.f * a.w[j] * e * a.inv_batch);
     }
 #pragma unroll
     for (int j = 9; j < 16; ++j) d[j] = __float2bfloat16_rn(0.f);
-    *reinterpret_cast<uint4*>(s1 + tile_offset(t, 0, kTileM)) = reinterpret_cast<const uint4*>(d)[0];
-    *reinterpret_cast<uint4*>(s1 + tile_offset(t, 8, kTileM)) = reinterpret_cast<const uint4*>(d)[1];
-    put_col16(s2, kMlpOutPad, t, 0, d);
+    put_grid16(sDY, kMlpOutPad, r, 0, d);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      const float s = warp_sum_f(__bfloat162float(d[j]));
+      if (lane == 0) sdb3[w * kMlpOutPad + j] = s;
+    }
     if (a.loss) {
       l = warp_sum_f(l * a.inv_batch);
-      if ((t & 31) == 0) atomicAdd(a.loss, l);
+      if (lane == 0) atomicAdd(a.loss, l);
     }
   }
-  // ---- G2 = (dY W3) * (H2 > 0): rows into sF (W2 free), transposed into sC (H1 free)
+  // ---- G2 = (dY W3) * (H2 > 0) [samples][h2] and dW3 = dY^T H2 [h2][16] (transposed)
   if (ok) {
-    ok = fused_mma(t0 + 128u, s1, s3, 128, kMlpOutPad, bar, ph);
+    round_begin();
+    if (t == 0) {
+      issue_product(t0, DY, W3T, 128, kMlpOutPad);
+      issue_product(t1, ST, DYT, kMlpOutPad, kTileM);
+    }
+    ok = round_end(bar, ph);
     ph ^= 1u;
   }
   if (ok) {
-    // H2 is no longer needed: X^T goes there while the next products run
-    load_tile_async(sB, a.XT + m0, a.ldxt, 128, 128, 128);
-    cp_async_commit();
-    for (int c = 0; c < 128; c += 16) {
+    act_epilogue<false>(a0 + (uint32_t)c0, nullptr, mask2, sG2, 128, r, c0);
+    if (g == 1) {
       float v[16];
-      tmem_ld16(tB + (uint32_t)c, v);
-      __align__(16) __nv_bfloat16 h[16];
+      tmem_ld16(a1, v);
 #pragma unroll
-      for (int j = 0; j < 16; ++j)
-        h[j] = __float2bfloat16_rn(((mask2[(c + j) >> 5] >> ((c + j) & 31)) & 1u) ? v[j] : 0.f);
-      put_row16(sF, t, c, h);
-      put_col16(sC, kTileM, t, c, h);
+      for (int j = 0; j < kMlpOutPad; ++j) gp[kMlpW3 + j * kTileM + r] = j < kMlpOut ? v[j] : 0.f;
+    } else if (r < kMlpOutPad) {
+      gp[kMlpB3 + r] = r < kMlpOut ? sdb3[r] + sdb3[kMlpOutPad + r] + sdb3[2 * kMlpOutPad + r] +
+                                         sdb3[3 * kMlpOutPad + r]
+                                   : 0.f;
     }
   }
-  // ---- dW3 += dY^T H2 (A = H2^T, B = dY^T), db3
+  // ---- G1 = (G2 W2) * (H1 > 0) [samples][h1], into the H2 slot; dW2 | db2 = G2^T [H1 | 1]
   if (ok) {
-    ok = fused_mma(t0, sE, s2, kMlpOutPad, 128, bar, ph);
+    round_begin();
+    if (t == 0) {
+      issue_product(t0, G2, W2T, 128, kMlpHidden);
+      issue_product(t1, G2T, H1T, kXC, kTileM);
+    }
+    ok = round_end(bar, ph);
     ph ^= 1u;
   }
   if (ok) {
-    float v[16];
-    tmem_ld16(tA, v);
-#pragma unroll
-    for (int j = 0; j < kMlpOutPad; ++j) gp[kMlpW3 + j * kTileM + t] = j < kMlpOut ? v[j] : 0.f;
-    bias_grad(s2, kMlpOutPad, kMlpOutPad, gp + kMlpB3);
+    act_epilogue<false>(a0 + (uint32_t)c0, nullptr, mask1, sS, 128, r, c0);
+    wgrad_epilogue(a1, gp + kMlpW2, gp + kMlpB2, r, g);
   }
-  // ---- G1 = (G2 W2) * (H1 > 0): transposed into sE (H2^T free)
+  // ---- dW1 | db1 = G1^T [X | 1] [h1][in + 1]
   if (ok) {
-    cp_async_wait_group<1>();   // W2^T (X^T may still be in flight)
-    ok = fused_mma(t0 + 128u, sF, sA, 128, 128, bar, ph);
+    round_begin();
+    if (t == 0) issue_product(t0, ST, XT, kXC, kTileM);
+    ok = round_end(bar, ph);
     ph ^= 1u;
   }
-  if (ok) {
-    for (int c = 0; c < 128; c += 16) {
-      float v[16];
-      tmem_ld16(tB + (uint32_t)c, v);
-      __align__(16) __nv_bfloat16 h[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j)
-        h[j] = __float2bfloat16_rn(((mask1[(c + j) >> 5] >> ((c + j) & 31)) & 1u) ? v[j] : 0.f);
-      put_col16(sE, kTileM, t, c, h);
-    }
-  }
-  // ---- dW2 += G2^T H1 (A = H1^T, B = G2^T), db2
-  if (ok) {
-    ok = fused_mma(t0, sD, sC, 128, 128, bar, ph);
-    ph ^= 1u;
-  }
-  if (ok) {
-    for (int c = 0; c < 128; c += 16) {
-      float v[16];
-      tmem_ld16(tA + (uint32_t)c, v);
-#pragma unroll
-      for (int j = 0; j < 16; ++j) gp[kMlpW2 + (c + j) * kTileM + t] = v[j];
-    }
-    bias_grad(sC, kTileM, kMlpHidden, gp + kMlpB2);
-  }
-  // ---- dW1 += G1^T X (A = X^T, B = G1^T), db1
-  if (ok) {
-    cp_async_wait_all();        // X^T
-    ok = fused_mma(t0 + 128u, sB, sE, 128, 128, bar, ph);
-    ph ^= 1u;
-  }
-  if (ok) {
-    for (int c = 0; c < 128; c += 16) {
-      float v[16];
-      tmem_ld16(tB + (uint32_t)c, v);
-#pragma unroll
-      for (int j = 0; j < 16; ++j) gp[kMlpW1 + (c + j) * kTileM + t] = v[j];
-    }
-    bias_grad(sE, kTileM, kMlpHidden, gp + kMlpB1);
-  }
+  if (ok) wgrad_epilogue(a0, gp + kMlpW1, gp + kMlpB1, r, g);
   if (!ok && t == 0 && a.err) atomicExch(a.err, 1);
   cp_async_wait_all();          // no copy may still target shared memory when the CTA ends
   tc_fence_before();
@@ -717,14 +691,29 @@ __global__ void k_mlp_features(int nq, int nv, const float* __restrict__ Pm, con
 // One thread per parameter: Adam (bias-corrected, step count from the state, learning rate
 // on a cosine schedule from lr to lr_final over total_steps), gradient reset to zero, and
 // the BF16 operand copies of the weights (W and, for W2 and W3, W^T) rewritten.
+// g0 + the fused step's per-CTA gradient entries i, added in block order; eight loads in
+// flight at a time.
+__device__ __forceinline__ float sum_partials(const float* __restrict__ gpart, int nb, int i, float g0) {
+  float g = g0;
+  int b = 0;
+  for (; b + 8 <= nb; b += 8) {
+    float p[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) p[u] = __ldcg(gpart + (int64_t)(b + u) * kMlpParams + i);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) g += p[u];
+  }
+  for (; b < nb; ++b) g += __ldcg(gpart + (int64_t)b * kMlpParams + i);
+  return g;
+}
+
 __global__ void k_mlp_adam(MlpState st, dqo_mlp_hparams hp, const float* __restrict__ gpart, int nb) {
   pdl_wait();
   pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kMlpParams) return;
   const int step = *st.step;
-  float g = st.grad[i];
-  for (int b = 0; b < nb; ++b) g += gpart[(int64_t)b * kMlpParams + i];   // in block order
+  const float g = sum_partials(gpart, nb, i, st.grad[i]);
   st.grad[i] = 0.f;
   const float m = hp.beta1 * st.m1[i] + (1.f - hp.beta1) * g;
   const float v = hp.beta2 * st.m2[i] + (1.f - hp.beta2) * g * g;
@@ -745,9 +734,7 @@ __global__ void k_mlp_sum_partials(const float* __restrict__ gpart, int nb, floa
   pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kMlpParams) return;
-  float g = 0.f;
-  for (int b = 0; b < nb; ++b) g += gpart[(int64_t)b * kMlpParams + i];
-  out[i] = g;
+  out[i] = sum_partials(gpart, nb, i, 0.f);
 }
 
 // Parameters -> state: master copy, BF16 copies, Adam moments and step reset.
@@ -787,10 +774,6 @@ cudaError_t mlp_gemm_setup() {
   if ((e = cudaFuncSetAttribute(k_mlp_gemm<kEpiRelu>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem)))
     return e;
   if ((e = cudaFuncSetAttribute(k_mlp_gemm<kEpiOut>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem)))
-    return e;
-  if ((e = cudaFuncSetAttribute(k_mlp_gemm<kEpiReluGrad>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem)))
-    return e;
-  if ((e = cudaFuncSetAttribute(k_mlp_gemm<kEpiWgrad>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem)))
     return e;
   return cudaFuncSetAttribute(k_mlp_train_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmem);
 }
@@ -869,18 +852,16 @@ cudaError_t launch_mlp_forward(const MlpState& st, const MlpWork& wk, int64_t n,
 }
 
 // Loss and gradients of a batch (n % 128 == 0) in one launch of n / 128 CTAs (the eight
-// products of launch_mlp_backward fused, intermediates in shared memory).  Each CTA's
+// products of a training step fused, intermediates in shared memory).  Each CTA's
 // gradient goes to gpart[blockIdx]; the loss is ADDED to *loss.
 cudaError_t launch_mlp_backward_fused(const MlpState& st, int* err, float* gpart, int64_t n, const uint16_t* X_,
-                                      const uint16_t* XT_, int64_t ldxt, const float* labels, const float* loss_w,
-                                      float* loss, int* step_inc, cudaStream_t s) {
+                                      const float* labels, const float* loss_w, float* loss, int* step_inc,
+                                      cudaStream_t s) {
   if (n <= 0 || n % kTileM || !gpart) return cudaErrorInvalidValue;
   FusedArgs a{};
   a.st = st;
   a.gpart = gpart;
   a.X = reinterpret_cast<const __nv_bfloat16*>(X_);
-  a.XT = reinterpret_cast<const __nv_bfloat16*>(XT_);
-  a.ldxt = ldxt;
   a.labels = labels;
 #pragma unroll
   for (int j = 0; j < 9; ++j) a.w[j] = loss_w[j];
@@ -889,79 +870,6 @@ cudaError_t launch_mlp_backward_fused(const MlpState& st, int* err, float* gpart
   a.step_inc = step_inc;
   a.err = err;
   return launch_dep_smem(k_mlp_train_fused, dim3((unsigned)(n / kTileM)), dim3(kFusedThreads), kFusedSmem, s, a);
-}
-
-// Loss and gradients of a batch (n % 128 == 0): eight launches.  Gradients are ADDED to
-// st.grad; the loss is ADDED to *loss.
-cudaError_t launch_mlp_backward(const MlpState& st, const MlpWork& wk, int64_t n, const uint16_t* X_,
-                                const uint16_t* XT_, int64_t ldxt, const float* labels, const float* loss_w,
-                                float* loss, int* step_inc, cudaStream_t s) {
-  const __nv_bfloat16* X = reinterpret_cast<const __nv_bfloat16*>(X_);
-  const __nv_bfloat16* XT = reinterpret_cast<const __nv_bfloat16*>(XT_);
-  const dim3 rows((unsigned)(n / kTileM), 1), ksplit(1, (unsigned)(n / kTileM));
-  cudaError_t e;
-  // forward, keeping activations in both layouts
-  GemmArgs a = base(X, kMlpIn, (int)n, st.w1b, kMlpHidden, 128, 128, wk.err);
-  a.bias = st.param + kMlpB1;
-  a.out = wk.h1;
-  a.ldo = kMlpHidden;
-  a.outT = wk.h1t;
-  a.ldt = n;
-  a.step_inc = step_inc;
-  if ((e = gemm<kEpiRelu>(a, rows, s))) return e;
-  a = base(wk.h1, kMlpHidden, (int)n, st.w2b, kMlpHidden, 128, 128, wk.err);
-  a.bias = st.param + kMlpB2;
-  a.out = wk.h2;
-  a.ldo = kMlpHidden;
-  a.outT = wk.h2t;
-  a.ldt = n;
-  if ((e = gemm<kEpiRelu>(a, rows, s))) return e;
-  a = base(wk.h2, kMlpHidden, (int)n, st.w3b, kMlpHidden, kMlpOutPad, 128, wk.err);
-  a.bias = st.param + kMlpB3;
-  a.labels = labels;
-  a.inv_batch = 1.f / (float)n;
-#pragma unroll
-  for (int j = 0; j < 9; ++j) a.w[j] = loss_w[j];
-  a.loss = loss;
-  a.out = wk.dy;
-  a.ldo = kMlpOutPad;
-  a.outT = wk.dyt;
-  a.ldt = n;
-  if ((e = gemm<kEpiOut>(a, rows, s))) return e;
-  // layer 3: dZ2 = (dY W3) * (H2 > 0), dW3 += dY^T H2
-  a = base(wk.dy, kMlpOutPad, (int)n, st.w3tb, kMlpOutPad, 128, kMlpOutPad, wk.err);
-  a.mask = wk.h2;
-  a.ldm = kMlpHidden;
-  a.out = wk.dz2;
-  a.ldo = kMlpHidden;
-  a.outT = wk.dz2t;
-  a.ldt = n;
-  if ((e = gemm<kEpiReluGrad>(a, rows, s))) return e;
-  a = base(wk.h2t, n, kMlpHidden, wk.dyt, n, kMlpOutPad, kTileM, wk.err);
-  a.dw = st.grad + kMlpW3;
-  a.dw_rows = kMlpOut;
-  a.db = st.grad + kMlpB3;
-  if ((e = gemm<kEpiWgrad>(a, ksplit, s))) return e;
-  // layer 2: dZ1 = (dZ2 W2) * (H1 > 0), dW2 += dZ2^T H1
-  a = base(wk.dz2, kMlpHidden, (int)n, st.w2tb, kMlpHidden, 128, 128, wk.err);
-  a.mask = wk.h1;
-  a.ldm = kMlpHidden;
-  a.out = wk.dz1;
-  a.ldo = kMlpHidden;
-  a.outT = wk.dz1t;
-  a.ldt = n;
-  if ((e = gemm<kEpiReluGrad>(a, rows, s))) return e;
-  a = base(wk.h1t, n, kMlpHidden, wk.dz2t, n, 128, kTileM, wk.err);
-  a.dw = st.grad + kMlpW2;
-  a.dw_rows = kMlpHidden;
-  a.db = st.grad + kMlpB2;
-  if ((e = gemm<kEpiWgrad>(a, ksplit, s))) return e;
-  // layer 1: dW1 += dZ1^T X
-  a = base(XT, ldxt, kMlpIn, wk.dz1t, n, 128, kTileM, wk.err);
-  a.dw = st.grad + kMlpW1;
-  a.dw_rows = kMlpHidden;
-  a.db = st.grad + kMlpB1;
-  return gemm<kEpiWgrad>(a, ksplit, s);
 }
 
 }  // namespace dqo

@@ -89,8 +89,8 @@ _SIGS = {
     "dqo_mlp_set_params": (c_i32, [c_p, c_p, c_p]),
     "dqo_mlp_get_params": (c_i32, [c_p, c_p, c_p]),
     "dqo_mlp_forward": (c_i32, [c_p, c_p, c_i64, c_p, c_p, c_p]),
-    "dqo_mlp_gradients": (c_i32, [c_p, c_p, c_i64, c_p, c_p, c_i64, c_p, c_p, c_p, c_p, c_p]),
-    "dqo_mlp_train_step": (c_i32, [c_p, c_p, c_p, c_i64, c_p, c_p, c_i64, c_p, c_p, c_p]),
+    "dqo_mlp_gradients": (c_i32, [c_p, c_p, c_i64, c_p, c_p, c_p, c_p, c_p, c_p]),
+    "dqo_mlp_train_step": (c_i32, [c_p, c_p, c_p, c_i64, c_p, c_p, c_p, c_p]),
     "dqo_mlp_check": (c_i32, [c_p, c_p]),
     "dqo_wait_probe": (c_i32, [c_p, c_p]),
     "dqo_alu_probe": (c_i32, [c_i32, c_i32, c_p, C.POINTER(C.c_double), c_p]),
@@ -497,33 +497,22 @@ def dqo_mlp_forward(ctx: Context, state: MlpState, X, out=None, stream=None):
     return out
 
 
-def dqo_mlp_gradients(ctx: Context, state: MlpState, X, XT, labels, loss_w, grads=None, loss=None, ldxt=None,
-                      stream=None):
+def dqo_mlp_gradients(ctx: Context, state: MlpState, X, labels, loss_w, grads=None, loss=None, stream=None):
     grads = torch.empty(MLP_PARAMS, device=X.device) if grads is None else grads
     loss = torch.empty(1, device=X.device) if loss is None else loss
     w = (c_f * 9)(*[float(v) for v in loss_w])
     _check("dqo_mlp_gradients",
-           load().dqo_mlp_gradients(ctx.handle, state.handle, X.shape[0], _ptr(X), _ptr(XT),
-                                    XT.shape[1] if ldxt is None else ldxt, _ptr(labels), C.cast(w, c_p),
+           load().dqo_mlp_gradients(ctx.handle, state.handle, X.shape[0], _ptr(X), _ptr(labels), C.cast(w, c_p),
                                     _ptr(grads), _ptr(loss), _stream(stream)), ctx.handle)
     return grads, loss
 
 
-def dqo_mlp_train_step(ctx: Context, state: MlpState, hp: dqo_mlp_hparams, X, XT, labels, loss=None, ldxt=None,
-                       stream=None):
-    """One Adam step on the batch X [n][128] (XT: a [128][ldxt] view whose first n columns are
-    this batch, passed as the tensor starting at the batch's first column)."""
+def dqo_mlp_train_step(ctx: Context, state: MlpState, hp: dqo_mlp_hparams, X, labels, loss=None, stream=None):
+    """One Adam step on the batch X [n][128] (contiguous rows; may be a row slice of a larger
+    feature matrix)."""
     _check("dqo_mlp_train_step",
-           load().dqo_mlp_train_step(ctx.handle, state.handle, C.byref(hp), X.shape[0], _ptr_any(X), _ptr_any(XT),
-                                     XT.shape[1] if ldxt is None else ldxt, _ptr(labels), _ptr(loss),
-                                     _stream(stream)), ctx.handle)
-
-
-def _ptr_any(t) -> int:
-    """Device pointer of a tensor that may be a strided view (row pitch passed separately)."""
-    if not t.is_cuda:
-        raise ValueError("tensor must be on a CUDA device")
-    return t.data_ptr()
+           load().dqo_mlp_train_step(ctx.handle, state.handle, C.byref(hp), X.shape[0], _ptr(X), _ptr(labels),
+                                     _ptr(loss), _stream(stream)), ctx.handle)
 
 
 def dqo_mlp_check(ctx: Context) -> bool:

@@ -58,9 +58,7 @@ class Trainer:
         dev = labels.device
         nq = d["q_ptr"].shape[0] - 1
         self.nq = nq
-        ldt = (nq + 7) // 8 * 8
         self.X = torch.empty(nq, dqo.MLP_FEATURES, dtype=torch.bfloat16, device=dev)
-        self.XT = torch.empty(dqo.MLP_FEATURES, ldt, dtype=torch.bfloat16, device=dev)
         self.counts = torch.empty(nq, dtype=torch.int32, device=dev)
         self.steps = n // batch
         self.loss = torch.zeros(self.steps, device=dev)
@@ -70,12 +68,11 @@ class Trainer:
         self.use_graph = use_graph
 
     def _epoch_body(self):
-        features(self.d, self.counts, self.X, self.XT, self.length_scale)
+        features(self.d, self.counts, self.X, None, self.length_scale)
         B = self.batch
         for i in range(self.steps):
             dqo.dqo_mlp_train_step(self.ctx, self.state, self.hp, self.X[i * B:(i + 1) * B],
-                                   self.XT[:, i * B:], self.labels[i * B:(i + 1) * B], self.loss[i:i + 1],
-                                   ldxt=self.XT.shape[1])
+                                   self.labels[i * B:(i + 1) * B], self.loss[i:i + 1])
 
     def epoch(self) -> float:
         """One pass over the samples with freshly drawn view counts; returns the mean batch loss."""

@@ -85,13 +85,6 @@ def _state(params):
     return st
 
 
-def _xt(X):
-    n = X.shape[0]
-    XT = torch.empty(128, n, dtype=torch.bfloat16, device="cuda")
-    XT.copy_(X.t())
-    return XT
-
-
 def test_forward_parity_with_ragged_tail():
     s, F, params, _ = _net_case(1103, 1000)            # 7 full tiles of 128 + 104 rows
     ctx = dqo.Context()
@@ -122,7 +115,7 @@ def test_gradients_parity():
     ctx = dqo.Context()
     st = _state(params)
     X = torch.from_numpy(F.astype(np.float32)).cuda().to(torch.bfloat16)
-    g, loss = dqo.dqo_mlp_gradients(ctx, st, X, _xt(X), torch.from_numpy(labels).cuda(), LOSS_W)
+    g, loss = dqo.dqo_mlp_gradients(ctx, st, X, torch.from_numpy(labels).cuda(), LOSS_W)
     g = g.cpu().numpy().astype(np.float64)
     ref, ref_loss = oracle.mlp_backward(F, labels, np.array(LOSS_W), params.astype(np.float64))
     assert abs(loss.item() - ref_loss) <= 1e-4 * ref_loss
@@ -138,7 +131,7 @@ def test_gradients_parity():
         assert np.all(e <= 5e-3 * np.maximum(rn, 1e-2 * rn.max())), (k, float((e / np.maximum(rn, 1e-2 * rn.max())).max()))
     assert np.all(g[33024 + 9 * 128:35072] == 0) and np.all(g[35072 + 9:] == 0)
     # the state's gradient buffer is left clean: a second call gives the same result
-    g2, _ = dqo.dqo_mlp_gradients(ctx, st, X, _xt(X), torch.from_numpy(labels).cuda(), LOSS_W)
+    g2, _ = dqo.dqo_mlp_gradients(ctx, st, X, torch.from_numpy(labels).cuda(), LOSS_W)
     assert np.abs(g2.cpu().numpy() - g).max() <= 1e-5 * np.abs(g).max()
     ctx.close()
 
@@ -148,12 +141,11 @@ def test_train_step_parity():
     ctx = dqo.Context()
     st = _state(params)
     X = torch.from_numpy(F.astype(np.float32)).cuda().to(torch.bfloat16)
-    XT = _xt(X)
     lab = torch.from_numpy(labels).cuda()
     lr = 1e-3
     hp = dqo.mlp_hparams(lr=lr, lr_final=lr, total_steps=0, loss_w=LOSS_W)
     loss = torch.zeros(1, device="cuda")
-    dqo.dqo_mlp_train_step(ctx, st, hp, X, XT, lab, loss)
+    dqo.dqo_mlp_train_step(ctx, st, hp, X, lab, loss)
     p1 = dqo.dqo_mlp_get_params(st).cpu().numpy().astype(np.float64)
     g, ref_loss = oracle.mlp_backward(F, labels, np.array(LOSS_W), params.astype(np.float64))
     r1, m, v = oracle.mlp_adam(params.astype(np.float64), g, 0, 0, 1, lr)
@@ -163,7 +155,7 @@ def test_train_step_parity():
     assert np.abs(p1 - r1)[clear].max() <= 1e-6 + 1e-3 * lr
     assert np.abs(p1 - r1).max() <= 2.0 * lr + 1e-6
     # the second step uses the updated BF16 copies and the advanced step count
-    dqo.dqo_mlp_train_step(ctx, st, hp, X, XT, lab, loss)
+    dqo.dqo_mlp_train_step(ctx, st, hp, X, lab, loss)
     g2, loss2 = oracle.mlp_backward(F, labels, np.array(LOSS_W), r1)
     assert abs(loss.item() - loss2) <= 2e-3 * loss2
     assert loss2 < ref_loss
@@ -175,7 +167,7 @@ def test_invalid_arguments():
     st = dqo.MlpState()
     X = torch.zeros(100, 128, dtype=torch.bfloat16, device="cuda")       # not a multiple of 128
     with pytest.raises(dqo.DqoError):
-        dqo.dqo_mlp_gradients(ctx, st, X, _xt(X), torch.zeros(100, 9, device="cuda"), LOSS_W)
+        dqo.dqo_mlp_gradients(ctx, st, X, torch.zeros(100, 9, device="cuda"), LOSS_W)
     with pytest.raises(dqo.DqoError):
         dqo.dqo_mlp_features(torch.zeros(1, 12, device="cuda"), torch.zeros(2, dtype=torch.int32, device="cuda"),
                              torch.zeros(0, dtype=torch.int32, device="cuda"), torch.zeros(0, 4, device="cuda"),
