@@ -817,12 +817,13 @@ def learned_section(ctx, dev, stream, world, fd, nfit, plain_fit_ms, fq):
     dqo.dqo_mlp_set_params(st, torch.from_numpy(synth.mlp_init_params(SEED + 3)).to(dev))
     tr = proposal.Trainer(ctx, st, d, labels, batch=MLP_BATCH, epochs=MLP_EPOCHS, length_scale=s["length_scale"],
                           lr=2e-3, lr_final=1e-5)
-    first = tr.epoch()                         # eager epoch, then captured
+    first = tr.epoch()                         # warm-up epoch (sizes the context's workspace)
     torch.cuda.synchronize()
     e0.record(stream)
-    hist = [tr.epoch() for _ in range(MLP_EPOCHS - 1)]
+    hist = [tr.epoch_async() for _ in range(MLP_EPOCHS - 1)]
     e1.record(stream)
     torch.cuda.synchronize()
+    hist = [float(v) for v in hist]
     train_ms = e0.elapsed_time(e1) / (MLP_EPOCHS - 1)
     samples = tr.steps * MLP_BATCH
     flops = MLP_FLOPS_PER_SAMPLE * samples

@@ -475,24 +475,35 @@ DQO_API dqo_status dqo_mlp_forward(dqo_ctx* ctx, const void* state, int64_t n, c
                                    dqo_stream stream);
 
 /* Loss L = (1/n) sum_rows sum_j loss_w[j] (y_j - labels_j)^2 of a batch and its gradient
- * w.r.t. the parameter vector.  n > 0, n % 128 == 0.  X [n][128] BF16 (16-byte aligned);
- * labels [n][9] fp32 (16-byte aligned); loss_w: 9 host floats.  grads (device, DQO_MLP_PARAMS) and loss
- * (device, 1 float) are OVERWRITTEN.  Backward precision: dL/dy rounded to BF16,
- * hidden-layer gradients rounded to BF16 after the ReLU derivative (the activation > 0);
- * weight and bias gradients accumulate in FP32.  One fused launch computes each 128-sample
- * block's gradient (every product of the step on tensor cores, intermediates in shared
- * memory, transposed operands read in place); the blocks' gradients are summed in block
- * order, so the result is the same on every run.
- * Errors: DQO_EINVAL, DQO_ECUDA (a tensor-core wait that ran out is reported by
- * dqo_mlp_check). */
+ * w.r.t. the parameter vector.  n > 0, n % 128 == 0.  X [n][128] BF16 and labels [n][9]
+ * fp32 (device, 16-byte aligned); loss_w: 9 host floats.  grads (device, DQO_MLP_PARAMS,
+ * 16-byte aligned) and loss (device, 1 float) are OVERWRITTEN.  Backward precision: dL/dy
+ * rounded to BF16, hidden-layer gradients rounded to BF16 after the ReLU derivative (the
+ * activation > 0); weight and bias gradients accumulate in FP32.  Each 128-sample tile's
+ * gradient comes from one CTA (every product on tensor cores, intermediates in shared
+ * memory); the tiles' gradients are summed in tile order, so the result is the same on
+ * every run.  One cooperative launch of one CTA per SM (the GPU must be able to hold the
+ * whole grid at once).
+ * Errors: DQO_EINVAL, DQO_ECUDA (a wait that ran out is reported by dqo_mlp_check). */
 DQO_API dqo_status dqo_mlp_gradients(dqo_ctx* ctx, void* state, int64_t n, const uint16_t* X, const float* labels,
                                      const float* loss_w, float* grads, float* loss, dqo_stream stream);
 
-/* One Adam step on a batch (as dqo_mlp_gradients, then the update; the learning rate
- * follows hp's cosine schedule at the state's step count).  loss (device, 1 float) is
- * OVERWRITTEN with the batch loss before the update; may be NULL.  Allocates nothing once
- * the context has seen a batch of this size, so a sequence of steps can be captured in a
- * CUDA graph after one call.  Errors: as dqo_mlp_gradients. */
+/* `steps` Adam steps, step k on rows [k batch, (k + 1) batch) of X [steps * batch][128]
+ * BF16 and labels [steps * batch][9] fp32 (device, 16-byte aligned; batch % 128 == 0).
+ * Each step is dqo_mlp_gradients' gradient of its batch followed by the Adam update (the
+ * learning rate follows hp's cosine schedule at the state's step count, which advances by
+ * one per step).  losses (device, `steps` floats, may be NULL) are OVERWRITTEN with each
+ * step's batch loss before its update.  One cooperative launch runs all the steps: per step
+ * the tiles' gradients, a grid-wide barrier, Adam on a slice of the parameters per CTA, a
+ * grid-wide barrier.  The result equals `steps` calls of dqo_mlp_train_step on the same
+ * batches.  Allocates nothing once the context has seen a batch of this size.
+ * Errors: as dqo_mlp_gradients. */
+DQO_API dqo_status dqo_mlp_train_steps(dqo_ctx* ctx, void* state, const dqo_mlp_hparams* hp, int32_t steps,
+                                       int64_t batch, const uint16_t* X, const float* labels, float* losses,
+                                       dqo_stream stream);
+
+/* One Adam step on a batch of n rows: dqo_mlp_train_steps with steps = 1; loss (device,
+ * 1 float, may be NULL) is OVERWRITTEN with the batch loss before the update. */
 DQO_API dqo_status dqo_mlp_train_step(dqo_ctx* ctx, void* state, const dqo_mlp_hparams* hp, int64_t n,
                                       const uint16_t* X, const float* labels, float* loss, dqo_stream stream);
 

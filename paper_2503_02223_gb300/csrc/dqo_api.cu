@@ -1144,6 +1144,7 @@ dqo_status mlp_work(dqo_ctx* c, int64_t n, MlpWork* wk) {
   wk->h1 = reinterpret_cast<__nv_bfloat16*>(b);
   wk->h2 = reinterpret_cast<__nv_bfloat16*>(b + big);
   wk->err = reinterpret_cast<int*>(b + 2 * big);
+  wk->bar = reinterpret_cast<unsigned*>(b + 2 * big + 64);
   wk->gpart = reinterpret_cast<float*>(b + 2 * big + kAlign);
   if (grow) DQO_CUDA(c, cudaMemset(wk->err, 0, sizeof(int)));
   c->mlp_n = nn;
@@ -1206,41 +1207,44 @@ dqo_status dqo_mlp_forward(dqo_ctx* c, const void* state, int64_t n, const uint1
 
 dqo_status dqo_mlp_gradients(dqo_ctx* c, void* state, int64_t n, const uint16_t* X, const float* labels,
                              const float* loss_w, float* grads, float* loss, dqo_stream stream_) {
-  if (!c || !state || !loss_w || !grads || !loss || (reinterpret_cast<uintptr_t>(state) % kAlign) != 0)
+  if (!c || !state || !loss_w || !grads || !loss || (reinterpret_cast<uintptr_t>(state) % kAlign) != 0 ||
+      !aligned16(grads))
     return DQO_EINVAL;
   dqo_status st = check_batch(n, X, labels);
   if (st != DQO_OK) return st;
   DQO_CUDA(c, cudaSetDevice(c->device));
   MlpWork wk;
   if ((st = mlp_work(c, n, &wk)) != DQO_OK) return st;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
-  const MlpState ms = state_view(state);
-  DQO_CUDA(c, cudaMemsetAsync(loss, 0, sizeof(float), s));
-  DQO_CUDA(c, launch_mlp_backward_fused(ms, wk.err, wk.gpart, n, X, labels, loss_w, loss, nullptr, s));
-  DQO_CUDA(c, launch_mlp_sum_partials(wk.gpart, (int)(n / 128), grads, s));
-  c->launches += 2;
+  dqo_mlp_hparams hp{};
+  for (int j = 0; j < 9; ++j) hp.loss_w[j] = loss_w[j];
+  DQO_CUDA(c, launch_mlp_train(state_view(state), hp, true, 1, n, X, labels, loss, grads, wk,
+                               reinterpret_cast<cudaStream_t>(stream_)));
+  c->launches += 1;
+  return DQO_OK;
+}
+
+dqo_status dqo_mlp_train_steps(dqo_ctx* c, void* state, const dqo_mlp_hparams* hp, int32_t steps, int64_t batch,
+                               const uint16_t* X, const float* labels, float* losses, dqo_stream stream_) {
+  if (!c || !state || !hp || steps < 0 || (reinterpret_cast<uintptr_t>(state) % kAlign) != 0) return DQO_EINVAL;
+  if (!(hp->lr >= 0.f) || !(hp->lr_final >= 0.f) || !(hp->beta1 >= 0.f && hp->beta1 < 1.f) ||
+      !(hp->beta2 >= 0.f && hp->beta2 < 1.f) || !(hp->eps > 0.f))
+    return DQO_EINVAL;
+  if (steps == 0) return DQO_OK;
+  if (batch <= 0 || (int64_t)steps * batch > (int64_t(1) << 30)) return DQO_EINVAL;
+  dqo_status st = check_batch(batch, X, labels);
+  if (st != DQO_OK) return st;
+  DQO_CUDA(c, cudaSetDevice(c->device));
+  MlpWork wk;
+  if ((st = mlp_work(c, batch, &wk)) != DQO_OK) return st;
+  DQO_CUDA(c, launch_mlp_train(state_view(state), *hp, false, steps, batch, X, labels, losses, nullptr, wk,
+                               reinterpret_cast<cudaStream_t>(stream_)));
+  c->launches += 1;
   return DQO_OK;
 }
 
 dqo_status dqo_mlp_train_step(dqo_ctx* c, void* state, const dqo_mlp_hparams* hp, int64_t n, const uint16_t* X,
                               const float* labels, float* loss, dqo_stream stream_) {
-  if (!c || !state || !hp || (reinterpret_cast<uintptr_t>(state) % kAlign) != 0) return DQO_EINVAL;
-  if (!(hp->lr >= 0.f) || !(hp->lr_final >= 0.f) || !(hp->beta1 >= 0.f && hp->beta1 < 1.f) ||
-      !(hp->beta2 >= 0.f && hp->beta2 < 1.f) || !(hp->eps > 0.f))
-    return DQO_EINVAL;
-  dqo_status st = check_batch(n, X, labels);
-  if (st != DQO_OK) return st;
-  DQO_CUDA(c, cudaSetDevice(c->device));
-  MlpWork wk;
-  if ((st = mlp_work(c, n, &wk)) != DQO_OK) return st;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
-  const MlpState ms = state_view(state);
-  float* lp = loss;
-  if (lp) DQO_CUDA(c, cudaMemsetAsync(lp, 0, sizeof(float), s));
-  DQO_CUDA(c, launch_mlp_backward_fused(ms, wk.err, wk.gpart, n, X, labels, hp->loss_w, lp, ms.step, s));
-  DQO_CUDA(c, launch_mlp_adam(ms, *hp, wk.gpart, (int)(n / 128), s));
-  c->launches += 2;
-  return DQO_OK;
+  return dqo_mlp_train_steps(c, state, hp, 1, n, X, labels, loss, stream_);
 }
 
 dqo_status dqo_mlp_check(dqo_ctx* c, int* timed_out) {

@@ -370,29 +370,37 @@ constexpr int kMlpViews = 8, kMlpIn = 128, kMlpHidden = 128, kMlpOut = 9, kMlpOu
 constexpr int kMlpW1 = 0, kMlpB1 = 16384, kMlpW2 = 16512, kMlpB2 = 32896, kMlpW3 = 33024, kMlpB3 = 35072,
               kMlpParams = 35088;
 
+// Element offset of (r, c) in a BF16 weight copy [R][128] kept in the tensor-core tile layout:
+// column blocks of 8, each R rows of 8 contiguous values (the kernels copy it unchanged into
+// shared memory).
+__host__ __device__ __forceinline__ int grid_index(int r, int c, int R) { return (c >> 3) * R * 8 + r * 8 + (c & 7); }
+
 // Views into the caller-owned state buffer.
 struct MlpState {
   float *param, *grad, *m1, *m2;       // [kMlpParams] each
-  __nv_bfloat16 *w1b, *w2b;            // [128][128]: W1, W2
-  __nv_bfloat16* w3b;                  // W3 [16][128]
+  __nv_bfloat16 *w1b, *w2b;            // W1, W2 [128][128], tile layout (grid_index)
+  __nv_bfloat16* w3b;                  // W3 [16][128], tile layout
   int* step;                           // optimiser steps taken
 };
 
-// Context workspace: the forward's activations and the training step's partial gradients.
+// Context workspace: the forward's activations and the training kernel's per-tile gradients.
 struct MlpWork {
   __nv_bfloat16 *h1, *h2;  // [n][128]
   int* err;
-  float* gpart;  // [n / 128][kMlpParams]: the fused step's per-CTA gradients
+  unsigned* bar;           // the training kernel's grid barrier counter
+  float* gpart;            // [n / 128][kMlpParams]
 };
 
 __device__ __forceinline__ void write_bf16_copies(const MlpState& st, int i, float p) {
   const __nv_bfloat16 b = __float2bfloat16_rn(p);
   if (i < kMlpB1) {
-    st.w1b[i] = b;
+    st.w1b[grid_index(i / kMlpIn, i % kMlpIn, kMlpHidden)] = b;
   } else if (i >= kMlpW2 && i < kMlpB2) {
-    st.w2b[i - kMlpW2] = b;
+    const int k = i - kMlpW2;
+    st.w2b[grid_index(k / kMlpHidden, k % kMlpHidden, kMlpHidden)] = b;
   } else if (i >= kMlpW3 && i < kMlpB3) {
-    st.w3b[i - kMlpW3] = b;
+    const int k = i - kMlpW3;
+    st.w3b[grid_index(k / kMlpHidden, k % kMlpHidden, kMlpOutPad)] = b;
   }
 }
 
@@ -404,19 +412,12 @@ cudaError_t launch_mlp_features(int nq, int nv, const float* P, const int32_t* q
                                 int npairs, const float* obs, const int32_t* counts, float inv_scale, uint16_t* X,
                                 uint16_t* XT, int64_t ldt, cudaStream_t s);
 cudaError_t launch_mlp_set(const MlpState& st, const float* params, cudaStream_t s);
-// Adam on st.grad plus the fused step's partial gradients (gpart, nb CTAs; may be NULL / 0).
-cudaError_t launch_mlp_adam(const MlpState& st, const dqo_mlp_hparams& hp, const float* gpart, int nb,
-                            cudaStream_t s);
 cudaError_t launch_mlp_forward(const MlpState& st, const MlpWork& wk, int64_t n, const uint16_t* X, float* y,
                                cudaStream_t s);
-// Loss and gradients of a batch (n % 128 == 0) in one launch: the eight products of a step
-// fused per 128-sample CTA with the intermediates in shared memory.
-// Each CTA writes its gradient (all kMlpParams entries) to gpart[blockIdx][...]; the sum
-// over the n / 128 CTAs is taken by launch_mlp_adam or launch_mlp_sum_partials, in block
-// order (deterministic).
-cudaError_t launch_mlp_backward_fused(const MlpState& st, int* err, float* gpart, int64_t n, const uint16_t* X,
-                                      const float* labels, const float* loss_w, float* loss, int* step_inc,
-                                      cudaStream_t s);
-// out[i] = sum over the nb CTAs of gpart[b][i].
-cudaError_t launch_mlp_sum_partials(const float* gpart, int nb, float* out, cudaStream_t s);
+// Training: `steps` Adam steps on consecutive batches of `batch` rows of X / labels (the
+// per-step losses into losses[steps], may be NULL), or with grad_mode the loss gradient of
+// one batch into grads.  One cooperative launch (mlp_gemm_setup first).
+cudaError_t launch_mlp_train(const MlpState& st, const dqo_mlp_hparams& hp, bool grad_mode, int steps,
+                             int64_t batch, const uint16_t* X, const float* labels, float* losses, float* grads,
+                             const MlpWork& wk, cudaStream_t s);
 }  // namespace dqo

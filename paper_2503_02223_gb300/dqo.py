@@ -91,6 +91,7 @@ _SIGS = {
     "dqo_mlp_forward": (c_i32, [c_p, c_p, c_i64, c_p, c_p, c_p]),
     "dqo_mlp_gradients": (c_i32, [c_p, c_p, c_i64, c_p, c_p, c_p, c_p, c_p, c_p]),
     "dqo_mlp_train_step": (c_i32, [c_p, c_p, c_p, c_i64, c_p, c_p, c_p, c_p]),
+    "dqo_mlp_train_steps": (c_i32, [c_p, c_p, c_p, c_i32, c_i64, c_p, c_p, c_p, c_p]),
     "dqo_mlp_check": (c_i32, [c_p, c_p]),
     "dqo_wait_probe": (c_i32, [c_p, c_p]),
     "dqo_alu_probe": (c_i32, [c_i32, c_i32, c_p, C.POINTER(C.c_double), c_p]),
@@ -513,6 +514,20 @@ def dqo_mlp_train_step(ctx: Context, state: MlpState, hp: dqo_mlp_hparams, X, la
     _check("dqo_mlp_train_step",
            load().dqo_mlp_train_step(ctx.handle, state.handle, C.byref(hp), X.shape[0], _ptr(X), _ptr(labels),
                                      _ptr(loss), _stream(stream)), ctx.handle)
+
+
+def dqo_mlp_train_steps(ctx: Context, state: MlpState, hp: dqo_mlp_hparams, X, labels, batch: int, losses=None,
+                        stream=None):
+    """X.shape[0] // batch Adam steps in one launch, step k on rows [k batch, (k + 1) batch) of
+    X [steps * batch][128] and labels; losses (device, one float per step) may be None."""
+    steps = X.shape[0] // batch
+    if steps * batch != X.shape[0] or labels.shape[0] != X.shape[0]:
+        raise ValueError("X and labels must hold a whole number of batches")
+    if losses is not None and losses.numel() < steps:
+        raise ValueError("losses must hold one float per step")
+    _check("dqo_mlp_train_steps",
+           load().dqo_mlp_train_steps(ctx.handle, state.handle, C.byref(hp), steps, batch, _ptr(X), _ptr(labels),
+                                      _ptr(losses), _stream(stream)), ctx.handle)
 
 
 def dqo_mlp_check(ctx: Context) -> bool:

@@ -11,7 +11,6 @@ library's kernels.
 """
 from __future__ import annotations
 
-import numpy as np
 import torch
 
 from . import dqo
@@ -42,18 +41,20 @@ def features(d: dict, counts: torch.Tensor | None, X=None, XT=None, length_scale
 
 
 class Trainer:
-    """Adam training of the proposal network on a fixed sample set, one CUDA graph per epoch
-    (feature computation for the epoch's view counts + every batch's train step)."""
+    """Adam training of the proposal network on a fixed sample set: per epoch, the features
+    for freshly drawn view counts (one launch) and every batch's step (one launch of
+    `dqo_mlp_train_steps`)."""
 
     def __init__(self, ctx, state: dqo.MlpState, d: dict, labels: torch.Tensor, batch: int = 4096,
-                 epochs: int = 30, seed: int = 0, length_scale: float = 1.0, use_graph: bool = True,
-                 min_views: int = 2, max_views: int = 8, **hp):
+                 epochs: int = 30, seed: int = 0, length_scale: float = 1.0, min_views: int = 2,
+                 max_views: int = 8, **hp):
         n = labels.shape[0] // batch * batch
         if n == 0:
             raise ValueError("fewer samples than one batch")
         self.ctx, self.state, self.d, self.batch, self.n = ctx, state, d, batch, n
         self.labels = labels
-        self.rng = np.random.default_rng(seed)
+        self.gen = torch.Generator(device=labels.device)   # view counts are drawn on the device
+        self.gen.manual_seed(seed)
         self.min_views, self.max_views = min_views, max_views
         dev = labels.device
         nq = d["q_ptr"].shape[0] - 1
@@ -64,38 +65,20 @@ class Trainer:
         self.loss = torch.zeros(self.steps, device=dev)
         self.hp = dqo.mlp_hparams(total_steps=epochs * self.steps, **hp)
         self.length_scale = length_scale
-        self.graph = None
-        self.use_graph = use_graph
 
-    def _epoch_body(self):
+    def epoch_async(self) -> torch.Tensor:
+        """One pass over the samples with freshly drawn view counts, without waiting for it;
+        returns the mean batch loss as a device scalar."""
+        torch.randint(self.min_views, self.max_views + 1, (self.nq,), generator=self.gen, device=self.counts.device,
+                      dtype=torch.int32, out=self.counts)
         features(self.d, self.counts, self.X, None, self.length_scale)
-        B = self.batch
-        for i in range(self.steps):
-            dqo.dqo_mlp_train_step(self.ctx, self.state, self.hp, self.X[i * B:(i + 1) * B],
-                                   self.labels[i * B:(i + 1) * B], self.loss[i:i + 1])
+        dqo.dqo_mlp_train_steps(self.ctx, self.state, self.hp, self.X[:self.n], self.labels[:self.n], self.batch,
+                                self.loss)
+        return self.loss.mean()
 
     def epoch(self) -> float:
         """One pass over the samples with freshly drawn view counts; returns the mean batch loss."""
-        c = self.rng.integers(self.min_views, self.max_views + 1, self.nq).astype(np.int32)
-        self.counts.copy_(torch.from_numpy(c), non_blocking=False)
-        if not self.use_graph:
-            self._epoch_body()
-        else:
-            if self.graph is None:
-                # first epoch runs eagerly (sizes the context's workspace), then is captured
-                self._epoch_body()
-                torch.cuda.synchronize()
-                self.graph = torch.cuda.CUDAGraph()
-                s = torch.cuda.Stream()
-                s.wait_stream(torch.cuda.current_stream())
-                with torch.cuda.stream(s):
-                    with torch.cuda.graph(self.graph, stream=s, capture_error_mode="thread_local"):
-                        self._epoch_body()
-                torch.cuda.current_stream().wait_stream(s)
-                # the capture did not run the body: restore nothing, the eager epoch counted
-                return float(self.loss.mean().item())
-            self.graph.replay()
-        return float(self.loss.mean().item())
+        return float(self.epoch_async().item())
 
 
 def propose(ctx, state: dqo.MlpState, d: dict, counts: torch.Tensor | None = None, length_scale: float = 1.0):

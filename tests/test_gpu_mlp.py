@@ -130,9 +130,9 @@ def test_gradients_parity():
         e = np.linalg.norm(G - R, axis=1)
         assert np.all(e <= 5e-3 * np.maximum(rn, 1e-2 * rn.max())), (k, float((e / np.maximum(rn, 1e-2 * rn.max())).max()))
     assert np.all(g[33024 + 9 * 128:35072] == 0) and np.all(g[35072 + 9:] == 0)
-    # the state's gradient buffer is left clean: a second call gives the same result
+    # a second call gives the same result bit for bit (the tiles are summed in tile order)
     g2, _ = dqo.dqo_mlp_gradients(ctx, st, X, torch.from_numpy(labels).cuda(), LOSS_W)
-    assert np.abs(g2.cpu().numpy() - g).max() <= 1e-5 * np.abs(g).max()
+    assert np.array_equal(g2.cpu().numpy().astype(np.float64), g)
     ctx.close()
 
 
@@ -162,12 +162,66 @@ def test_train_step_parity():
     ctx.close()
 
 
+def test_train_steps_equal_single_steps():
+    """One launch of k steps = k single-step calls on the same batches: the parameters
+    bitwise (every sum is in a fixed order), the per-step losses up to the order of the
+    loss sum's atomic additions."""
+    s, F, params, labels = _net_case(1107, 3 * 512)
+    ctx = dqo.Context()
+    X = torch.from_numpy(F.astype(np.float32)).cuda().to(torch.bfloat16)
+    lab = torch.from_numpy(labels).cuda()
+    hp = dqo.mlp_hparams(lr=1e-3, lr_final=1e-4, total_steps=5, loss_w=LOSS_W)
+    st1 = _state(params)
+    loss1 = torch.zeros(3, device="cuda")
+    for k in range(3):
+        dqo.dqo_mlp_train_step(ctx, st1, hp, X[k * 512:(k + 1) * 512], lab[k * 512:(k + 1) * 512], loss1[k:k + 1])
+    st3 = _state(params)
+    loss3 = torch.zeros(3, device="cuda")
+    dqo.dqo_mlp_train_steps(ctx, st3, hp, X, lab, 512, loss3)
+    p1, p3 = dqo.dqo_mlp_get_params(st1).cpu().numpy(), dqo.dqo_mlp_get_params(st3).cpu().numpy()
+    assert np.array_equal(p1, p3)
+    assert torch.allclose(loss1, loss3, rtol=1e-6, atol=0)
+    # the steps continue the schedule: a fourth step from either state agrees too
+    dqo.dqo_mlp_train_step(ctx, st1, hp, X[:512], lab[:512])
+    dqo.dqo_mlp_train_steps(ctx, st3, hp, X[:512], lab[:512], 512)
+    assert np.array_equal(dqo.dqo_mlp_get_params(st1).cpu().numpy(), dqo.dqo_mlp_get_params(st3).cpu().numpy())
+    assert not dqo.dqo_mlp_check(ctx)
+    ctx.close()
+
+
+def test_gradients_parity_more_tiles_than_sms():
+    """160 tiles of 128 samples: more tiles than the GPU has SMs, so CTAs take several tiles
+    of the step (and the gradient still sums the tiles in tile order)."""
+    n = 160 * 128
+    s, F, params, labels = _net_case(1108, n)
+    ctx = dqo.Context()
+    st = _state(params)
+    X = torch.from_numpy(F.astype(np.float32)).cuda().to(torch.bfloat16)
+    g, loss = dqo.dqo_mlp_gradients(ctx, st, X, torch.from_numpy(labels).cuda(), LOSS_W)
+    g = g.cpu().numpy().astype(np.float64)
+    ref, ref_loss = oracle.mlp_backward(F, labels, np.array(LOSS_W), params.astype(np.float64))
+    assert abs(loss.item() - ref_loss) <= 1e-4 * ref_loss
+    rel = _block_rel(g, ref)
+    assert all(v < 2e-3 for v in rel.values()), rel
+    g2, _ = dqo.dqo_mlp_gradients(ctx, st, X, torch.from_numpy(labels).cuda(), LOSS_W)
+    assert np.array_equal(g2.cpu().numpy().astype(np.float64), g)      # same sums in the same order
+    assert not dqo.dqo_mlp_check(ctx)
+    ctx.close()
+
+
 def test_invalid_arguments():
     ctx = dqo.Context()
     st = dqo.MlpState()
     X = torch.zeros(100, 128, dtype=torch.bfloat16, device="cuda")       # not a multiple of 128
     with pytest.raises(dqo.DqoError):
         dqo.dqo_mlp_gradients(ctx, st, X, torch.zeros(100, 9, device="cuda"), LOSS_W)
+    hp = dqo.mlp_hparams(lr=1e-3, lr_final=1e-3, total_steps=0, loss_w=LOSS_W)
+    with pytest.raises(dqo.DqoError):                                      # batch not a multiple of 128
+        dqo.dqo_mlp_train_steps(ctx, st, hp, torch.zeros(200, 128, dtype=torch.bfloat16, device="cuda"),
+                                torch.zeros(200, 9, device="cuda"), 100)
+    with pytest.raises(ValueError):                                        # not a whole number of batches
+        dqo.dqo_mlp_train_steps(ctx, st, hp, torch.zeros(300, 128, dtype=torch.bfloat16, device="cuda"),
+                                torch.zeros(300, 9, device="cuda"), 128)
     with pytest.raises(dqo.DqoError):
         dqo.dqo_mlp_features(torch.zeros(1, 12, device="cuda"), torch.zeros(2, dtype=torch.int32, device="cuda"),
                              torch.zeros(0, dtype=torch.int32, device="cuda"), torch.zeros(0, 4, device="cuda"),
