@@ -17,6 +17,12 @@ constexpr int kMaskWords = kMaxObjects / 32;
 constexpr int kIdSlots = 16;           // per-tile object slots held in shared memory per round
 constexpr int kRadixBits = 8;
 constexpr int kRadixBins = 1 << kRadixBits;
+// Scratch words of a radix sort over `tiles` CTA tiles and `passes` passes: per pass the
+// digit histogram, its exclusive scan and every tile's look-back status row; per pass a
+// tile counter; a block counter of the histogram kernel; an error word.
+constexpr size_t onesweep_scratch_words(int64_t tiles, int passes) {
+  return (size_t)passes * kRadixBins * (size_t)(tiles + 2) + (size_t)passes + 2;
+}
 constexpr int kSortItems = 16;         // keys per thread in the radix and scan kernels
 constexpr int kSortTile = kThreads * kSortItems;   // keys per CTA
 constexpr uint32_t kNoObject = 0x7FFFFFFFu;

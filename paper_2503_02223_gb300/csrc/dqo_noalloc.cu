@@ -31,7 +31,7 @@ constexpr int64_t kNoAllocMaxBlocks = kNoAllocMaxKeys / 2048;
 // layout: keys_a | keys_b | vals_b (uint32 each) | sort scratch (histograms, look-back status
 // of up to 8 passes, counters) | error word (256 bytes reserved)
 constexpr size_t kKeysBytes = sizeof(uint32_t) * kNoAllocMaxKeys;
-constexpr size_t kHistWords = (size_t)kMaxRadixPasses * kRadixBins * (kNoAllocMaxBlocks + 1) + kMaxRadixPasses + 1;
+constexpr size_t kHistWords = onesweep_scratch_words(kNoAllocMaxBlocks, kMaxRadixPasses);
 constexpr size_t kHistBytes = (sizeof(uint32_t) * kHistWords + 255) / 256 * 256;
 constexpr size_t kErrBytes = 256;
 constexpr size_t kScratchBytes = 3 * kKeysBytes + kHistBytes + kErrBytes;

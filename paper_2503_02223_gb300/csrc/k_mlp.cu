@@ -193,10 +193,25 @@ __device__ __forceinline__ void load_rows_grid(unsigned char* dst, const __nv_bf
     }
   }
 }
-// Contiguous copy of `bytes` (multiple of 16) from global to shared memory.
+// Contiguous copy of `bytes` (multiple of 16) from global to shared memory, eight 16-byte
+// loads per thread in flight before the first store.
 __device__ __forceinline__ void copy_contig(unsigned char* dst, const void* __restrict__ src, int bytes) {
+  constexpr int kUnroll = 8;
   const uint4* s4 = reinterpret_cast<const uint4*>(src);
-  for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) reinterpret_cast<uint4*>(dst)[i] = __ldg(s4 + i);
+  const int total = bytes / 16;
+  for (int base = threadIdx.x; base < total; base += kUnroll * blockDim.x) {
+    uint4 v[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int i = base + u * blockDim.x;
+      if (i < total) v[u] = __ldg(s4 + i);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int i = base + u * blockDim.x;
+      if (i < total) reinterpret_cast<uint4*>(dst)[i] = v[u];
+    }
+  }
 }
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }

@@ -169,10 +169,13 @@ __device__ __forceinline__ int64_t live_count(int64_t n, const uint64_t* n_dev) 
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kCountMask = (1u << 30) - 1;
 constexpr int kLookBatch = 8;   // predecessors a digit's look-back reads per round trip
 
+// Digit histograms of every pass; the last block to finish turns them into each pass's
+// exclusive digit offsets gex[pass][digit] (done: a block counter, zero before the launch).
 template <typename K, int IPT>
 __global__ void __launch_bounds__(kThreads) k_onesweep_hist(const K* __restrict__ keys, int64_t n_cap,
                                                             const uint64_t* __restrict__ n_dev, int begin_bit,
-                                                            int passes, uint32_t* __restrict__ ghist) {
+                                                            int passes, uint32_t* __restrict__ ghist,
+                                                            uint32_t* __restrict__ gex, uint32_t* __restrict__ done) {
   pdl_wait();
   pdl_trigger();
   __shared__ uint32_t h[kMaxRadixPasses][kRadixBins];
@@ -180,19 +183,35 @@ __global__ void __launch_bounds__(kThreads) k_onesweep_hist(const K* __restrict_
   __syncthreads();
   const int64_t n = live_count(n_cap, n_dev);
   const int64_t base = (int64_t)blockIdx.x * (kThreads * IPT);
+  K key[IPT];
+#pragma unroll
+  for (int k = 0; k < IPT; ++k) {   // the loads first, all in flight together
+    const int64_t i = base + k * kThreads + threadIdx.x;
+    key[k] = i < n ? keys[i] : K(0);
+  }
 #pragma unroll
   for (int k = 0; k < IPT; ++k) {
     const int64_t i = base + k * kThreads + threadIdx.x;
-    if (i < n) {
-      const K key = keys[i];
+    if (i < n)
       for (int p = 0; p < passes; ++p)
-        atomicAdd(&h[p][(uint32_t)(key >> (begin_bit + p * kRadixBits)) & (kRadixBins - 1)], 1u);
-    }
+        atomicAdd(&h[p][(uint32_t)(key[k] >> (begin_bit + p * kRadixBits)) & (kRadixBins - 1)], 1u);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < passes * kRadixBins; i += kThreads) {
     const uint32_t c = (&h[0][0])[i];
     if (c) atomicAdd(ghist + i, c);
+  }
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int p = 0; p < passes; ++p) {   // kThreads == kRadixBins: thread t owns digit t
+    uint32_t tot;
+    gex[p * kRadixBins + threadIdx.x] =
+        block_exclusive_scan<uint32_t>(__ldcg(ghist + p * kRadixBins + threadIdx.x), tot);
   }
 }
 
@@ -202,7 +221,7 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// One pass.  ghist: this pass's 256 global digit counts; status: [tiles][256] words, zero
+// One pass.  gex_in: this pass's 256 global digit starts; status: [tiles][256] words, zero
 // before the pass; counter: this pass's tile counter, zero before the pass.  rank (optional,
 // with values): rank[value] = destination.  err: set to 1 if a look-back wait gave up.
 template <typename K, bool kVals, int IPT>
@@ -210,35 +229,47 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep_pass(const K* __restri
                                                             const uint32_t* __restrict__ vin,
                                                             uint32_t* __restrict__ vout, int64_t n_cap,
                                                             const uint64_t* __restrict__ n_dev, int shift,
-                                                            const uint32_t* __restrict__ ghist,
+                                                            const uint32_t* __restrict__ gex_in,
                                                             uint32_t* __restrict__ status,
                                                             uint32_t* __restrict__ counter,
                                                             uint32_t* __restrict__ rank, uint32_t* __restrict__ err,
                                                             const PairOut po) {
-  pdl_wait();
-  pdl_trigger();
   __shared__ uint32_t cnt[kThreads / 32][kRadixBins];
   __shared__ uint32_t s_base[kRadixBins], s_lstart[kRadixBins];
   __shared__ K s_key[kThreads * IPT];
   __shared__ uint32_t s_val[kVals ? kThreads * IPT : 1];
   __shared__ uint32_t s_tile;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, t = threadIdx.x;
+  // the tile index and the counters do not depend on the previous kernel: taken while it
+  // drains (the counter was cleared before the sort's first kernel)
   if (t == 0) s_tile = atomicAdd(counter, 1u);
   for (int d = t; d < (kThreads / 32) * kRadixBins; d += kThreads) (&cnt[0][0])[d] = 0;
+  pdl_wait();
+  pdl_trigger();
   __syncthreads();
   const uint32_t tile = s_tile;
   const int64_t n = live_count(n_cap, n_dev);
+  // tiles past the live count (launches sized for a capacity) have nothing to do; every tile
+  // after them is empty too, so no look-back ever reads their status
+  if ((int64_t)tile * (kThreads * IPT) >= n && tile > 0) return;
+  const uint32_t gex = gex_in[t];   // the digit's global start (exclusive scan of the histogram)
   const int64_t wbase = (int64_t)tile * (kThreads * IPT) + (int64_t)warp * 32 * IPT;
   K key[IPT];
   uint32_t val[IPT];
   uint32_t pos[IPT];
   const uint32_t lt = lanemask_lt();
+  // every load of the tile first (all in flight together), then the ranking
 #pragma unroll
   for (int r = 0; r < IPT; ++r) {
     const int64_t i = wbase + r * 32 + lane;
     const bool ok = i < n;
     key[r] = ok ? kin[i] : K(0);
     if (kVals) val[r] = ok ? vin[i] : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < IPT; ++r) {
+    const int64_t i = wbase + r * 32 + lane;
+    const bool ok = i < n;
     const uint32_t d = (uint32_t)(key[r] >> shift) & (kRadixBins - 1);
     const uint32_t active = __ballot_sync(0xFFFFFFFFu, ok);
     uint32_t peers = __match_any_sync(0xFFFFFFFFu, ok ? d : 0xFFFFFFFFu);
@@ -268,9 +299,18 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep_pass(const K* __restri
   // the digit's start within the tile (keys of the tile in digit order)
   uint32_t tile_n;
   s_lstart[t] = block_exclusive_scan<uint32_t>(total, tile_n);
-  // the digit's global start: exclusive scan of the pass's histogram over digits
-  uint32_t gtot;
-  const uint32_t gex = block_exclusive_scan<uint32_t>(ghist[t], gtot);
+  __syncthreads();   // every digit's start is read below
+  // stage the tile's keys in digit order (local information only, so before the look-back,
+  // which then holds few registers); each digit's run is written out contiguously below
+  // (consecutive threads, consecutive addresses) instead of one scattered key per lane
+#pragma unroll
+  for (int r = 0; r < IPT; ++r) {
+    if (pos[r] == 0xFFFFFFFFu) continue;
+    const uint32_t d = (uint32_t)(key[r] >> shift) & (kRadixBins - 1);
+    const uint32_t li = s_lstart[d] + cnt[warp][d] + pos[r];
+    s_key[li] = key[r];
+    if (kVals) s_val[li] = val[r];
+  }
   uint32_t excl = 0;
   if (tile > 0) {
     // kLookBatch predecessors per round trip (independent loads in flight together): the
@@ -308,17 +348,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep_pass(const K* __restri
     st[(int64_t)tile * kRadixBins + t] = kFlagInc | (excl + total);
   }
   s_base[t] = gex + excl;
-  __syncthreads();
-  // stage the tile's keys in digit order, then write each digit's run out contiguously
-  // (consecutive threads, consecutive addresses) instead of one scattered key per lane
-#pragma unroll
-  for (int r = 0; r < IPT; ++r) {
-    if (pos[r] == 0xFFFFFFFFu) continue;
-    const uint32_t d = (uint32_t)(key[r] >> shift) & (kRadixBins - 1);
-    const uint32_t li = s_lstart[d] + cnt[warp][d] + pos[r];
-    s_key[li] = key[r];
-    if (kVals) s_val[li] = val[r];
-  }
   __syncthreads();
   for (uint32_t j = t; j < tile_n; j += kThreads) {
     const K k = s_key[j];
@@ -482,10 +511,6 @@ inline int sort_items(int64_t n) { return n < int64_t(current_sm_count()) * 4096
 
 // Scratch of one sort (uint32 words): [passes][256] histograms, [passes][tiles][256] status
 // words, [passes] tile counters and an error flag.
-inline size_t onesweep_words(int64_t tiles, int passes) {
-  return (size_t)passes * kRadixBins * (size_t)(tiles + 1) + (size_t)passes + 1;
-}
-
 // po (optional): the last pass writes the tile list and per-tile counts instead of keys.
 template <typename K, bool kVals, int IPT>
 cudaError_t radix_passes(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n, int begin_bit, int end_bit,
@@ -494,20 +519,22 @@ cudaError_t radix_passes(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n, in
   const unsigned nb = grid_for(n, kThreads * IPT);
   const int passes = (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;
   uint32_t* ghist = scratch;
-  uint32_t* status = ghist + (size_t)passes * kRadixBins;
+  uint32_t* gex = ghist + (size_t)passes * kRadixBins;
+  uint32_t* status = gex + (size_t)passes * kRadixBins;
   uint32_t* counters = status + (size_t)passes * nb * kRadixBins;
-  uint32_t* err = err_out ? err_out : counters + passes;
-  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * onesweep_words(nb, passes), s);
+  uint32_t* done = counters + passes;
+  uint32_t* err = err_out ? err_out : done + 1;
+  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * onesweep_scratch_words(nb, passes), s);
   if (e != cudaSuccess) return e;
-  launch_dep(k_onesweep_hist<K, IPT>, dim3(nb), dim3(kThreads), s, ka, n, n_dev, begin_bit, passes, ghist);
+  launch_dep(k_onesweep_hist<K, IPT>, dim3(nb), dim3(kThreads), s, ka, n, n_dev, begin_bit, passes, ghist, gex,
+             done);
   const PairOut none{nullptr, nullptr, nullptr, 0, 0u, 0u};
   K* kin = ka; K* kout = kb;
   uint32_t* vin = va; uint32_t* vout = vb;
   for (int p = 0; p < passes; ++p) {
     const bool last = p == passes - 1;
     launch_dep(k_onesweep_pass<K, kVals, IPT>, dim3(nb), dim3(kThreads), s, kin, kout, vin, vout, n, n_dev,
-                                                           begin_bit + p * kRadixBits,
-                                                           ghist + p * kRadixBins,
+                                                           begin_bit + p * kRadixBits, gex + p * kRadixBins,
                                                            status + (size_t)p * nb * kRadixBins, counters + p,
                                                            last ? rank : nullptr, err, last && po ? *po : none);
     std::swap(kin, kout);
@@ -556,7 +583,7 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, 
 
 size_t radix_scratch_words(int64_t n) {
   const int64_t m = n > 0 ? n : 1;
-  return onesweep_words(grid_for(m, kThreads * sort_items(m)), kMaxRadixPasses);
+  return onesweep_scratch_words(grid_for(m, kThreads * sort_items(m)), kMaxRadixPasses);
 }
 
 int64_t radix_sort_launches(int64_t n, int end_bit, int begin_bit) {
