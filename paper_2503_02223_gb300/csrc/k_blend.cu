@@ -624,6 +624,7 @@ __device__ __forceinline__ void ranges_from_counts(const uint32_t* __restrict__ 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // base: sum of the counts before the slice
   uint32_t b = 0;
+#pragma unroll 4
   for (uint32_t i = tid; i < first; i += kSchedThreads) b += counts[i];
   b = __reduce_add_sync(kFull, b);
   if (lane == 0) s_w[warp] = b;
@@ -634,11 +635,18 @@ __device__ __forceinline__ void ranges_from_counts(const uint32_t* __restrict__ 
     s_base = t;
   }
   __syncthreads();
-  // thread tid owns the contiguous chunk [tid * per, (tid + 1) * per) of the slice
+  // thread tid owns the contiguous chunk [tid * per, (tid + 1) * per) of the slice; chunks of
+  // up to kHeld counts are loaded once, together, and kept in registers
+  constexpr int kHeld = 8;
   const int per = (tiles + kSchedThreads - 1) / kSchedThreads;
   const int c0 = min(tid * per, tiles), c1 = min(c0 + per, tiles);
+  uint32_t held[kHeld];
+#pragma unroll
+  for (int k = 0; k < kHeld; ++k) held[k] = c0 + k < c1 ? counts[first + c0 + k] : 0u;
   uint32_t sum = 0;
-  for (int i = c0; i < c1; ++i) sum += counts[first + i];
+#pragma unroll
+  for (int k = 0; k < kHeld; ++k) sum += held[k];
+  for (int i = c0 + kHeld; i < c1; ++i) sum += counts[first + i];
   uint32_t inc = sum;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -659,7 +667,12 @@ __device__ __forceinline__ void ranges_from_counts(const uint32_t* __restrict__ 
   }
   __syncthreads();
   uint32_t run = s_base + s_w[warp] + inc - sum;
-  for (int i = c0; i < c1; ++i) {
+#pragma unroll
+  for (int k = 0; k < kHeld; ++k) {
+    if (c0 + k < c1) ranges[c0 + k] = make_uint2(run, run + held[k]);
+    run += held[k];
+  }
+  for (int i = c0 + kHeld; i < c1; ++i) {
     const uint32_t c = counts[first + i];
     ranges[i] = make_uint2(run, run + c);
     run += c;

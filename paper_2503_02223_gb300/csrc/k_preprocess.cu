@@ -136,20 +136,24 @@ __device__ __forceinline__ void footprint(const RasterParams& rp, const float me
   f.visible = true;
 }
 
-// Loads one Gaussian's [n,3] rows: whole warps with a 16-byte-aligned base stage the 96
-// floats of each array through shared memory as 24 float4 loads; others load scalars.
-__device__ __forceinline__ void load_rows3(const float* __restrict__ src, int64_t wbase, bool vec, int lane,
-                                           int64_t i, float* stage, float out[3]) {
+// A warp's 32 rows of an [n,3] array: whole warps with a 16-byte-aligned base load the 96
+// floats as 24 float4 loads (lanes 0..23, issued by load_rows3_vec) and pass them through
+// shared memory (take_rows3); others load scalars.
+__device__ __forceinline__ float4 load_rows3_vec(const float* __restrict__ src, int64_t wbase, bool vec, int lane) {
+  return vec && lane < 24 ? __ldg(reinterpret_cast<const float4*>(src + 3 * wbase) + lane)
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+__device__ __forceinline__ void take_rows3(const float* __restrict__ src, const float4 v, bool vec, int lane,
+                                           int64_t i, bool in, float* stage, float out[3]) {
   if (vec) {
     if (lane < 24) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(src + 3 * wbase) + lane);
       stage[4 * lane + 0] = v.x; stage[4 * lane + 1] = v.y;
       stage[4 * lane + 2] = v.z; stage[4 * lane + 3] = v.w;
     }
     __syncwarp();
     out[0] = stage[3 * lane]; out[1] = stage[3 * lane + 1]; out[2] = stage[3 * lane + 2];
     __syncwarp();
-  } else {
+  } else if (in) {
     out[0] = __ldg(src + 3 * i); out[1] = __ldg(src + 3 * i + 1); out[2] = __ldg(src + 3 * i + 2);
   }
 }
@@ -166,24 +170,35 @@ __device__ __forceinline__ void preprocess_item(const RasterParams& rp, const dq
   const bool vm = full && ((reinterpret_cast<uintptr_t>(g.means) & 15) == 0);
   const bool vl = full && ((reinterpret_cast<uintptr_t>(g.log_scales) & 15) == 0);
   const bool vc = full && ((reinterpret_cast<uintptr_t>(g.rgb) & 15) == 0);
-  if (full || in) {
-    if (vm || in) load_rows3(g.means, wbase, vm, lane, i, stage[warp], mean);
-    if (vl || in) load_rows3(g.log_scales, wbase, vl, lane, i, stage[warp], ls);
-    if (vc || in) load_rows3(g.rgb, wbase, vc, lane, i, stage[warp], rgb);
-  }
-  Footprint f;
-  f.visible = false;
+  // every load of the Gaussian first (all in flight together), then the staging
+  const float4 wm = load_rows3_vec(g.means, wbase, vm, lane);
+  const float4 wl = load_rows3_vec(g.log_scales, wbase, vl, lane);
+  const float4 wc = load_rows3_vec(g.rgb, wbase, vc, lane);
+  float4 q = make_float4(1.f, 0.f, 0.f, 0.f);
+  float logit = 0.f;
+  int32_t id = -1;
+  uint32_t flags = 0u;
   if (in) {
-    float4 q;
     if ((reinterpret_cast<uintptr_t>(g.quats) & 15) == 0) {
       q = __ldg(reinterpret_cast<const float4*>(g.quats) + i);
     } else {
       q = make_float4(g.quats[4 * i], g.quats[4 * i + 1], g.quats[4 * i + 2], g.quats[4 * i + 3]);
     }
-    footprint(rp, mean, ls, q, __ldg(g.opacity_logit + i), f);
-    const int32_t id = __ldg(g.obj_id + i);
+    logit = __ldg(g.opacity_logit + i);
+    id = __ldg(g.obj_id + i);
+    flags = __ldg(g.flags + i);
+  }
+  if (full || in) {
+    take_rows3(g.means, wm, vm, lane, i, in, stage[warp], mean);
+    take_rows3(g.log_scales, wl, vl, lane, i, in, stage[warp], ls);
+    take_rows3(g.rgb, wc, vc, lane, i, in, stage[warp], rgb);
+  }
+  Footprint f;
+  f.visible = false;
+  if (in) {
+    footprint(rp, mean, ls, q, logit, f);
     const bool has_obj = id >= 0 && id < rp.num_objects;
-    const uint32_t og = (__ldg(g.flags + i) & 1u) ? 0x80000000u : 0u;
+    const uint32_t og = (flags & 1u) ? 0x80000000u : 0u;
     const uint32_t idbits = (has_obj ? (uint32_t)id : kNoObject) | og;
     const float sc = -0.5f * kLog2e;
     const int64_t j = base + i;

@@ -382,30 +382,78 @@ __global__ void k_rank_scatter(const uint32_t* __restrict__ order, int64_t n, ui
   if (r < n) rank[order[r]] = (uint32_t)r;
 }
 
-// The warp writes the pairs of its 32 Gaussians together: lane l holds Gaussian l's tile
-// rectangle, first pair offset, pair count (0: none) and rank; one Gaussian at a time, the
-// lanes write its pairs row-major over its rectangle in strided (coalesced) order, so a
-// Gaussian covering many tiles does not leave the rest of its warp idle.
+// The CTA writes the pairs of its Gaussians together: thread l holds one Gaussian's tile
+// rectangle, first pair offset, pair count (0: none) and rank; pair k of a Gaussian is the
+// tile (k / w, k % w) of its rectangle, row-major.  A Gaussian with at least kBigPairs pairs
+// goes to a shared list that the whole CTA then writes one Gaussian at a time (consecutive
+// threads, consecutive pairs), so the largest footprint costs its pairs / kThreads steps.
+// The other Gaussians of a warp are numbered together, 0 .. small - 1 in lane order (a
+// prefix over their counts), and each lane writes every 32nd: pair j belongs to the last lane
+// whose prefix is <= j (a five-step search over the prefixes).  Called by every thread.
+constexpr uint32_t kBigPairs = 64;
+
 template <typename K>
-__device__ __forceinline__ void warp_emit(const ushort4 r, const uint64_t o, const uint32_t cnt, const K rk,
-                                          uint32_t tile_off, int ntx, int rank_bits, K* __restrict__ keys) {
+struct BigEmit {
+  uint64_t o;
+  K rk;
+  uint32_t cnt, w, t0, nt;
+  float iw;
+};
+
+// row q = floor(k / w): (k + 1/2) / w is at least 1/(2w) from an integer, so the float
+// product (relative error below 2^-22) rounds to q for k < 2^21; exact division past it
+template <typename K>
+__device__ __forceinline__ K pair_key(uint32_t k, uint32_t w, float iw, uint32_t t0, uint32_t nt, K rk,
+                                      int rank_bits) {
+  const uint32_t q = k < (1u << 21) ? __float2uint_rz(((float)k + 0.5f) * iw) : k / w;
+  return ((K)(t0 + q * nt + (k - q * w)) << rank_bits) | rk;
+}
+
+template <typename K>
+__device__ __forceinline__ void cta_emit(const ushort4 r, const uint64_t o, const uint32_t cnt, const K rk,
+                                         uint32_t tile_off, int ntx, int rank_bits, K* __restrict__ keys) {
+  __shared__ BigEmit<K> s_big[kThreads];
+  __shared__ uint32_t s_nbig;
   const int lane = threadIdx.x & 31;
-  uint32_t pending = __ballot_sync(0xFFFFFFFFu, cnt > 0);
-  while (pending) {
-    const int j = __ffs(pending) - 1;
-    pending &= pending - 1;
-    const uint32_t c = __shfl_sync(0xFFFFFFFFu, cnt, j);
-    const uint64_t oj = __shfl_sync(0xFFFFFFFFu, o, j);
-    const uint32_t x0 = __shfl_sync(0xFFFFFFFFu, (uint32_t)r.x, j);
-    const uint32_t y0 = __shfl_sync(0xFFFFFFFFu, (uint32_t)r.y, j);
-    const uint32_t w = __shfl_sync(0xFFFFFFFFu, (uint32_t)(r.z - r.x), j);
-    const K rj = __shfl_sync(0xFFFFFFFFu, rk, j);
-    const uint32_t toj = __shfl_sync(0xFFFFFFFFu, tile_off, j);   // the Gaussian's keyframe
-    const uint32_t ntxj = __shfl_sync(0xFFFFFFFFu, (uint32_t)ntx, j);
-    for (uint32_t k = lane; k < c; k += 32) {
-      const uint32_t ty = y0 + k / w, tx = x0 + k % w;
-      keys[oj + k] = ((K)(toj + ty * ntxj + tx) << rank_bits) | rj;
-    }
+  const uint32_t w = cnt ? (uint32_t)(r.z - r.x) : 1u;
+  const float inv_w = 1.f / (float)w;
+  const uint32_t first_tile = tile_off + (uint32_t)r.y * (uint32_t)ntx + (uint32_t)r.x;
+  if (threadIdx.x == 0) s_nbig = 0;
+  __syncthreads();
+  const bool big = cnt >= kBigPairs;
+  if (big) s_big[atomicAdd(&s_nbig, 1u)] = BigEmit<K>{o, rk, cnt, w, first_tile, (uint32_t)ntx, inv_w};
+  // the warp's small Gaussians
+  const uint32_t sc = big ? 0u : cnt;
+  uint32_t inc = sc;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+    if (lane >= d) inc += u;
+  }
+  const uint32_t ex = inc - sc;                                // this lane's first small pair
+  const uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
+  for (uint32_t base = 0; base < total; base += 32) {       // uniform over the warp
+    const uint32_t j = base + lane;
+    int own = 0;                                               // the last lane with prefix <= j
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1)
+      if (__shfl_sync(0xFFFFFFFFu, ex, own + step) <= j) own += step;
+    const uint32_t k = j - __shfl_sync(0xFFFFFFFFu, ex, own);
+    const uint32_t wo = __shfl_sync(0xFFFFFFFFu, w, own);
+    const float iw = __shfl_sync(0xFFFFFFFFu, inv_w, own);
+    const uint32_t t0 = __shfl_sync(0xFFFFFFFFu, first_tile, own);
+    const uint32_t nt = __shfl_sync(0xFFFFFFFFu, (uint32_t)ntx, own);
+    const uint64_t oo = __shfl_sync(0xFFFFFFFFu, o, own);
+    const K ro = __shfl_sync(0xFFFFFFFFu, rk, own);
+    if (j < total) keys[oo + k] = pair_key<K>(k, wo, iw, t0, nt, ro, rank_bits);
+  }
+  // the CTA's large Gaussians, by every thread
+  __syncthreads();
+  const uint32_t nbig = s_nbig;
+  for (uint32_t b = 0; b < nbig; ++b) {
+    const BigEmit<K> e = s_big[b];
+    for (uint32_t k = threadIdx.x; k < e.cnt; k += kThreads)
+      keys[e.o + k] = pair_key<K>(k, e.w, e.iw, e.t0, e.nt, e.rk, rank_bits);
   }
 }
 
@@ -431,7 +479,7 @@ __global__ void __launch_bounds__(kThreads) k_emit_pairs(const ushort4* __restri
       cnt = (uint32_t)(q.z - q.x) * (uint32_t)(q.w - q.y);
     }
   }
-  warp_emit<K>(q, o, cnt, (K)r, 0u, ntx, rank_bits, keys);
+  cta_emit<K>(q, o, cnt, (K)r, 0u, ntx, rank_bits, keys);
 }
 
 // The same over a batch of keyframes (joint rank r of all keyframes' Gaussians; the
@@ -471,7 +519,7 @@ __global__ void __launch_bounds__(kThreads) k_emit_pairs_batch(const __grid_cons
       }
     }
   }
-  warp_emit<K>(q, o, cnt, (K)r, t.kf[k].tile_off, t.kf[k].ntx, rank_bits, keys);
+  cta_emit<K>(q, o, cnt, (K)r, t.kf[k].tile_off, t.kf[k].ntx, rank_bits, keys);
 }
 
 template <typename K>
