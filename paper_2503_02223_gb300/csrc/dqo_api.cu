@@ -802,6 +802,14 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
   DQO_CUDA(c, cudaMemsetAsync(B.counters.p, 0, 32, s_));
   DQO_CUDA(c, cudaMemsetAsync(d_live, 0xFF, 8, s_));
   DQO_CUDA(c, cudaMemsetAsync(B.tile_count.p, 0, 4 * T, s_));   // the ranges are written from these
+  // the sorts' and the scan's scratch, cleared up front so that the chain from the projection
+  // to the blend runs kernel after kernel (programmatic launches, no copy engine between);
+  // a sizing call allocates the pair sort's scratch later and lets the sort clear it
+  DQO_CUDA(c, cudaMemsetAsync(B.depth_hist.p, 0, 4 * radix_scratch_used_words(N, 0, 32), s_));
+  DQO_CUDA(c, cudaMemsetAsync(B.scan_scratch.p, 0, 8 * scan_scratch_words(N), s_));
+  if (!sizing)
+    DQO_CUDA(c, cudaMemsetAsync(B.hist.p, 0, 4 * radix_scratch_used_words((int64_t)B.capacity, rank_bits, end_bit),
+                                s_));
   if (s->grads_zero) {
     // gradient buffers shared by several keyframes take atomic additions: clear them first
     // (once per buffer set); unshared ones are overwritten by the adjoint
@@ -867,10 +875,10 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
     PhaseTimer timer(c, DQO_PHASE_DEPTH_SORT, s_);
     DQO_CUDA(c, radix_sort_u32(as<uint32_t>(B.zkey_a), as<uint32_t>(B.zkey_b), as<uint32_t>(B.zval_a),
                                as<uint32_t>(B.zval_b), N, 32, as<uint32_t>(B.depth_hist), &sel, s_, nullptr,
-                               d_sort_err));
+                               d_sort_err, 0, true));
     order = sel ? as<uint32_t>(B.zval_b) : as<uint32_t>(B.zval_a);
     DQO_CUDA(c, launch_exclusive_scan(as<uint32_t>(B.ntiles), as<uint32_t>(B.offsets), N,
-                                      as<uint64_t>(B.scan_scratch), d_total, s_, d_sort_err, order));
+                                      as<uint64_t>(B.scan_scratch), d_total, s_, d_sort_err, order, true));
     launches += scan_launches(N) + radix_sort_launches(N, 32);
   }
 
@@ -912,10 +920,10 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
     int psel = 0;
     if (k32)
       DQO_CUDA(c, radix_sort_pairs_u32(as<uint32_t>(B.pair_a), as<uint32_t>(B.pair_b), (int64_t)cap, end_bit,
-                                       as<uint32_t>(B.hist), &psel, s_, d_live, d_sort_err, rank_bits, po));
+                                       as<uint32_t>(B.hist), &psel, s_, d_live, d_sort_err, rank_bits, po, !sizing));
     else
       DQO_CUDA(c, radix_sort_pairs_u64(as<uint64_t>(B.pair_a), as<uint64_t>(B.pair_b), (int64_t)cap, end_bit,
-                                       as<uint32_t>(B.hist), &psel, s_, d_live, d_sort_err, rank_bits, po));
+                                       as<uint32_t>(B.hist), &psel, s_, d_live, d_sort_err, rank_bits, po, !sizing));
     launches += 1 + radix_sort_launches((int64_t)cap, end_bit, rank_bits);
   }
 

@@ -23,8 +23,8 @@ constexpr int kRadixBins = 1 << kRadixBits;
 constexpr size_t onesweep_scratch_words(int64_t tiles, int passes) {
   return (size_t)passes * kRadixBins * (size_t)(tiles + 2) + (size_t)passes + 2;
 }
-constexpr int kSortItems = 16;         // keys per thread in the radix and scan kernels
-constexpr int kSortTile = kThreads * kSortItems;   // keys per CTA
+constexpr int kScanItems = 16;         // values per thread in the scan kernel
+constexpr int kScanTile = kThreads * kScanItems;   // values per CTA of the scan
 constexpr uint32_t kNoObject = 0x7FFFFFFFu;
 constexpr float kLog2e = 1.4426950408889634f;
 
@@ -222,11 +222,12 @@ cudaError_t launch_preprocess_backward_batch(const PreBwdTable& t, int nkf, int6
 
 // Exclusive scan of n uint32 values in[i] (in[gather[i]] when gather is given; one kernel,
 // decoupled look-back); total (uint64) written to *total.  scratch must hold
-// scan_scratch_words(n) uint64 words.  err (optional): set to 1 if a look-back wait gave up.
+// scan_scratch_words(n) uint64 words, cleared by the call unless `zeroed` says the caller
+// cleared them.  err (optional): set to 1 if a look-back wait gave up.
 size_t scan_scratch_words(int64_t n);
 cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint64_t* scratch,
                                   uint64_t* total, cudaStream_t s, uint32_t* err = nullptr,
-                                  const uint32_t* gather = nullptr);
+                                  const uint32_t* gather = nullptr, bool zeroed = false);
 
 // Stable LSD radix sort of n keys on bits [begin_bit, end_bit), optional uint32 values: one kernel
 // counts all digits, then one kernel per 8-bit digit with decoupled look-back.  Results
@@ -235,12 +236,15 @@ cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, 
 // (optional, with values): rank[value] = the value's position in the sorted order, written
 // by the last pass.  n_dev (optional): live count on the device, n being the capacity.
 // err (optional): set to 1 if a look-back wait gave up (about a second); NULL keeps the
-// flag inside scratch.
+// flag inside scratch.  The call clears the radix_scratch_used_words(n, begin_bit, end_bit)
+// words it uses first, unless `zeroed` says the caller already did (so that the sort's first
+// kernel follows the previous kernel directly).
 size_t radix_scratch_words(int64_t n);
+size_t radix_scratch_used_words(int64_t n, int begin_bit, int end_bit);
 int64_t radix_sort_launches(int64_t n, int end_bit, int begin_bit = 0);
 cudaError_t radix_sort_u32(uint32_t* keys_a, uint32_t* keys_b, uint32_t* vals_a, uint32_t* vals_b, int64_t n,
                            int end_bit, uint32_t* scratch, int* sel, cudaStream_t s, uint32_t* rank = nullptr,
-                           uint32_t* err = nullptr, int begin_bit = 0);
+                           uint32_t* err = nullptr, int begin_bit = 0, bool zeroed = false);
 cudaError_t radix_sort_u64(uint64_t* keys_a, uint64_t* keys_b, int64_t n, int end_bit, uint32_t* scratch, int* sel,
                            cudaStream_t s, const uint64_t* n_dev = nullptr, uint32_t* err = nullptr,
                            int begin_bit = 0);
@@ -295,10 +299,10 @@ struct PairOut {
 // Pair sorts whose last pass writes the tile list and the per-tile counts (po).
 cudaError_t radix_sort_pairs_u32(uint32_t* keys_a, uint32_t* keys_b, int64_t n, int end_bit, uint32_t* scratch,
                                  int* sel, cudaStream_t s, const uint64_t* n_dev, uint32_t* err, int begin_bit,
-                                 const PairOut& po);
+                                 const PairOut& po, bool zeroed = false);
 cudaError_t radix_sort_pairs_u64(uint64_t* keys_a, uint64_t* keys_b, int64_t n, int end_bit, uint32_t* scratch,
                                  int* sel, cudaStream_t s, const uint64_t* n_dev, uint32_t* err, int begin_bit,
-                                 const PairOut& po);
+                                 const PairOut& po, bool zeroed = false);
 
 cudaError_t launch_blend_forward(const BlendFwdArgs& a, bool with_id, cudaStream_t s);
 // Tile schedule: order[0..tiles) lists the tiles by decreasing cost (cost[t], or the

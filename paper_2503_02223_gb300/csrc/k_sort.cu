@@ -54,7 +54,7 @@ __device__ __forceinline__ uint64_t scan_ns() {
   return t;
 }
 
-// Single-pass exclusive scan with decoupled look-back: CTAs take tiles of 4096 values from
+// Single-pass exclusive scan with decoupled look-back: CTAs take tiles of kScanTile values from
 // an atomic counter, scan their tile, publish its sum (64-bit word: 2 flag bits, 62 value
 // bits) and add their predecessors' published sums back to the first inclusive prefix;
 // the last tile writes the total.  Waits give up after about a second (err).
@@ -68,24 +68,24 @@ __global__ void __launch_bounds__(kThreads) k_scan_lookback(const uint32_t* __re
                                                             uint32_t* __restrict__ err, uint64_t* __restrict__ total) {
   pdl_wait();
   pdl_trigger();
-  __shared__ uint32_t tile_s[kSortTile];
+  __shared__ uint32_t tile_s[kScanTile];
   __shared__ uint32_t s_tile;
   __shared__ uint64_t s_prefix;
   if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
   __syncthreads();
   const uint32_t tile = s_tile;
-  const int64_t base = (int64_t)tile * kSortTile;
+  const int64_t base = (int64_t)tile * kScanTile;
 #pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
+  for (int k = 0; k < kScanItems; ++k) {
     const int64_t i = base + k * kThreads + threadIdx.x;
     tile_s[k * kThreads + threadIdx.x] = i < n ? in[gather ? gather[i] : i] : 0u;
   }
   __syncthreads();
-  uint32_t v[kSortItems];
+  uint32_t v[kScanItems];
   uint32_t sum = 0;
 #pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
-    v[k] = tile_s[threadIdx.x * kSortItems + k];
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = tile_s[threadIdx.x * kScanItems + k];
     sum += v[k];
   }
   uint32_t tot;
@@ -128,19 +128,19 @@ __global__ void __launch_bounds__(kThreads) k_scan_lookback(const uint32_t* __re
     }
     if (lane == 0) {
       s_prefix = excl;
-      if (total && base + kSortTile >= n) *total = excl + tot;
+      if (total && base + kScanTile >= n) *total = excl + tot;
     }
   }
   __syncthreads();
   run += (uint32_t)s_prefix;
 #pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
-    tile_s[threadIdx.x * kSortItems + k] = run;
+  for (int k = 0; k < kScanItems; ++k) {
+    tile_s[threadIdx.x * kScanItems + k] = run;
     run += v[k];
   }
   __syncthreads();
 #pragma unroll
-  for (int k = 0; k < kSortItems; ++k) {
+  for (int k = 0; k < kScanItems; ++k) {
     const int64_t i = base + k * kThreads + threadIdx.x;
     if (i < n) out[i] = tile_s[k * kThreads + threadIdx.x];
   }
@@ -563,7 +563,7 @@ inline int sort_items(int64_t n) { return n < int64_t(current_sm_count()) * 4096
 template <typename K, bool kVals, int IPT>
 cudaError_t radix_passes(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n, int begin_bit, int end_bit,
                          uint32_t* scratch, int* sel, cudaStream_t s, const uint64_t* n_dev, uint32_t* rank,
-                         uint32_t* err_out, const PairOut* po) {
+                         uint32_t* err_out, const PairOut* po, bool zeroed) {
   const unsigned nb = grid_for(n, kThreads * IPT);
   const int passes = (end_bit - begin_bit + kRadixBits - 1) / kRadixBits;
   uint32_t* ghist = scratch;
@@ -572,8 +572,10 @@ cudaError_t radix_passes(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n, in
   uint32_t* counters = status + (size_t)passes * nb * kRadixBins;
   uint32_t* done = counters + passes;
   uint32_t* err = err_out ? err_out : done + 1;
-  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * onesweep_scratch_words(nb, passes), s);
-  if (e != cudaSuccess) return e;
+  if (!zeroed) {
+    const cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * onesweep_scratch_words(nb, passes), s);
+    if (e != cudaSuccess) return e;
+  }
   launch_dep(k_onesweep_hist<K, IPT>, dim3(nb), dim3(kThreads), s, ka, n, n_dev, begin_bit, passes, ghist, gex,
              done);
   const PairOut none{nullptr, nullptr, nullptr, 0, 0u, 0u};
@@ -595,7 +597,8 @@ cudaError_t radix_passes(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n, in
 template <typename K, bool kVals>
 cudaError_t radix_sort_impl(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n, int end_bit, uint32_t* hist,
                             int* sel, cudaStream_t s, const uint64_t* n_dev = nullptr, uint32_t* rank = nullptr,
-                            uint32_t* err = nullptr, int begin_bit = 0, const PairOut* po = nullptr) {
+                            uint32_t* err = nullptr, int begin_bit = 0, const PairOut* po = nullptr,
+                            bool zeroed = false) {
   *sel = 0;
   if (begin_bit < 0 || end_bit > (int)(8 * sizeof(K))) return cudaErrorInvalidValue;
   if (n <= 1 || end_bit <= begin_bit) {  // already in order: ranks from the values as they stand
@@ -605,24 +608,28 @@ cudaError_t radix_sort_impl(K* ka, K* kb, uint32_t* va, uint32_t* vb, int64_t n,
   }
   if (end_bit - begin_bit > kMaxRadixPasses * kRadixBits) return cudaErrorInvalidValue;
   if (sort_items(n) == 8)
-    return radix_passes<K, kVals, 8>(ka, kb, va, vb, n, begin_bit, end_bit, hist, sel, s, n_dev, rank, err, po);
-  return radix_passes<K, kVals, 16>(ka, kb, va, vb, n, begin_bit, end_bit, hist, sel, s, n_dev, rank, err, po);
+    return radix_passes<K, kVals, 8>(ka, kb, va, vb, n, begin_bit, end_bit, hist, sel, s, n_dev, rank, err, po,
+                                     zeroed);
+  return radix_passes<K, kVals, 16>(ka, kb, va, vb, n, begin_bit, end_bit, hist, sel, s, n_dev, rank, err, po,
+                                    zeroed);
 }
 
 }  // namespace
 
 // scratch: [tiles] look-back status words, a tile counter and an error flag (uint64 each)
-size_t scan_scratch_words(int64_t n) { return (size_t)grid_for(n > 0 ? n : 1, kSortTile) + 2; }
+size_t scan_scratch_words(int64_t n) { return (size_t)grid_for(n > 0 ? n : 1, kScanTile) + 2; }
 
 cudaError_t launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint64_t* scratch, uint64_t* total,
-                                  cudaStream_t s, uint32_t* err, const uint32_t* gather) {
+                                  cudaStream_t s, uint32_t* err, const uint32_t* gather, bool zeroed) {
   if (n <= 0) {
     if (total) return cudaMemsetAsync(total, 0, sizeof(uint64_t), s);
     return cudaSuccess;
   }
-  const unsigned nb = grid_for(n, kSortTile);
-  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(uint64_t) * (nb + 2), s);
-  if (e != cudaSuccess) return e;
+  const unsigned nb = grid_for(n, kScanTile);
+  if (!zeroed) {
+    const cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(uint64_t) * (nb + 2), s);
+    if (e != cudaSuccess) return e;
+  }
   uint32_t* counter = reinterpret_cast<uint32_t*>(scratch + nb);
   launch_dep(k_scan_lookback, dim3(nb), dim3(kThreads), s, in, gather, out, n, scratch, counter,
                                           err ? err : reinterpret_cast<uint32_t*>(scratch + nb + 1), total);
@@ -641,12 +648,18 @@ int64_t radix_sort_launches(int64_t n, int end_bit, int begin_bit) {
 
 cudaError_t radix_sort_u32(uint32_t* keys_a, uint32_t* keys_b, uint32_t* vals_a, uint32_t* vals_b, int64_t n,
                            int end_bit, uint32_t* scratch, int* sel, cudaStream_t s, uint32_t* rank, uint32_t* err,
-                           int begin_bit) {
+                           int begin_bit, bool zeroed) {
   if (vals_a)
     return radix_sort_impl<uint32_t, true>(keys_a, keys_b, vals_a, vals_b, n, end_bit, scratch, sel, s, nullptr,
-                                           rank, err, begin_bit);
+                                           rank, err, begin_bit, nullptr, zeroed);
   return radix_sort_impl<uint32_t, false>(keys_a, keys_b, nullptr, nullptr, n, end_bit, scratch, sel, s, nullptr,
-                                          nullptr, err, begin_bit);
+                                          nullptr, err, begin_bit, nullptr, zeroed);
+}
+
+size_t radix_scratch_used_words(int64_t n, int begin_bit, int end_bit) {
+  if (n <= 1 || end_bit <= begin_bit) return 0;
+  return onesweep_scratch_words(grid_for(n, kThreads * sort_items(n)),
+                                (end_bit - begin_bit + kRadixBits - 1) / kRadixBits);
 }
 
 cudaError_t radix_sort_u64(uint64_t* keys_a, uint64_t* keys_b, int64_t n, int end_bit, uint32_t* scratch, int* sel,
@@ -714,16 +727,16 @@ cudaError_t radix_sort_u32_dev(uint32_t* keys_a, uint32_t* keys_b, int64_t n, in
 
 cudaError_t radix_sort_pairs_u32(uint32_t* keys_a, uint32_t* keys_b, int64_t n, int end_bit, uint32_t* scratch,
                                  int* sel, cudaStream_t s, const uint64_t* n_dev, uint32_t* err, int begin_bit,
-                                 const PairOut& po) {
+                                 const PairOut& po, bool zeroed) {
   return radix_sort_impl<uint32_t, false>(keys_a, keys_b, nullptr, nullptr, n, end_bit, scratch, sel, s, n_dev,
-                                          nullptr, err, begin_bit, &po);
+                                          nullptr, err, begin_bit, &po, zeroed);
 }
 
 cudaError_t radix_sort_pairs_u64(uint64_t* keys_a, uint64_t* keys_b, int64_t n, int end_bit, uint32_t* scratch,
                                  int* sel, cudaStream_t s, const uint64_t* n_dev, uint32_t* err, int begin_bit,
-                                 const PairOut& po) {
+                                 const PairOut& po, bool zeroed) {
   return radix_sort_impl<uint64_t, false>(keys_a, keys_b, nullptr, nullptr, n, end_bit, scratch, sel, s, n_dev,
-                                          nullptr, err, begin_bit, &po);
+                                          nullptr, err, begin_bit, &po, zeroed);
 }
 
 
