@@ -512,11 +512,12 @@ DQO_API dqo_status dqo_mlp_train_step(dqo_ctx* ctx, void* state, const dqo_mlp_h
  * kernel then skipped its epilogue, freed its tensor memory and returned). */
 DQO_API dqo_status dqo_mlp_check(dqo_ctx* ctx, int* timed_out);
 
-/* Exercises the bounded device wait the tensor-core kernels use: one kernel waits on an
- * mbarrier that nothing arrives at, gives up after about one second and records it; the
- * call synchronises `stream` and returns DQO_ETIMEOUT (DQO_OK would mean the wait did not
- * give up).  The context stays usable afterwards.  No counterpart in the paper: this is
- * how a stalled completion is reported instead of hanging the GPU. */
+/* Exercises the bounded device waits the tensor-core kernels use: one kernel waits on an
+ * mbarrier that nothing arrives at, then on the training kernel's grid barrier with a
+ * count its single CTA never reaches; each gives up after about one second and records
+ * it.  The call synchronises `stream` and returns DQO_ETIMEOUT when both gave up (DQO_OK
+ * would mean one of them did not).  The context stays usable afterwards.  No counterpart
+ * in the paper: this is how a stalled completion is reported instead of hanging the GPU. */
 DQO_API dqo_status dqo_wait_probe(dqo_ctx* ctx, dqo_stream stream);
 
 /* Throughput probe of one arithmetic pipe, for the roofline the blend kernels are quoted

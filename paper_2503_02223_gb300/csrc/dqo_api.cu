@@ -1273,18 +1273,18 @@ dqo_status dqo_mlp_check(dqo_ctx* c, int* timed_out) {
 dqo_status dqo_wait_probe(dqo_ctx* c, dqo_stream stream_) {
   if (!c) return DQO_EINVAL;
   DQO_CUDA(c, cudaSetDevice(c->device));
-  int* flag = nullptr;
-  DQO_CUDA(c, cudaMalloc(&flag, sizeof(int)));
+  int* flag = nullptr;   // the probe's flag word and its grid-barrier counter
+  DQO_CUDA(c, cudaMalloc(&flag, 2 * sizeof(int)));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
   int v = 0;
-  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+  cudaError_t e = cudaMemsetAsync(flag, 0, 2 * sizeof(int), s);
   if (e == cudaSuccess) e = launch_bounded_wait_probe(flag, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&v, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(flag);
   if (e != cudaSuccess) return cuda_fail(c, e);
   c->launches += 1;
-  return v ? DQO_ETIMEOUT : DQO_OK;
+  return v == 3 ? DQO_ETIMEOUT : DQO_OK;   // both waits gave up
 }
 
 }  // extern "C"

@@ -23,7 +23,7 @@ constexpr int kRadixBins = 1 << kRadixBits;
 constexpr size_t onesweep_scratch_words(int64_t tiles, int passes) {
   return (size_t)passes * kRadixBins * (size_t)(tiles + 2) + (size_t)passes + 2;
 }
-constexpr int kScanItems = 16;         // values per thread in the scan kernel
+constexpr int kScanItems = 8;         // values per thread in the scan kernel
 constexpr int kScanTile = kThreads * kScanItems;   // values per CTA of the scan
 constexpr uint32_t kNoObject = 0x7FFFFFFFu;
 constexpr float kLog2e = 1.4426950408889634f;

@@ -565,11 +565,16 @@ __device__ __forceinline__ void schedule_tiles(const uint2* __restrict__ ranges,
   };
   for (int b = tid; b < kSchedBuckets; b += kSchedThreads) s_h[b] = 0u;
   __syncthreads();
+  // one round holds up to kSchedThreads * kSchedPer tiles: its buckets stay in registers for
+  // the placement below instead of being loaded again
+  const bool one_round = tiles <= kSchedThreads * kSchedPer;
+  int held[kSchedPer];
   for (int base = 0; base < tiles; base += kSchedThreads * kSchedPer) {
     int b[kSchedPer];
     buckets(base, b);
 #pragma unroll
     for (int j = 0; j < kSchedPer; ++j) {
+      held[j] = b[j];
       const uint32_t peers = __match_any_sync(kFull, b[j]);
       if (b[j] >= 0 && lane == __ffs(peers) - 1) atomicAdd(&s_h[b[j]], (uint32_t)__popc(peers));
     }
@@ -600,7 +605,12 @@ __device__ __forceinline__ void schedule_tiles(const uint2* __restrict__ ranges,
   __syncthreads();
   for (int base = 0; base < tiles; base += kSchedThreads * kSchedPer) {
     int b[kSchedPer];
-    buckets(base, b);
+    if (one_round) {
+#pragma unroll
+      for (int j = 0; j < kSchedPer; ++j) b[j] = held[j];
+    } else {
+      buckets(base, b);
+    }
 #pragma unroll
     for (int j = 0; j < kSchedPer; ++j) {
       const uint32_t peers = __match_any_sync(kFull, b[j]);
@@ -688,8 +698,12 @@ __global__ void __launch_bounds__(kSchedThreads) k_tile_schedule(const uint2* __
                                                                  const uint32_t* __restrict__ counts) {
   pdl_wait();
   pdl_trigger();
-  if (counts) ranges_from_counts(counts, 0u, tiles, const_cast<uint2*>(ranges));
-  schedule_tiles(ranges, cost, group, tiles, order);
+  if (counts) {
+    ranges_from_counts(counts, 0u, tiles, const_cast<uint2*>(ranges));
+    schedule_tiles(nullptr, cost ? cost : counts, cost ? group : 1, tiles, order);   // list length = count
+  } else {
+    schedule_tiles(ranges, cost, group, tiles, order);
+  }
 }
 
 // Sum over the warp of 10 per-lane values, transposing as it halves: stage 1 (lanes l and
@@ -1077,8 +1091,13 @@ __global__ void __launch_bounds__(kSchedThreads) k_tile_schedule_batch(const __g
   const int k = blockIdx.x;
   const int tiles = (int)(t.tile_off[k + 1] - t.tile_off[k]);
   if (which == 0) {
-    if (t.tile_count) ranges_from_counts(t.tile_count, t.tile_off[k], tiles, const_cast<uint2*>(t.f[k].ranges));
-    schedule_tiles(t.f[k].ranges, nullptr, 1, tiles, const_cast<uint32_t*>(t.f[k].tile_order));
+    if (t.tile_count) {
+      // the ranges from the pair counts; a tile's cost (its list length) is its count
+      ranges_from_counts(t.tile_count, t.tile_off[k], tiles, const_cast<uint2*>(t.f[k].ranges));
+      schedule_tiles(nullptr, t.tile_count + t.tile_off[k], 1, tiles, const_cast<uint32_t*>(t.f[k].tile_order));
+    } else {
+      schedule_tiles(t.f[k].ranges, nullptr, 1, tiles, const_cast<uint32_t*>(t.f[k].tile_order));
+    }
   }
   else
     schedule_tiles(nullptr, t.f[k].tile_cost, kTileParts, tiles, const_cast<uint32_t*>(t.b[k].tile_order));

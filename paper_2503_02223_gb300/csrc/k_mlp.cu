@@ -882,14 +882,16 @@ __global__ void k_mlp_set(MlpState st, const float* __restrict__ params) {
   write_bf16_copies(st, i, p);
 }
 
-// The bounded wait of the tensor-core kernels on an mbarrier that nothing arrives at: it
-// gives up after about one second and records that in *flag.
-__global__ void k_bounded_wait_probe(int* __restrict__ flag) {
+// The bounded waits of the tensor-core kernels: on an mbarrier that nothing arrives at
+// (bit 0 of *flag when it gives up, after about one second), then the training kernel's
+// grid barrier with a count that one CTA never reaches (bit 1).
+__global__ void k_bounded_wait_probe(int* __restrict__ flag, unsigned* __restrict__ counter) {
   __shared__ __align__(8) uint64_t bar;
   if (threadIdx.x == 0) mbar_init(smem_u32(&bar), 1);
   __syncthreads();
   const bool done = mbar_wait_bounded(smem_u32(&bar), 0);
-  if (!done && threadIdx.x == 0) atomicExch(flag, 1);
+  if (!done && threadIdx.x == 0) atomicOr(flag, 1);
+  if (!grid_barrier(counter, 2u) && threadIdx.x == 0) atomicOr(flag, 2);
 }
 
 }  // namespace
@@ -897,7 +899,7 @@ __global__ void k_bounded_wait_probe(int* __restrict__ flag) {
 // ----------------------------------------------------------------------------- launchers
 
 cudaError_t launch_bounded_wait_probe(int* flag, cudaStream_t s) {
-  k_bounded_wait_probe<<<1, 32, 0, s>>>(flag);
+  k_bounded_wait_probe<<<1, 32, 0, s>>>(flag, reinterpret_cast<unsigned*>(flag + 1));
   return cudaGetLastError();
 }
 
