@@ -480,6 +480,9 @@ __device__ __forceinline__ void loss_reduce(const float* __restrict__ part, int 
   __shared__ double s[3][kThreads];
   double acc[3] = {0, 0, 0};
   if (threadIdx.x < kThreads) {
+    // the same additions in the same order as a plain loop; unrolled so that several
+    // iterations' loads are in flight together
+#pragma unroll 8
     for (int t = threadIdx.x; t < tiles; t += kThreads)
 #pragma unroll
       for (int k = 0; k < 3; ++k) acc[k] += (double)part[3 * t + k];
