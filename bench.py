@@ -381,6 +381,17 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def tile_evals(nc, W: int, H: int, tw: int, th: int) -> int:
+    """E_tile: per tile, its pixel count times the longest walk of its pixels (the list
+    positions the tile's CTA goes through until its last pixel stops), summed over tiles."""
+    import torch
+    ntx, nty = (W + tw - 1) // tw, (H + th - 1) // th
+    img = torch.zeros(nty * th, ntx * tw, dtype=torch.int64, device=nc.device)
+    img[:H, :W] = nc.view(H, W).to(torch.int64)
+    per_tile = img.view(nty, th, ntx, tw).amax(dim=(1, 3))
+    return int(per_tile.sum().item()) * tw * th
+
+
 def workload_config(kf, m_pairs, args):
     cam = kf["camera"]
     return {"workload": "indoor keyframe: 300k Gaussians (30 ellipsoidal objects + room walls), "
@@ -436,6 +447,7 @@ def run_ours(args, rank, world, local_rank):
     dqo.dqo_get_buffer(ctx, dqo.DQO_BUF_N_CONTRIB, nc)
     torch.cuda.synchronize()
     evals = int(nc.to(torch.int64).sum().item())
+    evals_tile = tile_evals(nc, W, H, tw, th)
     uuid = getattr(torch.cuda.get_device_properties(local_rank), "uuid", None)
     smi_id = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else \
         (str(uuid) if uuid is not None else None)
@@ -472,6 +484,7 @@ def run_ours(args, rank, world, local_rank):
         dqo.dqo_get_buffer(ectx, dqo.DQO_BUF_N_CONTRIB, nc)
         torch.cuda.synchronize()
         evals = int(nc.to(torch.int64).sum().item())
+        evals_tile = tile_evals(nc, W, H, bst.tile_w, bst.tile_h)
         ectx.close()
     dqo.dqo_set_timing(bctx, True)
     graph = torch.cuda.CUDAGraph()
@@ -673,7 +686,9 @@ def run_ours(args, rank, world, local_rank):
     ex2_per_step = 2 * evals                 # one exponential per evaluation, forward and backward
     roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
             "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic_for(dom),
-            "evals_per_launch": evals, "flops_per_eval": FLOPS_PER_EVAL[dom],
+            "evals_per_launch": evals, "evals_tile_per_launch": evals_tile,
+            "eval_share_of_tile_walk": evals / evals_tile if evals_tile else None,
+            "flops_per_eval": FLOPS_PER_EVAL[dom],
             "frac_kernel_count": FLOPS_PER_EVAL_KERNEL[dom] * evals / (phases[dom] * 1e-3) / 1e12 / fp32_peak,
             "ex2_frac": ex2_per_step / (phases[dom] * 1e-3) / 1e12 / alu["ex2_tops"],
             "peak_basis": f"measured: FP32 FMA probe (dqo_alu_probe) on this GPU, best of 5 launches of ~5 ms "

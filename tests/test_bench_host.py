@@ -75,3 +75,14 @@ def test_peaks_fall_back_without_the_measured_file(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     peaks, src = bench.measured_peaks()
     assert src == "fallback" and peaks["hbm_gbs"] == 6800.0 and peaks["bf16_tflops_sustained"] == 1700.0
+
+
+def test_tile_walk_counts_each_tile_at_its_longest_pixel():
+    import torch
+    nc = torch.tensor([[1, 5, 0, 2, 7],
+                       [3, 0, 4, 4, 1],
+                       [9, 2, 0, 0, 6]], dtype=torch.int32).view(-1)
+    # 2x2 tiles: maxima 5, 4, 7 (top row), 9, 0, 6 (bottom row, padded); 4 pixels each
+    assert bench.tile_evals(nc, 5, 3, 2, 2) == 4 * (5 + 4 + 7 + 9 + 0 + 6)
+    assert bench.tile_evals(nc, 5, 3, 5, 3) == 15 * 9          # one tile
+    assert bench.tile_evals(nc, 5, 3, 1, 1) == int(nc.sum())   # a tile per pixel: E itself
