@@ -271,15 +271,21 @@ __device__ __forceinline__ void zero_grads(const PreBwdArgs& a, int64_t i) {
 // when several keyframes of a batch share them).
 __device__ __forceinline__ void preprocess_backward_item(const PreBwdArgs& a, int64_t i) {
   if (i >= a.n) return;
-  if (a.ntiles[i] == 0) {  // culled: never blended, zero gradient
-    zero_grads(a, i);
-    return;
-  }
-  const RasterParams& rp = a.rp;
+  // every load of the Gaussian first, in flight together (the moment record is read for
+  // every Gaussian and used only for the binned ones, the only ones it was written for)
+  const uint32_t nt = a.ntiles[i];
   const float mean[3] = {a.means[3 * i], a.means[3 * i + 1], a.means[3 * i + 2]};
   const float ls[3] = {a.log_scales[3 * i], a.log_scales[3 * i + 1], a.log_scales[3 * i + 2]};
   const float4 q = make_float4(a.quats[4 * i], a.quats[4 * i + 1], a.quats[4 * i + 2], a.quats[4 * i + 3]);
   const float logit = a.opacity_logit[i];
+  const float4 r0 = reinterpret_cast<const float4*>(a.grad2d)[3 * i + 0];  // m_x m_y m_xx m_xy
+  const float4 r1 = reinterpret_cast<const float4*>(a.grad2d)[3 * i + 1];  // m_yy d_opac d_r d_g
+  const float4 r2 = reinterpret_cast<const float4*>(a.grad2d)[3 * i + 2];  // d_b d_z - -
+  if (nt == 0) {  // culled: never blended, zero gradient
+    zero_grads(a, i);
+    return;
+  }
+  const RasterParams& rp = a.rp;
   Footprint f;
   footprint(rp, mean, ls, q, logit, f);
   if (!f.visible) {
@@ -287,9 +293,6 @@ __device__ __forceinline__ void preprocess_backward_item(const PreBwdArgs& a, in
     return;
   }
   const int mode = a.mode;
-  const float4 r0 = reinterpret_cast<const float4*>(a.grad2d)[3 * i + 0];  // m_x m_y m_xx m_xy
-  const float4 r1 = reinterpret_cast<const float4*>(a.grad2d)[3 * i + 1];  // m_yy d_opac d_r d_g
-  const float4 r2 = reinterpret_cast<const float4*>(a.grad2d)[3 * i + 2];  // d_b d_z - -
   const float ca = f.conic[0], cb = f.conic[1], cc = f.conic[2];
   // 2D mean and conic gradients from the moments (exponent -(a dx^2 + 2 b dx dy + c dy^2)/2)
   const float gx = ca * r0.x + cb * r0.y;
