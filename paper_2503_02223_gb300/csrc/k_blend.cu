@@ -537,8 +537,10 @@ __device__ __forceinline__ int sched_bucket(uint32_t x) {
 }
 
 // One CTA of kSchedThreads: counting sort of the tiles by decreasing bucket.  Each round
-// takes kSchedThreads * kSchedPer tiles with all their cost loads in flight; a warp's
-// lanes with equal buckets add to the bucket's counter once (match_any).
+// takes kSchedThreads * kSchedPer tiles with all their cost loads in flight; counts and
+// placements are shared-memory atomics per tile (one SM runs the whole schedule, where a
+// warp match per tile measured slower), so the order of tiles within a bucket is that of
+// the atomics: the schedule is a heuristic and the results do not depend on it.
 constexpr int kSchedThreads = 1024, kSchedPer = 8;
 
 // Item i's cost: tile i's list length (ranges), else the largest of cost[i * group + j],
@@ -547,7 +549,6 @@ __device__ __forceinline__ void schedule_tiles(const uint2* __restrict__ ranges,
                                                int group, int tiles, uint32_t* __restrict__ order) {
   __shared__ uint32_t s_h[kSchedBuckets];
   const int tid = threadIdx.x, lane = tid & 31;
-  const uint32_t lt = lanemask_lt();
   auto buckets = [&](int base, int (&b)[kSchedPer]) {
     uint32_t c[kSchedPer];
 #pragma unroll
@@ -578,8 +579,7 @@ __device__ __forceinline__ void schedule_tiles(const uint2* __restrict__ ranges,
 #pragma unroll
     for (int j = 0; j < kSchedPer; ++j) {
       held[j] = b[j];
-      const uint32_t peers = __match_any_sync(kFull, b[j]);
-      if (b[j] >= 0 && lane == __ffs(peers) - 1) atomicAdd(&s_h[b[j]], (uint32_t)__popc(peers));
+      if (b[j] >= 0) atomicAdd(&s_h[b[j]], 1u);
     }
   }
   __syncthreads();
@@ -615,14 +615,8 @@ __device__ __forceinline__ void schedule_tiles(const uint2* __restrict__ ranges,
       buckets(base, b);
     }
 #pragma unroll
-    for (int j = 0; j < kSchedPer; ++j) {
-      const uint32_t peers = __match_any_sync(kFull, b[j]);
-      const int leader = __ffs(peers) - 1;
-      uint32_t p0 = 0u;
-      if (b[j] >= 0 && lane == leader) p0 = atomicAdd(&s_h[b[j]], (uint32_t)__popc(peers));
-      p0 = __shfl_sync(kFull, p0, leader);
-      if (b[j] >= 0) order[p0 + __popc(peers & lt)] = (uint32_t)(base + j * kSchedThreads + tid);
-    }
+    for (int j = 0; j < kSchedPer; ++j)
+      if (b[j] >= 0) order[atomicAdd(&s_h[b[j]], 1u)] = (uint32_t)(base + j * kSchedThreads + tid);
   }
 }
 
