@@ -930,7 +930,6 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
   // ---- persistent forward + backward over all tiles, losses, projection adjoint
   {
     StepTable tt;
-    LossTable lt;
     PreBwdTable bt;
     for (int k = 0; k < nkf; ++k) {
       const dqo_keyframe& kf = kfs[k];
@@ -979,12 +978,12 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
       bb.tile_order = as<uint32_t>(B.tile_sched) + (1 + kTileParts) * T + kTileParts * (uint64_t)toff[k];
       bb.hitmask = a.hitmask;
       tt.tile_off[k] = toff[k];
-      lt.kf[k].part = a.loss_part;
-      lt.kf[k].tiles = (int)(toff[k + 1] - toff[k]);
-      lt.kf[k].lambda_ins = rp[k].lambda_ins;
-      lt.kf[k].scale = (float)(1.0 / ((double)rp[k].W * (double)rp[k].H));
-      lt.kf[k].loss = kf.out.loss;
-      tt.loss[k] = kf.out.loss;
+      LossKf& lk = bt.loss[k];
+      lk.part = a.loss_part;
+      lk.tiles = (int)(toff[k + 1] - toff[k]);
+      lk.lambda_ins = rp[k].lambda_ins;
+      lk.scale = (float)(1.0 / ((double)rp[k].W * (double)rp[k].H));
+      lk.loss = kf.out.loss;
       PreBwdArgs& pa = bt.kf[k];
       pa.rp = rp[k];
       pa.n = kf.gaussians.n;
@@ -1015,13 +1014,12 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
       const BlendCommon cm{pb.p0, pb.p1, pb.p2, pb.gid, as<uint32_t>(B.list), as<float>(B.grad2d), s->alpha_clamp,
                            s->alpha_min, s->t_stop, s->og_filter ? 1 : 0};
       DQO_CUDA(c, launch_blend_step(tt, cm, d_queue, s->tile_w, with_id, ctas_per_sm, B.sms, schedule, s_));
-      if (!blend_step_sums_losses(schedule)) DQO_CUDA(c, launch_loss_reduce_batch(lt, nkf, s_));
     }
     {
       PhaseTimer timer(c, DQO_PHASE_PROJECT_BWD, s_);
       DQO_CUDA(c, launch_preprocess_backward_batch(bt, nkf, max_n, s_));
     }
-    launches += (blend_step_sums_losses(schedule) ? 1 : 2) + (schedule == 0 ? 2 : schedule == 1 ? 4 : 2 * nkf + 2);
+    launches += 1 + (schedule == 0 ? 2 : schedule == 1 ? 4 : 2 * nkf + 2);
   }
   if (run_fits) DQO_CUDA(c, cudaStreamWaitEvent(s_, B.join, 0));
   c->launches += launches;

@@ -70,6 +70,62 @@ __device__ __forceinline__ bool eval_gaussian(const float4& p0, const float4& p1
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// Deterministic sum of the per-tile loss partials, scaled by 1/(HW).  The first kThreads
+// threads of the block each add their tiles t, t + kThreads, ... in that order in FP32
+// (loads issued eight tiles at a time before the additions), the per-thread sums are added
+// by a fixed FP32 shuffle tree within each warp, and thread 0 adds the warps' sums in
+// order in FP64.  The order depends on nothing but the tile count, so the result is the
+// same for any block of at least kThreads threads and on every run.  The partials are
+// non-negative, so the FP32 sums carry a relative error of a few 1e-7.  (An FP64 sum of
+// every partial took 10 us: this GPU's FP64 pipe is slow.)  Every thread takes part in
+// the barrier.
+__device__ __forceinline__ void loss_reduce(const float* __restrict__ part, int tiles, float lambda_ins, float scale,
+                                            float* __restrict__ loss) {
+  constexpr int kBatch = 8;
+  __shared__ float s[3][kThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x < kThreads) {
+    float acc[3] = {0.f, 0.f, 0.f};
+    for (int t0 = threadIdx.x; t0 < tiles; t0 += kBatch * kThreads) {
+      float v[kBatch][3];
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j) {
+        const int t = t0 + j * kThreads;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v[j][k] = t < tiles ? part[3 * t + k] : 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < kBatch; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) acc[k] += v[j][k];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float x = acc[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+      if (lane == 0) s[k][warp] = x;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0, d = 0, i = 0;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) {
+      r += (double)s[0][w];
+      d += (double)s[1][w];
+      i += (double)s[2][w];
+    }
+    r *= scale;
+    d *= scale;
+    i *= scale;
+    loss[0] = (float)r;
+    loss[1] = (float)d;
+    loss[2] = (float)i;
+    loss[3] = (float)(r + d + (double)lambda_ins * i);
+  }
+}
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_dep_smem(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                                    Args... args) {
@@ -213,8 +269,18 @@ struct PreKf {
 struct PreTable {
   PreKf kf[kMaxBatch];
 };
+// Keyframe k's loss: its per-tile partials, summed (loss_reduce) into loss[0..3].
+struct LossKf {
+  const float* part;
+  int tiles;
+  float lambda_ins, scale;
+  float* loss;
+};
+// The batch's projection adjoint also sums each keyframe's loss partials (CTA column 0):
+// the blend backward needs no loss value, so the sums run beside the adjoint's Gaussians.
 struct PreBwdTable {
   PreBwdArgs kf[kMaxBatch];
+  LossKf loss[kMaxBatch];
 };
 cudaError_t launch_preprocess_batch(const PreTable& t, int nkf, int64_t max_n, const ProjBuffers& out,
                                     cudaStream_t s);
@@ -322,7 +388,6 @@ cudaError_t launch_blend_backward(const BlendBwdArgs& a, cudaStream_t s);
 struct StepTable {
   BlendFwdArgs f[16];
   BlendBwdArgs b[16];
-  float* loss[16];        // keyframe k's loss output [4] (NULL: none)
   const uint32_t* tile_count;  // pairs per joint tile; the forward schedule turns them into ranges
   uint32_t tile_off[17];  // keyframe k owns joint tiles [tile_off[k], tile_off[k+1])
   int nkf;
@@ -346,19 +411,6 @@ struct BlendCommon {
 // keyframe.
 cudaError_t launch_blend_step(const StepTable& t, const BlendCommon& cm, uint32_t* queue, int tile_w, bool with_id,
                               int ctas_per_sm, int sms, int schedule, cudaStream_t s);
-struct LossKf {
-  const float* part;
-  int tiles;
-  float lambda_ins, scale;
-  float* loss;
-};
-struct LossTable {
-  LossKf kf[16];
-};
-cudaError_t launch_loss_reduce_batch(const LossTable& t, int nkf, cudaStream_t s);
-// True when launch_blend_step sums the keyframes' losses itself (the per-keyframe schedule
-// folds the sums into its backward tile-schedule launch).
-inline bool blend_step_sums_losses(int schedule) { return schedule == 2; }
 
 cudaError_t launch_quadric_project(int nq, const float* params, int nv, const float* P, const int32_t* q_ptr,
                                    const int32_t* pair_v, int npairs, float* conic, float* bbox, uint8_t* valid,

@@ -472,52 +472,11 @@ __global__ void __launch_bounds__(kThreads) k_blend_forward(BlendFwdArgs a) {
   blend_fwd_tile<TW, kId>(a, cm, a.tile_order ? (int)a.tile_order[blockIdx.x] : (int)blockIdx.x);
 }
 
-// Deterministic sum of the per-tile loss partials in double, scaled by 1/(HW).  The first
-// kThreads threads of the block do the arithmetic (the same order for any block size of at
-// least kThreads); every thread takes part in the barriers.
-__device__ __forceinline__ void loss_reduce(const float* __restrict__ part, int tiles, float lambda_ins, float scale,
-                                            float* __restrict__ loss) {
-  __shared__ double s[3][kThreads];
-  double acc[3] = {0, 0, 0};
-  if (threadIdx.x < kThreads) {
-    // the same additions in the same order as a plain loop; unrolled so that several
-    // iterations' loads are in flight together
-#pragma unroll 8
-    for (int t = threadIdx.x; t < tiles; t += kThreads)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) acc[k] += (double)part[3 * t + k];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) s[k][threadIdx.x] = acc[k];
-  }
-  __syncthreads();
-  for (int o = kThreads / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    const double r = s[0][0] * scale, d = s[1][0] * scale, i = s[2][0] * scale;
-    loss[0] = (float)r;
-    loss[1] = (float)d;
-    loss[2] = (float)i;
-    loss[3] = (float)(r + d + (double)lambda_ins * i);
-  }
-}
-
 __global__ void k_loss_reduce(const float* __restrict__ part, int tiles, float lambda_ins, float scale,
                               float* __restrict__ loss) {
   pdl_wait();
   pdl_trigger();
   loss_reduce(part, tiles, lambda_ins, scale, loss);
-}
-
-// One block per keyframe of a batch.
-__global__ void k_loss_reduce_batch(const __grid_constant__ LossTable t) {
-  pdl_wait();
-  pdl_trigger();
-  const LossKf& k = t.kf[blockIdx.x];
-  if (k.loss) loss_reduce(k.part, k.tiles, k.lambda_ins, k.scale, k.loss);
 }
 
 // ---------------------------------------------------------------- tile schedule
@@ -1071,20 +1030,11 @@ unsigned persistent_grid(Kernel k, int ctas_per_sm, int sms, uint32_t total, cud
 }
 
 // One CTA per keyframe of a step table: which = 0 orders t.f[k]'s tiles by list length
-// into t.f[k].tile_order, which = 1 by t.f[k].tile_cost into t.b[k].tile_order; with
-// which = 1 and 2 * nkf CTAs, CTA nkf + k sums keyframe k's loss partials.
+// into t.f[k].tile_order, which = 1 by t.f[k].tile_cost into t.b[k].tile_order.
 __global__ void __launch_bounds__(kSchedThreads) k_tile_schedule_batch(const __grid_constant__ StepTable t,
                                                                        int which) {
   pdl_wait();
   pdl_trigger();
-  if ((int)blockIdx.x >= t.nkf) {
-    const int k = (int)blockIdx.x - t.nkf;
-    const RasterParams& rp = t.f[k].rp;
-    if (t.loss[k])
-      loss_reduce(t.f[k].loss_part, (int)(t.tile_off[k + 1] - t.tile_off[k]), rp.lambda_ins,
-                  (float)(1.0 / ((double)rp.W * (double)rp.H)), t.loss[k]);
-    return;
-  }
   const int k = blockIdx.x;
   const int tiles = (int)(t.tile_off[k + 1] - t.tile_off[k]);
   if (which == 0) {
@@ -1150,20 +1100,7 @@ cudaError_t step_tw(const StepTable& t, const BlendCommon& cm, uint32_t* queue, 
       f.list = cm.list;
       launch_dep(k_blend_forward<TW, kId>, dim3(tiles), dim3(kThreads), s, f);
     }
-    // the backward's schedule, and the keyframes' loss sums in extra CTAs of that launch
-    if (sched) {
-      launch_dep(k_tile_schedule_batch, dim3((unsigned)(2 * t.nkf)), dim3(kSchedThreads), s, t, 1);
-    } else {
-      LossTable lt;
-      for (int k = 0; k < t.nkf; ++k) {
-        lt.kf[k].part = t.f[k].loss_part;
-        lt.kf[k].tiles = (int)(t.tile_off[k + 1] - t.tile_off[k]);
-        lt.kf[k].lambda_ins = t.f[k].rp.lambda_ins;
-        lt.kf[k].scale = (float)(1.0 / ((double)t.f[k].rp.W * (double)t.f[k].rp.H));
-        lt.kf[k].loss = t.loss[k];
-      }
-      launch_dep(k_loss_reduce_batch, dim3((unsigned)t.nkf), dim3(kThreads), s, lt);
-    }
+    if (sched) launch_dep(k_tile_schedule_batch, dim3((unsigned)t.nkf), dim3(kSchedThreads), s, t, 1);
     for (int k = 0; k < t.nkf; ++k) {
       const unsigned tiles = t.tile_off[k + 1] - t.tile_off[k];
       if (tiles == 0) continue;
@@ -1194,10 +1131,5 @@ cudaError_t launch_blend_step(const StepTable& t, const BlendCommon& cm, uint32_
   }
 }
 
-cudaError_t launch_loss_reduce_batch(const LossTable& t, int nkf, cudaStream_t s) {
-  if (nkf == 0) return cudaSuccess;
-  launch_dep(k_loss_reduce_batch, dim3((unsigned)nkf), dim3(kThreads), s, t);
-  return cudaGetLastError();
-}
 
 }  // namespace dqo

@@ -377,10 +377,17 @@ __global__ void __launch_bounds__(kThreads) k_preprocess_backward(PreBwdArgs a) 
 
 // Keyframe blockIdx.y of a batch (its ntiles and grad2d pointers already offset to its
 // first Gaussian); each keyframe in its own mode (atomic where keyframes share buffers).
+// CTA column 0 sums the keyframe's loss partials instead (launched first, so it runs beside
+// the Gaussians' CTAs); columns 1.. take the Gaussians.
 __global__ void __launch_bounds__(kThreads) k_preprocess_backward_batch(const __grid_constant__ PreBwdTable t) {
   pdl_wait();
   pdl_trigger();
-  preprocess_backward_item(t.kf[blockIdx.y], (int64_t)blockIdx.x * kThreads + threadIdx.x);
+  if (blockIdx.x == 0) {
+    const LossKf& l = t.loss[blockIdx.y];
+    if (l.loss) loss_reduce(l.part, l.tiles, l.lambda_ins, l.scale, l.loss);
+    return;
+  }
+  preprocess_backward_item(t.kf[blockIdx.y], (int64_t)(blockIdx.x - 1) * kThreads + threadIdx.x);
 }
 
 }  // namespace
@@ -402,8 +409,8 @@ cudaError_t launch_preprocess_batch(const PreTable& t, int nkf, int64_t max_n, c
 }
 
 cudaError_t launch_preprocess_backward_batch(const PreBwdTable& t, int nkf, int64_t max_n, cudaStream_t s) {
-  if (nkf == 0 || max_n == 0) return cudaSuccess;
-  const dim3 grid((unsigned)((max_n + kThreads - 1) / kThreads), (unsigned)nkf);
+  if (nkf == 0) return cudaSuccess;
+  const dim3 grid((unsigned)(1 + (max_n + kThreads - 1) / kThreads), (unsigned)nkf);
   launch_dep(k_preprocess_backward_batch, dim3(grid), dim3(kThreads), s, t);
   return cudaGetLastError();
 }
