@@ -144,7 +144,10 @@ typedef enum {
   DQO_BUF_PROJ = 0,        /* float4 [3][n]: (x, y, a', b') (c', opacity, z, id|OG<<31) (r, g, b, lvl);
                               a', b', c' = conic (a, 2b, c) scaled by -log2(e)/2; lvl = log2(opacity /
                               alpha_min) (slightly widened; < 0 if alpha never reaches alpha_min) */
-  DQO_BUF_RECT = 1,        /* uint16 [n][4]: tile rect (tx0, ty0, tx1, ty1), tx1/ty1 exclusive */
+  DQO_BUF_RECT = 1,        /* uint16 [n][4]: tile rect (tx0, ty0, tx1, ty1), tx1/ty1 exclusive:
+                              tiles holding a pixel centre in the 3-sigma square narrowed
+                              (alpha_min > 0) to the bounding box of the ellipse where alpha
+                              can reach alpha_min (K1 in csrc/k_preprocess.cu)             */
   DQO_BUF_DEPTH_ORDER = 2, /* uint32 [n]: Gaussian indices sorted by (z bits, index), visible first */
   DQO_BUF_TILE_RANGES = 3, /* uint32 [T][2]: [start, end) of each tile in the tile list */
   DQO_BUF_TILE_LIST = 4,   /* uint32 [M]: Gaussian indices ordered by (tile, z bits, index) */

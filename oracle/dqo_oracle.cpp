@@ -19,7 +19,15 @@
 //   pixel (u,v) centre at integer (u,v); u = fx x/z + cx.
 //   Gaussian: p_c = R_view mean + t_view; Sigma = R(q) diag(exp(2 s)) R(q)^T (q normalised);
 //   Sigma' = J W Sigma W^T J^T + lowpass I; conic = Sigma'^-1; radius = ceil(k sqrt(lmax)).
-//   Tile membership: tile contains a pixel centre inside [x-r, x+r] x [y-r, y+r].
+//   Tile membership: tile contains a pixel centre inside [x-hx, x+hx] x [y-hy, y+hy], the
+//   3-sigma square (hx = hy = r) narrowed, when alpha_min > 0, to the bounding box of the
+//   ellipse q <= T' outside of which no pixel can blend the Gaussian: alpha <= o G, so a
+//   blended pixel has q <= T = 2 ln(o / alpha_min).  T' = T (1 + 2^-10) + 2^-14 (a + c)
+//   R^2 + 2^-10 (a, c the conic's diagonal, R = r + max(tile_w, tile_h)) widens it by more
+//   than the single-precision evaluation of G can move q within the square's tiles;
+//   hx = min(r, sqrt(T' Sigma'_xx)), hy = min(r, sqrt(T' Sigma'_yy)); T' <= 0 culls.  The rule
+//   removes only (tile, Gaussian) pairs whose pixels all skip the Gaussian, so no pixel
+//   value depends on it (pinned by brute force in tests/).
 //   Per pixel: tile's Gaussians sorted by (float bit pattern of z, index), the 3DGS depth
 //   key; alpha = min(clamp, o exp(power));
 //   skip alpha < alpha_min; stop before the Gaussian that would make T(1-alpha) < t_stop.
@@ -109,10 +117,10 @@ void quat_to_rot(const double q[4], double R[3][3]) {
     R[2][0] = 2 * (x * z - w * y);     R[2][1] = 2 * (y * z + w * x);     R[2][2] = 1 - 2 * (x * x + y * y);
 }
 
-// Tiles containing a pixel centre inside the square [x-r, x+r] x [y-r, y+r].
-bool tile_rect(double x, double y, double r, const OSettings& st, const OCamera& cam, int rect[4]) {
-    double ulo = std::ceil(x - r), uhi = std::floor(x + r);
-    double vlo = std::ceil(y - r), vhi = std::floor(y + r);
+// Tiles containing a pixel centre inside the box [x-hx, x+hx] x [y-hy, y+hy].
+bool tile_rect(double x, double y, double hx, double hy, const OSettings& st, const OCamera& cam, int rect[4]) {
+    double ulo = std::ceil(x - hx), uhi = std::floor(x + hx);
+    double vlo = std::ceil(y - hy), vhi = std::floor(y + hy);
     if (ulo < 0) ulo = 0;
     if (vlo < 0) vlo = 0;
     if (uhi > cam.width - 1) uhi = cam.width - 1;
@@ -181,22 +189,44 @@ Proj project_gaussian(const OSettings& st, const OCamera& cam, const double* mea
     P.xy[0] = cam.fx * x / z + cam.cx;
     P.xy[1] = cam.fy * y / z + cam.cy;
     P.opac = 1.0 / (1.0 + std::exp(-opacity_logit));
-    P.visible = tile_rect(P.xy[0], P.xy[1], P.radius, st, cam, P.rect);
+    // the alpha_min ellipse's half-widths (infinite when alpha_min = 0: no narrowing)
+    double ex = INFINITY, ey = INFINITY, Tm = 1.0, Tscale = 0.0;
+    if (st.alpha_min > 0) {
+        const double T = 2.0 * std::log(P.opac / st.alpha_min);
+        const double R = P.radius + (double)std::max(st.tile_w, st.tile_h);
+        Tm = T * (1.0 + std::ldexp(1.0, -10)) + std::ldexp(1.0, -14) * (P.conic[0] + P.conic[2]) * R * R +
+             std::ldexp(1.0, -10);
+        Tscale = std::fabs(T) + 1.0;
+        if (Tm > 0) {
+            ex = std::sqrt(Tm * P.cov2[0]);
+            ey = std::sqrt(Tm * P.cov2[2]);
+        }
+    }
+    P.visible = Tm > 0 && tile_rect(P.xy[0], P.xy[1], std::min((double)P.radius, ex),
+                                    std::min((double)P.radius, ey), st, cam, P.rect);
+    if (!P.visible) P.rect[0] = P.rect[1] = P.rect[2] = P.rect[3] = 0;
 
     // Flag decisions that single precision may take the other way: the radius rounding,
-    // and the tile rect under a shift of the centre by amb_px.
+    // the sign of T', the ellipse's half-widths (relative amb_rel), and the tile rect under
+    // a shift of the centre by amb_px.  The rect grows with r, hx and hy, so the low and the
+    // high perturbations of all three bound every mix of them.
     int rlo = (int)std::ceil(rr * (1 - st.amb_rel)), rhi = (int)std::ceil(rr * (1 + st.amb_rel));
     bool amb = (rlo != P.radius) || (rhi != P.radius) ||
-               std::fabs(z - st.znear) <= st.amb_rel * st.znear;
+               std::fabs(z - st.znear) <= st.amb_rel * st.znear || std::fabs(Tm) <= st.amb_rel * Tscale;
     int u[4] = {P.rect[0], P.rect[1], P.rect[2], P.rect[3]};
     int in4[4] = {P.rect[0], P.rect[1], P.rect[2], P.rect[3]};
     bool all = P.visible;
     bool any = P.visible;
-    for (int rad : {rlo, rhi}) {
+    for (int side : {-1, 1}) {
+        const int rad = side < 0 ? rlo : rhi;
+        const double f = 1.0 + side * st.amb_rel;
+        const bool vis_t = Tm + side * st.amb_rel * Tscale > 0;
         for (int dxs = -1; dxs <= 1; ++dxs)
             for (int dys = -1; dys <= 1; ++dys) {
                 int r2[4];
-                bool v2 = tile_rect(P.xy[0] + dxs * st.amb_px, P.xy[1] + dys * st.amb_px, rad, st, cam, r2);
+                bool v2 = vis_t && tile_rect(P.xy[0] + dxs * st.amb_px, P.xy[1] + dys * st.amb_px,
+                                             std::min((double)rad, ex * f), std::min((double)rad, ey * f), st,
+                                             cam, r2);
                 if (v2 != P.visible || (v2 && (r2[0] != P.rect[0] || r2[1] != P.rect[1] ||
                                                r2[2] != P.rect[2] || r2[3] != P.rect[3])))
                     amb = true;

@@ -3,9 +3,9 @@
 // K1 maps each 3D Gaussian to its screen footprint (EWA splatting, the 3DGS rasterizer
 // DQO-MAP optimises with; Sec. IV impl.): camera-space mean, 2D covariance
 // Sigma' = J W M M^T W^T J^T + lowpass I with M = R(q) diag(exp(s)), its inverse (the
-// conic, pre-scaled for exp2), a 3-sigma tile rect, opacity = sigmoid(logit), and the
-// depth-sort key.  One thread per Gaussian; each warp stages its 32 Gaussians' [n,3]
-// rows through shared memory with float4 loads.
+// conic, pre-scaled for exp2), a 3-sigma tile rect narrowed to where alpha can reach
+// alpha_min, opacity = sigmoid(logit), and the depth-sort key.  One thread per Gaussian;
+// each warp stages its 32 Gaussians' [n,3] rows through shared memory with float4 loads.
 //
 // K8 recomputes the same forward quantities and chains the per-Gaussian moment record
 // of the blend backward through the conic inverse, the EWA Jacobian, the scale/rotation
@@ -121,9 +121,28 @@ __device__ __forceinline__ void footprint(const RasterParams& rp, const float me
   f.xy[0] = fmaf(rp.fx, x * iz, rp.cx);
   f.xy[1] = fmaf(rp.fy, y * iz, rp.cy);
   if (!isfinite(f.xy[0]) || !isfinite(f.xy[1]) || !isfinite(r)) return;
-  // tiles holding a pixel centre inside [x - r, x + r] x [y - r, y + r]
-  float ulo = ceilf(f.xy[0] - r), uhi = floorf(f.xy[0] + r);
-  float vlo = ceilf(f.xy[1] - r), vhi = floorf(f.xy[1] + r);
+  // The rect's half-widths: the 3-sigma radius r, narrowed (alpha_min > 0) to the bounding
+  // box of the ellipse q <= T' outside of which no pixel blends the Gaussian.  The blend
+  // skips alpha < alpha_min and alpha <= opacity * G, so a blended pixel has
+  // q <= T = 2 ln(opacity / alpha_min).  T' = T (1 + 2^-10) + 2^-14 (a + c) R^2 + 2^-10 with
+  // R = r + max(tile_w, tile_h) (no pixel of a tile of the square is farther from the
+  // centre along either axis) exceeds T by more than the rounding of the conic, of dx and
+  // dy and of the exponent's evaluation can move q at such a pixel (a few units of 2^-24
+  // times (a + c) R^2), so every tile dropped here holds only pixels that skip the
+  // Gaussian and no pixel value changes.  The box of {q <= T'} has half-widths
+  // sqrt(T' Sigma'_xx) and sqrt(T' Sigma'_yy); T' <= 0 (opacity below alpha_min) culls.
+  float hx = r, hy = r;
+  if (rp.alpha_min > 0.f) {
+    const float T = 2.f * (logf(f.opac) - logf(rp.alpha_min));
+    const float R = r + (float)max(rp.tile_w, rp.tile_h);
+    const float Tm = fmaf(T, 1.f + 0x1p-10f, fmaf(0x1p-14f * (f.conic[0] + f.conic[2]), R * R, 0x1p-10f));
+    if (!(Tm > 0.f)) return;
+    hx = fminf(r, sqrtf(Tm * f.cov[0]));
+    hy = fminf(r, sqrtf(Tm * f.cov[2]));
+  }
+  // tiles holding a pixel centre inside [x - hx, x + hx] x [y - hy, y + hy]
+  float ulo = ceilf(f.xy[0] - hx), uhi = floorf(f.xy[0] + hx);
+  float vlo = ceilf(f.xy[1] - hy), vhi = floorf(f.xy[1] + hy);
   ulo = fmaxf(ulo, 0.f);
   vlo = fmaxf(vlo, 0.f);
   uhi = fminf(uhi, (float)(rp.W - 1));

@@ -105,6 +105,109 @@ def test_culling_and_tile_rect():
     assert list(pp["rect"][0]) == [ulo // 16, vlo // 16, uhi // 16 + 1, vhi // 16 + 1]
 
 
+def _square_tiles(x, y, h, W, H, tw, th):
+    """Tile range [tx0, ty0, tx1, ty1) of the pixel centres in [x-h, x+h] x [y-h, y+h]
+    (h a scalar or a pair of half-widths); all zeros if it holds none."""
+    hx, hy = (h, h) if np.isscalar(h) else h
+    ulo, uhi = max(int(np.ceil(x - hx)), 0), min(int(np.floor(x + hx)), W - 1)
+    vlo, vhi = max(int(np.ceil(y - hy)), 0), min(int(np.floor(y + hy)), H - 1)
+    if ulo > uhi or vlo > vhi:
+        return [0, 0, 0, 0]
+    return [ulo // tw, vlo // th, uhi // tw + 1, vhi // th + 1]
+
+
+def _narrowing_scene(seed, n):
+    g = synth.tiny_gaussians(seed, n=n)
+    g["opacity_logit"] = 2.0 * g["opacity_logit"] - 1.5     # opacities from 0.1% to 90%
+    return g
+
+
+def test_tile_rect_holds_every_blending_pixel_and_is_narrowed_to_the_alpha_min_ellipse():
+    """Brute force over the pixel centres of each Gaussian's 3 sigma square: every pixel
+    where the FP64 alpha o exp(-q/2) reaches alpha_min lies in a tile of the Gaussian's
+    rect, and the rect holds no tile beyond the bounding box of the ellipse
+    q <= 2 ln(o / alpha_min) (Sigma' from the conic by numpy's inverse) widened by 0.05 px;
+    a Gaussian with o < alpha_min has no tiles.  Low-opacity Gaussians get rects strictly
+    inside their 3 sigma squares."""
+    W, H = 96, 80
+    cam = synth.tiny_camera(width=W, height=H, f=120.0)
+    g = _narrowing_scene(1021, 600)
+    for tw, th in ((16, 16), (8, 4)):
+        st = oracle.settings(num_objects=4, tile_w=tw, tile_h=th)
+        pp = oracle.preprocess(g, cam, st)
+        narrowed = checked = 0
+        for i in range(len(pp["opac"])):
+            if pp["conic"][i].any() == 0:
+                continue                                          # behind the camera
+            x, y = pp["xy"][i]
+            a, b, c = pp["conic"][i]
+            o, r = pp["opac"][i], int(pp["radius"][i])
+            rect = list(pp["rect"][i]) if pp["visible"][i] else [0, 0, 0, 0]
+            u = np.arange(max(int(np.ceil(x - r)), 0), min(int(np.floor(x + r)), W - 1) + 1)
+            v = np.arange(max(int(np.ceil(y - r)), 0), min(int(np.floor(y + r)), H - 1) + 1)
+            if u.size and v.size:
+                du, dv = np.meshgrid(u - x, v - y)
+                q = a * du * du + 2 * b * du * dv + c * dv * dv
+                hit = np.minimum(st.alpha_clamp, o * np.exp(-0.5 * q)) >= st.alpha_min
+                for uu, vv in zip(*np.nonzero(hit.T)):
+                    tx, ty = u[uu] // tw, v[vv] // th
+                    assert rect[0] <= tx < rect[2] and rect[1] <= ty < rect[3], (i, u[uu], v[vv], rect)
+                    checked += 1
+            T = 2 * np.log(o / st.alpha_min)
+            if T < -0.01:
+                assert rect == [0, 0, 0, 0], i
+                continue
+            S = np.linalg.inv(np.array([[a, b], [b, c]]))
+            hx, hy = np.sqrt(max(T, 0) * S[0, 0]) + 0.05, np.sqrt(max(T, 0) * S[1, 1]) + 0.05
+            box = _square_tiles(x, y, (min(r, hx), min(r, hy)), W, H, tw, th)
+            if rect != [0, 0, 0, 0]:
+                assert box[0] <= rect[0] and box[1] <= rect[1] and rect[2] <= box[2] and rect[3] <= box[3], \
+                    (i, rect, box)
+            sq = _square_tiles(x, y, r, W, H, tw, th)
+            area = lambda t: max(t[2] - t[0], 0) * max(t[3] - t[1], 0)
+            narrowed += area(rect) < area(sq)
+        assert checked > 1000 and narrowed > 50, (checked, narrowed)
+
+
+def test_narrowed_rects_change_no_pixel():
+    """A per-pixel brute force in numpy over all Gaussians in (float z bits, index) order,
+    with tile membership by the plain 3 sigma square (no narrowing): alpha = min(clamp,
+    o exp(-q/2)), skipped below alpha_min, stopping before T (1 - alpha) < t_stop.  The
+    oracle's render with its narrowed rects gives the same colour, alpha and T_final."""
+    W, H = 48, 40
+    cam = synth.tiny_camera(width=W, height=H, f=60.0)
+    g = _narrowing_scene(1022, 120)
+    st = oracle.settings(num_objects=4)
+    pp = oracle.preprocess(g, cam, st)
+    ref = oracle.render(g, cam, st)
+    zb = pp["z"].astype(np.float32).view(np.uint32)
+    order = np.lexsort((np.arange(len(zb)), zb))
+    live = [i for i in order if pp["conic"][i].any()]
+    sq = {i: _square_tiles(*pp["xy"][i], int(pp["radius"][i]), W, H, st.tile_w, st.tile_h) for i in live}
+    assert sum(pp["visible"]) < len(live) or any(
+        list(pp["rect"][i]) != sq[i] for i in live if pp["visible"][i])    # the narrowing acts here
+    for py in range(H):
+        for px in range(W):
+            tx, ty = px // st.tile_w, py // st.tile_h
+            T, C = 1.0, np.zeros(3)
+            for i in live:
+                t4 = sq[i]
+                if not (t4[0] <= tx < t4[2] and t4[1] <= ty < t4[3]):
+                    continue
+                a, b, c = pp["conic"][i]
+                du, dv = px - pp["xy"][i][0], py - pp["xy"][i][1]
+                al = min(st.alpha_clamp, pp["opac"][i] * np.exp(-0.5 * (a * du * du + 2 * b * du * dv + c * dv * dv)))
+                if al < st.alpha_min:
+                    continue
+                if T * (1 - al) < st.t_stop:
+                    break
+                C += al * T * g["rgb"][i]
+                T *= 1 - al
+            np.testing.assert_allclose(ref["rgb"][py, px], C + T * np.array(st.bg[:]), atol=1e-12)
+            assert abs(ref["T_final"][py, px] - T) < 1e-12
+            assert abs(ref["alpha"][py, px] - (1 - T)) < 1e-12
+
+
 def _two_layer_scene():
     # two overlapping Gaussians at different depths, plus one in another tile
     g = dict(means=np.array([[0.0, 0.0, 2.0], [0.0, 0.0, 3.0], [0.3, 0.2, 2.5]]),
