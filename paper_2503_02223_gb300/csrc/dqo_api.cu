@@ -780,7 +780,7 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
     DQO_CUDA(c, ensure(B.dl_ins, 4 * P));
     DQO_CUDA(c, ensure(B.depth_hist, 4 * radix_scratch_words(N)));
     DQO_CUDA(c, ensure(B.depth_scan_scratch, 8 * scan_scratch_words(radix_scratch_words(N))));
-    DQO_CUDA(c, ensure(B.scan_scratch, 8 * scan_scratch_words(N)));
+    DQO_CUDA(c, ensure(B.scan_scratch, 8 * std::max(scan_scratch_words(N), scan_emit_scratch_words(N))));
     DQO_CUDA(c, ensure(B.counters, 64));
     if (!B.host) DQO_CUDA(c, cudaMallocHost(reinterpret_cast<void**>(&B.host), 64));
     if (!B.side) DQO_CUDA(c, cudaStreamCreateWithFlags(&B.side, cudaStreamNonBlocking));
@@ -806,7 +806,8 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
   // to the blend runs kernel after kernel (programmatic launches, no copy engine between);
   // a sizing call allocates the pair sort's scratch later and lets the sort clear it
   DQO_CUDA(c, cudaMemsetAsync(B.depth_hist.p, 0, 4 * radix_scratch_used_words(N, 0, 32), s_));
-  DQO_CUDA(c, cudaMemsetAsync(B.scan_scratch.p, 0, 8 * scan_scratch_words(N), s_));
+  DQO_CUDA(c, cudaMemsetAsync(B.scan_scratch.p, 0, 8 * std::max(scan_scratch_words(N), scan_emit_scratch_words(N)),
+                              s_));
   if (!sizing)
     DQO_CUDA(c, cudaMemsetAsync(B.hist.p, 0, 4 * radix_scratch_used_words((int64_t)B.capacity, rank_bits, end_bit),
                                 s_));
@@ -867,8 +868,9 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
     launches += 1;
   }
   // ---- depth order (one sort over all keyframes: the order restricted to a keyframe is
-  // its (depth, index) order because its indices are contiguous), then pair offsets by
-  // depth rank
+  // its (depth, index) order because its indices are contiguous); a sizing call then scans
+  // the pair counts by depth rank here, to learn the pair total before it allocates (other
+  // calls scan them inside the pair emission)
   int sel = 0;
   const uint32_t* order = nullptr;
   {
@@ -877,9 +879,12 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
                                as<uint32_t>(B.zval_b), N, 32, as<uint32_t>(B.depth_hist), &sel, s_, nullptr,
                                d_sort_err, 0, true));
     order = sel ? as<uint32_t>(B.zval_b) : as<uint32_t>(B.zval_a);
-    DQO_CUDA(c, launch_exclusive_scan(as<uint32_t>(B.ntiles), as<uint32_t>(B.offsets), N,
-                                      as<uint64_t>(B.scan_scratch), d_total, s_, d_sort_err, order, true));
-    launches += scan_launches(N) + radix_sort_launches(N, 32);
+    if (sizing) {
+      DQO_CUDA(c, launch_exclusive_scan(as<uint32_t>(B.ntiles), as<uint32_t>(B.offsets), N,
+                                        as<uint64_t>(B.scan_scratch), d_total, s_, d_sort_err, order, true));
+      launches += scan_launches(N);
+    }
+    launches += radix_sort_launches(N, 32);
   }
 
   if (sizing) {
@@ -892,8 +897,8 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
     DQO_CUDA(c, ensure(B.pair_b, 8 * cap));
     DQO_CUDA(c, ensure(B.list, 4 * cap));
     DQO_CUDA(c, ensure(B.hist, 4 * radix_scratch_words((int64_t)cap)));
-    DQO_CUDA(c, ensure(B.scan_scratch, 8 * std::max(scan_scratch_words(N),
-                                                    scan_scratch_words(radix_scratch_words((int64_t)cap)))));
+    DQO_CUDA(c, ensure(B.scan_scratch, 8 * std::max({scan_scratch_words(N), scan_emit_scratch_words(N),
+                                                     scan_scratch_words(radix_scratch_words((int64_t)cap))})));
     DQO_CUDA(c, ensure(B.hitrec, 4 * hit_record_words(cap, T)));
     B.capacity = cap;
     B.sig = sig;
@@ -913,8 +918,13 @@ dqo_status dqo_batch_step(dqo_ctx* c, const dqo_settings* s, int32_t nkf, const 
     const bool k32 = end_bit <= 32;
     // the pair sort's last pass writes the tile list and each tile's pair count, from which
     // the forward's tile schedule writes the ranges
-    DQO_CUDA(c, launch_emit_pairs_batch(et, nkf, N, as<ushort4>(B.rect), as<uint32_t>(B.offsets), order, rank_bits,
-                                        cap, B.pair_a.p, k32, d_overflow, d_total, d_live, s_));
+    if (sizing)
+      DQO_CUDA(c, launch_emit_pairs_batch(et, nkf, N, as<ushort4>(B.rect), as<uint32_t>(B.offsets), order,
+                                          rank_bits, cap, B.pair_a.p, k32, d_overflow, d_total, d_live, s_));
+    else
+      DQO_CUDA(c, launch_scan_emit_pairs_batch(et, nkf, N, as<ushort4>(B.rect), order, rank_bits, cap, B.pair_a.p,
+                                               k32, d_overflow, as<uint64_t>(B.scan_scratch), d_sort_err, d_total,
+                                               d_live, s_));
     const PairOut po{order, as<uint32_t>(B.list), as<uint32_t>(B.tile_count), rank_bits, (uint32_t)T,
                      (uint32_t)N};
     int psel = 0;

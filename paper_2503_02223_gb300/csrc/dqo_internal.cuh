@@ -349,6 +349,15 @@ cudaError_t launch_emit_pairs_batch(const EmitTable& t, int nkf, int64_t n, cons
                                     const uint32_t* offsets, const uint32_t* order, int rank_bits, uint64_t capacity,
                                     void* keys, bool k32, uint32_t* overflow, const uint64_t* total, uint64_t* live,
                                     cudaStream_t s);
+// The same emission with the scan of the pair counts in the kernel (no offsets array):
+// scratch holds scan_emit_scratch_words(n) uint64 words, all zero before the call; the
+// pair total goes to *total and bounds *live.  err: look-back timeout flag (scratch's own
+// word if NULL).
+size_t scan_emit_scratch_words(int64_t n);
+cudaError_t launch_scan_emit_pairs_batch(const EmitTable& t, int nkf, int64_t n, const ushort4* rect,
+                                         const uint32_t* order, int rank_bits, uint64_t capacity, void* keys, bool k32,
+                                         uint32_t* overflow, uint64_t* scratch, uint32_t* err, uint64_t* total,
+                                         uint64_t* live, cudaStream_t s);
 
 // What the last pass of a pair sort writes instead of the sorted keys: the tile list
 // (list[p] = order[rank of key p]) and each tile's pair count (added to counts[tile], zero

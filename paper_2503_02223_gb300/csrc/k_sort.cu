@@ -60,6 +60,50 @@ __device__ __forceinline__ uint64_t scan_ns() {
 // the last tile writes the total.  Waits give up after about a second (err).
 constexpr uint64_t kScanAgg = 1ull << 62, kScanInc = 2ull << 62, kScanMask = (1ull << 62) - 1;
 
+// Warp 0 of a look-back CTA: publishes tile `tile`'s sum tot, adds the predecessors' published
+// sums back to the first inclusive prefix, 32 at a time (lane j reads tile p - j; the words
+// up to the nearest unpublished one are added, and the walk ends at the nearest inclusive
+// one), publishes the tile's inclusive prefix and returns its exclusive prefix on every
+// lane.  Tiles are numbered in the order their CTAs started, so every wait is on a running
+// CTA; a wait still gives up after about a second (err = 1, prefix incomplete).
+__device__ __forceinline__ uint64_t scan_lookback(uint64_t* __restrict__ status, uint32_t tile, uint64_t tot,
+                                                  uint32_t* __restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  volatile uint64_t* st = status;
+  if (lane == 0) st[tile] = (tile == 0 ? kScanInc : kScanAgg) | tot;
+  uint64_t excl = 0;
+  if (tile > 0) {
+    int64_t p = (int64_t)tile - 1;
+    const uint64_t t0 = scan_ns();
+    uint32_t it = 0;
+    for (;;) {
+      const uint64_t w = p - lane >= 0 ? (uint64_t)st[p - lane] : (uint64_t)kScanInc;   // before tile 0: an empty prefix
+      const uint64_t f = w & ~kScanMask;
+      const uint32_t unready = __ballot_sync(0xFFFFFFFFu, f == 0);
+      const uint32_t inc = __ballot_sync(0xFFFFFFFFu, f == kScanInc);
+      const uint32_t stop = unready | inc;
+      const int first = stop ? __ffs(stop) - 1 : 32;
+      const bool finish = first < 32 && ((inc >> first) & 1u);
+      const int take = finish ? first + 1 : first;
+      uint64_t v = lane < take ? (w & kScanMask) : 0ull;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+      excl += v;
+      if (finish) break;
+      p -= take;
+      if (take == 0 && (++it & 63u) == 0u) {
+        const bool late = __shfl_sync(0xFFFFFFFFu, lane == 0 && scan_ns() - t0 > 1000000000ull, 0);
+        if (late) {
+          if (lane == 0) atomicExch(err, 1u);
+          break;
+        }
+      }
+    }
+    if (lane == 0) st[tile] = kScanInc | (excl + tot);
+  }
+  return excl;
+}
+
 __global__ void __launch_bounds__(kThreads) k_scan_lookback(const uint32_t* __restrict__ in,
                                                             const uint32_t* __restrict__ gather,
                                                             uint32_t* __restrict__ out, int64_t n,
@@ -91,42 +135,8 @@ __global__ void __launch_bounds__(kThreads) k_scan_lookback(const uint32_t* __re
   uint32_t tot;
   uint32_t run = block_exclusive_scan<uint32_t>(sum, tot);
   if (threadIdx.x < 32) {
-    // warp 0 looks back 32 predecessors at a time: lane j reads tile p - j; the words up to
-    // the nearest unpublished one are added, and the walk ends at the nearest inclusive one
-    const int lane = threadIdx.x;
-    volatile uint64_t* st = status;
-    if (lane == 0) st[tile] = (tile == 0 ? kScanInc : kScanAgg) | (uint64_t)tot;
-    uint64_t excl = 0;
-    if (tile > 0) {
-      int64_t p = (int64_t)tile - 1;
-      const uint64_t t0 = scan_ns();
-      uint32_t it = 0;
-      for (;;) {
-        const uint64_t w = p - lane >= 0 ? (uint64_t)st[p - lane] : (uint64_t)kScanInc;   // before tile 0: an empty prefix
-        const uint64_t f = w & ~kScanMask;
-        const uint32_t unready = __ballot_sync(0xFFFFFFFFu, f == 0);
-        const uint32_t inc = __ballot_sync(0xFFFFFFFFu, f == kScanInc);
-        const uint32_t stop = unready | inc;
-        const int first = stop ? __ffs(stop) - 1 : 32;
-        const bool finish = first < 32 && ((inc >> first) & 1u);
-        const int take = finish ? first + 1 : first;
-        uint64_t v = lane < take ? (w & kScanMask) : 0ull;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-        excl += v;
-        if (finish) break;
-        p -= take;
-        if (take == 0 && (++it & 63u) == 0u) {
-          const bool late = __shfl_sync(0xFFFFFFFFu, lane == 0 && scan_ns() - t0 > 1000000000ull, 0);
-          if (late) {
-            if (lane == 0) atomicExch(err, 1u);
-            break;
-          }
-        }
-      }
-      if (lane == 0) st[tile] = kScanInc | (excl + tot);
-    }
-    if (lane == 0) {
+    const uint64_t excl = scan_lookback(status, tile, tot, err);
+    if (threadIdx.x == 0) {
       s_prefix = excl;
       if (total && base + kScanTile >= n) *total = excl + tot;
     }
@@ -522,6 +532,58 @@ __global__ void __launch_bounds__(kThreads) k_emit_pairs_batch(const __grid_cons
   cta_emit<K>(q, o, cnt, (K)r, t.kf[k].tile_off, t.kf[k].ntx, rank_bits, keys);
 }
 
+// k_emit_pairs_batch with the exclusive scan of the pair counts in the same kernel: CTA b
+// of the look-back order (a ticket taken before the programmatic wait, so that every lower
+// ticket's CTA has started) covers depth ranks [256 b, 256 b + 256), scans their counts,
+// finds its first pair by decoupled look-back (scan_lookback) and writes the pairs.  The
+// last CTA writes the pair total and bounds *live by it.  status: [ceil(n / 256)] words,
+// then the ticket counter; all zero before the launch.  Eight CTAs per SM (32 registers)
+// keep the indoor keyframe's 1172 CTAs resident together.
+template <typename K>
+__global__ void __launch_bounds__(kThreads, 8) k_scan_emit_pairs_batch(
+    const __grid_constant__ EmitTable t, int nkf, const ushort4* __restrict__ rect,
+    const uint32_t* __restrict__ order, int64_t n, int rank_bits, uint64_t capacity, K* __restrict__ keys,
+    uint32_t* __restrict__ overflow, uint64_t* __restrict__ status, uint32_t* __restrict__ counter,
+    uint32_t* __restrict__ err, unsigned long long* __restrict__ total, unsigned long long* __restrict__ live) {
+  __shared__ uint32_t s_tile;
+  __shared__ uint64_t s_prefix;
+  if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
+  pdl_wait();
+  pdl_trigger();
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const int64_t r = (int64_t)tile * kThreads + threadIdx.x;
+  ushort4 q = make_ushort4(0, 0, 0, 0);
+  uint32_t cnt = 0;
+  int k = 0;
+  if (r < n) {
+    const int64_t gi = order[r];
+    while (k + 1 < nkf && t.kf[k + 1].base <= gi) ++k;
+    q = rect[gi];
+    if (q.z > q.x && q.w > q.y) cnt = (uint32_t)(q.z - q.x) * (uint32_t)(q.w - q.y);
+  }
+  uint32_t tot;
+  const uint32_t run = block_exclusive_scan<uint32_t>(cnt, tot);
+  if (threadIdx.x < 32) {
+    const uint64_t excl = scan_lookback(status, tile, tot, err);
+    if (threadIdx.x == 0) {
+      s_prefix = excl;
+      if ((int64_t)(tile + 1) * kThreads >= n) {
+        *total = excl + tot;
+        atomicMin(live, excl + tot);
+      }
+    }
+  }
+  __syncthreads();
+  const uint64_t o = s_prefix + run;
+  if (cnt && o + cnt > capacity) {
+    atomicExch(overflow, 1u);
+    atomicMin(live, (unsigned long long)o);
+    cnt = 0;
+  }
+  cta_emit<K>(q, o, cnt, (K)r, t.kf[k].tile_off, t.kf[k].ntx, rank_bits, keys);
+}
+
 template <typename K>
 __global__ void __launch_bounds__(kThreads) k_tile_ranges(const K* __restrict__ keys, int64_t m_cap,
                                                           const uint64_t* __restrict__ m_dev, int rank_bits,
@@ -716,6 +778,27 @@ cudaError_t launch_emit_pairs_batch(const EmitTable& t, int nkf, int64_t n, cons
     launch_dep(k_emit_pairs_batch<uint64_t>, dim3(grid), dim3(kThreads), s, t, nkf, rect, offsets, order, n, rank_bits,
                capacity, static_cast<uint64_t*>(keys), overflow, reinterpret_cast<const unsigned long long*>(total),
                reinterpret_cast<unsigned long long*>(live));
+  return cudaGetLastError();
+}
+
+size_t scan_emit_scratch_words(int64_t n) { return (size_t)grid_for(n > 0 ? n : 1, kThreads) + 2; }
+
+cudaError_t launch_scan_emit_pairs_batch(const EmitTable& t, int nkf, int64_t n, const ushort4* rect,
+                                         const uint32_t* order, int rank_bits, uint64_t capacity, void* keys, bool k32,
+                                         uint32_t* overflow, uint64_t* scratch, uint32_t* err, uint64_t* total,
+                                         uint64_t* live, cudaStream_t s) {
+  if (nkf == 0 || n == 0) return cudaSuccess;
+  const unsigned grid = grid_for(n, kThreads);
+  uint32_t* counter = reinterpret_cast<uint32_t*>(scratch + grid);
+  if (!err) err = reinterpret_cast<uint32_t*>(scratch + grid + 1);
+  auto* tot = reinterpret_cast<unsigned long long*>(total);
+  auto* lv = reinterpret_cast<unsigned long long*>(live);
+  if (k32)
+    launch_dep(k_scan_emit_pairs_batch<uint32_t>, dim3(grid), dim3(kThreads), s, t, nkf, rect, order, n, rank_bits,
+               capacity, static_cast<uint32_t*>(keys), overflow, scratch, counter, err, tot, lv);
+  else
+    launch_dep(k_scan_emit_pairs_batch<uint64_t>, dim3(grid), dim3(kThreads), s, t, nkf, rect, order, n, rank_bits,
+               capacity, static_cast<uint64_t*>(keys), overflow, scratch, counter, err, tot, lv);
   return cudaGetLastError();
 }
 
