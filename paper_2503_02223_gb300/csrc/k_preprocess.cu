@@ -62,7 +62,11 @@ __device__ __forceinline__ float dot3_plus(float a0, float m0, float a1, float m
   return __fadd_rn(s, lo);
 }
 
-// Same footprint computation for K1 and K8 (identical code path, identical rounding).
+// Same footprint computation for K1 and K8 (identical code path, identical rounding).  K8
+// passes kRect = false: it recomputes only what its chain rule reads and takes visibility
+// from K1's tile count, so it stops before the tile rect (visible once the mean and conic
+// are finite, as they were in K1).
+template <bool kRect = true>
 __device__ __forceinline__ void footprint(const RasterParams& rp, const float mean[3], const float ls[3],
                                           const float4 q4, float logit, Footprint& f) {
   f.visible = false;
@@ -121,6 +125,10 @@ __device__ __forceinline__ void footprint(const RasterParams& rp, const float me
   f.xy[0] = fmaf(rp.fx, x * iz, rp.cx);
   f.xy[1] = fmaf(rp.fy, y * iz, rp.cy);
   if (!isfinite(f.xy[0]) || !isfinite(f.xy[1]) || !isfinite(r)) return;
+  if (!kRect) {
+    f.visible = true;
+    return;
+  }
   // The rect's half-widths: the 3-sigma radius r, narrowed (alpha_min > 0) to the bounding
   // box of the ellipse q <= T' outside of which no pixel blends the Gaussian.  The blend
   // skips alpha < alpha_min and alpha <= opacity * G, so a blended pixel has
@@ -306,7 +314,7 @@ __device__ __forceinline__ void preprocess_backward_item(const PreBwdArgs& a, in
   }
   const RasterParams& rp = a.rp;
   Footprint f;
-  footprint(rp, mean, ls, q, logit, f);
+  footprint<false>(rp, mean, ls, q, logit, f);
   if (!f.visible) {
     zero_grads(a, i);
     return;
