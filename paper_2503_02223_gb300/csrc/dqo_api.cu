@@ -277,8 +277,8 @@ void dqo_destroy(dqo_ctx* c) {
   for (Buf* b : all)
     if (b->p) cudaFree(b->p);
   dqo_ctx::Batch& B = c->b;
-  Buf* ball[] = {&B.p0, &B.p1, &B.p2, &B.rect, &B.ntiles, &B.zkey_a, &B.zkey_b, &B.zval_a, &B.zval_b,
-                 &B.gid, &B.offsets, &B.grad2d, &B.scan_scratch, &B.depth_scan_scratch, &B.depth_hist, &B.hist,
+  Buf* ball[] = {&B.p0, &B.p1, &B.p2, &B.rect, &B.ntiles, &B.tile_count, &B.zkey_a, &B.zkey_b, &B.zval_a,
+                 &B.zval_b, &B.gid, &B.offsets, &B.grad2d, &B.scan_scratch, &B.depth_scan_scratch, &B.depth_hist, &B.hist,
                  &B.pair_a, &B.pair_b, &B.list, &B.ranges, &B.loss_part, &B.T_final, &B.n_contrib, &B.dl_rgb,
                  &B.dl_depth, &B.dl_ins, &B.counters, &B.tile_sched, &B.hitrec, &c->mlp_work};
   for (Buf* b : ball)
