@@ -59,17 +59,17 @@ MLP_FLOPS_PER_SAMPLE = 2 * (128 * 128 + 128 * 128 + 9 * 128) + 2 * (2 * 9 * 128 
 # projection: reads means 12, log-scales 12, quaternion 16, logit 4, rgb 12, id 4, flags 1;
 #   writes 3 x float4 48, rect 8, tiles 4, depth key 4, value 4, id 4        -> 133 B/Gaussian
 # depth sort: one histogram kernel reads the keys 4; 4 radix passes read key+value 8 and
-#   write 8; the scan of tiles per Gaussian in depth order reads the order 4 and the count
-#   4 and writes the offset 4                                                -> 80 B/Gaussian
-# binning: emission reads order 4, rect 8, offset 4 per Gaussian and writes 4 per pair; the
-#   pair sort covers the tile bits only: histogram read 4 + 2 passes of (read 4, write 4);
-#   ranges read key 4 and the order 4, write the list 4 per pair             -> 16 B/Gaussian + 36 B/pair
+#   write 8                                                                  -> 68 B/Gaussian
+# binning: the emission (which also scans the pair counts in depth order) reads order 4 and
+#   rect 8 per Gaussian and writes 4 per pair; the pair sort covers the tile bits only:
+#   histogram read 4 + 2 passes of (read 4, write 4); ranges read key 4 and the order 4,
+#   write the list 4 per pair                                                -> 12 B/Gaussian + 36 B/pair
 #   (the algorithmic minimum: write each pair's value once and read it once in the blend,
 #   8 B/pair, plus 16 B/Gaussian)
 # projection adjoint: reads the 10 inputs 61, tiles 4, moment record 48; read-modify-write of
 #   the 14 gradient floats 112                                              -> 225 B/Gaussian
 REF_BUDGET_S = 240.0   # the reference arm's K + W steps take about this long
-HBM_BYTES = {"project": (133, 0), "depth_sort": (80, 0), "binning": (16, 36), "project_bwd": (225, 0)}
+HBM_BYTES = {"project": (133, 0), "depth_sort": (68, 0), "binning": (12, 36), "project_bwd": (225, 0)}
 SORT_MIN_BYTES = (16, 8)
 MLP_TRAIN_SAMPLES = 1 << 20
 MLP_EPOCHS = 10
