@@ -72,7 +72,7 @@ REF_BUDGET_S = 240.0   # the reference arm's K + W steps take about this long
 HBM_BYTES = {"project": (133, 0), "depth_sort": (68, 0), "binning": (12, 36), "project_bwd": (225, 0)}
 SORT_MIN_BYTES = (16, 8)
 MLP_TRAIN_SAMPLES = 1 << 20
-MLP_EPOCHS = 10
+MLP_EPOCHS = 40
 MLP_BATCH = 4096
 
 
