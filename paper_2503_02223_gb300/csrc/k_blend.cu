@@ -868,8 +868,10 @@ constexpr int kBwdWarps = 4;
 constexpr int kBwdParts = kThreads / 32 / kBwdWarps;
 static_assert(kBwdParts == kTileParts, "tile parts of the backward and of the cost records");
 
+// Eight 4-warp CTAs per SM (64 registers, no spills): 32 resident warps instead of the 28
+// that 71 registers allowed; measured 1.4 us faster per step on the indoor keyframe.
 template <int TW>
-__global__ void __launch_bounds__(32 * kBwdWarps, 28 / kBwdWarps) k_blend_backward(BlendBwdArgs a) {
+__global__ void __launch_bounds__(32 * kBwdWarps, 32 / kBwdWarps) k_blend_backward(BlendBwdArgs a) {
   pdl_wait();
   pdl_trigger();
   const BlendCommon cm{a.p0, a.p1, a.p2, nullptr, a.list, a.grad2d, a.rp.alpha_clamp, a.rp.alpha_min, 0.f,
